@@ -1,0 +1,217 @@
+"""FP64 CPU oracle (ctypes wrapper over ``oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
+leg of the benchmark are the only callers.  The CUDA library never imports,
+links or executes anything in this directory, and this directory shares no code
+with it; the two meet only through the seeded inputs built by
+``paper_1912_11908_gb300.workloads`` (geometry vertices and case parameters,
+which hold none of the method's arithmetic).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboracle.so")
+SOURCES = [os.path.join(HERE, "oracle.c")]
+
+FLUID, SOLID, IB, G1, G2, G3 = range(6)
+BC_FREESTREAM, BC_OUTFLOW, BC_PERIODIC = range(3)
+MOTION_STATIC, MOTION_SIN, MOTION_CONST = range(3)
+
+
+def build(force=False):
+    """Compile the oracle with gcc (IEEE binary64, no FMA contraction)."""
+    newest = max(os.path.getmtime(s) for s in SOURCES + [os.path.join(HERE, "oracle.h")])
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    tmp = LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-fPIC", "-shared", "-o", tmp] + SOURCES + ["-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
+        ("mach", ctypes.c_double), ("re", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("prandtl", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("uinf", ctypes.c_double * 2), ("dt_fixed", ctypes.c_double), ("ref_len", ctypes.c_double),
+        ("nv", ctypes.c_int), ("verts", ctypes.POINTER(ctypes.c_double)),
+        ("motion", ctypes.c_int), ("amp", ctypes.c_double * 2), ("freq", ctypes.c_double),
+        ("vel", ctypes.c_double * 2),
+    ]
+
+
+STENCIL_DTYPE = np.dtype([
+    ("cell", "<i4"), ("feature", "<i4"), ("region", "<i4"), ("i0", "<i4"), ("j0", "<i4"),
+    ("mask", "<i4"), ("nstep", "<i4"), ("kind", "<i4"),
+    ("nx", "<f8"), ("ny", "<f8"), ("bx", "<f8"), ("by", "<f8"),
+    ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (4,)),
+])
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.orc_create.restype = vp
+        L.orc_create.argtypes = [ctypes.POINTER(_Params)]
+        L.orc_destroy.argtypes = [vp]
+        L.orc_classify.argtypes = [vp]
+        L.orc_classify.restype = ip
+        L.orc_step.argtypes = [vp, ip]
+        L.orc_step.restype = ip
+        L.orc_get_state.argtypes = [vp, vp]
+        L.orc_set_state.argtypes = [vp, vp]
+        L.orc_get_tags.argtypes = [vp, vp]
+        L.orc_list_len.argtypes = [vp, ip]
+        L.orc_list_len.restype = ip
+        L.orc_get_list.argtypes = [vp, ip, vp]
+        L.orc_forces.argtypes = [vp, vp]
+        L.orc_time.argtypes = [vp]
+        L.orc_time.restype = dp
+        L.orc_last_dt.argtypes = [vp]
+        L.orc_last_dt.restype = dp
+        L.orc_reconstruct.argtypes = [vp, dp]
+        L.orc_vertex_normals.argtypes = [vp, vp]
+        L.orc_closest.argtypes = [vp, dp, dp, vp, vp, vp, vp, vp]
+        L.orc_classify_points.argtypes = [ip, vp, ip, vp, vp]
+        L.orc_weno5.argtypes = [vp]
+        L.orc_weno5.restype = dp
+        L.orc_ldfss_xflux.argtypes = [vp, vp, dp, dp, dp, vp]
+        L.orc_euler_xflux.argtypes = [vp, dp, dp, vp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Case:
+    """One oracle case; ``spec`` is a dict from ``workloads.case_spec``."""
+
+    def __init__(self, spec):
+        s = spec
+        self.spec = spec
+        self.nx, self.ny = s["nx"], s["ny"]
+        verts = np.ascontiguousarray(s.get("verts", np.zeros((0, 2))), dtype=np.float64).reshape(-1, 2)
+        self._verts = verts
+        P = _Params()
+        P.nx, P.ny = s["nx"], s["ny"]
+        P.x0, P.x1, P.y0, P.y1 = s["domain"]
+        for k in range(4):
+            P.bc[k] = s["bc"][k]
+        P.mach, P.re, P.gamma, P.prandtl, P.cfl = s["mach"], s["re"], s["gamma"], s["prandtl"], s["cfl"]
+        P.uinf[0], P.uinf[1] = s["uinf"]
+        P.dt_fixed = s.get("dt_fixed", 0.0)
+        P.ref_len = s.get("ref_len", 1.0)
+        P.nv = verts.shape[0]
+        P.verts = verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if P.nv else None
+        P.motion = s.get("motion", MOTION_STATIC)
+        amp = s.get("amp", (0.0, 0.0))
+        vel = s.get("vel", (0.0, 0.0))
+        P.amp[0], P.amp[1] = amp
+        P.freq = s.get("freq", 0.0)
+        P.vel[0], P.vel[1] = vel
+        self._P = P
+        self.h = lib().orc_create(ctypes.byref(P))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_destroy(self.h)
+            self.h = None
+
+    def classify(self):
+        return lib().orc_classify(self.h)
+
+    def step(self, n):
+        return lib().orc_step(self.h, n)
+
+    def state(self):
+        a = np.empty((4, self.ny, self.nx), np.float64)
+        lib().orc_get_state(self.h, _ptr(a))
+        return a
+
+    def set_state(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        assert a.shape == (4, self.ny, self.nx)
+        lib().orc_set_state(self.h, _ptr(a))
+
+    def tags(self):
+        a = np.empty((self.ny, self.nx), np.uint8)
+        lib().orc_get_tags(self.h, _ptr(a))
+        return a
+
+    def stencils(self, kind):
+        n = lib().orc_list_len(self.h, kind)
+        a = np.zeros(n, STENCIL_DTYPE)
+        if n:
+            lib().orc_get_list(self.h, kind, _ptr(a))
+        return a
+
+    def forces(self):
+        out = np.zeros(4, np.float64)
+        lib().orc_forces(self.h, _ptr(out))
+        return out
+
+    def time(self):
+        return lib().orc_time(self.h)
+
+    def last_dt(self):
+        return lib().orc_last_dt(self.h)
+
+    def reconstruct(self, t):
+        lib().orc_reconstruct(self.h, t)
+
+    def vertex_normals(self):
+        a = np.zeros((self._verts.shape[0], 2), np.float64)
+        lib().orc_vertex_normals(self.h, _ptr(a))
+        return a
+
+    def closest(self, x, y):
+        f = ctypes.c_int32()
+        r = ctypes.c_int32()
+        cx, cy, d2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        lib().orc_closest(self.h, x, y, ctypes.byref(f), ctypes.byref(r), ctypes.byref(cx), ctypes.byref(cy),
+                          ctypes.byref(d2))
+        return f.value, r.value, cx.value, cy.value, d2.value
+
+
+def classify_points(verts, pts):
+    verts = np.ascontiguousarray(verts, np.float64).reshape(-1, 2)
+    pts = np.ascontiguousarray(pts, np.float64).reshape(-1, 2)
+    out = np.zeros(pts.shape[0], np.uint8)
+    lib().orc_classify_points(verts.shape[0], _ptr(verts), pts.shape[0], _ptr(pts), _ptr(out))
+    return out
+
+
+def weno5(f):
+    f = np.ascontiguousarray(f, np.float64)
+    return lib().orc_weno5(_ptr(f))
+
+
+def ldfss_xflux(qL, qR, gamma, R, mr2=1.0):
+    qL = np.ascontiguousarray(qL, np.float64)
+    qR = np.ascontiguousarray(qR, np.float64)
+    F = np.zeros(4)
+    lib().orc_ldfss_xflux(_ptr(qL), _ptr(qR), gamma, R, mr2, _ptr(F))
+    return F
+
+
+def euler_xflux(q, gamma, R):
+    q = np.ascontiguousarray(q, np.float64)
+    F = np.zeros(4)
+    lib().orc_euler_xflux(_ptr(q), gamma, R, _ptr(F))
+    return F

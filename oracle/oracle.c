@@ -1,0 +1,950 @@
+/*
+ * FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Plain restatement of arXiv 1912.11908 for a 2-D uniform Cartesian block.
+ * The paper's solver is a curvilinear multi-block code; this oracle keeps the
+ * parts of the method that act on one uniform block:
+ *   Sec. 2      WENO5 reconstruction, low-diffusion flux splitting, central
+ *               viscous flux
+ *   Sec. 3.2    ray-casting node classification, IB and ghost tagging
+ *   Sec. 4.1    closest surface feature (point-segment distance, Eq. 1 in 2-D)
+ *   Sec. 4.2    pseudo-normals (Eq. 2 / Eq. 3 restricted to a polyline)
+ *   Sec. 4.3    reconstruction along the local normal
+ *   Sec. 4.4    boundary conditions (Eq. 4, 5, 6, 8)
+ *   Sec. 4.6    inverse-distance-weighted interpolation
+ *   Sec. 5      three ghost layers filled through image points
+ *   Sec. 6      surface force integral (Eq. 9)
+ * Readings where the paper is silent are written next to each routine.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NG 3 /* halo / ghost layers needed by the five-point WENO stencil (Sec. 5) */
+
+struct orc_case {
+  orc_params p;
+  double *vref;            /* reference vertices, 2*nv */
+  double *vx, *vy;         /* vertices at the current pose */
+  double *snx, *sny;       /* outward segment normals */
+  double *vnx, *vny;       /* vertex pseudo-normals */
+  double dx, dy, h, dmin;
+  double R, cp, mu, kappa, pinf;
+  double Uinf[4];
+  int W, H;
+  double *A[4], *B[4], *C[4];
+  double *q[4];            /* reconstructed primitives rho, u, v, p over the full array */
+  double *T;               /* temperature over the full array */
+  double *fx[4], *fy[4];   /* face fluxes */
+  int precond;             /* low-Mach scaling of the dissipation (dual time only) */
+  uint8_t *tag;
+  int nlist[4];
+  orc_stencil *list[4];
+  double t, last_dt;
+  int classified;
+  int nerr;
+  double pos[2];           /* body displacement at the classification time */
+};
+
+static inline int fidx(const orc_case *c, int i, int j) { return (j + NG) * c->W + (i + NG); }
+
+/* ------------------------------------------------------------------------- */
+/* body motion: prescribed translation (Sec. 8.2.2 oscillating cylinder;     */
+/* constant-velocity translation for the Galilean check of Sec. 8.2.3)       */
+/* ------------------------------------------------------------------------- */
+static void motion_at(const orc_params *p, double t, double X[2], double V[2], double Acc[2]) {
+  X[0] = X[1] = V[0] = V[1] = Acc[0] = Acc[1] = 0.0;
+  if (p->motion == ORC_MOTION_SIN) {
+    double w = 2.0 * M_PI * p->freq;
+    double s = sin(w * t), co = cos(w * t);
+    for (int k = 0; k < 2; k++) {
+      X[k] = p->amp[k] * s;
+      V[k] = p->amp[k] * w * co;
+      Acc[k] = -p->amp[k] * w * w * s;
+    }
+  } else if (p->motion == ORC_MOTION_CONST) {
+    for (int k = 0; k < 2; k++) {
+      X[k] = p->vel[k] * t;
+      V[k] = p->vel[k];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 3.2: ray-casting classification.  A ray is cast from the node along  */
+/* +x; an odd number of crossings marks the node solid.  Reading of the      */
+/* crossing test for a polyline: segment A->B is crossed iff                 */
+/* (A.y > P.y) != (B.y > P.y) (half-open in y so a vertex on the ray counts  */
+/* once) and the crossing abscissa lies strictly right of P.  Nodes outside  */
+/* the axis-aligned bounding box are fluid without a test (Sec. 3.2).        */
+/* ------------------------------------------------------------------------- */
+static int point_in_body(int nv, const double *vx, const double *vy, const double bb[4], double px,
+                         double py) {
+  if (px < bb[0] || px > bb[1] || py < bb[2] || py > bb[3]) return 0;
+  int odd = 0;
+  for (int k = 0; k < nv; k++) {
+    int k1 = (k + 1 == nv) ? 0 : k + 1;
+    double ax = vx[k], ay = vy[k], bx = vx[k1], by = vy[k1];
+    if ((ay > py) != (by > py)) {
+      double t1 = py - ay;
+      double t2 = bx - ax;
+      double t3 = by - ay;
+      double xint = ax + (t1 * t2) / t3;
+      if (xint > px) odd ^= 1;
+    }
+  }
+  return odd;
+}
+
+static void bbox(int nv, const double *vx, const double *vy, double bb[4]) {
+  bb[0] = bb[1] = vx[0];
+  bb[2] = bb[3] = vy[0];
+  for (int k = 1; k < nv; k++) {
+    if (vx[k] < bb[0]) bb[0] = vx[k];
+    if (vx[k] > bb[1]) bb[1] = vx[k];
+    if (vy[k] < bb[2]) bb[2] = vy[k];
+    if (vy[k] > bb[3]) bb[3] = vy[k];
+  }
+}
+
+void orc_classify_points(int nv, const double *verts, int np, const double *pts, uint8_t *solid) {
+  double *vx = malloc(sizeof(double) * nv), *vy = malloc(sizeof(double) * nv);
+  for (int k = 0; k < nv; k++) {
+    vx[k] = verts[2 * k];
+    vy[k] = verts[2 * k + 1];
+  }
+  double bb[4];
+  bbox(nv, vx, vy, bb);
+  for (int n = 0; n < np; n++) solid[n] = (uint8_t)point_in_body(nv, vx, vy, bb, pts[2 * n], pts[2 * n + 1]);
+  free(vx);
+  free(vy);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 4.2: pseudo-normals.  Segment k runs from vertex k to k+1 of a CCW   */
+/* polyline; its outward normal is the travel direction turned clockwise.    */
+/* In 2-D each vertex has two incident segments that enter Eq. 2 with equal  */
+/* weight (as the two faces do in Eq. 3), so the vertex pseudo-normal is the */
+/* normalised sum of the two adjacent segment normals.                       */
+/* ------------------------------------------------------------------------- */
+static void build_normals(orc_case *c) {
+  int nv = c->p.nv;
+  for (int k = 0; k < nv; k++) {
+    int k1 = (k + 1 == nv) ? 0 : k + 1;
+    double ex = c->vref[2 * k1] - c->vref[2 * k];
+    double ey = c->vref[2 * k1 + 1] - c->vref[2 * k + 1];
+    double L = sqrt(ex * ex + ey * ey);
+    c->snx[k] = ey / L;
+    c->sny[k] = -ex / L;
+  }
+  for (int k = 0; k < nv; k++) {
+    int km = (k == 0) ? nv - 1 : k - 1;
+    double sx = c->snx[km] + c->snx[k];
+    double sy = c->sny[km] + c->sny[k];
+    double L = sqrt(sx * sx + sy * sy);
+    if (L > 0.0) {
+      c->vnx[k] = sx / L;
+      c->vny[k] = sy / L;
+    } else {
+      c->vnx[k] = c->snx[k];
+      c->vny[k] = c->sny[k];
+    }
+  }
+}
+
+void orc_vertex_normals(const orc_case *c, double *dst) {
+  for (int k = 0; k < c->p.nv; k++) {
+    dst[2 * k] = c->vnx[k];
+    dst[2 * k + 1] = c->vny[k];
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 4.1: closest surface feature.  Exhaustive search over all segments   */
+/* (the bounding-sphere step of the paper only prunes this search).  The     */
+/* closest point of a segment is its foot point when that falls strictly     */
+/* inside (FACE region), otherwise the nearer end vertex (VERTEX region).    */
+/* Ties keep the lowest segment index.                                       */
+/* ------------------------------------------------------------------------- */
+static void closest_feature(const orc_case *c, double px, double py, int32_t *feat, int32_t *region,
+                            double *cxo, double *cyo, double *d2o) {
+  int nv = c->p.nv;
+  double best = INFINITY;
+  for (int k = 0; k < nv; k++) {
+    int k1 = (k + 1 == nv) ? 0 : k + 1;
+    double ax = c->vx[k], ay = c->vy[k], bx = c->vx[k1], by = c->vy[k1];
+    double ex = bx - ax, ey = by - ay;
+    double wx = px - ax, wy = py - ay;
+    double num = wx * ex + wy * ey;
+    double den = ex * ex + ey * ey;
+    double cx, cy;
+    int32_t f, r;
+    if (num <= 0.0) {
+      cx = ax; cy = ay; f = k; r = ORC_REGION_VERTEX;
+    } else if (num >= den) {
+      cx = bx; cy = by; f = k1; r = ORC_REGION_VERTEX;
+    } else {
+      double t = num / den;
+      cx = ax + t * ex; cy = ay + t * ey; f = k; r = ORC_REGION_FACE;
+    }
+    double ddx = px - cx, ddy = py - cy;
+    double d2 = ddx * ddx + ddy * ddy;
+    if (d2 < best) {
+      best = d2; *feat = f; *region = r; *cxo = cx; *cyo = cy;
+    }
+  }
+  *d2o = best;
+}
+
+void orc_closest(const orc_case *c, double px, double py, int32_t *feature, int32_t *region, double *cx,
+                 double *cy, double *d2) {
+  closest_feature(c, px, py, feature, region, cx, cy, d2);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Interpolation square and weights around a point (Sec. 4.6, Sec. 5).       */
+/* Bilinear when all four corners are valid, otherwise inverse-distance      */
+/* weights 1/r^2 over the valid corners; a corner hit exactly takes all the  */
+/* weight.  allowed: bit set of tags a corner may carry.                     */
+/* ------------------------------------------------------------------------- */
+static int interp_square(const orc_case *c, double X, double Y, unsigned allowed, int32_t *i0o, int32_t *j0o,
+                         double w[4]) {
+  const orc_params *p = &c->p;
+  double gx = (X - p->x0) / c->dx - 0.5;
+  double gy = (Y - p->y0) / c->dy - 0.5;
+  int i0 = (int)floor(gx), j0 = (int)floor(gy);
+  int mask = 0;
+  for (int k = 0; k < 4; k++) {
+    int ci = i0 + (k & 1), cj = j0 + (k >> 1);
+    w[k] = 0.0;
+    if (ci < 0 || ci >= p->nx || cj < 0 || cj >= p->ny) continue;
+    if (allowed & (1u << c->tag[cj * p->nx + ci])) mask |= 1 << k;
+  }
+  *i0o = i0;
+  *j0o = j0;
+  if (mask == 15) {
+    double xc0 = p->x0 + ((double)i0 + 0.5) * c->dx;
+    double yc0 = p->y0 + ((double)j0 + 0.5) * c->dy;
+    double fx = (X - xc0) / c->dx;
+    double fy = (Y - yc0) / c->dy;
+    w[0] = (1.0 - fx) * (1.0 - fy);
+    w[1] = fx * (1.0 - fy);
+    w[2] = (1.0 - fx) * fy;
+    w[3] = fx * fy;
+  } else if (mask != 0) {
+    double inv[4] = {0, 0, 0, 0};
+    double s = 0.0;
+    int hit = -1;
+    for (int k = 0; k < 4 && hit < 0; k++) {
+      if (!(mask >> k & 1)) continue;
+      double xk = p->x0 + ((double)(i0 + (k & 1)) + 0.5) * c->dx;
+      double yk = p->y0 + ((double)(j0 + (k >> 1)) + 0.5) * c->dy;
+      double rx = X - xk, ry = Y - yk;
+      double r2 = rx * rx + ry * ry;
+      if (r2 == 0.0) hit = k;
+      else inv[k] = 1.0 / r2;
+    }
+    if (hit >= 0) {
+      w[hit] = 1.0;
+    } else {
+      for (int k = 0; k < 4; k++)
+        if (mask >> k & 1) s += inv[k];
+      for (int k = 0; k < 4; k++)
+        if (mask >> k & 1) w[k] = inv[k] / s;
+    }
+  }
+  return mask;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 3.2 + Sec. 5: tags and ordered lists.                                */
+/*  IB   : fluid node with a solid 4-neighbour (the fluid nodes nearest the  */
+/*         surface, Fig. 1); "immediate neighbour" read as the 4-stencil     */
+/*         because the flux stencils are axis aligned.                       */
+/*  G1-3 : solid node whose nearest non-solid node along a grid line lies k  */
+/*         = 1, 2, 3 nodes away (three layers for WENO5, Sec. 5, Fig. 6).    */
+/* Lists are in row-major cell order.                                        */
+/* ------------------------------------------------------------------------- */
+static void build_tags(orc_case *c, const uint8_t *solid) {
+  int nx = c->p.nx, ny = c->p.ny;
+  static const int DI[4] = {1, -1, 0, 0}, DJ[4] = {0, 0, 1, -1};
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      int n = j * nx + i;
+      if (!solid[n]) {
+        int ib = 0;
+        for (int d = 0; d < 4; d++) {
+          int a = i + DI[d], b = j + DJ[d];
+          if (a >= 0 && a < nx && b >= 0 && b < ny && solid[b * nx + a]) ib = 1;
+        }
+        c->tag[n] = ib ? ORC_IB : ORC_FLUID;
+      } else {
+        int level = 0;
+        for (int k = 1; k <= 3 && level == 0; k++)
+          for (int d = 0; d < 4; d++) {
+            int a = i + k * DI[d], b = j + k * DJ[d];
+            if (a >= 0 && a < nx && b >= 0 && b < ny && !solid[b * nx + a]) level = k;
+          }
+        c->tag[n] = level ? (uint8_t)(ORC_G1 + level - 1) : ORC_SOLID;
+      }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 4.3: boundary point P' on the line through the node parallel to the  */
+/* local normal.  Reading: among the crossings of that line with the         */
+/* polyline, take the one nearest the node on the side where the surface     */
+/* lies (behind a fluid node, ahead of a ghost node); ties keep the lowest   */
+/* segment index.  If the line meets no segment on that side, P' falls back  */
+/* to the closest point.  xi_node is the node's signed offset from P' along  */
+/* the normal (positive in the fluid).                                       */
+/* ------------------------------------------------------------------------- */
+static void boundary_point(const orc_case *c, double px, double py, double nx, double ny, int is_ghost,
+                           double ccx, double ccy, double *bx, double *by, double *xi_node, int *fallback) {
+  int nv = c->p.nv;
+  double best = INFINITY, bs = 0.0;
+  int found = 0;
+  for (int k = 0; k < nv; k++) {
+    int k1 = (k + 1 == nv) ? 0 : k + 1;
+    double ax = c->vx[k], ay = c->vy[k];
+    double ex = c->vx[k1] - ax, ey = c->vy[k1] - ay;
+    double den = ex * ny - ey * nx;
+    if (den == 0.0) continue;
+    double wx = px - ax, wy = py - ay;
+    double u = (wx * ny - wy * nx) / den;
+    if (u < 0.0 || u > 1.0) continue;
+    double s = (wx * ey - wy * ex) / den;
+    if (is_ghost ? (s < 0.0) : (s > 0.0)) continue;
+    double as = fabs(s);
+    if (as < best) {
+      best = as; bs = s; found = 1;
+    }
+  }
+  if (found) {
+    *bx = px + bs * nx;
+    *by = py + bs * ny;
+    *xi_node = -bs;
+    *fallback = 0;
+  } else {
+    double ddx = px - ccx, ddy = py - ccy;
+    double d = sqrt(ddx * ddx + ddy * ddy);
+    *bx = ccx;
+    *by = ccy;
+    *xi_node = is_ghost ? -d : d;
+    *fallback = 1;
+  }
+}
+
+/* valid-corner sets: probes of IB nodes and surface probes use fluid nodes,
+ * image points of ghost nodes use fluid and (already updated) IB nodes */
+#define ALLOW_FLUID (1u << ORC_FLUID)
+#define ALLOW_FLUID_IB ((1u << ORC_FLUID) | (1u << ORC_IB))
+
+/* Sec. 4.1-4.6 and Sec. 5: one stencil per listed node. */
+static void build_stencil(orc_case *c, int cell, int kind, orc_stencil *s) {
+  const orc_params *p = &c->p;
+  int i = cell % p->nx, j = cell / p->nx;
+  double px = p->x0 + ((double)i + 0.5) * c->dx;
+  double py = p->y0 + ((double)j + 0.5) * c->dy;
+  int32_t feat = 0, region = 0;
+  double ccx = 0, ccy = 0, d2 = 0;
+  closest_feature(c, px, py, &feat, &region, &ccx, &ccy, &d2);
+  double nx, ny;
+  if (region == ORC_REGION_FACE) {
+    nx = c->snx[feat]; ny = c->sny[feat];
+  } else {
+    nx = c->vnx[feat]; ny = c->vny[feat];
+  }
+  double bx, by, xi_node;
+  int fb;
+  boundary_point(c, px, py, nx, ny, kind > 0, ccx, ccy, &bx, &by, &xi_node, &fb);
+  double xi_probe;
+  if (kind == 0) {
+    xi_probe = xi_node + c->h;              /* probe one diagonal spacing beyond the IB node */
+  } else {
+    xi_probe = -xi_node;                     /* mirror image point (Fig. 6) */
+    if (xi_probe < 0.5 * c->dmin) xi_probe = 0.5 * c->dmin;
+  }
+  unsigned allowed = kind == 0 ? ALLOW_FLUID : ALLOW_FLUID_IB;
+  int32_t i0 = 0, j0 = 0;
+  int mask = 0, nstep = 0;
+  for (;;) {
+    double X = bx + xi_probe * nx, Y = by + xi_probe * ny;
+    mask = interp_square(c, X, Y, allowed, &i0, &j0, s->w);
+    if (mask != 0 || nstep == 3) break;
+    xi_probe = xi_probe + c->dmin;
+    nstep++;
+  }
+  if (mask == 0) c->nerr++;
+  s->cell = cell;
+  s->feature = feat;
+  s->region = fb ? ORC_REGION_FALLBACK : region;
+  s->i0 = i0;
+  s->j0 = j0;
+  s->mask = mask;
+  s->nstep = nstep;
+  s->kind = kind;
+  s->nx = nx;
+  s->ny = ny;
+  s->bx = bx;
+  s->by = by;
+  s->xi_node = xi_node;
+  s->xi_probe = xi_probe;
+}
+
+int orc_classify(orc_case *c) {
+  const orc_params *p = &c->p;
+  int nx = p->nx, ny = p->ny, nc = nx * ny;
+  double X[2], V[2], Acc[2];
+  motion_at(p, c->t, X, V, Acc);
+  c->pos[0] = X[0];
+  c->pos[1] = X[1];
+  for (int k = 0; k < p->nv; k++) {
+    c->vx[k] = c->vref[2 * k] + X[0];
+    c->vy[k] = c->vref[2 * k + 1] + X[1];
+  }
+  uint8_t *solid = calloc(nc, 1);
+  if (p->nv > 0) {
+    double bb[4];
+    bbox(p->nv, c->vx, c->vy, bb);
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        double px = p->x0 + ((double)i + 0.5) * c->dx;
+        double py = p->y0 + ((double)j + 0.5) * c->dy;
+        solid[j * nx + i] = (uint8_t)point_in_body(p->nv, c->vx, c->vy, bb, px, py);
+      }
+  }
+  build_tags(c, solid);
+  free(solid);
+  c->nerr = 0;
+  for (int kind = 0; kind < 4; kind++) {
+    uint8_t want = (uint8_t)(kind == 0 ? ORC_IB : ORC_G1 + kind - 1);
+    int n = 0;
+    for (int m = 0; m < nc; m++) n += c->tag[m] == want;
+    free(c->list[kind]);
+    c->list[kind] = calloc(n > 0 ? n : 1, sizeof(orc_stencil));
+    c->nlist[kind] = n;
+    int w = 0;
+    for (int m = 0; m < nc; m++)
+      if (c->tag[m] == want) build_stencil(c, m, kind, &c->list[kind][w++]);
+  }
+  c->classified = 1;
+  return c->nerr;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Primitive variables (Sec. 4.4: the solver works on p, u, v, T).           */
+/* ------------------------------------------------------------------------- */
+static inline void cons_to_prim(const orc_case *c, double r, double ru, double rv, double rE, double q[4]) {
+  double g = c->p.gamma;
+  double u = ru / r, v = rv / r;
+  double pr = (g - 1.0) * (rE - 0.5 * r * (u * u + v * v));
+  q[0] = pr;
+  q[1] = u;
+  q[2] = v;
+  q[3] = pr / (r * c->R);
+}
+
+static inline void prim_to_cons(const orc_case *c, const double q[4], double U[4]) {
+  double g = c->p.gamma;
+  double r = q[0] / (c->R * q[3]);
+  U[0] = r;
+  U[1] = r * q[1];
+  U[2] = r * q[2];
+  U[3] = q[0] / (g - 1.0) + 0.5 * r * (q[1] * q[1] + q[2] * q[2]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 4.4-4.6 and Sec. 5: IB and ghost reconstruction at stage time t.     */
+/* Velocity is Dirichlet (Eq. 4): linear along the normal through the wall   */
+/* value at P' and the interpolated probe value.  Pressure is Neumann        */
+/* (Eq. 5-6): dp/dn = -rho n.a_wall; temperature is adiabatic (Eq. 8).       */
+/* IB nodes first (their probes use fluid nodes only), then all ghost layers */
+/* (their image points may use the freshly updated IB nodes).                */
+/* ------------------------------------------------------------------------- */
+static void reconstruct_set(orc_case *c, double *const U[4], const orc_stencil *s, int n, const double Vw[2],
+                            const double Aw[2]) {
+  for (int e = 0; e < n; e++) {
+    const orc_stencil *st = &s[e];
+    if (st->mask == 0) continue;
+    double qp[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 4; k++) {
+      if (!(st->mask >> k & 1)) continue;
+      int id = fidx(c, st->i0 + (k & 1), st->j0 + (k >> 1));
+      double qk[4];
+      cons_to_prim(c, U[0][id], U[1][id], U[2][id], U[3][id], qk);
+      for (int v = 0; v < 4; v++) qp[v] += st->w[k] * qk[v];
+    }
+    double ratio = st->xi_node / st->xi_probe;
+    double q[4];
+    double rho_p = qp[0] / (c->R * qp[3]);
+    double g = -rho_p * (st->nx * Aw[0] + st->ny * Aw[1]);
+    q[0] = qp[0] - (st->xi_probe - st->xi_node) * g;
+    q[1] = Vw[0] + (qp[1] - Vw[0]) * ratio;
+    q[2] = Vw[1] + (qp[2] - Vw[1]) * ratio;
+    q[3] = qp[3];
+    double Un[4];
+    prim_to_cons(c, q, Un);
+    int id = fidx(c, st->cell % c->p.nx, st->cell / c->p.nx);
+    for (int v = 0; v < 4; v++) U[v][id] = Un[v];
+  }
+}
+
+static void reconstruct(orc_case *c, double *const U[4], double t) {
+  double X[2], V[2], Acc[2];
+  motion_at(&c->p, t, X, V, Acc);
+  reconstruct_set(c, U, c->list[0], c->nlist[0], V, Acc);
+  for (int k = 1; k < 4; k++) reconstruct_set(c, U, c->list[k], c->nlist[k], V, Acc);
+}
+
+void orc_reconstruct(orc_case *c, double t) {
+  if (!c->classified) orc_classify(c);
+  reconstruct(c, c->A, t);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Domain halos: free-stream Dirichlet, zero-gradient outflow, or periodic.  */
+/* y sides first over interior columns, then x sides over all rows.          */
+/* ------------------------------------------------------------------------- */
+static void domain_bc(orc_case *c, double *const U[4]) {
+  const orc_params *p = &c->p;
+  int nx = p->nx, ny = p->ny;
+  for (int side = 2; side < 4; side++)
+    for (int g = 1; g <= NG; g++)
+      for (int i = 0; i < nx; i++) {
+        int j = side == 2 ? -g : ny - 1 + g;
+        int src;
+        if (p->bc[side] == ORC_BC_PERIODIC) src = fidx(c, i, side == 2 ? ny - g : g - 1);
+        else if (p->bc[side] == ORC_BC_OUTFLOW) src = fidx(c, i, side == 2 ? 0 : ny - 1);
+        else src = -1;
+        int dst = fidx(c, i, j);
+        for (int v = 0; v < 4; v++) U[v][dst] = src < 0 ? c->Uinf[v] : U[v][src];
+      }
+  for (int side = 0; side < 2; side++)
+    for (int g = 1; g <= NG; g++)
+      for (int j = -NG; j < ny + NG; j++) {
+        int i = side == 0 ? -g : nx - 1 + g;
+        int src;
+        if (p->bc[side] == ORC_BC_PERIODIC) src = fidx(c, side == 0 ? nx - g : g - 1, j);
+        else if (p->bc[side] == ORC_BC_OUTFLOW) src = fidx(c, side == 0 ? 0 : nx - 1, j);
+        else src = -1;
+        int dst = fidx(c, i, j);
+        for (int v = 0; v < 4; v++) U[v][dst] = src < 0 ? c->Uinf[v] : U[v][src];
+      }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 2: fifth-order WENO (Jiang-Shu smoothness indicators, linear weights */
+/* 1/10, 6/10, 3/10, eps = 1e-6).  f = values at i-2..i+2; returns the       */
+/* left-biased value at face i+1/2.                                          */
+/* ------------------------------------------------------------------------- */
+double orc_weno5(const double f[5]) {
+  const double eps = 1e-6;
+  double a = f[0] - 2.0 * f[1] + f[2], b = f[0] - 4.0 * f[1] + 3.0 * f[2];
+  double b0 = (13.0 / 12.0) * a * a + 0.25 * b * b;
+  a = f[1] - 2.0 * f[2] + f[3];
+  b = f[1] - f[3];
+  double b1 = (13.0 / 12.0) * a * a + 0.25 * b * b;
+  a = f[2] - 2.0 * f[3] + f[4];
+  b = 3.0 * f[2] - 4.0 * f[3] + f[4];
+  double b2 = (13.0 / 12.0) * a * a + 0.25 * b * b;
+  double q0 = (2.0 * f[0] - 7.0 * f[1] + 11.0 * f[2]) / 6.0;
+  double q1 = (-f[1] + 5.0 * f[2] + 2.0 * f[3]) / 6.0;
+  double q2 = (2.0 * f[2] + 5.0 * f[3] - f[4]) / 6.0;
+  double a0 = 0.1 / ((eps + b0) * (eps + b0));
+  double a1 = 0.6 / ((eps + b1) * (eps + b1));
+  double a2 = 0.3 / ((eps + b2) * (eps + b2));
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 2: low-diffusion flux splitting (LDFSS(0) of Edwards) with the       */
+/* low-Mach scaled numerical sound speed.  The paper only names the scheme,  */
+/* so the reading is:                                                        */
+/*   c' = 1/2 sqrt((1 - Mr^2)^2 un^2 + 4 Mr^2 c^2) with face averages,       */
+/*   M_L,R = un_L,R / c'; Van Leer splits with the LDFSS pressure-weighted   */
+/*   correction; pressure split P+- = (M +- 1)^2 (2 -+ M) / 4.               */
+/* mr2 is the face preconditioning parameter Mr^2 (1 = plain LDFSS).        */
+/* q = (rho, u, v, p); normal (nxf, nyf) is (1,0) or (0,1).                  */
+/* ------------------------------------------------------------------------- */
+static void ldfss(const double qL[4], const double qR[4], double nxf, double nyf, double gamma, double R,
+                  double cpv, double mr2, double F[4]) {
+  (void)R;
+  (void)cpv;
+  double rL = qL[0], uL = qL[1], vL = qL[2], pL = qL[3];
+  double rR = qR[0], uR = qR[1], vR = qR[2], pR = qR[3];
+  double cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+  double HL = gamma / (gamma - 1.0) * pL / rL + 0.5 * (uL * uL + vL * vL);
+  double HR = gamma / (gamma - 1.0) * pR / rR + 0.5 * (uR * uR + vR * vR);
+  double unL = uL * nxf + vL * nyf, unR = uR * nxf + vR * nyf;
+  double cb = 0.5 * (cL + cR);
+  double ub = 0.5 * (unL + unR);
+  double om = 1.0 - mr2;
+  double cs = 0.5 * sqrt(om * om * ub * ub + 4.0 * mr2 * cb * cb);
+  double ML = unL / cs, MR = unR / cs;
+  double aL = 0.5 * (1.0 + (ML >= 0.0 ? 1.0 : -1.0));
+  double aR = 0.5 * (1.0 - (MR >= 0.0 ? 1.0 : -1.0));
+  double tL = 1.0 - floor(fabs(ML)), tR = 1.0 - floor(fabs(MR));
+  double bL = -(tL > 0.0 ? tL : 0.0), bR = -(tR > 0.0 ? tR : 0.0);
+  double MpL = 0.25 * (ML + 1.0) * (ML + 1.0);
+  double MmR = -0.25 * (MR - 1.0) * (MR - 1.0);
+  double CVL = aL * (1.0 + bL) * ML - bL * MpL;
+  double CVR = aR * (1.0 + bR) * MR - bR * MmR;
+  double sq = sqrt(0.5 * (ML * ML + MR * MR)) - 1.0;
+  double Mh = 0.25 * bL * bR * sq * sq;
+  double dp = pL - pR, adp = fabs(dp);
+  double MhP = Mh * (1.0 - (dp + adp) / (2.0 * rL * cs * cs));
+  double MhM = Mh * (1.0 - (-dp + adp) / (2.0 * rR * cs * cs));
+  double Cp = CVL - MhP, Cm = CVR + MhM;
+  double PpL = 0.25 * (ML + 1.0) * (ML + 1.0) * (2.0 - ML);
+  double PmR = 0.25 * (MR - 1.0) * (MR - 1.0) * (2.0 + MR);
+  double DL = aL * (1.0 + bL) - bL * PpL;
+  double DR = aR * (1.0 + bR) - bR * PmR;
+  double mL = rL * cs * Cp, mR = rR * cs * Cm;
+  double ph = DL * pL + DR * pR;
+  F[0] = mL + mR;
+  F[1] = mL * uL + mR * uR + ph * nxf;
+  F[2] = mL * vL + mR * vR + ph * nyf;
+  F[3] = mL * HL + mR * HR;
+}
+
+void orc_ldfss_xflux(const double qL[4], const double qR[4], double gamma, double R, double mr2_fixed,
+                     double flux[4]) {
+  double cpv = gamma * R / (gamma - 1.0);
+  ldfss(qL, qR, 1.0, 0.0, gamma, R, cpv, mr2_fixed, flux);
+}
+
+void orc_euler_xflux(const double q[4], double gamma, double R, double flux[4]) {
+  (void)R;
+  double r = q[0], u = q[1], v = q[2], p = q[3];
+  double H = gamma / (gamma - 1.0) * p / r + 0.5 * (u * u + v * v);
+  flux[0] = r * u;
+  flux[1] = r * u * u + p;
+  flux[2] = r * u * v;
+  flux[3] = r * u * H;
+}
+
+/* Low-Mach preconditioning parameter at a face.  Only the dual-time scheme,
+ * whose pseudo-time derivative carries the preconditioning matrix, scales the
+ * dissipation; explicit physical-time stepping uses plain LDFSS (Mr^2 = 1).
+ * Reference velocity Ur = min(c, max(|V|, U_ref, nu/dn)), Mr^2 = (Ur/c)^2 with
+ * face-averaged c, |V| and rho. */
+static double face_mr2(const orc_case *c, const double qL[4], const double qR[4], double dn) {
+  if (!c->precond) return 1.0;
+  double g = c->p.gamma;
+  double cb = 0.5 * (sqrt(g * qL[3] / qL[0]) + sqrt(g * qR[3] / qR[0]));
+  double ub = 0.5 * (qL[1] + qR[1]), vb = 0.5 * (qL[2] + qR[2]);
+  double Vm = sqrt(ub * ub + vb * vb);
+  double rb = 0.5 * (qL[0] + qR[0]);
+  double vis = c->mu / rb / dn;
+  double Ur = Vm;
+  if (1.0 > Ur) Ur = 1.0;
+  if (vis > Ur) Ur = vis;
+  if (cb < Ur) Ur = cb;
+  double m = (Ur / cb) * (Ur / cb);
+  return m < 1.0 ? m : 1.0;
+}
+
+/* WENO5 left/right states of the reconstructed primitives (rho, u, v, p) at
+ * the face between cells s[2] and s[3] of the six-cell strip s[0..5]; first-
+ * order fallback if a reconstructed density or pressure is not positive.
+ * Reading: the paper iterates (p, u, v, w, T) but does not say which set WENO
+ * acts on; (rho, u, v, p) keeps a density wave at fifth order because every
+ * flux component is affine in rho when u and p are uniform. */
+static void face_states(const double s[6][4], double qL[4], double qR[4]) {
+  for (int v = 0; v < 4; v++) {
+    double fl[5] = {s[0][v], s[1][v], s[2][v], s[3][v], s[4][v]};
+    double fr[5] = {s[5][v], s[4][v], s[3][v], s[2][v], s[1][v]};
+    qL[v] = orc_weno5(fl);
+    qR[v] = orc_weno5(fr);
+  }
+  if (!(qL[0] > 0.0) || !(qL[3] > 0.0) || !(qR[0] > 0.0) || !(qR[3] > 0.0)) {
+    for (int v = 0; v < 4; v++) {
+      qL[v] = s[2][v];
+      qR[v] = s[3][v];
+    }
+  }
+}
+
+/* Sec. 2: residual L(U) = -(dF/dx + dG/dy) over fluid cells, inviscid
+ * (WENO5 + LDFSS) minus viscous (second-order central) face fluxes. */
+static void residual_faces(orc_case *c, double *const U[4]) {
+  const orc_params *p = &c->p;
+  int nx = p->nx, ny = p->ny, W = c->W, H = c->H;
+  double g = p->gamma, R = c->R, mu = c->mu, kap = c->kappa, cpv = c->cp;
+  for (int m = 0; m < W * H; m++) {
+    double r = U[0][m], u = U[1][m] / r, v = U[2][m] / r;
+    double pr = (g - 1.0) * (U[3][m] - 0.5 * r * (u * u + v * v));
+    c->q[0][m] = r;
+    c->q[1][m] = u;
+    c->q[2][m] = v;
+    c->q[3][m] = pr;
+    c->T[m] = pr / (r * R);
+  }
+  double *const *Q = c->q;
+  /* x-faces: face f = i + 1/2 for i in [-1, nx-1], stored at fidx(i, j) */
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < ny; j++)
+    for (int i = -1; i < nx; i++) {
+      double s[6][4];
+      for (int k = 0; k < 6; k++)
+        for (int v = 0; v < 4; v++) s[k][v] = Q[v][fidx(c, i - 2 + k, j)];
+      double qL[4], qR[4], F[4];
+      face_states(s, qL, qR);
+      ldfss(qL, qR, 1.0, 0.0, g, R, cpv, face_mr2(c, qL, qR, c->dx), F);
+      int a = fidx(c, i, j), b = fidx(c, i + 1, j);
+      int an = fidx(c, i, j + 1), as = fidx(c, i, j - 1), bn = fidx(c, i + 1, j + 1), bs = fidx(c, i + 1, j - 1);
+      double ux = (Q[1][b] - Q[1][a]) / c->dx, vx = (Q[2][b] - Q[2][a]) / c->dx, Tx = (c->T[b] - c->T[a]) / c->dx;
+      double uy = (Q[1][an] - Q[1][as] + Q[1][bn] - Q[1][bs]) / (4.0 * c->dy);
+      double vy = (Q[2][an] - Q[2][as] + Q[2][bn] - Q[2][bs]) / (4.0 * c->dy);
+      double txx = mu * ((4.0 / 3.0) * ux - (2.0 / 3.0) * vy);
+      double txy = mu * (uy + vx);
+      double qx = -kap * Tx;
+      double uf = 0.5 * (Q[1][a] + Q[1][b]), vf = 0.5 * (Q[2][a] + Q[2][b]);
+      c->fx[0][a] = F[0];
+      c->fx[1][a] = F[1] - txx;
+      c->fx[2][a] = F[2] - txy;
+      c->fx[3][a] = F[3] - (uf * txx + vf * txy - qx);
+    }
+  /* y-faces: face j + 1/2 for j in [-1, ny-1], stored at fidx(i, j) */
+#pragma omp parallel for schedule(static)
+  for (int j = -1; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      double s[6][4];
+      for (int k = 0; k < 6; k++)
+        for (int v = 0; v < 4; v++) s[k][v] = Q[v][fidx(c, i, j - 2 + k)];
+      double qL[4], qR[4], F[4];
+      face_states(s, qL, qR);
+      ldfss(qL, qR, 0.0, 1.0, g, R, cpv, face_mr2(c, qL, qR, c->dy), F);
+      int a = fidx(c, i, j), b = fidx(c, i, j + 1);
+      int ae = fidx(c, i + 1, j), aw = fidx(c, i - 1, j), be = fidx(c, i + 1, j + 1), bw = fidx(c, i - 1, j + 1);
+      double uy = (Q[1][b] - Q[1][a]) / c->dy, vy = (Q[2][b] - Q[2][a]) / c->dy, Ty = (c->T[b] - c->T[a]) / c->dy;
+      double ux = (Q[1][ae] - Q[1][aw] + Q[1][be] - Q[1][bw]) / (4.0 * c->dx);
+      double vx = (Q[2][ae] - Q[2][aw] + Q[2][be] - Q[2][bw]) / (4.0 * c->dx);
+      double tyy = mu * ((4.0 / 3.0) * vy - (2.0 / 3.0) * ux);
+      double txy = mu * (uy + vx);
+      double qy = -kap * Ty;
+      double uf = 0.5 * (Q[1][a] + Q[1][b]), vf = 0.5 * (Q[2][a] + Q[2][b]);
+      c->fy[0][a] = F[0];
+      c->fy[1][a] = F[1] - txy;
+      c->fy[2][a] = F[2] - tyy;
+      c->fy[3][a] = F[3] - (uf * txy + vf * tyy - qy);
+    }
+}
+
+/* SSP-RK3 (Shu-Osher) stage on fluid cells:
+ *   stage 1: out = Un + dt L(in)
+ *   stage 2: out = 3/4 Un + 1/4 (in + dt L(in))
+ *   stage 3: out = 1/3 Un + 2/3 (in + dt L(in)) */
+static void stage_update(orc_case *c, int stage, double *const Un[4], double *const In[4], double *const Out[4],
+                         double dt) {
+  const orc_params *p = &c->p;
+  int nx = p->nx, ny = p->ny;
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      if (c->tag[j * nx + i] != ORC_FLUID) continue;
+      int m = fidx(c, i, j), mw = fidx(c, i - 1, j), ms = fidx(c, i, j - 1);
+      for (int v = 0; v < 4; v++) {
+        double L = -((c->fx[v][m] - c->fx[v][mw]) / c->dx + (c->fy[v][m] - c->fy[v][ms]) / c->dy);
+        double o;
+        if (stage == 1) o = Un[v][m] + dt * L;
+        else if (stage == 2) o = 0.75 * Un[v][m] + 0.25 * (In[v][m] + dt * L);
+        else o = (1.0 / 3.0) * Un[v][m] + (2.0 / 3.0) * (In[v][m] + dt * L);
+        Out[v][m] = o;
+      }
+    }
+}
+
+/* Time step from the CFL rule over fluid cells:
+ * dt = CFL / max[(|u|+c)/dx + (|v|+c)/dy + 2 gamma mu/(Pr rho) (1/dx^2 + 1/dy^2)]. */
+static double compute_dt(orc_case *c) {
+  const orc_params *p = &c->p;
+  if (p->dt_fixed > 0.0) return p->dt_fixed;
+  double lmax = 0.0, g = p->gamma;
+  for (int j = 0; j < p->ny; j++)
+    for (int i = 0; i < p->nx; i++) {
+      if (c->tag[j * p->nx + i] != ORC_FLUID) continue;
+      int m = fidx(c, i, j);
+      double q[4];
+      cons_to_prim(c, c->A[0][m], c->A[1][m], c->A[2][m], c->A[3][m], q);
+      double cs = sqrt(g * c->R * q[3]);
+      double rho = c->A[0][m];
+      double lam = (fabs(q[1]) + cs) / c->dx + (fabs(q[2]) + cs) / c->dy +
+                   (2.0 * g * c->mu / (p->prandtl * rho)) * (1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy));
+      if (lam > lmax) lmax = lam;
+    }
+  return p->cfl / lmax;
+}
+
+int orc_step(orc_case *c, int nsteps) {
+  for (int s = 0; s < nsteps; s++) {
+    if (!c->classified || c->p.motion != ORC_MOTION_STATIC) orc_classify(c);
+    double dt = compute_dt(c);
+    double t = c->t;
+    double ts[3] = {t, t + dt, t + 0.5 * dt};
+    double *const *in[3] = {c->A, c->B, c->C};
+    double *const *out[3] = {c->B, c->C, c->A};
+    for (int k = 0; k < 3; k++) {
+      reconstruct(c, in[k], ts[k]);
+      domain_bc(c, in[k]);
+      residual_faces(c, in[k]);
+      stage_update(c, k + 1, c->A, in[k], out[k], dt);
+    }
+    c->t = t + dt;
+    c->last_dt = dt;
+  }
+  return c->nerr;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 6, Eq. 9: force on the body.  Midpoint rule per segment; surface     */
+/* pressure and wall shear from the probe one diagonal spacing out along the */
+/* segment normal (inverse-distance weighted as in Sec. 4.6).  The free-     */
+/* stream pressure is subtracted (its closed-surface integral is zero).      */
+/* Compensated (Kahan) summation.                                            */
+/* ------------------------------------------------------------------------- */
+void orc_forces(orc_case *c, double out[4]) {
+  const orc_params *p = &c->p;
+  if (!c->classified) orc_classify(c);
+  double X[2], V[2], Acc[2];
+  motion_at(p, c->t, X, V, Acc);
+  double sx = 0, cx = 0, sy = 0, cy = 0;
+  for (int k = 0; k < p->nv; k++) {
+    int k1 = (k + 1 == p->nv) ? 0 : k + 1;
+    double ax = c->vx[k], ay = c->vy[k];
+    double ex = c->vx[k1] - ax, ey = c->vy[k1] - ay;
+    double L = sqrt(ex * ex + ey * ey);
+    double tx = ex / L, ty = ey / L;
+    double nx = ty, ny = -tx;
+    double mx = ax + 0.5 * ex, my = ay + 0.5 * ey;
+    double xi = c->h, w[4];
+    int32_t i0, j0;
+    int mask = 0;
+    for (int st = 0; st <= 3; st++) {
+      mask = interp_square(c, mx + xi * nx, my + xi * ny, ALLOW_FLUID, &i0, &j0, w);
+      if (mask) break;
+      if (st < 3) xi = xi + c->dmin;
+    }
+    if (!mask) continue;
+    double qp[4] = {0, 0, 0, 0};
+    for (int kk = 0; kk < 4; kk++) {
+      if (!(mask >> kk & 1)) continue;
+      int id = fidx(c, i0 + (kk & 1), j0 + (kk >> 1));
+      double qk[4];
+      cons_to_prim(c, c->A[0][id], c->A[1][id], c->A[2][id], c->A[3][id], qk);
+      for (int v = 0; v < 4; v++) qp[v] += w[kk] * qk[v];
+    }
+    double rho_p = qp[0] / (c->R * qp[3]);
+    double gn = -rho_p * (nx * Acc[0] + ny * Acc[1]);
+    double ps = qp[0] - xi * gn;
+    double tau = c->mu * ((qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty) / xi;
+    double fx = (-(ps - c->pinf) * nx + tau * tx) * L;
+    double fy = (-(ps - c->pinf) * ny + tau * ty) * L;
+    double y1 = fx - cx, t1 = sx + y1;
+    cx = (t1 - sx) - y1;
+    sx = t1;
+    double y2 = fy - cy, t2 = sy + y2;
+    cy = (t2 - sy) - y2;
+    sy = t2;
+  }
+  double qref = 0.5 * p->ref_len;
+  out[0] = sx / qref;
+  out[1] = sy / qref;
+  out[2] = sx;
+  out[3] = sy;
+}
+
+/* ------------------------------------------------------------------------- */
+/* setup.  Non-dimensional free stream: rho = 1, T = 1, reference speed 1,    */
+/* p = 1/(gamma M^2), R = p, mu = 1/Re (reference length 1), k = mu cp / Pr. */
+/* ------------------------------------------------------------------------- */
+orc_case *orc_create(const orc_params *pp) {
+  orc_case *c = calloc(1, sizeof(orc_case));
+  c->p = *pp;
+  const orc_params *p = &c->p;
+  int nv = p->nv;
+  c->vref = calloc(2 * (nv > 0 ? nv : 1), sizeof(double));
+  if (nv > 0) memcpy(c->vref, pp->verts, sizeof(double) * 2 * nv);
+  c->p.verts = c->vref;
+  c->vx = calloc(nv > 0 ? nv : 1, sizeof(double));
+  c->vy = calloc(nv > 0 ? nv : 1, sizeof(double));
+  c->snx = calloc(nv > 0 ? nv : 1, sizeof(double));
+  c->sny = calloc(nv > 0 ? nv : 1, sizeof(double));
+  c->vnx = calloc(nv > 0 ? nv : 1, sizeof(double));
+  c->vny = calloc(nv > 0 ? nv : 1, sizeof(double));
+  if (nv > 0) build_normals(c);
+  {
+    double X[2], V[2], Acc[2];
+    motion_at(p, 0.0, X, V, Acc);
+    for (int k = 0; k < nv; k++) {
+      c->vx[k] = c->vref[2 * k] + X[0];
+      c->vy[k] = c->vref[2 * k + 1] + X[1];
+    }
+  }
+  c->dx = (p->x1 - p->x0) / p->nx;
+  c->dy = (p->y1 - p->y0) / p->ny;
+  c->h = sqrt(c->dx * c->dx + c->dy * c->dy);
+  c->dmin = c->dx < c->dy ? c->dx : c->dy;
+  double g = p->gamma;
+  c->pinf = 1.0 / (g * p->mach * p->mach);
+  c->R = c->pinf;
+  c->cp = g * c->R / (g - 1.0);
+  c->mu = p->re > 0.0 ? 1.0 / p->re : 0.0;
+  c->kappa = c->mu * c->cp / p->prandtl;
+  c->Uinf[0] = 1.0;
+  c->Uinf[1] = p->uinf[0];
+  c->Uinf[2] = p->uinf[1];
+  c->Uinf[3] = c->pinf / (g - 1.0) + 0.5 * (p->uinf[0] * p->uinf[0] + p->uinf[1] * p->uinf[1]);
+  c->W = p->nx + 2 * NG;
+  c->H = p->ny + 2 * NG;
+  size_t n = (size_t)c->W * c->H;
+  for (int v = 0; v < 4; v++) {
+    c->A[v] = malloc(n * sizeof(double));
+    c->B[v] = malloc(n * sizeof(double));
+    c->C[v] = malloc(n * sizeof(double));
+    c->q[v] = malloc(n * sizeof(double));
+    if (v == 0) c->T = malloc(n * sizeof(double));
+    c->fx[v] = calloc(n, sizeof(double));
+    c->fy[v] = calloc(n, sizeof(double));
+    for (size_t m = 0; m < n; m++) c->A[v][m] = c->B[v][m] = c->C[v][m] = c->Uinf[v];
+  }
+  c->tag = calloc((size_t)p->nx * p->ny, 1);
+  for (int k = 0; k < 4; k++) c->list[k] = calloc(1, sizeof(orc_stencil));
+  return c;
+}
+
+void orc_destroy(orc_case *c) {
+  if (!c) return;
+  for (int v = 0; v < 4; v++) {
+    if (v == 0) free(c->T);
+    free(c->A[v]); free(c->B[v]); free(c->C[v]); free(c->q[v]); free(c->fx[v]); free(c->fy[v]);
+  }
+  for (int k = 0; k < 4; k++) free(c->list[k]);
+  free(c->tag); free(c->vref); free(c->vx); free(c->vy); free(c->snx); free(c->sny); free(c->vnx); free(c->vny);
+  free(c);
+}
+
+void orc_get_state(const orc_case *c, double *dst) {
+  int nx = c->p.nx, ny = c->p.ny;
+  for (int v = 0; v < 4; v++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) dst[((size_t)v * ny + j) * nx + i] = c->A[v][fidx(c, i, j)];
+}
+
+void orc_set_state(orc_case *c, const double *src) {
+  int nx = c->p.nx, ny = c->p.ny;
+  for (int v = 0; v < 4; v++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) c->A[v][fidx(c, i, j)] = src[((size_t)v * ny + j) * nx + i];
+}
+
+void orc_get_tags(const orc_case *c, uint8_t *dst) { memcpy(dst, c->tag, (size_t)c->p.nx * c->p.ny); }
+int orc_list_len(const orc_case *c, int kind) { return c->nlist[kind]; }
+void orc_get_list(const orc_case *c, int kind, orc_stencil *dst) {
+  memcpy(dst, c->list[kind], sizeof(orc_stencil) * c->nlist[kind]);
+}
+double orc_time(const orc_case *c) { return c->t; }
+double orc_last_dt(const orc_case *c) { return c->last_dt; }

@@ -1,0 +1,107 @@
+/*
+ * FP64 CPU oracle for the sharp-interface immersed-boundary compressible solver
+ * of Seshadri & De, "A Novel Sharp Interface Immersed Boundary Framework for
+ * Viscous Flow Simulations at Arbitrary Mach Number Involving Complex and
+ * Moving Boundaries" (arXiv 1912.11908).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, obviously-correct
+ * restatement of what the paper computes, used to check the CUDA library.  It
+ * shares no code, header, table or helper with the CUDA path and must never be
+ * linked into, imported by, or called from the product path.  Only the test
+ * suite, the smoke check and the CPU-baseline leg of the benchmark may load it.
+ *
+ * Readings of the paper where it is silent are stated next to each function in
+ * oracle.c.  Every routine computes in IEEE binary64 with basic operations and
+ * sqrt only; the file is built with -ffp-contract=off so that the geometry
+ * (classification, tagging, closest features, image points, stencils) is
+ * reproducible bit for bit by any IEEE implementation that performs the same
+ * operations in the same order.
+ *
+ * Parity status per function (pins live in tests/test_oracle_*.py):
+ *   orc_classify_points  pinned: brute force with exact rationals (Sec. 3.2)
+ *   tagging / lists      pinned: independent definition on tiny grids (Sec. 3.2, Sec. 5)
+ *   pseudo-normals       pinned: regular polygon radial, bisector property (Sec. 4.2)
+ *   closest feature      pinned: dense sampling of the polyline (Sec. 4.1, Eq. 1)
+ *   weno5                pinned: polynomial exactness, 5th-order convergence (Sec. 2)
+ *   ldfss flux           pinned: consistency F(q,q) = Euler flux, Sod exact Riemann solution (Sec. 2)
+ *   viscous flux         pinned: shear-wave and entropy-wave decay rates (Sec. 2)
+ *   RK3 + residual       pinned: periodic mass/energy conservation, free-stream preservation
+ *   IB reconstruction    pinned: linear-field exactness at a flat wall, quiescent body (Sec. 4.4-4.6, Sec. 5)
+ *   forces               pinned: zero force in uniform flow / uniform pressure (Sec. 6, Eq. 9)
+ *   drag/lift values     parity unpinned (the paper prints none for these workloads)
+ */
+#ifndef IBM_ORACLE_H
+#define IBM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* node tags (Sec. 3.2, Fig. 1; Sec. 5, Fig. 6) */
+enum { ORC_FLUID = 0, ORC_SOLID = 1, ORC_IB = 2, ORC_G1 = 3, ORC_G2 = 4, ORC_G3 = 5 };
+/* domain sides: 0 x-low, 1 x-high, 2 y-low, 3 y-high */
+enum { ORC_BC_FREESTREAM = 0, ORC_BC_OUTFLOW = 1, ORC_BC_PERIODIC = 2 };
+enum { ORC_MOTION_STATIC = 0, ORC_MOTION_SIN = 1, ORC_MOTION_CONST = 2 };
+enum { ORC_REGION_FACE = 0, ORC_REGION_VERTEX = 1, ORC_REGION_FALLBACK = 2 };
+
+typedef struct {
+  int nx, ny;              /* cells */
+  double x0, x1, y0, y1;   /* domain */
+  int bc[4];
+  double mach, re, gamma, prandtl, cfl;  /* re <= 0: inviscid */
+  double uinf[2];          /* free-stream velocity in units of the reference speed */
+  double dt_fixed;         /* > 0: use this time step instead of the CFL rule */
+  double ref_len;          /* force normalisation length */
+  int nv;                  /* body vertices (closed CCW polyline); 0 = no body */
+  const double *verts;     /* 2*nv, interleaved x,y; copied */
+  int motion;
+  double amp[2], freq, vel[2];
+} orc_params;
+
+/* One immersed-boundary or ghost node and its reconstruction stencil. */
+typedef struct {
+  int32_t cell;      /* j*nx + i */
+  int32_t feature;   /* segment index (FACE) or vertex index (VERTEX) */
+  int32_t region;    /* ORC_REGION_* */
+  int32_t i0, j0;    /* lower-left cell of the interpolation square */
+  int32_t mask;      /* bit k: corner k valid; k = 0 (i0,j0), 1 (i0+1,j0), 2 (i0,j0+1), 3 (i0+1,j0+1) */
+  int32_t nstep;     /* probe push-outs taken */
+  int32_t kind;      /* 0 IB, 1..3 ghost layer */
+  double nx, ny;     /* local normal (out of the body) */
+  double bx, by;     /* boundary point P' */
+  double xi_node;    /* signed distance of the node from P' along the normal */
+  double xi_probe;   /* signed distance of the probe / image point from P' */
+  double w[4];       /* interpolation weights (0 for invalid corners) */
+} orc_stencil;
+
+typedef struct orc_case orc_case;
+
+orc_case *orc_create(const orc_params *p);
+void orc_destroy(orc_case *c);
+int orc_classify(orc_case *c);                   /* geometry at the current time */
+int orc_step(orc_case *c, int nsteps);           /* SSP-RK3 steps; returns #stencil errors */
+void orc_get_state(const orc_case *c, double *dst);      /* [4][ny][nx] conserved */
+void orc_set_state(orc_case *c, const double *src);      /* [4][ny][nx] conserved */
+void orc_get_tags(const orc_case *c, uint8_t *dst);      /* [ny][nx] */
+int orc_list_len(const orc_case *c, int kind);           /* 0 IB, 1..3 G1..G3 */
+void orc_get_list(const orc_case *c, int kind, orc_stencil *dst);
+void orc_forces(orc_case *c, double out[4]);             /* Cd, Cl, Fx, Fy */
+double orc_time(const orc_case *c);
+double orc_last_dt(const orc_case *c);
+void orc_reconstruct(orc_case *c, double t);             /* IB + ghost fill at time t (one call of the stage step) */
+void orc_vertex_normals(const orc_case *c, double *dst); /* 2*nv */
+void orc_closest(const orc_case *c, double px, double py, int32_t *feature, int32_t *region,
+                 double *cx, double *cy, double *d2);
+
+/* pure kernels exposed for pins; flux states are (rho, u, v, p) */
+void orc_classify_points(int nv, const double *verts, int np, const double *pts, uint8_t *solid);
+double orc_weno5(const double f[5]);
+void orc_ldfss_xflux(const double qL[4], const double qR[4], double gamma, double R,
+                     double mr2_fixed, double flux[4]);
+void orc_euler_xflux(const double q[4], double gamma, double R, double flux[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

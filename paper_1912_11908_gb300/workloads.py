@@ -1,0 +1,139 @@
+"""Seeded synthetic inputs: body polylines and case parameters.
+
+This module is the only code shared by the CUDA path's callers and the CPU
+oracle's callers.  It builds inputs only (closed-form body shapes, grid and
+flow parameters, request mixes) and contains none of the method's arithmetic.
+
+Bodies are closed counter-clockwise polylines (interior on the left of the
+travel direction), the 2-D form of the paper's closed oriented surface
+(Sec. 3.1).  Non-dimensional free stream: density 1, temperature 1, reference
+speed 1 along +x, reference length 1 (cylinder diameter, chord).
+"""
+import math
+
+import numpy as np
+
+BC_FREESTREAM, BC_OUTFLOW, BC_PERIODIC = 0, 1, 2
+MOTION_STATIC, MOTION_SIN, MOTION_CONST = 0, 1, 2
+PREC_FP64, PREC_FP32_BULK = 0, 1
+TIME_RK3, TIME_DUAL = 0, 1
+
+
+def cylinder(n=256, diameter=1.0, center=(0.0, 0.0)):
+    """Regular n-gon inscribed in the circle of the given diameter (Sec. 8.1.1, 8.2.2)."""
+    k = np.arange(n, dtype=np.float64)
+    a = 2.0 * math.pi * k / n
+    r = 0.5 * diameter
+    return np.stack([center[0] + r * np.cos(a), center[1] + r * np.sin(a)], axis=1)
+
+
+def naca00xx(thickness=0.12, n=400, alpha_deg=0.0, chord=1.0):
+    """Symmetric NACA 4-digit section with the closed (sharp) trailing edge.
+
+    Half thickness y_t = 5 t (0.2969 sqrt(x) - 0.1260 x - 0.3516 x^2 + 0.2843 x^3
+    - 0.1036 x^4); cosine spacing; one trailing-edge vertex, leading edge at the
+    origin; rotated nose-up by alpha about the leading edge so that the free
+    stream stays along +x (Sec. 7.1, 8.1.2).  n must be even.
+    """
+    assert n % 2 == 0
+    m = n // 2
+    k = np.arange(m + 1, dtype=np.float64)
+    x = 0.5 * (1.0 - np.cos(math.pi * k / m))
+    yt = 5.0 * thickness * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2 + 0.2843 * x ** 3 - 0.1036 * x ** 4)
+    yt[0] = 0.0
+    yt[-1] = 0.0
+    # trailing edge -> upper surface -> leading edge -> lower surface (CCW)
+    upper = np.stack([x[::-1], yt[::-1]], axis=1)[:-1]      # k = m .. 1
+    lower = np.stack([x[:-1], -yt[:-1]], axis=1)             # k = 0 .. m-1
+    pts = np.concatenate([upper, lower], axis=0) * chord
+    a = math.radians(alpha_deg)
+    ca, sa = math.cos(a), math.sin(a)
+    rot = np.stack([pts[:, 0] * ca + pts[:, 1] * sa, -pts[:, 0] * sa + pts[:, 1] * ca], axis=1)
+    return rot
+
+
+def wedge(half_angle_deg=15.0, chord=1.0):
+    """Wedge with its apex at the origin pointing upstream (Sec. 8.1.6)."""
+    t = math.tan(math.radians(half_angle_deg)) * chord
+    return np.array([[0.0, 0.0], [chord, -t], [chord, t]], dtype=np.float64)
+
+
+def case_spec(verts, nx, ny, domain, mach, re, bc, *, cfl=0.5, uinf=(1.0, 0.0), gamma=1.4, prandtl=0.72,
+              motion=MOTION_STATIC, amp=(0.0, 0.0), freq=0.0, vel=(0.0, 0.0), dt_fixed=0.0, ref_len=1.0,
+              precision=PREC_FP64, time_scheme=TIME_RK3, subiters=30, dt_phys=0.0, name=""):
+    verts = np.zeros((0, 2)) if verts is None else np.ascontiguousarray(verts, np.float64)
+    return dict(name=name, verts=verts, nx=int(nx), ny=int(ny), domain=tuple(float(v) for v in domain),
+                mach=float(mach), re=float(re), bc=tuple(int(b) for b in bc), cfl=float(cfl),
+                uinf=tuple(float(u) for u in uinf), gamma=float(gamma), prandtl=float(prandtl),
+                motion=int(motion), amp=tuple(float(a) for a in amp), freq=float(freq),
+                vel=tuple(float(v) for v in vel), dt_fixed=float(dt_fixed), ref_len=float(ref_len),
+                precision=int(precision), time_scheme=int(time_scheme), subiters=int(subiters),
+                dt_phys=float(dt_phys))
+
+
+FAR = (BC_FREESTREAM, BC_OUTFLOW, BC_FREESTREAM, BC_FREESTREAM)
+SUPERSONIC = (BC_FREESTREAM, BC_OUTFLOW, BC_OUTFLOW, BC_OUTFLOW)
+PERIODIC = (BC_PERIODIC,) * 4
+
+
+def cylinder_m02_re40(nx=160, ny=80, **kw):
+    """Stationary cylinder, 256 segments, M=0.2, Re=40, 160x80 cells over [-8,24]x[-8,8]; 200 RK3 steps."""
+    return case_spec(cylinder(256), nx, ny, (-8.0, 24.0, -8.0, 8.0), 0.2, 40.0, FAR,
+                     name="cylinder_M0.2_Re40_%dx%d" % (nx, ny), **kw)
+
+
+def wedge_m2_re1e4(nx=768, ny=384, **kw):
+    """15 deg half-angle wedge, chord 1, M=2, Re=1e4, 768x384 cells over [-1,3]x[-1,1]; 2000 RK3 steps."""
+    return case_spec(wedge(15.0), nx, ny, (-1.0, 3.0, -1.0, 1.0), 2.0, 1.0e4, SUPERSONIC,
+                     name="wedge15_M2_Re1e4_%dx%d" % (nx, ny), **kw)
+
+
+def oscillating_cylinder_m02_re185(nx=1024, ny=512, **kw):
+    """Cylinder oscillating transversely, y(t)=0.2 sin(2 pi 0.16 t), M=0.2, Re=185, 1024x512 over [-10,30]x[-10,10]."""
+    return case_spec(cylinder(256), nx, ny, (-10.0, 30.0, -10.0, 10.0), 0.2, 185.0, FAR, motion=MOTION_SIN,
+                     amp=(0.0, 0.2), freq=0.16, name="osc_cylinder_M0.2_Re185_%dx%d" % (nx, ny), **kw)
+
+
+def naca0012_a5_m0001(nx=2048, ny=1024, **kw):
+    """NACA0012 at 5 deg, 400 vertices, M=0.001, Re=1000, 2048x1024 over [-4,8]x[-3,3]; dual time, 30 sub-iterations."""
+    dx = 12.0 / nx
+    kw.setdefault("time_scheme", TIME_DUAL)
+    kw.setdefault("dt_phys", 0.5 * dx)
+    return case_spec(naca00xx(0.12, 400, 5.0), nx, ny, (-4.0, 8.0, -3.0, 3.0), 0.001, 1000.0, FAR,
+                     name="naca0012_a5_M0.001_Re1000_%dx%d" % (nx, ny), **kw)
+
+
+def random_polygon(rng, n, center=(0.0, 0.0), rmin=0.3, rmax=1.0):
+    """Star-shaped random polygon (CCW) for brute-force classification checks."""
+    a = np.sort(rng.uniform(0.0, 2.0 * math.pi, n))
+    r = rng.uniform(rmin, rmax, n)
+    return np.stack([center[0] + r * np.cos(a), center[1] + r * np.sin(a)], axis=1)
+
+
+def serving_mix(n=512, seed=20191224, mean_interarrival_s=0.05):
+    """Request mix for the batched loop: bodies, motions, Mach, Re and grids drawn from a seed."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(mean_interarrival_s, n))
+    reqs = []
+    nxs = [64, 128, 256, 512, 1024]
+    nys = [64, 128, 256, 512]
+    pairs = [(a, b) for a in nxs for b in nys if b <= a]
+    for k in range(n):
+        body = int(rng.integers(0, 3))
+        osc = bool(rng.integers(0, 2))
+        mach = float(math.exp(rng.uniform(math.log(0.001), math.log(2.0))))
+        re = float(math.exp(rng.uniform(math.log(40.0), math.log(1.0e4))))
+        gx, gy = pairs[int(rng.integers(0, len(pairs)))]
+        if body == 0:
+            verts = cylinder(256)
+        elif body == 1:
+            verts = naca00xx(float(rng.uniform(0.09, 0.15)), 400, 0.0)
+        else:
+            verts = wedge(float(rng.uniform(10.0, 20.0)))
+        aspect = gy / gx
+        dom = (-4.0, 8.0, -6.0 * aspect, 6.0 * aspect)
+        reqs.append(dict(arrival_s=float(t[k]), spec=case_spec(
+            verts, gx, gy, dom, mach, re, FAR if mach < 1.0 else SUPERSONIC,
+            motion=MOTION_SIN if osc else MOTION_STATIC, amp=(0.0, 0.2) if osc else (0.0, 0.0),
+            freq=0.16 if osc else 0.0, precision=PREC_FP32_BULK, name="req%03d" % k)))
+    return reqs

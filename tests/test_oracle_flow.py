@@ -1,0 +1,352 @@
+"""Pins of the FP64 oracle's flow solver against what the mathematics fixes.
+
+Each test checks the oracle against something other than itself: closed-form
+fluxes, the exact Riemann solution, convergence rates, linear-theory decay
+rates, conservation, exact free-stream solutions and the theta-beta-M
+relation.  A dropped term, a wrong sign or a transposed index in the WENO5,
+LDFSS, viscous, RK3 or boundary code fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1912_11908_gb300 import workloads as W
+
+GAMMA = 1.4
+
+
+def prim_to_cons(r, u, v, p, g=GAMMA):
+    return np.stack([r, r * u, r * v, p / (g - 1.0) + 0.5 * r * (u * u + v * v)])
+
+
+def cons_to_prim(U, g=GAMMA):
+    r = U[0]
+    u = U[1] / r
+    v = U[2] / r
+    p = (g - 1.0) * (U[3] - 0.5 * r * (u * u + v * v))
+    return r, u, v, p
+
+
+# ---------------------------------------------------------------- fluxes (Sec. 2)
+
+def test_ldfss_consistency_equals_euler_flux(orc):
+    """F(q, q) is the exact Euler flux at any Mach number and any Mr^2 (LDFSS splits sum to M and 1)."""
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        r = rng.uniform(0.2, 3.0)
+        p = rng.uniform(0.1, 5.0)
+        c = math.sqrt(GAMMA * p / r)
+        u = rng.uniform(-3.0, 3.0) * c
+        v = rng.uniform(-1.0, 1.0)
+        q = np.array([r, u, v, p])
+        E = orc.euler_xflux(q, GAMMA, 1.0)
+        # the Euler flux written out independently
+        H = GAMMA / (GAMMA - 1.0) * p / r + 0.5 * (u * u + v * v)
+        np.testing.assert_allclose(E, [r * u, r * u * u + p, r * u * v, r * u * H], rtol=1e-13, atol=1e-13)
+        for mr2 in (1.0, 0.04, 1e-4):
+            F = orc.ldfss_xflux(q, q, GAMMA, 1.0, mr2)
+            np.testing.assert_allclose(F, E, rtol=1e-12, atol=1e-12 * (abs(p) + r * u * u))
+
+
+def test_ldfss_upwinding_supersonic(orc):
+    """Supersonic to the right: the flux is the left state's Euler flux, whatever the right state."""
+    qL = np.array([1.0, 3.0, 0.2, 1.0])   # c = 1.18, M = 2.5
+    qR = np.array([0.5, 2.0, -0.1, 0.4])  # c = 1.06, M = 1.9
+    np.testing.assert_allclose(orc.ldfss_xflux(qL, qR, GAMMA, 1.0, 1.0), orc.euler_xflux(qL, GAMMA, 1.0),
+                               rtol=1e-13)
+
+
+# ---------------------------------------------------------------- WENO5 (Sec. 2)
+
+def _cell_avg_poly(coef, a, b):
+    """Average of sum c_k x^k over [a, b]."""
+    s = 0.0
+    for k, ck in enumerate(coef):
+        s += ck * (b ** (k + 1) - a ** (k + 1)) / (k + 1)
+    return s / (b - a)
+
+
+def test_weno5_exact_for_quadratics(orc):
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        coef = rng.normal(size=3)
+        f = np.array([_cell_avg_poly(coef, k - 0.5, k + 0.5) for k in range(-2, 3)])
+        exact = coef[0] + coef[1] * 0.5 + coef[2] * 0.25
+        assert abs(orc.weno5(f) - exact) < 1e-12
+
+
+def test_weno5_fifth_order_with_linear_weights(orc):
+    """Cell averages of a quartic with tiny amplitude (smoothness indicators << eps): linear weights,
+    and the five-point reconstruction is exact for degree-4 polynomials."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        coef = rng.normal(size=5) * 1e-12
+        f = np.array([_cell_avg_poly(coef, k - 0.5, k + 0.5) for k in range(-2, 3)])
+        exact = sum(ck * 0.5 ** k for k, ck in enumerate(coef))
+        assert abs(orc.weno5(f) - exact) < 1e-14 * np.abs(coef).sum()
+
+
+def test_weno5_step_no_overshoot(orc):
+    for jump in range(1, 5):
+        f = np.array([0.0] * jump + [1.0] * (5 - jump))
+        val = orc.weno5(f)
+        assert -1e-12 <= val <= 1.0 + 1e-12
+    # step ahead of the face: stays on the upwind side
+    assert orc.weno5(np.array([0.0, 0.0, 0.0, 1.0, 1.0])) < 0.05
+
+
+# ---------------------------------------------------------------- system tests
+
+def _box(orc, nx, ny, Lx, Ly, mach, re, bc=W.PERIODIC, dt_fixed=0.0, cfl=0.5, uinf=(0.0, 0.0)):
+    spec = W.case_spec(None, nx, ny, (0.0, Lx, 0.0, Ly), mach, re, bc, dt_fixed=dt_fixed, cfl=cfl, uinf=uinf)
+    c = orc.Case(spec)
+    xc = (np.arange(nx) + 0.5) * Lx / nx
+    yc = (np.arange(ny) + 0.5) * Ly / ny
+    X, Y = np.meshgrid(xc, yc)
+    return c, X, Y
+
+
+def _exact_riemann(rl, ul, pl, rr, ur, pr, x, t, g=GAMMA):
+    """Exact solution of the 1-D Riemann problem (textbook Newton iteration on the star pressure)."""
+    cl, cr = math.sqrt(g * pl / rl), math.sqrt(g * pr / rr)
+
+    def fk(p, rk, pk, ck):
+        if p > pk:
+            A = 2.0 / ((g + 1) * rk)
+            B = (g - 1) / (g + 1) * pk
+            return (p - pk) * math.sqrt(A / (p + B))
+        return 2 * ck / (g - 1) * ((p / pk) ** ((g - 1) / (2 * g)) - 1)
+
+    lo, hi = 1e-8, 10.0 * max(pl, pr)
+    for _ in range(200):
+        pm = 0.5 * (lo + hi)
+        if fk(pm, rl, pl, cl) + fk(pm, rr, pr, cr) + ur - ul > 0:
+            hi = pm
+        else:
+            lo = pm
+    ps = 0.5 * (lo + hi)
+    us = 0.5 * (ul + ur) + 0.5 * (fk(ps, rr, pr, cr) - fk(ps, rl, pl, cl))
+    out = np.zeros_like(x)
+    for n, xx in enumerate(x):
+        s = xx / t
+        if s < us:
+            if ps > pl:
+                rs = rl * ((ps / pl + (g - 1) / (g + 1)) / ((g - 1) / (g + 1) * ps / pl + 1))
+                S = ul - cl * math.sqrt((g + 1) / (2 * g) * ps / pl + (g - 1) / (2 * g))
+                out[n] = rl if s < S else rs
+            else:
+                rs = rl * (ps / pl) ** (1 / g)
+                csl = cl * (ps / pl) ** ((g - 1) / (2 * g))
+                if s < ul - cl:
+                    out[n] = rl
+                elif s > us - csl:
+                    out[n] = rs
+                else:
+                    out[n] = rl * (2 / (g + 1) + (g - 1) / ((g + 1) * cl) * (ul - s)) ** (2 / (g - 1))
+        else:
+            if ps > pr:
+                rs = rr * ((ps / pr + (g - 1) / (g + 1)) / ((g - 1) / (g + 1) * ps / pr + 1))
+                S = ur + cr * math.sqrt((g + 1) / (2 * g) * ps / pr + (g - 1) / (2 * g))
+                out[n] = rs if s < S else rr
+            else:
+                rs = rr * (ps / pr) ** (1 / g)
+                csr = cr * (ps / pr) ** ((g - 1) / (2 * g))
+                if s > ur + cr:
+                    out[n] = rr
+                elif s < us + csr:
+                    out[n] = rs
+                else:
+                    out[n] = rr * (2 / (g + 1) - (g - 1) / ((g + 1) * cr) * (ur - s)) ** (2 / (g - 1))
+    return out
+
+
+def _sod_error(orc, nx):
+    bc = (W.BC_OUTFLOW, W.BC_OUTFLOW, W.BC_PERIODIC, W.BC_PERIODIC)
+    nsteps = nx  # dt = 0.2/nx = 0.2 dx: CFL about 0.4 at the fastest wave
+    c, X, Y = _box(orc, nx, 4, 1.0, 4.0 / nx, 0.5, 0.0, bc=bc, dt_fixed=0.2 / nsteps)
+    left = X < 0.5
+    r = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    c.set_state(prim_to_cons(r, 0 * r, 0 * r, p))
+    c.step(nsteps)
+    rho = c.state()[0, 1]
+    ex = _exact_riemann(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, X[1] - 0.5, 0.2)
+    return np.mean(np.abs(rho - ex)), rho, ex
+
+
+def test_sod_shock_tube_matches_exact_riemann(orc):
+    """WENO5 + LDFSS + RK3 on Sod's problem: L1 density error small and decreasing with the grid."""
+    e1, rho, ex = _sod_error(orc, 100)
+    e2, _, _ = _sod_error(orc, 200)
+    assert e2 < 6e-3, e2
+    assert e2 < 0.7 * e1, (e1, e2)
+    assert rho.min() > 0.1 and rho.max() < 1.0 + 1e-3
+
+
+def _density_wave_error(orc, n):
+    L = 1.0
+    dx = L / n
+    tend = 0.5
+    dt = 0.25 * dx ** (5.0 / 3.0)
+    nsteps = int(math.ceil(tend / dt))
+    dt = tend / nsteps
+    c, X, Y = _box(orc, n, 4, L, 4 * dx, 0.5, 0.0, dt_fixed=dt)
+
+    def avg(t):
+        # exact cell averages of 1 + 0.2 sin(2 pi (x - t)) (the finite-volume state)
+        return 1.0 + 0.2 * (np.cos(2 * math.pi * (X - dx / 2 - t)) - np.cos(2 * math.pi * (X + dx / 2 - t))) / (
+            2 * math.pi * dx)
+
+    r = avg(0.0)
+    p = np.full_like(X, 1.0 / (GAMMA * 0.25))
+    c.set_state(prim_to_cons(r, np.ones_like(X), 0 * X, p))
+    c.step(nsteps)
+    rho = c.state()[0]
+    return np.mean(np.abs(rho - avg(tend)))
+
+
+def test_density_wave_fifth_order(orc):
+    """Smooth density wave advected through a periodic box: L1 error of the cell averages falls at
+    (about) fifth order with dt ~ dx^(5/3) (WENO5 reconstruction of rho, u, v, p)."""
+    errs = [_density_wave_error(orc, n) for n in (16, 32, 64)]
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert orders[-1] > 4.5, (errs, orders)
+
+
+def test_periodic_conservation(orc):
+    """Finite-volume form: mass, momentum and energy sums are conserved on a periodic box."""
+    rng = np.random.default_rng(5)
+    c, X, Y = _box(orc, 32, 24, 1.0, 0.75, 0.4, 100.0)
+    r = 1.0 + 0.1 * np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y / 0.75)
+    u = 0.3 + 0.1 * np.cos(2 * math.pi * Y / 0.75)
+    v = 0.1 * np.sin(2 * math.pi * X)
+    p = 1.0 / (GAMMA * 0.16) * (1.0 + 0.05 * rng.standard_normal(X.shape))
+    U0 = prim_to_cons(r, u, v, p)
+    c.set_state(U0)
+    c.step(50)
+    U1 = c.state()
+    for k in range(4):
+        scale = np.abs(U0[k]).sum()
+        assert abs(U1[k].sum() - U0[k].sum()) <= 1e-13 * scale, k
+
+
+def test_shear_wave_viscous_decay(orc):
+    """u = A sin(2 pi y): decays at nu k_h^2 with the discrete second-difference wavenumber."""
+    ny, Re, A = 64, 50.0, 0.01
+    c, X, Y = _box(orc, 4, ny, 4.0 / ny, 1.0, 0.5, Re)
+    r = np.ones_like(X)
+    u = A * np.sin(2 * math.pi * Y)
+    p = np.full_like(X, 1.0 / (GAMMA * 0.25))
+    c.set_state(prim_to_cons(r, u, 0 * X, p))
+    c.step(200)
+    t = c.time()
+    uu = c.state()[1] / c.state()[0]
+    amp = 2.0 * np.mean(uu * np.sin(2 * math.pi * Y))
+    dy = 1.0 / ny
+    kh2 = (2.0 * math.sin(math.pi * dy) / dy) ** 2
+    expect = A * math.exp(-(1.0 / Re) * kh2 * t)
+    assert abs(amp / expect - 1.0) < 2e-3, (amp, expect)
+
+
+def test_entropy_wave_thermal_decay(orc):
+    """Isobaric temperature wave at rest decays at the thermal diffusivity kappa/(rho c_p) = nu/Pr
+    (to O(chi k / c), kept small by the low reference Mach number)."""
+    nx, Re, A, M = 64, 50.0, 0.01, 0.1
+    c, X, Y = _box(orc, nx, 4, 1.0, 4.0 / nx, M, Re)
+    R = 1.0 / (GAMMA * M * M)
+    T = 1.0 + A * np.cos(2 * math.pi * X)
+    p = np.full_like(X, R)
+    r = p / (R * T)
+    c.set_state(prim_to_cons(r, 0 * X, 0 * X, p))
+    c.step(1400)
+    t = c.time()
+    U = c.state()
+    rr, uu, vv, pp = cons_to_prim(U)
+    TT = pp / (rr * R)
+    amp = 2.0 * np.mean((TT - TT.mean()) * np.cos(2 * math.pi * X))
+    dx = 1.0 / nx
+    kh2 = (2.0 * math.sin(math.pi * dx) / dx) ** 2
+    expect = A * math.exp(-(1.0 / Re) / 0.72 * kh2 * t)
+    assert abs(amp / expect - 1.0) < 1.5e-2, (amp, expect)
+
+
+# ---------------------------------------------------------------- immersed body
+
+def test_quiescent_gas_around_body_is_preserved(orc):
+    """Gas at rest around a sharp-edged body (NACA0012, 10 deg) is an exact solution (Eq. 4-8)."""
+    spec = W.case_spec(W.naca00xx(0.12, 200, 10.0), 96, 48, (-0.5, 1.5, -0.5, 0.5), 0.3, 500.0, W.FAR,
+                       uinf=(0.0, 0.0))
+    c = orc.Case(spec)
+    U0 = c.state()
+    c.step(100)
+    U1 = c.state()
+    tags = c.tags()
+    live = tags != 1
+    for k in range(4):
+        scale = max(1.0, np.abs(U0[k]).max())
+        assert np.abs(U1[k] - U0[k])[live].max() <= 1e-12 * scale, k
+
+
+def test_body_translating_with_stream_is_preserved(orc):
+    """Uniform stream with the body moving at the stream velocity: no-slip holds, the field stays uniform
+    (Galilean invariance, Sec. 8.2.3) while the body is re-classified every step."""
+    spec = W.case_spec(W.cylinder(64, 1.0), 96, 48, (-2.0, 6.0, -2.0, 2.0), 0.5, 100.0, W.FAR,
+                       motion=W.MOTION_CONST, vel=(1.0, 0.0))
+    c = orc.Case(spec)
+    U0 = c.state()
+    c.step(60)
+    assert c.time() > 0.4  # the body has crossed several cells
+    U1 = c.state()
+    live = c.tags() != 1
+    for k in range(4):
+        scale = max(1.0, np.abs(U0[k]).max())
+        assert np.abs(U1[k] - U0[k])[live].max() <= 1e-12 * scale, k
+    np.testing.assert_allclose(c.forces()[:2], 0.0, atol=1e-11)
+
+
+def _theta_beta_m(M, theta, g=GAMMA):
+    from scipy.optimize import brentq
+
+    def f(b):
+        return math.tan(theta) - 2.0 / math.tan(b) * (M * M * math.sin(b) ** 2 - 1) / (
+            M * M * (g + math.cos(2 * b)) + 2)
+
+    mu = math.asin(1.0 / M)
+    beta = brentq(f, mu + 1e-9, mu + 0.5 * (math.pi / 2 - mu))  # weak branch
+    Mn = M * math.sin(beta)
+    return beta, 1.0 + 2.0 * g / (g + 1) * (Mn * Mn - 1)
+
+
+@pytest.mark.slow
+def test_wedge_oblique_shock_theta_beta_m(orc):
+    """M=2 over the 15 deg wedge: the attached weak oblique shock.  Its slope between x = 0.45 and 0.75
+    gives the shock angle, the plateau behind it the pressure ratio (theta-beta-M and the normal-shock
+    relations).  The slope is measured, not the position: the no-slip immersed boundary shifts the
+    effective leading edge by a few cells."""
+    nx, ny = 384, 192
+    c = orc.Case(W.wedge_m2_re1e4(nx, ny))
+    while c.time() < 2.0:
+        c.step(50)
+    r, u, v, p = cons_to_prim(c.state())
+    tags = c.tags()
+    xc = -1.0 + (np.arange(nx) + 0.5) * (4.0 / nx)
+    yc = -1.0 + (np.arange(ny) + 0.5) * (2.0 / ny)
+    beta_e, pr_e = _theta_beta_m(2.0, math.radians(15.0))
+    p1 = 1.0 / (GAMMA * 4.0)
+    mid = p1 * (1.0 + pr_e) / 2.0
+    xs, ys, plateau = [], [], []
+    for xt in (0.45, 0.55, 0.65, 0.75):
+        i = int(np.argmin(np.abs(xc - xt)))
+        col = p[:, i]
+        j = max(jj for jj in range(ny - 1) if col[jj] >= mid and col[jj + 1] < mid)
+        ys.append(yc[j] + (col[j] - mid) / (col[j] - col[j + 1]) * (yc[j + 1] - yc[j]))
+        xs.append(xc[i])
+        wall = max(jj for jj in range(ny) if tags[jj, i] != 0)
+        plateau.append(np.median(col[wall + 3:j - 2]) / p1)
+    slope = np.polyfit(xs, ys, 1)[0]
+    # tolerances of a 384x192 grid (about 26 cells across the wedge base); the full-size run on the
+    # GPU checks the same relation more tightly
+    assert abs(math.degrees(math.atan(slope)) - math.degrees(beta_e)) < 3.0, (math.degrees(math.atan(slope)),
+                                                                              math.degrees(beta_e))
+    assert abs(np.median(plateau) / pr_e - 1.0) < 0.10, (plateau, pr_e)
