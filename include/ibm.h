@@ -1,0 +1,181 @@
+/*
+ * ibm.h -- C ABI of the GB300 (sm_103a) sharp-interface immersed-boundary
+ * compressible flow library.
+ *
+ * Method: Seshadri & De, arXiv 1912.11908.  One case is one 2-D uniform
+ * Cartesian block with an immersed body given as a closed polyline.  Per
+ * explicit time step the library runs, on the case's CUDA stream:
+ *   - ray-casting classification of every cell centre and IB / ghost tagging
+ *     (Sec. 3.2), for moving bodies at every step;
+ *   - closest surface feature, pseudo-normal, boundary point and interpolation
+ *     stencil of every IB and ghost node (Sec. 4.1-4.3, Eq. 1-3);
+ *   - per Runge-Kutta stage: IB reconstruction (Sec. 4.4-4.6, Eq. 4-8), ghost
+ *     field extension through image points into three layers (Sec. 5), domain
+ *     halos, and the fused residual -- WENO5 reconstruction, low-diffusion flux
+ *     splitting, central viscous flux -- with the stage update (Sec. 2);
+ *   - surface force integration (Sec. 6, Eq. 9) on request.
+ *
+ * Conventions
+ *   - Every call returns an ibm_status and never aborts; on error
+ *     ibm_last_error() returns a thread-local message.
+ *   - The library owns all device memory of a case.  Caller buffers passed to
+ *     ibm_create_case are copied before it returns.
+ *   - Work is enqueued on the stream given at creation (NULL = the legacy
+ *     default stream).  ibm_step is asynchronous; ibm_forces, ibm_get_state and
+ *     ibm_sync synchronise that stream and report asynchronous device errors
+ *     (list overflow -> IBM_ECAPACITY, empty interpolation stencil ->
+ *     IBM_ESTENCIL, CUDA errors -> IBM_ECUDA).
+ *   - Non-dimensionalisation: free-stream density 1 and temperature 1,
+ *     reference speed 1, reference length 1; p_inf = 1/(gamma M^2),
+ *     R = p_inf, mu = 1/Re (Re <= 0: inviscid), k = mu c_p / Pr.
+ *   - Grid: nx * ny cells over [lo, hi]; cell (i, j) has centre
+ *     (lo[0] + (i + 1/2) dx, lo[1] + (j + 1/2) dy).  Cell arrays exchanged with
+ *     the caller are row-major [j][i] over the nx * ny interior cells.
+ *   - A case is used by one host thread at a time.
+ */
+#ifndef IBM_GB300_H
+#define IBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibm_case ibm_case;
+
+typedef enum {
+  IBM_OK = 0,
+  IBM_EINVAL = 1,     /* bad argument */
+  IBM_ENOMEM = 2,     /* device allocation failed */
+  IBM_ECAPACITY = 3,  /* more IB / ghost nodes than the case's list capacity */
+  IBM_ESTENCIL = 4,   /* an IB / ghost node found no valid interpolation corner */
+  IBM_ECUDA = 5,      /* CUDA runtime error */
+  IBM_ESTATE = 6      /* call not valid in the case's current state */
+} ibm_status;
+
+/* node tags (Sec. 3.2, Sec. 5): fluid, solid, IB (fluid node with a solid
+ * 4-neighbour), ghost layers G1..G3 (solid nodes whose nearest non-solid node
+ * along a grid line is 1, 2 or 3 cells away) */
+enum { IBM_TAG_FLUID = 0, IBM_TAG_SOLID = 1, IBM_TAG_IB = 2, IBM_TAG_G1 = 3, IBM_TAG_G2 = 4, IBM_TAG_G3 = 5 };
+/* domain sides, in ibm_grid.bc order: x-low, x-high, y-low, y-high */
+enum { IBM_BC_FREESTREAM = 0, IBM_BC_OUTFLOW = 1, IBM_BC_PERIODIC = 2 };
+/* prescribed body motion: displacement X(t) = amp sin(2 pi freq t) (SIN) or vel t (CONST) */
+enum { IBM_MOTION_STATIC = 0, IBM_MOTION_SIN = 1, IBM_MOTION_CONST = 2 };
+/* arithmetic: FP64 throughout, or FP32 bulk (stage values and fluxes in FP32
+ * on perturbations from the free stream, FP64 state accumulation) */
+enum { IBM_PREC_FP64 = 0, IBM_PREC_FP32_BULK = 1 };
+/* stencil regions (Sec. 4.1): closest feature is a segment interior or a
+ * vertex; FALLBACK = the line along the local normal met no segment on the
+ * surface side, the boundary point is the closest point */
+enum { IBM_REGION_FACE = 0, IBM_REGION_VERTEX = 1, IBM_REGION_FALLBACK = 2 };
+
+/* Body: closed counter-clockwise polyline (interior on the left), nverts >= 3,
+ * verts = 2*nverts doubles (x0, y0, x1, y1, ...), host memory, copied.  dim
+ * must be 2. */
+typedef struct {
+  int dim;
+  int nverts;
+  const double *verts;
+} ibm_geometry;
+
+typedef struct {
+  int nx, ny;       /* cells, each >= 8 */
+  double lo[2], hi[2];
+  int bc[4];        /* IBM_BC_* per side */
+} ibm_grid;
+
+typedef struct {
+  double mach, re, gamma, prandtl, cfl;
+  double uinf[2];   /* free-stream velocity in reference-speed units */
+  double dt_fixed;  /* > 0: fixed time step, else the CFL rule */
+  double ref_len;   /* force normalisation length (> 0) */
+  int precision;    /* IBM_PREC_* */
+  int reserved[3];  /* zero */
+} ibm_flow;
+
+typedef struct {
+  int kind;         /* IBM_MOTION_* */
+  double amp[2];
+  double freq;
+  double vel[2];
+} ibm_motion;
+
+/* One IB or ghost node and its reconstruction stencil (Sec. 4.1-4.6, Sec. 5).
+ * The node value is rebuilt on the line P' + xi n through the boundary point
+ * P' along the local normal n (face normal or vertex pseudo-normal, pointing
+ * into the fluid); the probe (IB node) or image point (ghost node) sits at
+ * xi_probe, the node at xi_node. */
+typedef struct {
+  int32_t cell;     /* j*nx + i */
+  int32_t feature;  /* segment (FACE) or vertex (VERTEX) index */
+  int32_t region;   /* IBM_REGION_* */
+  int32_t i0, j0;   /* lower-left cell of the interpolation square */
+  int32_t mask;     /* bit k set: corner k = (i0 + (k&1), j0 + (k>>1)) is valid */
+  int32_t nstep;    /* probe push-outs (0..3) */
+  int32_t kind;     /* 0 IB, 1..3 ghost layer */
+  double nx, ny;    /* local normal */
+  double bx, by;    /* boundary point P' */
+  double xi_node, xi_probe;
+  double w[4];      /* interpolation weights, 0 on invalid corners */
+} ibm_stencil;
+
+/* what for ibm_get_state */
+enum {
+  IBM_STATE_FP64 = 0,   /* double[4][ny][nx]: rho, rho u, rho v, rho E */
+  IBM_TAGS = 1,         /* uint8_t[ny][nx] */
+  IBM_LIST_COUNTS = 2,  /* int32_t[4]: #IB, #G1, #G2, #G3 */
+  IBM_STENCILS = 3,     /* ibm_stencil[#IB + #G1 + #G2 + #G3], IB first then G1, G2, G3, each in row-major order */
+  IBM_TIME = 4,         /* double[2]: t, last dt */
+  IBM_STEPS = 5         /* int64_t: steps taken */
+};
+
+/* Create a case, initialised to the uniform free stream at t = 0 (no
+ * classification yet).  cuda_stream: a cudaStream_t or NULL.  motion may be
+ * NULL (static body).  geometry->nverts may be 0 (no body). */
+ibm_status ibm_create_case(const ibm_geometry *geometry, const ibm_grid *grid, const ibm_flow *flow,
+                           const ibm_motion *motion, void *cuda_stream, ibm_case **out);
+
+/* Classify cells, build IB / ghost lists and stencils at the current time
+ * (Sec. 3.2, 4.1-4.3).  Asynchronous. */
+ibm_status ibm_classify(ibm_case *c);
+
+/* Advance nsteps SSP-RK3 steps.  Moving bodies are re-classified at the start
+ * of every step; a static body is classified once if it has not been.
+ * Asynchronous. */
+ibm_status ibm_step(ibm_case *c, int nsteps);
+
+/* Copy a quantity out.  dst: host memory (dst_on_device = 0) or device memory
+ * on the case's device (1); bytes must be at least the size documented for
+ * `what`.  Synchronises the case stream. */
+ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t bytes, int dst_on_device);
+
+/* Overwrite the conserved state (double[4][ny][nx], as IBM_STATE_FP64) from
+ * host or device memory.  Asynchronous for device sources; a host source is
+ * copied before the call returns. */
+ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, int src_on_device);
+
+/* Surface force at the current time (Sec. 6, Eq. 9): out = {Cd, Cl, Fx, Fy}
+ * with C = F / (1/2 rho_inf U_ref^2 ref_len).  Synchronises. */
+ibm_status ibm_forces(ibm_case *c, double out[4]);
+
+/* Wait for the case's stream; report asynchronous errors. */
+ibm_status ibm_sync(ibm_case *c);
+
+/* Release every resource of the case (synchronises first).  NULL is a no-op. */
+ibm_status ibm_destroy_case(ibm_case *c);
+
+/* Device bytes held by a case of these sizes (admission control). */
+size_t ibm_case_device_bytes(const ibm_geometry *geometry, const ibm_grid *grid, const ibm_flow *flow,
+                             const ibm_motion *motion);
+
+/* Kernel launches enqueued by the case so far (instrumentation). */
+int64_t ibm_launch_count(const ibm_case *c);
+
+const char *ibm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,465 @@
+// C ABI (include/ibm.h): case lifetime, device memory, step orchestration.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ibm_internal.cuh"
+
+using namespace ibm;
+
+struct ibm_case {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Consts k{};
+  Geom g{};
+  int precision = IBM_PREC_FP64;
+  // device memory
+  double *vref = nullptr, *vx = nullptr, *vy = nullptr, *snx = nullptr, *sny = nullptr, *vnx = nullptr,
+         *vny = nullptr;
+  double *A = nullptr, *B = nullptr, *C = nullptr;  // FP64 conserved: state, stage arrays (FP64 mode)
+  float *M = nullptr, *F1 = nullptr, *F2 = nullptr;  // FP32-bulk: perturbation mirror and stage arrays
+  uint8_t *solid = nullptr, *tag = nullptr;
+  int *blockcounts = nullptr;
+  ibm_stencil *st = nullptr;
+  int cap = 0;
+  DevState *ds = nullptr;
+  DevState *hds = nullptr;  // pinned host mirror for read-backs
+  bool classified = false;
+  long long launches = 0;
+};
+
+static thread_local char g_err[512] = "";
+
+static ibm_status fail(ibm_status s, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CU(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(IBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Upper bound of IB + ghost nodes: every listed node lies within one cell
+// (IB) or three cells (ghost) of the body's bounding box, whatever the pose.
+static int list_capacity(const ibm_geometry *geo, const ibm_grid *gr) {
+  if (!geo || geo->nverts <= 0) return 0;
+  double xmin = geo->verts[0], xmax = xmin, ymin = geo->verts[1], ymax = ymin;
+  for (int v = 1; v < geo->nverts; v++) {
+    xmin = fmin(xmin, geo->verts[2 * v]);
+    xmax = fmax(xmax, geo->verts[2 * v]);
+    ymin = fmin(ymin, geo->verts[2 * v + 1]);
+    ymax = fmax(ymax, geo->verts[2 * v + 1]);
+  }
+  double dx = (gr->hi[0] - gr->lo[0]) / gr->nx, dy = (gr->hi[1] - gr->lo[1]) / gr->ny;
+  long long w = (long long)ceil((xmax - xmin) / dx) + 10;
+  long long h = (long long)ceil((ymax - ymin) / dy) + 10;
+  long long c = w * h;
+  long long all = (long long)gr->nx * gr->ny;
+  if (c > all) c = all;
+  return (int)c;
+}
+
+static size_t pitch_of(int nx) { return (size_t)((nx + 2 * NG + 31) / 32 * 32); }
+
+static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ibm_flow *fl, const ibm_motion *mo) {
+  if (!geo || !gr || !fl) return fail(IBM_EINVAL, "geometry, grid and flow are required");
+  if (geo->dim != 2) return fail(IBM_EINVAL, "only dim == 2 bodies are supported");
+  if (geo->nverts != 0 && (geo->nverts < 3 || !geo->verts)) return fail(IBM_EINVAL, "body needs >= 3 vertices");
+  if (gr->nx < 8 || gr->ny < 8) return fail(IBM_EINVAL, "grid must have at least 8x8 cells");
+  if ((long long)gr->nx * gr->ny > (1LL << 30)) return fail(IBM_EINVAL, "grid too large");
+  if (!(gr->hi[0] > gr->lo[0]) || !(gr->hi[1] > gr->lo[1])) return fail(IBM_EINVAL, "empty domain");
+  for (int s = 0; s < 4; s++)
+    if (gr->bc[s] < IBM_BC_FREESTREAM || gr->bc[s] > IBM_BC_PERIODIC) return fail(IBM_EINVAL, "bad bc[%d]", s);
+  if ((gr->bc[0] == IBM_BC_PERIODIC) != (gr->bc[1] == IBM_BC_PERIODIC) ||
+      (gr->bc[2] == IBM_BC_PERIODIC) != (gr->bc[3] == IBM_BC_PERIODIC))
+    return fail(IBM_EINVAL, "periodic sides must come in pairs");
+  if (!(fl->mach > 0) || !(fl->gamma > 1) || !(fl->prandtl > 0) || !(fl->ref_len > 0))
+    return fail(IBM_EINVAL, "bad flow parameters");
+  if (!(fl->cfl > 0) && !(fl->dt_fixed > 0)) return fail(IBM_EINVAL, "cfl or dt_fixed must be positive");
+  if (fl->precision != IBM_PREC_FP64 && fl->precision != IBM_PREC_FP32_BULK)
+    return fail(IBM_EINVAL, "bad precision");
+  if (mo && (mo->kind < IBM_MOTION_STATIC || mo->kind > IBM_MOTION_CONST)) return fail(IBM_EINVAL, "bad motion");
+  return IBM_OK;
+}
+
+extern "C" size_t ibm_case_device_bytes(const ibm_geometry *geo, const ibm_grid *gr, const ibm_flow *fl,
+                                        const ibm_motion *mo) {
+  if (validate(geo, gr, fl, mo) != IBM_OK) return 0;
+  size_t plane = pitch_of(gr->nx) * (size_t)(gr->ny + 2 * NG);
+  size_t ncell = (size_t)gr->nx * gr->ny;
+  size_t b = 3 * 4 * plane * sizeof(double);
+  if (fl->precision == IBM_PREC_FP32_BULK) b = 4 * plane * sizeof(double) + 3 * 4 * plane * sizeof(float);
+  b += 2 * ncell + ((ncell + 1023) / 1024) * 16 + (size_t)list_capacity(geo, gr) * sizeof(ibm_stencil);
+  b += 7 * (size_t)geo->nverts * 2 * sizeof(double) + sizeof(DevState);
+  return b;
+}
+
+static void free_case(ibm_case *c) {
+  if (!c) return;
+  void *ptrs[] = {c->vref, c->vx, c->vy, c->snx, c->sny, c->vnx, c->vny, c->A, c->B, c->C, c->M, c->F1,
+                  c->F2, c->solid, c->tag, c->blockcounts, c->st, c->ds};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (c->hds) cudaFreeHost(c->hds);
+  delete c;
+}
+
+template <typename T>
+static cudaError_t dalloc(T **p, size_t n) {
+  return cudaMalloc((void **)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+}
+
+extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *gr, const ibm_flow *fl,
+                                      const ibm_motion *mo, void *stream, ibm_case **out) {
+  if (!out) return fail(IBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  ibm_status st = validate(geo, gr, fl, mo);
+  if (st != IBM_OK) return st;
+  ibm_case *c = new (std::nothrow) ibm_case();
+  if (!c) return fail(IBM_ENOMEM, "host allocation failed");
+  cudaGetDevice(&c->device);
+  c->stream = (cudaStream_t)stream;
+  c->precision = fl->precision;
+  Consts &k = c->k;
+  k.nx = gr->nx;
+  k.ny = gr->ny;
+  k.pitch = (int)pitch_of(gr->nx);
+  k.rows = gr->ny + 2 * NG;
+  k.plane = (long long)k.pitch * k.rows;
+  k.x0 = gr->lo[0];
+  k.y0 = gr->lo[1];
+  k.dx = (gr->hi[0] - gr->lo[0]) / gr->nx;
+  k.dy = (gr->hi[1] - gr->lo[1]) / gr->ny;
+  k.h = sqrt(k.dx * k.dx + k.dy * k.dy);
+  k.dmin = k.dx < k.dy ? k.dx : k.dy;
+  k.gamma = fl->gamma;
+  k.pinf = 1.0 / (fl->gamma * fl->mach * fl->mach);
+  k.R = k.pinf;
+  k.cp = k.gamma * k.R / (k.gamma - 1.0);
+  k.mu = fl->re > 0.0 ? 1.0 / fl->re : 0.0;
+  k.kappa = k.mu * k.cp / fl->prandtl;
+  k.prandtl = fl->prandtl;
+  k.cfl = fl->cfl;
+  k.dt_fixed = fl->dt_fixed;
+  k.ref_len = fl->ref_len;
+  k.uinf[0] = fl->uinf[0];
+  k.uinf[1] = fl->uinf[1];
+  k.Uinf[0] = 1.0;
+  k.Uinf[1] = fl->uinf[0];
+  k.Uinf[2] = fl->uinf[1];
+  k.Uinf[3] = k.pinf / (k.gamma - 1.0) + 0.5 * (fl->uinf[0] * fl->uinf[0] + fl->uinf[1] * fl->uinf[1]);
+  k.Hinf = k.gamma / (k.gamma - 1.0) * k.pinf + 0.5 * (fl->uinf[0] * fl->uinf[0] + fl->uinf[1] * fl->uinf[1]);
+  for (int s = 0; s < 4; s++) k.bc[s] = gr->bc[s];
+  k.motion.kind = mo ? mo->kind : IBM_MOTION_STATIC;
+  for (int d = 0; d < 2; d++) {
+    k.motion.amp[d] = mo ? mo->amp[d] : 0.0;
+    k.motion.vel[d] = mo ? mo->vel[d] : 0.0;
+  }
+  k.motion.freq = mo ? mo->freq : 0.0;
+
+  const int nv = geo->nverts;
+  const size_t ncell = (size_t)k.nx * k.ny;
+  const size_t plane = (size_t)k.plane;
+  c->cap = list_capacity(geo, gr);
+  cudaError_t e = cudaSuccess;
+#define ALLOC(p, n) \
+  if (e == cudaSuccess) e = dalloc(&(p), (n))
+  ALLOC(c->vref, 2 * (size_t)(nv > 0 ? nv : 1));
+  ALLOC(c->vx, (size_t)(nv > 0 ? nv : 1));
+  ALLOC(c->vy, (size_t)(nv > 0 ? nv : 1));
+  ALLOC(c->snx, (size_t)(nv > 0 ? nv : 1));
+  ALLOC(c->sny, (size_t)(nv > 0 ? nv : 1));
+  ALLOC(c->vnx, (size_t)(nv > 0 ? nv : 1));
+  ALLOC(c->vny, (size_t)(nv > 0 ? nv : 1));
+  ALLOC(c->A, 4 * plane);
+  if (c->precision == IBM_PREC_FP64) {
+    ALLOC(c->B, 4 * plane);
+    ALLOC(c->C, 4 * plane);
+  } else {
+    ALLOC(c->M, 4 * plane);
+    ALLOC(c->F1, 4 * plane);
+    ALLOC(c->F2, 4 * plane);
+  }
+  ALLOC(c->solid, ncell);
+  ALLOC(c->tag, ncell);
+  ALLOC(c->blockcounts, 4 * ((ncell + 1023) / 1024));
+  ALLOC(c->st, (size_t)(c->cap > 0 ? c->cap : 1));
+  ALLOC(c->ds, 1);
+#undef ALLOC
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hds, sizeof(DevState));
+  if (e != cudaSuccess) {
+    free_case(c);
+    cudaGetLastError();
+    return fail(IBM_ENOMEM, "device allocation failed: %s", cudaGetErrorString(e));
+  }
+  c->g.nv = nv;
+  c->g.vref = c->vref;
+  c->g.vx = c->vx;
+  c->g.vy = c->vy;
+  c->g.snx = c->snx;
+  c->g.sny = c->sny;
+  c->g.vnx = c->vnx;
+  c->g.vny = c->vny;
+
+  cudaStream_t s = c->stream;
+  ibm_status rs = IBM_OK;
+  do {
+    if (nv > 0) {
+      if (cudaMemcpyAsync(c->vref, geo->verts, sizeof(double) * 2 * nv, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        rs = fail(IBM_ECUDA, "vertex upload failed");
+        break;
+      }
+      launch_normals(nv, c->vref, c->snx, c->sny, c->vnx, c->vny, s);
+      c->launches++;
+    }
+    std::memset(c->hds, 0, sizeof(DevState));
+    if (cudaMemcpyAsync(c->ds, c->hds, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(c->tag, 0, ncell, s) != cudaSuccess) {
+      rs = fail(IBM_ECUDA, "state initialisation failed");
+      break;
+    }
+    // free stream everywhere (halo included)
+    double *hU = new (std::nothrow) double[plane];
+    if (!hU) {
+      rs = fail(IBM_ENOMEM, "host allocation failed");
+      break;
+    }
+    for (int v = 0; v < 4 && rs == IBM_OK; v++) {
+      for (size_t m = 0; m < plane; m++) hU[m] = k.Uinf[v];
+      if (cudaMemcpy(c->A + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        rs = fail(IBM_ECUDA, "state upload failed");
+      if (c->B && cudaMemcpy(c->B + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        rs = fail(IBM_ECUDA, "state upload failed");
+      if (c->C && cudaMemcpy(c->C + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        rs = fail(IBM_ECUDA, "state upload failed");
+    }
+    delete[] hU;
+    if (rs != IBM_OK) break;
+    if (c->M) {
+      for (float *p : {c->M, c->F1, c->F2})
+        if (cudaMemsetAsync(p, 0, 4 * plane * sizeof(float), s) != cudaSuccess) rs = fail(IBM_ECUDA, "memset failed");
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) rs = fail(IBM_ECUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+  } while (0);
+  if (rs != IBM_OK) {
+    free_case(c);
+    return rs;
+  }
+  *out = c;
+  return IBM_OK;
+}
+
+static ibm_status do_classify(ibm_case *c) {
+  cudaStream_t s = c->stream;
+  int nl = 0;
+  if (c->g.nv > 0) {
+    launch_pose(c->k, c->g, c->ds, s);
+    launch_classify(c->k, c->g, c->solid, c->ds, s);
+    nl += 2;
+  } else {
+    cudaMemsetAsync(c->solid, 0, (size_t)c->k.nx * c->k.ny, s);
+  }
+  launch_tags(c->k, c->solid, c->tag, c->blockcounts, c->ds, c->cap, c->st, s, &nl);
+  if (c->g.nv > 0) {
+    launch_stencils(c->k, c->g, c->tag, c->st, c->cap, c->ds, s);
+    nl += 1;
+  }
+  c->launches += nl;
+  c->classified = true;
+  CU(cudaGetLastError());
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_classify(ibm_case *c) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  return do_classify(c);
+}
+
+static ibm_status step_fp64(ibm_case *c) {
+  cudaStream_t s = c->stream;
+  int nl = 0;
+  launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
+  double *in[3] = {c->A, c->B, c->C};
+  double *out[3] = {c->B, c->C, c->A};
+  for (int st = 1; st <= 3; st++) {
+    launch_recon_f64(c->k, in[st - 1], c->st, c->cap, c->ds, st, s, &nl);
+    launch_bc_f64(c->k, in[st - 1], s);
+    launch_stage_f64(c->k, st, c->A, in[st - 1], out[st - 1], c->tag, c->ds, s);
+    nl += 2;
+  }
+  launch_step_end(c->k, c->ds, s);
+  nl += 1;
+  c->launches += nl;
+  return IBM_OK;
+}
+
+static ibm_status step_fp32(ibm_case *c) {
+  cudaStream_t s = c->stream;
+  int nl = 0;
+  launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
+  float *in[3] = {c->M, c->F1, c->F2};
+  float *out[3] = {c->F1, c->F2, nullptr};
+  for (int st = 1; st <= 3; st++) {
+    launch_recon_f32(c->k, in[st - 1], c->A, c->st, c->cap, c->ds, st, s, &nl);
+    launch_bc_f32(c->k, in[st - 1], s);
+    launch_stage_f32(c->k, st, c->M, in[st - 1], out[st - 1], c->A, c->tag, c->ds, s);
+    nl += 2;
+  }
+  launch_step_end(c->k, c->ds, s);
+  nl += 1;
+  c->launches += nl;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_step(ibm_case *c, int nsteps) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  if (nsteps < 0) return fail(IBM_EINVAL, "nsteps < 0");
+  for (int n = 0; n < nsteps; n++) {
+    if (!c->classified || c->k.motion.kind != IBM_MOTION_STATIC) {
+      ibm_status r = do_classify(c);
+      if (r != IBM_OK) return r;
+    }
+    ibm_status r = c->precision == IBM_PREC_FP64 ? step_fp64(c) : step_fp32(c);
+    if (r != IBM_OK) return r;
+  }
+  CU(cudaGetLastError());
+  return IBM_OK;
+}
+
+static ibm_status sync_and_check(ibm_case *c) {
+  CU(cudaStreamSynchronize(c->stream));
+  CU(cudaMemcpy(c->hds, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost));
+  if (c->hds->err & ERR_CAPACITY)
+    return fail(IBM_ECAPACITY, "IB/ghost list overflow: %d nodes, capacity %d", c->hds->offset[4], c->cap);
+  if (c->hds->err & ERR_STENCIL) return fail(IBM_ESTENCIL, "an IB/ghost node found no valid interpolation corner");
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_sync(ibm_case *c) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  return sync_and_check(c);
+}
+
+// copy between a [4][ny][nx] host/device buffer and the padded state planes
+static ibm_status copy_state(ibm_case *c, double *dst, const double *src, bool to_user, bool user_on_device) {
+  const Consts &k = c->k;
+  cudaMemcpyKind kind = to_user ? (user_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost)
+                                : (user_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  for (int v = 0; v < 4; v++) {
+    double *dev = c->A + v * k.plane + cidx(k, 0, 0);
+    double *usr = (to_user ? dst : (double *)src) + (size_t)v * k.nx * k.ny;
+    if (to_user)
+      CU(cudaMemcpy2DAsync(usr, sizeof(double) * k.nx, dev, sizeof(double) * k.pitch, sizeof(double) * k.nx, k.ny,
+                           kind, c->stream));
+    else
+      CU(cudaMemcpy2DAsync(dev, sizeof(double) * k.pitch, usr, sizeof(double) * k.nx, sizeof(double) * k.nx, k.ny,
+                           kind, c->stream));
+  }
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t bytes, int dst_on_device) {
+  if (!c || !dst) return fail(IBM_EINVAL, "case or dst is NULL");
+  const Consts &k = c->k;
+  const size_t ncell = (size_t)k.nx * k.ny;
+  ibm_status r = sync_and_check(c);
+  if (r != IBM_OK && r != IBM_ECAPACITY && r != IBM_ESTENCIL) return r;
+  const DevState &h = *c->hds;
+  cudaMemcpyKind d2x = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  switch (what) {
+    case IBM_STATE_FP64:
+      if (bytes < 4 * ncell * sizeof(double)) return fail(IBM_EINVAL, "dst too small");
+      {
+        ibm_status q = copy_state(c, (double *)dst, nullptr, true, dst_on_device);
+        if (q != IBM_OK) return q;
+      }
+      break;
+    case IBM_TAGS:
+      if (bytes < ncell) return fail(IBM_EINVAL, "dst too small");
+      CU(cudaMemcpyAsync(dst, c->tag, ncell, d2x, c->stream));
+      break;
+    case IBM_LIST_COUNTS:
+      if (bytes < 4 * sizeof(int32_t)) return fail(IBM_EINVAL, "dst too small");
+      if (dst_on_device)
+        CU(cudaMemcpyAsync(dst, c->ds->count, 4 * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+      else
+        std::memcpy(dst, h.count, 4 * sizeof(int32_t));
+      break;
+    case IBM_STENCILS: {
+      size_t n = (size_t)(h.offset[4] < c->cap ? h.offset[4] : c->cap);
+      if (bytes < n * sizeof(ibm_stencil)) return fail(IBM_EINVAL, "dst too small for %zu stencils", n);
+      if (n) CU(cudaMemcpyAsync(dst, c->st, n * sizeof(ibm_stencil), d2x, c->stream));
+      break;
+    }
+    case IBM_TIME: {
+      if (bytes < 2 * sizeof(double)) return fail(IBM_EINVAL, "dst too small");
+      double tt[2] = {h.t, h.dt};
+      if (dst_on_device) CU(cudaMemcpy(dst, tt, sizeof tt, cudaMemcpyHostToDevice));
+      else std::memcpy(dst, tt, sizeof tt);
+      break;
+    }
+    case IBM_STEPS: {
+      if (bytes < sizeof(int64_t)) return fail(IBM_EINVAL, "dst too small");
+      int64_t n = h.steps;
+      if (dst_on_device) CU(cudaMemcpy(dst, &n, sizeof n, cudaMemcpyHostToDevice));
+      else std::memcpy(dst, &n, sizeof n);
+      break;
+    }
+    default:
+      return fail(IBM_EINVAL, "unknown quantity %d", what);
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  return r;
+}
+
+extern "C" ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, int src_on_device) {
+  if (!c || !src) return fail(IBM_EINVAL, "case or src is NULL");
+  const size_t ncell = (size_t)c->k.nx * c->k.ny;
+  if (bytes < 4 * ncell * sizeof(double)) return fail(IBM_EINVAL, "src too small");
+  ibm_status q = copy_state(c, nullptr, (const double *)src, false, src_on_device);
+  if (q != IBM_OK) return q;
+  if (c->M) {
+    launch_to_pert(c->k, c->A, c->M, c->stream);
+    c->launches++;
+  }
+  if (!src_on_device) CU(cudaStreamSynchronize(c->stream));
+  CU(cudaGetLastError());
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_forces(ibm_case *c, double out[4]) {
+  if (!c || !out) return fail(IBM_EINVAL, "case or out is NULL");
+  if (c->g.nv <= 0) {
+    for (int q = 0; q < 4; q++) out[q] = 0.0;
+    return IBM_OK;
+  }
+  if (!c->classified) {
+    ibm_status r = do_classify(c);
+    if (r != IBM_OK) return r;
+  }
+  launch_forces_f64(c->k, c->g, c->tag, c->A, c->ds, c->stream);
+  c->launches++;
+  ibm_status r = sync_and_check(c);
+  for (int q = 0; q < 4; q++) out[q] = c->hds->force[q];
+  return r;
+}
+
+extern "C" ibm_status ibm_destroy_case(ibm_case *c) {
+  if (!c) return IBM_OK;
+  cudaStreamSynchronize(c->stream);
+  free_case(c);
+  return IBM_OK;
+}
+
+extern "C" int64_t ibm_launch_count(const ibm_case *c) { return c ? c->launches : 0; }
+
+extern "C" const char *ibm_last_error(void) { return g_err; }

@@ -1,0 +1,397 @@
+// FP64 flow kernels: time step, IB / ghost reconstruction, domain halos and
+// the fused residual + SSP-RK3 stage update.
+//
+// State layout: structure of arrays, four conserved planes (rho, rho u,
+// rho v, rho E), each (ny + 6) rows of `pitch` doubles; cell (i, j) of the
+// interior sits at (j + 3) * pitch + (i + 3).  Rows are padded to a multiple
+// of 32 elements so every row starts 256-byte aligned.
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+// ---------------------------------------------------------------------------
+// Time step from the CFL rule over fluid cells:
+//   dt = CFL / max[(|u|+c)/dx + (|v|+c)/dy + 2 gamma mu/(Pr rho)(1/dx^2+1/dy^2)].
+// Positive doubles order like their bit patterns, so the maximum is an
+// integer atomicMax (order-independent, exact).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_dt(Consts k, const double *__restrict__ A,
+                                            const uint8_t *__restrict__ tag, DevState *ds) {
+  const int ncell = k.nx * k.ny;
+  double lmax = 0.0;
+  const double vis = (2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy));
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ncell; n += gridDim.x * blockDim.x) {
+    if (tag[n] != FLUID) continue;
+    long long id = cidx(k, n % k.nx, n / k.nx);
+    double r = A[id], u = A[id + k.plane] / r, v = A[id + 2 * k.plane] / r;
+    double p = (k.gamma - 1.0) * (A[id + 3 * k.plane] - 0.5 * r * (u * u + v * v));
+    double c = sqrt(k.gamma * p / r);
+    double lam = (fabs(u) + c) / k.dx + (fabs(v) + c) / k.dy + vis / r;
+    lmax = fmax(lmax, lam);
+  }
+  for (int off = 16; off > 0; off >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
+  __shared__ double wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = lmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = wm[0];
+    for (int w = 1; w < 8; w++) m = fmax(m, wm[w]);
+    atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch) {
+  cudaMemsetAsync(&ds->lmax_bits, 0, sizeof(unsigned long long), s);
+  if (k.dt_fixed > 0.0) return;
+  int ncell = k.nx * k.ny;
+  int blocks = min((ncell + 255) / 256, 152 * 8);
+  k_dt<<<blocks, 256, 0, s>>>(k, A, tag, ds);
+  *nlaunch += 1;
+}
+
+__device__ inline double step_dt(const Consts &k, const DevState *ds) {
+  if (k.dt_fixed > 0.0) return k.dt_fixed;
+  return k.cfl / __longlong_as_double((long long)ds->lmax_bits);
+}
+
+// stage c-coefficients of SSP-RK3: t_k = t + c_k dt
+__device__ inline double stage_time(const Consts &k, const DevState *ds, int stage) {
+  double dt = step_dt(k, ds);
+  return stage == 1 ? ds->t : (stage == 2 ? ds->t + dt : ds->t + 0.5 * dt);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 4.4-4.6, Sec. 5: rebuild IB nodes (pass 0) or ghost nodes (pass 1)
+// from their stencils.  Primitives p, u, v, T are interpolated at the probe
+// / image point; velocity is Dirichlet (Eq. 4), linear along the normal
+// through the wall velocity at P'; pressure is Neumann with
+// dp/dn = -rho n.a_wall (Eq. 5-6); temperature is adiabatic (Eq. 8).
+// One thread per list entry; in place on the stage array.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_recon_f64(Consts k, double *U, const ibm_stencil *__restrict__ st,
+                                                   int cap, const DevState *__restrict__ ds, int stage, int pass) {
+  const int lo = pass == 0 ? 0 : ds->offset[1];
+  const int hi = min(pass == 0 ? ds->offset[1] : ds->offset[4], cap);
+  const int e = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= hi) return;
+  const ibm_stencil &s = st[e];
+  if (s.mask == 0) return;
+  double X[2], V[2], Acc[2];
+  motion_at(k.motion, stage_time(k, ds, stage), X, V, Acc);
+  double qp[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = 0; q < 4; q++) {
+    if (!(s.mask >> q & 1)) continue;
+    long long id = cidx(k, s.i0 + (q & 1), s.j0 + (q >> 1));
+    double r = U[id], u = U[id + k.plane] / r, v = U[id + 2 * k.plane] / r;
+    double p = (k.gamma - 1.0) * (U[id + 3 * k.plane] - 0.5 * r * (u * u + v * v));
+    double w = s.w[q];
+    qp[0] += w * p;
+    qp[1] += w * u;
+    qp[2] += w * v;
+    qp[3] += w * (p / (r * k.R));
+  }
+  const double ratio = s.xi_node / s.xi_probe;
+  const double rho_p = qp[0] / (k.R * qp[3]);
+  const double g = -rho_p * (s.nx * Acc[0] + s.ny * Acc[1]);
+  const double p = qp[0] - (s.xi_probe - s.xi_node) * g;
+  const double u = V[0] + (qp[1] - V[0]) * ratio;
+  const double v = V[1] + (qp[2] - V[1]) * ratio;
+  const double T = qp[3];
+  const double r = p / (k.R * T);
+  const long long id = cidx(k, s.cell % k.nx, s.cell / k.nx);
+  U[id] = r;
+  U[id + k.plane] = r * u;
+  U[id + 2 * k.plane] = r * v;
+  U[id + 3 * k.plane] = p / (k.gamma - 1.0) + 0.5 * r * (u * u + v * v);
+}
+
+void launch_recon_f64(const Consts &k, double *U, const ibm_stencil *st, int cap, const DevState *ds, int stage,
+                      cudaStream_t s, int *nlaunch) {
+  if (cap <= 0) return;
+  int blocks = (cap + 127) / 128;
+  k_recon_f64<<<blocks, 128, 0, s>>>(k, U, st, cap, ds, stage, 0);
+  k_recon_f64<<<blocks, 128, 0, s>>>(k, U, st, cap, ds, stage, 1);
+  *nlaunch += 2;
+}
+
+// ---------------------------------------------------------------------------
+// Domain halos: free-stream Dirichlet, zero-gradient outflow, or periodic.
+// A halo cell beyond both an x side and a y side takes the x rule applied to
+// the y-filled column, i.e. the free stream if either side is free stream,
+// otherwise the interior cell both source maps point to.
+// ---------------------------------------------------------------------------
+__device__ inline int halo_src(int side_bc, int idx, int n, bool low) {
+  // returns the interior index feeding halo index idx, or -1 for free stream
+  if (side_bc == IBM_BC_PERIODIC) return low ? idx + n : idx - n;
+  if (side_bc == IBM_BC_OUTFLOW) return low ? 0 : n - 1;
+  return -1;
+}
+
+template <typename T>
+__global__ void k_bc(Consts k, T *U, T f0, T f1, T f2, T f3) {
+  const int nx = k.nx, ny = k.ny;
+  const int ny_side = NG * nx;          // cells per y side
+  const int nx_side = NG * (ny + 2 * NG);  // cells per x side
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j;
+  if (t < 2 * ny_side) {
+    int side = t / ny_side, r = t % ny_side;
+    int g = r / nx + 1;
+    i = r % nx;
+    j = side == 0 ? -g : ny - 1 + g;
+  } else if (t < 2 * ny_side + 2 * nx_side) {
+    t -= 2 * ny_side;
+    int side = t / nx_side, r = t % nx_side;
+    int g = r / (ny + 2 * NG) + 1;
+    j = r % (ny + 2 * NG) - NG;
+    i = side == 0 ? -g : nx - 1 + g;
+  } else {
+    return;
+  }
+  int si = i, sj = j;
+  bool fs = false;
+  if (i < 0 || i >= nx) {
+    int b = k.bc[i < 0 ? 0 : 1];
+    si = halo_src(b, i, nx, i < 0);
+    fs |= si < 0;
+  }
+  if (j < 0 || j >= ny) {
+    int b = k.bc[j < 0 ? 2 : 3];
+    sj = halo_src(b, j, ny, j < 0);
+    fs |= sj < 0;
+  }
+  long long d = cidx(k, i, j);
+  if (fs) {
+    U[d] = f0;
+    U[d + k.plane] = f1;
+    U[d + 2 * k.plane] = f2;
+    U[d + 3 * k.plane] = f3;
+  } else {
+    long long s = cidx(k, si, sj);
+    for (int v = 0; v < 4; v++) U[d + v * k.plane] = U[s + v * k.plane];
+  }
+}
+
+void launch_bc_f64(const Consts &k, double *U, cudaStream_t s) {
+  int n = 2 * NG * k.nx + 2 * NG * (k.ny + 2 * NG);
+  k_bc<double><<<(n + 255) / 256, 256, 0, s>>>(k, U, k.Uinf[0], k.Uinf[1], k.Uinf[2], k.Uinf[3]);
+}
+
+void launch_bc_f32(const Consts &k, float *U, cudaStream_t s) {
+  int n = 2 * NG * k.nx + 2 * NG * (k.ny + 2 * NG);
+  k_bc<float><<<(n + 255) / 256, 256, 0, s>>>(k, U, 0.f, 0.f, 0.f, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2: fifth-order WENO (Jiang-Shu smoothness indicators, linear weights
+// 1/10, 6/10, 3/10, eps = 1e-6); value at the face right of f2.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R weno5(R f0, R f1, R f2, R f3, R f4) {
+  const R eps = R(1e-6);
+  R a = f0 - R(2) * f1 + f2, b = f0 - R(4) * f1 + R(3) * f2;
+  R b0 = R(13.0 / 12.0) * a * a + R(0.25) * b * b;
+  a = f1 - R(2) * f2 + f3;
+  b = f1 - f3;
+  R b1 = R(13.0 / 12.0) * a * a + R(0.25) * b * b;
+  a = f2 - R(2) * f3 + f4;
+  b = R(3) * f2 - R(4) * f3 + f4;
+  R b2 = R(13.0 / 12.0) * a * a + R(0.25) * b * b;
+  R q0 = (R(2) * f0 - R(7) * f1 + R(11) * f2) * R(1.0 / 6.0);
+  R q1 = (-f1 + R(5) * f2 + R(2) * f3) * R(1.0 / 6.0);
+  R q2 = (R(2) * f2 + R(5) * f3 - f4) * R(1.0 / 6.0);
+  R e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+  // a_k = d_k / e_k^2, normalised; one division for all three weights
+  R e01 = e0 * e1, e12 = e1 * e2, e02 = e0 * e2;
+  R a0 = R(0.1) * e12 * e12, a1 = R(0.6) * e02 * e02, a2 = R(0.3) * e01 * e01;
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2: LDFSS(0) face flux (plain, Mr^2 = 1: explicit time stepping does
+// not precondition the dissipation).  States (rho, u, v, p); normal along
+// the first velocity component un, tangential ut.  F = (mass, normal
+// momentum, tangential momentum, energy).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ldfss_f64(double rL, double unL, double utL, double pL, double rR, double unR,
+                                          double utR, double pR, double gamma, double F[4]) {
+  const double gg = gamma / (gamma - 1.0);
+  const double cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+  const double HL = gg * pL / rL + 0.5 * (unL * unL + utL * utL);
+  const double HR = gg * pR / rR + 0.5 * (unR * unR + utR * utR);
+  const double cs = 0.5 * (cL + cR);
+  const double ics = 1.0 / cs;
+  const double ML = unL * ics, MR = unR * ics;
+  const double aL = ML >= 0.0 ? 1.0 : 0.0;
+  const double aR = MR >= 0.0 ? 0.0 : 1.0;
+  const double tL = 1.0 - floor(fabs(ML)), tR = 1.0 - floor(fabs(MR));
+  const double bL = -fmax(tL, 0.0), bR = -fmax(tR, 0.0);
+  const double MpL = 0.25 * (ML + 1.0) * (ML + 1.0);
+  const double MmR = -0.25 * (MR - 1.0) * (MR - 1.0);
+  const double CVL = aL * (1.0 + bL) * ML - bL * MpL;
+  const double CVR = aR * (1.0 + bR) * MR - bR * MmR;
+  const double sq = sqrt(0.5 * (ML * ML + MR * MR)) - 1.0;
+  const double Mh = 0.25 * bL * bR * sq * sq;
+  const double dp = pL - pR, adp = fabs(dp);
+  const double ic2 = 0.5 * ics * ics;
+  const double MhP = Mh * (1.0 - (dp + adp) * ic2 / rL);
+  const double MhM = Mh * (1.0 - (adp - dp) * ic2 / rR);
+  const double Cp = CVL - MhP, Cm = CVR + MhM;
+  const double PpL = MpL * (2.0 - ML);
+  const double PmR = -MmR * (2.0 + MR);
+  const double DL = aL * (1.0 + bL) - bL * PpL;
+  const double DR = aR * (1.0 + bR) - bR * PmR;
+  const double mL = rL * cs * Cp, mR = rR * cs * Cm;
+  F[0] = mL + mR;
+  F[1] = mL * unL + mR * unR + DL * pL + DR * pR;
+  F[2] = mL * utL + mR * utR;
+  F[3] = mL * HL + mR * HR;
+}
+
+// ---------------------------------------------------------------------------
+// Fused residual + stage update, FP64.  One 16x16 tile of cells per block:
+// the tile and its 3-cell halo are loaded once, converted to primitives in
+// shared memory; every x- and y-face of the tile is computed once (WENO5 +
+// LDFSS + central viscous flux); each fluid cell then takes the flux
+// divergence and applies its SSP-RK3 stage:
+//   stage 1: out = Un + dt L(in)
+//   stage 2: out = 3/4 Un + 1/4 (in + dt L(in))
+//   stage 3: out = 1/3 Un + 2/3 (in + dt L(in))
+// Tiles without a fluid cell exit at once.
+// ---------------------------------------------------------------------------
+constexpr int TX = 16, TY = 16, HX = TX + 2 * NG, HY = TY + 2 * NG;
+
+template <int STAGE>
+__global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, const double *__restrict__ In,
+                                                   double *Out, const uint8_t *__restrict__ tag,
+                                                   const DevState *__restrict__ ds) {
+  __shared__ double sq[4][HY][HX];  // rho, u, v, p
+  __shared__ double sT[HY][HX];     // temperature
+  __shared__ double sfx[4][TY][TX + 1];
+  __shared__ double sfy[4][TY + 1][TX];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int ci = i0 + tx, cj = j0 + ty;
+  const bool inside = ci < k.nx && cj < k.ny;
+  const bool fluid = inside && tag[cj * k.nx + ci] == FLUID;
+  if (!__syncthreads_or(fluid)) return;
+
+  const long long P = k.plane;
+  const double g1 = k.gamma - 1.0;
+  for (int m = threadIdx.x; m < HX * HY; m += 256) {
+    const int a = m % HX, b = m / HX;
+    const int gi = min(i0 - NG + a, k.nx + NG - 1), gj = min(j0 - NG + b, k.ny + NG - 1);
+    const long long id = cidx(k, gi, gj);
+    const double r = In[id];
+    const double ir = 1.0 / r;
+    const double u = In[id + P] * ir, v = In[id + 2 * P] * ir;
+    const double p = g1 * (In[id + 3 * P] - 0.5 * r * (u * u + v * v));
+    sq[0][b][a] = r;
+    sq[1][b][a] = u;
+    sq[2][b][a] = v;
+    sq[3][b][a] = p;
+    sT[b][a] = p * ir / k.R;
+  }
+  __syncthreads();
+
+  const double mu = k.mu, kap = k.kappa;
+  const double idx = 1.0 / k.dx, idy = 1.0 / k.dy;
+  // x-faces: face f sits between local columns f+2 and f+3 (global i0-1+f, i0+f)
+  for (int m = threadIdx.x; m < (TX + 1) * TY; m += 256) {
+    const int f = m % (TX + 1), row = m / (TX + 1);
+    const int b = row + NG;
+    double qL[4], qR[4];
+    for (int v = 0; v < 4; v++) {
+      const double *s = &sq[v][b][f];
+      qL[v] = weno5(s[0], s[1], s[2], s[3], s[4]);
+      qR[v] = weno5(s[5], s[4], s[3], s[2], s[1]);
+    }
+    if (!(qL[0] > 0.0) || !(qL[3] > 0.0) || !(qR[0] > 0.0) || !(qR[3] > 0.0)) {
+      for (int v = 0; v < 4; v++) {
+        qL[v] = sq[v][b][f + 2];
+        qR[v] = sq[v][b][f + 3];
+      }
+    }
+    double F[4];
+    ldfss_f64(qL[0], qL[1], qL[2], qL[3], qR[0], qR[1], qR[2], qR[3], k.gamma, F);
+    const int a = f + 2, a1 = f + 3;
+    const double ux = (sq[1][b][a1] - sq[1][b][a]) * idx;
+    const double vx = (sq[2][b][a1] - sq[2][b][a]) * idx;
+    const double Tx = (sT[b][a1] - sT[b][a]) * idx;
+    const double uy = (sq[1][b + 1][a] - sq[1][b - 1][a] + sq[1][b + 1][a1] - sq[1][b - 1][a1]) * (0.25 * idy);
+    const double vy = (sq[2][b + 1][a] - sq[2][b - 1][a] + sq[2][b + 1][a1] - sq[2][b - 1][a1]) * (0.25 * idy);
+    const double txx = mu * ((4.0 / 3.0) * ux - (2.0 / 3.0) * vy);
+    const double txy = mu * (uy + vx);
+    const double uf = 0.5 * (sq[1][b][a] + sq[1][b][a1]), vf = 0.5 * (sq[2][b][a] + sq[2][b][a1]);
+    sfx[0][row][f] = F[0];
+    sfx[1][row][f] = F[1] - txx;
+    sfx[2][row][f] = F[2] - txy;
+    sfx[3][row][f] = F[3] - (uf * txx + vf * txy + kap * Tx);
+  }
+  // y-faces: face f sits between local rows f+2 and f+3
+  for (int m = threadIdx.x; m < TX * (TY + 1); m += 256) {
+    const int col = m % TX, f = m / TX;
+    const int a = col + NG;
+    double qL[4], qR[4];
+    for (int v = 0; v < 4; v++) {
+      const double s0 = sq[v][f][a], s1 = sq[v][f + 1][a], s2 = sq[v][f + 2][a];
+      const double s3 = sq[v][f + 3][a], s4 = sq[v][f + 4][a], s5 = sq[v][f + 5][a];
+      qL[v] = weno5(s0, s1, s2, s3, s4);
+      qR[v] = weno5(s5, s4, s3, s2, s1);
+    }
+    if (!(qL[0] > 0.0) || !(qL[3] > 0.0) || !(qR[0] > 0.0) || !(qR[3] > 0.0)) {
+      for (int v = 0; v < 4; v++) {
+        qL[v] = sq[v][f + 2][a];
+        qR[v] = sq[v][f + 3][a];
+      }
+    }
+    double F[4];
+    // normal velocity v, tangential u
+    ldfss_f64(qL[0], qL[2], qL[1], qL[3], qR[0], qR[2], qR[1], qR[3], k.gamma, F);
+    const int b = f + 2, b1 = f + 3;
+    const double uy = (sq[1][b1][a] - sq[1][b][a]) * idy;
+    const double vy = (sq[2][b1][a] - sq[2][b][a]) * idy;
+    const double Ty = (sT[b1][a] - sT[b][a]) * idy;
+    const double ux = (sq[1][b][a + 1] - sq[1][b][a - 1] + sq[1][b1][a + 1] - sq[1][b1][a - 1]) * (0.25 * idx);
+    const double vx = (sq[2][b][a + 1] - sq[2][b][a - 1] + sq[2][b1][a + 1] - sq[2][b1][a - 1]) * (0.25 * idx);
+    const double tyy = mu * ((4.0 / 3.0) * vy - (2.0 / 3.0) * ux);
+    const double txy = mu * (uy + vx);
+    const double uf = 0.5 * (sq[1][b][a] + sq[1][b1][a]), vf = 0.5 * (sq[2][b][a] + sq[2][b1][a]);
+    sfy[0][f][col] = F[0];
+    sfy[1][f][col] = F[2] - txy;
+    sfy[2][f][col] = F[1] - tyy;
+    sfy[3][f][col] = F[3] - (uf * txy + vf * tyy + kap * Ty);
+  }
+  __syncthreads();
+  if (!fluid) return;
+  const double dt = step_dt(k, ds);
+  const long long id = cidx(k, ci, cj);
+  for (int v = 0; v < 4; v++) {
+    const double L = -((sfx[v][ty][tx + 1] - sfx[v][ty][tx]) * idx + (sfy[v][ty + 1][tx] - sfy[v][ty][tx]) * idy);
+    const long long o = id + v * P;
+    double r;
+    if (STAGE == 1) r = Un[o] + dt * L;
+    else if (STAGE == 2) r = 0.75 * Un[o] + 0.25 * (In[o] + dt * L);
+    else r = (1.0 / 3.0) * Un[o] + (2.0 / 3.0) * (In[o] + dt * L);
+    Out[o] = r;
+  }
+}
+
+void launch_stage_f64(const Consts &k, int stage, const double *Un, const double *In, double *Out,
+                      const uint8_t *tag, const DevState *ds, cudaStream_t s) {
+  dim3 grid((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY);
+  if (stage == 1) k_stage_f64<1><<<grid, 256, 0, s>>>(k, Un, In, Out, tag, ds);
+  else if (stage == 2) k_stage_f64<2><<<grid, 256, 0, s>>>(k, Un, In, Out, tag, ds);
+  else k_stage_f64<3><<<grid, 256, 0, s>>>(k, Un, In, Out, tag, ds);
+}
+
+__global__ void k_step_end(DevState *ds, Consts k) {
+  double dt = step_dt(k, ds);
+  ds->dt = dt;
+  ds->t = ds->t + dt;
+  ds->steps += 1;
+}
+
+void launch_step_end(const Consts &k, DevState *ds, cudaStream_t s) { k_step_end<<<1, 1, 0, s>>>(ds, k); }
+
+}  // namespace ibm

@@ -1,0 +1,366 @@
+// FP32-bulk flow kernels.
+//
+// Stage values, reconstruction and fluxes run in FP32 on perturbations from
+// the free stream, dU = (rho - rho_inf, rho u - rho_inf u_inf,
+// rho v - rho_inf v_inf, W'), W' = (rho E - rho_inf E_inf) - H_inf (rho -
+// rho_inf).  Primitives are (rho', u, v, p') with p' = p - p_inf and
+// T' = T - T_inf formed without ever adding p_inf or H_inf to an FP32 value,
+// so O(M^2) pressure and temperature fluctuations keep their FP32 precision
+// at any free-stream Mach number.  The conserved state is accumulated in FP64
+// at the last stage of every step (FP64 U^{n+1} from FP32 U^(2) and L).
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+struct PertConsts {  // FP32 copies of the free-stream constants
+  float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin;
+};
+
+__host__ inline PertConsts pert_consts(const Consts &k) {
+  PertConsts c;
+  c.gamma = (float)k.gamma;
+  c.g1 = (float)(k.gamma - 1.0);
+  c.gg = (float)(k.gamma / (k.gamma - 1.0));
+  c.R = (float)k.R;
+  c.Hinf = (float)k.Hinf;
+  c.ux = (float)k.uinf[0];
+  c.uy = (float)k.uinf[1];
+  c.mu = (float)k.mu;
+  c.kappa = (float)k.kappa;
+  c.idx = (float)(1.0 / k.dx);
+  c.idy = (float)(1.0 / k.dy);
+  c.dmin = (float)k.dmin;
+  return c;
+}
+
+// perturbation conserved -> (rho', u, v, p', T')
+__device__ __forceinline__ void pert_prim(const PertConsts &c, float dr, float dmx, float dmy, float W, float &u,
+                                          float &v, float &pp, float &Tp) {
+  const float r = 1.f + dr;
+  const float ir = 1.f / r;
+  u = (c.ux + dmx) * ir;
+  v = (c.uy + dmy) * ir;
+  const float du = (dmx - dr * c.ux) * ir, dv = (dmy - dr * c.uy) * ir;
+  const float dq = du * (u + c.ux) + dv * (v + c.uy);  // |u|^2 - |u_inf|^2
+  const float ke = 0.5f * (dr * (u * u + v * v) + dq);  // (rho |u|^2 - rho_inf |u_inf|^2) / 2
+  pp = c.g1 * (W + c.Hinf * dr - ke);
+  Tp = (pp - c.R * dr) * ir / c.R;
+}
+
+// (p', u, v, T') -> perturbation conserved
+__device__ __forceinline__ void prim_pert(const PertConsts &c, float pp, float u, float v, float Tp, float &dr,
+                                          float &dmx, float &dmy, float &W) {
+  dr = (pp - c.R * Tp) / (c.R * (1.f + Tp));
+  dmx = dr * u + (u - c.ux);
+  dmy = dr * v + (v - c.uy);
+  const float dq = (u - c.ux) * (u + c.ux) + (v - c.uy) * (v + c.uy);
+  const float ke = 0.5f * (dr * (u * u + v * v) + dq);
+  W = pp / c.g1 + ke - c.Hinf * dr;
+}
+
+// FP64 absolute conserved -> FP32 perturbation
+__device__ __forceinline__ void abs_to_pert(const Consts &k, double r, double mx, double my, double E, float &dr,
+                                            float &dmx, float &dmy, float &W) {
+  const double d = r - 1.0;
+  dr = (float)d;
+  dmx = (float)(mx - k.Uinf[1]);
+  dmy = (float)(my - k.Uinf[2]);
+  W = (float)((E - k.Uinf[3]) - k.Hinf * d);
+}
+
+__global__ void k_to_pert(Consts k, const double *__restrict__ A, float *__restrict__ M) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= k.plane) return;
+  const long long P = k.plane;
+  float a, b, c, d;
+  abs_to_pert(k, A[n], A[n + P], A[n + 2 * P], A[n + 3 * P], a, b, c, d);
+  M[n] = a;
+  M[n + P] = b;
+  M[n + 2 * P] = c;
+  M[n + 3 * P] = d;
+}
+
+void launch_to_pert(const Consts &k, const double *A, float *M, cudaStream_t s) {
+  k_to_pert<<<(unsigned)((k.plane + 255) / 256), 256, 0, s>>>(k, A, M);
+}
+
+__device__ inline double step_dt32(const Consts &k, const DevState *ds) {
+  if (k.dt_fixed > 0.0) return k.dt_fixed;
+  return k.cfl / __longlong_as_double((long long)ds->lmax_bits);
+}
+
+// ---------------------------------------------------------------------------
+// IB / ghost reconstruction in perturbation form (same rules as the FP64
+// path: Dirichlet velocity Eq. 4, Neumann pressure Eq. 5-6, adiabatic
+// temperature Eq. 8).  At stage 1 the rebuilt value is also written to the
+// FP64 state so both copies of U^n agree on IB and ghost nodes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_recon_f32(Consts k, PertConsts c, float *U, double *A,
+                                                   const ibm_stencil *__restrict__ st, int cap,
+                                                   const DevState *__restrict__ ds, int stage, int pass) {
+  const int lo = pass == 0 ? 0 : ds->offset[1];
+  const int hi = min(pass == 0 ? ds->offset[1] : ds->offset[4], cap);
+  const int e = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= hi) return;
+  const ibm_stencil &s = st[e];
+  if (s.mask == 0) return;
+  const double dt = step_dt32(k, ds);
+  const double ts = stage == 1 ? ds->t : (stage == 2 ? ds->t + dt : ds->t + 0.5 * dt);
+  double X[2], V[2], Acc[2];
+  motion_at(k.motion, ts, X, V, Acc);
+  const long long P = k.plane;
+  float qp[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int q = 0; q < 4; q++) {
+    if (!(s.mask >> q & 1)) continue;
+    const long long id = cidx(k, s.i0 + (q & 1), s.j0 + (q >> 1));
+    float u, v, pp, Tp;
+    pert_prim(c, U[id], U[id + P], U[id + 2 * P], U[id + 3 * P], u, v, pp, Tp);
+    const float w = (float)s.w[q];
+    qp[0] += w * pp;
+    qp[1] += w * u;
+    qp[2] += w * v;
+    qp[3] += w * Tp;
+  }
+  const float ratio = (float)(s.xi_node / s.xi_probe);
+  const float rho_p = 1.f + (qp[0] - c.R * qp[3]) / (c.R * (1.f + qp[3]));
+  const float g = -rho_p * (float)(s.nx * Acc[0] + s.ny * Acc[1]);
+  const float pp = qp[0] - (float)(s.xi_probe - s.xi_node) * g;
+  const float Vx = (float)V[0], Vy = (float)V[1];
+  const float u = Vx + (qp[1] - Vx) * ratio;
+  const float v = Vy + (qp[2] - Vy) * ratio;
+  float dr, dmx, dmy, W;
+  prim_pert(c, pp, u, v, qp[3], dr, dmx, dmy, W);
+  const long long id = cidx(k, s.cell % k.nx, s.cell / k.nx);
+  U[id] = dr;
+  U[id + P] = dmx;
+  U[id + 2 * P] = dmy;
+  U[id + 3 * P] = W;
+  if (stage == 1) {
+    A[id] = 1.0 + (double)dr;
+    A[id + P] = k.Uinf[1] + (double)dmx;
+    A[id + 2 * P] = k.Uinf[2] + (double)dmy;
+    A[id + 3 * P] = k.Uinf[3] + (double)W + k.Hinf * (double)dr;
+  }
+}
+
+void launch_recon_f32(const Consts &k, float *U, double *A, const ibm_stencil *st, int cap, const DevState *ds,
+                      int stage, cudaStream_t s, int *nlaunch) {
+  if (cap <= 0) return;
+  PertConsts c = pert_consts(k);
+  int blocks = (cap + 127) / 128;
+  k_recon_f32<<<blocks, 128, 0, s>>>(k, c, U, A, st, cap, ds, stage, 0);
+  k_recon_f32<<<blocks, 128, 0, s>>>(k, c, U, A, st, cap, ds, stage, 1);
+  *nlaunch += 2;
+}
+
+__device__ __forceinline__ float weno5f(float f0, float f1, float f2, float f3, float f4) {
+  const float eps = 1e-6f;
+  float a = f0 - 2.f * f1 + f2, b = f0 - 4.f * f1 + 3.f * f2;
+  const float b0 = (13.f / 12.f) * a * a + 0.25f * b * b;
+  a = f1 - 2.f * f2 + f3;
+  b = f1 - f3;
+  const float b1 = (13.f / 12.f) * a * a + 0.25f * b * b;
+  a = f2 - 2.f * f3 + f4;
+  b = 3.f * f2 - 4.f * f3 + f4;
+  const float b2 = (13.f / 12.f) * a * a + 0.25f * b * b;
+  const float q0 = 2.f * f0 - 7.f * f1 + 11.f * f2;
+  const float q1 = -f1 + 5.f * f2 + 2.f * f3;
+  const float q2 = 2.f * f2 + 5.f * f3 - f4;
+  // a_k = d_k / (eps + b_k)^2: scale by the three squared sums to avoid
+  // three divisions; the 1/6 of the candidate stencils folds into the last one
+  const float e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+  const float e01 = e0 * e1, e12 = e1 * e2, e02 = e0 * e2;
+  const float a0 = 0.1f * e12 * e12, a1 = 0.6f * e02 * e02, a2 = 0.3f * e01 * e01;
+  return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, 6.f * (a0 + a1 + a2));
+}
+
+// LDFSS(0) in perturbation form (Mr^2 = 1).  States (rho', un, ut, p');
+// un_inf / ut_inf the free-stream components along the face normal and
+// tangent.  Momentum flux drops the constant p_inf n (its divergence is
+// zero); D_L + D_R - 1 is formed in factored form for two subsonic sides so
+// p_inf (D_L + D_R - 1) keeps its precision.
+__device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float unL, float utL, float ppL,
+                                           float drR, float unR, float utR, float ppR, float un_inf, float ut_inf,
+                                           float F[4]) {
+  const float rL = 1.f + drL, rR = 1.f + drR;
+  const float irL = 1.f / rL, irR = 1.f / rR;
+  const float cL = sqrtf(c.gamma * (c.R + ppL) * irL), cR = sqrtf(c.gamma * (c.R + ppR) * irR);
+  const float HL = c.gg * (ppL - c.R * drL) * irL +
+                   0.5f * ((unL - un_inf) * (unL + un_inf) + (utL - ut_inf) * (utL + ut_inf));
+  const float HR = c.gg * (ppR - c.R * drR) * irR +
+                   0.5f * ((unR - un_inf) * (unR + un_inf) + (utR - ut_inf) * (utR + ut_inf));
+  const float cs = 0.5f * (cL + cR);
+  const float ics = 1.f / cs;
+  const float ML = unL * ics, MR = unR * ics;
+  const float aL = ML >= 0.f ? 1.f : 0.f;
+  const float aR = MR >= 0.f ? 0.f : 1.f;
+  const bool subL = fabsf(ML) < 1.f, subR = fabsf(MR) < 1.f;
+  const float bL = subL ? -1.f : 0.f, bR = subR ? -1.f : 0.f;
+  const float MpL = 0.25f * (ML + 1.f) * (ML + 1.f);
+  const float MmR = -0.25f * (MR - 1.f) * (MR - 1.f);
+  const float CVL = aL * (1.f + bL) * ML - bL * MpL;
+  const float CVR = aR * (1.f + bR) * MR - bR * MmR;
+  const float sq = sqrtf(0.5f * (ML * ML + MR * MR)) - 1.f;
+  const float Mh = 0.25f * bL * bR * sq * sq;
+  const float dp = ppL - ppR, adp = fabsf(dp);
+  const float ic2 = 0.5f * ics * ics;
+  const float MhP = Mh * (1.f - (dp + adp) * ic2 * irL);
+  const float MhM = Mh * (1.f - (adp - dp) * ic2 * irR);
+  const float Cp = CVL - MhP, Cm = CVR + MhM;
+  const float PpL = MpL * (2.f - ML);
+  const float PmR = -MmR * (2.f + MR);
+  const float DL = aL * (1.f + bL) - bL * PpL;
+  const float DR = aR * (1.f + bR) - bR * PmR;
+  const float Dm1 = (subL && subR) ? 0.25f * (MR - ML) * (MR * MR + MR * ML + ML * ML - 3.f) : (DL + DR - 1.f);
+  const float mL = rL * cs * Cp, mR = rR * cs * Cm;
+  F[0] = mL + mR;
+  F[1] = mL * unL + mR * unR + c.R * Dm1 + DL * ppL + DR * ppR;
+  F[2] = mL * utL + mR * utR;
+  F[3] = mL * HL + mR * HR;
+}
+
+// ---------------------------------------------------------------------------
+// Fused residual + stage update in FP32 perturbation form, same tiling as
+// the FP64 kernel.  Stage 3 accumulates U^{n+1} in FP64 and refreshes the
+// FP32 mirror of U^{n+1}.
+// ---------------------------------------------------------------------------
+constexpr int TX = 16, TY = 16, HX = TX + 2 * NG, HY = TY + 2 * NG;
+
+template <int STAGE>
+__global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, const float *Mn,
+                                                   const float *__restrict__ In, float *Out, double *A,
+                                                   const uint8_t *__restrict__ tag,
+                                                   const DevState *__restrict__ ds) {
+  __shared__ float sq[4][HY][HX];  // rho', u, v, p'
+  __shared__ float sT[HY][HX];     // T'
+  __shared__ float sfx[4][TY][TX + 1];
+  __shared__ float sfy[4][TY + 1][TX];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int ci = i0 + tx, cj = j0 + ty;
+  const bool inside = ci < k.nx && cj < k.ny;
+  const bool fluid = inside && tag[cj * k.nx + ci] == FLUID;
+  if (!__syncthreads_or(fluid)) return;
+
+  const long long P = k.plane;
+  for (int m = threadIdx.x; m < HX * HY; m += 256) {
+    const int a = m % HX, b = m / HX;
+    const int gi = min(i0 - NG + a, k.nx + NG - 1), gj = min(j0 - NG + b, k.ny + NG - 1);
+    const long long id = cidx(k, gi, gj);
+    const float dr = In[id];
+    float u, v, pp, Tp;
+    pert_prim(c, dr, In[id + P], In[id + 2 * P], In[id + 3 * P], u, v, pp, Tp);
+    sq[0][b][a] = dr;
+    sq[1][b][a] = u;
+    sq[2][b][a] = v;
+    sq[3][b][a] = pp;
+    sT[b][a] = Tp;
+  }
+  __syncthreads();
+
+  const float mu = c.mu, kap = c.kappa, idx = c.idx, idy = c.idy;
+  for (int m = threadIdx.x; m < (TX + 1) * TY; m += 256) {
+    const int f = m % (TX + 1), row = m / (TX + 1);
+    const int b = row + NG;
+    float qL[4], qR[4];
+    for (int v = 0; v < 4; v++) {
+      const float *s = &sq[v][b][f];
+      qL[v] = weno5f(s[0], s[1], s[2], s[3], s[4]);
+      qR[v] = weno5f(s[5], s[4], s[3], s[2], s[1]);
+    }
+    if (!(qL[0] > -1.f) || !(qL[3] > -c.R) || !(qR[0] > -1.f) || !(qR[3] > -c.R)) {
+      for (int v = 0; v < 4; v++) {
+        qL[v] = sq[v][b][f + 2];
+        qR[v] = sq[v][b][f + 3];
+      }
+    }
+    float F[4];
+    ldfss_pert(c, qL[0], qL[1], qL[2], qL[3], qR[0], qR[1], qR[2], qR[3], c.ux, c.uy, F);
+    const int a = f + 2, a1 = f + 3;
+    const float ux = (sq[1][b][a1] - sq[1][b][a]) * idx;
+    const float vx = (sq[2][b][a1] - sq[2][b][a]) * idx;
+    const float Tx = (sT[b][a1] - sT[b][a]) * idx;
+    const float uy = (sq[1][b + 1][a] - sq[1][b - 1][a] + sq[1][b + 1][a1] - sq[1][b - 1][a1]) * (0.25f * idy);
+    const float vy = (sq[2][b + 1][a] - sq[2][b - 1][a] + sq[2][b + 1][a1] - sq[2][b - 1][a1]) * (0.25f * idy);
+    const float txx = mu * ((4.f / 3.f) * ux - (2.f / 3.f) * vy);
+    const float txy = mu * (uy + vx);
+    const float uf = 0.5f * (sq[1][b][a] + sq[1][b][a1]), vf = 0.5f * (sq[2][b][a] + sq[2][b][a1]);
+    sfx[0][row][f] = F[0];
+    sfx[1][row][f] = F[1] - txx;
+    sfx[2][row][f] = F[2] - txy;
+    sfx[3][row][f] = F[3] - (uf * txx + vf * txy + kap * Tx);
+  }
+  for (int m = threadIdx.x; m < TX * (TY + 1); m += 256) {
+    const int col = m % TX, f = m / TX;
+    const int a = col + NG;
+    float qL[4], qR[4];
+    for (int v = 0; v < 4; v++) {
+      const float s0 = sq[v][f][a], s1 = sq[v][f + 1][a], s2 = sq[v][f + 2][a];
+      const float s3 = sq[v][f + 3][a], s4 = sq[v][f + 4][a], s5 = sq[v][f + 5][a];
+      qL[v] = weno5f(s0, s1, s2, s3, s4);
+      qR[v] = weno5f(s5, s4, s3, s2, s1);
+    }
+    if (!(qL[0] > -1.f) || !(qL[3] > -c.R) || !(qR[0] > -1.f) || !(qR[3] > -c.R)) {
+      for (int v = 0; v < 4; v++) {
+        qL[v] = sq[v][f + 2][a];
+        qR[v] = sq[v][f + 3][a];
+      }
+    }
+    float F[4];
+    ldfss_pert(c, qL[0], qL[2], qL[1], qL[3], qR[0], qR[2], qR[1], qR[3], c.uy, c.ux, F);
+    const int b = f + 2, b1 = f + 3;
+    const float uy = (sq[1][b1][a] - sq[1][b][a]) * idy;
+    const float vy = (sq[2][b1][a] - sq[2][b][a]) * idy;
+    const float Ty = (sT[b1][a] - sT[b][a]) * idy;
+    const float ux = (sq[1][b][a + 1] - sq[1][b][a - 1] + sq[1][b1][a + 1] - sq[1][b1][a - 1]) * (0.25f * idx);
+    const float vx = (sq[2][b][a + 1] - sq[2][b][a - 1] + sq[2][b1][a + 1] - sq[2][b1][a - 1]) * (0.25f * idx);
+    const float tyy = mu * ((4.f / 3.f) * vy - (2.f / 3.f) * ux);
+    const float txy = mu * (uy + vx);
+    const float uf = 0.5f * (sq[1][b][a] + sq[1][b1][a]), vf = 0.5f * (sq[2][b][a] + sq[2][b1][a]);
+    sfy[0][f][col] = F[0];
+    sfy[1][f][col] = F[2] - txy;
+    sfy[2][f][col] = F[1] - tyy;
+    sfy[3][f][col] = F[3] - (uf * txy + vf * tyy + kap * Ty);
+  }
+  __syncthreads();
+  if (!fluid) return;
+  const double dtd = step_dt32(k, ds);
+  const float dt = (float)dtd;
+  const long long id = cidx(k, ci, cj);
+  float L[4];
+  for (int v = 0; v < 4; v++)
+    L[v] = -((sfx[v][ty][tx + 1] - sfx[v][ty][tx]) * idx + (sfy[v][ty + 1][tx] - sfy[v][ty][tx]) * idy);
+  if (STAGE == 1) {
+    for (int v = 0; v < 4; v++) Out[id + v * P] = Mn[id + v * P] + dt * L[v];
+  } else if (STAGE == 2) {
+    for (int v = 0; v < 4; v++) Out[id + v * P] = 0.75f * Mn[id + v * P] + 0.25f * (In[id + v * P] + dt * L[v]);
+  } else {
+    // FP64 accumulation of U^{n+1} = 1/3 U^n + 2/3 (U^(2) + dt L), absolute conserved variables
+    const double dr = In[id], dmx = In[id + P], dmy = In[id + 2 * P], W = In[id + 3 * P];
+    const double u2[4] = {1.0 + dr, k.Uinf[1] + dmx, k.Uinf[2] + dmy, k.Uinf[3] + W + k.Hinf * dr};
+    const double La[4] = {(double)L[0], (double)L[1], (double)L[2], (double)L[3] + k.Hinf * (double)L[0]};
+    double an[4];
+    for (int v = 0; v < 4; v++) {
+      an[v] = (1.0 / 3.0) * A[id + v * P] + (2.0 / 3.0) * (u2[v] + dtd * La[v]);
+      A[id + v * P] = an[v];
+    }
+    float a, b2, c2, d;
+    abs_to_pert(k, an[0], an[1], an[2], an[3], a, b2, c2, d);
+    float *Mw = const_cast<float *>(Mn);
+    Mw[id] = a;
+    Mw[id + P] = b2;
+    Mw[id + 2 * P] = c2;
+    Mw[id + 3 * P] = d;
+  }
+}
+
+void launch_stage_f32(const Consts &k, int stage, const float *Mn, const float *In, float *Out, double *A,
+                      const uint8_t *tag, const DevState *ds, cudaStream_t s) {
+  PertConsts c = pert_consts(k);
+  dim3 grid((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY);
+  if (stage == 1) k_stage_f32<1><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, A, tag, ds);
+  else if (stage == 2) k_stage_f32<2><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, A, tag, ds);
+  else k_stage_f32<3><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, A, tag, ds);
+}
+
+}  // namespace ibm

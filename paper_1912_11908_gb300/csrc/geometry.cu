@@ -1,0 +1,549 @@
+// Immersed-boundary geometry kernels: body pose, ray-casting classification,
+// IB / ghost tagging with ordered list compaction, closest features,
+// pseudo-normals, boundary points, probe / image points, interpolation
+// stencils, and the surface force integral.
+//
+// This translation unit is compiled with -fmad=false: every floating-point
+// result here is a sequence of IEEE binary64 basic operations (and sqrt) with
+// no contraction, so tags, lists and stencils are reproducible bit for bit by
+// any IEEE implementation that performs the same operations in the same
+// order.  No transcendental function is used on these paths.
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+// ---------------------------------------------------------------------------
+// Sec. 4.2: pseudo-normals.  Segment k of the CCW polyline runs from vertex k
+// to k+1; its outward normal is the travel direction turned clockwise.  The
+// 2-D vertex pseudo-normal weights its two incident segments equally (each
+// incident "face" enters Eq. 2 / Eq. 3 with the same weight) and is
+// normalised.  One thread per vertex.
+// ---------------------------------------------------------------------------
+__global__ void k_normals(int nv, const double *__restrict__ v, double *snx, double *sny, double *vnx,
+                          double *vny) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nv) return;
+  int k1 = (k + 1 == nv) ? 0 : k + 1;
+  int km = (k == 0) ? nv - 1 : k - 1;
+  // own segment normal
+  double ex = v[2 * k1] - v[2 * k], ey = v[2 * k1 + 1] - v[2 * k + 1];
+  double L = sqrt(ex * ex + ey * ey);
+  double nx = ey / L, ny = -ex / L;
+  snx[k] = nx;
+  sny[k] = ny;
+  // previous segment normal (recomputed with the same operations)
+  double fx = v[2 * k] - v[2 * km], fy = v[2 * k + 1] - v[2 * km + 1];
+  double Lm = sqrt(fx * fx + fy * fy);
+  double mx = fy / Lm, my = -fx / Lm;
+  double sx = mx + nx, sy = my + ny;
+  double S = sqrt(sx * sx + sy * sy);
+  if (S > 0.0) {
+    vnx[k] = sx / S;
+    vny[k] = sy / S;
+  } else {
+    vnx[k] = nx;
+    vny[k] = ny;
+  }
+}
+
+void launch_normals(int nv, const double *v, double *snx, double *sny, double *vnx, double *vny,
+                    cudaStream_t s) {
+  if (nv <= 0) return;
+  k_normals<<<(nv + 127) / 128, 128, 0, s>>>(nv, v, snx, sny, vnx, vny);
+}
+
+// ---------------------------------------------------------------------------
+// Body pose at the start of the step (prescribed translation) and its
+// axis-aligned bounding box.  One block.
+// ---------------------------------------------------------------------------
+__global__ void k_pose(Consts k, Geom g, DevState *ds) {
+  __shared__ double X[2];
+  if (threadIdx.x == 0) {
+    double V[2], A[2], P[2];
+    motion_at(k.motion, ds->t, P, V, A);
+    X[0] = P[0];
+    X[1] = P[1];
+    ds->pos[0] = P[0];
+    ds->pos[1] = P[1];
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < g.nv; v += blockDim.x) {
+    g.vx[v] = g.vref[2 * v] + X[0];
+    g.vy[v] = g.vref[2 * v + 1] + X[1];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b0 = g.vx[0], b1 = g.vx[0], b2 = g.vy[0], b3 = g.vy[0];
+    for (int v = 1; v < g.nv; v++) {
+      if (g.vx[v] < b0) b0 = g.vx[v];
+      if (g.vx[v] > b1) b1 = g.vx[v];
+      if (g.vy[v] < b2) b2 = g.vy[v];
+      if (g.vy[v] > b3) b3 = g.vy[v];
+    }
+    ds->bbox[0] = b0;
+    ds->bbox[1] = b1;
+    ds->bbox[2] = b2;
+    ds->bbox[3] = b3;
+  }
+}
+
+void launch_pose(const Consts &k, const Geom &g, DevState *ds, cudaStream_t s) {
+  k_pose<<<1, 256, 0, s>>>(k, g, ds);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.2: ray-casting classification of cell centres.  Ray along +x; the
+// segment A->B is crossed iff (A.y > P.y) != (B.y > P.y) and the crossing
+// abscissa A.x + (P.y-A.y)(B.x-A.x)/(B.y-A.y) lies strictly right of P; odd
+// parity = solid.  Centres outside the axis-aligned bounding box are fluid.
+// One thread per cell; vertices staged through shared memory in chunks.
+// ---------------------------------------------------------------------------
+constexpr int CLS_CHUNK = 512;
+
+__global__ void __launch_bounds__(256) k_classify(Consts k, Geom g, uint8_t *__restrict__ solid,
+                                                  const DevState *__restrict__ ds) {
+  __shared__ double sx[CLS_CHUNK + 1], sy[CLS_CHUNK + 1];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ncell = k.nx * k.ny;
+  const int i = n % k.nx, j = n / k.nx;
+  const double px = k.x0 + ((double)i + 0.5) * k.dx;
+  const double py = k.y0 + ((double)j + 0.5) * k.dy;
+  const double b0 = ds->bbox[0], b1 = ds->bbox[1], b2 = ds->bbox[2], b3 = ds->bbox[3];
+  const bool test = n < ncell && !(px < b0 || px > b1 || py < b2 || py > b3);
+  int odd = 0;
+  // the whole block walks the vertex list if any of its cells needs a test
+  if (__syncthreads_or(test)) {
+    for (int base = 0; base < g.nv; base += CLS_CHUNK) {
+      int cnt = min(CLS_CHUNK, g.nv - base);
+      __syncthreads();
+      for (int v = threadIdx.x; v <= cnt; v += blockDim.x) {
+        int src = base + v;
+        if (src == g.nv) src = 0;
+        if (v < cnt || src < g.nv) {
+          sx[v] = g.vx[src];
+          sy[v] = g.vy[src];
+        }
+      }
+      __syncthreads();
+      if (test) {
+        for (int e = 0; e < cnt; e++) {
+          double ax = sx[e], ay = sy[e], bx = sx[e + 1], by = sy[e + 1];
+          if ((ay > py) != (by > py)) {
+            double t1 = py - ay;
+            double t2 = bx - ax;
+            double t3 = by - ay;
+            double xint = ax + (t1 * t2) / t3;
+            if (xint > px) odd ^= 1;
+          }
+        }
+      }
+    }
+  }
+  if (n < ncell) solid[n] = (uint8_t)odd;
+}
+
+void launch_classify(const Consts &k, const Geom &g, uint8_t *solid, const DevState *ds, cudaStream_t s) {
+  int ncell = k.nx * k.ny;
+  if (g.nv <= 0) {
+    cudaMemsetAsync(solid, 0, (size_t)ncell, s);
+    return;
+  }
+  k_classify<<<(ncell + 255) / 256, 256, 0, s>>>(k, g, solid, ds);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.2 + Sec. 5: tags and ordered lists.
+//  IB  : fluid cell with a solid 4-neighbour.
+//  Gk  : solid cell whose nearest non-solid cell along a grid line is k = 1, 2
+//        or 3 cells away (three ghost layers for WENO5).
+// Lists are compacted in row-major cell order: per-block counts by warp
+// ballots, one-block scan of the block counts, then a ballot-ranked scatter.
+// ---------------------------------------------------------------------------
+constexpr int TAG_BLOCK = 1024;
+
+__device__ inline uint8_t tag_of(const Consts &k, const uint8_t *__restrict__ solid, int i, int j) {
+  const int nx = k.nx, ny = k.ny;
+  if (!solid[j * nx + i]) {
+    bool ib = (i + 1 < nx && solid[j * nx + i + 1]) || (i > 0 && solid[j * nx + i - 1]) ||
+              (j + 1 < ny && solid[(j + 1) * nx + i]) || (j > 0 && solid[(j - 1) * nx + i]);
+    return ib ? IB : FLUID;
+  }
+  for (int d = 1; d <= 3; d++) {
+    if ((i + d < nx && !solid[j * nx + i + d]) || (i - d >= 0 && !solid[j * nx + i - d]) ||
+        (j + d < ny && !solid[(j + d) * nx + i]) || (j - d >= 0 && !solid[(j - d) * nx + i]))
+      return (uint8_t)(G1 + d - 1);
+  }
+  return SOLID;
+}
+
+__device__ inline int list_kind(uint8_t t) {  // -1: not listed; 0 IB; 1..3 G1..G3
+  return t == IB ? 0 : (t >= G1 ? (int)t - G1 + 1 : -1);
+}
+
+__global__ void __launch_bounds__(TAG_BLOCK) k_tag_count(Consts k, const uint8_t *__restrict__ solid,
+                                                         uint8_t *__restrict__ tag, int *__restrict__ blockcounts) {
+  __shared__ int wc[TAG_BLOCK / 32][4];
+  const int n = blockIdx.x * TAG_BLOCK + threadIdx.x;
+  const int ncell = k.nx * k.ny;
+  int kind = -1;
+  if (n < ncell) {
+    uint8_t t = tag_of(k, solid, n % k.nx, n / k.nx);
+    tag[n] = t;
+    kind = list_kind(t);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < 4; q++) {
+    unsigned m = __ballot_sync(0xffffffffu, kind == q);
+    if (lane == 0) wc[warp][q] = __popc(m);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    int s = 0;
+    for (int w = 0; w < TAG_BLOCK / 32; w++) s += wc[w][threadIdx.x];
+    blockcounts[blockIdx.x * 4 + threadIdx.x] = s;
+  }
+}
+
+// exclusive scan of per-block counts for each kind (in place), totals and
+// kind offsets into the concatenated list (IB, G1, G2, G3)
+__global__ void __launch_bounds__(1024) k_scan_blocks(int nblk, int *blockcounts, DevState *ds, int cap) {
+  __shared__ int part[1024][4];
+  __shared__ int tot[4];
+  const int tid = threadIdx.x;
+  const int per = (nblk + 1023) / 1024;
+  const int b0 = tid * per, b1 = min(nblk, b0 + per);
+  int s[4] = {0, 0, 0, 0};
+  for (int b = b0; b < b1; b++)
+    for (int q = 0; q < 4; q++) s[q] += blockcounts[b * 4 + q];
+  for (int q = 0; q < 4; q++) part[tid][q] = s[q];
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the 1024 partial sums
+  for (int off = 1; off < 1024; off <<= 1) {
+    int v[4];
+    for (int q = 0; q < 4; q++) v[q] = tid >= off ? part[tid - off][q] : 0;
+    __syncthreads();
+    for (int q = 0; q < 4; q++) part[tid][q] += v[q];
+    __syncthreads();
+  }
+  if (tid == 1023)
+    for (int q = 0; q < 4; q++) tot[q] = part[1023][q];
+  __syncthreads();
+  int run[4];
+  for (int q = 0; q < 4; q++) run[q] = part[tid][q] - s[q];
+  for (int b = b0; b < b1; b++)
+    for (int q = 0; q < 4; q++) {
+      int c = blockcounts[b * 4 + q];
+      blockcounts[b * 4 + q] = run[q];
+      run[q] += c;
+    }
+  if (tid == 0) {
+    int off = 0;
+    for (int q = 0; q < 4; q++) {
+      ds->count[q] = tot[q];
+      ds->offset[q] = off;
+      off += tot[q];
+    }
+    ds->offset[4] = off;
+    if (off > cap) ds->err |= ERR_CAPACITY;
+  }
+}
+
+__global__ void __launch_bounds__(TAG_BLOCK) k_scatter(Consts k, const uint8_t *__restrict__ tag,
+                                                       const int *__restrict__ blockoff, const DevState *ds,
+                                                       ibm_stencil *__restrict__ st, int cap) {
+  __shared__ int wc[TAG_BLOCK / 32][4];
+  const int n = blockIdx.x * TAG_BLOCK + threadIdx.x;
+  const int ncell = k.nx * k.ny;
+  const int kind = n < ncell ? list_kind(tag[n]) : -1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int rank = 0;
+  for (int q = 0; q < 4; q++) {
+    unsigned m = __ballot_sync(0xffffffffu, kind == q);
+    if (lane == 0) wc[warp][q] = __popc(m);
+    if (kind == q) rank = __popc(m & lt);
+  }
+  __syncthreads();
+  if (kind >= 0) {
+    int before = 0;
+    for (int w = 0; w < warp; w++) before += wc[w][kind];
+    int pos = ds->offset[kind] + blockoff[blockIdx.x * 4 + kind] + before + rank;
+    if (pos < cap) {
+      st[pos].cell = n;
+      st[pos].kind = kind;
+    }
+  }
+}
+
+void launch_tags(const Consts &k, const uint8_t *solid, uint8_t *tag, int *blockcounts, DevState *ds, int cap,
+                 ibm_stencil *st, cudaStream_t s, int *nlaunch) {
+  const int ncell = k.nx * k.ny;
+  const int nblk = (ncell + TAG_BLOCK - 1) / TAG_BLOCK;
+  k_tag_count<<<nblk, TAG_BLOCK, 0, s>>>(k, solid, tag, blockcounts);
+  k_scan_blocks<<<1, 1024, 0, s>>>(nblk, blockcounts, ds, cap);
+  k_scatter<<<nblk, TAG_BLOCK, 0, s>>>(k, tag, blockcounts, ds, st, cap);
+  *nlaunch += 3;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 4.1: closest feature (exhaustive, ties -> lowest segment index).
+// ---------------------------------------------------------------------------
+__device__ void closest_feature(const Geom &g, double px, double py, int *feat, int *region, double *cxo,
+                                double *cyo) {
+  double best = INFINITY;
+  const int nv = g.nv;
+  for (int kk = 0; kk < nv; kk++) {
+    int k1 = (kk + 1 == nv) ? 0 : kk + 1;
+    double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
+    double ex = bx - ax, ey = by - ay;
+    double wx = px - ax, wy = py - ay;
+    double num = wx * ex + wy * ey;
+    double den = ex * ex + ey * ey;
+    double cx, cy;
+    int f, r;
+    if (num <= 0.0) {
+      cx = ax; cy = ay; f = kk; r = IBM_REGION_VERTEX;
+    } else if (num >= den) {
+      cx = bx; cy = by; f = k1; r = IBM_REGION_VERTEX;
+    } else {
+      double t = num / den;
+      cx = ax + t * ex; cy = ay + t * ey; f = kk; r = IBM_REGION_FACE;
+    }
+    double ddx = px - cx, ddy = py - cy;
+    double d2 = ddx * ddx + ddy * ddy;
+    if (d2 < best) {
+      best = d2; *feat = f; *region = r; *cxo = cx; *cyo = cy;
+    }
+  }
+}
+
+// Sec. 4.3: boundary point on the line through the node along the local
+// normal, nearest crossing on the surface side (behind a fluid node, ahead of
+// a ghost node); closest point if the line meets no segment on that side.
+__device__ void boundary_point(const Geom &g, double px, double py, double nx, double ny, bool ghost,
+                               double ccx, double ccy, double *bx, double *by, double *xi_node, int *fallback) {
+  double best = INFINITY, bs = 0.0;
+  bool found = false;
+  const int nv = g.nv;
+  for (int kk = 0; kk < nv; kk++) {
+    int k1 = (kk + 1 == nv) ? 0 : kk + 1;
+    double ax = g.vx[kk], ay = g.vy[kk];
+    double ex = g.vx[k1] - ax, ey = g.vy[k1] - ay;
+    double den = ex * ny - ey * nx;
+    if (den == 0.0) continue;
+    double wx = px - ax, wy = py - ay;
+    double u = (wx * ny - wy * nx) / den;
+    if (u < 0.0 || u > 1.0) continue;
+    double s = (wx * ey - wy * ex) / den;
+    if (ghost ? (s < 0.0) : (s > 0.0)) continue;
+    double as = fabs(s);
+    if (as < best) {
+      best = as; bs = s; found = true;
+    }
+  }
+  if (found) {
+    *bx = px + bs * nx;
+    *by = py + bs * ny;
+    *xi_node = -bs;
+    *fallback = 0;
+  } else {
+    double ddx = px - ccx, ddy = py - ccy;
+    double d = sqrt(ddx * ddx + ddy * ddy);
+    *bx = ccx;
+    *by = ccy;
+    *xi_node = ghost ? -d : d;
+    *fallback = 1;
+  }
+}
+
+// Sec. 4.6 / Sec. 5: interpolation square around (X, Y); bilinear when all
+// four corners carry an allowed tag, inverse-distance (1/r^2) weights over
+// the allowed corners otherwise, all weight on a corner hit exactly.
+__device__ int interp_square(const Consts &k, const uint8_t *__restrict__ tag, double X, double Y,
+                             unsigned allowed, int *i0o, int *j0o, double w[4]) {
+  double gx = (X - k.x0) / k.dx - 0.5;
+  double gy = (Y - k.y0) / k.dy - 0.5;
+  int i0 = (int)floor(gx), j0 = (int)floor(gy);
+  int mask = 0;
+  for (int q = 0; q < 4; q++) {
+    int ci = i0 + (q & 1), cj = j0 + (q >> 1);
+    w[q] = 0.0;
+    if (ci < 0 || ci >= k.nx || cj < 0 || cj >= k.ny) continue;
+    if (allowed & (1u << tag[cj * k.nx + ci])) mask |= 1 << q;
+  }
+  *i0o = i0;
+  *j0o = j0;
+  if (mask == 15) {
+    double xc0 = k.x0 + ((double)i0 + 0.5) * k.dx;
+    double yc0 = k.y0 + ((double)j0 + 0.5) * k.dy;
+    double fx = (X - xc0) / k.dx;
+    double fy = (Y - yc0) / k.dy;
+    w[0] = (1.0 - fx) * (1.0 - fy);
+    w[1] = fx * (1.0 - fy);
+    w[2] = (1.0 - fx) * fy;
+    w[3] = fx * fy;
+  } else if (mask != 0) {
+    double inv[4] = {0.0, 0.0, 0.0, 0.0};
+    int hit = -1;
+    for (int q = 0; q < 4 && hit < 0; q++) {
+      if (!(mask >> q & 1)) continue;
+      double xk = k.x0 + ((double)(i0 + (q & 1)) + 0.5) * k.dx;
+      double yk = k.y0 + ((double)(j0 + (q >> 1)) + 0.5) * k.dy;
+      double rx = X - xk, ry = Y - yk;
+      double r2 = rx * rx + ry * ry;
+      if (r2 == 0.0) hit = q;
+      else inv[q] = 1.0 / r2;
+    }
+    if (hit >= 0) {
+      w[hit] = 1.0;
+    } else {
+      double s = 0.0;
+      for (int q = 0; q < 4; q++)
+        if (mask >> q & 1) s += inv[q];
+      for (int q = 0; q < 4; q++)
+        if (mask >> q & 1) w[q] = inv[q] / s;
+    }
+  }
+  return mask;
+}
+
+constexpr unsigned ALLOW_FLUID = 1u << FLUID;
+constexpr unsigned ALLOW_FLUID_IB = (1u << FLUID) | (1u << IB);
+
+// Sec. 4.1-4.6, Sec. 5: one stencil per listed node.  One thread per entry.
+__global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_t *__restrict__ tag,
+                                                  ibm_stencil *__restrict__ st, int cap, DevState *ds) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int total = min(ds->offset[4], cap);
+  if (e >= total) return;
+  ibm_stencil s = st[e];
+  const int kind = s.kind;
+  const int i = s.cell % k.nx, j = s.cell / k.nx;
+  const double px = k.x0 + ((double)i + 0.5) * k.dx;
+  const double py = k.y0 + ((double)j + 0.5) * k.dy;
+  int feat = 0, region = 0;
+  double ccx = 0.0, ccy = 0.0;
+  closest_feature(g, px, py, &feat, &region, &ccx, &ccy);
+  double nx, ny;
+  if (region == IBM_REGION_FACE) {
+    nx = g.snx[feat];
+    ny = g.sny[feat];
+  } else {
+    nx = g.vnx[feat];
+    ny = g.vny[feat];
+  }
+  double bx, by, xi_node;
+  int fb;
+  boundary_point(g, px, py, nx, ny, kind > 0, ccx, ccy, &bx, &by, &xi_node, &fb);
+  double xi_probe;
+  if (kind == 0) {
+    xi_probe = xi_node + k.h;
+  } else {
+    xi_probe = -xi_node;
+    if (xi_probe < 0.5 * k.dmin) xi_probe = 0.5 * k.dmin;
+  }
+  const unsigned allowed = kind == 0 ? ALLOW_FLUID : ALLOW_FLUID_IB;
+  int i0 = 0, j0 = 0, mask = 0, nstep = 0;
+  double w[4];
+  for (;;) {
+    double X = bx + xi_probe * nx, Y = by + xi_probe * ny;
+    mask = interp_square(k, tag, X, Y, allowed, &i0, &j0, w);
+    if (mask != 0 || nstep == 3) break;
+    xi_probe = xi_probe + k.dmin;
+    nstep++;
+  }
+  if (mask == 0) atomicOr(&ds->err, ERR_STENCIL);
+  s.feature = feat;
+  s.region = fb ? IBM_REGION_FALLBACK : region;
+  s.i0 = i0;
+  s.j0 = j0;
+  s.mask = mask;
+  s.nstep = nstep;
+  s.nx = nx;
+  s.ny = ny;
+  s.bx = bx;
+  s.by = by;
+  s.xi_node = xi_node;
+  s.xi_probe = xi_probe;
+  for (int q = 0; q < 4; q++) s.w[q] = w[q];
+  st[e] = s;
+}
+
+void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
+                     cudaStream_t s) {
+  if (cap <= 0) return;
+  k_stencils<<<(cap + 127) / 128, 128, 0, s>>>(k, g, tag, st, cap, ds);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 6, Eq. 9: force on the body, midpoint rule per segment; surface
+// pressure and wall shear from a probe one diagonal spacing out along the
+// segment normal (inverse-distance weighted, Sec. 4.6); free-stream pressure
+// subtracted.  One block; fixed-order tree reduction (deterministic).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint8_t *__restrict__ tag,
+                                                    const double *__restrict__ A, DevState *ds) {
+  __shared__ double rx[256], ry[256];
+  double V[2], Acc[2], X[2];
+  motion_at(k.motion, ds->t, X, V, Acc);
+  double sx = 0.0, sy = 0.0;
+  for (int e = threadIdx.x; e < g.nv; e += blockDim.x) {
+    int e1 = (e + 1 == g.nv) ? 0 : e + 1;
+    double ax = g.vx[e], ay = g.vy[e];
+    double ex = g.vx[e1] - ax, ey = g.vy[e1] - ay;
+    double L = sqrt(ex * ex + ey * ey);
+    double tx = ex / L, ty = ey / L;
+    double nx = ty, ny = -tx;
+    double mx = ax + 0.5 * ex, my = ay + 0.5 * ey;
+    double xi = k.h, w[4];
+    int i0 = 0, j0 = 0, mask = 0;
+    for (int stp = 0; stp <= 3; stp++) {
+      mask = interp_square(k, tag, mx + xi * nx, my + xi * ny, ALLOW_FLUID, &i0, &j0, w);
+      if (mask) break;
+      if (stp < 3) xi = xi + k.dmin;
+    }
+    if (!mask) continue;
+    double qp[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < 4; q++) {
+      if (!(mask >> q & 1)) continue;
+      long long id = cidx(k, i0 + (q & 1), j0 + (q >> 1));
+      double r = A[id], u = A[id + k.plane] / r, v = A[id + 2 * k.plane] / r;
+      double pr = (k.gamma - 1.0) * (A[id + 3 * k.plane] - 0.5 * r * (u * u + v * v));
+      double T = pr / (r * k.R);
+      qp[0] += w[q] * pr;
+      qp[1] += w[q] * u;
+      qp[2] += w[q] * v;
+      qp[3] += w[q] * T;
+    }
+    double rho_p = qp[0] / (k.R * qp[3]);
+    double gn = -rho_p * (nx * Acc[0] + ny * Acc[1]);
+    double ps = qp[0] - xi * gn;
+    double tau = k.mu * ((qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty) / xi;
+    sx += (-(ps - k.pinf) * nx + tau * tx) * L;
+    sy += (-(ps - k.pinf) * ny + tau * ty) * L;
+  }
+  rx[threadIdx.x] = sx;
+  ry[threadIdx.x] = sy;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      rx[threadIdx.x] += rx[threadIdx.x + off];
+      ry[threadIdx.x] += ry[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double q = 0.5 * k.ref_len;
+    ds->force[0] = rx[0] / q;
+    ds->force[1] = ry[0] / q;
+    ds->force[2] = rx[0];
+    ds->force[3] = ry[0];
+  }
+}
+
+void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, DevState *ds,
+                       cudaStream_t s) {
+  k_forces_f64<<<1, 256, 0, s>>>(k, g, tag, A, ds);
+}
+
+}  // namespace ibm

@@ -1,0 +1,223 @@
+"""ctypes binding of the C ABI in include/ibm.h (argument marshalling only).
+
+Every function of the C ABI is exposed under the same name; ``Case`` wraps a
+case handle for convenience.  All computation runs in libibm_gb300.so on the
+GPU; there is no CPU path.  Importing this module without the built library
+raises at once.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libibm_gb300.so")
+
+IBM_OK, IBM_EINVAL, IBM_ENOMEM, IBM_ECAPACITY, IBM_ESTENCIL, IBM_ECUDA, IBM_ESTATE = range(7)
+IBM_STATE_FP64, IBM_TAGS, IBM_LIST_COUNTS, IBM_STENCILS, IBM_TIME, IBM_STEPS = range(6)
+STATUS_NAMES = {0: "IBM_OK", 1: "IBM_EINVAL", 2: "IBM_ENOMEM", 3: "IBM_ECAPACITY", 4: "IBM_ESTENCIL",
+                5: "IBM_ECUDA", 6: "IBM_ESTATE"}
+
+
+class ibm_geometry(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nverts", ctypes.c_int), ("verts", ctypes.POINTER(ctypes.c_double))]
+
+
+class ibm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("lo", ctypes.c_double * 2),
+                ("hi", ctypes.c_double * 2), ("bc", ctypes.c_int * 4)]
+
+
+class ibm_flow(ctypes.Structure):
+    _fields_ = [("mach", ctypes.c_double), ("re", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("prandtl", ctypes.c_double), ("cfl", ctypes.c_double), ("uinf", ctypes.c_double * 2),
+                ("dt_fixed", ctypes.c_double), ("ref_len", ctypes.c_double), ("precision", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
+
+
+class ibm_motion(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("amp", ctypes.c_double * 2), ("freq", ctypes.c_double),
+                ("vel", ctypes.c_double * 2)]
+
+
+STENCIL_DTYPE = np.dtype([
+    ("cell", "<i4"), ("feature", "<i4"), ("region", "<i4"), ("i0", "<i4"), ("j0", "<i4"),
+    ("mask", "<i4"), ("nstep", "<i4"), ("kind", "<i4"),
+    ("nx", "<f8"), ("ny", "<f8"), ("bx", "<f8"), ("by", "<f8"),
+    ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (4,)),
+])
+
+EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state", "ibm_forces",
+           "ibm_sync", "ibm_destroy_case", "ibm_case_device_bytes", "ibm_launch_count", "ibm_last_error"]
+
+
+class IbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libibm_gb300.so is not built; run __graft_entry__.build() "
+                          "(the library has no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    L.ibm_create_case.argtypes = [ctypes.POINTER(ibm_geometry), ctypes.POINTER(ibm_grid),
+                                  ctypes.POINTER(ibm_flow), ctypes.POINTER(ibm_motion), vp,
+                                  ctypes.POINTER(vp)]
+    L.ibm_classify.argtypes = [vp]
+    L.ibm_step.argtypes = [vp, ip]
+    L.ibm_get_state.argtypes = [vp, ip, vp, sz, ip]
+    L.ibm_set_state.argtypes = [vp, vp, sz, ip]
+    L.ibm_forces.argtypes = [vp, vp]
+    L.ibm_sync.argtypes = [vp]
+    L.ibm_destroy_case.argtypes = [vp]
+    L.ibm_case_device_bytes.argtypes = [ctypes.POINTER(ibm_geometry), ctypes.POINTER(ibm_grid),
+                                        ctypes.POINTER(ibm_flow), ctypes.POINTER(ibm_motion)]
+    L.ibm_case_device_bytes.restype = sz
+    L.ibm_launch_count.argtypes = [vp]
+    L.ibm_launch_count.restype = ctypes.c_int64
+    L.ibm_last_error.restype = ctypes.c_char_p
+    for name in ("ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state",
+                 "ibm_forces", "ibm_sync", "ibm_destroy_case"):
+        getattr(L, name).restype = ip
+    return L
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def _check(status):
+    if status != IBM_OK:
+        raise IbmError(status, lib().ibm_last_error().decode())
+    return status
+
+
+def marshal(spec):
+    """Case spec (workloads.case_spec) -> C structs (kept alive by the returned tuple)."""
+    verts = np.ascontiguousarray(spec["verts"], np.float64).reshape(-1, 2)
+    geo = ibm_geometry(2, verts.shape[0],
+                       verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if verts.shape[0] else None)
+    gr = ibm_grid()
+    gr.nx, gr.ny = spec["nx"], spec["ny"]
+    x0, x1, y0, y1 = spec["domain"]
+    gr.lo[0], gr.lo[1], gr.hi[0], gr.hi[1] = x0, y0, x1, y1
+    for s in range(4):
+        gr.bc[s] = spec["bc"][s]
+    fl = ibm_flow()
+    fl.mach, fl.re, fl.gamma, fl.prandtl, fl.cfl = spec["mach"], spec["re"], spec["gamma"], spec["prandtl"], \
+        spec["cfl"]
+    fl.uinf[0], fl.uinf[1] = spec["uinf"]
+    fl.dt_fixed = spec.get("dt_fixed", 0.0)
+    fl.ref_len = spec.get("ref_len", 1.0)
+    fl.precision = spec.get("precision", W.PREC_FP64)
+    mo = ibm_motion()
+    mo.kind = spec.get("motion", W.MOTION_STATIC)
+    mo.amp[0], mo.amp[1] = spec.get("amp", (0.0, 0.0))
+    mo.freq = spec.get("freq", 0.0)
+    mo.vel[0], mo.vel[1] = spec.get("vel", (0.0, 0.0))
+    return verts, geo, gr, fl, mo
+
+
+def case_device_bytes(spec):
+    verts, geo, gr, fl, mo = marshal(spec)
+    return lib().ibm_case_device_bytes(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo))
+
+
+class Case:
+    """A solver case on the current CUDA device (owned by the library)."""
+
+    def __init__(self, spec, stream=None):
+        self.spec = spec
+        self.nx, self.ny = spec["nx"], spec["ny"]
+        self._keep = marshal(spec)
+        verts, geo, gr, fl, mo = self._keep
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        _check(lib().ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), st,
+                                     ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ibm_destroy_case(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def classify(self):
+        _check(lib().ibm_classify(self.h))
+
+    def step(self, n=1):
+        _check(lib().ibm_step(self.h, int(n)))
+
+    def sync(self):
+        _check(lib().ibm_sync(self.h))
+
+    def _get(self, what, arr, on_device=False, ptr=None):
+        p = ptr if ptr is not None else arr.ctypes.data_as(ctypes.c_void_p)
+        nbytes = arr.nbytes if arr is not None else 0
+        _check(lib().ibm_get_state(self.h, what, p, nbytes, 1 if on_device else 0))
+        return arr
+
+    def state(self):
+        return self._get(IBM_STATE_FP64, np.empty((4, self.ny, self.nx), np.float64))
+
+    def state_to_device(self, tensor):
+        """Copy the FP64 state into a CUDA tensor of shape (4, ny, nx), float64."""
+        assert tensor.is_cuda and tensor.dtype.itemsize == 8 and tensor.is_contiguous()
+        _check(lib().ibm_get_state(self.h, IBM_STATE_FP64, ctypes.c_void_p(tensor.data_ptr()),
+                                   tensor.numel() * 8, 1))
+
+    def set_state(self, a):
+        a = np.ascontiguousarray(a, np.float64)
+        assert a.shape == (4, self.ny, self.nx)
+        _check(lib().ibm_set_state(self.h, a.ctypes.data_as(ctypes.c_void_p), a.nbytes, 0))
+
+    def set_state_from_ptr(self, ptr, nbytes, on_device):
+        _check(lib().ibm_set_state(self.h, ctypes.c_void_p(ptr), nbytes, 1 if on_device else 0))
+
+    def tags(self):
+        return self._get(IBM_TAGS, np.empty((self.ny, self.nx), np.uint8))
+
+    def counts(self):
+        return self._get(IBM_LIST_COUNTS, np.zeros(4, np.int32))
+
+    def stencils(self):
+        n = int(self.counts().sum())
+        a = np.zeros(n, STENCIL_DTYPE)
+        if n:
+            self._get(IBM_STENCILS, a)
+        return a
+
+    def time(self):
+        return self._get(IBM_TIME, np.zeros(2, np.float64))
+
+    def steps(self):
+        return int(self._get(IBM_STEPS, np.zeros(1, np.int64))[0])
+
+    def forces(self):
+        out = np.zeros(4, np.float64)
+        _check(lib().ibm_forces(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def forces_into(self, ptr):
+        """Forces written to caller memory at ptr (host, 4 doubles)."""
+        _check(lib().ibm_forces(self.h, ctypes.c_void_p(ptr)))
+
+    def launches(self):
+        return int(lib().ibm_launch_count(self.h))
