@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark: Mcell-updates/s per RK stage of the immersed-boundary solver.
+
+Workload (default): M=2, Re=1e4 flow over a 15 deg wedge (3-vertex polyline,
+chord 1) on a 768x384 grid over [-1,3]x[-1,1], WENO5 + LDFSS + RK3, CFL 0.5,
+FP32-bulk arithmetic (FP64 state accumulation).  One benchmark step is one
+full SSP-RK3 time step of the hot path: time-step reduction, three rounds of
+IB / ghost reconstruction, domain halos and the fused residual + stage
+update (the body is static, so classification and stencils are built once
+before timing).  The same step in plain FP64 is timed beside it.
+
+value  = active (non-solid) cells x 3 stages x K steps / device time, all ranks
+e2e    = the same metric through the C ABI from pinned host memory: every step
+         uploads the FP64 state, steps, and reads the forces back.
+
+Multi-GPU (torchrun): each rank runs its own replica of the workload (weak
+scaling, no data-path collective); ranks are timed between barriers and the
+maximum time is used.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "wedge_768x384": "wedge_m2_re1e4",
+    "cylinder_160x80": "cylinder_m02_re40",
+    "osc_cylinder_1024x512": "oscillating_cylinder_m02_re185",
+}
+# algorithmic DRAM bytes per cell and stage of the fused residual kernel
+# (each stage reads its input planes and tags once and writes its output once;
+# halos are re-read from L2/shared memory, not counted)
+BYTES_PER_CELL_STAGE = {"fp32_bulk": 179.0 / 3.0, "fp64": 259.0 / 3.0}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _spec(name, precision, grid=None):
+    from paper_1912_11908_gb300 import workloads as W
+    fn = getattr(W, WORKLOADS[name])
+    kw = {}
+    if grid:
+        kw["nx"], kw["ny"] = (int(v) for v in grid.lower().split("x"))
+    return fn(precision=W.PREC_FP32_BULK if precision == "fp32_bulk" else W.PREC_FP64, **kw)
+
+
+def _active_cells(case):
+    import numpy as np
+    return int((case.tags() != 1).sum())
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic(kernel_file):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "k_stage_f32_wedge768x384.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    src = os.path.join(ROOT, "paper_1912_11908_gb300", "csrc", kernel_file)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if d.get("source_sha256") != h:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "bench_clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _time_steps(case, torch, flush, K, stream):
+    """Device time of K steps, one CUDA-event pair per step on the case stream, L2 flushed in between."""
+    total = 0.0
+    for _ in range(K):
+        flush.add_(1)  # writes more than L2 between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        case.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1912_11908_gb300 import _build, ibm
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if local == 0:
+        _build.build()  # the other ranks wait for it in the process-group rendezvous
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    spec = _spec(args.workload, args.precision, args.grid)
+    case = ibm.Case(spec, stream=stream.cuda_stream)
+    case.classify()
+    cells = _active_cells(case)
+    case.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    dev_index = torch.cuda.current_device()
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = phys[dev_index] if phys and phys[0] not in ("",) else dev_index
+    n0 = case.launches()
+    barrier()
+    with ClockSampler(smi_index) as clk:
+        t_dev_ms = _time_steps(case, torch, flush, args.steps, stream)
+    barrier()
+    launches = case.launches() - n0
+    if dist:
+        t = torch.tensor([t_dev_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev_ms = float(t.item())
+    units = cells * 3 * args.steps * world
+    value = units / (t_dev_ms * 1e-3) / 1e6
+
+    # live kernel timing for the roofline: the same steps with CUDA events around every kernel group
+    case.profile(True)
+    nprof = min(args.steps, 50)
+    case.profile_read()
+    case.step(nprof)
+    prof = case.profile_read()
+    case.profile(False)
+    stage_ms, stage_launches = prof["residual_stage"]
+    stage_avg_ms = stage_ms / max(1, stage_launches)
+    bpc = BYTES_PER_CELL_STAGE[args.precision]
+    bytes_per_launch = bpc * spec["nx"] * spec["ny"]
+    achieved = bytes_per_launch / (stage_avg_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = _traffic("flow32.cu" if args.precision == "fp32_bulk" else "flow.cu")
+
+    # plain FP64 path on the same workload and GPU
+    fp64 = None
+    if args.precision == "fp32_bulk" and not args.skip_fp64:
+        c64 = ibm.Case(_spec(args.workload, "fp64", args.grid), stream=stream.cuda_stream)
+        c64.classify()
+        c64.step(max(3, args.warmup // 4))
+        k64 = max(3, min(args.steps, 40))
+        t64 = _time_steps(c64, torch, flush, k64, stream)
+        v64 = cells * 3 * k64 / (t64 * 1e-3) / 1e6
+        fp64 = {"value": v64, "ms_per_step": t64 / k64, "steps": k64,
+                "fp32_bulk_speedup": value / world / v64}
+        c64.close()
+
+    # end to end through the C ABI from pinned host memory
+    state = case.state()
+    host = torch.empty(state.shape, dtype=torch.float64, pin_memory=True)
+    host.numpy()[...] = state
+    forces = torch.empty(4, dtype=torch.float64, pin_memory=True)
+    ke = max(3, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        case.set_state_from_ptr(host.data_ptr(), host.numel() * 8, False)
+        case.step(1)
+        case.forces_into(forces.data_ptr())
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": cells * 3 * ke * world / t_e2e / 1e6, "unit": "Mcell-updates/s",
+           "h2d_bytes_per_step": int(host.numel() * 8), "d2h_bytes_per_step": int(forces.numel() * 8),
+           "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(args, cells)
+
+    out = {
+        "metric": "Mcell-updates/s per RK stage (FP32-bulk vs FP64)",
+        "value": value,
+        "unit": "Mcell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_dev_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32_bulk" else "f64",
+        "data": "synthetic (closed-form wedge, uniform free-stream start)",
+        "config": {"workload": spec["name"], "grid": [spec["nx"], spec["ny"]], "active_cells": cells,
+                   "precision": args.precision, "stages_per_step": 3, "time_scheme": "SSP-RK3",
+                   "l2": "flushed between timed steps (512 MiB write outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "cuda_graphs": True},
+        "roofline": {"bound": "hbm", "kernel": "k_stage_f32" if args.precision == "fp32_bulk" else "k_stage_f64",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_kind, "traffic": traffic,
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": stage_avg_ms,
+                     "timed_launches": stage_launches},
+        "kernel_ms_per_step": {g: ms / nprof for g, (ms, n) in prof.items()},
+        "fp64": fp64,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    case.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, cells_gpu=None, sample_s=10.0, max_steps=400):
+    """The FP64 oracle as it stands, on this host's cores, over a bounded number of steps."""
+    import oracle
+    spec = _spec(args.workload, "fp64")
+    oracle.build()
+    c = oracle.Case(spec)
+    c.step(1)
+    cells = int((c.tags() != 1).sum())
+    n, t = 0, 0.0
+    while t < sample_s and n < max_steps:
+        t0 = time.perf_counter()
+        c.step(1)
+        t += time.perf_counter() - t0
+        n += 1
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": cells * 3 * n / t / 1e6, "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": "%d RK3 steps of %s after 1 warm-up step (%.1f s)" % (n, spec["name"], t)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle timed on this host's cores, one full RK3 step per bench step."""
+    if rank != 0:
+        return
+    import oracle
+    spec = _spec(args.workload, "fp64")
+    oracle.build()
+    c = oracle.Case(spec)
+    c.step(1)
+    cells = int((c.tags() != 1).sum())
+    c.step(args.warmup)
+    t0 = time.perf_counter()
+    c.step(args.steps)
+    t = time.perf_counter() - t0
+    value = cells * 3 * args.steps / t / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {
+        "impl": "reference",
+        "metric": "Mcell-updates/s per RK stage (FP32-bulk vs FP64)",
+        "value": value, "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (closed-form wedge, uniform free-stream start)",
+        "config": {"workload": spec["name"], "grid": [spec["nx"], spec["ny"]], "active_cells": cells,
+                   "precision": "fp64", "stages_per_step": 3, "time_scheme": "SSP-RK3"},
+        "cpu_baseline": {"value": value, "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d full RK3 steps of %s" % (args.steps, spec["name"])},
+        "e2e": {"value": value, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="wedge_768x384", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32_bulk", choices=["fp32_bulk", "fp64"])
+    ap.add_argument("--grid", default=None, help="override the workload grid, e.g. 3072x1536 (profiling)")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -20,8 +20,9 @@
  *     ibm_last_error() returns a thread-local message.
  *   - The library owns all device memory of a case.  Caller buffers passed to
  *     ibm_create_case are copied before it returns.
- *   - Work is enqueued on the stream given at creation (NULL = the legacy
- *     default stream).  ibm_step is asynchronous; ibm_forces, ibm_get_state and
+ *   - Work is enqueued on the stream given at creation; with NULL the case
+ *     creates its own stream, which synchronises with the legacy default
+ *     stream.  ibm_step is asynchronous; ibm_forces, ibm_get_state and
  *     ibm_sync synchronise that stream and report asynchronous device errors
  *     (list overflow -> IBM_ECAPACITY, empty interpolation stencil ->
  *     IBM_ESTENCIL, CUDA errors -> IBM_ECUDA).
@@ -170,8 +171,23 @@ ibm_status ibm_destroy_case(ibm_case *c);
 size_t ibm_case_device_bytes(const ibm_geometry *geometry, const ibm_grid *grid, const ibm_flow *flow,
                              const ibm_motion *motion);
 
-/* Kernel launches enqueued by the case so far (instrumentation). */
+/* Kernel launches enqueued by the case so far (instrumentation; a step
+ * replayed from a CUDA graph counts the kernels it contains). */
 int64_t ibm_launch_count(const ibm_case *c);
+
+/* Instrumentation.  While enabled, ibm_step launches kernels directly (no
+ * graph replay) and records CUDA events on the case stream around each kernel
+ * group; ibm_profile_read synchronises, writes per group the summed device
+ * time in ms and the number of timed launches, and clears the record.
+ * Groups: 0 fused residual + stage update, 1 IB / ghost reconstruction,
+ * 2 domain halos, 3 time-step reduction, 4 geometry (pose, classification,
+ * tags, lists, stencils), 5 end of step.  n_groups <= 6. */
+ibm_status ibm_profile_enable(ibm_case *c, int enable);
+ibm_status ibm_profile_read(ibm_case *c, double *ms, int64_t *launches, int n_groups);
+
+/* Replay each step from a CUDA graph captured on first use (default on);
+ * enable = 0 launches every kernel directly. */
+ibm_status ibm_use_graphs(ibm_case *c, int enable);
 
 const char *ibm_last_error(void);
 

@@ -29,8 +29,38 @@ struct ibm_case {
   DevState *ds = nullptr;
   DevState *hds = nullptr;  // pinned host mirror for read-backs
   bool classified = false;
+  bool own_stream = false;
   long long launches = 0;
+  // CUDA graph of one step (captured on first use)
+  bool use_graphs = true;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_launches = 0;  // kernels per replayed step
+  // profiling: event pairs per kernel group
+  static constexpr int NGROUP = 6, NEV = 4096;
+  bool profiling = false;
+  cudaEvent_t ev[NEV] = {};
+  int nev = 0;
+  int ev_group[NEV / 2] = {};
+  bool ev_overflow = false;
 };
+
+// record a group boundary (start when begin, end otherwise) while profiling
+static void prof_mark(ibm_case *c, int group, bool begin) {
+  if (!c->profiling) return;
+  if (begin) {
+    if (c->nev + 2 > ibm_case::NEV) {
+      c->ev_overflow = true;
+      return;
+    }
+    c->ev_group[c->nev / 2] = group;
+    cudaEventRecord(c->ev[c->nev], c->stream);
+    c->nev++;
+  } else {
+    if (c->nev % 2 == 0) return;  // start was dropped
+    cudaEventRecord(c->ev[c->nev], c->stream);
+    c->nev++;
+  }
+}
 
 static thread_local char g_err[512] = "";
 
@@ -110,6 +140,10 @@ static void free_case(ibm_case *c) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->hds) cudaFreeHost(c->hds);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (int q = 0; q < ibm_case::NEV; q++)
+    if (c->ev[q]) cudaEventDestroy(c->ev[q]);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
@@ -128,6 +162,14 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   if (!c) return fail(IBM_ENOMEM, "host allocation failed");
   cudaGetDevice(&c->device);
   c->stream = (cudaStream_t)stream;
+  if (!c->stream) {
+    if (cudaStreamCreate(&c->stream) != cudaSuccess) {
+      delete c;
+      cudaGetLastError();
+      return fail(IBM_ECUDA, "stream creation failed");
+    }
+    c->own_stream = true;
+  }
   c->precision = fl->precision;
   Consts &k = c->k;
   k.nx = gr->nx;
@@ -261,6 +303,7 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
 static ibm_status do_classify(ibm_case *c) {
   cudaStream_t s = c->stream;
   int nl = 0;
+  prof_mark(c, 4, true);
   if (c->g.nv > 0) {
     launch_pose(c->k, c->g, c->ds, s);
     launch_classify(c->k, c->g, c->solid, c->ds, s);
@@ -273,6 +316,7 @@ static ibm_status do_classify(ibm_case *c) {
     launch_stencils(c->k, c->g, c->tag, c->st, c->cap, c->ds, s);
     nl += 1;
   }
+  prof_mark(c, 4, false);
   c->launches += nl;
   c->classified = true;
   CU(cudaGetLastError());
@@ -284,54 +328,126 @@ extern "C" ibm_status ibm_classify(ibm_case *c) {
   return do_classify(c);
 }
 
-static ibm_status step_fp64(ibm_case *c) {
+// one explicit step on the case stream (kernels only; graph-capturable)
+static int enqueue_step(ibm_case *c) {
   cudaStream_t s = c->stream;
   int nl = 0;
+  if (!c->classified || c->k.motion.kind != IBM_MOTION_STATIC) {
+    int before = (int)c->launches;
+    do_classify(c);
+    nl += (int)c->launches - before;
+    c->launches = before;
+  }
+  prof_mark(c, 3, true);
   launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
-  double *in[3] = {c->A, c->B, c->C};
-  double *out[3] = {c->B, c->C, c->A};
+  prof_mark(c, 3, false);
+  const bool f64 = c->precision == IBM_PREC_FP64;
+  double *in64[3] = {c->A, c->B, c->C};
+  double *out64[3] = {c->B, c->C, c->A};
+  float *in32[3] = {c->M, c->F1, c->F2};
+  float *out32[3] = {c->F1, c->F2, nullptr};
   for (int st = 1; st <= 3; st++) {
-    launch_recon_f64(c->k, in[st - 1], c->st, c->cap, c->ds, st, s, &nl);
-    launch_bc_f64(c->k, in[st - 1], s);
-    launch_stage_f64(c->k, st, c->A, in[st - 1], out[st - 1], c->tag, c->ds, s);
+    prof_mark(c, 1, true);
+    if (f64) launch_recon_f64(c->k, in64[st - 1], c->st, c->cap, c->ds, st, s, &nl);
+    else launch_recon_f32(c->k, in32[st - 1], c->A, c->st, c->cap, c->ds, st, s, &nl);
+    prof_mark(c, 1, false);
+    prof_mark(c, 2, true);
+    if (f64) launch_bc_f64(c->k, in64[st - 1], s);
+    else launch_bc_f32(c->k, in32[st - 1], s);
+    prof_mark(c, 2, false);
+    prof_mark(c, 0, true);
+    if (f64) launch_stage_f64(c->k, st, c->A, in64[st - 1], out64[st - 1], c->tag, c->ds, s);
+    else launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->ds, s);
+    prof_mark(c, 0, false);
     nl += 2;
   }
+  prof_mark(c, 5, true);
   launch_step_end(c->k, c->ds, s);
+  prof_mark(c, 5, false);
   nl += 1;
-  c->launches += nl;
-  return IBM_OK;
+  return nl;
 }
 
-static ibm_status step_fp32(ibm_case *c) {
-  cudaStream_t s = c->stream;
-  int nl = 0;
-  launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
-  float *in[3] = {c->M, c->F1, c->F2};
-  float *out[3] = {c->F1, c->F2, nullptr};
-  for (int st = 1; st <= 3; st++) {
-    launch_recon_f32(c->k, in[st - 1], c->A, c->st, c->cap, c->ds, st, s, &nl);
-    launch_bc_f32(c->k, in[st - 1], s);
-    launch_stage_f32(c->k, st, c->M, in[st - 1], out[st - 1], c->A, c->tag, c->ds, s);
-    nl += 2;
+static ibm_status capture_step_graph(ibm_case *c) {
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int nl = enqueue_step(c);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IBM_ECUDA, "step capture failed: %s", cudaGetErrorString(e));
   }
-  launch_step_end(c->k, c->ds, s);
-  nl += 1;
-  c->launches += nl;
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    cudaGetLastError();
+    return fail(IBM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  c->graph_launches = nl;
   return IBM_OK;
 }
 
 extern "C" ibm_status ibm_step(ibm_case *c, int nsteps) {
   if (!c) return fail(IBM_EINVAL, "case is NULL");
   if (nsteps < 0) return fail(IBM_EINVAL, "nsteps < 0");
-  for (int n = 0; n < nsteps; n++) {
-    if (!c->classified || c->k.motion.kind != IBM_MOTION_STATIC) {
-      ibm_status r = do_classify(c);
-      if (r != IBM_OK) return r;
-    }
-    ibm_status r = c->precision == IBM_PREC_FP64 ? step_fp64(c) : step_fp32(c);
+  if (nsteps == 0) return IBM_OK;
+  if (!c->classified) {
+    // the first classification runs outside any graph so that a static body's
+    // graph holds only the flow kernels
+    ibm_status r = do_classify(c);
     if (r != IBM_OK) return r;
   }
+  if (c->use_graphs && !c->profiling) {
+    if (!c->graph) {
+      ibm_status r = capture_step_graph(c);
+      if (r != IBM_OK) return r;
+    }
+    for (int n = 0; n < nsteps; n++) CU(cudaGraphLaunch(c->graph, c->stream));
+    c->launches += (long long)nsteps * c->graph_launches;
+  } else {
+    for (int n = 0; n < nsteps; n++) c->launches += enqueue_step(c);
+  }
   CU(cudaGetLastError());
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_use_graphs(ibm_case *c, int enable) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  c->use_graphs = enable != 0;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_profile_enable(ibm_case *c, int enable) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  if (enable && !c->ev[0]) {
+    for (int q = 0; q < ibm_case::NEV; q++) CU(cudaEventCreate(&c->ev[q]));
+  }
+  c->profiling = enable != 0;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_profile_read(ibm_case *c, double *ms, int64_t *launches, int n_groups) {
+  if (!c || !ms || !launches || n_groups < 0 || n_groups > ibm_case::NGROUP)
+    return fail(IBM_EINVAL, "bad arguments");
+  CU(cudaStreamSynchronize(c->stream));
+  for (int g = 0; g < n_groups; g++) {
+    ms[g] = 0.0;
+    launches[g] = 0;
+  }
+  for (int q = 0; q + 1 < c->nev; q += 2) {
+    int g = c->ev_group[q / 2];
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, c->ev[q], c->ev[q + 1]));
+    if (g < n_groups) {
+      ms[g] += t;
+      launches[g] += 1;
+    }
+  }
+  bool over = c->ev_overflow;
+  c->nev = 0;
+  c->ev_overflow = false;
+  if (over) return fail(IBM_ESTATE, "profiling record overflowed; read more often");
   return IBM_OK;
 }
 

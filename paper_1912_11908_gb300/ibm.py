@@ -50,7 +50,9 @@ STENCIL_DTYPE = np.dtype([
 ])
 
 EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state", "ibm_forces",
-           "ibm_sync", "ibm_destroy_case", "ibm_case_device_bytes", "ibm_launch_count", "ibm_last_error"]
+           "ibm_sync", "ibm_destroy_case", "ibm_case_device_bytes", "ibm_launch_count", "ibm_last_error",
+           "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs"]
+PROFILE_GROUPS = ["residual_stage", "ib_reconstruct", "domain_halo", "time_step", "geometry", "step_end"]
 
 
 class IbmError(RuntimeError):
@@ -81,8 +83,12 @@ def load():
     L.ibm_launch_count.argtypes = [vp]
     L.ibm_launch_count.restype = ctypes.c_int64
     L.ibm_last_error.restype = ctypes.c_char_p
+    L.ibm_profile_enable.argtypes = [vp, ip]
+    L.ibm_profile_read.argtypes = [vp, vp, vp, ip]
+    L.ibm_use_graphs.argtypes = [vp, ip]
     for name in ("ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state",
-                 "ibm_forces", "ibm_sync", "ibm_destroy_case"):
+                 "ibm_forces", "ibm_sync", "ibm_destroy_case", "ibm_profile_enable", "ibm_profile_read",
+                 "ibm_use_graphs"):
         getattr(L, name).restype = ip
     return L
 
@@ -221,3 +227,18 @@ class Case:
 
     def launches(self):
         return int(lib().ibm_launch_count(self.h))
+
+    def use_graphs(self, enable):
+        _check(lib().ibm_use_graphs(self.h, 1 if enable else 0))
+
+    def profile(self, enable):
+        _check(lib().ibm_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{group: (ms, launches)} summed since the last read."""
+        n = len(PROFILE_GROUPS)
+        ms = np.zeros(n, np.float64)
+        cnt = np.zeros(n, np.int64)
+        _check(lib().ibm_profile_read(self.h, ms.ctypes.data_as(ctypes.c_void_p), cnt.ctypes.data_as(ctypes.c_void_p),
+                                      n))
+        return {g: (float(ms[k]), int(cnt[k])) for k, g in enumerate(PROFILE_GROUPS)}
