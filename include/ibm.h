@@ -191,6 +191,36 @@ ibm_status ibm_use_graphs(ibm_case *c, int enable);
 
 const char *ibm_last_error(void);
 
+/* Allocation-free classification, tagging and list compaction.  (The paper
+ * has no counterpart; this is a library facility.)
+ *
+ * For callers that cannot allocate device memory: code that runs where
+ * cudaMalloc is unavailable or not allowed (a host callback, an embedding
+ * that owns every device allocation, a memory pool that must not grow after
+ * start-up).  It computes the same tags and the same row-major IB / G1 / G2 /
+ * G3 lists as ibm_classify, for a body given at its current pose, without any
+ * case and without allocating: its intermediate data lives in one fixed
+ * device array inside the library (about 4.3 MiB, held on every GPU that
+ * loads the library until the process exits).
+ *
+ * grid:     host struct (bc is ignored); nx * ny <= 4194304 cells.
+ * d_verts:  device, 2*nverts doubles (x0, y0, x1, y1, ...), closed CCW
+ *           polyline, 3 <= nverts <= 4096.
+ * d_tags:   device output, uint8_t[ny][nx] (IBM_TAG_*).
+ * d_cells:  device output, int32_t[capacity]: cell indices j*nx+i of the IB
+ *           nodes, then G1, G2, G3, each in row-major order; entries past
+ *           capacity are not written.
+ * d_counts: device output, int32_t[4]: #IB, #G1, #G2, #G3 (full totals, even
+ *           when they exceed capacity).
+ * Asynchronous on cuda_stream (NULL = legacy default stream).  Sizes beyond
+ * the limits return IBM_EINVAL before any GPU work.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array, so calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller. */
+ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, int nverts, uint8_t *d_tags,
+                                 int32_t *d_cells, int32_t capacity, int32_t *d_counts, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -579,3 +579,5 @@ extern "C" ibm_status ibm_destroy_case(ibm_case *c) {
 extern "C" int64_t ibm_launch_count(const ibm_case *c) { return c ? c->launches : 0; }
 
 extern "C" const char *ibm_last_error(void) { return g_err; }
+
+extern "C" ibm_status ibm__noalloc_fail(ibm_status s, const char *msg) { return fail(s, "%s", msg); }

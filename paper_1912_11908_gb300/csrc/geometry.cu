@@ -8,6 +8,8 @@
 // no contraction, so tags, lists and stencils are reproducible bit for bit by
 // any IEEE implementation that performs the same operations in the same
 // order.  No transcendental function is used on these paths.
+#include <mutex>
+
 #include "ibm_internal.cuh"
 
 namespace ibm {
@@ -547,3 +549,144 @@ void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const
 }
 
 }  // namespace ibm
+
+using namespace ibm;
+
+// ===========================================================================
+// Allocation-free classification + tagging + list compaction.
+//
+// For callers that cannot allocate device memory themselves or through the
+// library: code running where cudaMalloc is unavailable or forbidden (inside
+// a host callback, under a memory pool that must not grow, in an embedding
+// that owns every device allocation), or a caller that must keep its device
+// footprint fixed after start-up.  The caller passes the body and the output
+// buffers; the intermediate data (solid flags, per-block counts, bounding box,
+// list offsets) lives in the fixed file-scope device array below.  Every GPU
+// that loads this library holds that array until the process exits.
+// ===========================================================================
+namespace {
+
+constexpr int NOALLOC_MAX_CELLS = 1 << 22;  // 4,194,304 cells (e.g. 2048 x 2048)
+constexpr int NOALLOC_MAX_VERTS = 4096;
+constexpr int NOALLOC_MAX_BLOCKS = (NOALLOC_MAX_CELLS + TAG_BLOCK - 1) / TAG_BLOCK;
+
+struct NoAllocScratch {
+  DevState ds;
+  double vx[NOALLOC_MAX_VERTS];
+  double vy[NOALLOC_MAX_VERTS];
+  int blockcounts[4 * NOALLOC_MAX_BLOCKS];
+  uint8_t solid[NOALLOC_MAX_CELLS];
+};
+
+// total: about 4.3 MiB per device
+__device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+__global__ void k_noalloc_prepare(const double *__restrict__ verts, int nv, NoAllocScratch *s) {
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    s->vx[v] = verts[2 * v];
+    s->vy[v] = verts[2 * v + 1];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b0 = s->vx[0], b1 = s->vx[0], b2 = s->vy[0], b3 = s->vy[0];
+    for (int v = 1; v < nv; v++) {
+      if (s->vx[v] < b0) b0 = s->vx[v];
+      if (s->vx[v] > b1) b1 = s->vx[v];
+      if (s->vy[v] < b2) b2 = s->vy[v];
+      if (s->vy[v] > b3) b3 = s->vy[v];
+    }
+    s->ds.bbox[0] = b0;
+    s->ds.bbox[1] = b1;
+    s->ds.bbox[2] = b2;
+    s->ds.bbox[3] = b3;
+    s->ds.err = 0;
+  }
+}
+
+// same ranking as k_scatter, writing plain cell indices
+__global__ void __launch_bounds__(TAG_BLOCK) k_scatter_cells(Consts k, const uint8_t *__restrict__ tag,
+                                                             const int *__restrict__ blockoff, const DevState *ds,
+                                                             int32_t *__restrict__ cells, int cap) {
+  __shared__ int wc[TAG_BLOCK / 32][4];
+  const int n = blockIdx.x * TAG_BLOCK + threadIdx.x;
+  const int ncell = k.nx * k.ny;
+  const int kind = n < ncell ? list_kind(tag[n]) : -1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int rank = 0;
+  for (int q = 0; q < 4; q++) {
+    unsigned m = __ballot_sync(0xffffffffu, kind == q);
+    if (lane == 0) wc[warp][q] = __popc(m);
+    if (kind == q) rank = __popc(m & lt);
+  }
+  __syncthreads();
+  if (kind >= 0) {
+    int before = 0;
+    for (int w = 0; w < warp; w++) before += wc[w][kind];
+    int pos = ds->offset[kind] + blockoff[blockIdx.x * 4 + kind] + before + rank;
+    if (pos < cap) cells[pos] = n;
+  }
+}
+
+std::mutex g_noalloc_mu;
+NoAllocScratch *g_noalloc_ptr[256] = {};
+
+}  // namespace
+
+// Defined in the C ABI unit.
+extern "C" ibm_status ibm__noalloc_fail(ibm_status s, const char *msg);
+
+extern "C" ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, int nverts,
+                                            uint8_t *d_tags, int32_t *d_cells, int32_t capacity,
+                                            int32_t *d_counts, void *cuda_stream) {
+  using namespace ibm;
+  if (!grid || !d_verts || !d_tags || !d_cells || !d_counts)
+    return ibm__noalloc_fail(IBM_EINVAL, "ibm_tag_nodes_noalloc: NULL argument");
+  if (grid->nx < 1 || grid->ny < 1 || !(grid->hi[0] > grid->lo[0]) || !(grid->hi[1] > grid->lo[1]))
+    return ibm__noalloc_fail(IBM_EINVAL, "ibm_tag_nodes_noalloc: bad grid");
+  if ((long long)grid->nx * grid->ny > NOALLOC_MAX_CELLS)
+    return ibm__noalloc_fail(IBM_EINVAL, "ibm_tag_nodes_noalloc: grid exceeds the 4194304-cell scratch limit");
+  if (nverts < 3 || nverts > NOALLOC_MAX_VERTS)
+    return ibm__noalloc_fail(IBM_EINVAL, "ibm_tag_nodes_noalloc: nverts must be in [3, 4096]");
+  if (capacity < 0) return ibm__noalloc_fail(IBM_EINVAL, "ibm_tag_nodes_noalloc: negative capacity");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256)
+    return ibm__noalloc_fail(IBM_ECUDA, "ibm_tag_nodes_noalloc: no current device");
+  NoAllocScratch *s = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return ibm__noalloc_fail(IBM_ECUDA, "ibm_tag_nodes_noalloc: cudaGetSymbolAddress failed");
+      }
+      g_noalloc_ptr[dev] = (NoAllocScratch *)p;
+    }
+    s = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Consts k{};
+  k.nx = grid->nx;
+  k.ny = grid->ny;
+  k.x0 = grid->lo[0];
+  k.y0 = grid->lo[1];
+  k.dx = (grid->hi[0] - grid->lo[0]) / grid->nx;
+  k.dy = (grid->hi[1] - grid->lo[1]) / grid->ny;
+  Geom g{};
+  g.nv = nverts;
+  g.vx = s->vx;
+  g.vy = s->vy;
+  k_noalloc_prepare<<<1, 256, 0, st>>>(d_verts, nverts, s);
+  launch_classify(k, g, s->solid, &s->ds, st);
+  const int ncell = k.nx * k.ny;
+  const int nblk = (ncell + TAG_BLOCK - 1) / TAG_BLOCK;
+  k_tag_count<<<nblk, TAG_BLOCK, 0, st>>>(k, s->solid, d_tags, s->blockcounts);
+  k_scan_blocks<<<1, 1024, 0, st>>>(nblk, s->blockcounts, &s->ds, capacity);
+  k_scatter_cells<<<nblk, TAG_BLOCK, 0, st>>>(k, d_tags, s->blockcounts, &s->ds, d_cells, capacity);
+  cudaError_t e = cudaMemcpyAsync(d_counts, s->ds.count, 4 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return ibm__noalloc_fail(IBM_ECUDA, cudaGetErrorString(e));
+  return IBM_OK;
+}

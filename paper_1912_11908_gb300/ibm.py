@@ -51,7 +51,7 @@ STENCIL_DTYPE = np.dtype([
 
 EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state", "ibm_forces",
            "ibm_sync", "ibm_destroy_case", "ibm_case_device_bytes", "ibm_launch_count", "ibm_last_error",
-           "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs"]
+           "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs", "ibm_tag_nodes_noalloc"]
 PROFILE_GROUPS = ["residual_stage", "ib_reconstruct", "domain_halo", "time_step", "geometry", "step_end"]
 
 
@@ -86,6 +86,8 @@ def load():
     L.ibm_profile_enable.argtypes = [vp, ip]
     L.ibm_profile_read.argtypes = [vp, vp, vp, ip]
     L.ibm_use_graphs.argtypes = [vp, ip]
+    L.ibm_tag_nodes_noalloc.argtypes = [ctypes.POINTER(ibm_grid), vp, ip, vp, vp, ctypes.c_int32, vp, vp]
+    L.ibm_tag_nodes_noalloc.restype = ip
     for name in ("ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state",
                  "ibm_forces", "ibm_sync", "ibm_destroy_case", "ibm_profile_enable", "ibm_profile_read",
                  "ibm_use_graphs"):
@@ -133,6 +135,14 @@ def marshal(spec):
     mo.freq = spec.get("freq", 0.0)
     mo.vel[0], mo.vel[1] = spec.get("vel", (0.0, 0.0))
     return verts, geo, gr, fl, mo
+
+
+def ibm_tag_nodes_noalloc(spec, d_verts, nverts, d_tags, d_cells, capacity, d_counts, stream=None):
+    """Allocation-free tagging (device pointers in, device pointers out); see include/ibm.h."""
+    verts, geo, gr, fl, mo = marshal(spec)
+    _check(lib().ibm_tag_nodes_noalloc(ctypes.byref(gr), ctypes.c_void_p(d_verts), int(nverts),
+                                       ctypes.c_void_p(d_tags), ctypes.c_void_p(d_cells), int(capacity),
+                                       ctypes.c_void_p(d_counts), ctypes.c_void_p(stream) if stream else None))
 
 
 def case_device_bytes(spec):
