@@ -22,6 +22,7 @@ struct ibm_case {
          *vny = nullptr;
   double *A = nullptr, *B = nullptr, *C = nullptr;  // FP64 conserved: state, stage arrays (FP64 mode)
   float *M = nullptr, *F1 = nullptr, *F2 = nullptr;  // FP32-bulk: perturbation mirror and stage arrays
+  double *stage64 = nullptr;  // FP32-bulk: absolute-variable staging for ibm_get_state (allocated on first use)
   uint8_t *solid = nullptr, *tag = nullptr;
   int *blockcounts = nullptr;
   ibm_stencil *st = nullptr;
@@ -136,7 +137,7 @@ extern "C" size_t ibm_case_device_bytes(const ibm_geometry *geo, const ibm_grid 
 static void free_case(ibm_case *c) {
   if (!c) return;
   void *ptrs[] = {c->vref, c->vx, c->vy, c->snx, c->sny, c->vnx, c->vny, c->A, c->B, c->C, c->M, c->F1,
-                  c->F2, c->solid, c->tag, c->blockcounts, c->st, c->ds};
+                  c->F2, c->stage64, c->solid, c->tag, c->blockcounts, c->st, c->ds};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->hds) cudaFreeHost(c->hds);
@@ -264,6 +265,10 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
       c->launches++;
     }
     std::memset(c->hds, 0, sizeof(DevState));
+    if (k.dt_fixed > 0.0) {
+      c->hds->dt = k.dt_fixed;
+      c->hds->dtf = (float)k.dt_fixed;
+    }
     if (cudaMemcpyAsync(c->ds, c->hds, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(c->tag, 0, ncell, s) != cudaSuccess) {
       rs = fail(IBM_ECUDA, "state initialisation failed");
@@ -275,8 +280,9 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
       rs = fail(IBM_ENOMEM, "host allocation failed");
       break;
     }
+    const bool pert = c->precision == IBM_PREC_FP32_BULK;  // the FP64 state then holds dU = U - U_inf
     for (int v = 0; v < 4 && rs == IBM_OK; v++) {
-      for (size_t m = 0; m < plane; m++) hU[m] = k.Uinf[v];
+      for (size_t m = 0; m < plane; m++) hU[m] = pert ? 0.0 : k.Uinf[v];
       if (cudaMemcpy(c->A + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         rs = fail(IBM_ECUDA, "state upload failed");
       if (c->B && cudaMemcpy(c->B + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -338,10 +344,11 @@ static int enqueue_step(ibm_case *c) {
     nl += (int)c->launches - before;
     c->launches = before;
   }
-  prof_mark(c, 3, true);
-  launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
-  prof_mark(c, 3, false);
   const bool f64 = c->precision == IBM_PREC_FP64;
+  prof_mark(c, 3, true);
+  if (f64) launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
+  else launch_dt_f32(c->k, c->M, c->tag, c->ds, s, &nl);
+  prof_mark(c, 3, false);
   double *in64[3] = {c->A, c->B, c->C};
   double *out64[3] = {c->B, c->C, c->A};
   float *in32[3] = {c->M, c->F1, c->F2};
@@ -351,20 +358,14 @@ static int enqueue_step(ibm_case *c) {
     if (f64) launch_recon_f64(c->k, in64[st - 1], c->st, c->cap, c->ds, st, s, &nl);
     else launch_recon_f32(c->k, in32[st - 1], c->A, c->st, c->cap, c->ds, st, s, &nl);
     prof_mark(c, 1, false);
-    prof_mark(c, 2, true);
-    if (f64) launch_bc_f64(c->k, in64[st - 1], s);
-    else launch_bc_f32(c->k, in32[st - 1], s);
-    prof_mark(c, 2, false);
+    // domain halos are applied inside the stage kernel's tile load; the end
+    // of the step (t += dt) is folded into stage 3
     prof_mark(c, 0, true);
     if (f64) launch_stage_f64(c->k, st, c->A, in64[st - 1], out64[st - 1], c->tag, c->ds, s);
     else launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->ds, s);
     prof_mark(c, 0, false);
-    nl += 2;
+    nl += 1;
   }
-  prof_mark(c, 5, true);
-  launch_step_end(c->k, c->ds, s);
-  prof_mark(c, 5, false);
-  nl += 1;
   return nl;
 }
 
@@ -468,10 +469,18 @@ extern "C" ibm_status ibm_sync(ibm_case *c) {
 // copy between a [4][ny][nx] host/device buffer and the padded state planes
 static ibm_status copy_state(ibm_case *c, double *dst, const double *src, bool to_user, bool user_on_device) {
   const Consts &k = c->k;
+  double *base = c->A;
+  if (to_user && c->precision == IBM_PREC_FP32_BULK) {
+    // the FP64 state holds dU; hand out absolute conserved variables
+    if (!c->stage64) CU(cudaMalloc((void **)&c->stage64, 4 * (size_t)k.plane * sizeof(double)));
+    launch_pert_to_abs64(k, c->A, c->stage64, c->stream);
+    c->launches++;
+    base = c->stage64;
+  }
   cudaMemcpyKind kind = to_user ? (user_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost)
                                 : (user_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
   for (int v = 0; v < 4; v++) {
-    double *dev = c->A + v * k.plane + cidx(k, 0, 0);
+    double *dev = (to_user ? base : c->A) + v * k.plane + cidx(k, 0, 0);
     double *usr = (to_user ? dst : (double *)src) + (size_t)v * k.nx * k.ny;
     if (to_user)
       CU(cudaMemcpy2DAsync(usr, sizeof(double) * k.nx, dev, sizeof(double) * k.pitch, sizeof(double) * k.nx, k.ny,
@@ -544,8 +553,9 @@ extern "C" ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, 
   ibm_status q = copy_state(c, nullptr, (const double *)src, false, src_on_device);
   if (q != IBM_OK) return q;
   if (c->M) {
-    launch_to_pert(c->k, c->A, c->M, c->stream);
-    c->launches++;
+    launch_abs_to_pert64(c->k, c->A, c->stream);
+    launch_to_mirror(c->k, c->A, c->M, c->stream);
+    c->launches += 2;
   }
   if (!src_on_device) CU(cudaStreamSynchronize(c->stream));
   CU(cudaGetLastError());
@@ -562,7 +572,7 @@ extern "C" ibm_status ibm_forces(ibm_case *c, double out[4]) {
     ibm_status r = do_classify(c);
     if (r != IBM_OK) return r;
   }
-  launch_forces_f64(c->k, c->g, c->tag, c->A, c->ds, c->stream);
+  launch_forces_f64(c->k, c->g, c->tag, c->A, c->precision == IBM_PREC_FP32_BULK, c->ds, c->stream);
   c->launches++;
   ibm_status r = sync_and_check(c);
   for (int q = 0; q < 4; q++) out[q] = c->hds->force[q];

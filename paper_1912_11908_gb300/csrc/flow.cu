@@ -1,5 +1,6 @@
-// FP64 flow kernels: time step, IB / ghost reconstruction, domain halos and
-// the fused residual + SSP-RK3 stage update.
+// FP64 flow kernels: time step, IB / ghost reconstruction and the fused
+// residual + SSP-RK3 stage update (domain halos are applied while the stage
+// kernel loads its tile).
 //
 // State layout: structure of arrays, four conserved planes (rho, rho u,
 // rho v, rho E), each (ny + 6) rows of `pitch` doubles; cell (i, j) of the
@@ -13,7 +14,8 @@ namespace ibm {
 // Time step from the CFL rule over fluid cells:
 //   dt = CFL / max[(|u|+c)/dx + (|v|+c)/dy + 2 gamma mu/(Pr rho)(1/dx^2+1/dy^2)].
 // Positive doubles order like their bit patterns, so the maximum is an
-// integer atomicMax (order-independent, exact).
+// integer atomicMax (order-independent, exact); the last block to finish
+// turns it into dt.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_dt(Consts k, const double *__restrict__ A,
                                             const uint8_t *__restrict__ tag, DevState *ds) {
@@ -37,27 +39,16 @@ __global__ void __launch_bounds__(256) k_dt(Consts k, const double *__restrict__
     double m = wm[0];
     for (int w = 1; w < 8; w++) m = fmax(m, wm[w]);
     atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong(m));
+    finish_cfl(k, ds);
   }
 }
 
 void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch) {
-  cudaMemsetAsync(&ds->lmax_bits, 0, sizeof(unsigned long long), s);
-  if (k.dt_fixed > 0.0) return;
+  if (k.dt_fixed > 0.0) return;  // ds->dt was set at creation
   int ncell = k.nx * k.ny;
   int blocks = min((ncell + 255) / 256, 152 * 8);
   k_dt<<<blocks, 256, 0, s>>>(k, A, tag, ds);
   *nlaunch += 1;
-}
-
-__device__ inline double step_dt(const Consts &k, const DevState *ds) {
-  if (k.dt_fixed > 0.0) return k.dt_fixed;
-  return k.cfl / __longlong_as_double((long long)ds->lmax_bits);
-}
-
-// stage c-coefficients of SSP-RK3: t_k = t + c_k dt
-__device__ inline double stage_time(const Consts &k, const DevState *ds, int stage) {
-  double dt = step_dt(k, ds);
-  return stage == 1 ? ds->t : (stage == 2 ? ds->t + dt : ds->t + 0.5 * dt);
 }
 
 // ---------------------------------------------------------------------------
@@ -68,16 +59,9 @@ __device__ inline double stage_time(const Consts &k, const DevState *ds, int sta
 // dp/dn = -rho n.a_wall (Eq. 5-6); temperature is adiabatic (Eq. 8).
 // One thread per list entry; in place on the stage array.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_recon_f64(Consts k, double *U, const ibm_stencil *__restrict__ st,
-                                                   int cap, const DevState *__restrict__ ds, int stage, int pass) {
-  const int lo = pass == 0 ? 0 : ds->offset[1];
-  const int hi = min(pass == 0 ? ds->offset[1] : ds->offset[4], cap);
-  const int e = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= hi) return;
-  const ibm_stencil &s = st[e];
+__device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const ibm_stencil &s, const double V[2],
+                                              const double Acc[2]) {
   if (s.mask == 0) return;
-  double X[2], V[2], Acc[2];
-  motion_at(k.motion, stage_time(k, ds, stage), X, V, Acc);
   double qp[4] = {0.0, 0.0, 0.0, 0.0};
   for (int q = 0; q < 4; q++) {
     if (!(s.mask >> q & 1)) continue;
@@ -105,81 +89,41 @@ __global__ void __launch_bounds__(128) k_recon_f64(Consts k, double *U, const ib
   U[id + 3 * k.plane] = p / (k.gamma - 1.0) + 0.5 * r * (u * u + v * v);
 }
 
+// one block: all IB nodes, a barrier, then all ghost nodes
+__global__ void __launch_bounds__(1024) k_recon1_f64(Consts k, double *U, const ibm_stencil *__restrict__ st,
+                                                     int cap, const DevState *__restrict__ ds, int stage) {
+  double X[2], V[2], Acc[2];
+  motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
+  const int nib = min(ds->offset[1], cap), tot = min(ds->offset[4], cap);
+  for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc);
+  __syncthreads();
+  for (int e = nib + threadIdx.x; e < tot; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc);
+}
+
+// many blocks, one pass (0: IB nodes, 1: ghost nodes) per launch
+__global__ void __launch_bounds__(128) k_recon_f64(Consts k, double *U, const ibm_stencil *__restrict__ st,
+                                                   int cap, const DevState *__restrict__ ds, int stage, int pass) {
+  const int lo = pass == 0 ? 0 : ds->offset[1];
+  const int hi = min(pass == 0 ? ds->offset[1] : ds->offset[4], cap);
+  const int e = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= hi) return;
+  double X[2], V[2], Acc[2];
+  motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
+  recon_one_f64(k, U, st[e], V, Acc);
+}
+
 void launch_recon_f64(const Consts &k, double *U, const ibm_stencil *st, int cap, const DevState *ds, int stage,
                       cudaStream_t s, int *nlaunch) {
   if (cap <= 0) return;
+  if (cap <= RECON_ONE_BLOCK_MAX) {
+    k_recon1_f64<<<1, 1024, 0, s>>>(k, U, st, cap, ds, stage);
+    *nlaunch += 1;
+    return;
+  }
   int blocks = (cap + 127) / 128;
   k_recon_f64<<<blocks, 128, 0, s>>>(k, U, st, cap, ds, stage, 0);
   k_recon_f64<<<blocks, 128, 0, s>>>(k, U, st, cap, ds, stage, 1);
   *nlaunch += 2;
-}
-
-// ---------------------------------------------------------------------------
-// Domain halos: free-stream Dirichlet, zero-gradient outflow, or periodic.
-// A halo cell beyond both an x side and a y side takes the x rule applied to
-// the y-filled column, i.e. the free stream if either side is free stream,
-// otherwise the interior cell both source maps point to.
-// ---------------------------------------------------------------------------
-__device__ inline int halo_src(int side_bc, int idx, int n, bool low) {
-  // returns the interior index feeding halo index idx, or -1 for free stream
-  if (side_bc == IBM_BC_PERIODIC) return low ? idx + n : idx - n;
-  if (side_bc == IBM_BC_OUTFLOW) return low ? 0 : n - 1;
-  return -1;
-}
-
-template <typename T>
-__global__ void k_bc(Consts k, T *U, T f0, T f1, T f2, T f3) {
-  const int nx = k.nx, ny = k.ny;
-  const int ny_side = NG * nx;          // cells per y side
-  const int nx_side = NG * (ny + 2 * NG);  // cells per x side
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int i, j;
-  if (t < 2 * ny_side) {
-    int side = t / ny_side, r = t % ny_side;
-    int g = r / nx + 1;
-    i = r % nx;
-    j = side == 0 ? -g : ny - 1 + g;
-  } else if (t < 2 * ny_side + 2 * nx_side) {
-    t -= 2 * ny_side;
-    int side = t / nx_side, r = t % nx_side;
-    int g = r / (ny + 2 * NG) + 1;
-    j = r % (ny + 2 * NG) - NG;
-    i = side == 0 ? -g : nx - 1 + g;
-  } else {
-    return;
-  }
-  int si = i, sj = j;
-  bool fs = false;
-  if (i < 0 || i >= nx) {
-    int b = k.bc[i < 0 ? 0 : 1];
-    si = halo_src(b, i, nx, i < 0);
-    fs |= si < 0;
-  }
-  if (j < 0 || j >= ny) {
-    int b = k.bc[j < 0 ? 2 : 3];
-    sj = halo_src(b, j, ny, j < 0);
-    fs |= sj < 0;
-  }
-  long long d = cidx(k, i, j);
-  if (fs) {
-    U[d] = f0;
-    U[d + k.plane] = f1;
-    U[d + 2 * k.plane] = f2;
-    U[d + 3 * k.plane] = f3;
-  } else {
-    long long s = cidx(k, si, sj);
-    for (int v = 0; v < 4; v++) U[d + v * k.plane] = U[s + v * k.plane];
-  }
-}
-
-void launch_bc_f64(const Consts &k, double *U, cudaStream_t s) {
-  int n = 2 * NG * k.nx + 2 * NG * (k.ny + 2 * NG);
-  k_bc<double><<<(n + 255) / 256, 256, 0, s>>>(k, U, k.Uinf[0], k.Uinf[1], k.Uinf[2], k.Uinf[3]);
-}
-
-void launch_bc_f32(const Consts &k, float *U, cudaStream_t s) {
-  int n = 2 * NG * k.nx + 2 * NG * (k.ny + 2 * NG);
-  k_bc<float><<<(n + 255) / 256, 256, 0, s>>>(k, U, 0.f, 0.f, 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -263,8 +207,7 @@ constexpr int TX = 16, TY = 16, HX = TX + 2 * NG, HY = TY + 2 * NG;
 
 template <int STAGE>
 __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, const double *__restrict__ In,
-                                                   double *Out, const uint8_t *__restrict__ tag,
-                                                   const DevState *__restrict__ ds) {
+                                                   double *Out, const uint8_t *__restrict__ tag, DevState *ds) {
   __shared__ double sq[4][HY][HX];  // rho, u, v, p
   __shared__ double sT[HY][HX];     // temperature
   __shared__ double sfx[4][TY][TX + 1];
@@ -274,18 +217,36 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
   const int ci = i0 + tx, cj = j0 + ty;
   const bool inside = ci < k.nx && cj < k.ny;
   const bool fluid = inside && tag[cj * k.nx + ci] == FLUID;
+  const double dt = ds->dt;
+  if (STAGE == 3 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    // end of the step (no other kernel of this stage reads t)
+    ds->t = ds->t + dt;
+    ds->steps += 1;
+  }
   if (!__syncthreads_or(fluid)) return;
 
   const long long P = k.plane;
   const double g1 = k.gamma - 1.0;
   for (int m = threadIdx.x; m < HX * HY; m += 256) {
     const int a = m % HX, b = m / HX;
-    const int gi = min(i0 - NG + a, k.nx + NG - 1), gj = min(j0 - NG + b, k.ny + NG - 1);
-    const long long id = cidx(k, gi, gj);
-    const double r = In[id];
+    int gi = i0 - NG + a, gj = j0 - NG + b;
+    double U0, U1, U2, U3;
+    if (halo_map(k, gi, gj)) {
+      const long long id = cidx(k, gi, gj);
+      U0 = In[id];
+      U1 = In[id + P];
+      U2 = In[id + 2 * P];
+      U3 = In[id + 3 * P];
+    } else {
+      U0 = k.Uinf[0];
+      U1 = k.Uinf[1];
+      U2 = k.Uinf[2];
+      U3 = k.Uinf[3];
+    }
+    const double r = U0;
     const double ir = 1.0 / r;
-    const double u = In[id + P] * ir, v = In[id + 2 * P] * ir;
-    const double p = g1 * (In[id + 3 * P] - 0.5 * r * (u * u + v * v));
+    const double u = U1 * ir, v = U2 * ir;
+    const double p = g1 * (U3 - 0.5 * r * (u * u + v * v));
     sq[0][b][a] = r;
     sq[1][b][a] = u;
     sq[2][b][a] = v;
@@ -364,7 +325,6 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
   }
   __syncthreads();
   if (!fluid) return;
-  const double dt = step_dt(k, ds);
   const long long id = cidx(k, ci, cj);
   for (int v = 0; v < 4; v++) {
     const double L = -((sfx[v][ty][tx + 1] - sfx[v][ty][tx]) * idx + (sfy[v][ty + 1][tx] - sfy[v][ty][tx]) * idy);
@@ -378,20 +338,11 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
 }
 
 void launch_stage_f64(const Consts &k, int stage, const double *Un, const double *In, double *Out,
-                      const uint8_t *tag, const DevState *ds, cudaStream_t s) {
+                      const uint8_t *tag, DevState *ds, cudaStream_t s) {
   dim3 grid((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY);
   if (stage == 1) k_stage_f64<1><<<grid, 256, 0, s>>>(k, Un, In, Out, tag, ds);
   else if (stage == 2) k_stage_f64<2><<<grid, 256, 0, s>>>(k, Un, In, Out, tag, ds);
   else k_stage_f64<3><<<grid, 256, 0, s>>>(k, Un, In, Out, tag, ds);
 }
-
-__global__ void k_step_end(DevState *ds, Consts k) {
-  double dt = step_dt(k, ds);
-  ds->dt = dt;
-  ds->t = ds->t + dt;
-  ds->steps += 1;
-}
-
-void launch_step_end(const Consts &k, DevState *ds, cudaStream_t s) { k_step_end<<<1, 1, 0, s>>>(ds, k); }
 
 }  // namespace ibm

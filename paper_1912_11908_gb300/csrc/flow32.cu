@@ -6,8 +6,12 @@
 // rho_inf).  Primitives are (rho', u, v, p') with p' = p - p_inf and
 // T' = T - T_inf formed without ever adding p_inf or H_inf to an FP32 value,
 // so O(M^2) pressure and temperature fluctuations keep their FP32 precision
-// at any free-stream Mach number.  The conserved state is accumulated in FP64
-// at the last stage of every step (FP64 U^{n+1} from FP32 U^(2) and L).
+// at any free-stream Mach number.  The state U^n is held in FP64 as the same
+// perturbation dU and accumulated in FP64 at the last stage of every step:
+// dU^{n+1} = dU^n + (double)[2/3 ((dU^(2) - dU^n) + dt L)], where the bracket
+// is an O(dt) increment formed in FP32 (the FP32 mirror of dU^n is rounded
+// from the FP64 state after every step, so FP32 rounding never accumulates in
+// U^n).
 #include "ibm_internal.cuh"
 
 namespace ibm {
@@ -58,35 +62,84 @@ __device__ __forceinline__ void prim_pert(const PertConsts &c, float pp, float u
   W = pp / c.g1 + ke - c.Hinf * dr;
 }
 
-// FP64 absolute conserved -> FP32 perturbation
-__device__ __forceinline__ void abs_to_pert(const Consts &k, double r, double mx, double my, double E, float &dr,
-                                            float &dmx, float &dmy, float &W) {
-  const double d = r - 1.0;
-  dr = (float)d;
-  dmx = (float)(mx - k.Uinf[1]);
-  dmy = (float)(my - k.Uinf[2]);
-  W = (float)((E - k.Uinf[3]) - k.Hinf * d);
-}
-
-__global__ void k_to_pert(Consts k, const double *__restrict__ A, float *__restrict__ M) {
+// FP64 absolute conserved <-> FP64 perturbation, in place / out of place
+__global__ void k_abs_to_pert64(Consts k, double *D) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= k.plane) return;
   const long long P = k.plane;
-  float a, b, c, d;
-  abs_to_pert(k, A[n], A[n + P], A[n + 2 * P], A[n + 3 * P], a, b, c, d);
-  M[n] = a;
-  M[n + P] = b;
-  M[n + 2 * P] = c;
-  M[n + 3 * P] = d;
+  const double d = D[n] - 1.0;
+  D[n] = d;
+  D[n + P] = D[n + P] - k.Uinf[1];
+  D[n + 2 * P] = D[n + 2 * P] - k.Uinf[2];
+  D[n + 3 * P] = (D[n + 3 * P] - k.Uinf[3]) - k.Hinf * d;
 }
 
-void launch_to_pert(const Consts &k, const double *A, float *M, cudaStream_t s) {
-  k_to_pert<<<(unsigned)((k.plane + 255) / 256), 256, 0, s>>>(k, A, M);
+__global__ void k_pert_to_abs64(Consts k, const double *__restrict__ D, double *__restrict__ A) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= k.plane) return;
+  const long long P = k.plane;
+  const double d = D[n];
+  A[n] = 1.0 + d;
+  A[n + P] = k.Uinf[1] + D[n + P];
+  A[n + 2 * P] = k.Uinf[2] + D[n + 2 * P];
+  A[n + 3 * P] = k.Uinf[3] + D[n + 3 * P] + k.Hinf * d;
 }
 
-__device__ inline double step_dt32(const Consts &k, const DevState *ds) {
-  if (k.dt_fixed > 0.0) return k.dt_fixed;
-  return k.cfl / __longlong_as_double((long long)ds->lmax_bits);
+__global__ void k_to_mirror(Consts k, const double *__restrict__ D, float *__restrict__ M) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= 4 * k.plane) return;
+  M[n] = (float)D[n];
+}
+
+void launch_abs_to_pert64(const Consts &k, double *D, cudaStream_t s) {
+  k_abs_to_pert64<<<(unsigned)((k.plane + 255) / 256), 256, 0, s>>>(k, D);
+}
+void launch_pert_to_abs64(const Consts &k, const double *D, double *A, cudaStream_t s) {
+  k_pert_to_abs64<<<(unsigned)((k.plane + 255) / 256), 256, 0, s>>>(k, D, A);
+}
+void launch_to_mirror(const Consts &k, const double *D, float *M, cudaStream_t s) {
+  k_to_mirror<<<(unsigned)((4 * k.plane + 255) / 256), 256, 0, s>>>(k, D, M);
+}
+
+// CFL rule (same expression as the FP64 path) evaluated in FP32 on the mirror
+// of U^n; the last block converts the maximum into dt.
+__global__ void __launch_bounds__(256) k_dt_f32(Consts k, PertConsts c, const float *__restrict__ M,
+                                                const uint8_t *__restrict__ tag, DevState *ds) {
+  const int ncell = k.nx * k.ny;
+  const long long P = k.plane;
+  const float idx = c.idx, idy = c.idy;
+  const float vis = (float)((2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy)));
+  float lmax = 0.f;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ncell; n += gridDim.x * blockDim.x) {
+    if (tag[n] != FLUID) continue;
+    const long long id = cidx(k, n % k.nx, n / k.nx);
+    float u, v, pp, Tp;
+    const float dr = M[id];
+    pert_prim(c, dr, M[id + P], M[id + 2 * P], M[id + 3 * P], u, v, pp, Tp);
+    const float r = 1.f + dr;
+    const float cs = sqrtf(c.gamma * (c.R + pp) / r);
+    const float lam = (fabsf(u) + cs) * idx + (fabsf(v) + cs) * idy + vis / r;
+    lmax = fmaxf(lmax, lam);
+  }
+  for (int off = 16; off > 0; off >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
+  __shared__ float wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = lmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = wm[0];
+    for (int w = 1; w < 8; w++) m = fmaxf(m, wm[w]);
+    atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong((double)m));
+    finish_cfl(k, ds);
+  }
+}
+
+void launch_dt_f32(const Consts &k, const float *M, const uint8_t *tag, DevState *ds, cudaStream_t s,
+                   int *nlaunch) {
+  if (k.dt_fixed > 0.0) return;
+  const int ncell = k.nx * k.ny;
+  const int blocks = min((ncell + 255) / 256, 152 * 4);
+  k_dt_f32<<<blocks, 256, 0, s>>>(k, pert_consts(k), M, tag, ds);
+  *nlaunch += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -95,19 +148,10 @@ __device__ inline double step_dt32(const Consts &k, const DevState *ds) {
 // temperature Eq. 8).  At stage 1 the rebuilt value is also written to the
 // FP64 state so both copies of U^n agree on IB and ghost nodes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_recon_f32(Consts k, PertConsts c, float *U, double *A,
-                                                   const ibm_stencil *__restrict__ st, int cap,
-                                                   const DevState *__restrict__ ds, int stage, int pass) {
-  const int lo = pass == 0 ? 0 : ds->offset[1];
-  const int hi = min(pass == 0 ? ds->offset[1] : ds->offset[4], cap);
-  const int e = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= hi) return;
-  const ibm_stencil &s = st[e];
+__device__ __forceinline__ void recon_one_f32(const Consts &k, const PertConsts &c, float *U, double *D,
+                                              const ibm_stencil &s, int stage, const double V[2],
+                                              const double Acc[2]) {
   if (s.mask == 0) return;
-  const double dt = step_dt32(k, ds);
-  const double ts = stage == 1 ? ds->t : (stage == 2 ? ds->t + dt : ds->t + 0.5 * dt);
-  double X[2], V[2], Acc[2];
-  motion_at(k.motion, ts, X, V, Acc);
   const long long P = k.plane;
   float qp[4] = {0.f, 0.f, 0.f, 0.f};
   for (int q = 0; q < 4; q++) {
@@ -135,21 +179,49 @@ __global__ void __launch_bounds__(128) k_recon_f32(Consts k, PertConsts c, float
   U[id + P] = dmx;
   U[id + 2 * P] = dmy;
   U[id + 3 * P] = W;
-  if (stage == 1) {
-    A[id] = 1.0 + (double)dr;
-    A[id + P] = k.Uinf[1] + (double)dmx;
-    A[id + 2 * P] = k.Uinf[2] + (double)dmy;
-    A[id + 3 * P] = k.Uinf[3] + (double)W + k.Hinf * (double)dr;
+  if (stage == 1) {  // keep the FP64 copy of U^n in step on IB and ghost nodes
+    D[id] = dr;
+    D[id + P] = dmx;
+    D[id + 2 * P] = dmy;
+    D[id + 3 * P] = W;
   }
 }
 
-void launch_recon_f32(const Consts &k, float *U, double *A, const ibm_stencil *st, int cap, const DevState *ds,
+__global__ void __launch_bounds__(1024) k_recon1_f32(Consts k, PertConsts c, float *U, double *D,
+                                                     const ibm_stencil *__restrict__ st, int cap,
+                                                     const DevState *__restrict__ ds, int stage) {
+  double X[2], V[2], Acc[2];
+  motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
+  const int nib = min(ds->offset[1], cap), tot = min(ds->offset[4], cap);
+  for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f32(k, c, U, D, st[e], stage, V, Acc);
+  __syncthreads();
+  for (int e = nib + threadIdx.x; e < tot; e += blockDim.x) recon_one_f32(k, c, U, D, st[e], stage, V, Acc);
+}
+
+__global__ void __launch_bounds__(128) k_recon_f32(Consts k, PertConsts c, float *U, double *D,
+                                                   const ibm_stencil *__restrict__ st, int cap,
+                                                   const DevState *__restrict__ ds, int stage, int pass) {
+  const int lo = pass == 0 ? 0 : ds->offset[1];
+  const int hi = min(pass == 0 ? ds->offset[1] : ds->offset[4], cap);
+  const int e = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= hi) return;
+  double X[2], V[2], Acc[2];
+  motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
+  recon_one_f32(k, c, U, D, st[e], stage, V, Acc);
+}
+
+void launch_recon_f32(const Consts &k, float *U, double *D, const ibm_stencil *st, int cap, const DevState *ds,
                       int stage, cudaStream_t s, int *nlaunch) {
   if (cap <= 0) return;
   PertConsts c = pert_consts(k);
+  if (cap <= RECON_ONE_BLOCK_MAX) {
+    k_recon1_f32<<<1, 1024, 0, s>>>(k, c, U, D, st, cap, ds, stage);
+    *nlaunch += 1;
+    return;
+  }
   int blocks = (cap + 127) / 128;
-  k_recon_f32<<<blocks, 128, 0, s>>>(k, c, U, A, st, cap, ds, stage, 0);
-  k_recon_f32<<<blocks, 128, 0, s>>>(k, c, U, A, st, cap, ds, stage, 1);
+  k_recon_f32<<<blocks, 128, 0, s>>>(k, c, U, D, st, cap, ds, stage, 0);
+  k_recon_f32<<<blocks, 128, 0, s>>>(k, c, U, D, st, cap, ds, stage, 1);
   *nlaunch += 2;
 }
 
@@ -227,10 +299,9 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
 constexpr int TX = 16, TY = 16, HX = TX + 2 * NG, HY = TY + 2 * NG;
 
 template <int STAGE>
-__global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, const float *Mn,
-                                                   const float *__restrict__ In, float *Out, double *A,
-                                                   const uint8_t *__restrict__ tag,
-                                                   const DevState *__restrict__ ds) {
+__global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, float *Mn, const float *__restrict__ In,
+                                                   float *Out, double *D, const uint8_t *__restrict__ tag,
+                                                   DevState *ds) {
   __shared__ float sq[4][HY][HX];  // rho', u, v, p'
   __shared__ float sT[HY][HX];     // T'
   __shared__ float sfx[4][TY][TX + 1];
@@ -240,16 +311,28 @@ __global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, const
   const int ci = i0 + tx, cj = j0 + ty;
   const bool inside = ci < k.nx && cj < k.ny;
   const bool fluid = inside && tag[cj * k.nx + ci] == FLUID;
+  const double dtd = ds->dt;
+  if (STAGE == 3 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    // end of the step (no other kernel of this stage reads t)
+    ds->t = ds->t + dtd;
+    ds->steps += 1;
+  }
   if (!__syncthreads_or(fluid)) return;
 
   const long long P = k.plane;
   for (int m = threadIdx.x; m < HX * HY; m += 256) {
     const int a = m % HX, b = m / HX;
-    const int gi = min(i0 - NG + a, k.nx + NG - 1), gj = min(j0 - NG + b, k.ny + NG - 1);
-    const long long id = cidx(k, gi, gj);
-    const float dr = In[id];
+    int gi = i0 - NG + a, gj = j0 - NG + b;
+    float dr = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;  // free stream: zero perturbation
+    if (halo_map(k, gi, gj)) {
+      const long long id = cidx(k, gi, gj);
+      dr = In[id];
+      d1 = In[id + P];
+      d2 = In[id + 2 * P];
+      d3 = In[id + 3 * P];
+    }
     float u, v, pp, Tp;
-    pert_prim(c, dr, In[id + P], In[id + 2 * P], In[id + 3 * P], u, v, pp, Tp);
+    pert_prim(c, dr, d1, d2, d3, u, v, pp, Tp);
     sq[0][b][a] = dr;
     sq[1][b][a] = u;
     sq[2][b][a] = v;
@@ -324,8 +407,7 @@ __global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, const
   }
   __syncthreads();
   if (!fluid) return;
-  const double dtd = step_dt32(k, ds);
-  const float dt = (float)dtd;
+  const float dt = ds->dtf;
   const long long id = cidx(k, ci, cj);
   float L[4];
   for (int v = 0; v < 4; v++)
@@ -335,32 +417,24 @@ __global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, const
   } else if (STAGE == 2) {
     for (int v = 0; v < 4; v++) Out[id + v * P] = 0.75f * Mn[id + v * P] + 0.25f * (In[id + v * P] + dt * L[v]);
   } else {
-    // FP64 accumulation of U^{n+1} = 1/3 U^n + 2/3 (U^(2) + dt L), absolute conserved variables
-    const double dr = In[id], dmx = In[id + P], dmy = In[id + 2 * P], W = In[id + 3 * P];
-    const double u2[4] = {1.0 + dr, k.Uinf[1] + dmx, k.Uinf[2] + dmy, k.Uinf[3] + W + k.Hinf * dr};
-    const double La[4] = {(double)L[0], (double)L[1], (double)L[2], (double)L[3] + k.Hinf * (double)L[0]};
-    double an[4];
+    // FP64 accumulation: dU^{n+1} = dU^n + (double)[2/3 ((dU^(2) - dU^n) + dt L)]
     for (int v = 0; v < 4; v++) {
-      an[v] = (1.0 / 3.0) * A[id + v * P] + (2.0 / 3.0) * (u2[v] + dtd * La[v]);
-      A[id + v * P] = an[v];
+      const long long o = id + v * P;
+      const float inc = (2.f / 3.f) * ((In[o] - Mn[o]) + dt * L[v]);
+      const double dn = D[o] + (double)inc;
+      D[o] = dn;
+      Mn[o] = (float)dn;
     }
-    float a, b2, c2, d;
-    abs_to_pert(k, an[0], an[1], an[2], an[3], a, b2, c2, d);
-    float *Mw = const_cast<float *>(Mn);
-    Mw[id] = a;
-    Mw[id + P] = b2;
-    Mw[id + 2 * P] = c2;
-    Mw[id + 3 * P] = d;
   }
 }
 
-void launch_stage_f32(const Consts &k, int stage, const float *Mn, const float *In, float *Out, double *A,
-                      const uint8_t *tag, const DevState *ds, cudaStream_t s) {
+void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
+                      const uint8_t *tag, DevState *ds, cudaStream_t s) {
   PertConsts c = pert_consts(k);
   dim3 grid((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY);
-  if (stage == 1) k_stage_f32<1><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, A, tag, ds);
-  else if (stage == 2) k_stage_f32<2><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, A, tag, ds);
-  else k_stage_f32<3><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, A, tag, ds);
+  if (stage == 1) k_stage_f32<1><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, ds);
+  else if (stage == 2) k_stage_f32<2><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, ds);
+  else k_stage_f32<3><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, ds);
 }
 
 }  // namespace ibm

@@ -484,7 +484,7 @@ void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_ste
 // subtracted.  One block; fixed-order tree reduction (deterministic).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint8_t *__restrict__ tag,
-                                                    const double *__restrict__ A, DevState *ds) {
+                                                    const double *__restrict__ A, bool pert, DevState *ds) {
   __shared__ double rx[256], ry[256];
   double V[2], Acc[2], X[2];
   motion_at(k.motion, ds->t, X, V, Acc);
@@ -509,8 +509,15 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
     for (int q = 0; q < 4; q++) {
       if (!(mask >> q & 1)) continue;
       long long id = cidx(k, i0 + (q & 1), j0 + (q >> 1));
-      double r = A[id], u = A[id + k.plane] / r, v = A[id + 2 * k.plane] / r;
-      double pr = (k.gamma - 1.0) * (A[id + 3 * k.plane] - 0.5 * r * (u * u + v * v));
+      double U0 = A[id], U1 = A[id + k.plane], U2 = A[id + 2 * k.plane], U3 = A[id + 3 * k.plane];
+      if (pert) {  // perturbation state dU -> absolute conserved
+        U3 = k.Uinf[3] + U3 + k.Hinf * U0;
+        U0 = 1.0 + U0;
+        U1 = k.Uinf[1] + U1;
+        U2 = k.Uinf[2] + U2;
+      }
+      double r = U0, u = U1 / r, v = U2 / r;
+      double pr = (k.gamma - 1.0) * (U3 - 0.5 * r * (u * u + v * v));
       double T = pr / (r * k.R);
       qp[0] += w[q] * pr;
       qp[1] += w[q] * u;
@@ -543,9 +550,9 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
   }
 }
 
-void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, DevState *ds,
-                       cudaStream_t s) {
-  k_forces_f64<<<1, 256, 0, s>>>(k, g, tag, A, ds);
+void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, bool pert,
+                       DevState *ds, cudaStream_t s) {
+  k_forces_f64<<<1, 256, 0, s>>>(k, g, tag, A, pert, ds);
 }
 
 }  // namespace ibm

@@ -15,8 +15,10 @@ enum : uint8_t { FLUID = 0, SOLID = 1, IB = 2, G1 = 3, G2 = 4, G3 = 5 };
 // device-resident per-case scalars
 struct DevState {
   double t;                      // time at the start of the current step
-  double dt;                     // step size of the current step
-  unsigned long long lmax_bits;  // max spectral radius (bits of a positive double)
+  double dt;                     // step size of the current step (set by the CFL reduction)
+  unsigned long long lmax_bits;  // max spectral radius (bits of a positive double); 0 between reductions
+  unsigned int done;             // blocks of the CFL reduction that have finished; 0 between reductions
+  float dtf;                     // dt rounded to FP32
   int count[4];                  // #IB, #G1, #G2, #G3
   int offset[5];                 // exclusive prefix of count; offset[4] = total
   int err;                       // bit 0: list capacity exceeded, bit 1: empty stencil
@@ -26,6 +28,11 @@ struct DevState {
   double force[4];               // Cd, Cl, Fx, Fy
   long long steps;
 };
+
+// IB / ghost lists up to this capacity are rebuilt by a single 1024-thread
+// block per stage (IB nodes, barrier, ghost nodes); larger lists use two
+// launches.
+constexpr int RECON_ONE_BLOCK_MAX = 1 << 16;
 
 constexpr int ERR_CAPACITY = 1;
 constexpr int ERR_STENCIL = 2;
@@ -61,6 +68,53 @@ __host__ __device__ inline long long cidx(const Consts &k, int i, int j) {
   return (long long)(j + NG) * k.pitch + (i + NG);
 }
 
+// Domain halos, applied while a tile is loaded: maps a cell index outside
+// [0, n) to the interior cell that feeds it (periodic or zero-gradient
+// outflow), or returns false for a free-stream side.  A corner takes the free
+// stream if either side is free stream.
+__device__ __forceinline__ bool halo_axis(int bc_lo, int bc_hi, int n, int &i) {
+  if (i >= 0 && i < n) return true;
+  const int b = i < 0 ? bc_lo : bc_hi;
+  if (b == IBM_BC_PERIODIC) {
+    i = ((i % n) + n) % n;
+    return true;
+  }
+  if (b == IBM_BC_OUTFLOW) {
+    i = i < 0 ? 0 : n - 1;
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool halo_map(const Consts &k, int &i, int &j) {
+  const bool ax = halo_axis(k.bc[0], k.bc[1], k.nx, i);
+  const bool ay = halo_axis(k.bc[2], k.bc[3], k.ny, j);
+  return ax && ay;
+}
+
+// stage times of SSP-RK3: t_k = t + c_k dt, c = (0, 1, 1/2)
+__device__ __forceinline__ double stage_time(const DevState *ds, int stage) {
+  const double dt = ds->dt;
+  return stage == 1 ? ds->t : (stage == 2 ? ds->t + dt : ds->t + 0.5 * dt);
+}
+
+// Last block of a CFL reduction: turn the maximum spectral radius into dt and
+// reset the reduction state for the next step.  Call from thread 0 after the
+// block's atomicMax.
+__device__ __forceinline__ void finish_cfl(const Consts &k, DevState *ds) {
+  __threadfence();
+  const unsigned int ticket = atomicAdd(&ds->done, 1u);
+  if (ticket == gridDim.x * gridDim.y - 1) {
+    __threadfence();
+    const unsigned long long bits = atomicAdd(&ds->lmax_bits, 0ull);
+    const double dt = k.cfl / __longlong_as_double((long long)bits);
+    ds->dt = dt;
+    ds->dtf = (float)dt;
+    ds->lmax_bits = 0ull;
+    ds->done = 0u;
+  }
+}
+
 // motion state at time t
 __device__ inline void motion_at(const Motion &m, double t, double X[2], double V[2], double A[2]) {
   X[0] = X[1] = V[0] = V[1] = A[0] = A[1] = 0.0;
@@ -89,24 +143,26 @@ void launch_tags(const Consts &k, const uint8_t *solid, uint8_t *tag, int *block
                  ibm_stencil *st, cudaStream_t s, int *nlaunch);
 void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
                      cudaStream_t s);
-void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, DevState *ds,
-                       cudaStream_t s);
+// A: FP64 state, absolute conserved (pert = false) or perturbation (pert = true)
+void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, bool pert,
+                       DevState *ds, cudaStream_t s);
 
 // ---- launchers (flow.cu) ----
 void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch);
 void launch_recon_f64(const Consts &k, double *U, const ibm_stencil *st, int cap, const DevState *ds,
                       int stage, cudaStream_t s, int *nlaunch);
-void launch_bc_f64(const Consts &k, double *U, cudaStream_t s);
 void launch_stage_f64(const Consts &k, int stage, const double *Un, const double *In, double *Out,
-                      const uint8_t *tag, const DevState *ds, cudaStream_t s);
-void launch_step_end(const Consts &k, DevState *ds, cudaStream_t s);
+                      const uint8_t *tag, DevState *ds, cudaStream_t s);
 
-// FP32-bulk path (flow32.cu)
-void launch_to_pert(const Consts &k, const double *A, float *M, cudaStream_t s);
-void launch_recon_f32(const Consts &k, float *U, double *A, const ibm_stencil *st, int cap, const DevState *ds,
+// FP32-bulk path (flow32.cu).  The FP64 state D of this mode holds the
+// perturbation dU from the free stream (same variables as the FP32 arrays).
+void launch_abs_to_pert64(const Consts &k, double *D, cudaStream_t s);          // in place
+void launch_pert_to_abs64(const Consts &k, const double *D, double *A, cudaStream_t s);
+void launch_to_mirror(const Consts &k, const double *D, float *M, cudaStream_t s);
+void launch_dt_f32(const Consts &k, const float *M, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch);
+void launch_recon_f32(const Consts &k, float *U, double *D, const ibm_stencil *st, int cap, const DevState *ds,
                       int stage, cudaStream_t s, int *nlaunch);
-void launch_bc_f32(const Consts &k, float *U, cudaStream_t s);
-void launch_stage_f32(const Consts &k, int stage, const float *Mn, const float *In, float *Out, double *A,
-                      const uint8_t *tag, const DevState *ds, cudaStream_t s);
+void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
+                      const uint8_t *tag, DevState *ds, cudaStream_t s);
 
 }  // namespace ibm
