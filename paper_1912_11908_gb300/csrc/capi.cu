@@ -26,7 +26,10 @@ struct ibm_case {
   uint8_t *solid = nullptr, *tag = nullptr;
   int *blockcounts = nullptr;
   ibm_stencil *st = nullptr;
+  RStencil32 *rst = nullptr;  // FP32-bulk: compact stencils
+  int *sid = nullptr;         // FP32-bulk: cell -> stencil index (-1 if none)
   int cap = 0;
+  bool dt_valid = false;      // FP32-bulk static body: dt of the next step is already in DevState
   DevState *ds = nullptr;
   DevState *hds = nullptr;  // pinned host mirror for read-backs
   bool classified = false;
@@ -137,7 +140,7 @@ extern "C" size_t ibm_case_device_bytes(const ibm_geometry *geo, const ibm_grid 
 static void free_case(ibm_case *c) {
   if (!c) return;
   void *ptrs[] = {c->vref, c->vx, c->vy, c->snx, c->sny, c->vnx, c->vny, c->A, c->B, c->C, c->M, c->F1,
-                  c->F2, c->stage64, c->solid, c->tag, c->blockcounts, c->st, c->ds};
+                  c->F2, c->stage64, c->solid, c->tag, c->blockcounts, c->st, c->rst, c->sid, c->ds};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->hds) cudaFreeHost(c->hds);
@@ -231,6 +234,8 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
     ALLOC(c->M, 4 * plane);
     ALLOC(c->F1, 4 * plane);
     ALLOC(c->F2, 4 * plane);
+    ALLOC(c->rst, (size_t)(c->cap > 0 ? c->cap : 1));
+    ALLOC(c->sid, ncell);
   }
   ALLOC(c->solid, ncell);
   ALLOC(c->tag, ncell);
@@ -316,11 +321,16 @@ static ibm_status do_classify(ibm_case *c) {
     nl += 2;
   } else {
     cudaMemsetAsync(c->solid, 0, (size_t)c->k.nx * c->k.ny, s);
+    if (c->sid) cudaMemsetAsync(c->sid, 0xff, sizeof(int) * (size_t)c->k.nx * c->k.ny, s);
   }
   launch_tags(c->k, c->solid, c->tag, c->blockcounts, c->ds, c->cap, c->st, s, &nl);
   if (c->g.nv > 0) {
     launch_stencils(c->k, c->g, c->tag, c->st, c->cap, c->ds, s);
     nl += 1;
+    if (c->rst) {
+      launch_compact_stencils(c->k, c->st, c->rst, c->sid, c->cap, c->ds, s);
+      nl += 1;
+    }
   }
   prof_mark(c, 4, false);
   c->launches += nl;
@@ -334,6 +344,12 @@ extern "C" ibm_status ibm_classify(ibm_case *c) {
   return do_classify(c);
 }
 
+// FP32-bulk with a static body and the CFL rule: the last stage of each step
+// computes the next step's dt (the fluid set cannot change between steps)
+static bool fused_cfl(const ibm_case *c) {
+  return c->precision == IBM_PREC_FP32_BULK && c->k.motion.kind == IBM_MOTION_STATIC && !(c->k.dt_fixed > 0.0);
+}
+
 // one explicit step on the case stream (kernels only; graph-capturable)
 static int enqueue_step(ibm_case *c) {
   cudaStream_t s = c->stream;
@@ -345,24 +361,28 @@ static int enqueue_step(ibm_case *c) {
     c->launches = before;
   }
   const bool f64 = c->precision == IBM_PREC_FP64;
+  const bool fuse_cfl = fused_cfl(c);
   prof_mark(c, 3, true);
   if (f64) launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
-  else launch_dt_f32(c->k, c->M, c->tag, c->ds, s, &nl);
+  else if (!fuse_cfl) launch_dt_f32(c->k, c->M, c->tag, c->ds, s, &nl);
   prof_mark(c, 3, false);
   double *in64[3] = {c->A, c->B, c->C};
   double *out64[3] = {c->B, c->C, c->A};
   float *in32[3] = {c->M, c->F1, c->F2};
   float *out32[3] = {c->F1, c->F2, nullptr};
   for (int st = 1; st <= 3; st++) {
-    prof_mark(c, 1, true);
-    if (f64) launch_recon_f64(c->k, in64[st - 1], c->st, c->cap, c->ds, st, s, &nl);
-    else launch_recon_f32(c->k, in32[st - 1], c->A, c->st, c->cap, c->ds, st, s, &nl);
-    prof_mark(c, 1, false);
-    // domain halos are applied inside the stage kernel's tile load; the end
-    // of the step (t += dt) is folded into stage 3
+    if (f64) {
+      prof_mark(c, 1, true);
+      launch_recon_f64(c->k, in64[st - 1], c->st, c->cap, c->ds, st, s, &nl);
+      prof_mark(c, 1, false);
+    }
+    // domain halos (and, in FP32-bulk mode, IB / ghost nodes) are applied
+    // inside the stage kernel's tile load; the end of the step (t += dt) is
+    // folded into stage 3
     prof_mark(c, 0, true);
     if (f64) launch_stage_f64(c->k, st, c->A, in64[st - 1], out64[st - 1], c->tag, c->ds, s);
-    else launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->ds, s);
+    else launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->ds, fuse_cfl,
+                          s);
     prof_mark(c, 0, false);
     nl += 1;
   }
@@ -398,6 +418,14 @@ extern "C" ibm_status ibm_step(ibm_case *c, int nsteps) {
     // graph holds only the flow kernels
     ibm_status r = do_classify(c);
     if (r != IBM_OK) return r;
+  }
+  if (fused_cfl(c) && !c->dt_valid) {
+    // first step (or state replaced): dt from the current state; afterwards
+    // every step's last stage provides the next dt
+    int nl = 0;
+    launch_dt_f32(c->k, c->M, c->tag, c->ds, c->stream, &nl);
+    c->launches += nl;
+    c->dt_valid = true;
   }
   if (c->use_graphs && !c->profiling) {
     if (!c->graph) {
@@ -556,6 +584,7 @@ extern "C" ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, 
     launch_abs_to_pert64(c->k, c->A, c->stream);
     launch_to_mirror(c->k, c->A, c->M, c->stream);
     c->launches += 2;
+    c->dt_valid = false;
   }
   if (!src_on_device) CU(cudaStreamSynchronize(c->stream));
   CU(cudaGetLastError());

@@ -17,7 +17,7 @@
 namespace ibm {
 
 struct PertConsts {  // FP32 copies of the free-stream constants
-  float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin;
+  float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin, vis;
 };
 
 __host__ inline PertConsts pert_consts(const Consts &k) {
@@ -34,6 +34,7 @@ __host__ inline PertConsts pert_consts(const Consts &k) {
   c.idx = (float)(1.0 / k.dx);
   c.idy = (float)(1.0 / k.dy);
   c.dmin = (float)k.dmin;
+  c.vis = (float)((2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy)));
   return c;
 }
 
@@ -142,108 +143,32 @@ void launch_dt_f32(const Consts &k, const float *M, const uint8_t *tag, DevState
   *nlaunch += 1;
 }
 
-// ---------------------------------------------------------------------------
-// IB / ghost reconstruction in perturbation form (same rules as the FP64
-// path: Dirichlet velocity Eq. 4, Neumann pressure Eq. 5-6, adiabatic
-// temperature Eq. 8).  At stage 1 the rebuilt value is also written to the
-// FP64 state so both copies of U^n agree on IB and ghost nodes.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void recon_one_f32(const Consts &k, const PertConsts &c, float *U, double *D,
-                                              const ibm_stencil &s, int stage, const double V[2],
-                                              const double Acc[2]) {
-  if (s.mask == 0) return;
-  const long long P = k.plane;
-  float qp[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int q = 0; q < 4; q++) {
-    if (!(s.mask >> q & 1)) continue;
-    const long long id = cidx(k, s.i0 + (q & 1), s.j0 + (q >> 1));
-    float u, v, pp, Tp;
-    pert_prim(c, U[id], U[id + P], U[id + 2 * P], U[id + 3 * P], u, v, pp, Tp);
-    const float w = (float)s.w[q];
-    qp[0] += w * pp;
-    qp[1] += w * u;
-    qp[2] += w * v;
-    qp[3] += w * Tp;
-  }
-  const float ratio = (float)(s.xi_node / s.xi_probe);
-  const float rho_p = 1.f + (qp[0] - c.R * qp[3]) / (c.R * (1.f + qp[3]));
-  const float g = -rho_p * (float)(s.nx * Acc[0] + s.ny * Acc[1]);
-  const float pp = qp[0] - (float)(s.xi_probe - s.xi_node) * g;
-  const float Vx = (float)V[0], Vy = (float)V[1];
-  const float u = Vx + (qp[1] - Vx) * ratio;
-  const float v = Vy + (qp[2] - Vy) * ratio;
-  float dr, dmx, dmy, W;
-  prim_pert(c, pp, u, v, qp[3], dr, dmx, dmy, W);
-  const long long id = cidx(k, s.cell % k.nx, s.cell / k.nx);
-  U[id] = dr;
-  U[id + P] = dmx;
-  U[id + 2 * P] = dmy;
-  U[id + 3 * P] = W;
-  if (stage == 1) {  // keep the FP64 copy of U^n in step on IB and ghost nodes
-    D[id] = dr;
-    D[id + P] = dmx;
-    D[id + 2 * P] = dmy;
-    D[id + 3 * P] = W;
-  }
+// FP32 copy of every IB / ghost stencil and the cell -> stencil map used by the
+// fused reconstruction (sid must be -1 on entry)
+__global__ void k_compact_stencils(Consts k, const ibm_stencil *__restrict__ st, RStencil32 *__restrict__ rs,
+                                   int *__restrict__ sid, int cap, const DevState *__restrict__ ds) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= min(ds->offset[4], cap)) return;
+  const ibm_stencil s = st[e];
+  RStencil32 r;
+  r.cell = (int)cidx(k, s.cell % k.nx, s.cell / k.nx);
+  r.corner = s.mask ? (int)cidx(k, s.i0, s.j0) : 0;
+  r.ccell = s.mask ? s.j0 * k.nx + s.i0 : 0;
+  r.mask = s.mask;
+  r.ratio = (float)(s.xi_node / s.xi_probe);
+  r.dxi = (float)(s.xi_probe - s.xi_node);
+  r.nx = (float)s.nx;
+  r.ny = (float)s.ny;
+  for (int q = 0; q < 4; q++) r.w[q] = (float)s.w[q];
+  rs[e] = r;
+  sid[s.cell] = e;
 }
 
-__global__ void __launch_bounds__(1024) k_recon1_f32(Consts k, PertConsts c, float *U, double *D,
-                                                     const ibm_stencil *__restrict__ st, int cap,
-                                                     const DevState *__restrict__ ds, int stage) {
-  double X[2], V[2], Acc[2];
-  motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
-  const int nib = min(ds->offset[1], cap), tot = min(ds->offset[4], cap);
-  for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f32(k, c, U, D, st[e], stage, V, Acc);
-  __syncthreads();
-  for (int e = nib + threadIdx.x; e < tot; e += blockDim.x) recon_one_f32(k, c, U, D, st[e], stage, V, Acc);
-}
-
-__global__ void __launch_bounds__(128) k_recon_f32(Consts k, PertConsts c, float *U, double *D,
-                                                   const ibm_stencil *__restrict__ st, int cap,
-                                                   const DevState *__restrict__ ds, int stage, int pass) {
-  const int lo = pass == 0 ? 0 : ds->offset[1];
-  const int hi = min(pass == 0 ? ds->offset[1] : ds->offset[4], cap);
-  const int e = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= hi) return;
-  double X[2], V[2], Acc[2];
-  motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
-  recon_one_f32(k, c, U, D, st[e], stage, V, Acc);
-}
-
-void launch_recon_f32(const Consts &k, float *U, double *D, const ibm_stencil *st, int cap, const DevState *ds,
-                      int stage, cudaStream_t s, int *nlaunch) {
+void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 *rs, int *sid, int cap,
+                             const DevState *ds, cudaStream_t s) {
+  cudaMemsetAsync(sid, 0xff, sizeof(int) * (size_t)k.nx * k.ny, s);
   if (cap <= 0) return;
-  PertConsts c = pert_consts(k);
-  if (cap <= RECON_ONE_BLOCK_MAX) {
-    k_recon1_f32<<<1, 1024, 0, s>>>(k, c, U, D, st, cap, ds, stage);
-    *nlaunch += 1;
-    return;
-  }
-  int blocks = (cap + 127) / 128;
-  k_recon_f32<<<blocks, 128, 0, s>>>(k, c, U, D, st, cap, ds, stage, 0);
-  k_recon_f32<<<blocks, 128, 0, s>>>(k, c, U, D, st, cap, ds, stage, 1);
-  *nlaunch += 2;
-}
-
-__device__ __forceinline__ float weno5f(float f0, float f1, float f2, float f3, float f4) {
-  const float eps = 1e-6f;
-  float a = f0 - 2.f * f1 + f2, b = f0 - 4.f * f1 + 3.f * f2;
-  const float b0 = (13.f / 12.f) * a * a + 0.25f * b * b;
-  a = f1 - 2.f * f2 + f3;
-  b = f1 - f3;
-  const float b1 = (13.f / 12.f) * a * a + 0.25f * b * b;
-  a = f2 - 2.f * f3 + f4;
-  b = 3.f * f2 - 4.f * f3 + f4;
-  const float b2 = (13.f / 12.f) * a * a + 0.25f * b * b;
-  const float q0 = 2.f * f0 - 7.f * f1 + 11.f * f2;
-  const float q1 = -f1 + 5.f * f2 + 2.f * f3;
-  const float q2 = 2.f * f2 + 5.f * f3 - f4;
-  // a_k = d_k / (eps + b_k)^2: scale by the three squared sums to avoid
-  // three divisions; the 1/6 of the candidate stencils folds into the last one
-  const float e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
-  const float e01 = e0 * e1, e12 = e1 * e2, e02 = e0 * e2;
-  const float a0 = 0.1f * e12 * e12, a1 = 0.6f * e02 * e02, a2 = 0.3f * e01 * e01;
-  return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, 6.f * (a0 + a1 + a2));
+  k_compact_stencils<<<(cap + 127) / 128, 128, 0, s>>>(k, st, rs, sid, cap, ds);
 }
 
 // LDFSS(0) in perturbation form (Mr^2 = 1).  States (rho', un, ut, p');
@@ -298,143 +223,335 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
 // ---------------------------------------------------------------------------
 constexpr int TX = 16, TY = 16, HX = TX + 2 * NG, HY = TY + 2 * NG;
 
+// spectral radius of the CFL rule for one cell of the FP32 mirror
+__device__ __forceinline__ float cfl_lambda(const Consts &k, const PertConsts &c, const float m[4]) {
+  float u, v, pp, Tp;
+  pert_prim(c, m[0], m[1], m[2], m[3], u, v, pp, Tp);
+  const float r = 1.f + m[0];
+  const float cs = sqrtf(c.gamma * (c.R + pp) / r);
+  return (fabsf(u) + cs) * c.idx + (fabsf(v) + cs) * c.idy + c.vis / r;
+}
+
+// block maximum of lam (all 256 threads call), then the grid-wide maximum and
+// dt through the last-block pattern
+__device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float *red, DevState *ds) {
+  for (int off = 16; off > 0; off >>= 1) lam = fmaxf(lam, __shfl_xor_sync(0xffffffffu, lam, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lam;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = red[0];
+    for (int w = 1; w < 8; w++) m = fmaxf(m, red[w]);
+    atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong((double)m));
+    finish_cfl(k, ds);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// IB / ghost reconstruction (Sec. 4.4-4.6, Eq. 4-8; Sec. 5) evaluated while a
+// tile is loaded.  Values are primitives (p', u, v, T').  A ghost node's
+// image point may use IB nodes, which are rebuilt from their own stencils
+// (their corners are fluid), so every rebuilt value depends only on fluid
+// values of the stage input -- the same order as rebuilding all IB nodes
+// first and the ghost nodes after.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void raw_prim(const PertConsts &c, const float *U, long long id, long long P,
+                                         float q[4]) {
+  float u, v, pp, Tp;
+  pert_prim(c, U[id], U[id + P], U[id + 2 * P], U[id + 3 * P], u, v, pp, Tp);
+  q[0] = pp;
+  q[1] = u;
+  q[2] = v;
+  q[3] = Tp;
+}
+
+__device__ __forceinline__ void wall_bc(const PertConsts &c, const RStencil32 &s, const float qp[4], const float *wm,
+                                        float q[4]) {
+  // wm = (Vx, Vy, Ax, Ay) at the stage time
+  const float rho_p = 1.f + (qp[0] - c.R * qp[3]) / (c.R * (1.f + qp[3]));
+  const float g = -rho_p * (s.nx * wm[2] + s.ny * wm[3]);
+  q[0] = qp[0] - s.dxi * g;
+  q[1] = wm[0] + (qp[1] - wm[0]) * s.ratio;
+  q[2] = wm[1] + (qp[2] - wm[1]) * s.ratio;
+  q[3] = qp[3];
+}
+
+__device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts &c, const float *U,
+                                        const RStencil32 &s, const float *wm, float q[4]) {
+  float qp[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int b = 0; b < 4; b++) {
+    if (!(s.mask >> b & 1)) continue;
+    float cq[4];
+    raw_prim(c, U, s.corner + (b & 1) + (b >> 1) * k.pitch, k.plane, cq);
+    for (int v = 0; v < 4; v++) qp[v] += s.w[b] * cq[v];
+  }
+  wall_bc(c, s, qp, wm, q);
+}
+
+__device__ __noinline__ void rebuild_ghost(const Consts &k, const PertConsts &c, const float *U,
+                                           const uint8_t *__restrict__ tag, const int *__restrict__ sid,
+                                           const RStencil32 *__restrict__ rs, const RStencil32 &s, const float *wm,
+                                           float q[4]) {
+  float qp[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int b = 0; b < 4; b++) {
+    if (!(s.mask >> b & 1)) continue;
+    float cq[4];
+    const int cn = s.ccell + (b & 1) + (b >> 1) * k.nx;
+    const int e2 = tag[cn] == IB ? sid[cn] : -1;
+    if (e2 >= 0 && rs[e2].mask) rebuild_ib(k, c, U, rs[e2], wm, cq);
+    else raw_prim(c, U, s.corner + (b & 1) + (b >> 1) * k.pitch, k.plane, cq);
+    for (int v = 0; v < 4; v++) qp[v] += s.w[b] * cq[v];
+  }
+  wall_bc(c, s, qp, wm, q);
+}
+
+// ---------------------------------------------------------------------------
+// Fused residual + stage update in FP32 perturbation form.  One 16x16 tile
+// per block.  (1) Load tile + 3-cell halo: domain halos by index mapping, IB
+// and ghost nodes rebuilt on the fly, conversion to (rho', u, v, p', T') in
+// shared memory.  (2) WENO5 per cell and direction: the three smoothness
+// indicators of a cell's five-point window serve both the left state of its
+// right face and the right state of its left face.  (3) LDFSS + central
+// viscous flux per face.  (4) Flux divergence and SSP-RK3 stage update;
+// stage 3 accumulates U^{n+1} in FP64.
+// ---------------------------------------------------------------------------
 template <int STAGE>
 __global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, float *Mn, const float *__restrict__ In,
                                                    float *Out, double *D, const uint8_t *__restrict__ tag,
-                                                   DevState *ds) {
+                                                   const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
+                                                   DevState *ds, bool fuse_cfl) {
   __shared__ float sq[4][HY][HX];  // rho', u, v, p'
   __shared__ float sT[HY][HX];     // T'
-  __shared__ float sfx[4][TY][TX + 1];
-  __shared__ float sfy[4][TY + 1][TX];
+  __shared__ float fLx[4][TY][TX + 1], fRx[4][TY][TX + 1];  // x-face states; fLx then holds the x flux
+  __shared__ float fLy[4][TY + 1][TX], fRy[4][TY + 1][TX];  // y-face states; fLy then holds the y flux
+  __shared__ float wm[4];
+  __shared__ float lred[8];
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int ci = i0 + tx, cj = j0 + ty;
   const bool inside = ci < k.nx && cj < k.ny;
-  const bool fluid = inside && tag[cj * k.nx + ci] == FLUID;
+  const uint8_t mytag = inside ? tag[cj * k.nx + ci] : (uint8_t)SOLID;
+  const bool fluid = mytag == FLUID;
+  // every block reads dt before any block can finish the fused CFL reduction
   const double dtd = ds->dt;
+  const float dt = ds->dtf;
   if (STAGE == 3 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-    // end of the step (no other kernel of this stage reads t)
-    ds->t = ds->t + dtd;
+    ds->t = ds->t + dtd;  // end of the step (no other kernel of this stage reads t)
     ds->steps += 1;
   }
-  if (!__syncthreads_or(fluid)) return;
+  // stages 1 and 3 also keep the IB / ghost nodes of U^n current; stage 2 only needs fluid cells
+  const bool work = STAGE == 2 ? fluid : (mytag != SOLID);
+  if (!__syncthreads_or(work)) {
+    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    double X[2], V[2], Acc[2];
+    motion_at(k.motion, stage_time(ds, STAGE), X, V, Acc);
+    wm[0] = (float)V[0];
+    wm[1] = (float)V[1];
+    wm[2] = (float)Acc[0];
+    wm[3] = (float)Acc[1];
+  }
+  __syncthreads();
 
   const long long P = k.plane;
   for (int m = threadIdx.x; m < HX * HY; m += 256) {
     const int a = m % HX, b = m / HX;
     int gi = i0 - NG + a, gj = j0 - NG + b;
-    float dr = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;  // free stream: zero perturbation
+    float q[4] = {0.f, c.ux, c.uy, 0.f};  // (p', u, v, T'); free stream: zero perturbation
+    float dr = 0.f;
     if (halo_map(k, gi, gj)) {
-      const long long id = cidx(k, gi, gj);
-      dr = In[id];
-      d1 = In[id + P];
-      d2 = In[id + 2 * P];
-      d3 = In[id + 3 * P];
+      const int n = gj * k.nx + gi;
+      const uint8_t t = tag[n];
+      const int e = (t == FLUID || t == SOLID) ? -1 : sid[n];
+      if (e >= 0 && rs[e].mask) {
+        const RStencil32 s = rs[e];
+        if (t == IB) rebuild_ib(k, c, In, s, wm, q);
+        else rebuild_ghost(k, c, In, tag, sid, rs, s, wm, q);
+        dr = (q[0] - c.R * q[3]) / (c.R * (1.f + q[3]));
+        const bool own = a >= NG && a < NG + TX && b >= NG && b < NG + TY;
+        if (own && STAGE == 1) {  // U^n on this node for output and for a node that turns fluid
+          float d0, d1, d2, d3;
+          prim_pert(c, q[0], q[1], q[2], q[3], d0, d1, d2, d3);
+          D[s.cell] = d0;
+          D[s.cell + P] = d1;
+          D[s.cell + 2 * P] = d2;
+          D[s.cell + 3 * P] = d3;
+        }
+      } else {
+        const long long id = cidx(k, gi, gj);
+        dr = In[id];
+        raw_prim(c, In, id, P, q);
+      }
     }
-    float u, v, pp, Tp;
-    pert_prim(c, dr, d1, d2, d3, u, v, pp, Tp);
     sq[0][b][a] = dr;
-    sq[1][b][a] = u;
-    sq[2][b][a] = v;
-    sq[3][b][a] = pp;
-    sT[b][a] = Tp;
+    sq[1][b][a] = q[1];
+    sq[2][b][a] = q[2];
+    sq[3][b][a] = q[0];
+    sT[b][a] = q[3];
+  }
+  __syncthreads();
+
+  // WENO5 per cell: x windows for local columns 2..TX+3 of interior rows,
+  // y windows for local rows 2..TY+3 of interior columns
+  constexpr int NXW = (TX + 2) * TY, NYW = TX * (TY + 2);
+  for (int m = threadIdx.x; m < NXW + NYW; m += 256) {
+    const bool xdir = m < NXW;
+    const int mm = xdir ? m : m - NXW;
+    int ccol, crow;
+    if (xdir) {
+      ccol = 2 + mm % (TX + 2);
+      crow = NG + mm / (TX + 2);
+    } else {
+      ccol = NG + mm % TX;
+      crow = 2 + mm / TX;
+    }
+    for (int v = 0; v < 4; v++) {
+      float f0, f1, f2, f3, f4;
+      if (xdir) {
+        const float *s = &sq[v][crow][ccol - 2];
+        f0 = s[0]; f1 = s[1]; f2 = s[2]; f3 = s[3]; f4 = s[4];
+      } else {
+        f0 = sq[v][crow - 2][ccol]; f1 = sq[v][crow - 1][ccol]; f2 = sq[v][crow][ccol];
+        f3 = sq[v][crow + 1][ccol]; f4 = sq[v][crow + 2][ccol];
+      }
+      const float eps = 1e-6f;
+      float aa = f0 - 2.f * f1 + f2, bb = f0 - 4.f * f1 + 3.f * f2;
+      const float b0 = (13.f / 12.f) * aa * aa + 0.25f * bb * bb;
+      aa = f1 - 2.f * f2 + f3;
+      bb = f1 - f3;
+      const float b1 = (13.f / 12.f) * aa * aa + 0.25f * bb * bb;
+      aa = f2 - 2.f * f3 + f4;
+      bb = 3.f * f2 - 4.f * f3 + f4;
+      const float b2 = (13.f / 12.f) * aa * aa + 0.25f * bb * bb;
+      const float e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+      const float e01 = e0 * e1, e12 = e1 * e2, e02 = e0 * e2;
+      const float s01 = e01 * e01, s12 = e12 * e12, s02 = e02 * e02;
+      // left state at the cell's right face: weights (0.1, 0.6, 0.3) / e_k^2
+      const float l0 = 2.f * f0 - 7.f * f1 + 11.f * f2;
+      const float l1 = -f1 + 5.f * f2 + 2.f * f3;
+      const float l2 = 2.f * f2 + 5.f * f3 - f4;
+      const float la0 = 0.1f * s12, la1 = 0.6f * s02, la2 = 0.3f * s01;
+      const float qL = __fdividef(la0 * l0 + la1 * l1 + la2 * l2, 6.f * (la0 + la1 + la2));
+      // right state at the cell's left face: mirrored window, indicators reversed
+      const float r0 = 2.f * f4 - 7.f * f3 + 11.f * f2;
+      const float r1 = -f3 + 5.f * f2 + 2.f * f1;
+      const float r2 = 2.f * f2 + 5.f * f1 - f0;
+      const float ra0 = 0.1f * s01, ra1 = 0.6f * s02, ra2 = 0.3f * s12;
+      const float qR = __fdividef(ra0 * r0 + ra1 * r1 + ra2 * r2, 6.f * (ra0 + ra1 + ra2));
+      if (xdir) {
+        const int row = crow - NG;
+        if (ccol - 2 <= TX) fLx[v][row][ccol - 2] = qL;  // face between ccol and ccol+1
+        if (ccol >= 3) fRx[v][row][ccol - 3] = qR;        // face between ccol-1 and ccol
+      } else {
+        const int col = ccol - NG;
+        if (crow - 2 <= TY) fLy[v][crow - 2][col] = qL;
+        if (crow >= 3) fRy[v][crow - 3][col] = qR;
+      }
+    }
   }
   __syncthreads();
 
   const float mu = c.mu, kap = c.kappa, idx = c.idx, idy = c.idy;
-  for (int m = threadIdx.x; m < (TX + 1) * TY; m += 256) {
-    const int f = m % (TX + 1), row = m / (TX + 1);
-    const int b = row + NG;
-    float qL[4], qR[4];
-    for (int v = 0; v < 4; v++) {
-      const float *s = &sq[v][b][f];
-      qL[v] = weno5f(s[0], s[1], s[2], s[3], s[4]);
-      qR[v] = weno5f(s[5], s[4], s[3], s[2], s[1]);
-    }
-    if (!(qL[0] > -1.f) || !(qL[3] > -c.R) || !(qR[0] > -1.f) || !(qR[3] > -c.R)) {
+  for (int m = threadIdx.x; m < (TX + 1) * TY + TX * (TY + 1); m += 256) {
+    const bool xdir = m < (TX + 1) * TY;
+    float qL[4], qR[4], F[4];
+    if (xdir) {
+      const int f = m % (TX + 1), row = m / (TX + 1);
+      const int b = row + NG, a = f + 2, a1 = f + 3;
       for (int v = 0; v < 4; v++) {
-        qL[v] = sq[v][b][f + 2];
-        qR[v] = sq[v][b][f + 3];
+        qL[v] = fLx[v][row][f];
+        qR[v] = fRx[v][row][f];
       }
-    }
-    float F[4];
-    ldfss_pert(c, qL[0], qL[1], qL[2], qL[3], qR[0], qR[1], qR[2], qR[3], c.ux, c.uy, F);
-    const int a = f + 2, a1 = f + 3;
-    const float ux = (sq[1][b][a1] - sq[1][b][a]) * idx;
-    const float vx = (sq[2][b][a1] - sq[2][b][a]) * idx;
-    const float Tx = (sT[b][a1] - sT[b][a]) * idx;
-    const float uy = (sq[1][b + 1][a] - sq[1][b - 1][a] + sq[1][b + 1][a1] - sq[1][b - 1][a1]) * (0.25f * idy);
-    const float vy = (sq[2][b + 1][a] - sq[2][b - 1][a] + sq[2][b + 1][a1] - sq[2][b - 1][a1]) * (0.25f * idy);
-    const float txx = mu * ((4.f / 3.f) * ux - (2.f / 3.f) * vy);
-    const float txy = mu * (uy + vx);
-    const float uf = 0.5f * (sq[1][b][a] + sq[1][b][a1]), vf = 0.5f * (sq[2][b][a] + sq[2][b][a1]);
-    sfx[0][row][f] = F[0];
-    sfx[1][row][f] = F[1] - txx;
-    sfx[2][row][f] = F[2] - txy;
-    sfx[3][row][f] = F[3] - (uf * txx + vf * txy + kap * Tx);
-  }
-  for (int m = threadIdx.x; m < TX * (TY + 1); m += 256) {
-    const int col = m % TX, f = m / TX;
-    const int a = col + NG;
-    float qL[4], qR[4];
-    for (int v = 0; v < 4; v++) {
-      const float s0 = sq[v][f][a], s1 = sq[v][f + 1][a], s2 = sq[v][f + 2][a];
-      const float s3 = sq[v][f + 3][a], s4 = sq[v][f + 4][a], s5 = sq[v][f + 5][a];
-      qL[v] = weno5f(s0, s1, s2, s3, s4);
-      qR[v] = weno5f(s5, s4, s3, s2, s1);
-    }
-    if (!(qL[0] > -1.f) || !(qL[3] > -c.R) || !(qR[0] > -1.f) || !(qR[3] > -c.R)) {
+      if (!(qL[0] > -1.f) || !(qL[3] > -c.R) || !(qR[0] > -1.f) || !(qR[3] > -c.R)) {
+        for (int v = 0; v < 4; v++) {
+          qL[v] = sq[v][b][a];
+          qR[v] = sq[v][b][a1];
+        }
+      }
+      ldfss_pert(c, qL[0], qL[1], qL[2], qL[3], qR[0], qR[1], qR[2], qR[3], c.ux, c.uy, F);
+      const float ux = (sq[1][b][a1] - sq[1][b][a]) * idx;
+      const float vx = (sq[2][b][a1] - sq[2][b][a]) * idx;
+      const float Tx = (sT[b][a1] - sT[b][a]) * idx;
+      const float uy = (sq[1][b + 1][a] - sq[1][b - 1][a] + sq[1][b + 1][a1] - sq[1][b - 1][a1]) * (0.25f * idy);
+      const float vy = (sq[2][b + 1][a] - sq[2][b - 1][a] + sq[2][b + 1][a1] - sq[2][b - 1][a1]) * (0.25f * idy);
+      const float txx = mu * ((4.f / 3.f) * ux - (2.f / 3.f) * vy);
+      const float txy = mu * (uy + vx);
+      const float uf = 0.5f * (sq[1][b][a] + sq[1][b][a1]), vf = 0.5f * (sq[2][b][a] + sq[2][b][a1]);
+      fLx[0][row][f] = F[0];
+      fLx[1][row][f] = F[1] - txx;
+      fLx[2][row][f] = F[2] - txy;
+      fLx[3][row][f] = F[3] - (uf * txx + vf * txy + kap * Tx);
+    } else {
+      const int mm = m - (TX + 1) * TY;
+      const int col = mm % TX, f = mm / TX;
+      const int a = col + NG, b = f + 2, b1 = f + 3;
       for (int v = 0; v < 4; v++) {
-        qL[v] = sq[v][f + 2][a];
-        qR[v] = sq[v][f + 3][a];
+        qL[v] = fLy[v][f][col];
+        qR[v] = fRy[v][f][col];
       }
+      if (!(qL[0] > -1.f) || !(qL[3] > -c.R) || !(qR[0] > -1.f) || !(qR[3] > -c.R)) {
+        for (int v = 0; v < 4; v++) {
+          qL[v] = sq[v][b][a];
+          qR[v] = sq[v][b1][a];
+        }
+      }
+      ldfss_pert(c, qL[0], qL[2], qL[1], qL[3], qR[0], qR[2], qR[1], qR[3], c.uy, c.ux, F);
+      const float uy = (sq[1][b1][a] - sq[1][b][a]) * idy;
+      const float vy = (sq[2][b1][a] - sq[2][b][a]) * idy;
+      const float Ty = (sT[b1][a] - sT[b][a]) * idy;
+      const float ux = (sq[1][b][a + 1] - sq[1][b][a - 1] + sq[1][b1][a + 1] - sq[1][b1][a - 1]) * (0.25f * idx);
+      const float vx = (sq[2][b][a + 1] - sq[2][b][a - 1] + sq[2][b1][a + 1] - sq[2][b1][a - 1]) * (0.25f * idx);
+      const float tyy = mu * ((4.f / 3.f) * vy - (2.f / 3.f) * ux);
+      const float txy = mu * (uy + vx);
+      const float uf = 0.5f * (sq[1][b][a] + sq[1][b1][a]), vf = 0.5f * (sq[2][b][a] + sq[2][b1][a]);
+      fLy[0][f][col] = F[0];
+      fLy[1][f][col] = F[2] - txy;
+      fLy[2][f][col] = F[1] - tyy;
+      fLy[3][f][col] = F[3] - (uf * txy + vf * tyy + kap * Ty);
     }
-    float F[4];
-    ldfss_pert(c, qL[0], qL[2], qL[1], qL[3], qR[0], qR[2], qR[1], qR[3], c.uy, c.ux, F);
-    const int b = f + 2, b1 = f + 3;
-    const float uy = (sq[1][b1][a] - sq[1][b][a]) * idy;
-    const float vy = (sq[2][b1][a] - sq[2][b][a]) * idy;
-    const float Ty = (sT[b1][a] - sT[b][a]) * idy;
-    const float ux = (sq[1][b][a + 1] - sq[1][b][a - 1] + sq[1][b1][a + 1] - sq[1][b1][a - 1]) * (0.25f * idx);
-    const float vx = (sq[2][b][a + 1] - sq[2][b][a - 1] + sq[2][b1][a + 1] - sq[2][b1][a - 1]) * (0.25f * idx);
-    const float tyy = mu * ((4.f / 3.f) * vy - (2.f / 3.f) * ux);
-    const float txy = mu * (uy + vx);
-    const float uf = 0.5f * (sq[1][b][a] + sq[1][b1][a]), vf = 0.5f * (sq[2][b][a] + sq[2][b1][a]);
-    sfy[0][f][col] = F[0];
-    sfy[1][f][col] = F[2] - txy;
-    sfy[2][f][col] = F[1] - tyy;
-    sfy[3][f][col] = F[3] - (uf * txy + vf * tyy + kap * Ty);
   }
   __syncthreads();
-  if (!fluid) return;
-  const float dt = ds->dtf;
+
+  float lam = 0.f;
   const long long id = cidx(k, ci, cj);
-  float L[4];
-  for (int v = 0; v < 4; v++)
-    L[v] = -((sfx[v][ty][tx + 1] - sfx[v][ty][tx]) * idx + (sfy[v][ty + 1][tx] - sfy[v][ty][tx]) * idy);
-  if (STAGE == 1) {
-    for (int v = 0; v < 4; v++) Out[id + v * P] = Mn[id + v * P] + dt * L[v];
-  } else if (STAGE == 2) {
-    for (int v = 0; v < 4; v++) Out[id + v * P] = 0.75f * Mn[id + v * P] + 0.25f * (In[id + v * P] + dt * L[v]);
-  } else {
-    // FP64 accumulation: dU^{n+1} = dU^n + (double)[2/3 ((dU^(2) - dU^n) + dt L)]
-    for (int v = 0; v < 4; v++) {
-      const long long o = id + v * P;
-      const float inc = (2.f / 3.f) * ((In[o] - Mn[o]) + dt * L[v]);
-      const double dn = D[o] + (double)inc;
-      D[o] = dn;
-      Mn[o] = (float)dn;
+  if (fluid) {
+    float L[4];
+    for (int v = 0; v < 4; v++)
+      L[v] = -((fLx[v][ty][tx + 1] - fLx[v][ty][tx]) * idx + (fLy[v][ty + 1][tx] - fLy[v][ty][tx]) * idy);
+    if (STAGE == 1) {
+      for (int v = 0; v < 4; v++) Out[id + v * P] = Mn[id + v * P] + dt * L[v];
+    } else if (STAGE == 2) {
+      for (int v = 0; v < 4; v++) Out[id + v * P] = 0.75f * Mn[id + v * P] + 0.25f * (In[id + v * P] + dt * L[v]);
+    } else {
+      // FP64 accumulation: dU^{n+1} = dU^n + (double)[2/3 ((dU^(2) - dU^n) + dt L)]
+      float mnew[4];
+      for (int v = 0; v < 4; v++) {
+        const long long o = id + v * P;
+        const float inc = (2.f / 3.f) * ((In[o] - Mn[o]) + dt * L[v]);
+        const double dn = D[o] + (double)inc;
+        D[o] = dn;
+        mnew[v] = (float)dn;
+        Mn[o] = mnew[v];
+      }
+      if (fuse_cfl) lam = cfl_lambda(k, c, mnew);
     }
+  } else if (STAGE == 3 && inside && mytag != SOLID) {
+    // IB / ghost node: the mirror of U^{n+1} takes the value rebuilt at stage 1
+    for (int v = 0; v < 4; v++) Mn[id + v * P] = (float)D[id + v * P];
   }
+  // one call site for the whole block (the reduction has a barrier)
+  if (STAGE == 3 && fuse_cfl) cfl_block_max(k, lam, lred, ds);
 }
 
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
-                      const uint8_t *tag, DevState *ds, cudaStream_t s) {
+                      const uint8_t *tag, const int *sid, const RStencil32 *rs, DevState *ds, bool fuse_cfl,
+                      cudaStream_t s) {
   PertConsts c = pert_consts(k);
   dim3 grid((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY);
-  if (stage == 1) k_stage_f32<1><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, ds);
-  else if (stage == 2) k_stage_f32<2><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, ds);
-  else k_stage_f32<3><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, ds);
+  if (stage == 1) k_stage_f32<1><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, ds, false);
+  else if (stage == 2) k_stage_f32<2><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, ds, false);
+  else k_stage_f32<3><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, ds, fuse_cfl);
 }
 
 }  // namespace ibm

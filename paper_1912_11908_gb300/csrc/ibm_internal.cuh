@@ -154,15 +154,33 @@ void launch_recon_f64(const Consts &k, double *U, const ibm_stencil *st, int cap
 void launch_stage_f64(const Consts &k, int stage, const double *Un, const double *In, double *Out,
                       const uint8_t *tag, DevState *ds, cudaStream_t s);
 
+// Compact FP32 form of an IB / ghost stencil for the FP32-bulk reconstruction
+// (built once per classification from the FP64 record).
+struct RStencil32 {
+  int cell;     // state index of the node
+  int corner;   // state index of corner (i0, j0)
+  int mask;
+  float ratio;  // xi_node / xi_probe
+  float dxi;    // xi_probe - xi_node
+  float nx, ny;
+  int ccell;    // interior index j0*nx + i0 of corner (i0, j0)
+  float w[4];
+};
+
 // FP32-bulk path (flow32.cu).  The FP64 state D of this mode holds the
 // perturbation dU from the free stream (same variables as the FP32 arrays).
 void launch_abs_to_pert64(const Consts &k, double *D, cudaStream_t s);          // in place
 void launch_pert_to_abs64(const Consts &k, const double *D, double *A, cudaStream_t s);
 void launch_to_mirror(const Consts &k, const double *D, float *M, cudaStream_t s);
 void launch_dt_f32(const Consts &k, const float *M, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch);
-void launch_recon_f32(const Consts &k, float *U, double *D, const ibm_stencil *st, int cap, const DevState *ds,
-                      int stage, cudaStream_t s, int *nlaunch);
+void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 *rs, int *sid, int cap,
+                             const DevState *ds, cudaStream_t s);
+// fuse_cfl: stage 3 also reduces the CFL maximum of the new state and sets the
+// next step's dt (static bodies: the fluid set does not change between steps)
+// The stage kernel rebuilds IB and ghost nodes from rs / sid while it loads
+// its tile (no separate reconstruction launch).
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
-                      const uint8_t *tag, DevState *ds, cudaStream_t s);
+                      const uint8_t *tag, const int *sid, const RStencil32 *rs, DevState *ds, bool fuse_cfl,
+                      cudaStream_t s);
 
 }  // namespace ibm

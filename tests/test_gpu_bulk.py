@@ -77,4 +77,21 @@ def test_bulk_set_get_roundtrip(ibm):
     np.testing.assert_allclose(h.state(), a, rtol=1e-15, atol=1e-12)
     g.step(5)
     h.step(5)
-    np.testing.assert_allclose(h.state(), g.state(), rtol=1e-12, atol=1e-9)
+    # the absolute -> perturbation round trip of set_state is exact to FP64 rounding (~1e-16); FP32 stage
+    # arithmetic then amplifies flipped last bits to FP32 level, so the continuation agrees to FP32 precision
+    np.testing.assert_allclose(h.state(), g.state(), rtol=1e-5, atol=1e-6)
+
+
+def test_bulk_moving_body_vs_fp64_oracle(ibm, orc):
+    """Oscillating cylinder with large motion: cells change role every few steps; the FP32-bulk path rebuilds
+    IB / ghost nodes inside the stage kernel and must track the FP64 oracle's forces."""
+    spec = lambda p: dict(W.oscillating_cylinder_m02_re185(128, 64, precision=p), amp=(0.0, 0.6), freq=0.5)
+    g, o = ibm.Case(spec(W.PREC_FP32_BULK)), orc.Case(spec(W.PREC_FP64))
+    for _ in range(4):
+        g.step(25)
+        o.step(25)
+        np.testing.assert_array_equal(g.tags(), o.tags())
+        fg, fo = g.forces(), o.forces()
+        assert abs(fg[0] - fo[0]) <= 1e-3 and abs(fg[1] - fo[1]) <= 1e-3, (fg, fo)
+    err = _compare(g, o)
+    assert max(err.values()) <= 1e-3, err
