@@ -28,6 +28,11 @@ struct ibm_case {
   ibm_stencil *st = nullptr;
   RStencil32 *rst = nullptr;  // FP32-bulk: compact stencils
   int *sid = nullptr;         // FP32-bulk: cell -> stencil index (-1 if none)
+  uint8_t *tile_body = nullptr;  // FP32-bulk: stage tiles that rebuild IB / ghost nodes
+  int *body_tiles = nullptr;
+  int body_cap = 0;
+  cudaStream_t sb = nullptr;     // FP32-bulk: stream of the body-tile kernels (forked from / joined to stream)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int cap = 0;
   bool dt_valid = false;      // FP32-bulk static body: dt of the next step is already in DevState
   DevState *ds = nullptr;
@@ -104,6 +109,25 @@ static int list_capacity(const ibm_geometry *geo, const ibm_grid *gr) {
 
 static size_t pitch_of(int nx) { return (size_t)((nx + 2 * NG + 31) / 32 * 32); }
 
+// Upper bound of stage tiles (16x16) whose cells or 3-cell halo can hold IB /
+// ghost nodes: tiles meeting the body's bounding box grown by 4 cells, for any
+// pose (plus one tile per axis for the offset against the tile grid).
+static int body_tile_capacity(const ibm_geometry *geo, const ibm_grid *gr, int ntiles) {
+  if (!geo || geo->nverts <= 0) return 0;
+  double xmin = geo->verts[0], xmax = xmin, ymin = geo->verts[1], ymax = ymin;
+  for (int v = 1; v < geo->nverts; v++) {
+    xmin = fmin(xmin, geo->verts[2 * v]);
+    xmax = fmax(xmax, geo->verts[2 * v]);
+    ymin = fmin(ymin, geo->verts[2 * v + 1]);
+    ymax = fmax(ymax, geo->verts[2 * v + 1]);
+  }
+  double dx = (gr->hi[0] - gr->lo[0]) / gr->nx, dy = (gr->hi[1] - gr->lo[1]) / gr->ny;
+  long long w = ((long long)ceil((xmax - xmin) / dx) + 8 + 15) / 16 + 2;
+  long long h = ((long long)ceil((ymax - ymin) / dy) + 8 + 15) / 16 + 2;
+  long long c = w * h;
+  return (int)(c < ntiles ? c : ntiles);
+}
+
 static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ibm_flow *fl, const ibm_motion *mo) {
   if (!geo || !gr || !fl) return fail(IBM_EINVAL, "geometry, grid and flow are required");
   if (geo->dim != 2) return fail(IBM_EINVAL, "only dim == 2 bodies are supported");
@@ -140,13 +164,17 @@ extern "C" size_t ibm_case_device_bytes(const ibm_geometry *geo, const ibm_grid 
 static void free_case(ibm_case *c) {
   if (!c) return;
   void *ptrs[] = {c->vref, c->vx, c->vy, c->snx, c->sny, c->vnx, c->vny, c->A, c->B, c->C, c->M, c->F1,
-                  c->F2, c->stage64, c->solid, c->tag, c->blockcounts, c->st, c->rst, c->sid, c->ds};
+                  c->F2, c->stage64, c->solid, c->tag, c->blockcounts, c->st, c->rst, c->sid, c->tile_body,
+                  c->body_tiles, c->ds};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->hds) cudaFreeHost(c->hds);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (int q = 0; q < ibm_case::NEV; q++)
     if (c->ev[q]) cudaEventDestroy(c->ev[q]);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->sb) cudaStreamDestroy(c->sb);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -236,6 +264,9 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
     ALLOC(c->F2, 4 * plane);
     ALLOC(c->rst, (size_t)(c->cap > 0 ? c->cap : 1));
     ALLOC(c->sid, ncell);
+    c->body_cap = body_tile_capacity(geo, gr, stage_tiles(k));
+    ALLOC(c->tile_body, (size_t)stage_tiles(k));
+    ALLOC(c->body_tiles, (size_t)(c->body_cap > 0 ? c->body_cap : 1));
   }
   ALLOC(c->solid, ncell);
   ALLOC(c->tag, ncell);
@@ -244,6 +275,14 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   ALLOC(c->ds, 1);
 #undef ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hds, sizeof(DevState));
+  if (e == cudaSuccess && c->precision == IBM_PREC_FP32_BULK) {
+    // body tiles are on the critical path of every stage: give their stream the highest priority
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    e = cudaStreamCreateWithPriority(&c->sb, cudaStreamNonBlocking, prio_hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     free_case(c);
     cudaGetLastError();
@@ -332,6 +371,10 @@ static ibm_status do_classify(ibm_case *c) {
       nl += 1;
     }
   }
+  if (c->tile_body) {
+    launch_tile_lists(c->k, c->tag, c->tile_body, c->body_tiles, c->body_cap, c->ds, s);
+    nl += 2;
+  }
   prof_mark(c, 4, false);
   c->launches += nl;
   c->classified = true;
@@ -381,8 +424,16 @@ static int enqueue_step(ibm_case *c) {
     // folded into stage 3
     prof_mark(c, 0, true);
     if (f64) launch_stage_f64(c->k, st, c->A, in64[st - 1], out64[st - 1], c->tag, c->ds, s);
-    else launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->ds, fuse_cfl,
-                          s);
+    else {
+      // body tiles run on a forked stream, concurrently with the plain tiles
+      cudaEventRecord(c->ev_fork, s);
+      cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
+      launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->tile_body,
+                       c->body_tiles, c->body_cap, c->ds, fuse_cfl, s, c->sb);
+      cudaEventRecord(c->ev_join, c->sb);
+      cudaStreamWaitEvent(s, c->ev_join, 0);
+      if (c->body_cap > 0) nl += 1;
+    }
     prof_mark(c, 0, false);
     nl += 1;
   }

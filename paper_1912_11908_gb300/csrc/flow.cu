@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_dt(Consts k, const double *__restrict__
     double m = wm[0];
     for (int w = 1; w < 8; w++) m = fmax(m, wm[w]);
     atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong(m));
-    finish_cfl(k, ds);
+    finish_cfl(k, ds, gridDim.x * gridDim.y);
   }
 }
 

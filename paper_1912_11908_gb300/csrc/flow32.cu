@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_dt_f32(Consts k, PertConsts c, const fl
     float m = wm[0];
     for (int w = 1; w < 8; w++) m = fmaxf(m, wm[w]);
     atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong((double)m));
-    finish_cfl(k, ds);
+    finish_cfl(k, ds, gridDim.x * gridDim.y);
   }
 }
 
@@ -154,7 +154,7 @@ __global__ void k_compact_stencils(Consts k, const ibm_stencil *__restrict__ st,
   r.cell = (int)cidx(k, s.cell % k.nx, s.cell / k.nx);
   r.corner = s.mask ? (int)cidx(k, s.i0, s.j0) : 0;
   r.ccell = s.mask ? s.j0 * k.nx + s.i0 : 0;
-  r.mask = s.mask;
+  r.mask = s.mask | (s.kind == 0 ? 16 : 0);  // bit 4: IB node
   r.ratio = (float)(s.xi_node / s.xi_probe);
   r.dxi = (float)(s.xi_probe - s.xi_node);
   r.nx = (float)s.nx;
@@ -234,7 +234,8 @@ __device__ __forceinline__ float cfl_lambda(const Consts &k, const PertConsts &c
 
 // block maximum of lam (all 256 threads call), then the grid-wide maximum and
 // dt through the last-block pattern
-__device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float *red, DevState *ds) {
+__device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float *red, DevState *ds,
+                                              unsigned int nblocks) {
   for (int off = 16; off > 0; off >>= 1) lam = fmaxf(lam, __shfl_xor_sync(0xffffffffu, lam, off));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lam;
   __syncthreads();
@@ -242,7 +243,7 @@ __device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float 
     float m = red[0];
     for (int w = 1; w < 8; w++) m = fmaxf(m, red[w]);
     atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong((double)m));
-    finish_cfl(k, ds);
+    finish_cfl(k, ds, nblocks);
   }
 }
 
@@ -250,9 +251,9 @@ __device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float 
 // IB / ghost reconstruction (Sec. 4.4-4.6, Eq. 4-8; Sec. 5) evaluated while a
 // tile is loaded.  Values are primitives (p', u, v, T').  A ghost node's
 // image point may use IB nodes, which are rebuilt from their own stencils
-// (their corners are fluid), so every rebuilt value depends only on fluid
-// values of the stage input -- the same order as rebuilding all IB nodes
-// first and the ghost nodes after.
+// (their corners are fluid): a body tile rebuilds all IB nodes of its loaded
+// region, then all ghost nodes, reading corners from shared memory and only
+// corners outside the region from the stage input.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void raw_prim(const PertConsts &c, const float *U, long long id, long long P,
                                          float q[4]) {
@@ -279,26 +280,9 @@ __device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts &c, co
                                         const RStencil32 &s, const float *wm, float q[4]) {
   float qp[4] = {0.f, 0.f, 0.f, 0.f};
   for (int b = 0; b < 4; b++) {
-    if (!(s.mask >> b & 1)) continue;
+    if (!(s.mask >> b & 1)) continue;  // bits 0-3: valid corners (bit 4: IB node)
     float cq[4];
     raw_prim(c, U, s.corner + (b & 1) + (b >> 1) * k.pitch, k.plane, cq);
-    for (int v = 0; v < 4; v++) qp[v] += s.w[b] * cq[v];
-  }
-  wall_bc(c, s, qp, wm, q);
-}
-
-__device__ __noinline__ void rebuild_ghost(const Consts &k, const PertConsts &c, const float *U,
-                                           const uint8_t *__restrict__ tag, const int *__restrict__ sid,
-                                           const RStencil32 *__restrict__ rs, const RStencil32 &s, const float *wm,
-                                           float q[4]) {
-  float qp[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int b = 0; b < 4; b++) {
-    if (!(s.mask >> b & 1)) continue;
-    float cq[4];
-    const int cn = s.ccell + (b & 1) + (b >> 1) * k.nx;
-    const int e2 = tag[cn] == IB ? sid[cn] : -1;
-    if (e2 >= 0 && rs[e2].mask) rebuild_ib(k, c, U, rs[e2], wm, cq);
-    else raw_prim(c, U, s.corner + (b & 1) + (b >> 1) * k.pitch, k.plane, cq);
     for (int v = 0; v < 4; v++) qp[v] += s.w[b] * cq[v];
   }
   wall_bc(c, s, qp, wm, q);
@@ -314,39 +298,57 @@ __device__ __noinline__ void rebuild_ghost(const Consts &k, const PertConsts &c,
 // viscous flux per face.  (4) Flux divergence and SSP-RK3 stage update;
 // stage 3 accumulates U^{n+1} in FP64.
 // ---------------------------------------------------------------------------
-template <int STAGE>
+template <int STAGE, bool BODY>
 __global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, float *Mn, const float *__restrict__ In,
                                                    float *Out, double *D, const uint8_t *__restrict__ tag,
                                                    const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
-                                                   DevState *ds, bool fuse_cfl) {
+                                                   const uint8_t *__restrict__ tile_body,
+                                                   const int *__restrict__ body_tiles, DevState *ds, bool fuse_cfl,
+                                                   unsigned int ncfl) {
   __shared__ float sq[4][HY][HX];  // rho', u, v, p'
   __shared__ float sT[HY][HX];     // T'
   __shared__ float fLx[4][TY][TX + 1], fRx[4][TY][TX + 1];  // x-face states; fLx then holds the x flux
   __shared__ float fLy[4][TY + 1][TX], fRy[4][TY + 1][TX];  // y-face states; fLy then holds the y flux
   __shared__ float wm[4];
   __shared__ float lred[8];
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int ntx = (k.nx + TX - 1) / TX;
+  // every block reads dt before any block can finish the fused CFL reduction
+  const double dtd = ds->dt;
+  const float dt = ds->dtf;
+  int tile;
+  if (BODY) {
+    tile = (int)blockIdx.x < ds->nbody_tiles ? body_tiles[blockIdx.x] : -1;
+  } else {
+    tile = tile_body[blockIdx.x] ? -1 : (int)blockIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (STAGE == 1) {  // stage times for the body kernels of stages 2 and 3
+        ds->tst[0] = ds->t + dtd;
+        ds->tst[1] = ds->t + 0.5 * dtd;
+      } else if (STAGE == 3) {  // end of the step; the body kernel of stage 3 reads tst, not t
+        ds->t = ds->t + dtd;
+        ds->steps += 1;
+      }
+    }
+  }
+  if (tile < 0) {
+    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds, ncfl);
+    return;
+  }
+  const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int ci = i0 + tx, cj = j0 + ty;
   const bool inside = ci < k.nx && cj < k.ny;
   const uint8_t mytag = inside ? tag[cj * k.nx + ci] : (uint8_t)SOLID;
   const bool fluid = mytag == FLUID;
-  // every block reads dt before any block can finish the fused CFL reduction
-  const double dtd = ds->dt;
-  const float dt = ds->dtf;
-  if (STAGE == 3 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-    ds->t = ds->t + dtd;  // end of the step (no other kernel of this stage reads t)
-    ds->steps += 1;
-  }
   // stages 1 and 3 also keep the IB / ghost nodes of U^n current; stage 2 only needs fluid cells
   const bool work = STAGE == 2 ? fluid : (mytag != SOLID);
   if (!__syncthreads_or(work)) {
-    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds);
+    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds, ncfl);
     return;
   }
-  if (threadIdx.x == 0) {
+  if (BODY && threadIdx.x == 0) {
     double X[2], V[2], Acc[2];
-    motion_at(k.motion, stage_time(ds, STAGE), X, V, Acc);
+    motion_at(k.motion, STAGE == 1 ? ds->t : ds->tst[STAGE - 2], X, V, Acc);
     wm[0] = (float)V[0];
     wm[1] = (float)V[1];
     wm[2] = (float)Acc[0];
@@ -355,33 +357,31 @@ __global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, float
   __syncthreads();
 
   const long long P = k.plane;
+  // body tiles: every IB / ghost node of the loaded region, with its stencil staged in shared memory
+  constexpr int RB_MAX = 192;
+  __shared__ int s_nrb;
+  __shared__ int s_rbm[BODY ? RB_MAX : 1];
+  __shared__ int s_rbe[BODY ? RB_MAX : 1];
+  __shared__ RStencil32 s_rs[BODY ? RB_MAX : 1];
+  if (BODY && threadIdx.x == 0) s_nrb = 0;
+  if (BODY) __syncthreads();
   for (int m = threadIdx.x; m < HX * HY; m += 256) {
     const int a = m % HX, b = m / HX;
     int gi = i0 - NG + a, gj = j0 - NG + b;
     float q[4] = {0.f, c.ux, c.uy, 0.f};  // (p', u, v, T'); free stream: zero perturbation
     float dr = 0.f;
     if (halo_map(k, gi, gj)) {
-      const int n = gj * k.nx + gi;
-      const uint8_t t = tag[n];
-      const int e = (t == FLUID || t == SOLID) ? -1 : sid[n];
-      if (e >= 0 && rs[e].mask) {
-        const RStencil32 s = rs[e];
-        if (t == IB) rebuild_ib(k, c, In, s, wm, q);
-        else rebuild_ghost(k, c, In, tag, sid, rs, s, wm, q);
-        dr = (q[0] - c.R * q[3]) / (c.R * (1.f + q[3]));
-        const bool own = a >= NG && a < NG + TX && b >= NG && b < NG + TY;
-        if (own && STAGE == 1) {  // U^n on this node for output and for a node that turns fluid
-          float d0, d1, d2, d3;
-          prim_pert(c, q[0], q[1], q[2], q[3], d0, d1, d2, d3);
-          D[s.cell] = d0;
-          D[s.cell + P] = d1;
-          D[s.cell + 2 * P] = d2;
-          D[s.cell + 3 * P] = d3;
+      const long long id = cidx(k, gi, gj);
+      int e = -1;
+      if (BODY) e = sid[gj * k.nx + gi];
+      dr = In[id];
+      raw_prim(c, In, id, P, q);
+      if (BODY && e >= 0) {
+        const int slot = atomicAdd(&s_nrb, 1);
+        if (slot < RB_MAX) {
+          s_rbm[slot] = m;
+          s_rbe[slot] = e;
         }
-      } else {
-        const long long id = cidx(k, gi, gj);
-        dr = In[id];
-        raw_prim(c, In, id, P, q);
       }
     }
     sq[0][b][a] = dr;
@@ -391,7 +391,58 @@ __global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, float
     sT[b][a] = q[3];
   }
   __syncthreads();
-
+  if (BODY) {
+    const int nrb = min(s_nrb, RB_MAX);
+    for (int r = threadIdx.x; r < nrb; r += 256) s_rs[r] = rs[s_rbe[r]];
+    __syncthreads();
+    // rebuild the listed nodes in place: IB nodes, barrier, ghost nodes (whose image points may use IB
+    // nodes); corners inside the loaded region come from shared memory
+    for (int pass = 0; pass < 2; pass++) {
+      for (int r = threadIdx.x; r < nrb; r += 256) {
+        const RStencil32 &st = s_rs[r];
+        const bool is_ib = (st.mask & 16) != 0;
+        if (is_ib != (pass == 0) || !(st.mask & 15)) continue;
+        const int m = s_rbm[r], a = m % HX, b = m / HX;
+        float qp[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int cq = 0; cq < 4; cq++) {
+          if (!(st.mask >> cq & 1)) continue;
+          const int cn = st.ccell + (cq & 1) + (cq >> 1) * k.nx;
+          const int la = cn % k.nx - (i0 - NG), lb = cn / k.nx - (j0 - NG);
+          float v4[4];
+          if (la >= 0 && la < HX && lb >= 0 && lb < HY) {
+            v4[0] = sq[3][lb][la];
+            v4[1] = sq[1][lb][la];
+            v4[2] = sq[2][lb][la];
+            v4[3] = sT[lb][la];
+          } else {
+            // corner outside the loaded region: fluid value, or an IB node rebuilt from its own stencil
+            const int e2 = pass == 1 ? sid[cn] : -1;
+            if (e2 >= 0 && (rs[e2].mask & 15)) rebuild_ib(k, c, In, rs[e2], wm, v4);
+            else raw_prim(c, In, st.corner + (cq & 1) + (cq >> 1) * k.pitch, P, v4);
+          }
+          for (int v = 0; v < 4; v++) qp[v] += st.w[cq] * v4[v];
+        }
+        float q[4];
+        wall_bc(c, st, qp, wm, q);
+        sq[0][b][a] = (q[0] - c.R * q[3]) / (c.R * (1.f + q[3]));
+        sq[1][b][a] = q[1];
+        sq[2][b][a] = q[2];
+        sq[3][b][a] = q[0];
+        sT[b][a] = q[3];
+        const bool own = a >= NG && a < NG + TX && b >= NG && b < NG + TY;
+        if (own && STAGE == 1) {  // U^n on this node for output and for a node that turns fluid
+          float d0, d1, d2, d3;
+          prim_pert(c, q[0], q[1], q[2], q[3], d0, d1, d2, d3);
+          D[st.cell] = d0;
+          D[st.cell + P] = d1;
+          D[st.cell + 2 * P] = d2;
+          D[st.cell + 3 * P] = d3;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0 && s_nrb > RB_MAX) atomicOr(&ds->err, ERR_CAPACITY);
+  }
   // WENO5 per cell: x windows for local columns 2..TX+3 of interior rows,
   // y windows for local rows 2..TY+3 of interior columns
   constexpr int NXW = (TX + 2) * TY, NYW = TX * (TY + 2);
@@ -536,22 +587,89 @@ __global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, float
       }
       if (fuse_cfl) lam = cfl_lambda(k, c, mnew);
     }
-  } else if (STAGE == 3 && inside && mytag != SOLID) {
+  } else if (BODY && STAGE == 3 && inside && mytag != SOLID) {
     // IB / ghost node: the mirror of U^{n+1} takes the value rebuilt at stage 1
     for (int v = 0; v < 4; v++) Mn[id + v * P] = (float)D[id + v * P];
   }
   // one call site for the whole block (the reduction has a barrier)
-  if (STAGE == 3 && fuse_cfl) cfl_block_max(k, lam, lred, ds);
+  if (STAGE == 3 && fuse_cfl) cfl_block_max(k, lam, lred, ds, ncfl);
+}
+
+int stage_tiles(const Consts &k) { return ((k.nx + TX - 1) / TX) * ((k.ny + TY - 1) / TY); }
+
+// flag every stage tile whose cells or 3-cell halo (after domain mapping) hold
+// an IB or ghost node; one warp per tile
+__global__ void k_tile_flags(Consts k, const uint8_t *__restrict__ tag, uint8_t *__restrict__ tile_body) {
+  const int ntx = (k.nx + TX - 1) / TX, nt = ntx * ((k.ny + TY - 1) / TY);
+  const int tile = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (tile >= nt) return;
+  const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
+  bool hit = false;
+  for (int m = lane; m < HX * HY; m += 32) {
+    int gi = i0 - NG + m % HX, gj = j0 - NG + m / HX;
+    if (!halo_map(k, gi, gj)) continue;
+    const uint8_t t = tag[gj * k.nx + gi];
+    hit |= (t == IB || t >= G1);
+  }
+  hit = __any_sync(0xffffffffu, hit);
+  if (lane == 0) tile_body[tile] = hit ? 1 : 0;
+}
+
+// compact the flagged tiles (ascending) into body_tiles; one block
+__global__ void __launch_bounds__(1024) k_tile_list(int nt, const uint8_t *__restrict__ tile_body,
+                                                    int *__restrict__ body_tiles, int body_cap, DevState *ds) {
+  __shared__ int part[1024];
+  const int per = (nt + 1023) / 1024;
+  const int t0 = threadIdx.x * per, t1 = min(nt, t0 + per);
+  int cnt = 0;
+  for (int t = t0; t < t1; t++) cnt += tile_body[t];
+  part[threadIdx.x] = cnt;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int pos = part[threadIdx.x] - cnt;
+  for (int t = t0; t < t1; t++)
+    if (tile_body[t]) {
+      if (pos < body_cap) body_tiles[pos] = t;
+      pos++;
+    }
+  if (threadIdx.x == 1023) {
+    ds->nbody_tiles = min(part[1023], body_cap);
+    if (part[1023] > body_cap) ds->err |= ERR_CAPACITY;
+  }
+}
+
+void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, int *body_tiles, int body_cap,
+                       DevState *ds, cudaStream_t s) {
+  const int nt = stage_tiles(k);
+  k_tile_flags<<<(nt + 7) / 8, 256, 0, s>>>(k, tag, tile_body);
+  k_tile_list<<<1, 1024, 0, s>>>(nt, tile_body, body_tiles, body_cap, ds);
 }
 
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
-                      const uint8_t *tag, const int *sid, const RStencil32 *rs, DevState *ds, bool fuse_cfl,
-                      cudaStream_t s) {
+                      const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
+                      const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
+                      cudaStream_t sb) {
   PertConsts c = pert_consts(k);
-  dim3 grid((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY);
-  if (stage == 1) k_stage_f32<1><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, ds, false);
-  else if (stage == 2) k_stage_f32<2><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, ds, false);
-  else k_stage_f32<3><<<grid, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, ds, fuse_cfl);
+  const int nt = stage_tiles(k);
+  const int nb = body_cap > 0 ? body_cap : 0;
+  const unsigned int ncfl = (unsigned int)(nt + nb);
+#define IBM_STAGE_PAIR(S)                                                                                    \
+  do {                                                                                                       \
+    if (nb) k_stage_f32<S, true><<<nb, 256, 0, sb>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, \
+                                                     ds, fuse_cfl, ncfl);                                    \
+    k_stage_f32<S, false><<<nt, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds,    \
+                                             fuse_cfl, ncfl);                                                \
+  } while (0)
+  if (stage == 1) IBM_STAGE_PAIR(1);
+  else if (stage == 2) IBM_STAGE_PAIR(2);
+  else IBM_STAGE_PAIR(3);
+#undef IBM_STAGE_PAIR
 }
 
 }  // namespace ibm

@@ -19,6 +19,8 @@ struct DevState {
   unsigned long long lmax_bits;  // max spectral radius (bits of a positive double); 0 between reductions
   unsigned int done;             // blocks of the CFL reduction that have finished; 0 between reductions
   float dtf;                     // dt rounded to FP32
+  int nbody_tiles;               // FP32-bulk: tiles that rebuild IB / ghost nodes
+  double tst[2];                 // FP32-bulk: times of stages 2 and 3 (written during stage 1)
   int count[4];                  // #IB, #G1, #G2, #G3
   int offset[5];                 // exclusive prefix of count; offset[4] = total
   int err;                       // bit 0: list capacity exceeded, bit 1: empty stencil
@@ -100,11 +102,11 @@ __device__ __forceinline__ double stage_time(const DevState *ds, int stage) {
 
 // Last block of a CFL reduction: turn the maximum spectral radius into dt and
 // reset the reduction state for the next step.  Call from thread 0 after the
-// block's atomicMax.
-__device__ __forceinline__ void finish_cfl(const Consts &k, DevState *ds) {
+// block's atomicMax; nblocks = blocks taking part (of one or more kernels).
+__device__ __forceinline__ void finish_cfl(const Consts &k, DevState *ds, unsigned int nblocks) {
   __threadfence();
   const unsigned int ticket = atomicAdd(&ds->done, 1u);
-  if (ticket == gridDim.x * gridDim.y - 1) {
+  if (ticket == nblocks - 1) {
     __threadfence();
     const unsigned long long bits = atomicAdd(&ds->lmax_bits, 0ull);
     const double dt = k.cfl / __longlong_as_double((long long)bits);
@@ -159,7 +161,7 @@ void launch_stage_f64(const Consts &k, int stage, const double *Un, const double
 struct RStencil32 {
   int cell;     // state index of the node
   int corner;   // state index of corner (i0, j0)
-  int mask;
+  int mask;     // bits 0-3 valid corners, bit 4 set for an IB node (ghost otherwise)
   float ratio;  // xi_node / xi_probe
   float dxi;    // xi_probe - xi_node
   float nx, ny;
@@ -175,12 +177,20 @@ void launch_to_mirror(const Consts &k, const double *D, float *M, cudaStream_t s
 void launch_dt_f32(const Consts &k, const float *M, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch);
 void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 *rs, int *sid, int cap,
                              const DevState *ds, cudaStream_t s);
+// Tiles of the stage kernel whose cells or 3-cell halo hold IB / ghost nodes
+// ("body tiles"): flag per tile and a compact list (capacity body_cap).
+void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, int *body_tiles, int body_cap,
+                       DevState *ds, cudaStream_t s);
+int stage_tiles(const Consts &k);
 // fuse_cfl: stage 3 also reduces the CFL maximum of the new state and sets the
 // next step's dt (static bodies: the fluid set does not change between steps)
-// The stage kernel rebuilds IB and ghost nodes from rs / sid while it loads
-// its tile (no separate reconstruction launch).
+// Stage kernels: the plain kernel (stream s) covers tiles without IB / ghost
+// nodes near them; the body kernel (stream sb, may run concurrently) covers
+// the listed body tiles and rebuilds IB and ghost nodes from rs / sid while it
+// loads a tile (no separate reconstruction launch).
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
-                      const uint8_t *tag, const int *sid, const RStencil32 *rs, DevState *ds, bool fuse_cfl,
-                      cudaStream_t s);
+                      const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
+                      const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
+                      cudaStream_t sb);
 
 }  // namespace ibm
