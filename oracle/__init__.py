@@ -46,6 +46,8 @@ class _Params(ctypes.Structure):
         ("nv", ctypes.c_int), ("verts", ctypes.POINTER(ctypes.c_double)),
         ("motion", ctypes.c_int), ("amp", ctypes.c_double * 2), ("freq", ctypes.c_double),
         ("vel", ctypes.c_double * 2),
+        ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("dt_phys", ctypes.c_double),
+        ("cfl_tau", ctypes.c_double),
     ]
 
 
@@ -91,6 +93,10 @@ def lib():
         L.orc_weno5.restype = dp
         L.orc_ldfss_xflux.argtypes = [vp, vp, dp, dp, dp, vp]
         L.orc_euler_xflux.argtypes = [vp, dp, dp, vp]
+        L.orc_precond_matrix.argtypes = [vp, dp, dp, dp, vp]
+        L.orc_dwdq.argtypes = [vp, dp, dp, vp]
+        L.orc_solve4.argtypes = [vp, vp, vp]
+        L.orc_solve4.restype = ip
         _lib = L
     return _lib
 
@@ -125,6 +131,10 @@ class Case:
         P.amp[0], P.amp[1] = amp
         P.freq = s.get("freq", 0.0)
         P.vel[0], P.vel[1] = vel
+        P.time_scheme = s.get("time_scheme", 0)
+        P.subiters = s.get("subiters", 30)
+        P.dt_phys = s.get("dt_phys", 0.0)
+        P.cfl_tau = s.get("cfl_tau", 0.8)
         self._P = P
         self.h = lib().orc_create(ctypes.byref(P))
 
@@ -215,3 +225,25 @@ def euler_xflux(q, gamma, R):
     F = np.zeros(4)
     lib().orc_euler_xflux(_ptr(q), gamma, R, _ptr(F))
     return F
+
+
+def precond_matrix(Q, gamma, R, Ur):
+    Q = np.ascontiguousarray(Q, np.float64)
+    out = np.zeros(16)
+    lib().orc_precond_matrix(_ptr(Q), gamma, R, Ur, _ptr(out))
+    return out.reshape(4, 4)
+
+
+def dwdq(Q, gamma, R):
+    Q = np.ascontiguousarray(Q, np.float64)
+    out = np.zeros(16)
+    lib().orc_dwdq(_ptr(Q), gamma, R, _ptr(out))
+    return out.reshape(4, 4)
+
+
+def solve4(A, b):
+    A = np.ascontiguousarray(A, np.float64).ravel()
+    b = np.ascontiguousarray(b, np.float64)
+    x = np.zeros(4)
+    rc = lib().orc_solve4(_ptr(A), _ptr(b), _ptr(x))
+    return x if rc == 0 else None

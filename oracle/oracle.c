@@ -39,6 +39,8 @@ struct orc_case {
   double *T;               /* temperature over the full array */
   double *fx[4], *fy[4];   /* face fluxes */
   int precond;             /* low-Mach scaling of the dissipation (dual time only) */
+  double *Wn[4], *Wm[4];   /* dual time: conserved state at time levels n and n-1 */
+  long nphys;              /* dual time: physical steps taken (BDF1 on the first) */
   uint8_t *tag;
   int nlist[4];
   orc_stencil *list[4];
@@ -598,10 +600,23 @@ static void ldfss(const double qL[4], const double qR[4], double nxf, double nyf
   double MhP = Mh * (1.0 - (dp + adp) / (2.0 * rL * cs * cs));
   double MhM = Mh * (1.0 - (-dp + adp) / (2.0 * rR * cs * cs));
   double Cp = CVL - MhP, Cm = CVR + MhM;
-  double PpL = 0.25 * (ML + 1.0) * (ML + 1.0) * (2.0 - ML);
-  double PmR = 0.25 * (MR - 1.0) * (MR - 1.0) * (2.0 + MR);
-  double DL = aL * (1.0 + bL) - bL * PpL;
-  double DR = aR * (1.0 + bR) - bR * PmR;
+  /* pressure split: with low-Mach scaling (mr2 < 1) it uses the physical Mach
+   * numbers un/c (reading: the split with the scaled Mach numbers made the
+   * preconditioned pseudo-time iteration diverge below M = 0.01) */
+  double pL_ = ML, pR_ = MR, paL = aL, paR = aR, pbL = bL, pbR = bR;
+  if (mr2 < 1.0) {
+    pL_ = unL / cb;
+    pR_ = unR / cb;
+    paL = 0.5 * (1.0 + (pL_ >= 0.0 ? 1.0 : -1.0));
+    paR = 0.5 * (1.0 - (pR_ >= 0.0 ? 1.0 : -1.0));
+    double uL_ = 1.0 - floor(fabs(pL_)), uR_ = 1.0 - floor(fabs(pR_));
+    pbL = -(uL_ > 0.0 ? uL_ : 0.0);
+    pbR = -(uR_ > 0.0 ? uR_ : 0.0);
+  }
+  double PpL = 0.25 * (pL_ + 1.0) * (pL_ + 1.0) * (2.0 - pL_);
+  double PmR = 0.25 * (pR_ - 1.0) * (pR_ - 1.0) * (2.0 + pR_);
+  double DL = paL * (1.0 + pbL) - pbL * PpL;
+  double DR = paR * (1.0 + pbR) - pbR * PmR;
   double mL = rL * cs * Cp, mR = rR * cs * Cm;
   double ph = DL * pL + DR * pR;
   F[0] = mL + mR;
@@ -629,8 +644,12 @@ void orc_euler_xflux(const double q[4], double gamma, double R, double flux[4]) 
 /* Low-Mach preconditioning parameter at a face.  Only the dual-time scheme,
  * whose pseudo-time derivative carries the preconditioning matrix, scales the
  * dissipation; explicit physical-time stepping uses plain LDFSS (Mr^2 = 1).
- * Reference velocity Ur = min(c, max(|V|, U_ref, nu/dn)), Mr^2 = (Ur/c)^2 with
- * face-averaged c, |V| and rho. */
+ * Reference velocity Ur = min(c, max(|V|, U_ref, nu/dn, c/3)), Mr^2 = (Ur/c)^2
+ * with face-averaged c, |V| and rho.  Reading: the floor c/3 bounds the
+ * preconditioning; with lower floors (c/5 and below, or U_ref alone) the
+ * explicit pseudo-time iteration diverged next to an immersed body at
+ * M <= 0.01 (and without a body below M = 0.003). */
+#define UR_FLOOR (1.0 / 3.0)
 static double face_mr2(const orc_case *c, const double qL[4], const double qR[4], double dn) {
   if (!c->precond) return 1.0;
   double g = c->p.gamma;
@@ -642,6 +661,7 @@ static double face_mr2(const orc_case *c, const double qL[4], const double qR[4]
   double Ur = Vm;
   if (1.0 > Ur) Ur = 1.0;
   if (vis > Ur) Ur = vis;
+  if (UR_FLOOR * cb > Ur) Ur = UR_FLOOR * cb;
   if (cb < Ur) Ur = cb;
   double m = (Ur / cb) * (Ur / cb);
   return m < 1.0 ? m : 1.0;
@@ -779,7 +799,165 @@ static double compute_dt(orc_case *c) {
   return p->cfl / lmax;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Dual time stepping (Sec. 2): three-point (BDF2) physical-time derivative,  */
+/* two-point Euler pseudo-time derivative with the low-Mach preconditioning   */
+/* matrix, point-implicit in the physical-time term.  The increment of one   */
+/* pseudo step, for each fluid cell,                                         */
+/*   [Gamma/dtau + (3/(2 dt)) dW/dQ] dQ = -( R(W) + (3W - 4W^n + W^{n-1})/(2 dt) )      */
+/* is applied as the three stages of SSP-RK3 in Q (reading: a single forward  */
+/* Euler pseudo step diverges at low Mach, where the physical-time term does  */
+/* not damp the preconditioned acoustic mode); one sub-iteration = one such  */
+/* three-stage pseudo step.                                                  */
+/* (first physical step: BDF1, (1/dt) dW/dQ and (W^k - W^n)/dt), with        */
+/* R = dF/dx + dG/dy the residual (preconditioned LDFSS dissipation).  The    */
+/* paper names the scheme only; the matrix is the Weiss-Smith form in        */
+/* primitive variables Q = (p, u, v, T):                                     */
+/*   rows [T, 0, 0, rT], [T u, r, 0, rT u], [T v, 0, r, rT v],                */
+/*        [T H - 1, r u, r v, rT H + r cp]                                   */
+/* with rT = -r/T and T = 1/Ur^2 - rT/(r cp) (Gamma) or 1/(R T) (dW/dQ).       */
+/* Ur = min(c, max(|V|, U_ref, nu/dmin, c/3)); local dtau = CFL_tau / [(|u'|+c') */
+/* (1/dx + 1/dy) + 2 gamma mu/(Pr r)(1/dx^2 + 1/dy^2)], u', c' the           */
+/* eigenvalue terms of the preconditioned system.  The 4x4 system is solved  */
+/* by Gaussian elimination with partial pivoting.                            */
+/* ------------------------------------------------------------------------- */
+static void wq_matrix(double theta, const double Q[4], double gamma, double R, double M[16]) {
+  double p = Q[0], u = Q[1], v = Q[2], T = Q[3];
+  double r = p / (R * T);
+  double cpv = gamma * R / (gamma - 1.0);
+  double rT = -r / T;
+  double H = cpv * T + 0.5 * (u * u + v * v);
+  double row[16] = {theta,           0.0,   0.0,   rT,
+                    theta * u,       r,     0.0,   rT * u,
+                    theta * v,       0.0,   r,     rT * v,
+                    theta * H - 1.0, r * u, r * v, rT * H + r * cpv};
+  for (int i = 0; i < 16; i++) M[i] = row[i];
+}
+
+void orc_precond_matrix(const double Q[4], double gamma, double R, double Ur, double out[16]) {
+  double r = Q[0] / (R * Q[3]);
+  double cpv = gamma * R / (gamma - 1.0);
+  double theta = 1.0 / (Ur * Ur) - (-r / Q[3]) / (r * cpv);
+  wq_matrix(theta, Q, gamma, R, out);
+}
+
+void orc_dwdq(const double Q[4], double gamma, double R, double out[16]) {
+  wq_matrix(1.0 / (R * Q[3]), Q, gamma, R, out);
+}
+
+int orc_solve4(const double Ain[16], const double bin[4], double x[4]) {
+  double A[4][5];
+  for (int i = 0; i < 4; i++) {
+    for (int j = 0; j < 4; j++) A[i][j] = Ain[4 * i + j];
+    A[i][4] = bin[i];
+  }
+  for (int col = 0; col < 4; col++) {
+    int piv = col;
+    for (int i = col + 1; i < 4; i++)
+      if (fabs(A[i][col]) > fabs(A[piv][col])) piv = i;
+    if (A[piv][col] == 0.0) return -1;
+    if (piv != col)
+      for (int j = 0; j < 5; j++) {
+        double t = A[col][j];
+        A[col][j] = A[piv][j];
+        A[piv][j] = t;
+      }
+    for (int i = col + 1; i < 4; i++) {
+      double f = A[i][col] / A[col][col];
+      for (int j = col; j < 5; j++) A[i][j] -= f * A[col][j];
+    }
+  }
+  for (int i = 3; i >= 0; i--) {
+    double s = A[i][4];
+    for (int j = i + 1; j < 4; j++) s -= A[i][j] * x[j];
+    x[i] = s / A[i][i];
+  }
+  return 0;
+}
+
+static void dual_update(orc_case *c, int stage, double *const In[4], double *const Out[4], int bdf2) {
+  const orc_params *p = &c->p;
+  int nx = p->nx, ny = p->ny;
+  double g = p->gamma, R = c->R, dt = p->dt_phys;
+  double vis = (2.0 * g * c->mu / p->prandtl) * (1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy));
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      if (c->tag[j * nx + i] != ORC_FLUID) continue;
+      int m = fidx(c, i, j), mw = fidx(c, i - 1, j), ms = fidx(c, i, j - 1);
+      double W[4], Q[4], S[4];
+      for (int v = 0; v < 4; v++) W[v] = In[v][m];
+      cons_to_prim(c, W[0], W[1], W[2], W[3], Q);
+      for (int v = 0; v < 4; v++) {
+        double Rv = (c->fx[v][m] - c->fx[v][mw]) / c->dx + (c->fy[v][m] - c->fy[v][ms]) / c->dy;
+        double tdt = bdf2 ? (3.0 * W[v] - 4.0 * c->Wn[v][m] + c->Wm[v][m]) / (2.0 * dt) : (W[v] - c->Wn[v][m]) / dt;
+        S[v] = -(Rv + tdt);
+      }
+      double r = W[0];
+      double cs = sqrt(g * Q[0] / r);
+      double Vm = sqrt(Q[1] * Q[1] + Q[2] * Q[2]);
+      double Ur = Vm;
+      if (1.0 > Ur) Ur = 1.0;
+      if (c->mu / r / c->dmin > Ur) Ur = c->mu / r / c->dmin;
+      if (UR_FLOOR * cs > Ur) Ur = UR_FLOOR * cs;
+      if (cs < Ur) Ur = cs;
+      double mr2 = (Ur / cs) * (Ur / cs);
+      double up = 0.5 * Vm * (1.0 + mr2);
+      double om = 1.0 - mr2;
+      double cp_ = 0.5 * sqrt(om * om * Vm * Vm + 4.0 * Ur * Ur);
+      double lam = (up + cp_) * (1.0 / c->dx + 1.0 / c->dy) + vis / r;
+      double dtau = p->cfl_tau / lam;
+      double G[16], J[16], M[16], dQ[4];
+      orc_precond_matrix(Q, g, R, Ur, G);
+      orc_dwdq(Q, g, R, J);
+      double a = bdf2 ? 1.5 / dt : 1.0 / dt;
+      for (int q = 0; q < 16; q++) M[q] = G[q] / dtau + a * J[q];
+      if (orc_solve4(M, S, dQ) != 0) continue;
+      /* SSP-RK3 combination in Q with the sub-iteration's starting iterate Q0 (held in A) */
+      double Q0[4], Qn[4];
+      cons_to_prim(c, c->A[0][m], c->A[1][m], c->A[2][m], c->A[3][m], Q0);
+      for (int v = 0; v < 4; v++) {
+        double e = Q[v] + dQ[v];
+        if (stage == 1) Qn[v] = e;
+        else if (stage == 2) Qn[v] = 0.75 * Q0[v] + 0.25 * e;
+        else Qn[v] = (1.0 / 3.0) * Q0[v] + (2.0 / 3.0) * e;
+      }
+      double Un[4];
+      prim_to_cons(c, Qn, Un);
+      for (int v = 0; v < 4; v++) Out[v][m] = Un[v];
+    }
+}
+
+static void dual_step(orc_case *c) {
+  if (!c->classified || c->p.motion != ORC_MOTION_STATIC) orc_classify(c);
+  const orc_params *p = &c->p;
+  size_t n = (size_t)c->W * c->H;
+  for (int v = 0; v < 4; v++) {
+    if (c->nphys > 0) memcpy(c->Wm[v], c->Wn[v], n * sizeof(double));
+    memcpy(c->Wn[v], c->A[v], n * sizeof(double));
+  }
+  int bdf2 = c->nphys > 0;
+  double t1 = c->t + p->dt_phys;
+  double *const *in[3] = {c->A, c->B, c->C};
+  double *const *out[3] = {c->B, c->C, c->A};
+  for (int k = 0; k < p->subiters; k++)
+    for (int st = 0; st < 3; st++) {
+      reconstruct(c, in[st], t1);
+      domain_bc(c, in[st]);
+      residual_faces(c, in[st]);
+      dual_update(c, st + 1, in[st], out[st], bdf2);
+    }
+  (void)n;
+  c->t = t1;
+  c->last_dt = p->dt_phys;
+  c->nphys++;
+}
+
 int orc_step(orc_case *c, int nsteps) {
+  if (c->p.time_scheme == ORC_TIME_DUAL) {
+    for (int s = 0; s < nsteps; s++) dual_step(c);
+    return c->nerr;
+  }
   for (int s = 0; s < nsteps; s++) {
     if (!c->classified || c->p.motion != ORC_MOTION_STATIC) orc_classify(c);
     double dt = compute_dt(c);
@@ -909,9 +1087,12 @@ orc_case *orc_create(const orc_params *pp) {
     if (v == 0) c->T = malloc(n * sizeof(double));
     c->fx[v] = calloc(n, sizeof(double));
     c->fy[v] = calloc(n, sizeof(double));
-    for (size_t m = 0; m < n; m++) c->A[v][m] = c->B[v][m] = c->C[v][m] = c->Uinf[v];
+    c->Wn[v] = malloc(n * sizeof(double));
+    c->Wm[v] = malloc(n * sizeof(double));
+    for (size_t m = 0; m < n; m++) c->A[v][m] = c->B[v][m] = c->C[v][m] = c->Wn[v][m] = c->Wm[v][m] = c->Uinf[v];
   }
   c->tag = calloc((size_t)p->nx * p->ny, 1);
+  c->precond = p->time_scheme == ORC_TIME_DUAL;
   for (int k = 0; k < 4; k++) c->list[k] = calloc(1, sizeof(orc_stencil));
   return c;
 }
@@ -921,6 +1102,7 @@ void orc_destroy(orc_case *c) {
   for (int v = 0; v < 4; v++) {
     if (v == 0) free(c->T);
     free(c->A[v]); free(c->B[v]); free(c->C[v]); free(c->q[v]); free(c->fx[v]); free(c->fy[v]);
+    free(c->Wn[v]); free(c->Wm[v]);
   }
   for (int k = 0; k < 4; k++) free(c->list[k]);
   free(c->tag); free(c->vref); free(c->vx); free(c->vy); free(c->snx); free(c->sny); free(c->vnx); free(c->vny);

@@ -44,6 +44,7 @@ enum { ORC_FLUID = 0, ORC_SOLID = 1, ORC_IB = 2, ORC_G1 = 3, ORC_G2 = 4, ORC_G3 
 enum { ORC_BC_FREESTREAM = 0, ORC_BC_OUTFLOW = 1, ORC_BC_PERIODIC = 2 };
 enum { ORC_MOTION_STATIC = 0, ORC_MOTION_SIN = 1, ORC_MOTION_CONST = 2 };
 enum { ORC_REGION_FACE = 0, ORC_REGION_VERTEX = 1, ORC_REGION_FALLBACK = 2 };
+enum { ORC_TIME_RK3 = 0, ORC_TIME_DUAL = 1 };
 
 typedef struct {
   int nx, ny;              /* cells */
@@ -57,6 +58,10 @@ typedef struct {
   const double *verts;     /* 2*nv, interleaved x,y; copied */
   int motion;
   double amp[2], freq, vel[2];
+  int time_scheme;         /* ORC_TIME_RK3 or ORC_TIME_DUAL */
+  int subiters;            /* dual time: pseudo-time sub-iterations per physical step */
+  double dt_phys;          /* dual time: physical time step */
+  double cfl_tau;          /* dual time: pseudo-time CFL number */
 } orc_params;
 
 /* One immersed-boundary or ghost node and its reconstruction stencil. */
@@ -80,7 +85,7 @@ typedef struct orc_case orc_case;
 orc_case *orc_create(const orc_params *p);
 void orc_destroy(orc_case *c);
 int orc_classify(orc_case *c);                   /* geometry at the current time */
-int orc_step(orc_case *c, int nsteps);           /* SSP-RK3 steps; returns #stencil errors */
+int orc_step(orc_case *c, int nsteps);           /* RK3 or dual-time physical steps; returns #stencil errors */
 void orc_get_state(const orc_case *c, double *dst);      /* [4][ny][nx] conserved */
 void orc_set_state(orc_case *c, const double *src);      /* [4][ny][nx] conserved */
 void orc_get_tags(const orc_case *c, uint8_t *dst);      /* [ny][nx] */
@@ -100,6 +105,10 @@ double orc_weno5(const double f[5]);
 void orc_ldfss_xflux(const double qL[4], const double qR[4], double gamma, double R,
                      double mr2_fixed, double flux[4]);
 void orc_euler_xflux(const double q[4], double gamma, double R, double flux[4]);
+/* dual time: preconditioning matrix Gamma (Ur) and dW/dQ at Q = (p, u, v, T), row-major 4x4 */
+void orc_precond_matrix(const double Q[4], double gamma, double R, double Ur, double out[16]);
+void orc_dwdq(const double Q[4], double gamma, double R, double out[16]);
+int orc_solve4(const double A[16], const double b[4], double x[4]);
 
 #ifdef __cplusplus
 }

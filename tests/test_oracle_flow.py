@@ -6,6 +6,7 @@ rates, conservation, exact free-stream solutions and the theta-beta-M
 relation.  A dropped term, a wrong sign or a transposed index in the WENO5,
 LDFSS, viscous, RK3 or boundary code fails at least one of them.
 """
+import decimal
 import math
 
 import numpy as np
@@ -350,3 +351,109 @@ def test_wedge_oblique_shock_theta_beta_m(orc):
     assert abs(math.degrees(math.atan(slope)) - math.degrees(beta_e)) < 3.0, (math.degrees(math.atan(slope)),
                                                                               math.degrees(beta_e))
     assert abs(np.median(plateau) / pr_e - 1.0) < 0.10, (plateau, pr_e)
+
+
+# ---------------------------------------------------------------- dual time (Sec. 2)
+
+def test_preconditioning_matrix_identities(orc):
+    """dW/dQ against finite differences of W(Q); Gamma(Ur = c) = dW/dQ for an ideal gas; the eigenvalues of
+    Gamma^-1 dF/dQ are u, u, u' +- c' of the preconditioned system; the 4x4 solver against numpy."""
+    rng = np.random.default_rng(17)
+    decimal.getcontext().prec = 60
+    for M in (0.5, 0.01, 0.001):
+        R = 1.0 / (GAMMA * M * M)
+        for _ in range(5):
+            Q = np.array([R * rng.uniform(0.8, 1.2), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.8, 1.2)])
+
+            Rd, gd = decimal.Decimal(R), decimal.Decimal(GAMMA)
+
+            def Wd(q):
+                r = q[0] / (Rd * q[3])
+                return [r, r * q[1], r * q[2], q[0] / (gd - 1) + r * (q[1] ** 2 + q[2] ** 2) / 2]
+
+            def Fd(q):
+                r = q[0] / (Rd * q[3])
+                H = gd / (gd - 1) * q[0] / r + (q[1] ** 2 + q[2] ** 2) / 2
+                return [r * q[1], r * q[1] ** 2 + q[0], r * q[1] * q[2], r * q[1] * H]
+
+            J = orc.dwdq(Q, GAMMA, R)
+            A = np.zeros((4, 4))
+            Jfd = np.zeros((4, 4))
+            for j in range(4):
+                # central differences in 60-digit decimal arithmetic (W and F are rational in Q)
+                h = decimal.Decimal(1e-20) * decimal.Decimal(max(1.0, abs(Q[j])))
+                qp = [decimal.Decimal(x) for x in Q]
+                qm = [decimal.Decimal(x) for x in Q]
+                qp[j] += h
+                qm[j] -= h
+                Jfd[:, j] = [float((a - b) / (2 * h)) for a, b in zip(Wd(qp), Wd(qm))]
+                A[:, j] = [float((a - b) / (2 * h)) for a, b in zip(Fd(qp), Fd(qm))]
+            # the T column of the energy row cancels rho c_p terms: absolute rounding scales with rho c_p
+            rcp = Q[0] / (R * Q[3]) * GAMMA * R / (GAMMA - 1)
+            np.testing.assert_allclose(J, Jfd, rtol=1e-12, atol=1e-14 * max(1.0, rcp))
+            c = math.sqrt(GAMMA * Q[0] / (Q[0] / (R * Q[3])))
+            np.testing.assert_allclose(orc.precond_matrix(Q, GAMMA, R, c), J, rtol=1e-12, atol=1e-12 * np.abs(J).max())
+            Ur = 0.5 * c
+            G = orc.precond_matrix(Q, GAMMA, R, Ur)
+            ev = np.sort(np.linalg.eigvals(np.linalg.solve(G, A)).real)
+            mr2 = (Ur / c) ** 2
+            up = 0.5 * Q[1] * (1 + mr2)
+            cp = 0.5 * math.sqrt(Q[1] ** 2 * (1 - mr2) ** 2 + 4 * Ur * Ur)
+            np.testing.assert_allclose(ev, np.sort([up - cp, Q[1], Q[1], up + cp]), rtol=1e-5, atol=1e-5 * c)
+            b = rng.normal(size=4)
+            np.testing.assert_allclose(orc.solve4(G, b), np.linalg.solve(G, b), rtol=1e-9)
+
+
+def _dual_box(orc, M, nx=32, subiters=30):
+    dx = 1.0 / nx
+    spec = W.case_spec(None, nx, 4, (0.0, 1.0, 0.0, 4 * dx), M, 0.0, W.PERIODIC, time_scheme=W.TIME_DUAL,
+                       dt_phys=0.5 * dx, subiters=subiters, uinf=(1.0, 0.0))
+    c = orc.Case(spec)
+    X = np.tile((np.arange(nx) + 0.5) * dx, (4, 1))
+    return c, X
+
+
+@pytest.mark.parametrize("M", [0.3, 0.01, 0.001])
+def test_dual_time_advects_entropy_wave_without_pressure(orc, M):
+    """An entropy wave (density varies, u and p uniform) advected at low Mach with the preconditioned dual-time
+    scheme keeps p and u uniform to a small fraction of the dynamic pressure rho U^2 (= 1) and of U."""
+    c, X = _dual_box(orc, M)
+    pinf = 1.0 / (GAMMA * M * M)
+    c.set_state(prim_to_cons(1.0 + 0.01 * np.sin(2 * math.pi * X), np.ones_like(X), 0 * X, np.full_like(X, pinf)))
+    c.step(20)
+    r, u, v, p = cons_to_prim(c.state())
+    assert np.abs(u - 1).max() < 1e-3 and np.abs(p - pinf).max() < 0.05, (np.abs(u - 1).max(), np.abs(p - pinf).max())
+    assert 0.989 < r.min() and r.max() < 1.011
+
+
+def test_dual_time_quiescent_body_and_free_stream(orc):
+    """Gas at rest around a body and a uniform stream are exact solutions of the dual-time scheme too."""
+    for uinf in ((0.0, 0.0), (1.0, 0.0)):
+        spec = W.case_spec(W.naca00xx(0.12, 200, 10.0), 96, 48, (-0.5, 1.5, -0.5, 0.5), 0.01, 500.0, W.FAR,
+                           uinf=uinf, time_scheme=W.TIME_DUAL, dt_phys=0.01, subiters=10)
+        if uinf[0] != 0.0:
+            spec = dict(spec, verts=np.zeros((0, 2)))
+        c = orc.Case(spec)
+        U0 = c.state()
+        c.step(5)
+        U1 = c.state()
+        live = c.tags() != 1
+        for k in range(4):
+            assert np.abs(U1[k] - U0[k])[live].max() <= 1e-12 * max(1.0, np.abs(U0[k]).max()), (uinf, k)
+
+
+def test_dual_time_cylinder_low_mach_is_stable(orc):
+    """Impulsively started cylinder at M = 0.01 with dual time (30 sub-iterations, BDF2): bounded, drag of the
+    expected size for Re = 40 on a coarse grid."""
+    nx, ny = 160, 80
+    spec = W.case_spec(W.cylinder(256), nx, ny, (-8.0, 24.0, -8.0, 8.0), 0.01, 40.0, W.FAR,
+                       time_scheme=W.TIME_DUAL, dt_phys=0.5 * 32.0 / nx, subiters=30)
+    c = orc.Case(spec)
+    c.step(40)
+    U = c.state()
+    fl = c.tags() == 0
+    assert np.isfinite(U).all()
+    u = U[1] / U[0]
+    assert u[fl].max() < 1.5 and u[fl].min() > -0.5
+    cd = c.forces()[0]
+    assert 1.0 < cd < 3.0, cd
