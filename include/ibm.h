@@ -67,6 +67,11 @@ enum { IBM_MOTION_STATIC = 0, IBM_MOTION_SIN = 1, IBM_MOTION_CONST = 2 };
 /* arithmetic: FP64 throughout, or FP32 bulk (stage values and fluxes in FP32
  * on perturbations from the free stream, FP64 state accumulation) */
 enum { IBM_PREC_FP64 = 0, IBM_PREC_FP32_BULK = 1 };
+/* time stepping: explicit SSP-RK3 with the CFL rule, or dual time (Sec. 2):
+ * three-point (BDF2) physical-time derivative, preconditioned pseudo time,
+ * each sub-iteration one point-implicit three-stage pseudo step with a 4x4
+ * FP64 solve per cell; low-Mach scaling bounded at Ur >= c/3 */
+enum { IBM_TIME_RK3 = 0, IBM_TIME_DUAL = 1 };
 /* stencil regions (Sec. 4.1): closest feature is a segment interior or a
  * vertex; FALLBACK = the line along the local normal met no segment on the
  * surface side, the boundary point is the closest point */
@@ -90,10 +95,14 @@ typedef struct {
 typedef struct {
   double mach, re, gamma, prandtl, cfl;
   double uinf[2];   /* free-stream velocity in reference-speed units */
-  double dt_fixed;  /* > 0: fixed time step, else the CFL rule */
+  double dt_fixed;  /* > 0: fixed time step, else the CFL rule (explicit scheme) */
   double ref_len;   /* force normalisation length (> 0) */
   int precision;    /* IBM_PREC_* */
-  int reserved[3];  /* zero */
+  int time_scheme;  /* IBM_TIME_* */
+  int subiters;     /* dual time: pseudo-time sub-iterations per physical step (>= 1) */
+  int reserved;     /* zero */
+  double dt_phys;   /* dual time: physical time step (> 0) */
+  double cfl_tau;   /* dual time: pseudo-time CFL number (> 0) */
 } ibm_flow;
 
 typedef struct {
@@ -142,9 +151,9 @@ ibm_status ibm_create_case(const ibm_geometry *geometry, const ibm_grid *grid, c
  * (Sec. 3.2, 4.1-4.3).  Asynchronous. */
 ibm_status ibm_classify(ibm_case *c);
 
-/* Advance nsteps SSP-RK3 steps.  Moving bodies are re-classified at the start
- * of every step; a static body is classified once if it has not been.
- * Asynchronous. */
+/* Advance nsteps physical steps (SSP-RK3, or dual time with `subiters`
+ * sub-iterations).  Moving bodies are re-classified at the start of every
+ * step; a static body is classified once if it has not been.  Asynchronous. */
 ibm_status ibm_step(ibm_case *c, int nsteps);
 
 /* Copy a quantity out.  dst: host memory (dst_on_device = 0) or device memory

@@ -21,6 +21,7 @@ struct ibm_case {
   double *vref = nullptr, *vx = nullptr, *vy = nullptr, *snx = nullptr, *sny = nullptr, *vnx = nullptr,
          *vny = nullptr;
   double *A = nullptr, *B = nullptr, *C = nullptr;  // FP64 conserved: state, stage arrays (FP64 mode)
+  double *Wn = nullptr, *Wm = nullptr;               // dual time: states at time levels n and n-1
   float *M = nullptr, *F1 = nullptr, *F2 = nullptr;  // FP32-bulk: perturbation mirror and stage arrays
   double *stage64 = nullptr;  // FP32-bulk: absolute-variable staging for ibm_get_state (allocated on first use)
   uint8_t *solid = nullptr, *tag = nullptr;
@@ -146,6 +147,12 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
   if (fl->precision != IBM_PREC_FP64 && fl->precision != IBM_PREC_FP32_BULK)
     return fail(IBM_EINVAL, "bad precision");
   if (mo && (mo->kind < IBM_MOTION_STATIC || mo->kind > IBM_MOTION_CONST)) return fail(IBM_EINVAL, "bad motion");
+  if (fl->time_scheme != IBM_TIME_RK3 && fl->time_scheme != IBM_TIME_DUAL) return fail(IBM_EINVAL, "bad time scheme");
+  if (fl->time_scheme == IBM_TIME_DUAL) {
+    if (!(fl->dt_phys > 0) || !(fl->cfl_tau > 0) || fl->subiters < 1)
+      return fail(IBM_EINVAL, "dual time needs dt_phys > 0, cfl_tau > 0, subiters >= 1");
+    if (fl->precision != IBM_PREC_FP64) return fail(IBM_EINVAL, "dual time runs in FP64");
+  }
   return IBM_OK;
 }
 
@@ -163,7 +170,7 @@ extern "C" size_t ibm_case_device_bytes(const ibm_geometry *geo, const ibm_grid 
 
 static void free_case(ibm_case *c) {
   if (!c) return;
-  void *ptrs[] = {c->vref, c->vx, c->vy, c->snx, c->sny, c->vnx, c->vny, c->A, c->B, c->C, c->M, c->F1,
+  void *ptrs[] = {c->Wn, c->Wm, c->vref, c->vx, c->vy, c->snx, c->sny, c->vnx, c->vny, c->A, c->B, c->C, c->M, c->F1,
                   c->F2, c->stage64, c->solid, c->tag, c->blockcounts, c->st, c->rst, c->sid, c->tile_body,
                   c->body_tiles, c->ds};
   for (void *p : ptrs)
@@ -239,6 +246,10 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
     k.motion.vel[d] = mo ? mo->vel[d] : 0.0;
   }
   k.motion.freq = mo ? mo->freq : 0.0;
+  k.dual = fl->time_scheme == IBM_TIME_DUAL;
+  k.subiters = fl->subiters;
+  k.dt_phys = fl->dt_phys;
+  k.cfl_tau = fl->cfl_tau;
 
   const int nv = geo->nverts;
   const size_t ncell = (size_t)k.nx * k.ny;
@@ -258,6 +269,10 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   if (c->precision == IBM_PREC_FP64) {
     ALLOC(c->B, 4 * plane);
     ALLOC(c->C, 4 * plane);
+    if (k.dual) {
+      ALLOC(c->Wn, 4 * plane);
+      ALLOC(c->Wm, 4 * plane);
+    }
   } else {
     ALLOC(c->M, 4 * plane);
     ALLOC(c->F1, 4 * plane);
@@ -309,9 +324,9 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
       c->launches++;
     }
     std::memset(c->hds, 0, sizeof(DevState));
-    if (k.dt_fixed > 0.0) {
-      c->hds->dt = k.dt_fixed;
-      c->hds->dtf = (float)k.dt_fixed;
+    if (k.dt_fixed > 0.0 || k.dual) {
+      c->hds->dt = k.dual ? k.dt_phys : k.dt_fixed;
+      c->hds->dtf = (float)c->hds->dt;
     }
     if (cudaMemcpyAsync(c->ds, c->hds, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(c->tag, 0, ncell, s) != cudaSuccess) {
@@ -333,6 +348,9 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
         rs = fail(IBM_ECUDA, "state upload failed");
       if (c->C && cudaMemcpy(c->C + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         rs = fail(IBM_ECUDA, "state upload failed");
+      for (double *w : {c->Wn, c->Wm})
+        if (w && cudaMemcpy(w + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+          rs = fail(IBM_ECUDA, "state upload failed");
     }
     delete[] hU;
     if (rs != IBM_OK) break;
@@ -402,6 +420,26 @@ static int enqueue_step(ibm_case *c) {
     do_classify(c);
     nl += (int)c->launches - before;
     c->launches = before;
+  }
+  if (c->k.dual) {
+    // dual time: W^{n-1} <- W^n <- W, then sub-iterations of three pseudo stages at t + dt
+    const size_t bytes = 4 * (size_t)c->k.plane * sizeof(double);
+    cudaMemcpyAsync(c->Wm, c->Wn, bytes, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->Wn, c->A, bytes, cudaMemcpyDeviceToDevice, s);
+    double *din[3] = {c->A, c->B, c->C};
+    double *dout[3] = {c->B, c->C, c->A};
+    for (int it = 0; it < c->k.subiters; it++)
+      for (int st = 1; st <= 3; st++) {
+        prof_mark(c, 1, true);
+        launch_recon_f64(c->k, din[st - 1], c->st, c->cap, c->ds, 2, s, &nl);
+        prof_mark(c, 1, false);
+        prof_mark(c, 0, true);
+        launch_dual_f64(c->k, st, c->A, din[st - 1], dout[st - 1], c->Wn, c->Wm, c->tag, c->ds, s);
+        prof_mark(c, 0, false);
+        nl += 1;
+      }
+    launch_dual_end(c->k, c->ds, s);
+    return nl + 1;
   }
   const bool f64 = c->precision == IBM_PREC_FP64;
   const bool fuse_cfl = fused_cfl(c);

@@ -157,13 +157,19 @@ __device__ __forceinline__ R weno5(R f0, R f1, R f2, R f3, R f4) {
 // the first velocity component un, tangential ut.  F = (mass, normal
 // momentum, tangential momentum, energy).
 // ---------------------------------------------------------------------------
+template <bool PRE>
 __device__ __forceinline__ void ldfss_f64(double rL, double unL, double utL, double pL, double rR, double unR,
-                                          double utR, double pR, double gamma, double F[4]) {
+                                          double utR, double pR, double gamma, double mr2, double F[4]) {
   const double gg = gamma / (gamma - 1.0);
   const double cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
   const double HL = gg * pL / rL + 0.5 * (unL * unL + utL * utL);
   const double HR = gg * pR / rR + 0.5 * (unR * unR + utR * utR);
-  const double cs = 0.5 * (cL + cR);
+  const double cb = 0.5 * (cL + cR);
+  double cs = cb;
+  if (PRE) {  // low-Mach numerical sound speed c' = 1/2 sqrt((1-Mr^2)^2 un^2 + 4 Mr^2 c^2)
+    const double ub = 0.5 * (unL + unR), om = 1.0 - mr2;
+    cs = 0.5 * sqrt(om * om * ub * ub + 4.0 * mr2 * cb * cb);
+  }
   const double ics = 1.0 / cs;
   const double ML = unL * ics, MR = unR * ics;
   const double aL = ML >= 0.0 ? 1.0 : 0.0;
@@ -181,10 +187,22 @@ __device__ __forceinline__ void ldfss_f64(double rL, double unL, double utL, dou
   const double MhP = Mh * (1.0 - (dp + adp) * ic2 / rL);
   const double MhM = Mh * (1.0 - (adp - dp) * ic2 / rR);
   const double Cp = CVL - MhP, Cm = CVR + MhM;
-  const double PpL = MpL * (2.0 - ML);
-  const double PmR = -MmR * (2.0 + MR);
-  const double DL = aL * (1.0 + bL) - bL * PpL;
-  const double DR = aR * (1.0 + bR) - bR * PmR;
+  double DL, DR;
+  if (PRE && mr2 < 1.0) {  // pressure split with the physical Mach numbers
+    const double ic = 1.0 / cb;
+    const double mL = unL * ic, mR = unR * ic;
+    const double paL = mL >= 0.0 ? 1.0 : 0.0, paR = mR >= 0.0 ? 0.0 : 1.0;
+    const double pbL = -fmax(1.0 - floor(fabs(mL)), 0.0), pbR = -fmax(1.0 - floor(fabs(mR)), 0.0);
+    const double PpL = 0.25 * (mL + 1.0) * (mL + 1.0) * (2.0 - mL);
+    const double PmR = 0.25 * (mR - 1.0) * (mR - 1.0) * (2.0 + mR);
+    DL = paL * (1.0 + pbL) - pbL * PpL;
+    DR = paR * (1.0 + pbR) - pbR * PmR;
+  } else {
+    const double PpL = MpL * (2.0 - ML);
+    const double PmR = -MmR * (2.0 + MR);
+    DL = aL * (1.0 + bL) - bL * PpL;
+    DR = aR * (1.0 + bR) - bR * PmR;
+  }
   const double mL = rL * cs * Cp, mR = rR * cs * Cm;
   F[0] = mL + mR;
   F[1] = mL * unL + mR * unR + DL * pL + DR * pR;
@@ -205,9 +223,77 @@ __device__ __forceinline__ void ldfss_f64(double rL, double unL, double utL, dou
 // ---------------------------------------------------------------------------
 constexpr int TX = 16, TY = 16, HX = TX + 2 * NG, HY = TY + 2 * NG;
 
-template <int STAGE>
+// Low-Mach preconditioning parameter at a face (dual time): reference velocity
+// Ur = min(c, max(|V|, U_ref, nu/dn, c/3)) from face-averaged c, |V|, rho;
+// returns Mr^2 = (Ur/c)^2.  States (rho, u, v, p).
+__device__ __forceinline__ double face_mr2(const Consts &k, const double qL[4], const double qR[4], double dn) {
+  const double cb = 0.5 * (sqrt(k.gamma * qL[3] / qL[0]) + sqrt(k.gamma * qR[3] / qR[0]));
+  const double ub = 0.5 * (qL[1] + qR[1]), vb = 0.5 * (qL[2] + qR[2]);
+  const double Vm = sqrt(ub * ub + vb * vb);
+  const double rb = 0.5 * (qL[0] + qR[0]);
+  double Ur = fmax(fmax(Vm, 1.0), k.mu / rb / dn);
+  Ur = fmax(Ur, UR_FLOOR * cb);
+  Ur = fmin(Ur, cb);
+  const double m = (Ur / cb) * (Ur / cb);
+  return fmin(m, 1.0);
+}
+
+// Weiss-Smith matrix in Q = (p, u, v, T) with first-column parameter theta:
+// Gamma (theta = 1/Ur^2 - rT/(r cp)) or dW/dQ (theta = 1/(R T)); row major
+__device__ __forceinline__ void wq_matrix(double theta, double p, double u, double v, double T, double r, double cpv,
+                                          double M[16]) {
+  const double rT = -r / T;
+  const double H = cpv * T + 0.5 * (u * u + v * v);
+  M[0] = theta;           M[1] = 0.0;    M[2] = 0.0;    M[3] = rT;
+  M[4] = theta * u;       M[5] = r;      M[6] = 0.0;    M[7] = rT * u;
+  M[8] = theta * v;       M[9] = 0.0;    M[10] = r;     M[11] = rT * v;
+  M[12] = theta * H - 1.0; M[13] = r * u; M[14] = r * v; M[15] = rT * H + r * cpv;
+  (void)p;
+}
+
+// Gaussian elimination with partial pivoting; false if singular
+__device__ __forceinline__ bool solve4(double A[16], double b[4], double x[4]) {
+#pragma unroll
+  for (int col = 0; col < 4; col++) {
+    int piv = col;
+#pragma unroll
+    for (int i = col + 1; i < 4; i++)
+      if (fabs(A[4 * i + col]) > fabs(A[4 * piv + col])) piv = i;
+    if (A[4 * piv + col] == 0.0) return false;
+    if (piv != col) {
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const double t = A[4 * col + j];
+        A[4 * col + j] = A[4 * piv + j];
+        A[4 * piv + j] = t;
+      }
+      const double t = b[col];
+      b[col] = b[piv];
+      b[piv] = t;
+    }
+#pragma unroll
+    for (int i = col + 1; i < 4; i++) {
+      const double f = A[4 * i + col] / A[4 * col + col];
+#pragma unroll
+      for (int j = col; j < 4; j++) A[4 * i + j] -= f * A[4 * col + j];
+      b[i] -= f * b[col];
+    }
+  }
+#pragma unroll
+  for (int i = 3; i >= 0; i--) {
+    double s = b[i];
+#pragma unroll
+    for (int j = i + 1; j < 4; j++) s -= A[4 * i + j] * x[j];
+    x[i] = s / A[4 * i + i];
+  }
+  return true;
+}
+
+template <int STAGE, bool DUAL>
 __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, const double *__restrict__ In,
-                                                   double *Out, const uint8_t *__restrict__ tag, DevState *ds) {
+                                                   double *Out, const double *__restrict__ Wn,
+                                                   const double *__restrict__ Wm, const uint8_t *__restrict__ tag,
+                                                   DevState *ds) {
   __shared__ double sq[4][HY][HX];  // rho, u, v, p
   __shared__ double sT[HY][HX];     // temperature
   __shared__ double sfx[4][TY][TX + 1];
@@ -218,7 +304,7 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
   const bool inside = ci < k.nx && cj < k.ny;
   const bool fluid = inside && tag[cj * k.nx + ci] == FLUID;
   const double dt = ds->dt;
-  if (STAGE == 3 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+  if (!DUAL && STAGE == 3 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     // end of the step (no other kernel of this stage reads t)
     ds->t = ds->t + dt;
     ds->steps += 1;
@@ -274,7 +360,8 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
       }
     }
     double F[4];
-    ldfss_f64(qL[0], qL[1], qL[2], qL[3], qR[0], qR[1], qR[2], qR[3], k.gamma, F);
+    ldfss_f64<DUAL>(qL[0], qL[1], qL[2], qL[3], qR[0], qR[1], qR[2], qR[3], k.gamma,
+                    DUAL ? face_mr2(k, qL, qR, k.dx) : 1.0, F);
     const int a = f + 2, a1 = f + 3;
     const double ux = (sq[1][b][a1] - sq[1][b][a]) * idx;
     const double vx = (sq[2][b][a1] - sq[2][b][a]) * idx;
@@ -308,7 +395,8 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
     }
     double F[4];
     // normal velocity v, tangential u
-    ldfss_f64(qL[0], qL[2], qL[1], qL[3], qR[0], qR[2], qR[1], qR[3], k.gamma, F);
+    ldfss_f64<DUAL>(qL[0], qL[2], qL[1], qL[3], qR[0], qR[2], qR[1], qR[3], k.gamma,
+                    DUAL ? face_mr2(k, qL, qR, k.dy) : 1.0, F);
     const int b = f + 2, b1 = f + 3;
     const double uy = (sq[1][b1][a] - sq[1][b][a]) * idy;
     const double vy = (sq[2][b1][a] - sq[2][b][a]) * idy;
@@ -326,23 +414,91 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
   __syncthreads();
   if (!fluid) return;
   const long long id = cidx(k, ci, cj);
-  for (int v = 0; v < 4; v++) {
-    const double L = -((sfx[v][ty][tx + 1] - sfx[v][ty][tx]) * idx + (sfy[v][ty + 1][tx] - sfy[v][ty][tx]) * idy);
-    const long long o = id + v * P;
-    double r;
-    if (STAGE == 1) r = Un[o] + dt * L;
-    else if (STAGE == 2) r = 0.75 * Un[o] + 0.25 * (In[o] + dt * L);
-    else r = (1.0 / 3.0) * Un[o] + (2.0 / 3.0) * (In[o] + dt * L);
-    Out[o] = r;
+  if (!DUAL) {
+    for (int v = 0; v < 4; v++) {
+      const double L = -((sfx[v][ty][tx + 1] - sfx[v][ty][tx]) * idx + (sfy[v][ty + 1][tx] - sfy[v][ty][tx]) * idy);
+      const long long o = id + v * P;
+      double r;
+      if (STAGE == 1) r = Un[o] + dt * L;
+      else if (STAGE == 2) r = 0.75 * Un[o] + 0.25 * (In[o] + dt * L);
+      else r = (1.0 / 3.0) * Un[o] + (2.0 / 3.0) * (In[o] + dt * L);
+      Out[o] = r;
+    }
+    return;
   }
+  // Dual time (Sec. 2): pseudo-time stage of the point-implicit preconditioned update
+  //   [Gamma/dtau + a dW/dQ] dQ = -(R + BDF(W)),  a = 3/(2 dt) (BDF2) or 1/dt (first step)
+  // combined with the sub-iteration's start Q0 as SSP-RK3 stage STAGE.  FP64 4x4 solve.
+  const bool bdf2 = ds->steps > 0;
+  const double dtp = k.dt_phys;
+  double W[4], S[4];
+  for (int v = 0; v < 4; v++) W[v] = In[id + v * P];
+  const double r = W[0], iu = W[1] / r, iv = W[2] / r;
+  const double pr = g1 * (W[3] - 0.5 * r * (iu * iu + iv * iv));
+  const double T = pr / (r * k.R);
+  for (int v = 0; v < 4; v++) {
+    const double Rv = (sfx[v][ty][tx + 1] - sfx[v][ty][tx]) / k.dx + (sfy[v][ty + 1][tx] - sfy[v][ty][tx]) / k.dy;
+    const long long o = id + v * P;
+    const double tdt = bdf2 ? (3.0 * W[v] - 4.0 * Wn[o] + Wm[o]) / (2.0 * dtp) : (W[v] - Wn[o]) / dtp;
+    S[v] = -(Rv + tdt);
+  }
+  const double cs = sqrt(k.gamma * pr / r);
+  const double Vm = sqrt(iu * iu + iv * iv);
+  double Ur = fmax(fmax(Vm, 1.0), k.mu / r / k.dmin);
+  Ur = fmin(fmax(Ur, UR_FLOOR * cs), cs);
+  const double mr2 = (Ur / cs) * (Ur / cs);
+  const double up = 0.5 * Vm * (1.0 + mr2);
+  const double om = 1.0 - mr2;
+  const double cp_ = 0.5 * sqrt(om * om * Vm * Vm + 4.0 * Ur * Ur);
+  const double vis = (2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy));
+  const double lam = (up + cp_) * (1.0 / k.dx + 1.0 / k.dy) + vis / r;
+  const double dtau = k.cfl_tau / lam;
+  const double theta = 1.0 / (Ur * Ur) - (-r / T) / (r * k.cp);
+  double G[16], J[16];
+  wq_matrix(theta, pr, iu, iv, T, r, k.cp, G);
+  wq_matrix(1.0 / (k.R * T), pr, iu, iv, T, r, k.cp, J);
+  const double a = bdf2 ? 1.5 / dtp : 1.0 / dtp;
+  for (int q = 0; q < 16; q++) G[q] = G[q] / dtau + a * J[q];
+  double dQ[4];
+  if (!solve4(G, S, dQ)) return;
+  // Q0 of the sub-iteration (held in Un = A)
+  const double r0 = Un[id], u0 = Un[id + P] / r0, v0 = Un[id + 2 * P] / r0;
+  const double p0 = g1 * (Un[id + 3 * P] - 0.5 * r0 * (u0 * u0 + v0 * v0));
+  const double Q0[4] = {p0, u0, v0, p0 / (r0 * k.R)};
+  const double Qk[4] = {pr, iu, iv, T};
+  double Qn[4];
+  for (int v = 0; v < 4; v++) {
+    const double e = Qk[v] + dQ[v];
+    Qn[v] = STAGE == 1 ? e : (STAGE == 2 ? 0.75 * Q0[v] + 0.25 * e : (1.0 / 3.0) * Q0[v] + (2.0 / 3.0) * e);
+  }
+  const double rn = Qn[0] / (k.R * Qn[3]);
+  Out[id] = rn;
+  Out[id + P] = rn * Qn[1];
+  Out[id + 2 * P] = rn * Qn[2];
+  Out[id + 3 * P] = Qn[0] / (k.gamma - 1.0) + 0.5 * rn * (Qn[1] * Qn[1] + Qn[2] * Qn[2]);
 }
+
+void launch_dual_f64(const Consts &k, int stage, const double *A, const double *In, double *Out, const double *Wn,
+                     const double *Wm, const uint8_t *tag, DevState *ds, cudaStream_t s) {
+  dim3 grid((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY);
+  if (stage == 1) k_stage_f64<1, true><<<grid, 256, 0, s>>>(k, A, In, Out, Wn, Wm, tag, ds);
+  else if (stage == 2) k_stage_f64<2, true><<<grid, 256, 0, s>>>(k, A, In, Out, Wn, Wm, tag, ds);
+  else k_stage_f64<3, true><<<grid, 256, 0, s>>>(k, A, In, Out, Wn, Wm, tag, ds);
+}
+
+__global__ void k_dual_end(Consts k, DevState *ds) {
+  ds->t = ds->t + k.dt_phys;
+  ds->steps += 1;
+}
+
+void launch_dual_end(const Consts &k, DevState *ds, cudaStream_t s) { k_dual_end<<<1, 1, 0, s>>>(k, ds); }
 
 void launch_stage_f64(const Consts &k, int stage, const double *Un, const double *In, double *Out,
                       const uint8_t *tag, DevState *ds, cudaStream_t s) {
   dim3 grid((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY);
-  if (stage == 1) k_stage_f64<1><<<grid, 256, 0, s>>>(k, Un, In, Out, tag, ds);
-  else if (stage == 2) k_stage_f64<2><<<grid, 256, 0, s>>>(k, Un, In, Out, tag, ds);
-  else k_stage_f64<3><<<grid, 256, 0, s>>>(k, Un, In, Out, tag, ds);
+  if (stage == 1) k_stage_f64<1, false><<<grid, 256, 0, s>>>(k, Un, In, Out, nullptr, nullptr, tag, ds);
+  else if (stage == 2) k_stage_f64<2, false><<<grid, 256, 0, s>>>(k, Un, In, Out, nullptr, nullptr, tag, ds);
+  else k_stage_f64<3, false><<<grid, 256, 0, s>>>(k, Un, In, Out, nullptr, nullptr, tag, ds);
 }
 
 }  // namespace ibm

@@ -56,7 +56,14 @@ struct Consts {
   double Hinf;      // free-stream total enthalpy
   int bc[4];
   Motion motion;
+  int dual;         // dual time stepping (preconditioned pseudo time, BDF2 physical time)
+  int subiters;     // dual time: sub-iterations per physical step
+  double dt_phys;   // dual time: physical step
+  double cfl_tau;   // dual time: pseudo-time CFL number
 };
+
+// Bounded low-Mach preconditioning: reference velocity never below c/3.
+constexpr double UR_FLOOR = 1.0 / 3.0;
 
 // geometry arrays (device)
 struct Geom {
@@ -155,6 +162,11 @@ void launch_recon_f64(const Consts &k, double *U, const ibm_stencil *st, int cap
                       int stage, cudaStream_t s, int *nlaunch);
 void launch_stage_f64(const Consts &k, int stage, const double *Un, const double *In, double *Out,
                       const uint8_t *tag, DevState *ds, cudaStream_t s);
+// dual time: one pseudo-time stage (RK3 stage 1..3) of a sub-iteration; Q0 = iterate at the sub-iteration
+// start (held in A), Wn / Wm the states at time levels n and n-1
+void launch_dual_f64(const Consts &k, int stage, const double *A, const double *In, double *Out, const double *Wn,
+                     const double *Wm, const uint8_t *tag, DevState *ds, cudaStream_t s);
+void launch_dual_end(const Consts &k, DevState *ds, cudaStream_t s);
 
 // Compact FP32 form of an IB / ghost stencil for the FP32-bulk reconstruction
 // (built once per classification from the FP64 record).
