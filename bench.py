@@ -39,6 +39,13 @@ WORKLOADS = {
 # (each stage reads its input planes and tags once and writes its output once;
 # halos are re-read from L2/shared memory, not counted)
 BYTES_PER_CELL_STAGE = {"fp32_bulk": 179.0 / 3.0, "fp64": 259.0 / 3.0}
+# algorithmic floating-point operations per cell and stage (counted from the
+# formulas, FMA = 2): WENO5 per variable and direction 91 (x 4 x 2), LDFSS
+# 110 per face (x 2), viscous 40 per face (x 2), primitives 25, update 20
+FLOPS_PER_CELL_STAGE = 91 * 8 + 110 * 2 + 40 * 2 + 25 + 20
+# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
+def fp32_peak_tflops(sm_mhz=2070.0):
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -204,6 +211,8 @@ def run_ours(args, rank, world):
     achieved = bytes_per_launch / (stage_avg_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     traffic = _traffic("flow32.cu" if args.precision == "fp32_bulk" else "flow.cu")
+    flops_per_launch = FLOPS_PER_CELL_STAGE * spec["nx"] * spec["ny"]
+    achieved_tf = flops_per_launch / (stage_avg_ms * 1e-3) / 1e12
 
     # plain FP64 path on the same workload and GPU
     fp64 = None
@@ -217,6 +226,44 @@ def run_ours(args, rank, world):
         fp64 = {"value": v64, "ms_per_step": t64 / k64, "steps": k64,
                 "fp32_bulk_speedup": value / world / v64}
         c64.close()
+
+    # dual time (NACA0012 at 5 deg, M = 0.001, 2048x1024, FP64, 30 sub-iterations of three pseudo stages)
+    dual = None
+    if not args.skip_dual:
+        from paper_1912_11908_gb300 import workloads as W
+        dspec = W.naca0012_a5_m0001()
+        cd = ibm.Case(dspec, stream=stream.cuda_stream)
+        cd.classify()
+        dcells = _active_cells(cd)
+        cd.step(1)
+        kd = 2
+        td = _time_steps(cd, torch, flush, kd, stream)
+        nst = 3 * dspec["subiters"]
+        dual = {"workload": dspec["name"], "precision": "fp64", "subiters": dspec["subiters"],
+                "pseudo_stages_per_step": nst, "value": dcells * nst * kd / (td * 1e-3) / 1e6,
+                "unit": "Mcell-updates/s per pseudo stage", "ms_per_physical_step": td / kd, "steps": kd}
+        cd.close()
+
+    # moving body (oscillating cylinder, 1024x512, FP32-bulk): re-classification and stencils every step
+    moving = None
+    if not args.skip_moving:
+        from paper_1912_11908_gb300 import workloads as W
+        mspec = W.oscillating_cylinder_m02_re185(precision=W.PREC_FP32_BULK)
+        cm = ibm.Case(mspec, stream=stream.cuda_stream)
+        cm.classify()
+        mcells = _active_cells(cm)
+        cm.step(5)
+        km = 50
+        tm = _time_steps(cm, torch, flush, km, stream)
+        cm.profile(True)
+        cm.profile_read()
+        cm.step(10)
+        mprof = cm.profile_read()
+        cm.profile(False)
+        moving = {"workload": mspec["name"], "precision": "fp32_bulk", "value": mcells * 3 * km / (tm * 1e-3) / 1e6,
+                  "unit": "Mcell-updates/s", "ms_per_step": tm / km, "steps": km,
+                  "geometry_ms_per_step": mprof["geometry"][0] / 10, "stage_ms_per_step": mprof["residual_stage"][0] / 10}
+        cm.close()
 
     # end to end through the C ABI from pinned host memory
     state = case.state()
@@ -260,13 +307,17 @@ def run_ours(args, rank, world):
                    "precision": args.precision, "stages_per_step": 3, "time_scheme": "SSP-RK3",
                    "l2": "flushed between timed steps (512 MiB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU", "cuda_graphs": True},
-        "roofline": {"bound": "hbm", "kernel": "k_stage_f32" if args.precision == "fp32_bulk" else "k_stage_f64",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_kind, "traffic": traffic,
-                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": stage_avg_ms,
-                     "timed_launches": stage_launches},
+        "roofline": {"bound": "alu", "kernel": "k_stage_f32 (plain + body tiles)" if args.precision == "fp32_bulk"
+                     else "k_stage_f64", "achieved": achieved_tf, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp32_peak_tflops(), "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                     "flops_per_launch": flops_per_launch, "traffic": traffic, "avg_launch_ms": stage_avg_ms,
+                     "timed_launches": stage_launches,
+                     "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                  "peak_source": peak_kind, "bytes_per_launch": bytes_per_launch}},
         "kernel_ms_per_step": {g: ms / nprof for g, (ms, n) in prof.items()},
         "fp64": fp64,
+        "dual_time": dual,
+        "moving_body": moving,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -340,6 +391,8 @@ def main():
     ap.add_argument("--grid", default=None, help="override the workload grid, e.g. 3072x1536 (profiling)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-dual", action="store_true")
+    ap.add_argument("--skip-moving", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
