@@ -32,6 +32,7 @@ struct ibm_case {
   uint8_t *tile_body = nullptr;  // FP32-bulk: stage tiles that rebuild IB / ghost nodes
   int *body_tiles = nullptr;
   int body_cap = 0;
+  int box_w = 0, box_h = 0;      // cells spanned by the body's bounding box (any pose), for classification
   cudaStream_t sb = nullptr;     // FP32-bulk: stream of the body-tile kernels (forked from / joined to stream)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int cap = 0;
@@ -255,6 +256,17 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   const size_t ncell = (size_t)k.nx * k.ny;
   const size_t plane = (size_t)k.plane;
   c->cap = list_capacity(geo, gr);
+  if (geo->nverts > 0) {
+    double xmin = geo->verts[0], xmax = xmin, ymin = geo->verts[1], ymax = ymin;
+    for (int v = 1; v < geo->nverts; v++) {
+      xmin = fmin(xmin, geo->verts[2 * v]);
+      xmax = fmax(xmax, geo->verts[2 * v]);
+      ymin = fmin(ymin, geo->verts[2 * v + 1]);
+      ymax = fmax(ymax, geo->verts[2 * v + 1]);
+    }
+    c->box_w = (int)fmin((double)k.nx, ceil((xmax - xmin) / k.dx) + 4);
+    c->box_h = (int)fmin((double)k.ny, ceil((ymax - ymin) / k.dy) + 4);
+  }
   cudaError_t e = cudaSuccess;
 #define ALLOC(p, n) \
   if (e == cudaSuccess) e = dalloc(&(p), (n))
@@ -374,7 +386,7 @@ static ibm_status do_classify(ibm_case *c) {
   prof_mark(c, 4, true);
   if (c->g.nv > 0) {
     launch_pose(c->k, c->g, c->ds, s);
-    launch_classify(c->k, c->g, c->solid, c->ds, s);
+    launch_classify(c->k, c->g, c->solid, c->ds, c->box_w, c->box_h, s);
     nl += 2;
   } else {
     cudaMemsetAsync(c->solid, 0, (size_t)c->k.nx * c->k.ny, s);

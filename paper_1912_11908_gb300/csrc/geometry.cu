@@ -97,60 +97,46 @@ void launch_pose(const Consts &k, const Geom &g, DevState *ds, cudaStream_t s) {
 // Sec. 3.2: ray-casting classification of cell centres.  Ray along +x; the
 // segment A->B is crossed iff (A.y > P.y) != (B.y > P.y) and the crossing
 // abscissa A.x + (P.y-A.y)(B.x-A.x)/(B.y-A.y) lies strictly right of P; odd
-// parity = solid.  Centres outside the axis-aligned bounding box are fluid.
-// One thread per cell; vertices staged through shared memory in chunks.
+// parity = solid.  Centres outside the axis-aligned bounding box are fluid
+// (all cells are cleared first).  One warp per cell inside the box: the lanes
+// split the segments and the crossing parity is the XOR over lanes.
 // ---------------------------------------------------------------------------
-constexpr int CLS_CHUNK = 512;
-
 __global__ void __launch_bounds__(256) k_classify(Consts k, Geom g, uint8_t *__restrict__ solid,
-                                                  const DevState *__restrict__ ds) {
-  __shared__ double sx[CLS_CHUNK + 1], sy[CLS_CHUNK + 1];
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ncell = k.nx * k.ny;
-  const int i = n % k.nx, j = n / k.nx;
+                                                  const DevState *__restrict__ ds, int maxw, int maxh) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const double b0 = ds->bbox[0], b1 = ds->bbox[1], b2 = ds->bbox[2], b3 = ds->bbox[3];
+  // cell range covering the box: centres x0 + (i + 1/2) dx in [b0, b1]
+  const int ilo = max(0, (int)floor((b0 - k.x0) / k.dx - 0.5) - 1);
+  const int jlo = max(0, (int)floor((b2 - k.y0) / k.dy - 0.5) - 1);
+  if (warp >= maxw * maxh) return;
+  const int i = ilo + warp % maxw, j = jlo + warp / maxw;
+  if (i >= k.nx || j >= k.ny) return;
   const double px = k.x0 + ((double)i + 0.5) * k.dx;
   const double py = k.y0 + ((double)j + 0.5) * k.dy;
-  const double b0 = ds->bbox[0], b1 = ds->bbox[1], b2 = ds->bbox[2], b3 = ds->bbox[3];
-  const bool test = n < ncell && !(px < b0 || px > b1 || py < b2 || py > b3);
+  if (px < b0 || px > b1 || py < b2 || py > b3) return;  // stays fluid
   int odd = 0;
-  // the whole block walks the vertex list if any of its cells needs a test
-  if (__syncthreads_or(test)) {
-    for (int base = 0; base < g.nv; base += CLS_CHUNK) {
-      int cnt = min(CLS_CHUNK, g.nv - base);
-      __syncthreads();
-      for (int v = threadIdx.x; v <= cnt; v += blockDim.x) {
-        int src = base + v;
-        if (src == g.nv) src = 0;
-        if (v < cnt || src < g.nv) {
-          sx[v] = g.vx[src];
-          sy[v] = g.vy[src];
-        }
-      }
-      __syncthreads();
-      if (test) {
-        for (int e = 0; e < cnt; e++) {
-          double ax = sx[e], ay = sy[e], bx = sx[e + 1], by = sy[e + 1];
-          if ((ay > py) != (by > py)) {
-            double t1 = py - ay;
-            double t2 = bx - ax;
-            double t3 = by - ay;
-            double xint = ax + (t1 * t2) / t3;
-            if (xint > px) odd ^= 1;
-          }
-        }
-      }
+  for (int e = lane; e < g.nv; e += 32) {
+    const int e1 = (e + 1 == g.nv) ? 0 : e + 1;
+    const double ax = g.vx[e], ay = g.vy[e], bx = g.vx[e1], by = g.vy[e1];
+    if ((ay > py) != (by > py)) {
+      double t1 = py - ay;
+      double t2 = bx - ax;
+      double t3 = by - ay;
+      double xint = ax + (t1 * t2) / t3;
+      if (xint > px) odd ^= 1;
     }
   }
-  if (n < ncell) solid[n] = (uint8_t)odd;
+  odd = __popc(__ballot_sync(0xffffffffu, odd)) & 1;
+  if (lane == 0) solid[j * k.nx + i] = (uint8_t)odd;
 }
 
-void launch_classify(const Consts &k, const Geom &g, uint8_t *solid, const DevState *ds, cudaStream_t s) {
-  int ncell = k.nx * k.ny;
-  if (g.nv <= 0) {
-    cudaMemsetAsync(solid, 0, (size_t)ncell, s);
-    return;
-  }
-  k_classify<<<(ncell + 255) / 256, 256, 0, s>>>(k, g, solid, ds);
+void launch_classify(const Consts &k, const Geom &g, uint8_t *solid, const DevState *ds, int maxw, int maxh,
+                     cudaStream_t s) {
+  const int ncell = k.nx * k.ny;
+  cudaMemsetAsync(solid, 0, (size_t)ncell, s);
+  if (g.nv <= 0 || maxw <= 0 || maxh <= 0) return;
+  const long long warps = (long long)maxw * maxh;
+  k_classify<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(k, g, solid, ds, maxw, maxh);
 }
 
 // ---------------------------------------------------------------------------
@@ -287,77 +273,6 @@ void launch_tags(const Consts &k, const uint8_t *solid, uint8_t *tag, int *block
   *nlaunch += 3;
 }
 
-// ---------------------------------------------------------------------------
-// Sec. 4.1: closest feature (exhaustive, ties -> lowest segment index).
-// ---------------------------------------------------------------------------
-__device__ void closest_feature(const Geom &g, double px, double py, int *feat, int *region, double *cxo,
-                                double *cyo) {
-  double best = INFINITY;
-  const int nv = g.nv;
-  for (int kk = 0; kk < nv; kk++) {
-    int k1 = (kk + 1 == nv) ? 0 : kk + 1;
-    double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
-    double ex = bx - ax, ey = by - ay;
-    double wx = px - ax, wy = py - ay;
-    double num = wx * ex + wy * ey;
-    double den = ex * ex + ey * ey;
-    double cx, cy;
-    int f, r;
-    if (num <= 0.0) {
-      cx = ax; cy = ay; f = kk; r = IBM_REGION_VERTEX;
-    } else if (num >= den) {
-      cx = bx; cy = by; f = k1; r = IBM_REGION_VERTEX;
-    } else {
-      double t = num / den;
-      cx = ax + t * ex; cy = ay + t * ey; f = kk; r = IBM_REGION_FACE;
-    }
-    double ddx = px - cx, ddy = py - cy;
-    double d2 = ddx * ddx + ddy * ddy;
-    if (d2 < best) {
-      best = d2; *feat = f; *region = r; *cxo = cx; *cyo = cy;
-    }
-  }
-}
-
-// Sec. 4.3: boundary point on the line through the node along the local
-// normal, nearest crossing on the surface side (behind a fluid node, ahead of
-// a ghost node); closest point if the line meets no segment on that side.
-__device__ void boundary_point(const Geom &g, double px, double py, double nx, double ny, bool ghost,
-                               double ccx, double ccy, double *bx, double *by, double *xi_node, int *fallback) {
-  double best = INFINITY, bs = 0.0;
-  bool found = false;
-  const int nv = g.nv;
-  for (int kk = 0; kk < nv; kk++) {
-    int k1 = (kk + 1 == nv) ? 0 : kk + 1;
-    double ax = g.vx[kk], ay = g.vy[kk];
-    double ex = g.vx[k1] - ax, ey = g.vy[k1] - ay;
-    double den = ex * ny - ey * nx;
-    if (den == 0.0) continue;
-    double wx = px - ax, wy = py - ay;
-    double u = (wx * ny - wy * nx) / den;
-    if (u < 0.0 || u > 1.0) continue;
-    double s = (wx * ey - wy * ex) / den;
-    if (ghost ? (s < 0.0) : (s > 0.0)) continue;
-    double as = fabs(s);
-    if (as < best) {
-      best = as; bs = s; found = true;
-    }
-  }
-  if (found) {
-    *bx = px + bs * nx;
-    *by = py + bs * ny;
-    *xi_node = -bs;
-    *fallback = 0;
-  } else {
-    double ddx = px - ccx, ddy = py - ccy;
-    double d = sqrt(ddx * ddx + ddy * ddy);
-    *bx = ccx;
-    *by = ccy;
-    *xi_node = ghost ? -d : d;
-    *fallback = 1;
-  }
-}
-
 // Sec. 4.6 / Sec. 5: interpolation square around (X, Y); bilinear when all
 // four corners carry an allowed tag, inverse-distance (1/r^2) weights over
 // the allowed corners otherwise, all weight on a corner hit exactly.
@@ -412,10 +327,29 @@ __device__ int interp_square(const Consts &k, const uint8_t *__restrict__ tag, d
 constexpr unsigned ALLOW_FLUID = 1u << FLUID;
 constexpr unsigned ALLOW_FLUID_IB = (1u << FLUID) | (1u << IB);
 
-// Sec. 4.1-4.6, Sec. 5: one stencil per listed node.  One thread per entry.
+// lexicographic (value, index) minimum across a warp; every lane gets the winner's lane
+__device__ __forceinline__ int warp_argmin(double v, int idx) {
+  int src = threadIdx.x & 31;
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    const int os = __shfl_xor_sync(0xffffffffu, src, off);
+    if (ov < v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+      src = os;
+    }
+  }
+  return src;
+}
+
+// Sec. 4.1-4.6, Sec. 5: one stencil per listed node, one warp per node.  The
+// lanes split the segments of the two exhaustive searches (closest feature,
+// boundary point); the warp keeps the (distance, segment) lexicographic
+// minimum, which is the first minimum of a sequential scan.
 __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_t *__restrict__ tag,
                                                   ibm_stencil *__restrict__ st, int cap, DevState *ds) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int total = min(ds->offset[4], cap);
   if (e >= total) return;
   ibm_stencil s = st[e];
@@ -423,9 +357,38 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
   const int i = s.cell % k.nx, j = s.cell / k.nx;
   const double px = k.x0 + ((double)i + 0.5) * k.dx;
   const double py = k.y0 + ((double)j + 0.5) * k.dy;
-  int feat = 0, region = 0;
-  double ccx = 0.0, ccy = 0.0;
-  closest_feature(g, px, py, &feat, &region, &ccx, &ccy);
+  const int nv = g.nv;
+  // closest feature (Sec. 4.1)
+  double best = INFINITY, bcx = 0.0, bcy = 0.0;
+  int bseg = 0x7fffffff, bfeat = 0, breg = 0;
+  for (int kk = lane; kk < nv; kk += 32) {
+    const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
+    const double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
+    const double ex = bx - ax, ey = by - ay;
+    const double wx = px - ax, wy = py - ay;
+    const double num = wx * ex + wy * ey;
+    const double den = ex * ex + ey * ey;
+    double cx, cy;
+    int f, r;
+    if (num <= 0.0) {
+      cx = ax; cy = ay; f = kk; r = IBM_REGION_VERTEX;
+    } else if (num >= den) {
+      cx = bx; cy = by; f = k1; r = IBM_REGION_VERTEX;
+    } else {
+      const double t = num / den;
+      cx = ax + t * ex; cy = ay + t * ey; f = kk; r = IBM_REGION_FACE;
+    }
+    const double ddx = px - cx, ddy = py - cy;
+    const double d2 = ddx * ddx + ddy * ddy;
+    if (d2 < best) {
+      best = d2; bseg = kk; bfeat = f; breg = r; bcx = cx; bcy = cy;
+    }
+  }
+  int src = warp_argmin(best, bseg);
+  const int feat = __shfl_sync(0xffffffffu, bfeat, src);
+  const int region = __shfl_sync(0xffffffffu, breg, src);
+  const double ccx = __shfl_sync(0xffffffffu, bcx, src);
+  const double ccy = __shfl_sync(0xffffffffu, bcy, src);
   double nx, ny;
   if (region == IBM_REGION_FACE) {
     nx = g.snx[feat];
@@ -434,9 +397,45 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
     nx = g.vnx[feat];
     ny = g.vny[feat];
   }
+  // boundary point on the line along the local normal (Sec. 4.3)
+  const bool ghost = kind > 0;
+  double bs_best = INFINITY, bs_s = 0.0;
+  int bs_seg = 0x7fffffff;
+  for (int kk = lane; kk < nv; kk += 32) {
+    const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
+    const double ax = g.vx[kk], ay = g.vy[kk];
+    const double ex = g.vx[k1] - ax, ey = g.vy[k1] - ay;
+    const double den = ex * ny - ey * nx;
+    if (den == 0.0) continue;
+    const double wx = px - ax, wy = py - ay;
+    const double u = (wx * ny - wy * nx) / den;
+    if (u < 0.0 || u > 1.0) continue;
+    const double sv = (wx * ey - wy * ex) / den;
+    if (ghost ? (sv < 0.0) : (sv > 0.0)) continue;
+    const double as = fabs(sv);
+    if (as < bs_best) {
+      bs_best = as; bs_s = sv; bs_seg = kk;
+    }
+  }
+  src = warp_argmin(bs_best, bs_seg);
+  const double found_abs = __shfl_sync(0xffffffffu, bs_best, src);
+  const double bsv = __shfl_sync(0xffffffffu, bs_s, src);
+  if (lane != 0) return;
   double bx, by, xi_node;
   int fb;
-  boundary_point(g, px, py, nx, ny, kind > 0, ccx, ccy, &bx, &by, &xi_node, &fb);
+  if (found_abs < INFINITY) {
+    bx = px + bsv * nx;
+    by = py + bsv * ny;
+    xi_node = -bsv;
+    fb = 0;
+  } else {
+    const double ddx = px - ccx, ddy = py - ccy;
+    const double d = sqrt(ddx * ddx + ddy * ddy);
+    bx = ccx;
+    by = ccy;
+    xi_node = ghost ? -d : d;
+    fb = 1;
+  }
   double xi_probe;
   if (kind == 0) {
     xi_probe = xi_node + k.h;
@@ -474,7 +473,7 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
 void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
                      cudaStream_t s) {
   if (cap <= 0) return;
-  k_stencils<<<(cap + 127) / 128, 128, 0, s>>>(k, g, tag, st, cap, ds);
+  k_stencils<<<(unsigned)(((long long)cap * 32 + 127) / 128), 128, 0, s>>>(k, g, tag, st, cap, ds);
 }
 
 // ---------------------------------------------------------------------------
@@ -686,7 +685,7 @@ extern "C" ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *
   g.vx = s->vx;
   g.vy = s->vy;
   k_noalloc_prepare<<<1, 256, 0, st>>>(d_verts, nverts, s);
-  launch_classify(k, g, s->solid, &s->ds, st);
+  launch_classify(k, g, s->solid, &s->ds, k.nx, k.ny, st);
   const int ncell = k.nx * k.ny;
   const int nblk = (ncell + TAG_BLOCK - 1) / TAG_BLOCK;
   k_tag_count<<<nblk, TAG_BLOCK, 0, st>>>(k, s->solid, d_tags, s->blockcounts);

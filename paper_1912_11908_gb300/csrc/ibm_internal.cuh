@@ -147,7 +147,9 @@ __device__ inline void motion_at(const Motion &m, double t, double X[2], double 
 // ---- launchers (geometry.cu) ----
 void launch_normals(int nv, const double *v, double *snx, double *sny, double *vnx, double *vny, cudaStream_t s);
 void launch_pose(const Consts &k, const Geom &g, DevState *ds, cudaStream_t s);
-void launch_classify(const Consts &k, const Geom &g, uint8_t *solid, const DevState *ds, cudaStream_t s);
+// maxw x maxh: upper bound (cells) of the body's bounding box for any pose
+void launch_classify(const Consts &k, const Geom &g, uint8_t *solid, const DevState *ds, int maxw, int maxh,
+                     cudaStream_t s);
 void launch_tags(const Consts &k, const uint8_t *solid, uint8_t *tag, int *blockcounts, DevState *ds, int cap,
                  ibm_stencil *st, cudaStream_t s, int *nlaunch);
 void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
