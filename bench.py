@@ -29,6 +29,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the request loop runs up to --serve-slots cases on their own streams: give them
+# that many hardware work queues (read when the CUDA context is created)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 WORKLOADS = {
     "wedge_768x384": "wedge_m2_re1e4",
@@ -265,6 +268,19 @@ def run_ours(args, rank, world):
                   "geometry_ms_per_step": mprof["geometry"][0] / 10, "stage_ms_per_step": mprof["residual_stage"][0] / 10}
         cm.close()
 
+    # serving mix through the request loop: Poisson arrivals (latency) and all at once (throughput)
+    serving = None
+    if not args.skip_serving and rank == 0:
+        from paper_1912_11908_gb300 import workloads as W
+        mix0 = W.serving_mix(args.serve_requests)
+        serving = {"workload": "serving mix: %d seeded requests (cylinder / NACA00xx / wedge, static or oscillating, "
+                               "M 0.001-2, Re 40-1e4, grids 64x64-1024x512, FP32-bulk SSP-RK3, %d steps each), "
+                               "Poisson arrivals mean 50 ms" % (args.serve_requests, mix0[0]["nsteps"]),
+                   "slots": args.serve_slots, "steps_per_chunk": args.serve_chunk,
+                   "memory_budget": "80% of free device memory",
+                   "poisson": run_serving(ibm, W, args.serve_requests, args.serve_slots, args.serve_chunk, False),
+                   "burst": run_serving(ibm, W, args.serve_requests, args.serve_slots, args.serve_chunk, True)}
+
     # end to end through the C ABI from pinned host memory
     state = case.state()
     host = torch.empty(state.shape, dtype=torch.float64, pin_memory=True)
@@ -318,6 +334,7 @@ def run_ours(args, rank, world):
         "fp64": fp64,
         "dual_time": dual,
         "moving_body": moving,
+        "serving": serving,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -328,6 +345,58 @@ def run_ours(args, rank, world):
     case.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_serving(ibm, W, n, slots, chunk, burst):
+    """The seeded serving mix through the native request loop (ibm_server_*).
+
+    Poisson mode submits each request when its arrival time has passed;
+    burst mode submits all of them at once.  Latency (time to solution) runs
+    from the arrival to the retirement of the request; throughput counts grid
+    cells x 3 stages x steps of all requests over the span from the first
+    arrival to the last retirement.
+    """
+    reqs = W.serving_mix(n)
+    srv = ibm.Server(max_active=slots, steps_per_chunk=chunk)
+    ids, lag = {}, {}
+    k = 0
+    max_running = 0
+    passes = 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while k < n and (burst or reqs[k]["arrival_s"] <= now):
+            rid = srv.submit(reqs[k]["spec"], reqs[k]["nsteps"])
+            ids[rid] = k
+            lag[rid] = 0.0 if burst else max(0.0, (time.perf_counter() - t0) - reqs[k]["arrival_s"])
+            k += 1
+        na, npend = srv.progress()
+        passes += 1
+        max_running = max(max_running, na)
+        if k == n and na == 0 and npend == 0:
+            break
+        if na == 0 and npend == 0:
+            time.sleep(max(0.0, reqs[k]["arrival_s"] - (time.perf_counter() - t0)))
+    span = time.perf_counter() - t0 - (0.0 if burst else reqs[0]["arrival_s"])
+    lat, work, failed = [], 0, 0
+    for rid, kk in ids.items():
+        r = srv.poll(rid)
+        if r["state"] != ibm.REQ_DONE:
+            failed += 1
+            continue
+        lat.append(r["finish_s"] - r["submit_s"] + lag[rid])
+        sp = reqs[kk]["spec"]
+        work += sp["nx"] * sp["ny"] * 3 * r["steps_done"]
+    srv.close()
+    lat.sort()
+
+    def pct(q):
+        return lat[max(0, min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1))] * 1e3 if lat else None
+
+    return {"requests": n, "failed": failed, "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": pct(1.0),
+            "mean_ms": statistics.fmean(lat) * 1e3 if lat else None, "span_s": span,
+            "value": work / span / 1e6, "unit": "Mcell-updates/s (grid cells x stages)",
+            "max_running": max_running, "loop_passes": passes}
 
 
 def cpu_baseline(args, cells_gpu=None, sample_s=10.0, max_steps=400):
@@ -393,6 +462,10 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-dual", action="store_true")
     ap.add_argument("--skip-moving", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-slots", type=int, default=32)
+    ap.add_argument("--serve-chunk", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -230,6 +230,64 @@ const char *ibm_last_error(void);
 ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, int nverts, uint8_t *d_tags,
                                  int32_t *d_cells, int32_t capacity, int32_t *d_counts, void *cuda_stream);
 
+/* Request loop (continuous batching of many cases on one GPU).  (The paper
+ * solves one configuration at a time and has no counterpart; this is a
+ * library facility built on the calls above.)
+ *
+ * A server queues solve requests -- body, grid, flow, motion and a number of
+ * explicit steps -- and admits them in arrival order while fewer than
+ * max_active cases are running and the device bytes of the running cases
+ * (ibm_case_device_bytes) plus the next request's stay within the budget.
+ * Each admitted case owns its device state, tags and lists and a stream of
+ * its own; it is classified once and advanced in chunks of steps_per_chunk
+ * steps replayed from its CUDA graph, so the kernels of all running cases
+ * overlap on the device.  A case that has taken all its steps is retired:
+ * its forces and time are read, its device memory is freed and the slot
+ * goes to the next waiting request.  Cases share nothing on the device, so
+ * a request gives the same result alone and in any mix.
+ *
+ * The server is driven by the caller's thread: ibm_server_progress does one
+ * non-blocking pass (retire finished cases, admit waiting requests, enqueue
+ * the next chunk of every case whose previous chunk is done).  Call it in a
+ * loop until it reports no running and no waiting request.  One host thread
+ * at a time per server; cases are created on the current device. */
+typedef struct ibm_server ibm_server;
+
+enum { IBM_REQ_PENDING = 0, IBM_REQ_RUNNING = 1, IBM_REQ_DONE = 2, IBM_REQ_FAILED = 3 };
+
+typedef struct {
+  int64_t id;
+  int32_t state;      /* IBM_REQ_* */
+  int32_t status;     /* ibm_status of the request (IBM_OK unless FAILED) */
+  int64_t steps_done; /* steps enqueued for the case */
+  double t;           /* simulated time reached */
+  double forces[4];   /* as ibm_forces, at the end of the last step */
+  double submit_s;    /* host times in seconds since ibm_server_create: */
+  double start_s;     /*   admission (case created and classified) */
+  double finish_s;    /*   retirement (result read back) */
+} ibm_result;
+
+/* device_bytes_budget = 0: 80 % of the device memory free at creation.
+ * max_active >= 1, steps_per_chunk >= 1. */
+ibm_status ibm_server_create(size_t device_bytes_budget, int max_active, int steps_per_chunk, ibm_server **out);
+
+/* Queue a request; the arguments are validated and copied (the vertices too).
+ * IBM_ENOMEM if the case alone exceeds the budget.  *id receives a positive
+ * request id. */
+ibm_status ibm_server_submit(ibm_server *s, const ibm_geometry *geometry, const ibm_grid *grid, const ibm_flow *flow,
+                             const ibm_motion *motion, int nsteps, int64_t *id);
+
+/* One non-blocking pass of the loop; *n_active / *n_pending (either may be
+ * NULL) receive the running and waiting request counts after the pass. */
+ibm_status ibm_server_progress(ibm_server *s, int *n_active, int *n_pending);
+
+/* Copy the current record of a request. */
+ibm_status ibm_server_poll(ibm_server *s, int64_t id, ibm_result *out);
+
+/* Wait for the running cases, retire them as failed (IBM_ESTATE) and free
+ * every resource of the server.  NULL is a no-op. */
+ibm_status ibm_server_destroy(ibm_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "ibm_internal.cuh"
 
@@ -38,7 +39,9 @@ struct ibm_case {
   int cap = 0;
   bool dt_valid = false;      // FP32-bulk static body: dt of the next step is already in DevState
   DevState *ds = nullptr;
-  DevState *hds = nullptr;  // pinned host mirror for read-backs
+  DevState *hds = nullptr;  // host mirror for read-backs
+  char *arena = nullptr;    // every device buffer above except stage64, carved from one stream-ordered allocation
+  size_t arena_bytes = 0;
   bool classified = false;
   bool own_stream = false;
   long long launches = 0;
@@ -157,59 +160,55 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
   return IBM_OK;
 }
 
-extern "C" size_t ibm_case_device_bytes(const ibm_geometry *geo, const ibm_grid *gr, const ibm_flow *fl,
-                                        const ibm_motion *mo) {
-  if (validate(geo, gr, fl, mo) != IBM_OK) return 0;
-  size_t plane = pitch_of(gr->nx) * (size_t)(gr->ny + 2 * NG);
-  size_t ncell = (size_t)gr->nx * gr->ny;
-  size_t b = 3 * 4 * plane * sizeof(double);
-  if (fl->precision == IBM_PREC_FP32_BULK) b = 4 * plane * sizeof(double) + 3 * 4 * plane * sizeof(float);
-  b += 2 * ncell + ((ncell + 1023) / 1024) * 16 + (size_t)list_capacity(geo, gr) * sizeof(ibm_stencil);
-  b += 7 * (size_t)geo->nverts * 2 * sizeof(double) + sizeof(DevState);
-  return b;
-}
-
-static void free_case(ibm_case *c) {
-  if (!c) return;
-  void *ptrs[] = {c->Wn, c->Wm, c->vref, c->vx, c->vy, c->snx, c->sny, c->vnx, c->vny, c->A, c->B, c->C, c->M, c->F1,
-                  c->F2, c->stage64, c->solid, c->tag, c->blockcounts, c->st, c->rst, c->sid, c->tile_body,
-                  c->body_tiles, c->ds};
-  for (void *p : ptrs)
-    if (p) cudaFree(p);
-  if (c->hds) cudaFreeHost(c->hds);
-  if (c->graph) cudaGraphExecDestroy(c->graph);
-  for (int q = 0; q < ibm_case::NEV; q++)
-    if (c->ev[q]) cudaEventDestroy(c->ev[q]);
-  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
-  if (c->sb) cudaStreamDestroy(c->sb);
-  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-  delete c;
-}
-
-template <typename T>
-static cudaError_t dalloc(T **p, size_t n) {
-  return cudaMalloc((void **)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
-}
-
-extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *gr, const ibm_flow *fl,
-                                      const ibm_motion *mo, void *stream, ibm_case **out) {
-  if (!out) return fail(IBM_EINVAL, "out is NULL");
-  *out = nullptr;
-  ibm_status st = validate(geo, gr, fl, mo);
-  if (st != IBM_OK) return st;
-  ibm_case *c = new (std::nothrow) ibm_case();
-  if (!c) return fail(IBM_ENOMEM, "host allocation failed");
-  cudaGetDevice(&c->device);
-  c->stream = (cudaStream_t)stream;
-  if (!c->stream) {
-    if (cudaStreamCreate(&c->stream) != cudaSuccess) {
-      delete c;
-      cudaGetLastError();
-      return fail(IBM_ECUDA, "stream creation failed");
+// Assign every device buffer of the case an offset in one allocation starting
+// at base (NULL: only count) and return the total size.  Buffers start on
+// 256-byte boundaries.
+static size_t carve(ibm_case *c, char *base) {
+  const Consts &k = c->k;
+  const size_t ncell = (size_t)k.nx * k.ny, plane = (size_t)k.plane;
+  const size_t nv = c->g.nv > 0 ? (size_t)c->g.nv : 1;
+  size_t off = 0;
+  auto take = [&](auto **p, size_t n) {
+    using T = typename std::remove_reference<decltype(**p)>::type;
+    *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += (n * sizeof(T) + 255) & ~(size_t)255;
+  };
+  take(&c->vref, 2 * nv);
+  take(&c->vx, nv);
+  take(&c->vy, nv);
+  take(&c->snx, nv);
+  take(&c->sny, nv);
+  take(&c->vnx, nv);
+  take(&c->vny, nv);
+  take(&c->A, 4 * plane);
+  if (c->precision == IBM_PREC_FP64) {
+    take(&c->B, 4 * plane);
+    take(&c->C, 4 * plane);
+    if (k.dual) {
+      take(&c->Wn, 4 * plane);
+      take(&c->Wm, 4 * plane);
     }
-    c->own_stream = true;
+  } else {
+    take(&c->M, 4 * plane);
+    take(&c->F1, 4 * plane);
+    take(&c->F2, 4 * plane);
+    take(&c->rst, (size_t)(c->cap > 0 ? c->cap : 1));
+    take(&c->sid, ncell);
+    take(&c->tile_body, (size_t)stage_tiles(k));
+    take(&c->body_tiles, (size_t)(c->body_cap > 0 ? c->body_cap : 1));
   }
+  take(&c->solid, ncell);
+  take(&c->tag, ncell);
+  take(&c->blockcounts, 4 * ((ncell + 1023) / 1024));
+  take(&c->st, (size_t)(c->cap > 0 ? c->cap : 1));
+  take(&c->ds, 1);
+  return off;
+}
+
+// Host-side set-up of a case from validated arguments: constants, list and
+// tile capacities, the body's bounding-box extent in cells.
+static void init_case(ibm_case *c, const ibm_geometry *geo, const ibm_grid *gr, const ibm_flow *fl,
+                      const ibm_motion *mo) {
   c->precision = fl->precision;
   Consts &k = c->k;
   k.nx = gr->nx;
@@ -251,11 +250,9 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   k.subiters = fl->subiters;
   k.dt_phys = fl->dt_phys;
   k.cfl_tau = fl->cfl_tau;
-
-  const int nv = geo->nverts;
-  const size_t ncell = (size_t)k.nx * k.ny;
-  const size_t plane = (size_t)k.plane;
+  c->g.nv = geo->nverts;
   c->cap = list_capacity(geo, gr);
+  if (c->precision == IBM_PREC_FP32_BULK) c->body_cap = body_tile_capacity(geo, gr, stage_tiles(k));
   if (geo->nverts > 0) {
     double xmin = geo->verts[0], xmax = xmin, ymin = geo->verts[1], ymax = ymin;
     for (int v = 1; v < geo->nverts; v++) {
@@ -267,41 +264,84 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
     c->box_w = (int)fmin((double)k.nx, ceil((xmax - xmin) / k.dx) + 4);
     c->box_h = (int)fmin((double)k.ny, ceil((ymax - ymin) / k.dy) + 4);
   }
-  cudaError_t e = cudaSuccess;
-#define ALLOC(p, n) \
-  if (e == cudaSuccess) e = dalloc(&(p), (n))
-  ALLOC(c->vref, 2 * (size_t)(nv > 0 ? nv : 1));
-  ALLOC(c->vx, (size_t)(nv > 0 ? nv : 1));
-  ALLOC(c->vy, (size_t)(nv > 0 ? nv : 1));
-  ALLOC(c->snx, (size_t)(nv > 0 ? nv : 1));
-  ALLOC(c->sny, (size_t)(nv > 0 ? nv : 1));
-  ALLOC(c->vnx, (size_t)(nv > 0 ? nv : 1));
-  ALLOC(c->vny, (size_t)(nv > 0 ? nv : 1));
-  ALLOC(c->A, 4 * plane);
-  if (c->precision == IBM_PREC_FP64) {
-    ALLOC(c->B, 4 * plane);
-    ALLOC(c->C, 4 * plane);
-    if (k.dual) {
-      ALLOC(c->Wn, 4 * plane);
-      ALLOC(c->Wm, 4 * plane);
-    }
-  } else {
-    ALLOC(c->M, 4 * plane);
-    ALLOC(c->F1, 4 * plane);
-    ALLOC(c->F2, 4 * plane);
-    ALLOC(c->rst, (size_t)(c->cap > 0 ? c->cap : 1));
-    ALLOC(c->sid, ncell);
-    c->body_cap = body_tile_capacity(geo, gr, stage_tiles(k));
-    ALLOC(c->tile_body, (size_t)stage_tiles(k));
-    ALLOC(c->body_tiles, (size_t)(c->body_cap > 0 ? c->body_cap : 1));
+}
+
+extern "C" size_t ibm_case_device_bytes(const ibm_geometry *geo, const ibm_grid *gr, const ibm_flow *fl,
+                                        const ibm_motion *mo) {
+  if (validate(geo, gr, fl, mo) != IBM_OK) return 0;
+  ibm_case *c = new (std::nothrow) ibm_case();
+  if (!c) {
+    fail(IBM_ENOMEM, "host allocation failed");
+    return 0;
   }
-  ALLOC(c->solid, ncell);
-  ALLOC(c->tag, ncell);
-  ALLOC(c->blockcounts, 4 * ((ncell + 1023) / 1024));
-  ALLOC(c->st, (size_t)(c->cap > 0 ? c->cap : 1));
-  ALLOC(c->ds, 1);
-#undef ALLOC
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hds, sizeof(DevState));
+  init_case(c, geo, gr, fl, mo);
+  size_t b = carve(c, nullptr);
+  delete c;
+  return b;
+}
+
+// Stream-ordered release: nothing here waits for the device, so cases can be
+// retired while other cases run.
+static void free_case(ibm_case *c) {
+  if (!c) return;
+  if (c->stage64) cudaFreeAsync(c->stage64, c->stream);
+  if (c->arena) cudaFreeAsync(c->arena, c->stream);
+  delete c->hds;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (int q = 0; q < ibm_case::NEV; q++)
+    if (c->ev[q]) cudaEventDestroy(c->ev[q]);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->sb) cudaStreamDestroy(c->sb);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+__global__ void k_fill(double *p, size_t n, double v0, double v1, double v2, double v3) {
+  const size_t q = n / 4;
+  for (size_t m = blockIdx.x * (size_t)blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = m / q;
+    p[m] = v == 0 ? v0 : v == 1 ? v1 : v == 2 ? v2 : v3;
+  }
+}
+
+// the four planes of p set to the four values (n = 4 planes)
+static cudaError_t fill4(double *p, size_t n, const double *v, cudaStream_t s) {
+  k_fill<<<4 * 152, 256, 0, s>>>(p, n, v[0], v[1], v[2], v[3]);
+  return cudaGetLastError();
+}
+
+extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *gr, const ibm_flow *fl,
+                                      const ibm_motion *mo, void *stream, ibm_case **out) {
+  if (!out) return fail(IBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  ibm_status st = validate(geo, gr, fl, mo);
+  if (st != IBM_OK) return st;
+  ibm_case *c = new (std::nothrow) ibm_case();
+  if (!c) return fail(IBM_ENOMEM, "host allocation failed");
+  cudaGetDevice(&c->device);
+  c->stream = (cudaStream_t)stream;
+  if (!c->stream) {
+    if (cudaStreamCreate(&c->stream) != cudaSuccess) {
+      delete c;
+      cudaGetLastError();
+      return fail(IBM_ECUDA, "stream creation failed");
+    }
+    c->own_stream = true;
+  }
+  init_case(c, geo, gr, fl, mo);
+  const Consts &k = c->k;
+  const int nv = geo->nverts;
+  const size_t ncell = (size_t)k.nx * k.ny;
+  const size_t plane = (size_t)k.plane;
+  cudaStream_t s = c->stream;
+
+  c->arena_bytes = carve(c, nullptr);
+  cudaError_t e = cudaMallocAsync((void **)&c->arena, c->arena_bytes, s);
+  if (e == cudaSuccess) carve(c, c->arena);
+  else c->arena = nullptr;
+  c->hds = new (std::nothrow) DevState();
+  if (e == cudaSuccess && !c->hds) e = cudaErrorMemoryAllocation;
   if (e == cudaSuccess && c->precision == IBM_PREC_FP32_BULK) {
     // body tiles are on the critical path of every stage: give their stream the highest priority
     int prio_lo = 0, prio_hi = 0;
@@ -315,7 +355,6 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
     cudaGetLastError();
     return fail(IBM_ENOMEM, "device allocation failed: %s", cudaGetErrorString(e));
   }
-  c->g.nv = nv;
   c->g.vref = c->vref;
   c->g.vx = c->vx;
   c->g.vy = c->vy;
@@ -324,7 +363,6 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   c->g.vnx = c->vnx;
   c->g.vny = c->vny;
 
-  cudaStream_t s = c->stream;
   ibm_status rs = IBM_OK;
   do {
     if (nv > 0) {
@@ -340,37 +378,23 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
       c->hds->dt = k.dual ? k.dt_phys : k.dt_fixed;
       c->hds->dtf = (float)c->hds->dt;
     }
+    // (the copy from pageable memory is staged before the call returns)
     if (cudaMemcpyAsync(c->ds, c->hds, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(c->tag, 0, ncell, s) != cudaSuccess) {
       rs = fail(IBM_ECUDA, "state initialisation failed");
       break;
     }
-    // free stream everywhere (halo included)
-    double *hU = new (std::nothrow) double[plane];
-    if (!hU) {
-      rs = fail(IBM_ENOMEM, "host allocation failed");
-      break;
-    }
-    const bool pert = c->precision == IBM_PREC_FP32_BULK;  // the FP64 state then holds dU = U - U_inf
-    for (int v = 0; v < 4 && rs == IBM_OK; v++) {
-      for (size_t m = 0; m < plane; m++) hU[m] = pert ? 0.0 : k.Uinf[v];
-      if (cudaMemcpy(c->A + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-        rs = fail(IBM_ECUDA, "state upload failed");
-      if (c->B && cudaMemcpy(c->B + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-        rs = fail(IBM_ECUDA, "state upload failed");
-      if (c->C && cudaMemcpy(c->C + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-        rs = fail(IBM_ECUDA, "state upload failed");
-      for (double *w : {c->Wn, c->Wm})
-        if (w && cudaMemcpy(w + v * plane, hU, plane * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-          rs = fail(IBM_ECUDA, "state upload failed");
-    }
-    delete[] hU;
+    // free stream everywhere (halo included); the FP32-bulk FP64 state holds dU = U - U_inf
+    const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+    const double *u0 = c->precision == IBM_PREC_FP32_BULK ? zero : k.Uinf;
+    for (double *w : {c->A, c->B, c->C, c->Wn, c->Wm})
+      if (w && fill4(w, 4 * plane, u0, s) != cudaSuccess) rs = fail(IBM_ECUDA, "state initialisation failed");
     if (rs != IBM_OK) break;
     if (c->M) {
       for (float *p : {c->M, c->F1, c->F2})
         if (cudaMemsetAsync(p, 0, 4 * plane * sizeof(float), s) != cudaSuccess) rs = fail(IBM_ECUDA, "memset failed");
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess) rs = fail(IBM_ECUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+    c->launches += (c->B ? 3 : 1) + (c->Wn ? 2 : 0);
   } while (0);
   if (rs != IBM_OK) {
     free_case(c);
@@ -582,8 +606,8 @@ extern "C" ibm_status ibm_profile_read(ibm_case *c, double *ms, int64_t *launche
 }
 
 static ibm_status sync_and_check(ibm_case *c) {
+  CU(cudaMemcpyAsync(c->hds, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  CU(cudaMemcpy(c->hds, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost));
   if (c->hds->err & ERR_CAPACITY)
     return fail(IBM_ECAPACITY, "IB/ghost list overflow: %d nodes, capacity %d", c->hds->offset[4], c->cap);
   if (c->hds->err & ERR_STENCIL) return fail(IBM_ESTENCIL, "an IB/ghost node found no valid interpolation corner");
@@ -601,7 +625,7 @@ static ibm_status copy_state(ibm_case *c, double *dst, const double *src, bool t
   double *base = c->A;
   if (to_user && c->precision == IBM_PREC_FP32_BULK) {
     // the FP64 state holds dU; hand out absolute conserved variables
-    if (!c->stage64) CU(cudaMalloc((void **)&c->stage64, 4 * (size_t)k.plane * sizeof(double)));
+    if (!c->stage64) CU(cudaMallocAsync((void **)&c->stage64, 4 * (size_t)k.plane * sizeof(double), c->stream));
     launch_pert_to_abs64(k, c->A, c->stage64, c->stream);
     c->launches++;
     base = c->stage64;
@@ -657,15 +681,19 @@ extern "C" ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t byt
     case IBM_TIME: {
       if (bytes < 2 * sizeof(double)) return fail(IBM_EINVAL, "dst too small");
       double tt[2] = {h.t, h.dt};
-      if (dst_on_device) CU(cudaMemcpy(dst, tt, sizeof tt, cudaMemcpyHostToDevice));
-      else std::memcpy(dst, tt, sizeof tt);
+      if (dst_on_device) {
+        CU(cudaMemcpyAsync(dst, tt, sizeof tt, cudaMemcpyHostToDevice, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+      } else std::memcpy(dst, tt, sizeof tt);
       break;
     }
     case IBM_STEPS: {
       if (bytes < sizeof(int64_t)) return fail(IBM_EINVAL, "dst too small");
       int64_t n = h.steps;
-      if (dst_on_device) CU(cudaMemcpy(dst, &n, sizeof n, cudaMemcpyHostToDevice));
-      else std::memcpy(dst, &n, sizeof n);
+      if (dst_on_device) {
+        CU(cudaMemcpyAsync(dst, &n, sizeof n, cudaMemcpyHostToDevice, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+      } else std::memcpy(dst, &n, sizeof n);
       break;
     }
     default:

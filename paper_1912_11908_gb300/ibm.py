@@ -50,9 +50,18 @@ STENCIL_DTYPE = np.dtype([
     ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (4,)),
 ])
 
+class ibm_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("steps_done", ctypes.c_int64), ("t", ctypes.c_double), ("forces", ctypes.c_double * 4),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
+
+
 EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state", "ibm_forces",
            "ibm_sync", "ibm_destroy_case", "ibm_case_device_bytes", "ibm_launch_count", "ibm_last_error",
-           "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs", "ibm_tag_nodes_noalloc"]
+           "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs", "ibm_tag_nodes_noalloc",
+           "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
+           "ibm_server_destroy"]
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 PROFILE_GROUPS = ["residual_stage", "ib_reconstruct", "domain_halo", "time_step", "geometry", "step_end"]
 
 
@@ -89,6 +98,16 @@ def load():
     L.ibm_use_graphs.argtypes = [vp, ip]
     L.ibm_tag_nodes_noalloc.argtypes = [ctypes.POINTER(ibm_grid), vp, ip, vp, vp, ctypes.c_int32, vp, vp]
     L.ibm_tag_nodes_noalloc.restype = ip
+    L.ibm_server_create.argtypes = [sz, ip, ip, ctypes.POINTER(vp)]
+    L.ibm_server_submit.argtypes = [vp, ctypes.POINTER(ibm_geometry), ctypes.POINTER(ibm_grid),
+                                    ctypes.POINTER(ibm_flow), ctypes.POINTER(ibm_motion), ip,
+                                    ctypes.POINTER(ctypes.c_int64)]
+    L.ibm_server_progress.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.ibm_server_poll.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ibm_result)]
+    L.ibm_server_destroy.argtypes = [vp]
+    for name in ("ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
+                 "ibm_server_destroy"):
+        getattr(L, name).restype = ip
     for name in ("ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state",
                  "ibm_forces", "ibm_sync", "ibm_destroy_case", "ibm_profile_enable", "ibm_profile_read",
                  "ibm_use_graphs"):
@@ -257,3 +276,58 @@ class Case:
         _check(lib().ibm_profile_read(self.h, ms.ctypes.data_as(ctypes.c_void_p), cnt.ctypes.data_as(ctypes.c_void_p),
                                       n))
         return {g: (float(ms[k]), int(cnt[k])) for k, g in enumerate(PROFILE_GROUPS)}
+
+
+class Server:
+    """Request loop over many cases on the current CUDA device (see ibm_server_* in include/ibm.h).
+
+    ``submit`` queues a case spec with a step count; ``progress`` runs one
+    non-blocking pass of the native loop (retire, admit, enqueue); ``poll``
+    returns the request's record as a dict.
+    """
+
+    def __init__(self, device_bytes_budget=0, max_active=16, steps_per_chunk=10):
+        h = ctypes.c_void_p()
+        _check(lib().ibm_server_create(int(device_bytes_budget), int(max_active), int(steps_per_chunk),
+                                       ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().ibm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, spec, nsteps):
+        verts, geo, gr, fl, mo = marshal(spec)
+        rid = ctypes.c_int64()
+        _check(lib().ibm_server_submit(self.h, ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl),
+                                       ctypes.byref(mo), int(nsteps), ctypes.byref(rid)))
+        return rid.value
+
+    def progress(self):
+        na, npend = ctypes.c_int(), ctypes.c_int()
+        _check(lib().ibm_server_progress(self.h, ctypes.byref(na), ctypes.byref(npend)))
+        return na.value, npend.value
+
+    def poll(self, rid):
+        r = ibm_result()
+        _check(lib().ibm_server_poll(self.h, int(rid), ctypes.byref(r)))
+        return dict(id=r.id, state=r.state, status=r.status, steps_done=r.steps_done, t=r.t,
+                    forces=np.array(r.forces[:], np.float64), submit_s=r.submit_s, start_s=r.start_s,
+                    finish_s=r.finish_s)
+
+    def drain(self, sleep_s=0.0):
+        """Run the loop until no request is running or waiting."""
+        import time
+        while True:
+            na, npend = self.progress()
+            if na == 0 and npend == 0:
+                return
+            if sleep_s:
+                time.sleep(sleep_s)

@@ -110,8 +110,12 @@ def random_polygon(rng, n, center=(0.0, 0.0), rmin=0.3, rmax=1.0):
     return np.stack([center[0] + r * np.cos(a), center[1] + r * np.sin(a)], axis=1)
 
 
-def serving_mix(n=512, seed=20191224, mean_interarrival_s=0.05):
-    """Request mix for the batched loop: bodies, motions, Mach, Re and grids drawn from a seed."""
+def serving_mix(n=512, seed=20191224, mean_interarrival_s=0.05, nsteps=200):
+    """Request mix for the request loop: bodies, motions, Mach, Re and grids drawn from a seed.
+
+    Each entry: arrival time (Poisson process), case spec (FP32-bulk, SSP-RK3)
+    and the number of explicit steps the request asks for.
+    """
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(mean_interarrival_s, n))
     reqs = []
@@ -130,9 +134,10 @@ def serving_mix(n=512, seed=20191224, mean_interarrival_s=0.05):
             verts = naca00xx(float(rng.uniform(0.09, 0.15)), 400, 0.0)
         else:
             verts = wedge(float(rng.uniform(10.0, 20.0)))
-        aspect = gy / gx
-        dom = (-4.0, 8.0, -6.0 * aspect, 6.0 * aspect)
-        reqs.append(dict(arrival_s=float(t[k]), spec=case_spec(
+        # square cells; at least 12 body lengths along x and 3 across, body 4 lengths from the inflow
+        h = max(12.0 / gx, 3.0 / gy)
+        dom = (-4.0, -4.0 + gx * h, -0.5 * gy * h, 0.5 * gy * h)
+        reqs.append(dict(arrival_s=float(t[k]), nsteps=int(nsteps), spec=case_spec(
             verts, gx, gy, dom, mach, re, FAR if mach < 1.0 else SUPERSONIC,
             motion=MOTION_SIN if osc else MOTION_STATIC, amp=(0.0, 0.2) if osc else (0.0, 0.0),
             freq=0.16 if osc else 0.0, precision=PREC_FP32_BULK, name="req%03d" % k)))
