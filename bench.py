@@ -278,8 +278,14 @@ def run_ours(args, rank, world):
                                "Poisson arrivals mean 50 ms" % (args.serve_requests, mix0[0]["nsteps"]),
                    "slots": args.serve_slots, "steps_per_chunk": args.serve_chunk,
                    "memory_budget": "80% of free device memory",
-                   "poisson": run_serving(ibm, W, args.serve_requests, args.serve_slots, args.serve_chunk, False),
-                   "burst": run_serving(ibm, W, args.serve_requests, args.serve_slots, args.serve_chunk, True)}
+                   "modes": {"batched": "size-class groups, one plain-tile and one body-tile launch per RK stage over "
+                                        "the group's block table, group step in a CUDA graph, autotuned schedule",
+                             "streams": "one stream and one step graph per case"}}
+        bm = ibm.SERVE_BATCHED | ibm.SERVE_AUTOTUNE
+        for name, mode in (("batched", bm), ("streams", 0)):
+            serving[name] = {
+                "poisson": run_serving(ibm, W, args.serve_requests, args.serve_slots, args.serve_chunk, False, mode),
+                "burst": run_serving(ibm, W, args.serve_requests, args.serve_slots, args.serve_chunk, True, mode)}
 
     # end to end through the C ABI from pinned host memory
     state = case.state()
@@ -322,7 +328,8 @@ def run_ours(args, rank, world):
         "config": {"workload": spec["name"], "grid": [spec["nx"], spec["ny"]], "active_cells": cells,
                    "precision": args.precision, "stages_per_step": 3, "time_scheme": "SSP-RK3",
                    "l2": "flushed between timed steps (512 MiB write outside the events)",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "cuda_graphs": True},
+                   "parallelism": "replicas" if world > 1 else "single GPU", "cuda_graphs": True,
+                   "autotuned_plain_variant": case.tuning()},
         "roofline": {"bound": "alu", "kernel": "k_stage_f32 (plain + body tiles)" if args.precision == "fp32_bulk"
                      else "k_stage_f64", "achieved": achieved_tf, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
                      "frac": achieved_tf / fp32_peak_tflops(), "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
@@ -347,7 +354,7 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
-def run_serving(ibm, W, n, slots, chunk, burst):
+def run_serving(ibm, W, n, slots, chunk, burst, mode):
     """The seeded serving mix through the native request loop (ibm_server_*).
 
     Poisson mode submits each request when its arrival time has passed;
@@ -357,7 +364,7 @@ def run_serving(ibm, W, n, slots, chunk, burst):
     arrival to the last retirement.
     """
     reqs = W.serving_mix(n)
-    srv = ibm.Server(max_active=slots, steps_per_chunk=chunk)
+    srv = ibm.Server(max_active=slots, steps_per_chunk=chunk, mode=mode)
     ids, lag = {}, {}
     k = 0
     max_running = 0
@@ -378,6 +385,7 @@ def run_serving(ibm, W, n, slots, chunk, burst):
         if na == 0 and npend == 0:
             time.sleep(max(0.0, reqs[k]["arrival_s"] - (time.perf_counter() - t0)))
     span = time.perf_counter() - t0 - (0.0 if burst else reqs[0]["arrival_s"])
+    stats = srv.stats()
     lat, work, failed = [], 0, 0
     for rid, kk in ids.items():
         r = srv.poll(rid)
@@ -396,7 +404,7 @@ def run_serving(ibm, W, n, slots, chunk, burst):
     return {"requests": n, "failed": failed, "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": pct(1.0),
             "mean_ms": statistics.fmean(lat) * 1e3 if lat else None, "span_s": span,
             "value": work / span / 1e6, "unit": "Mcell-updates/s (grid cells x stages)",
-            "max_running": max_running, "loop_passes": passes}
+            "max_running": max_running, "loop_passes": passes, "loop_stats": stats}
 
 
 def cpu_baseline(args, cells_gpu=None, sample_s=10.0, max_steps=400):

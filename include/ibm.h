@@ -138,7 +138,9 @@ enum {
   IBM_LIST_COUNTS = 2,  /* int32_t[4]: #IB, #G1, #G2, #G3 */
   IBM_STENCILS = 3,     /* ibm_stencil[#IB + #G1 + #G2 + #G3], IB first then G1, G2, G3, each in row-major order */
   IBM_TIME = 4,         /* double[2]: t, last dt */
-  IBM_STEPS = 5         /* int64_t: steps taken */
+  IBM_STEPS = 5,        /* int64_t: steps taken */
+  IBM_TUNING = 6        /* int32_t (host only): register-budget variant of the FP32-bulk plain stage kernel
+                           picked by the autotuner (0..2; -1 before the first step, or FP64) */
 };
 
 /* Create a case, initialised to the uniform free stream at t = 0 (no
@@ -194,6 +196,15 @@ int64_t ibm_launch_count(const ibm_case *c);
 ibm_status ibm_profile_enable(ibm_case *c, int enable);
 ibm_status ibm_profile_read(ibm_case *c, double *ms, int64_t *launches, int n_groups);
 
+/* Autotuning (default on).  FP32-bulk cases time the plain-tile stage kernel
+ * under three register budgets (six, five and four resident blocks per SM)
+ * on their first ibm_step -- a few extra launches and one host wait -- and
+ * keep the fastest; the choice is cached per device and grid size for the
+ * process.  enable = 0 uses the compiler's default budget.  Results do not
+ * depend on the choice beyond FP32 rounding.  Only before the first step
+ * (IBM_ESTATE afterwards). */
+ibm_status ibm_autotune(ibm_case *c, int enable);
+
 /* Replay each step from a CUDA graph captured on first use (default on);
  * enable = 0 launches every kernel directly. */
 ibm_status ibm_use_graphs(ibm_case *c, int enable);
@@ -246,14 +257,31 @@ ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, in
  * goes to the next waiting request.  Cases share nothing on the device, so
  * a request gives the same result alone and in any mix.
  *
+ * Batched mode (default) for FP32-bulk explicit RK3 requests: the requests
+ * admitted in one pass form groups of up to 24 cases of similar size (grids
+ * within a factor four in cells) and equal step counts; one step of a group is
+ * one CUDA graph with the per-case pre-stage work (re-classification of moving
+ * bodies, dt) on the cases' streams and, per RK stage, one launch of the
+ * plain-tile kernel and one of the body-tile kernel over the block table of
+ * all member cases.  A group's membership is fixed when it forms (its graph is
+ * captured once and its members finish together); later arrivals form new
+ * groups, which run beside the old ones.  With IBM_SERVE_AUTOTUNE the
+ * plain-tile launch's schedule (one block per tile, or a persistent grid
+ * striding over the table) is picked by timing the candidates on the group,
+ * once per size class and membership size.  Other requests (FP64, dual time),
+ * and all requests when batching is off, advance on their own streams as
+ * described above.  Results do not depend on the mode or the mix.
+ *
  * The server is driven by the caller's thread: ibm_server_progress does one
  * non-blocking pass (retire finished cases, admit waiting requests, enqueue
- * the next chunk of every case whose previous chunk is done).  Call it in a
- * loop until it reports no running and no waiting request.  One host thread
- * at a time per server; cases are created on the current device. */
+ * the next chunk of every case or group whose previous chunk is done).  Call
+ * it in a loop until it reports no running and no waiting request.  One host
+ * thread at a time per server; cases are created on the current device. */
 typedef struct ibm_server ibm_server;
 
 enum { IBM_REQ_PENDING = 0, IBM_REQ_RUNNING = 1, IBM_REQ_DONE = 2, IBM_REQ_FAILED = 3 };
+enum { IBM_SERVE_BATCHED = 1, IBM_SERVE_AUTOTUNE = 2 };
+#define IBM_SERVER_NSTATS 5
 
 typedef struct {
   int64_t id;
@@ -270,6 +298,16 @@ typedef struct {
 /* device_bytes_budget = 0: 80 % of the device memory free at creation.
  * max_active >= 1, steps_per_chunk >= 1. */
 ibm_status ibm_server_create(size_t device_bytes_budget, int max_active, int steps_per_chunk, ibm_server **out);
+
+/* mode: IBM_SERVE_BATCHED | IBM_SERVE_AUTOTUNE (the default), either, or 0
+ * (every case on its own stream).  Only before the first submit
+ * (IBM_ESTATE afterwards). */
+ibm_status ibm_server_set_mode(ibm_server *s, int mode);
+
+/* Counters since creation, n <= IBM_SERVER_NSTATS: [0] group graphs captured,
+ * [1] group steps launched, [2] kernels in those steps, [3] autotuner runs,
+ * [4] host microseconds spent capturing group graphs and autotuning. */
+ibm_status ibm_server_stats(const ibm_server *s, int64_t *out, int n);
 
 /* Queue a request; the arguments are validated and copied (the vertices too).
  * IBM_ENOMEM if the case alone exceeds the budget.  *id receives a positive

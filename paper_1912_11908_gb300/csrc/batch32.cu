@@ -1,0 +1,78 @@
+// Block-table stage kernels of the request loop: one launch per RK stage over
+// all member cases of a group.  Kept in a module of their own: linked into the
+// single-case module, these kernels slowed the replay of single-case step
+// graphs by ~10% on GB300 (measured; kernel durations themselves unchanged).
+#include "stage32.cuh"
+
+namespace ibm {
+
+// One launch per stage for all member cases of a group.  Blocks walk the block
+// table with a grid stride, so a grid smaller than the table makes the launch
+// persistent.  Per entry the block runs the per-tile code of the case the
+// entry falls in (the same source as the single-case kernel; the two kernels
+// are compiled separately, so FP32 roundings may differ between them).
+template <int STAGE, bool BODY>
+__global__ void __launch_bounds__(256, BODY ? 1 : 6) k_stage_f32_batch(const __grid_constant__ StageBatch b) {
+  const int *start = BODY ? b.body_start : b.plain_start;
+  const int total = start[b.n];
+  for (int e = blockIdx.x; e < total; e += gridDim.x) {
+    int q = 0;
+    while (q + 1 < b.n && start[q + 1] <= e) q++;
+    const StageCase &sc = b.cs[q];
+    const float *In = STAGE == 1 ? sc.M : (STAGE == 2 ? sc.F1 : sc.F2);
+    float *Out = STAGE == 1 ? sc.F1 : (STAGE == 2 ? sc.F2 : nullptr);
+    stage_tile<STAGE, BODY>(sc.k, sc.c, sc.M, In, Out, sc.D, sc.tag, sc.sid, sc.rs, sc.tile_body, sc.body_tiles,
+                            sc.ds, sc.fuse_cfl != 0, sc.ncfl, e - start[q]);
+    __syncthreads();  // shared memory is reused by the next entry
+  }
+}
+
+void launch_stage_f32_batch(const StageBatch &b, int stage, int plain_grid, int body_grid, cudaStream_t s,
+                            cudaStream_t sb, bool with_body) {
+  const int nplain = b.plain_start[b.n], nbody = with_body ? b.body_start[b.n] : 0;
+  const int gp = plain_grid > 0 && plain_grid < nplain ? plain_grid : nplain;
+  const int gb = body_grid > 0 && body_grid < nbody ? body_grid : nbody;
+#define IBM_STAGE_PAIR(S)                                          \
+  do {                                                             \
+    if (gb > 0) k_stage_f32_batch<S, true><<<gb, 256, 0, sb>>>(b); \
+    if (gp > 0) k_stage_f32_batch<S, false><<<gp, 256, 0, s>>>(b); \
+  } while (0)
+  if (stage == 1) IBM_STAGE_PAIR(1);
+  else if (stage == 2) IBM_STAGE_PAIR(2);
+  else IBM_STAGE_PAIR(3);
+#undef IBM_STAGE_PAIR
+}
+
+void build_stage_batch(const StageCase *cases, int n, StageBatch *b) {
+  b->n = n;
+  b->plain_start[0] = b->body_start[0] = 0;
+  for (int q = 0; q < n; q++) {
+    b->cs[q] = cases[q];
+    b->plain_start[q + 1] = b->plain_start[q] + cases[q].nt;
+    b->body_start[q + 1] = b->body_start[q] + cases[q].nb;
+  }
+}
+
+void fill_stage_case(const Consts &k, float *M, float *F1, float *F2, double *D, const uint8_t *tag, const int *sid,
+                     const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
+                     DevState *ds, bool fuse_cfl, StageCase *out) {
+  out->k = k;
+  out->c = pert_consts(k);
+  out->M = M;
+  out->F1 = F1;
+  out->F2 = F2;
+  out->D = D;
+  out->tag = tag;
+  out->sid = sid;
+  out->rs = rs;
+  out->tile_body = tile_body;
+  out->body_tiles = body_tiles;
+  out->ds = ds;
+  out->nt = stage_tiles(k);
+  out->nb = body_cap > 0 ? body_cap : 0;
+  out->fuse_cfl = fuse_cfl ? 1 : 0;
+  out->ncfl = (unsigned int)(out->nt + out->nb);
+}
+
+
+}  // namespace ibm

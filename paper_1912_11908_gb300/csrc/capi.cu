@@ -5,7 +5,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <type_traits>
 
 #include "ibm_internal.cuh"
@@ -33,6 +36,8 @@ struct ibm_case {
   uint8_t *tile_body = nullptr;  // FP32-bulk: stage tiles that rebuild IB / ghost nodes
   int *body_tiles = nullptr;
   int body_cap = 0;
+  int plain_variant = -1;  // FP32-bulk: register budget of the plain stage kernel (-1: not tuned yet)
+  bool autotune = true;
   int box_w = 0, box_h = 0;      // cells spanned by the body's bounding box (any pose), for classification
   cudaStream_t sb = nullptr;     // FP32-bulk: stream of the body-tile kernels (forked from / joined to stream)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -395,6 +400,7 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
         if (cudaMemsetAsync(p, 0, 4 * plane * sizeof(float), s) != cudaSuccess) rs = fail(IBM_ECUDA, "memset failed");
     }
     c->launches += (c->B ? 3 : 1) + (c->Wn ? 2 : 0);
+
   } while (0);
   if (rs != IBM_OK) {
     free_case(c);
@@ -503,7 +509,8 @@ static int enqueue_step(ibm_case *c) {
       cudaEventRecord(c->ev_fork, s);
       cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
       launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->tile_body,
-                       c->body_tiles, c->body_cap, c->ds, fuse_cfl, s, c->sb);
+                       c->body_tiles, c->body_cap, c->ds, fuse_cfl, s, c->sb, c->plain_variant < 0 ? 0 : c->plain_variant,
+                       true);
       cudaEventRecord(c->ev_join, c->sb);
       cudaStreamWaitEvent(s, c->ev_join, 0);
       if (c->body_cap > 0) nl += 1;
@@ -512,6 +519,66 @@ static int enqueue_step(ibm_case *c) {
     nl += 1;
   }
   return nl;
+}
+
+// Autotuner of the FP32-bulk step: time the plain-tile kernel of stage 1 under
+// each register budget (resident blocks per SM) and keep the fastest, once per
+// device and grid size for the whole process.  Between steps that kernel has
+// no effect on the solution: it reads the mirror of U^n and writes only the
+// stage-1 array and the stage times, which the step's own stage 1 rewrites.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned;
+
+static ibm_status tune_plain_variant(ibm_case *c) {
+  if (c->precision != IBM_PREC_FP32_BULK || c->plain_variant >= 0) return IBM_OK;
+  if (!c->autotune) {
+    c->plain_variant = 0;
+    return IBM_OK;
+  }
+  const auto key = std::make_tuple(c->device, c->k.nx, c->k.ny);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      c->plain_variant = it->second;
+      return IBM_OK;
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 1e30f;
+  const bool fuse = fused_cfl(c);
+  for (int v = 0; v < PLAIN_VARIANTS; v++) {
+    auto launch = [&]() {
+      launch_stage_f32(c->k, 1, c->M, c->M, c->F1, c->A, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles,
+                       c->body_cap, c->ds, fuse, c->stream, c->sb, v, false);
+    };
+    launch();  // warm-up
+    cudaEventRecord(e0, c->stream);
+    for (int rep = 0; rep < 3; rep++) launch();
+    cudaEventRecord(e1, c->stream);
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(IBM_ECUDA, "autotuning failed: %s", cudaGetErrorString(e));
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->launches += 4 * PLAIN_VARIANTS;
+  c->plain_variant = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = best;
+  return IBM_OK;
 }
 
 static ibm_status capture_step_graph(ibm_case *c) {
@@ -552,6 +619,10 @@ extern "C" ibm_status ibm_step(ibm_case *c, int nsteps) {
     c->launches += nl;
     c->dt_valid = true;
   }
+  if (c->plain_variant < 0) {
+    ibm_status r = tune_plain_variant(c);
+    if (r != IBM_OK) return r;
+  }
   if (c->use_graphs && !c->profiling) {
     if (!c->graph) {
       ibm_status r = capture_step_graph(c);
@@ -563,6 +634,56 @@ extern "C" ibm_status ibm_step(ibm_case *c, int nsteps) {
     for (int n = 0; n < nsteps; n++) c->launches += enqueue_step(c);
   }
   CU(cudaGetLastError());
+  return IBM_OK;
+}
+
+namespace ibm {
+
+bool case_batchable(const ibm_case *c) { return c->precision == IBM_PREC_FP32_BULK && !c->k.dual; }
+
+ibm_status case_prepare_batch(ibm_case *c) {
+  if (!c->classified) {
+    ibm_status r = do_classify(c);
+    if (r != IBM_OK) return r;
+  }
+  if (fused_cfl(c) && !c->dt_valid) {
+    int nl = 0;
+    launch_dt_f32(c->k, c->M, c->tag, c->ds, c->stream, &nl);
+    c->launches += nl;
+    c->dt_valid = true;
+  }
+  CU(cudaGetLastError());
+  return IBM_OK;
+}
+
+int case_enqueue_prestage(ibm_case *c) {
+  int nl = 0;
+  if (c->k.motion.kind != IBM_MOTION_STATIC) {
+    const long long before = c->launches;
+    do_classify(c);
+    nl += (int)(c->launches - before);
+    c->launches = before;
+  }
+  if (!fused_cfl(c)) launch_dt_f32(c->k, c->M, c->tag, c->ds, c->stream, &nl);
+  return nl;
+}
+
+void case_stage_desc(const ibm_case *c, StageCase *out) {
+  fill_stage_case(c->k, c->M, c->F1, c->F2, c->A, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap,
+                  c->ds, fused_cfl(c), out);
+}
+
+cudaStream_t case_stream(const ibm_case *c) { return c->stream; }
+
+void case_add_launches(ibm_case *c, long long n) { c->launches += n; }
+
+}  // namespace ibm
+
+extern "C" ibm_status ibm_autotune(ibm_case *c, int enable) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  if (c->graph) return fail(IBM_ESTATE, "ibm_autotune: the case has already stepped");
+  c->autotune = enable != 0;
+  c->plain_variant = -1;
   return IBM_OK;
 }
 
@@ -694,6 +815,12 @@ extern "C" ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t byt
         CU(cudaMemcpyAsync(dst, &n, sizeof n, cudaMemcpyHostToDevice, c->stream));
         CU(cudaStreamSynchronize(c->stream));
       } else std::memcpy(dst, &n, sizeof n);
+      break;
+    }
+    case IBM_TUNING: {
+      if (bytes < sizeof(int32_t) || dst_on_device) return fail(IBM_EINVAL, "IBM_TUNING: host int32 destination");
+      const int32_t v = c->plain_variant;
+      std::memcpy(dst, &v, sizeof v);
       break;
     }
     default:

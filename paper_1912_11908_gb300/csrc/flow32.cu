@@ -1,67 +1,9 @@
-// FP32-bulk flow kernels.
-//
-// Stage values, reconstruction and fluxes run in FP32 on perturbations from
-// the free stream, dU = (rho - rho_inf, rho u - rho_inf u_inf,
-// rho v - rho_inf v_inf, W'), W' = (rho E - rho_inf E_inf) - H_inf (rho -
-// rho_inf).  Primitives are (rho', u, v, p') with p' = p - p_inf and
-// T' = T - T_inf formed without ever adding p_inf or H_inf to an FP32 value,
-// so O(M^2) pressure and temperature fluctuations keep their FP32 precision
-// at any free-stream Mach number.  The state U^n is held in FP64 as the same
-// perturbation dU and accumulated in FP64 at the last stage of every step:
-// dU^{n+1} = dU^n + (double)[2/3 ((dU^(2) - dU^n) + dt L)], where the bracket
-// is an O(dt) increment formed in FP32 (the FP32 mirror of dU^n is rounded
-// from the FP64 state after every step, so FP32 rounding never accumulates in
-// U^n).
-#include "ibm_internal.cuh"
+// FP32-bulk flow kernels of one case: conversions between the FP64 master and
+// the FP32 mirror, the CFL reduction, compact stencils, body-tile lists and
+// the stage kernels (per-tile code in stage32.cuh).
+#include "stage32.cuh"
 
 namespace ibm {
-
-struct PertConsts {  // FP32 copies of the free-stream constants
-  float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin, vis;
-};
-
-__host__ inline PertConsts pert_consts(const Consts &k) {
-  PertConsts c;
-  c.gamma = (float)k.gamma;
-  c.g1 = (float)(k.gamma - 1.0);
-  c.gg = (float)(k.gamma / (k.gamma - 1.0));
-  c.R = (float)k.R;
-  c.Hinf = (float)k.Hinf;
-  c.ux = (float)k.uinf[0];
-  c.uy = (float)k.uinf[1];
-  c.mu = (float)k.mu;
-  c.kappa = (float)k.kappa;
-  c.idx = (float)(1.0 / k.dx);
-  c.idy = (float)(1.0 / k.dy);
-  c.dmin = (float)k.dmin;
-  c.vis = (float)((2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy)));
-  return c;
-}
-
-// perturbation conserved -> (rho', u, v, p', T')
-__device__ __forceinline__ void pert_prim(const PertConsts &c, float dr, float dmx, float dmy, float W, float &u,
-                                          float &v, float &pp, float &Tp) {
-  const float r = 1.f + dr;
-  const float ir = 1.f / r;
-  u = (c.ux + dmx) * ir;
-  v = (c.uy + dmy) * ir;
-  const float du = (dmx - dr * c.ux) * ir, dv = (dmy - dr * c.uy) * ir;
-  const float dq = du * (u + c.ux) + dv * (v + c.uy);  // |u|^2 - |u_inf|^2
-  const float ke = 0.5f * (dr * (u * u + v * v) + dq);  // (rho |u|^2 - rho_inf |u_inf|^2) / 2
-  pp = c.g1 * (W + c.Hinf * dr - ke);
-  Tp = (pp - c.R * dr) * ir / c.R;
-}
-
-// (p', u, v, T') -> perturbation conserved
-__device__ __forceinline__ void prim_pert(const PertConsts &c, float pp, float u, float v, float Tp, float &dr,
-                                          float &dmx, float &dmy, float &W) {
-  dr = (pp - c.R * Tp) / (c.R * (1.f + Tp));
-  dmx = dr * u + (u - c.ux);
-  dmy = dr * v + (v - c.uy);
-  const float dq = (u - c.ux) * (u + c.ux) + (v - c.uy) * (v + c.uy);
-  const float ke = 0.5f * (dr * (u * u + v * v) + dq);
-  W = pp / c.g1 + ke - c.Hinf * dr;
-}
 
 // FP64 absolute conserved <-> FP64 perturbation, in place / out of place
 __global__ void k_abs_to_pert64(Consts k, double *D) {
@@ -171,428 +113,19 @@ void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 
   k_compact_stencils<<<(cap + 127) / 128, 128, 0, s>>>(k, st, rs, sid, cap, ds);
 }
 
-// LDFSS(0) in perturbation form (Mr^2 = 1).  States (rho', un, ut, p');
-// un_inf / ut_inf the free-stream components along the face normal and
-// tangent.  Momentum flux drops the constant p_inf n (its divergence is
-// zero); D_L + D_R - 1 is formed in factored form for two subsonic sides so
-// p_inf (D_L + D_R - 1) keeps its precision.
-__device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float unL, float utL, float ppL,
-                                           float drR, float unR, float utR, float ppR, float un_inf, float ut_inf,
-                                           float F[4]) {
-  const float rL = 1.f + drL, rR = 1.f + drR;
-  const float irL = 1.f / rL, irR = 1.f / rR;
-  const float cL = sqrtf(c.gamma * (c.R + ppL) * irL), cR = sqrtf(c.gamma * (c.R + ppR) * irR);
-  const float HL = c.gg * (ppL - c.R * drL) * irL +
-                   0.5f * ((unL - un_inf) * (unL + un_inf) + (utL - ut_inf) * (utL + ut_inf));
-  const float HR = c.gg * (ppR - c.R * drR) * irR +
-                   0.5f * ((unR - un_inf) * (unR + un_inf) + (utR - ut_inf) * (utR + ut_inf));
-  const float cs = 0.5f * (cL + cR);
-  const float ics = 1.f / cs;
-  const float ML = unL * ics, MR = unR * ics;
-  const float aL = ML >= 0.f ? 1.f : 0.f;
-  const float aR = MR >= 0.f ? 0.f : 1.f;
-  const bool subL = fabsf(ML) < 1.f, subR = fabsf(MR) < 1.f;
-  const float bL = subL ? -1.f : 0.f, bR = subR ? -1.f : 0.f;
-  const float MpL = 0.25f * (ML + 1.f) * (ML + 1.f);
-  const float MmR = -0.25f * (MR - 1.f) * (MR - 1.f);
-  const float CVL = aL * (1.f + bL) * ML - bL * MpL;
-  const float CVR = aR * (1.f + bR) * MR - bR * MmR;
-  const float sq = sqrtf(0.5f * (ML * ML + MR * MR)) - 1.f;
-  const float Mh = 0.25f * bL * bR * sq * sq;
-  const float dp = ppL - ppR, adp = fabsf(dp);
-  const float ic2 = 0.5f * ics * ics;
-  const float MhP = Mh * (1.f - (dp + adp) * ic2 * irL);
-  const float MhM = Mh * (1.f - (adp - dp) * ic2 * irR);
-  const float Cp = CVL - MhP, Cm = CVR + MhM;
-  const float PpL = MpL * (2.f - ML);
-  const float PmR = -MmR * (2.f + MR);
-  const float DL = aL * (1.f + bL) - bL * PpL;
-  const float DR = aR * (1.f + bR) - bR * PmR;
-  const float Dm1 = (subL && subR) ? 0.25f * (MR - ML) * (MR * MR + MR * ML + ML * ML - 3.f) : (DL + DR - 1.f);
-  const float mL = rL * cs * Cp, mR = rR * cs * Cm;
-  F[0] = mL + mR;
-  F[1] = mL * unL + mR * unR + c.R * Dm1 + DL * ppL + DR * ppR;
-  F[2] = mL * utL + mR * utR;
-  F[3] = mL * HL + mR * HR;
-}
-
-// ---------------------------------------------------------------------------
-// Fused residual + stage update in FP32 perturbation form, same tiling as
-// the FP64 kernel.  Stage 3 accumulates U^{n+1} in FP64 and refreshes the
-// FP32 mirror of U^{n+1}.
-// ---------------------------------------------------------------------------
-constexpr int TX = 16, TY = 16, HX = TX + 2 * NG, HY = TY + 2 * NG;
-
-// spectral radius of the CFL rule for one cell of the FP32 mirror
-__device__ __forceinline__ float cfl_lambda(const Consts &k, const PertConsts &c, const float m[4]) {
-  float u, v, pp, Tp;
-  pert_prim(c, m[0], m[1], m[2], m[3], u, v, pp, Tp);
-  const float r = 1.f + m[0];
-  const float cs = sqrtf(c.gamma * (c.R + pp) / r);
-  return (fabsf(u) + cs) * c.idx + (fabsf(v) + cs) * c.idy + c.vis / r;
-}
-
-// block maximum of lam (all 256 threads call), then the grid-wide maximum and
-// dt through the last-block pattern
-__device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float *red, DevState *ds,
-                                              unsigned int nblocks) {
-  for (int off = 16; off > 0; off >>= 1) lam = fmaxf(lam, __shfl_xor_sync(0xffffffffu, lam, off));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lam;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float m = red[0];
-    for (int w = 1; w < 8; w++) m = fmaxf(m, red[w]);
-    atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong((double)m));
-    finish_cfl(k, ds, nblocks);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// IB / ghost reconstruction (Sec. 4.4-4.6, Eq. 4-8; Sec. 5) evaluated while a
-// tile is loaded.  Values are primitives (p', u, v, T').  A ghost node's
-// image point may use IB nodes, which are rebuilt from their own stencils
-// (their corners are fluid): a body tile rebuilds all IB nodes of its loaded
-// region, then all ghost nodes, reading corners from shared memory and only
-// corners outside the region from the stage input.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void raw_prim(const PertConsts &c, const float *U, long long id, long long P,
-                                         float q[4]) {
-  float u, v, pp, Tp;
-  pert_prim(c, U[id], U[id + P], U[id + 2 * P], U[id + 3 * P], u, v, pp, Tp);
-  q[0] = pp;
-  q[1] = u;
-  q[2] = v;
-  q[3] = Tp;
-}
-
-__device__ __forceinline__ void wall_bc(const PertConsts &c, const RStencil32 &s, const float qp[4], const float *wm,
-                                        float q[4]) {
-  // wm = (Vx, Vy, Ax, Ay) at the stage time
-  const float rho_p = 1.f + (qp[0] - c.R * qp[3]) / (c.R * (1.f + qp[3]));
-  const float g = -rho_p * (s.nx * wm[2] + s.ny * wm[3]);
-  q[0] = qp[0] - s.dxi * g;
-  q[1] = wm[0] + (qp[1] - wm[0]) * s.ratio;
-  q[2] = wm[1] + (qp[2] - wm[1]) * s.ratio;
-  q[3] = qp[3];
-}
-
-__device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts &c, const float *U,
-                                        const RStencil32 &s, const float *wm, float q[4]) {
-  float qp[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int b = 0; b < 4; b++) {
-    if (!(s.mask >> b & 1)) continue;  // bits 0-3: valid corners (bit 4: IB node)
-    float cq[4];
-    raw_prim(c, U, s.corner + (b & 1) + (b >> 1) * k.pitch, k.plane, cq);
-    for (int v = 0; v < 4; v++) qp[v] += s.w[b] * cq[v];
-  }
-  wall_bc(c, s, qp, wm, q);
-}
-
-// ---------------------------------------------------------------------------
-// Fused residual + stage update in FP32 perturbation form.  One 16x16 tile
-// per block.  (1) Load tile + 3-cell halo: domain halos by index mapping, IB
-// and ghost nodes rebuilt on the fly, conversion to (rho', u, v, p', T') in
-// shared memory.  (2) WENO5 per cell and direction: the three smoothness
-// indicators of a cell's five-point window serve both the left state of its
-// right face and the right state of its left face.  (3) LDFSS + central
-// viscous flux per face.  (4) Flux divergence and SSP-RK3 stage update;
-// stage 3 accumulates U^{n+1} in FP64.
-// ---------------------------------------------------------------------------
-template <int STAGE, bool BODY>
-__global__ void __launch_bounds__(256) k_stage_f32(Consts k, PertConsts c, float *Mn, const float *__restrict__ In,
+// A case stepped on its own: one block per tile (plain) or body-tile slot.
+// MINB: resident blocks per SM the register allocation must allow (0: left to
+// the compiler, 40 registers; 5: 48 registers; 4: about 60 registers) -- the
+// autotuner picks one per grid size.
+template <int STAGE, bool BODY, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_stage_f32(Consts k, PertConsts c, float *Mn, const float *__restrict__ In,
                                                    float *Out, double *D, const uint8_t *__restrict__ tag,
                                                    const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
                                                    const uint8_t *__restrict__ tile_body,
                                                    const int *__restrict__ body_tiles, DevState *ds, bool fuse_cfl,
                                                    unsigned int ncfl) {
-  __shared__ float sq[4][HY][HX];  // rho', u, v, p'
-  __shared__ float sT[HY][HX];     // T'
-  __shared__ float fLx[4][TY][TX + 1], fRx[4][TY][TX + 1];  // x-face states; fLx then holds the x flux
-  __shared__ float fLy[4][TY + 1][TX], fRy[4][TY + 1][TX];  // y-face states; fLy then holds the y flux
-  __shared__ float wm[4];
-  __shared__ float lred[8];
-  const int ntx = (k.nx + TX - 1) / TX;
-  // every block reads dt before any block can finish the fused CFL reduction
-  const double dtd = ds->dt;
-  const float dt = ds->dtf;
-  int tile;
-  if (BODY) {
-    tile = (int)blockIdx.x < ds->nbody_tiles ? body_tiles[blockIdx.x] : -1;
-  } else {
-    tile = tile_body[blockIdx.x] ? -1 : (int)blockIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      if (STAGE == 1) {  // stage times for the body kernels of stages 2 and 3
-        ds->tst[0] = ds->t + dtd;
-        ds->tst[1] = ds->t + 0.5 * dtd;
-      } else if (STAGE == 3) {  // end of the step; the body kernel of stage 3 reads tst, not t
-        ds->t = ds->t + dtd;
-        ds->steps += 1;
-      }
-    }
-  }
-  if (tile < 0) {
-    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds, ncfl);
-    return;
-  }
-  const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int ci = i0 + tx, cj = j0 + ty;
-  const bool inside = ci < k.nx && cj < k.ny;
-  const uint8_t mytag = inside ? tag[cj * k.nx + ci] : (uint8_t)SOLID;
-  const bool fluid = mytag == FLUID;
-  // stages 1 and 3 also keep the IB / ghost nodes of U^n current; stage 2 only needs fluid cells
-  const bool work = STAGE == 2 ? fluid : (mytag != SOLID);
-  if (!__syncthreads_or(work)) {
-    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds, ncfl);
-    return;
-  }
-  if (BODY && threadIdx.x == 0) {
-    double X[2], V[2], Acc[2];
-    motion_at(k.motion, STAGE == 1 ? ds->t : ds->tst[STAGE - 2], X, V, Acc);
-    wm[0] = (float)V[0];
-    wm[1] = (float)V[1];
-    wm[2] = (float)Acc[0];
-    wm[3] = (float)Acc[1];
-  }
-  __syncthreads();
-
-  const long long P = k.plane;
-  // body tiles: every IB / ghost node of the loaded region, with its stencil staged in shared memory
-  constexpr int RB_MAX = 192;
-  __shared__ int s_nrb;
-  __shared__ int s_rbm[BODY ? RB_MAX : 1];
-  __shared__ int s_rbe[BODY ? RB_MAX : 1];
-  __shared__ RStencil32 s_rs[BODY ? RB_MAX : 1];
-  if (BODY && threadIdx.x == 0) s_nrb = 0;
-  if (BODY) __syncthreads();
-  for (int m = threadIdx.x; m < HX * HY; m += 256) {
-    const int a = m % HX, b = m / HX;
-    int gi = i0 - NG + a, gj = j0 - NG + b;
-    float q[4] = {0.f, c.ux, c.uy, 0.f};  // (p', u, v, T'); free stream: zero perturbation
-    float dr = 0.f;
-    if (halo_map(k, gi, gj)) {
-      const long long id = cidx(k, gi, gj);
-      int e = -1;
-      if (BODY) e = sid[gj * k.nx + gi];
-      dr = In[id];
-      raw_prim(c, In, id, P, q);
-      if (BODY && e >= 0) {
-        const int slot = atomicAdd(&s_nrb, 1);
-        if (slot < RB_MAX) {
-          s_rbm[slot] = m;
-          s_rbe[slot] = e;
-        }
-      }
-    }
-    sq[0][b][a] = dr;
-    sq[1][b][a] = q[1];
-    sq[2][b][a] = q[2];
-    sq[3][b][a] = q[0];
-    sT[b][a] = q[3];
-  }
-  __syncthreads();
-  if (BODY) {
-    const int nrb = min(s_nrb, RB_MAX);
-    for (int r = threadIdx.x; r < nrb; r += 256) s_rs[r] = rs[s_rbe[r]];
-    __syncthreads();
-    // rebuild the listed nodes in place: IB nodes, barrier, ghost nodes (whose image points may use IB
-    // nodes); corners inside the loaded region come from shared memory
-    for (int pass = 0; pass < 2; pass++) {
-      for (int r = threadIdx.x; r < nrb; r += 256) {
-        const RStencil32 &st = s_rs[r];
-        const bool is_ib = (st.mask & 16) != 0;
-        if (is_ib != (pass == 0) || !(st.mask & 15)) continue;
-        const int m = s_rbm[r], a = m % HX, b = m / HX;
-        float qp[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int cq = 0; cq < 4; cq++) {
-          if (!(st.mask >> cq & 1)) continue;
-          const int cn = st.ccell + (cq & 1) + (cq >> 1) * k.nx;
-          const int la = cn % k.nx - (i0 - NG), lb = cn / k.nx - (j0 - NG);
-          float v4[4];
-          if (la >= 0 && la < HX && lb >= 0 && lb < HY) {
-            v4[0] = sq[3][lb][la];
-            v4[1] = sq[1][lb][la];
-            v4[2] = sq[2][lb][la];
-            v4[3] = sT[lb][la];
-          } else {
-            // corner outside the loaded region: fluid value, or an IB node rebuilt from its own stencil
-            const int e2 = pass == 1 ? sid[cn] : -1;
-            if (e2 >= 0 && (rs[e2].mask & 15)) rebuild_ib(k, c, In, rs[e2], wm, v4);
-            else raw_prim(c, In, st.corner + (cq & 1) + (cq >> 1) * k.pitch, P, v4);
-          }
-          for (int v = 0; v < 4; v++) qp[v] += st.w[cq] * v4[v];
-        }
-        float q[4];
-        wall_bc(c, st, qp, wm, q);
-        sq[0][b][a] = (q[0] - c.R * q[3]) / (c.R * (1.f + q[3]));
-        sq[1][b][a] = q[1];
-        sq[2][b][a] = q[2];
-        sq[3][b][a] = q[0];
-        sT[b][a] = q[3];
-        const bool own = a >= NG && a < NG + TX && b >= NG && b < NG + TY;
-        if (own && STAGE == 1) {  // U^n on this node for output and for a node that turns fluid
-          float d0, d1, d2, d3;
-          prim_pert(c, q[0], q[1], q[2], q[3], d0, d1, d2, d3);
-          D[st.cell] = d0;
-          D[st.cell + P] = d1;
-          D[st.cell + 2 * P] = d2;
-          D[st.cell + 3 * P] = d3;
-        }
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0 && s_nrb > RB_MAX) atomicOr(&ds->err, ERR_CAPACITY);
-  }
-  // WENO5 per cell: x windows for local columns 2..TX+3 of interior rows,
-  // y windows for local rows 2..TY+3 of interior columns
-  constexpr int NXW = (TX + 2) * TY, NYW = TX * (TY + 2);
-  for (int m = threadIdx.x; m < NXW + NYW; m += 256) {
-    const bool xdir = m < NXW;
-    const int mm = xdir ? m : m - NXW;
-    int ccol, crow;
-    if (xdir) {
-      ccol = 2 + mm % (TX + 2);
-      crow = NG + mm / (TX + 2);
-    } else {
-      ccol = NG + mm % TX;
-      crow = 2 + mm / TX;
-    }
-    for (int v = 0; v < 4; v++) {
-      float f0, f1, f2, f3, f4;
-      if (xdir) {
-        const float *s = &sq[v][crow][ccol - 2];
-        f0 = s[0]; f1 = s[1]; f2 = s[2]; f3 = s[3]; f4 = s[4];
-      } else {
-        f0 = sq[v][crow - 2][ccol]; f1 = sq[v][crow - 1][ccol]; f2 = sq[v][crow][ccol];
-        f3 = sq[v][crow + 1][ccol]; f4 = sq[v][crow + 2][ccol];
-      }
-      const float eps = 1e-6f;
-      float aa = f0 - 2.f * f1 + f2, bb = f0 - 4.f * f1 + 3.f * f2;
-      const float b0 = (13.f / 12.f) * aa * aa + 0.25f * bb * bb;
-      aa = f1 - 2.f * f2 + f3;
-      bb = f1 - f3;
-      const float b1 = (13.f / 12.f) * aa * aa + 0.25f * bb * bb;
-      aa = f2 - 2.f * f3 + f4;
-      bb = 3.f * f2 - 4.f * f3 + f4;
-      const float b2 = (13.f / 12.f) * aa * aa + 0.25f * bb * bb;
-      const float e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
-      const float e01 = e0 * e1, e12 = e1 * e2, e02 = e0 * e2;
-      const float s01 = e01 * e01, s12 = e12 * e12, s02 = e02 * e02;
-      // left state at the cell's right face: weights (0.1, 0.6, 0.3) / e_k^2
-      const float l0 = 2.f * f0 - 7.f * f1 + 11.f * f2;
-      const float l1 = -f1 + 5.f * f2 + 2.f * f3;
-      const float l2 = 2.f * f2 + 5.f * f3 - f4;
-      const float la0 = 0.1f * s12, la1 = 0.6f * s02, la2 = 0.3f * s01;
-      const float qL = __fdividef(la0 * l0 + la1 * l1 + la2 * l2, 6.f * (la0 + la1 + la2));
-      // right state at the cell's left face: mirrored window, indicators reversed
-      const float r0 = 2.f * f4 - 7.f * f3 + 11.f * f2;
-      const float r1 = -f3 + 5.f * f2 + 2.f * f1;
-      const float r2 = 2.f * f2 + 5.f * f1 - f0;
-      const float ra0 = 0.1f * s01, ra1 = 0.6f * s02, ra2 = 0.3f * s12;
-      const float qR = __fdividef(ra0 * r0 + ra1 * r1 + ra2 * r2, 6.f * (ra0 + ra1 + ra2));
-      if (xdir) {
-        const int row = crow - NG;
-        if (ccol - 2 <= TX) fLx[v][row][ccol - 2] = qL;  // face between ccol and ccol+1
-        if (ccol >= 3) fRx[v][row][ccol - 3] = qR;        // face between ccol-1 and ccol
-      } else {
-        const int col = ccol - NG;
-        if (crow - 2 <= TY) fLy[v][crow - 2][col] = qL;
-        if (crow >= 3) fRy[v][crow - 3][col] = qR;
-      }
-    }
-  }
-  __syncthreads();
-
-  const float mu = c.mu, kap = c.kappa, idx = c.idx, idy = c.idy;
-  for (int m = threadIdx.x; m < (TX + 1) * TY + TX * (TY + 1); m += 256) {
-    const bool xdir = m < (TX + 1) * TY;
-    float qL[4], qR[4], F[4];
-    if (xdir) {
-      const int f = m % (TX + 1), row = m / (TX + 1);
-      const int b = row + NG, a = f + 2, a1 = f + 3;
-      for (int v = 0; v < 4; v++) {
-        qL[v] = fLx[v][row][f];
-        qR[v] = fRx[v][row][f];
-      }
-      if (!(qL[0] > -1.f) || !(qL[3] > -c.R) || !(qR[0] > -1.f) || !(qR[3] > -c.R)) {
-        for (int v = 0; v < 4; v++) {
-          qL[v] = sq[v][b][a];
-          qR[v] = sq[v][b][a1];
-        }
-      }
-      ldfss_pert(c, qL[0], qL[1], qL[2], qL[3], qR[0], qR[1], qR[2], qR[3], c.ux, c.uy, F);
-      const float ux = (sq[1][b][a1] - sq[1][b][a]) * idx;
-      const float vx = (sq[2][b][a1] - sq[2][b][a]) * idx;
-      const float Tx = (sT[b][a1] - sT[b][a]) * idx;
-      const float uy = (sq[1][b + 1][a] - sq[1][b - 1][a] + sq[1][b + 1][a1] - sq[1][b - 1][a1]) * (0.25f * idy);
-      const float vy = (sq[2][b + 1][a] - sq[2][b - 1][a] + sq[2][b + 1][a1] - sq[2][b - 1][a1]) * (0.25f * idy);
-      const float txx = mu * ((4.f / 3.f) * ux - (2.f / 3.f) * vy);
-      const float txy = mu * (uy + vx);
-      const float uf = 0.5f * (sq[1][b][a] + sq[1][b][a1]), vf = 0.5f * (sq[2][b][a] + sq[2][b][a1]);
-      fLx[0][row][f] = F[0];
-      fLx[1][row][f] = F[1] - txx;
-      fLx[2][row][f] = F[2] - txy;
-      fLx[3][row][f] = F[3] - (uf * txx + vf * txy + kap * Tx);
-    } else {
-      const int mm = m - (TX + 1) * TY;
-      const int col = mm % TX, f = mm / TX;
-      const int a = col + NG, b = f + 2, b1 = f + 3;
-      for (int v = 0; v < 4; v++) {
-        qL[v] = fLy[v][f][col];
-        qR[v] = fRy[v][f][col];
-      }
-      if (!(qL[0] > -1.f) || !(qL[3] > -c.R) || !(qR[0] > -1.f) || !(qR[3] > -c.R)) {
-        for (int v = 0; v < 4; v++) {
-          qL[v] = sq[v][b][a];
-          qR[v] = sq[v][b1][a];
-        }
-      }
-      ldfss_pert(c, qL[0], qL[2], qL[1], qL[3], qR[0], qR[2], qR[1], qR[3], c.uy, c.ux, F);
-      const float uy = (sq[1][b1][a] - sq[1][b][a]) * idy;
-      const float vy = (sq[2][b1][a] - sq[2][b][a]) * idy;
-      const float Ty = (sT[b1][a] - sT[b][a]) * idy;
-      const float ux = (sq[1][b][a + 1] - sq[1][b][a - 1] + sq[1][b1][a + 1] - sq[1][b1][a - 1]) * (0.25f * idx);
-      const float vx = (sq[2][b][a + 1] - sq[2][b][a - 1] + sq[2][b1][a + 1] - sq[2][b1][a - 1]) * (0.25f * idx);
-      const float tyy = mu * ((4.f / 3.f) * vy - (2.f / 3.f) * ux);
-      const float txy = mu * (uy + vx);
-      const float uf = 0.5f * (sq[1][b][a] + sq[1][b1][a]), vf = 0.5f * (sq[2][b][a] + sq[2][b1][a]);
-      fLy[0][f][col] = F[0];
-      fLy[1][f][col] = F[2] - txy;
-      fLy[2][f][col] = F[1] - tyy;
-      fLy[3][f][col] = F[3] - (uf * txy + vf * tyy + kap * Ty);
-    }
-  }
-  __syncthreads();
-
-  float lam = 0.f;
-  const long long id = cidx(k, ci, cj);
-  if (fluid) {
-    float L[4];
-    for (int v = 0; v < 4; v++)
-      L[v] = -((fLx[v][ty][tx + 1] - fLx[v][ty][tx]) * idx + (fLy[v][ty + 1][tx] - fLy[v][ty][tx]) * idy);
-    if (STAGE == 1) {
-      for (int v = 0; v < 4; v++) Out[id + v * P] = Mn[id + v * P] + dt * L[v];
-    } else if (STAGE == 2) {
-      for (int v = 0; v < 4; v++) Out[id + v * P] = 0.75f * Mn[id + v * P] + 0.25f * (In[id + v * P] + dt * L[v]);
-    } else {
-      // FP64 accumulation: dU^{n+1} = dU^n + (double)[2/3 ((dU^(2) - dU^n) + dt L)]
-      float mnew[4];
-      for (int v = 0; v < 4; v++) {
-        const long long o = id + v * P;
-        const float inc = (2.f / 3.f) * ((In[o] - Mn[o]) + dt * L[v]);
-        const double dn = D[o] + (double)inc;
-        D[o] = dn;
-        mnew[v] = (float)dn;
-        Mn[o] = mnew[v];
-      }
-      if (fuse_cfl) lam = cfl_lambda(k, c, mnew);
-    }
-  } else if (BODY && STAGE == 3 && inside && mytag != SOLID) {
-    // IB / ghost node: the mirror of U^{n+1} takes the value rebuilt at stage 1
-    for (int v = 0; v < 4; v++) Mn[id + v * P] = (float)D[id + v * P];
-  }
-  // one call site for the whole block (the reduction has a barrier)
-  if (STAGE == 3 && fuse_cfl) cfl_block_max(k, lam, lred, ds, ncfl);
+  stage_tile<STAGE, BODY>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, fuse_cfl, ncfl,
+                          (int)blockIdx.x);
 }
 
 int stage_tiles(const Consts &k) { return ((k.nx + TX - 1) / TX) * ((k.ny + TY - 1) / TY); }
@@ -654,17 +187,25 @@ void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, 
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
                       const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                       const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
-                      cudaStream_t sb) {
+                      cudaStream_t sb, int plain_variant, bool with_body) {
   PertConsts c = pert_consts(k);
   const int nt = stage_tiles(k);
   const int nb = body_cap > 0 ? body_cap : 0;
   const unsigned int ncfl = (unsigned int)(nt + nb);
-#define IBM_STAGE_PAIR(S)                                                                                    \
-  do {                                                                                                       \
-    if (nb) k_stage_f32<S, true><<<nb, 256, 0, sb>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, \
-                                                     ds, fuse_cfl, ncfl);                                    \
-    k_stage_f32<S, false><<<nt, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds,    \
-                                             fuse_cfl, ncfl);                                                \
+#define IBM_STAGE_PAIR(S)                                                                                      \
+  do {                                                                                                         \
+    if (nb && with_body)                                                                                       \
+      k_stage_f32<S, true, 0><<<nb, 256, 0, sb>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, \
+                                                  fuse_cfl, ncfl);                                             \
+    if (plain_variant == 1)                                                                                    \
+      k_stage_f32<S, false, 5><<<nt, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, \
+                                                  fuse_cfl, ncfl);                                             \
+    else if (plain_variant == 2)                                                                               \
+      k_stage_f32<S, false, 4><<<nt, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, \
+                                                  fuse_cfl, ncfl);                                             \
+    else                                                                                                       \
+      k_stage_f32<S, false, 0><<<nt, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, \
+                                                  fuse_cfl, ncfl);                                             \
   } while (0)
   if (stage == 1) IBM_STAGE_PAIR(1);
   else if (stage == 2) IBM_STAGE_PAIR(2);

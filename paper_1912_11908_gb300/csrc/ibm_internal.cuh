@@ -196,15 +196,103 @@ void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 
 void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, int *body_tiles, int body_cap,
                        DevState *ds, cudaStream_t s);
 int stage_tiles(const Consts &k);
+struct PertConsts {  // FP32 copies of the free-stream constants
+  float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin, vis;
+};
+
+__host__ inline PertConsts pert_consts(const Consts &k) {
+  PertConsts c;
+  c.gamma = (float)k.gamma;
+  c.g1 = (float)(k.gamma - 1.0);
+  c.gg = (float)(k.gamma / (k.gamma - 1.0));
+  c.R = (float)k.R;
+  c.Hinf = (float)k.Hinf;
+  c.ux = (float)k.uinf[0];
+  c.uy = (float)k.uinf[1];
+  c.mu = (float)k.mu;
+  c.kappa = (float)k.kappa;
+  c.idx = (float)(1.0 / k.dx);
+  c.idy = (float)(1.0 / k.dy);
+  c.dmin = (float)k.dmin;
+  c.vis = (float)((2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy)));
+  return c;
+}
+
+
+// One FP32-bulk case of a stage batch: everything its stage kernels take.
 // fuse_cfl: stage 3 also reduces the CFL maximum of the new state and sets the
-// next step's dt (static bodies: the fluid set does not change between steps)
-// Stage kernels: the plain kernel (stream s) covers tiles without IB / ghost
-// nodes near them; the body kernel (stream sb, may run concurrently) covers
-// the listed body tiles and rebuilds IB and ghost nodes from rs / sid while it
-// loads a tile (no separate reconstruction launch).
+// next step's dt (static bodies: the fluid set does not change between steps).
+// Stage kernels of one case: the plain kernel (stream s) covers tiles without
+// IB / ghost nodes near them; the body kernel (stream sb, may run concurrently)
+// covers the listed body tiles and rebuilds IB and ghost nodes from rs / sid
+// while it loads a tile (no separate reconstruction launch).  plain_variant
+// selects the plain kernel's register budget, i.e. its resident blocks per SM
+// (0: compiler's choice, 40 registers, six blocks; 1: 48 registers, five
+// blocks; 2: about 60 registers, four blocks); with_body = false launches the
+// plain kernel only (autotuning).
+constexpr int PLAIN_VARIANTS = 3;
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
                       const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                       const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
-                      cudaStream_t sb);
+                      cudaStream_t sb, int plain_variant, bool with_body);
+// The same two kernels over a group's block table: the plain kernel (stream s) covers tiles
+// without IB / ghost nodes near them; the body kernel (stream sb, may run
+// concurrently) covers the listed body tiles and rebuilds IB and ghost nodes
+// from rs / sid while it loads a tile (no separate reconstruction launch).
+struct StageCase {
+  Consts k;
+  PertConsts c;
+  float *M, *F1, *F2;  // mirror of U^n and the stage arrays
+  double *D;           // FP64 master (perturbation)
+  const uint8_t *tag;
+  const int *sid;
+  const RStencil32 *rs;
+  const uint8_t *tile_body;
+  const int *body_tiles;
+  DevState *ds;
+  int nt, nb;          // stage tiles, body-tile slots
+  int fuse_cfl;
+  unsigned int ncfl;   // blocks of the fused CFL reduction (nt + nb)
+};
+
+// Block table of a batched stage launch over the member cases of a group,
+// passed by value in kernel parameter space: case q owns plain entries
+// [plain_start[q], plain_start[q+1]) and body entries [body_start[q],
+// body_start[q+1]).
+constexpr int MAX_BATCH = 24;
+struct StageBatch {
+  int n;
+  int plain_start[MAX_BATCH + 1];
+  int body_start[MAX_BATCH + 1];
+  StageCase cs[MAX_BATCH];
+};
+static_assert(sizeof(StageBatch) <= 32000, "kernel parameter space");
+// fill b from n <= MAX_BATCH case descriptors
+void build_stage_batch(const StageCase *cases, int n, StageBatch *b);
+
+void fill_stage_case(const Consts &k, float *M, float *F1, float *F2, double *D, const uint8_t *tag, const int *sid,
+                     const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
+                     DevState *ds, bool fuse_cfl, StageCase *out);
+// Stage `stage` of every case of the table: body entries on sb, plain entries on s.
+// plain_grid / body_grid: blocks of the launch (<= 0 or >= the entries: one
+// block per entry; fewer: persistent blocks striding over the table).
+// with_body = false launches the plain-tile kernel only.
+void launch_stage_f32_batch(const StageBatch &b, int stage, int plain_grid, int body_grid, cudaStream_t s,
+                            cudaStream_t sb, bool with_body);
+
+// ---- batching support (capi.cu), used by the request loop (serve.cu) ----
+// FP32-bulk explicit RK3 cases advance through batched stage launches.
+bool case_batchable(const ibm_case *c);
+// Work that must precede batched steps, on the case stream: the first
+// classification and, for the fused CFL rule, the first dt (as ibm_step does
+// outside its graph).
+ibm_status case_prepare_batch(ibm_case *c);
+// Per-step work before the stages, on the case stream: re-classification and
+// stencils of a moving body, and dt unless stage 3 provides it.  Returns the
+// kernels enqueued (0: nothing to do).  Graph-capturable.
+int case_enqueue_prestage(ibm_case *c);
+void case_stage_desc(const ibm_case *c, StageCase *out);
+cudaStream_t case_stream(const ibm_case *c);
+void case_add_launches(ibm_case *c, long long n);
 
 }  // namespace ibm

@@ -3,26 +3,48 @@
 //
 // Requests (body, grid, flow, motion, number of steps) wait in a host queue
 // and are admitted while a slot and enough device memory are free; each
-// admitted case owns its device state and a stream, is classified once and
-// then advanced in chunks of steps (CUDA-graph replays), so the kernels of all
-// admitted cases overlap on the device.  A case that has taken all its steps
-// is retired: its forces are read, its memory freed, and the next waiting
-// request can take the slot.  Requests are independent, so a case gives the
-// same result alone and in a mix.
+// admitted case owns its device state, tags and lists.
+//
+// Batched mode (default) for FP32-bulk explicit RK3 cases: the requests
+// admitted in one pass of the loop form groups of cases of similar size (grids
+// within a factor four in cells) and equal step counts, up to MAX_BATCH cases
+// per group.  One step of a group is one CUDA graph: the per-case work that
+// precedes the stages (re-classification and stencils of moving bodies, dt)
+// forked onto the cases' own streams, then per RK stage ONE launch of the
+// plain-tile kernel and one of the body-tile kernel over the block table of all
+// member cases.  A group's membership is fixed when it forms, so its graph is
+// captured once and its members finish together; requests that arrive later
+// form new groups, which run beside the old ones on their own streams.  A small
+// autotuner picks the plain-tile launch's schedule (one block per table entry,
+// or a persistent grid striding over the table) by timing the candidates on
+// the group itself, once per size class and membership size.
+//
+// Other cases (FP64, dual time), and every case when batching is off, advance
+// on their own streams in chunks of steps replayed from their own graphs.
+//
+// A case that has taken all its steps is retired: its forces and time are
+// read, its memory freed, and the next waiting request can take the slot.
+// Cases share nothing on the device and the batched kernels run per table
+// entry the same code as the single-case kernels, so a request gives the same
+// result alone and in any mix.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <new>
 #include <vector>
 
-#include "ibm.h"
+#include "ibm_internal.cuh"
 
 extern "C" ibm_status ibm__noalloc_fail(ibm_status s, const char *msg);  // sets ibm_last_error()
 
 namespace {
+
+using namespace ibm;
 
 struct Request {
   int64_t id;
@@ -36,16 +58,39 @@ struct Request {
   ibm_result res;
 };
 
+struct Group;
+
 struct Active {
-  Request *req;
-  ibm_case *c;
-  cudaStream_t stream;
-  cudaEvent_t done;     // recorded after the last enqueued chunk
-  int launched;         // steps enqueued so far
+  Request *req = nullptr;
+  ibm_case *c = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;  // own-stream mode: recorded after the last enqueued chunk
+  cudaEvent_t join = nullptr;  // batched mode: end of the case's pre-stage work inside the group step
+  int launched = 0;            // steps enqueued so far
+  Group *group = nullptr;
+  bool prestage = false;       // has per-step work before the stages
+};
+
+struct Group {
+  int bucket = 0;
+  std::vector<Active *> members;
+  cudaStream_t s = nullptr, sb = nullptr;
+  cudaEvent_t fork = nullptr, join_b = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool dirty = true;
+  long long graph_kernels = 0;
+  int plain_grid = 0;
+  StageBatch *batch = nullptr;  // the group's block table (kernel parameter of the stage launches)
 };
 
 double now_s(const std::chrono::steady_clock::time_point &t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// size class: cell counts within a factor four share a group
+int bucket_of(const Request *r) {
+  const double cells = (double)r->grid.nx * (double)r->grid.ny;
+  return (int)std::floor(std::log2(cells) / 2.0);
 }
 
 }  // namespace
@@ -54,12 +99,49 @@ struct ibm_server {
   size_t budget = 0, used = 0;
   int max_active = 0;
   int chunk = 0;
+  int mode = IBM_SERVE_BATCHED | IBM_SERVE_AUTOTUNE;
   int64_t next_id = 1;
+  int nsms = 152;
   std::chrono::steady_clock::time_point t0;
   std::deque<Request *> pending;
-  std::vector<Active> active;
+  std::vector<Active *> active;
+  std::vector<Group *> groups;
   std::map<int64_t, Request *> all;
+  std::map<int, int> tuned;  // (size class, membership class) -> plain-tile grid (0: one block per entry)
+  int64_t stats[IBM_SERVER_NSTATS] = {};
 };
+
+static void group_destroy(Group *g) {
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  for (cudaEvent_t e : {g->fork, g->join_b, g->done, g->t0, g->t1})
+    if (e) cudaEventDestroy(e);
+  if (g->sb) cudaStreamDestroy(g->sb);
+  if (g->s) cudaStreamDestroy(g->s);
+  delete g->batch;
+  delete g;
+}
+
+static Group *group_create(int bucket) {
+  Group *g = new (std::nothrow) Group();
+  if (!g) return nullptr;
+  g->bucket = bucket;
+  g->batch = new (std::nothrow) StageBatch();
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaError_t e = g->batch ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g->sb, cudaStreamNonBlocking, hi);
+  for (cudaEvent_t *ev : {&g->fork, &g->join_b, &g->done})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&g->t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&g->t1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    group_destroy(g);
+    return nullptr;
+  }
+  return g;
+}
 
 extern "C" ibm_status ibm_server_create(size_t device_bytes_budget, int max_active, int steps_per_chunk,
                                         ibm_server **out) {
@@ -76,11 +158,28 @@ extern "C" ibm_status ibm_server_create(size_t device_bytes_budget, int max_acti
     }
     device_bytes_budget = fr / 10 * 8;
   }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&s->nsms, cudaDevAttrMultiProcessorCount, dev);
   s->budget = device_bytes_budget;
   s->max_active = max_active;
   s->chunk = steps_per_chunk;
   s->t0 = std::chrono::steady_clock::now();
   *out = s;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_server_set_mode(ibm_server *s, int mode) {
+  if (!s || (mode & ~(IBM_SERVE_BATCHED | IBM_SERVE_AUTOTUNE)))
+    return ibm__noalloc_fail(IBM_EINVAL, "ibm_server_set_mode: bad arguments");
+  if (!s->all.empty()) return ibm__noalloc_fail(IBM_ESTATE, "ibm_server_set_mode: requests already submitted");
+  s->mode = mode;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_server_stats(const ibm_server *s, int64_t *out, int n) {
+  if (!s || !out || n < 0 || n > IBM_SERVER_NSTATS) return ibm__noalloc_fail(IBM_EINVAL, "ibm_server_stats: bad arguments");
+  for (int q = 0; q < n; q++) out[q] = s->stats[q];
   return IBM_OK;
 }
 
@@ -113,61 +212,198 @@ extern "C" ibm_status ibm_server_submit(ibm_server *s, const ibm_geometry *geo, 
   return IBM_OK;
 }
 
-static void retire(ibm_server *s, size_t k, ibm_status st) {
-  Active &a = s->active[k];
-  Request *r = a.req;
-  if (st == IBM_OK) st = ibm_forces(a.c, r->res.forces);
+// Read the result, free the case and drop it from its group (the group graph
+// is re-captured before its next launch).  The case's work must be complete.
+static void retire(ibm_server *s, Active *a, ibm_status st) {
+  Request *r = a->req;
+  if (st == IBM_OK) st = ibm_forces(a->c, r->res.forces);
   double tt[2] = {0.0, 0.0};
-  if (st == IBM_OK) st = ibm_get_state(a.c, IBM_TIME, tt, sizeof tt, 0);
+  if (st == IBM_OK) st = ibm_get_state(a->c, IBM_TIME, tt, sizeof tt, 0);
   r->res.t = tt[0];
-  r->res.steps_done = a.launched;
+  r->res.steps_done = a->launched;
   r->res.status = st;
   r->res.state = st == IBM_OK ? IBM_REQ_DONE : IBM_REQ_FAILED;
   r->res.finish_s = now_s(s->t0);
-  ibm_destroy_case(a.c);
-  cudaEventDestroy(a.done);
-  cudaStreamDestroy(a.stream);
+  if (a->group) {
+    auto &m = a->group->members;
+    m.erase(std::remove(m.begin(), m.end(), a), m.end());
+    a->group->dirty = true;
+  }
+  ibm_destroy_case(a->c);
+  if (a->done) cudaEventDestroy(a->done);
+  if (a->join) cudaEventDestroy(a->join);
+  cudaStreamDestroy(a->stream);
   s->used -= r->bytes;
-  s->active.erase(s->active.begin() + (long)k);
+  s->active.erase(std::remove(s->active.begin(), s->active.end(), a), s->active.end());
+  delete a;
+}
+
+// the group's table: member descriptors and tile offsets (kernel parameters of the stage launches)
+static void build_table(Group *g) {
+  const int n = (int)g->members.size();
+  StageCase cs[MAX_BATCH];
+  for (int q = 0; q < n; q++) case_stage_desc(g->members[q]->c, &cs[q]);
+  build_stage_batch(cs, n, g->batch);
+}
+
+// Capture one step of the group: pre-stage work of each member on its own
+// stream, then the three batched stages (body entries on sb, plain on s).
+static ibm_status capture_group(ibm_server *s, Group *g) {
+  build_table(g);
+  const StageBatch &b = *g->batch;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return ibm__noalloc_fail(IBM_ECUDA, "request loop: stream capture failed");
+  }
+  long long nk = 0;
+  bool any_pre = false;
+  for (Active *a : g->members) any_pre |= a->prestage;
+  if (any_pre) {
+    cudaEventRecord(g->fork, g->s);
+    for (Active *a : g->members) {
+      if (!a->prestage) continue;
+      cudaStreamWaitEvent(a->stream, g->fork, 0);
+      nk += case_enqueue_prestage(a->c);
+      cudaEventRecord(a->join, a->stream);
+      cudaStreamWaitEvent(g->s, a->join, 0);
+    }
+  }
+  for (int st = 1; st <= 3; st++) {
+    cudaEventRecord(g->fork, g->s);
+    cudaStreamWaitEvent(g->sb, g->fork, 0);
+    launch_stage_f32_batch(b, st, g->plain_grid, 0, g->s, g->sb, true);
+    cudaEventRecord(g->join_b, g->sb);
+    cudaStreamWaitEvent(g->s, g->join_b, 0);
+    nk += (b.plain_start[b.n] > 0) + (b.body_start[b.n] > 0);
+  }
+  cudaError_t e = cudaStreamEndCapture(g->s, &graph);
+  if (e == cudaSuccess && g->graph) {
+    // same topology (only the table and pointers changed): update the executable graph in place
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(g->graph, graph, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(g->graph);
+      g->graph = nullptr;
+    }
+  }
+  if (e == cudaSuccess && !g->graph) e = cudaGraphInstantiate(&g->graph, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g->graph = nullptr;
+    cudaGetLastError();
+    return ibm__noalloc_fail(IBM_ECUDA, "request loop: group graph capture failed");
+  }
+  g->graph_kernels = nk;
+  g->dirty = false;
+  s->stats[0]++;
+  return IBM_OK;
+}
+
+// Autotuner: time the plain-tile kernel of stage 1 over the group's table
+// under each candidate schedule and keep the fastest for this size class and
+// membership size.  Between steps that kernel is free of side effects on the
+// solution: it reads the mirror of U^n and writes only the stage-1 array and
+// the stage times, which the next step's stage 1 rewrites.
+static void autotune(ibm_server *s, Group *g) {
+  int mclass = 0;
+  while ((2 << mclass) <= (int)g->members.size()) mclass++;
+  const int key = g->bucket * 16 + mclass;
+  auto it = s->tuned.find(key);
+  if (it != s->tuned.end()) {
+    g->plain_grid = it->second;
+    return;
+  }
+  const int entries = g->batch->plain_start[g->batch->n];
+  const int cands[3] = {0, 6 * s->nsms, 3 * s->nsms};
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int ci = 0; ci < 3; ci++) {
+    const int grid = cands[ci];
+    if (ci > 0 && grid >= entries) continue;
+    launch_stage_f32_batch(*g->batch, 1, grid, 0, g->s, g->sb, false);  // warm-up
+    cudaEventRecord(g->t0, g->s);
+    for (int rep = 0; rep < 3; rep++) launch_stage_f32_batch(*g->batch, 1, grid, 0, g->s, g->sb, false);
+    cudaEventRecord(g->t1, g->s);
+    cudaEventSynchronize(g->t1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->t0, g->t1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = grid;
+    }
+  }
+  cudaGetLastError();
+  s->tuned[key] = best;
+  g->plain_grid = best;
+  s->stats[3]++;
 }
 
 extern "C" ibm_status ibm_server_progress(ibm_server *s, int *n_active, int *n_pending) {
   if (!s) return ibm__noalloc_fail(IBM_EINVAL, "ibm_server_progress: server is NULL");
-  // retire cases whose last chunk has finished and that have taken all their steps
-  for (size_t k = 0; k < s->active.size();) {
-    Active &a = s->active[k];
-    cudaError_t q = cudaEventQuery(a.done);
-    if (q == cudaErrorNotReady) {
-      k++;
-      continue;
-    }
+  // 1. retire: own-stream cases whose last chunk finished, group members whose group step finished
+  std::vector<Active *> snapshot = s->active;
+  for (Active *a : snapshot) {
+    cudaError_t q = a->group ? cudaEventQuery(a->group->done) : cudaEventQuery(a->done);
+    if (q == cudaErrorNotReady) continue;
     if (q != cudaSuccess) {
       cudaGetLastError();
-      retire(s, k, IBM_ECUDA);
-      continue;
+      retire(s, a, IBM_ECUDA);
+    } else if (a->launched >= a->req->nsteps) {
+      retire(s, a, a->req->res.status == IBM_OK ? IBM_OK : (ibm_status)a->req->res.status);
     }
-    if (a.launched >= a.req->nsteps) {
-      retire(s, k, IBM_OK);
-      continue;
-    }
-    k++;
   }
-  // admit waiting requests, in arrival order, while a slot and memory are free
-  while (!s->pending.empty() && (int)s->active.size() < s->max_active && s->used + s->pending.front()->bytes <= s->budget) {
+  for (size_t k = 0; k < s->groups.size();) {
+    if (s->groups[k]->members.empty() && cudaEventQuery(s->groups[k]->done) != cudaErrorNotReady) {
+      cudaGetLastError();
+      group_destroy(s->groups[k]);
+      s->groups.erase(s->groups.begin() + (long)k);
+    } else {
+      k++;
+    }
+  }
+  // 2. admit waiting requests, in arrival order, while a slot and memory are free.  Batchable requests
+  // admitted in this pass form new groups by (size class, steps): a group's membership is fixed when it
+  // is formed, so its step graph is captured once and all its members finish together.
+  std::map<long long, Group *> forming;
+  while (!s->pending.empty() && (int)s->active.size() < s->max_active &&
+         s->used + s->pending.front()->bytes <= s->budget) {
     Request *r = s->pending.front();
     s->pending.pop_front();
-    Active a{};
-    a.req = r;
-    cudaError_t e = cudaStreamCreateWithFlags(&a.stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming);
-    ibm_status st = e == cudaSuccess ? ibm_create_case(&r->geo, &r->grid, &r->flow, &r->motion, a.stream, &a.c)
-                                     : IBM_ECUDA;
-    if (st == IBM_OK) st = ibm_classify(a.c);
+    Active *a = new (std::nothrow) Active();
+    ibm_status st = a ? IBM_OK : IBM_ENOMEM;
+    cudaError_t e = cudaSuccess;
+    if (st == IBM_OK) e = cudaStreamCreateWithFlags(&a->stream, cudaStreamNonBlocking);
+    if (st == IBM_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&a->done, cudaEventDisableTiming);
+    if (st == IBM_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&a->join, cudaEventDisableTiming);
+    if (st == IBM_OK && e != cudaSuccess) st = IBM_ECUDA;
+    if (st == IBM_OK) st = ibm_create_case(&r->geo, &r->grid, &r->flow, &r->motion, a->stream, &a->c);
+    const bool batched = st == IBM_OK && (s->mode & IBM_SERVE_BATCHED) && case_batchable(a->c) && r->nsteps > 0;
+    if (st == IBM_OK) st = batched ? case_prepare_batch(a->c) : ibm_classify(a->c);
+    Group *g = nullptr;
+    if (st == IBM_OK && batched) {
+      const long long key = (long long)bucket_of(r) << 32 | (long long)r->nsteps;
+      auto it = forming.find(key);
+      if (it != forming.end() && (int)it->second->members.size() < MAX_BATCH) g = it->second;
+      if (!g) {
+        g = group_create(bucket_of(r));
+        if (g) {
+          s->groups.push_back(g);
+          forming[key] = g;
+        } else {
+          st = IBM_ECUDA;
+        }
+      }
+    }
     if (st != IBM_OK) {
       cudaGetLastError();
-      if (a.c) ibm_destroy_case(a.c);
-      if (a.done) cudaEventDestroy(a.done);
-      if (a.stream) cudaStreamDestroy(a.stream);
+      if (a) {
+        if (a->c) ibm_destroy_case(a->c);
+        if (a->done) cudaEventDestroy(a->done);
+        if (a->join) cudaEventDestroy(a->join);
+        if (a->stream) cudaStreamDestroy(a->stream);
+        delete a;
+      }
       r->res.status = st;
       r->res.state = IBM_REQ_FAILED;
       r->res.finish_s = now_s(s->t0);
@@ -176,22 +412,65 @@ extern "C" ibm_status ibm_server_progress(ibm_server *s, int *n_active, int *n_p
     r->res.state = IBM_REQ_RUNNING;
     r->res.start_s = now_s(s->t0);
     s->used += r->bytes;
-    cudaEventRecord(a.done, a.stream);
+    a->req = r;
+    cudaEventRecord(a->done, a->stream);
+    if (g) {
+      // the group's next step starts after the case's set-up work
+      a->group = g;
+      // a moving body is re-classified and its dt reduced before the stages of every step; a static body's dt
+      // comes from stage 3 (or is fixed)
+      a->prestage = r->motion.kind != IBM_MOTION_STATIC;
+      g->members.push_back(a);
+      g->dirty = true;
+      cudaStreamWaitEvent(g->s, a->done, 0);
+    }
     s->active.push_back(a);
   }
-  // enqueue the next chunk of steps of every case whose previous chunk is done
-  for (Active &a : s->active) {
-    if (a.launched >= a.req->nsteps) continue;
-    if (cudaEventQuery(a.done) == cudaErrorNotReady) continue;
-    const int n = a.req->nsteps - a.launched < s->chunk ? a.req->nsteps - a.launched : s->chunk;
-    ibm_status st = ibm_step(a.c, n);
+  // 3a. own-stream cases: enqueue the next chunk of every case whose previous chunk is done
+  for (Active *a : s->active) {
+    if (a->group || a->launched >= a->req->nsteps) continue;
+    if (cudaEventQuery(a->done) == cudaErrorNotReady) continue;
+    const int n = std::min(a->req->nsteps - a->launched, s->chunk);
+    ibm_status st = ibm_step(a->c, n);
     if (st != IBM_OK) {
-      a.launched = a.req->nsteps;  // retired (as failed) on the next round
-      a.req->res.status = st;
+      a->launched = a->req->nsteps;  // retired (as failed) on the next pass
+      a->req->res.status = st;
     } else {
-      a.launched += n;
+      a->launched += n;
     }
-    cudaEventRecord(a.done, a.stream);
+    cudaEventRecord(a->done, a->stream);
+  }
+  // 3b. groups: next chunk of group steps (no member takes more steps than it asked for)
+  for (Group *g : s->groups) {
+    if (g->members.empty()) continue;
+    if (cudaEventQuery(g->done) == cudaErrorNotReady) continue;
+    int n = s->chunk;
+    for (Active *a : g->members) n = std::min(n, a->req->nsteps - a->launched);
+    if (n <= 0) continue;  // a member is finished; it is retired on the next pass
+    ibm_status st = IBM_OK;
+    if (g->dirty) {
+      const auto h0 = std::chrono::steady_clock::now();
+      if (s->mode & IBM_SERVE_AUTOTUNE) {
+        build_table(g);
+        autotune(s, g);
+      }
+      st = capture_group(s, g);
+      s->stats[4] += (int64_t)(1e6 * std::chrono::duration<double>(std::chrono::steady_clock::now() - h0).count());
+    }
+    for (int q = 0; q < n && st == IBM_OK; q++)
+      if (cudaGraphLaunch(g->graph, g->s) != cudaSuccess) st = IBM_ECUDA;
+    if (st != IBM_OK) {
+      cudaGetLastError();
+      for (Active *a : g->members) {
+        a->launched = a->req->nsteps;
+        a->req->res.status = st;
+      }
+    } else {
+      for (Active *a : g->members) a->launched += n;
+      s->stats[1] += n;
+      s->stats[2] += n * g->graph_kernels;
+    }
+    cudaEventRecord(g->done, g->s);
   }
   if (n_active) *n_active = (int)s->active.size();
   if (n_pending) *n_pending = (int)s->pending.size();
@@ -208,10 +487,13 @@ extern "C" ibm_status ibm_server_poll(ibm_server *s, int64_t id, ibm_result *out
 
 extern "C" ibm_status ibm_server_destroy(ibm_server *s) {
   if (!s) return IBM_OK;
+  for (Group *g : s->groups) cudaStreamSynchronize(g->s);
   while (!s->active.empty()) {
-    cudaStreamSynchronize(s->active.back().stream);
-    retire(s, s->active.size() - 1, IBM_ESTATE);
+    Active *a = s->active.back();
+    cudaStreamSynchronize(a->stream);
+    retire(s, a, IBM_ESTATE);
   }
+  for (Group *g : s->groups) group_destroy(g);
   for (auto &kv : s->all) delete kv.second;
   delete s;
   return IBM_OK;

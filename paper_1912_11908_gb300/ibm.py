@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libibm_gb300.so")
 
 IBM_OK, IBM_EINVAL, IBM_ENOMEM, IBM_ECAPACITY, IBM_ESTENCIL, IBM_ECUDA, IBM_ESTATE = range(7)
-IBM_STATE_FP64, IBM_TAGS, IBM_LIST_COUNTS, IBM_STENCILS, IBM_TIME, IBM_STEPS = range(6)
+IBM_STATE_FP64, IBM_TAGS, IBM_LIST_COUNTS, IBM_STENCILS, IBM_TIME, IBM_STEPS, IBM_TUNING = range(7)
 STATUS_NAMES = {0: "IBM_OK", 1: "IBM_EINVAL", 2: "IBM_ENOMEM", 3: "IBM_ECAPACITY", 4: "IBM_ESTENCIL",
                 5: "IBM_ECUDA", 6: "IBM_ESTATE"}
 
@@ -60,8 +60,10 @@ EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_
            "ibm_sync", "ibm_destroy_case", "ibm_case_device_bytes", "ibm_launch_count", "ibm_last_error",
            "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs", "ibm_tag_nodes_noalloc",
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
-           "ibm_server_destroy"]
+           "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats", "ibm_autotune"]
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
+SERVE_BATCHED, SERVE_AUTOTUNE = 1, 2
+SERVER_STATS = ["group_graphs", "group_steps", "group_kernels", "autotune_runs", "capture_us"]
 PROFILE_GROUPS = ["residual_stage", "ib_reconstruct", "domain_halo", "time_step", "geometry", "step_end"]
 
 
@@ -96,6 +98,8 @@ def load():
     L.ibm_profile_enable.argtypes = [vp, ip]
     L.ibm_profile_read.argtypes = [vp, vp, vp, ip]
     L.ibm_use_graphs.argtypes = [vp, ip]
+    L.ibm_autotune.argtypes = [vp, ip]
+    L.ibm_autotune.restype = ip
     L.ibm_tag_nodes_noalloc.argtypes = [ctypes.POINTER(ibm_grid), vp, ip, vp, vp, ctypes.c_int32, vp, vp]
     L.ibm_tag_nodes_noalloc.restype = ip
     L.ibm_server_create.argtypes = [sz, ip, ip, ctypes.POINTER(vp)]
@@ -105,8 +109,10 @@ def load():
     L.ibm_server_progress.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.ibm_server_poll.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ibm_result)]
     L.ibm_server_destroy.argtypes = [vp]
+    L.ibm_server_set_mode.argtypes = [vp, ip]
+    L.ibm_server_stats.argtypes = [vp, vp, ip]
     for name in ("ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
-                 "ibm_server_destroy"):
+                 "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats"):
         getattr(L, name).restype = ip
     for name in ("ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state",
                  "ibm_forces", "ibm_sync", "ibm_destroy_case", "ibm_profile_enable", "ibm_profile_read",
@@ -262,6 +268,14 @@ class Case:
     def launches(self):
         return int(lib().ibm_launch_count(self.h))
 
+    def autotune(self, enable):
+        _check(lib().ibm_autotune(self.h, int(enable)))
+
+    def tuning(self):
+        out = np.zeros(1, np.int32)
+        _check(lib().ibm_get_state(self.h, IBM_TUNING, out.ctypes.data_as(ctypes.c_void_p), 4, 0))
+        return int(out[0])
+
     def use_graphs(self, enable):
         _check(lib().ibm_use_graphs(self.h, 1 if enable else 0))
 
@@ -286,11 +300,18 @@ class Server:
     returns the request's record as a dict.
     """
 
-    def __init__(self, device_bytes_budget=0, max_active=16, steps_per_chunk=10):
+    def __init__(self, device_bytes_budget=0, max_active=16, steps_per_chunk=10,
+                 mode=SERVE_BATCHED | SERVE_AUTOTUNE):
         h = ctypes.c_void_p()
         _check(lib().ibm_server_create(int(device_bytes_budget), int(max_active), int(steps_per_chunk),
                                        ctypes.byref(h)))
         self.h = h
+        _check(lib().ibm_server_set_mode(self.h, int(mode)))
+
+    def stats(self):
+        out = np.zeros(len(SERVER_STATS), np.int64)
+        _check(lib().ibm_server_stats(self.h, out.ctypes.data_as(ctypes.c_void_p), len(SERVER_STATS)))
+        return dict(zip(SERVER_STATS, (int(v) for v in out)))
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

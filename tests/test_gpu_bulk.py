@@ -95,3 +95,26 @@ def test_bulk_moving_body_vs_fp64_oracle(ibm, orc):
         assert abs(fg[0] - fo[0]) <= 1e-3 and abs(fg[1] - fo[1]) <= 1e-3, (fg, fo)
     err = _compare(g, o)
     assert max(err.values()) <= 1e-3, err
+
+
+def test_autotuned_register_budgets_agree(ibm):
+    """The plain stage kernel's register-budget variants compute the same scheme: a case run with the
+    autotuner's pick agrees with one run on the compiler's default budget up to FP32 rounding, and the
+    pick is cached per grid size."""
+    spec = W.wedge_m2_re1e4(192, 96, precision=W.PREC_FP32_BULK)
+    a = ibm.Case(spec)
+    a.autotune(False)
+    a.step(40)
+    assert a.tuning() == 0
+    b = ibm.Case(spec)
+    assert b.tuning() == -1
+    b.step(40)
+    v = b.tuning()
+    assert 0 <= v <= 2
+    c = ibm.Case(spec)
+    c.step(1)
+    assert c.tuning() == v
+    fa, fb = a.forces(), b.forces()
+    np.testing.assert_allclose(fb, fa, rtol=1e-5, atol=1e-5 * np.abs(fa).max())
+    with pytest.raises(ibm.IbmError):
+        b.autotune(True)  # only before the first step
