@@ -139,8 +139,9 @@ enum {
   IBM_STENCILS = 3,     /* ibm_stencil[#IB + #G1 + #G2 + #G3], IB first then G1, G2, G3, each in row-major order */
   IBM_TIME = 4,         /* double[2]: t, last dt */
   IBM_STEPS = 5,        /* int64_t: steps taken */
-  IBM_TUNING = 6        /* int32_t (host only): register-budget variant of the FP32-bulk plain stage kernel
-                           picked by the autotuner (0..2; -1 before the first step, or FP64) */
+  IBM_TUNING = 6        /* int32_t[2] (host only): register-budget variants of the FP32-bulk plain stage
+                           kernel picked by the autotuner for stage 1 and for stages 2-3 (0..2; -1 before
+                           the first step, or FP64) */
 };
 
 /* Create a case, initialised to the uniform free stream at t = 0 (no
@@ -196,11 +197,12 @@ int64_t ibm_launch_count(const ibm_case *c);
 ibm_status ibm_profile_enable(ibm_case *c, int enable);
 ibm_status ibm_profile_read(ibm_case *c, double *ms, int64_t *launches, int n_groups);
 
-/* Autotuning (default on).  FP32-bulk cases time the plain-tile stage kernel
- * under three register budgets (six, five and four resident blocks per SM)
- * on their first ibm_step -- a few extra launches and one host wait -- and
- * keep the fastest; the choice is cached per device and grid size for the
- * process.  enable = 0 uses the compiler's default budget.  Results do not
+/* Autotuning (default on).  FP32-bulk explicit cases time the stage kernels
+ * (plain tiles and the concurrent body tiles) under three register budgets of
+ * the plain kernel (six, five and four resident blocks per SM), separately
+ * for stage 1 and stage 2, on their first ibm_step -- about a hundred extra
+ * launches and a few host waits -- and keep the fastest (stage 3 follows
+ * stage 2); the choice is cached per device and grid size for the process.  enable = 0 uses the compiler's default budget.  Results do not
  * depend on the choice beyond FP32 rounding.  Only before the first step
  * (IBM_ESTATE afterwards). */
 ibm_status ibm_autotune(ibm_case *c, int enable);
@@ -270,7 +272,9 @@ ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, in
  * striding over the table) is picked by timing the candidates on the group,
  * once per size class and membership size.  Other requests (FP64, dual time),
  * and all requests when batching is off, advance on their own streams as
- * described above.  Results do not depend on the mode or the mix.
+ * described above.  Results do not depend on the mix; they are bit-identical
+ * to a case stepped alone on the own-stream path and equal up to FP32
+ * rounding in a group (its kernels are compiled separately).
  *
  * The server is driven by the caller's thread: ibm_server_progress does one
  * non-blocking pass (retire finished cases, admit waiting requests, enqueue

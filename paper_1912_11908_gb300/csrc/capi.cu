@@ -36,7 +36,8 @@ struct ibm_case {
   uint8_t *tile_body = nullptr;  // FP32-bulk: stage tiles that rebuild IB / ghost nodes
   int *body_tiles = nullptr;
   int body_cap = 0;
-  int plain_variant = -1;  // FP32-bulk: register budget of the plain stage kernel (-1: not tuned yet)
+  int plain_variant[2] = {-1, -1};  // FP32-bulk: register budget of the plain stage kernel for stage 1 and for
+                                    // stages 2-3 (-1: not tuned yet)
   bool autotune = true;
   int box_w = 0, box_h = 0;      // cells spanned by the body's bounding box (any pose), for classification
   cudaStream_t sb = nullptr;     // FP32-bulk: stream of the body-tile kernels (forked from / joined to stream)
@@ -160,7 +161,6 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
   if (fl->time_scheme == IBM_TIME_DUAL) {
     if (!(fl->dt_phys > 0) || !(fl->cfl_tau > 0) || fl->subiters < 1)
       return fail(IBM_EINVAL, "dual time needs dt_phys > 0, cfl_tau > 0, subiters >= 1");
-    if (fl->precision != IBM_PREC_FP64) return fail(IBM_EINVAL, "dual time runs in FP64");
   }
   return IBM_OK;
 }
@@ -197,6 +197,12 @@ static size_t carve(ibm_case *c, char *base) {
     take(&c->M, 4 * plane);
     take(&c->F1, 4 * plane);
     take(&c->F2, 4 * plane);
+    if (k.dual) {  // FP64 pseudo-stage iterates and time levels
+      take(&c->B, 4 * plane);
+      take(&c->C, 4 * plane);
+      take(&c->Wn, 4 * plane);
+      take(&c->Wm, 4 * plane);
+    }
     take(&c->rst, (size_t)(c->cap > 0 ? c->cap : 1));
     take(&c->sid, ncell);
     take(&c->tile_body, (size_t)stage_tiles(k));
@@ -450,7 +456,8 @@ extern "C" ibm_status ibm_classify(ibm_case *c) {
 // FP32-bulk with a static body and the CFL rule: the last stage of each step
 // computes the next step's dt (the fluid set cannot change between steps)
 static bool fused_cfl(const ibm_case *c) {
-  return c->precision == IBM_PREC_FP32_BULK && c->k.motion.kind == IBM_MOTION_STATIC && !(c->k.dt_fixed > 0.0);
+  return c->precision == IBM_PREC_FP32_BULK && c->k.motion.kind == IBM_MOTION_STATIC && !(c->k.dt_fixed > 0.0) &&
+         !c->k.dual;
 }
 
 // one explicit step on the case stream (kernels only; graph-capturable)
@@ -470,6 +477,25 @@ static int enqueue_step(ibm_case *c) {
     cudaMemcpyAsync(c->Wn, c->A, bytes, cudaMemcpyDeviceToDevice, s);
     double *din[3] = {c->A, c->B, c->C};
     double *dout[3] = {c->B, c->C, c->A};
+    if (c->precision == IBM_PREC_FP32_BULK) {
+      // FP32 residual of the mirror, FP64 point-implicit update; IB / ghost nodes rebuilt in the tile loads
+      float *fin[3] = {c->M, c->F1, c->F2};
+      float *fout[3] = {c->F1, c->F2, c->M};
+      for (int it = 0; it < c->k.subiters; it++)
+        for (int st = 1; st <= 3; st++) {
+          prof_mark(c, 0, true);
+          cudaEventRecord(c->ev_fork, s);
+          cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
+          launch_dual_f32(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->Wn, c->Wm, c->tag,
+                          c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, s, c->sb);
+          cudaEventRecord(c->ev_join, c->sb);
+          cudaStreamWaitEvent(s, c->ev_join, 0);
+          prof_mark(c, 0, false);
+          nl += 1 + (c->body_cap > 0);
+        }
+      launch_dual_end(c->k, c->ds, s);
+      return nl + 1;
+    }
     for (int it = 0; it < c->k.subiters; it++)
       for (int st = 1; st <= 3; st++) {
         prof_mark(c, 1, true);
@@ -509,8 +535,8 @@ static int enqueue_step(ibm_case *c) {
       cudaEventRecord(c->ev_fork, s);
       cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
       launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->tile_body,
-                       c->body_tiles, c->body_cap, c->ds, fuse_cfl, s, c->sb, c->plain_variant < 0 ? 0 : c->plain_variant,
-                       true);
+                       c->body_tiles, c->body_cap, c->ds, fuse_cfl, s, c->sb,
+                       c->plain_variant[st == 1 ? 0 : 1] < 0 ? 0 : c->plain_variant[st == 1 ? 0 : 1], true);
       cudaEventRecord(c->ev_join, c->sb);
       cudaStreamWaitEvent(s, c->ev_join, 0);
       if (c->body_cap > 0) nl += 1;
@@ -521,18 +547,21 @@ static int enqueue_step(ibm_case *c) {
   return nl;
 }
 
-// Autotuner of the FP32-bulk step: time the plain-tile kernel of stage 1 under
-// each register budget (resident blocks per SM) and keep the fastest, once per
-// device and grid size for the whole process.  Between steps that kernel has
-// no effect on the solution: it reads the mirror of U^n and writes only the
-// stage-1 array and the stage times, which the step's own stage 1 rewrites.
+// Autotuner of the FP32-bulk step: time the stage pair (plain-tile kernel and
+// concurrent body-tile kernel, as in the step) under each register budget of
+// the plain kernel, separately for stage 1 and stage 2, in interleaved rounds
+// keeping each candidate's best time; stage 3 takes stage 2's choice.  Picked
+// once per device and grid size for the whole process.  Between steps stages
+// 1 and 2 leave the solution unchanged: they read the mirror of U^n (and the
+// stage-1 array) and write the stage arrays, the stage times, and U^n on IB /
+// ghost nodes with the values the step's own stage 1 writes again.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, int> g_tuned;
+static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;
 
 static ibm_status tune_plain_variant(ibm_case *c) {
-  if (c->precision != IBM_PREC_FP32_BULK || c->plain_variant >= 0) return IBM_OK;
-  if (!c->autotune) {
-    c->plain_variant = 0;
+  if (c->precision != IBM_PREC_FP32_BULK || c->plain_variant[0] >= 0) return IBM_OK;
+  if (!c->autotune || c->k.dual) {  // dual time has its own kernels
+    c->plain_variant[0] = c->plain_variant[1] = 0;
     return IBM_OK;
   }
   const auto key = std::make_tuple(c->device, c->k.nx, c->k.ny);
@@ -540,44 +569,56 @@ static ibm_status tune_plain_variant(ibm_case *c) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      c->plain_variant = it->second;
+      c->plain_variant[0] = it->second.first;
+      c->plain_variant[1] = it->second.second;
       return IBM_OK;
     }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  int best = 0;
-  float best_ms = 1e30f;
   const bool fuse = fused_cfl(c);
-  for (int v = 0; v < PLAIN_VARIANTS; v++) {
-    auto launch = [&]() {
-      launch_stage_f32(c->k, 1, c->M, c->M, c->F1, c->A, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles,
-                       c->body_cap, c->ds, fuse, c->stream, c->sb, v, false);
-    };
-    launch();  // warm-up
-    cudaEventRecord(e0, c->stream);
-    for (int rep = 0; rep < 3; rep++) launch();
-    cudaEventRecord(e1, c->stream);
-    float ms = 0.f;
-    cudaError_t e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return fail(IBM_ECUDA, "autotuning failed: %s", cudaGetErrorString(e));
-    }
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = v;
-    }
-  }
+  cudaStream_t s = c->stream;
+  auto pair = [&](int stage, int v) {
+    cudaEventRecord(c->ev_fork, s);
+    cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
+    launch_stage_f32(c->k, stage, c->M, stage == 1 ? c->M : c->F1, stage == 1 ? c->F1 : c->F2, c->A, c->tag, c->sid,
+                     c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, s, c->sb, v, true);
+    cudaEventRecord(c->ev_join, c->sb);
+    cudaStreamWaitEvent(s, c->ev_join, 0);
+  };
+  constexpr int ROUNDS = 3, REPS = 5;
+  float best[2][PLAIN_VARIANTS];
+  for (int st = 0; st < 2; st++)
+    for (int v = 0; v < PLAIN_VARIANTS; v++) best[st][v] = 1e30f;
+  pair(1, 0);  // stage-1 array for the stage-2 timings
+  long long nl = 0;
+  cudaError_t e = cudaSuccess;
+  for (int round = 0; round < ROUNDS && e == cudaSuccess; round++)
+    for (int st = 0; st < 2 && e == cudaSuccess; st++)
+      for (int v = 0; v < PLAIN_VARIANTS && e == cudaSuccess; v++) {
+        pair(st + 1, v);  // warm-up
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < REPS; rep++) pair(st + 1, v);
+        cudaEventRecord(e1, s);
+        nl += (REPS + 1) * (1 + (c->body_cap > 0));
+        float ms = 0.f;
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best[st][v]) best[st][v] = ms;
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->launches += 4 * PLAIN_VARIANTS;
-  c->plain_variant = best;
+  if (e != cudaSuccess) return fail(IBM_ECUDA, "autotuning failed: %s", cudaGetErrorString(e));
+  for (int st = 0; st < 2; st++) {
+    int b = 0;
+    for (int v = 1; v < PLAIN_VARIANTS; v++)
+      if (best[st][v] < best[st][b]) b = v;
+    c->plain_variant[st] = b;
+  }
+  c->launches += nl + 1 + (c->body_cap > 0);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tuned[key] = best;
+  g_tuned[key] = std::make_pair(c->plain_variant[0], c->plain_variant[1]);
   return IBM_OK;
 }
 
@@ -619,7 +660,7 @@ extern "C" ibm_status ibm_step(ibm_case *c, int nsteps) {
     c->launches += nl;
     c->dt_valid = true;
   }
-  if (c->plain_variant < 0) {
+  if (c->plain_variant[0] < 0) {
     ibm_status r = tune_plain_variant(c);
     if (r != IBM_OK) return r;
   }
@@ -683,7 +724,7 @@ extern "C" ibm_status ibm_autotune(ibm_case *c, int enable) {
   if (!c) return fail(IBM_EINVAL, "case is NULL");
   if (c->graph) return fail(IBM_ESTATE, "ibm_autotune: the case has already stepped");
   c->autotune = enable != 0;
-  c->plain_variant = -1;
+  c->plain_variant[0] = c->plain_variant[1] = -1;
   return IBM_OK;
 }
 
@@ -818,9 +859,10 @@ extern "C" ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t byt
       break;
     }
     case IBM_TUNING: {
-      if (bytes < sizeof(int32_t) || dst_on_device) return fail(IBM_EINVAL, "IBM_TUNING: host int32 destination");
-      const int32_t v = c->plain_variant;
-      std::memcpy(dst, &v, sizeof v);
+      if (bytes < 2 * sizeof(int32_t) || dst_on_device)
+        return fail(IBM_EINVAL, "IBM_TUNING: host int32[2] destination");
+      const int32_t v[2] = {c->plain_variant[0], c->plain_variant[1]};
+      std::memcpy(dst, v, sizeof v);
       break;
     }
     default:

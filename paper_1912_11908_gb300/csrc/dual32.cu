@@ -1,0 +1,50 @@
+// Dual-time pseudo stages in FP32-bulk form (Sec. 2): FP32 perturbation
+// residual with preconditioned faces, FP64 point-implicit update (per-tile
+// code in stage32.cuh).  A module of its own: kernels added to the module of
+// the explicit stage kernels slowed the replay of explicit step graphs by
+// ~10% on GB300 (measured; kernel durations themselves unchanged).
+#include "stage32.cuh"
+
+namespace ibm {
+
+// Dual-time pseudo stage of one case (FP32 residual, FP64 point-implicit
+// update): plain tiles and body tiles as for the explicit stages.
+template <int STAGE, bool BODY>
+__global__ void __launch_bounds__(256) k_dual_f32(Consts k, PertConsts c, const float *__restrict__ In,
+                                                  float *Out32, double *D, const uint8_t *__restrict__ tag,
+                                                  const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
+                                                  const uint8_t *__restrict__ tile_body,
+                                                  const int *__restrict__ body_tiles, DevState *ds, unsigned int ncfl,
+                                                  DualPtrs dp) {
+  stage_tile<STAGE, BODY, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body, body_tiles, ds, false, ncfl,
+                                (int)blockIdx.x, dp);
+}
+
+void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,
+                     double *Out64, const double *Wn, const double *Wm, const uint8_t *tag, const int *sid,
+                     const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
+                     DevState *ds, cudaStream_t s, cudaStream_t sb) {
+  PertConsts c = pert_consts(k);
+  const int nt = stage_tiles(k);
+  const int nb = body_cap > 0 ? body_cap : 0;
+  const unsigned int ncfl = (unsigned int)(nt + nb);
+  DualPtrs dp;
+  dp.In64 = In64;
+  dp.Out64 = Out64;
+  dp.Wn = Wn;
+  dp.Wm = Wm;
+#define IBM_DUAL_PAIR(S)                                                                                          \
+  do {                                                                                                            \
+    if (nb)                                                                                                       \
+      k_dual_f32<S, true><<<nb, 256, 0, sb>>>(k, c, In32, Out32, D, tag, sid, rs, tile_body, body_tiles, ds, ncfl, \
+                                              dp);                                                                \
+    k_dual_f32<S, false><<<nt, 256, 0, s>>>(k, c, In32, Out32, D, tag, sid, rs, tile_body, body_tiles, ds, ncfl,   \
+                                            dp);                                                                  \
+  } while (0)
+  if (stage == 1) IBM_DUAL_PAIR(1);
+  else if (stage == 2) IBM_DUAL_PAIR(2);
+  else IBM_DUAL_PAIR(3);
+#undef IBM_DUAL_PAIR
+}
+
+}  // namespace ibm

@@ -235,6 +235,14 @@ void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, fl
                       const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                       const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
                       cudaStream_t sb, int plain_variant, bool with_body);
+// Dual-time pseudo stage (1..3) in FP32-bulk form: residual of the FP32
+// mirror In32, FP64 point-implicit update of the iterate In64 into Out64 (and
+// its mirror Out32); D holds the sub-iteration's starting iterate, Wn / Wm
+// the time levels n and n-1 (all FP64 perturbations).  Body tiles on sb.
+void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,
+                     double *Out64, const double *Wn, const double *Wm, const uint8_t *tag, const int *sid,
+                     const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
+                     DevState *ds, cudaStream_t s, cudaStream_t sb);
 // The same two kernels over a group's block table: the plain kernel (stream s) covers tiles
 // without IB / ghost nodes near them; the body kernel (stream sb, may run
 // concurrently) covers the listed body tiles and rebuilds IB and ghost nodes

@@ -24,9 +24,11 @@
 //
 // A case that has taken all its steps is retired: its forces and time are
 // read, its memory freed, and the next waiting request can take the slot.
-// Cases share nothing on the device and the batched kernels run per table
-// entry the same code as the single-case kernels, so a request gives the same
-// result alone and in any mix.
+// Cases share nothing on the device and every kernel is deterministic, so a
+// request gives the same result alone and in any mix: bit for bit on its own
+// stream (the kernels of a case stepped alone), and up to FP32 rounding in a
+// group, whose block-table kernels compile the same per-tile source
+// separately (fused multiply-adds may round differently).
 #include <cuda_runtime.h>
 
 #include <algorithm>

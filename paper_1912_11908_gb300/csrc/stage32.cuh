@@ -52,9 +52,16 @@ __device__ __forceinline__ void prim_pert(const PertConsts &c, float pp, float u
 // tangent.  Momentum flux drops the constant p_inf n (its divergence is
 // zero); D_L + D_R - 1 is formed in factored form for two subsonic sides so
 // p_inf (D_L + D_R - 1) keeps its precision.
+//
+// PRE (dual time, Sec. 2): the low-Mach numerical sound speed
+// c' = 1/2 sqrt((1 - Mr^2)^2 un^2 + 4 Mr^2 c^2), Mr^2 = (Ur/c)^2 with
+// Ur = min(c, max(|V|, U_ref, nu/dn, c/3)) from face averages (idn = 1/dn),
+// scales the mass-flux (dissipation) part; the pressure split keeps the
+// physical face Mach numbers, as in the FP64 path.
+template <bool PRE = false>
 __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float unL, float utL, float ppL,
                                            float drR, float unR, float utR, float ppR, float un_inf, float ut_inf,
-                                           float F[4]) {
+                                           float F[4], float idn = 0.f) {
   const float rL = 1.f + drL, rR = 1.f + drR;
   const float irL = 1.f / rL, irR = 1.f / rR;
   const float cL = sqrtf(c.gamma * (c.R + ppL) * irL), cR = sqrtf(c.gamma * (c.R + ppR) * irR);
@@ -62,7 +69,18 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
                    0.5f * ((unL - un_inf) * (unL + un_inf) + (utL - ut_inf) * (utL + ut_inf));
   const float HR = c.gg * (ppR - c.R * drR) * irR +
                    0.5f * ((unR - un_inf) * (unR + un_inf) + (utR - ut_inf) * (utR + ut_inf));
-  const float cs = 0.5f * (cL + cR);
+  const float cb = 0.5f * (cL + cR);
+  float cs = cb, mr2 = 1.f;
+  if (PRE) {
+    const float ub = 0.5f * (unL + unR), vb = 0.5f * (utL + utR);
+    const float Vm = sqrtf(ub * ub + vb * vb);
+    const float rb = 0.5f * (rL + rR);
+    float Ur = fmaxf(fmaxf(Vm, 1.f), c.mu / rb * idn);
+    Ur = fminf(fmaxf(Ur, (float)UR_FLOOR * cb), cb);
+    mr2 = fminf((Ur / cb) * (Ur / cb), 1.f);
+    const float om = 1.f - mr2;
+    cs = 0.5f * sqrtf(om * om * ub * ub + 4.f * mr2 * cb * cb);
+  }
   const float ics = 1.f / cs;
   const float ML = unL * ics, MR = unR * ics;
   const float aL = ML >= 0.f ? 1.f : 0.f;
@@ -80,11 +98,26 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
   const float MhP = Mh * (1.f - (dp + adp) * ic2 * irL);
   const float MhM = Mh * (1.f - (adp - dp) * ic2 * irR);
   const float Cp = CVL - MhP, Cm = CVR + MhM;
-  const float PpL = MpL * (2.f - ML);
-  const float PmR = -MmR * (2.f + MR);
-  const float DL = aL * (1.f + bL) - bL * PpL;
-  const float DR = aR * (1.f + bR) - bR * PmR;
-  const float Dm1 = (subL && subR) ? 0.25f * (MR - ML) * (MR * MR + MR * ML + ML * ML - 3.f) : (DL + DR - 1.f);
+  float DL, DR, Dm1;
+  if (PRE && mr2 < 1.f) {
+    // pressure split with the physical face Mach numbers
+    const float icb = 1.f / cb;
+    const float pML = unL * icb, pMR = unR * icb;
+    const float paL = pML >= 0.f ? 1.f : 0.f, paR = pMR >= 0.f ? 0.f : 1.f;
+    const bool psL = fabsf(pML) < 1.f, psR = fabsf(pMR) < 1.f;
+    const float pbL = psL ? -1.f : 0.f, pbR = psR ? -1.f : 0.f;
+    const float PpL = 0.25f * (pML + 1.f) * (pML + 1.f) * (2.f - pML);
+    const float PmR = 0.25f * (pMR - 1.f) * (pMR - 1.f) * (2.f + pMR);
+    DL = paL * (1.f + pbL) - pbL * PpL;
+    DR = paR * (1.f + pbR) - pbR * PmR;
+    Dm1 = (psL && psR) ? 0.25f * (pMR - pML) * (pMR * pMR + pMR * pML + pML * pML - 3.f) : (DL + DR - 1.f);
+  } else {
+    const float PpL = MpL * (2.f - ML);
+    const float PmR = -MmR * (2.f + MR);
+    DL = aL * (1.f + bL) - bL * PpL;
+    DR = aR * (1.f + bR) - bR * PmR;
+    Dm1 = (subL && subR) ? 0.25f * (MR - ML) * (MR * MR + MR * ML + ML * ML - 3.f) : (DL + DR - 1.f);
+  }
   const float mL = rL * cs * Cp, mR = rR * cs * Cm;
   F[0] = mL + mR;
   F[1] = mL * unL + mR * unR + c.R * Dm1 + DL * ppL + DR * ppR;
@@ -120,6 +153,119 @@ __device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float 
     for (int w = 1; w < 8; w++) m = fmaxf(m, red[w]);
     atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong((double)m));
     finish_cfl(k, ds, nblocks);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dual time in FP32-bulk form (Sec. 2).  The residual of a pseudo stage is the
+// FP32 perturbation residual above (preconditioned LDFSS faces); the
+// point-implicit update of each fluid cell runs in FP64:
+//   [T Gamma / dtau + a T dW/dQ] dQ = -(R' + BDF'),   a = 3/(2 dt) or 1/dt,
+// in perturbation variables W' = T W (T subtracts H_inf times the mass row
+// from the energy row), so the energy rows of the Weiss-Smith matrices carry
+// H - H_inf instead of H and never cancel against H_inf; R' = -L is the FP32
+// residual, BDF' is formed from the FP64 iterates and time levels, the 4x4
+// system is solved exactly in FP64 through its structure (solve_precond),
+// Q' = (p', u, v, T') is updated and combined with the sub-iteration's start
+// as SSP-RK3 stage, and the new iterate is stored in FP64 with its FP32
+// mirror.
+// ---------------------------------------------------------------------------
+struct DualPtrs {
+  const double *In64;    // FP64 iterate the stage starts from (perturbation)
+  double *Out64;         // FP64 iterate it produces
+  const double *Wn, *Wm; // FP64 states at time levels n and n-1 (perturbation)
+};
+
+// FP64 perturbation conserved -> (p', u, v, T')
+__device__ __forceinline__ void pert_prim64(const Consts &k, double dr, double dmx, double dmy, double W,
+                                            double q[4]) {
+  const double r = 1.0 + dr, ir = 1.0 / r;
+  const double u = (k.uinf[0] + dmx) * ir, v = (k.uinf[1] + dmy) * ir;
+  const double du = (dmx - dr * k.uinf[0]) * ir, dv = (dmy - dr * k.uinf[1]) * ir;
+  const double dq = du * (u + k.uinf[0]) + dv * (v + k.uinf[1]);
+  const double ke = 0.5 * (dr * (u * u + v * v) + dq);
+  const double pp = (k.gamma - 1.0) * (W + k.Hinf * dr - ke);
+  q[0] = pp;
+  q[1] = u;
+  q[2] = v;
+  q[3] = (pp - k.R * dr) * ir / k.R;
+}
+
+// (p', u, v, T') -> FP64 perturbation conserved
+__device__ __forceinline__ void prim_pert64(const Consts &k, const double q[4], double w[4]) {
+  const double pp = q[0], u = q[1], v = q[2], Tp = q[3];
+  const double dr = (pp - k.R * Tp) / (k.R * (1.0 + Tp));
+  const double dq = (u - k.uinf[0]) * (u + k.uinf[0]) + (v - k.uinf[1]) * (v + k.uinf[1]);
+  const double ke = 0.5 * (dr * (u * u + v * v) + dq);
+  w[0] = dr;
+  w[1] = dr * u + (u - k.uinf[0]);
+  w[2] = dr * v + (v - k.uinf[1]);
+  w[3] = pp / (k.gamma - 1.0) + ke - k.Hinf * dr;
+}
+
+// Exact solution of the point-implicit system in perturbation rows.  With
+// s = 1/dtau + a the operator is s times the Weiss-Smith matrix whose first
+// column parameter is tau = (theta_G/dtau + a theta_J) / s (the other columns
+// are shared by Gamma and dW/dQ), so the momentum rows give du, dv directly
+// (after subtracting u, v times the first row) and the first and energy rows
+// leave a 2x2 system in dp, dT:
+//   tau dp + rho_T dT = S0/s,   -dp + rho cp dT = (S3 - dH S0)/s - rho (u du + v dv).
+__device__ __forceinline__ void solve_precond(double s, double tau, double r, double u, double v, double rT,
+                                              double cpv, double dH, const double S[4], double dQ[4]) {
+  const double is = 1.0 / s, irs = is / r;
+  const double du = (S[1] - u * S[0]) * irs;
+  const double dv = (S[2] - v * S[0]) * irs;
+  const double X = (S[3] - dH * S[0]) * is - r * (u * du + v * dv);
+  const double Y = S[0] * is;
+  const double dT = (Y + tau * X) / (tau * r * cpv + rT);
+  dQ[0] = r * cpv * dT - X;
+  dQ[1] = du;
+  dQ[2] = dv;
+  dQ[3] = dT;
+}
+
+// pseudo stage STAGE of one fluid cell (id: state index); L = FP32 residual
+template <int STAGE>
+__device__ __forceinline__ void dual_update_cell(const Consts &k, const PertConsts &c, long long id, long long P,
+                                                 const float L[4], const double *Q0w, const DualPtrs &dp,
+                                                 float *Out32, bool bdf2) {
+  const double idt = 1.0 / k.dt_phys;
+  double W[4], S[4], Qk[4];
+  for (int v = 0; v < 4; v++) W[v] = dp.In64[id + v * P];
+  pert_prim64(k, W[0], W[1], W[2], W[3], Qk);
+  for (int v = 0; v < 4; v++) {
+    const long long o = id + v * P;
+    const double tdt = bdf2 ? (3.0 * W[v] - 4.0 * dp.Wn[o] + dp.Wm[o]) * (0.5 * idt) : (W[v] - dp.Wn[o]) * idt;
+    S[v] = (double)L[v] - tdt;  // -(R' + BDF') with R' = -L
+  }
+  const double r = 1.0 + W[0], ir = 1.0 / r, u = Qk[1], v = Qk[2], T = 1.0 + Qk[3], iT = 1.0 / T;
+  const double cs = sqrt(k.gamma * (k.R + Qk[0]) * ir), ics = 1.0 / cs;
+  const double Vm = sqrt(u * u + v * v);
+  double Ur = fmax(fmax(Vm, 1.0), k.mu * ir / k.dmin);
+  Ur = fmin(fmax(Ur, UR_FLOOR * cs), cs);
+  const double mr2 = (Ur * ics) * (Ur * ics);
+  const double up = 0.5 * Vm * (1.0 + mr2);
+  const double om = 1.0 - mr2;
+  const double cp_ = 0.5 * sqrt(om * om * Vm * Vm + 4.0 * Ur * Ur);
+  const double lam = (up + cp_) * ((double)c.idx + (double)c.idy) + (double)c.vis * ir;
+  const double idtau = lam / k.cfl_tau;
+  const double a = bdf2 ? 1.5 * idt : idt;
+  const double thG = 1.0 / (Ur * Ur) + iT / k.cp, thJ = iT / k.R;
+  const double s = idtau + a;
+  const double tau = (thG * idtau + a * thJ) / s;
+  const double dH = k.cp * Qk[3] + 0.5 * ((u - k.uinf[0]) * (u + k.uinf[0]) + (v - k.uinf[1]) * (v + k.uinf[1]));
+  double dQ[4];
+  solve_precond(s, tau, r, u, v, -r * iT, k.cp, dH, S, dQ);
+  double Q0[4], Qn[4], Wo[4];
+  pert_prim64(k, Q0w[id], Q0w[id + P], Q0w[id + 2 * P], Q0w[id + 3 * P], Q0);
+  for (int q = 0; q < 4; q++) {
+    const double e = Qk[q] + dQ[q];
+    Qn[q] = STAGE == 1 ? e : (STAGE == 2 ? 0.75 * Q0[q] + 0.25 * e : (1.0 / 3.0) * Q0[q] + (2.0 / 3.0) * e);
+  }
+  prim_pert64(k, Qn, Wo);
+  for (int q = 0; q < 4; q++) {
+    dp.Out64[id + q * P] = Wo[q];
+    Out32[id + q * P] = (float)Wo[q];
   }
 }
 
@@ -176,13 +322,16 @@ static __device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts
 // ---------------------------------------------------------------------------
 // blk: the block's index within this case's launch (plain: tile index; body:
 // slot in the body-tile list).  Every thread of the block calls it.
-template <int STAGE, bool BODY>
+// DUAL: a pseudo stage of dual time -- preconditioned faces, wall motion at
+// t + dt_phys, FP64 point-implicit update (dp; D holds the sub-iteration's
+// start, Out receives the FP32 mirror of the new iterate).
+template <int STAGE, bool BODY, bool DUAL = false>
 __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c, float *Mn,
                                            const float *__restrict__ In, float *Out, double *D,
                                            const uint8_t *__restrict__ tag, const int *__restrict__ sid,
                                            const RStencil32 *__restrict__ rs, const uint8_t *__restrict__ tile_body,
                                            const int *__restrict__ body_tiles, DevState *ds, bool fuse_cfl,
-                                           unsigned int ncfl, int blk) {
+                                           unsigned int ncfl, int blk, const DualPtrs &dp = DualPtrs{}) {
   __shared__ float sq[4][HY][HX];  // rho', u, v, p'
   __shared__ float sT[HY][HX];     // T'
   __shared__ float fLx[4][TY][TX + 1], fRx[4][TY][TX + 1];  // x-face states; fLx then holds the x flux
@@ -198,7 +347,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     tile = blk < ds->nbody_tiles ? body_tiles[blk] : -1;
   } else {
     tile = tile_body[blk] ? -1 : blk;
-    if (blk == 0 && threadIdx.x == 0) {
+    if (!DUAL && blk == 0 && threadIdx.x == 0) {
       if (STAGE == 1) {  // stage times for the body kernels of stages 2 and 3
         ds->tst[0] = ds->t + dtd;
         ds->tst[1] = ds->t + 0.5 * dtd;
@@ -226,7 +375,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
   }
   if (BODY && threadIdx.x == 0) {
     double X[2], V[2], Acc[2];
-    motion_at(k.motion, STAGE == 1 ? ds->t : ds->tst[STAGE - 2], X, V, Acc);
+    motion_at(k.motion, DUAL ? ds->t + k.dt_phys : (STAGE == 1 ? ds->t : ds->tst[STAGE - 2]), X, V, Acc);
     wm[0] = (float)V[0];
     wm[1] = (float)V[1];
     wm[2] = (float)Acc[0];
@@ -398,7 +547,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
           qR[v] = sq[v][b][a1];
         }
       }
-      ldfss_pert(c, qL[0], qL[1], qL[2], qL[3], qR[0], qR[1], qR[2], qR[3], c.ux, c.uy, F);
+      ldfss_pert<DUAL>(c, qL[0], qL[1], qL[2], qL[3], qR[0], qR[1], qR[2], qR[3], c.ux, c.uy, F, idx);
       const float ux = (sq[1][b][a1] - sq[1][b][a]) * idx;
       const float vx = (sq[2][b][a1] - sq[2][b][a]) * idx;
       const float Tx = (sT[b][a1] - sT[b][a]) * idx;
@@ -425,7 +574,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
           qR[v] = sq[v][b1][a];
         }
       }
-      ldfss_pert(c, qL[0], qL[2], qL[1], qL[3], qR[0], qR[2], qR[1], qR[3], c.uy, c.ux, F);
+      ldfss_pert<DUAL>(c, qL[0], qL[2], qL[1], qL[3], qR[0], qR[2], qR[1], qR[3], c.uy, c.ux, F, idy);
       const float uy = (sq[1][b1][a] - sq[1][b][a]) * idy;
       const float vy = (sq[2][b1][a] - sq[2][b][a]) * idy;
       const float Ty = (sT[b1][a] - sT[b][a]) * idy;
@@ -448,7 +597,9 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     float L[4];
     for (int v = 0; v < 4; v++)
       L[v] = -((fLx[v][ty][tx + 1] - fLx[v][ty][tx]) * idx + (fLy[v][ty + 1][tx] - fLy[v][ty][tx]) * idy);
-    if (STAGE == 1) {
+    if (DUAL) {
+      dual_update_cell<STAGE>(k, c, id, P, L, D, dp, Out, ds->steps > 0);
+    } else if (STAGE == 1) {
       for (int v = 0; v < 4; v++) Out[id + v * P] = Mn[id + v * P] + dt * L[v];
     } else if (STAGE == 2) {
       for (int v = 0; v < 4; v++) Out[id + v * P] = 0.75f * Mn[id + v * P] + 0.25f * (In[id + v * P] + dt * L[v]);
@@ -465,7 +616,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
       }
       if (fuse_cfl) lam = cfl_lambda(k, c, mnew);
     }
-  } else if (BODY && STAGE == 3 && inside && mytag != SOLID) {
+  } else if (!DUAL && BODY && STAGE == 3 && inside && mytag != SOLID) {
     // IB / ghost node: the mirror of U^{n+1} takes the value rebuilt at stage 1
     for (int v = 0; v < 4; v++) Mn[id + v * P] = (float)D[id + v * P];
   }

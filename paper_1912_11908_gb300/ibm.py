@@ -272,9 +272,10 @@ class Case:
         _check(lib().ibm_autotune(self.h, int(enable)))
 
     def tuning(self):
-        out = np.zeros(1, np.int32)
-        _check(lib().ibm_get_state(self.h, IBM_TUNING, out.ctypes.data_as(ctypes.c_void_p), 4, 0))
-        return int(out[0])
+        """Register-budget variants of the plain stage kernel: (stage 1, stages 2-3)."""
+        out = np.zeros(2, np.int32)
+        _check(lib().ibm_get_state(self.h, IBM_TUNING, out.ctypes.data_as(ctypes.c_void_p), 8, 0))
+        return int(out[0]), int(out[1])
 
     def use_graphs(self, enable):
         _check(lib().ibm_use_graphs(self.h, 1 if enable else 0))
