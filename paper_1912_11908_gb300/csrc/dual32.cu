@@ -1,8 +1,8 @@
 // Dual-time pseudo stages in FP32-bulk form (Sec. 2): FP32 perturbation
 // residual with preconditioned faces, FP64 point-implicit update (per-tile
-// code in stage32.cuh).  A module of its own: kernels added to the module of
-// the explicit stage kernels slowed the replay of explicit step graphs by
-// ~10% on GB300 (measured; kernel durations themselves unchanged).
+// code in stage32.cuh).  A module of its own, like the block-table kernels:
+// the explicit stage kernels' module holds only what an explicit step
+// launches.
 #include "stage32.cuh"
 
 namespace ibm {

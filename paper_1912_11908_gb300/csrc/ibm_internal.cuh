@@ -197,7 +197,7 @@ void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, 
                        DevState *ds, cudaStream_t s);
 int stage_tiles(const Consts &k);
 struct PertConsts {  // FP32 copies of the free-stream constants
-  float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin, vis;
+  float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin, vis, cp;
 };
 
 __host__ inline PertConsts pert_consts(const Consts &k) {
@@ -215,6 +215,7 @@ __host__ inline PertConsts pert_consts(const Consts &k) {
   c.idy = (float)(1.0 / k.dy);
   c.dmin = (float)k.dmin;
   c.vis = (float)((2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy)));
+  c.cp = (float)k.cp;
   return c;
 }
 

@@ -238,24 +238,28 @@ __device__ __forceinline__ void dual_update_cell(const Consts &k, const PertCons
     const double tdt = bdf2 ? (3.0 * W[v] - 4.0 * dp.Wn[o] + dp.Wm[o]) * (0.5 * idt) : (W[v] - dp.Wn[o]) * idt;
     S[v] = (double)L[v] - tdt;  // -(R' + BDF') with R' = -L
   }
-  const double r = 1.0 + W[0], ir = 1.0 / r, u = Qk[1], v = Qk[2], T = 1.0 + Qk[3], iT = 1.0 / T;
-  const double cs = sqrt(k.gamma * (k.R + Qk[0]) * ir), ics = 1.0 / cs;
-  const double Vm = sqrt(u * u + v * v);
-  double Ur = fmax(fmax(Vm, 1.0), k.mu * ir / k.dmin);
-  Ur = fmin(fmax(Ur, UR_FLOOR * cs), cs);
-  const double mr2 = (Ur * ics) * (Ur * ics);
-  const double up = 0.5 * Vm * (1.0 + mr2);
-  const double om = 1.0 - mr2;
-  const double cp_ = 0.5 * sqrt(om * om * Vm * Vm + 4.0 * Ur * Ur);
-  const double lam = (up + cp_) * ((double)c.idx + (double)c.idy) + (double)c.vis * ir;
-  const double idtau = lam / k.cfl_tau;
-  const double a = bdf2 ? 1.5 * idt : idt;
-  const double thG = 1.0 / (Ur * Ur) + iT / k.cp, thJ = iT / k.R;
-  const double s = idtau + a;
-  const double tau = (thG * idtau + a * thJ) / s;
+  // pseudo-time coefficients (local dtau, preconditioning parameter) in FP32: they set the pseudo-time path,
+  // not the fixed point R' + BDF' = 0
+  const double r = 1.0 + W[0], u = Qk[1], v = Qk[2];
+  const float rf = (float)r, irf = 1.f / rf, uf = (float)u, vf = (float)v;
+  const float Tf = 1.f + (float)Qk[3], iTf = 1.f / Tf;
+  const float csf = sqrtf(c.gamma * (c.R + (float)Qk[0]) * irf), icsf = 1.f / csf;
+  const float Vm = sqrtf(uf * uf + vf * vf);
+  float Ur = fmaxf(fmaxf(Vm, 1.f), c.mu * irf / c.dmin);
+  Ur = fminf(fmaxf(Ur, (float)UR_FLOOR * csf), csf);
+  const float mr2 = (Ur * icsf) * (Ur * icsf);
+  const float up = 0.5f * Vm * (1.f + mr2);
+  const float om = 1.f - mr2;
+  const float cp_ = 0.5f * sqrtf(om * om * Vm * Vm + 4.f * Ur * Ur);
+  const float lam = (up + cp_) * (c.idx + c.idy) + c.vis * irf;
+  const float idtau = lam / (float)k.cfl_tau;
+  const float af = bdf2 ? 1.5f * (float)idt : (float)idt;
+  const float thG = 1.f / (Ur * Ur) + iTf / c.cp, thJ = iTf / c.R;
+  const float sf = idtau + af;
+  const float tau = (thG * idtau + af * thJ) / sf;
   const double dH = k.cp * Qk[3] + 0.5 * ((u - k.uinf[0]) * (u + k.uinf[0]) + (v - k.uinf[1]) * (v + k.uinf[1]));
   double dQ[4];
-  solve_precond(s, tau, r, u, v, -r * iT, k.cp, dH, S, dQ);
+  solve_precond((double)sf, (double)tau, r, u, v, -(double)(rf * iTf), k.cp, dH, S, dQ);
   double Q0[4], Qn[4], Wo[4];
   pert_prim64(k, Q0w[id], Q0w[id + P], Q0w[id + 2 * P], Q0w[id + 3 * P], Q0);
   for (int q = 0; q < 4; q++) {
