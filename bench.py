@@ -37,6 +37,7 @@ WORKLOADS = {
     "wedge_768x384": "wedge_m2_re1e4",
     "cylinder_160x80": "cylinder_m02_re40",
     "osc_cylinder_1024x512": "oscillating_cylinder_m02_re185",
+    "naca_dual_2048x1024": "naca0012_a5_m0001",
 }
 # algorithmic DRAM bytes per cell and stage of the fused residual kernel
 # (each stage reads its input planes and tags once and writes its output once;
@@ -46,6 +47,12 @@ BYTES_PER_CELL_STAGE = {"fp32_bulk": 179.0 / 3.0, "fp64": 259.0 / 3.0}
 # formulas, FMA = 2): WENO5 per variable and direction 91 (x 4 x 2), LDFSS
 # 110 per face (x 2), viscous 40 per face (x 2), primitives 25, update 20
 FLOPS_PER_CELL_STAGE = 91 * 8 + 110 * 2 + 40 * 2 + 25 + 20
+# dual time, FP32-bulk: algorithmic DRAM bytes per cell and pseudo stage (FP32 tile 16 + tag 1 + FP64 iterate
+# 32 + sub-iteration start 32 + time levels n, n-1 64 + FP64 output 32 + FP32 mirror 16) and FP64 flops per cell
+# and pseudo stage of the point-implicit update (counted from the formulas: BDF2 term 28, two conversions to
+# primitives 66, enthalpy 9, structured solve 27, stage combination 16, conversion back 29, misc 2)
+DUAL_BYTES_PER_CELL_STAGE = 193.0
+DUAL_FP64_FLOPS_PER_CELL = 177
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
 def fp32_peak_tflops(sm_mhz=2070.0):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -75,16 +82,22 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _traffic(kernel_file):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
-    p = os.path.join(ROOT, "profiles", "k_stage_f32_wedge768x384.json")
+def source_sha256(files):
+    """sha256 over the concatenated kernel sources (paper_1912_11908_gb300/csrc)."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1912_11908_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def _traffic(summary):
+    """DRAM bytes per launch from a committed ncu summary (profiles/*.json), if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    src = os.path.join(ROOT, "paper_1912_11908_gb300", "csrc", kernel_file)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if d.get("source_sha256") != h:
+    if d.get("source_sha256") != source_sha256(d.get("sources", [])):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -197,7 +210,9 @@ def run_ours(args, rank, world):
         t = torch.tensor([t_dev_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_dev_ms = float(t.item())
-    units = cells * 3 * args.steps * world
+    is_dual = spec["time_scheme"] == 1
+    stages_per_step = 3 * spec["subiters"] if is_dual else 3
+    units = cells * stages_per_step * args.steps * world
     value = units / (t_dev_ms * 1e-3) / 1e6
 
     # live kernel timing for the roofline: the same steps with CUDA events around every kernel group
@@ -209,13 +224,24 @@ def run_ours(args, rank, world):
     case.profile(False)
     stage_ms, stage_launches = prof["residual_stage"]
     stage_avg_ms = stage_ms / max(1, stage_launches)
-    bpc = BYTES_PER_CELL_STAGE[args.precision]
+    bpc = DUAL_BYTES_PER_CELL_STAGE if is_dual else BYTES_PER_CELL_STAGE[args.precision]
     bytes_per_launch = bpc * spec["nx"] * spec["ny"]
     achieved = bytes_per_launch / (stage_avg_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _traffic("flow32.cu" if args.precision == "fp32_bulk" else "flow.cu")
-    flops_per_launch = FLOPS_PER_CELL_STAGE * spec["nx"] * spec["ny"]
+    if args.precision == "fp32_bulk":
+        traffic = _traffic("k_dual_f32_naca1024x512.json" if is_dual else "k_stage_f32_wedge768x384.json")
+    else:
+        traffic = None
+    flops_per_launch = (DUAL_FP64_FLOPS_PER_CELL if is_dual else FLOPS_PER_CELL_STAGE) * spec["nx"] * spec["ny"]
     achieved_tf = flops_per_launch / (stage_avg_ms * 1e-3) / 1e12
+    if is_dual:
+        # the FP64 point-implicit update bounds the pseudo stage (GB300 FP64 runs at 1/64 of the FP32 rate)
+        rl_bound, rl_kernel, rl_peak = "fp64", "k_dual_f32 (plain + body tiles)", fp32_peak_tflops() / 64.0
+        rl_src = "derived: FP32 peak / 64 (GB300 FP64 rate)"
+    else:
+        rl_bound, rl_peak = "alu", fp32_peak_tflops()
+        rl_kernel = "k_stage_f32 (plain + body tiles)" if args.precision == "fp32_bulk" else "k_stage_f64"
+        rl_src = "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
 
     # plain FP64 path on the same workload and GPU
     fp64 = None
@@ -307,7 +333,7 @@ def run_ours(args, rank, world):
         t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_e2e = float(t.item())
-    e2e = {"value": cells * 3 * ke * world / t_e2e / 1e6, "unit": "Mcell-updates/s",
+    e2e = {"value": cells * stages_per_step * ke * world / t_e2e / 1e6, "unit": "Mcell-updates/s",
            "h2d_bytes_per_step": int(host.numel() * 8), "d2h_bytes_per_step": int(forces.numel() * 8),
            "steps": ke}
 
@@ -327,15 +353,15 @@ def run_ours(args, rank, world):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32_bulk" else "f64",
-        "data": "synthetic (closed-form wedge, uniform free-stream start)",
+        "data": "synthetic (closed-form body, uniform free-stream start)",
         "config": {"workload": spec["name"], "grid": [spec["nx"], spec["ny"]], "active_cells": cells,
-                   "precision": args.precision, "stages_per_step": 3, "time_scheme": "SSP-RK3",
+                   "precision": args.precision, "stages_per_step": stages_per_step,
+                   "time_scheme": "dual time (BDF2, %d sub-iterations)" % spec["subiters"] if is_dual else "SSP-RK3",
                    "l2": "flushed between timed steps (512 MiB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU", "cuda_graphs": True,
                    "autotuned_plain_variants": list(case.tuning())},
-        "roofline": {"bound": "alu", "kernel": "k_stage_f32 (plain + body tiles)" if args.precision == "fp32_bulk"
-                     else "k_stage_f64", "achieved": achieved_tf, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp32_peak_tflops(), "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+        "roofline": {"bound": rl_bound, "kernel": rl_kernel, "achieved": achieved_tf, "peak": rl_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / rl_peak, "peak_source": rl_src,
                      "flops_per_launch": flops_per_launch, "traffic": traffic, "avg_launch_ms": stage_avg_ms,
                      "timed_launches": stage_launches,
                      "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
