@@ -390,8 +390,10 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
       c->hds->dtf = (float)c->hds->dt;
     }
     // (the copy from pageable memory is staged before the call returns)
+    // fluid, untagged and unlisted everywhere (the geometry kernels keep that outside the body's rectangle)
     if (cudaMemcpyAsync(c->ds, c->hds, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(c->tag, 0, ncell, s) != cudaSuccess) {
+        cudaMemsetAsync(c->tag, 0, ncell, s) != cudaSuccess || cudaMemsetAsync(c->solid, 0, ncell, s) != cudaSuccess ||
+        (c->sid && cudaMemsetAsync(c->sid, 0xff, ncell * sizeof(int), s) != cudaSuccess)) {
       rs = fail(IBM_ECUDA, "state initialisation failed");
       break;
     }
@@ -420,6 +422,16 @@ static ibm_status do_classify(ibm_case *c) {
   cudaStream_t s = c->stream;
   int nl = 0;
   prof_mark(c, 4, true);
+  if (c->g.nv > 0 && c->g.nv <= FUSED_MAX_VERTS) {
+    // pose + classification, tags / lists / tile lists, stencils: three kernels over the body's rectangle
+    nl += launch_fused_geometry(c->k, c->g, c->solid, c->tag, c->st, c->cap, c->rst, c->sid, c->tile_body,
+                                c->body_tiles, c->body_cap, c->box_w, c->box_h, c->ds, s);
+    prof_mark(c, 4, false);
+    c->launches += nl;
+    c->classified = true;
+    CU(cudaGetLastError());
+    return IBM_OK;
+  }
   if (c->g.nv > 0) {
     launch_pose(c->k, c->g, c->ds, s);
     launch_classify(c->k, c->g, c->solid, c->ds, c->box_w, c->box_h, s);
@@ -438,7 +450,7 @@ static ibm_status do_classify(ibm_case *c) {
     }
   }
   if (c->tile_body) {
-    launch_tile_lists(c->k, c->tag, c->tile_body, c->body_tiles, c->body_cap, c->ds, s);
+    launch_tile_lists(c->k, c->tag, c->tile_body, c->body_tiles, c->body_cap, c->ds, c->g.nv > 0, s);
     nl += 2;
   }
   prof_mark(c, 4, false);

@@ -130,14 +130,38 @@ __global__ void __launch_bounds__(256, MINB) k_stage_f32(Consts k, PertConsts c,
 
 int stage_tiles(const Consts &k) { return ((k.nx + TX - 1) / TX) * ((k.ny + TY - 1) / TY); }
 
+// does the tile's loaded range [lo, hi] (before domain mapping) along one axis
+// reach the cells [blo, bhi]?  Outflow and free-stream sides map into / drop
+// the outside cells, so clamping is exact-or-conservative; a periodic side
+// that the range crosses wraps it, so that case answers yes
+__device__ __forceinline__ bool axis_reaches(int lo, int hi, int n, int bc_lo, int bc_hi, int blo, int bhi) {
+  if ((lo < 0 && bc_lo == IBM_BC_PERIODIC) || (hi >= n && bc_hi == IBM_BC_PERIODIC)) return true;
+  lo = max(lo, 0);
+  hi = min(hi, n - 1);
+  return lo <= bhi && hi >= blo;
+}
+
 // flag every stage tile whose cells or 3-cell halo (after domain mapping) hold
-// an IB or ghost node; one warp per tile
-__global__ void k_tile_flags(Consts k, const uint8_t *__restrict__ tag, uint8_t *__restrict__ tile_body) {
+// an IB or ghost node; one warp per tile.  Non-fluid tags lie within one cell
+// of the cells whose centres fall in the body's bounding box, so a tile whose
+// loaded region misses that cell range (ds->bcell, 3-cell margin) has none.
+__global__ void k_tile_flags(Consts k, const uint8_t *__restrict__ tag, uint8_t *__restrict__ tile_body,
+                             const DevState *__restrict__ ds, int has_body) {
   const int ntx = (k.nx + TX - 1) / TX, nt = ntx * ((k.ny + TY - 1) / TY);
   const int tile = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (tile >= nt) return;
   const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
+  if (!has_body) {
+    if (lane == 0) tile_body[tile] = 0;
+    return;
+  }
+  const int ilo = ds->bcell[0], ihi = ds->bcell[1], jlo = ds->bcell[2], jhi = ds->bcell[3];
+  if (!axis_reaches(i0 - NG, i0 + TX + NG - 1, k.nx, k.bc[0], k.bc[1], ilo, ihi) ||
+      !axis_reaches(j0 - NG, j0 + TY + NG - 1, k.ny, k.bc[2], k.bc[3], jlo, jhi)) {
+    if (lane == 0) tile_body[tile] = 0;
+    return;
+  }
   bool hit = false;
   for (int m = lane; m < HX * HY; m += 32) {
     int gi = i0 - NG + m % HX, gj = j0 - NG + m / HX;
@@ -178,9 +202,9 @@ __global__ void __launch_bounds__(1024) k_tile_list(int nt, const uint8_t *__res
 }
 
 void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, int *body_tiles, int body_cap,
-                       DevState *ds, cudaStream_t s) {
+                       DevState *ds, bool has_body, cudaStream_t s) {
   const int nt = stage_tiles(k);
-  k_tile_flags<<<(nt + 7) / 8, 256, 0, s>>>(k, tag, tile_body);
+  k_tile_flags<<<(nt + 7) / 8, 256, 0, s>>>(k, tag, tile_body, ds, has_body ? 1 : 0);
   k_tile_list<<<1, 1024, 0, s>>>(nt, tile_body, body_tiles, body_cap, ds);
 }
 

@@ -10,6 +10,8 @@
 // order.  No transcendental function is used on these paths.
 #include <mutex>
 
+#include <algorithm>
+
 #include "ibm_internal.cuh"
 
 namespace ibm {
@@ -69,23 +71,40 @@ __global__ void k_pose(Consts k, Geom g, DevState *ds) {
     ds->pos[1] = P[1];
   }
   __syncthreads();
+  // each thread keeps the extremes of its own vertices; then warp and block reductions (min / max are exact)
+  double b[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
   for (int v = threadIdx.x; v < g.nv; v += blockDim.x) {
-    g.vx[v] = g.vref[2 * v] + X[0];
-    g.vy[v] = g.vref[2 * v + 1] + X[1];
+    const double x = g.vref[2 * v] + X[0], y = g.vref[2 * v + 1] + X[1];
+    g.vx[v] = x;
+    g.vy[v] = y;
+    b[0] = fmin(b[0], x);
+    b[1] = fmax(b[1], x);
+    b[2] = fmin(b[2], y);
+    b[3] = fmax(b[3], y);
   }
+  for (int off = 16; off > 0; off >>= 1) {
+    b[0] = fmin(b[0], __shfl_xor_sync(0xffffffffu, b[0], off));
+    b[1] = fmax(b[1], __shfl_xor_sync(0xffffffffu, b[1], off));
+    b[2] = fmin(b[2], __shfl_xor_sync(0xffffffffu, b[2], off));
+    b[3] = fmax(b[3], __shfl_xor_sync(0xffffffffu, b[3], off));
+  }
+  __shared__ double wb[32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0)
+    for (int q = 0; q < 4; q++) wb[warp][q] = b[q];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b0 = g.vx[0], b1 = g.vx[0], b2 = g.vy[0], b3 = g.vy[0];
-    for (int v = 1; v < g.nv; v++) {
-      if (g.vx[v] < b0) b0 = g.vx[v];
-      if (g.vx[v] > b1) b1 = g.vx[v];
-      if (g.vy[v] < b2) b2 = g.vy[v];
-      if (g.vy[v] > b3) b3 = g.vy[v];
+    for (int w = 1; w < nw; w++) {
+      b[0] = fmin(b[0], wb[w][0]);
+      b[1] = fmax(b[1], wb[w][1]);
+      b[2] = fmin(b[2], wb[w][2]);
+      b[3] = fmax(b[3], wb[w][3]);
     }
-    ds->bbox[0] = b0;
-    ds->bbox[1] = b1;
-    ds->bbox[2] = b2;
-    ds->bbox[3] = b3;
+    for (int q = 0; q < 4; q++) ds->bbox[q] = b[q];
+    ds->bcell[0] = (int)floor((b[0] - k.x0) / k.dx - 0.5) - 3;
+    ds->bcell[1] = (int)ceil((b[1] - k.x0) / k.dx - 0.5) + 3;
+    ds->bcell[2] = (int)floor((b[2] - k.y0) / k.dy - 0.5) - 3;
+    ds->bcell[3] = (int)ceil((b[3] - k.y0) / k.dy - 0.5) + 3;
   }
 }
 
@@ -195,29 +214,40 @@ __global__ void __launch_bounds__(TAG_BLOCK) k_tag_count(Consts k, const uint8_t
 // exclusive scan of per-block counts for each kind (in place), totals and
 // kind offsets into the concatenated list (IB, G1, G2, G3)
 __global__ void __launch_bounds__(1024) k_scan_blocks(int nblk, int *blockcounts, DevState *ds, int cap) {
-  __shared__ int part[1024][4];
+  __shared__ int wsum[32][4];
   __shared__ int tot[4];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int per = (nblk + 1023) / 1024;
   const int b0 = tid * per, b1 = min(nblk, b0 + per);
   int s[4] = {0, 0, 0, 0};
   for (int b = b0; b < b1; b++)
     for (int q = 0; q < 4; q++) s[q] += blockcounts[b * 4 + q];
-  for (int q = 0; q < 4; q++) part[tid][q] = s[q];
-  __syncthreads();
-  // Hillis-Steele inclusive scan over the 1024 partial sums
-  for (int off = 1; off < 1024; off <<= 1) {
-    int v[4];
-    for (int q = 0; q < 4; q++) v[q] = tid >= off ? part[tid - off][q] : 0;
-    __syncthreads();
-    for (int q = 0; q < 4; q++) part[tid][q] += v[q];
-    __syncthreads();
+  // inclusive scan of the 1024 partial sums: within each warp by shuffles, then over the 32 warp totals
+  int inc[4];
+  for (int q = 0; q < 4; q++) {
+    inc[q] = s[q];
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc[q], off);
+      if (lane >= off) inc[q] += v;
+    }
   }
-  if (tid == 1023)
-    for (int q = 0; q < 4; q++) tot[q] = part[1023][q];
+  if (lane == 31)
+    for (int q = 0; q < 4; q++) wsum[warp][q] = inc[q];
+  __syncthreads();
+  if (warp == 0) {
+    for (int q = 0; q < 4; q++) {
+      int w = wsum[lane][q];
+      for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += v;
+      }
+      wsum[lane][q] = w;  // inclusive over warps
+      if (lane == 31) tot[q] = w;
+    }
+  }
   __syncthreads();
   int run[4];
-  for (int q = 0; q < 4; q++) run[q] = part[tid][q] - s[q];
+  for (int q = 0; q < 4; q++) run[q] = inc[q] - s[q] + (warp > 0 ? wsum[warp - 1][q] : 0);
   for (int b = b0; b < b1; b++)
     for (int q = 0; q < 4; q++) {
       int c = blockcounts[b * 4 + q];
@@ -343,137 +373,547 @@ __device__ __forceinline__ int warp_argmin(double v, int idx) {
   return src;
 }
 
-// Sec. 4.1-4.6, Sec. 5: one stencil per listed node, one warp per node.  The
-// lanes split the segments of the two exhaustive searches (closest feature,
-// boundary point); the warp keeps the (distance, segment) lexicographic
-// minimum, which is the first minimum of a sequential scan.
+// lexicographic (value, index) minimum across a 128-thread block; every
+// thread gets the winning thread's index.  sv / si / ss: 4-entry shared arrays
+__device__ __forceinline__ int block_argmin128(double v, int idx, double *sv, int *si, int *ss) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int src = warp_argmin(v, idx);
+  const double wv = __shfl_sync(0xffffffffu, v, src);
+  const int wi = __shfl_sync(0xffffffffu, idx, src);
+  if (lane == 0) {
+    sv[w] = wv;
+    si[w] = wi;
+    ss[w] = w * 32 + src;
+  }
+  __syncthreads();
+  double bv = sv[0];
+  int bi = si[0], bs = ss[0];
+  for (int q = 1; q < 4; q++)
+    if (sv[q] < bv || (sv[q] == bv && si[q] < bi)) {
+      bv = sv[q];
+      bi = si[q];
+      bs = ss[q];
+    }
+  __syncthreads();
+  return bs;
+}
+
+// Sec. 4.1-4.6, Sec. 5: one stencil per listed node, one 128-thread block per
+// node (blocks stride over the list).  The threads split the segments of the
+// two exhaustive searches (closest feature, boundary point); the block keeps
+// the (distance, segment) lexicographic minimum, which is the first minimum of
+// a sequential scan.
+// rs / sid (optional): the FP32 compact form of each stencil and the cell ->
+// stencil map of the FP32-bulk reconstruction.
 __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_t *__restrict__ tag,
-                                                  ibm_stencil *__restrict__ st, int cap, DevState *ds) {
-  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+                                                  ibm_stencil *__restrict__ st, int cap, DevState *ds,
+                                                  RStencil32 *__restrict__ rs, int *__restrict__ sid) {
+  __shared__ double s_v[4];
+  __shared__ int s_i[4], s_s[4];
+  __shared__ double s_d[4];
+  __shared__ int s_n[2];
   const int total = min(ds->offset[4], cap);
-  if (e >= total) return;
-  ibm_stencil s = st[e];
-  const int kind = s.kind;
-  const int i = s.cell % k.nx, j = s.cell / k.nx;
-  const double px = k.x0 + ((double)i + 0.5) * k.dx;
-  const double py = k.y0 + ((double)j + 0.5) * k.dy;
-  const int nv = g.nv;
-  // closest feature (Sec. 4.1)
-  double best = INFINITY, bcx = 0.0, bcy = 0.0;
-  int bseg = 0x7fffffff, bfeat = 0, breg = 0;
-  for (int kk = lane; kk < nv; kk += 32) {
-    const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
-    const double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
-    const double ex = bx - ax, ey = by - ay;
-    const double wx = px - ax, wy = py - ay;
-    const double num = wx * ex + wy * ey;
-    const double den = ex * ex + ey * ey;
-    double cx, cy;
-    int f, r;
-    if (num <= 0.0) {
-      cx = ax; cy = ay; f = kk; r = IBM_REGION_VERTEX;
-    } else if (num >= den) {
-      cx = bx; cy = by; f = k1; r = IBM_REGION_VERTEX;
+  for (int e = blockIdx.x; e < total; e += gridDim.x) {
+    const ibm_stencil s0 = st[e];
+    const int kind = s0.kind;
+    const int i = s0.cell % k.nx, j = s0.cell / k.nx;
+    const double px = k.x0 + ((double)i + 0.5) * k.dx;
+    const double py = k.y0 + ((double)j + 0.5) * k.dy;
+    const int nv = g.nv;
+    // closest feature (Sec. 4.1)
+    double best = INFINITY, bcx = 0.0, bcy = 0.0;
+    int bseg = 0x7fffffff, bfeat = 0, breg = 0;
+    for (int kk = threadIdx.x; kk < nv; kk += 128) {
+      const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
+      const double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
+      const double ex = bx - ax, ey = by - ay;
+      const double wx = px - ax, wy = py - ay;
+      const double num = wx * ex + wy * ey;
+      const double den = ex * ex + ey * ey;
+      double cx, cy;
+      int f, r;
+      if (num <= 0.0) {
+        cx = ax; cy = ay; f = kk; r = IBM_REGION_VERTEX;
+      } else if (num >= den) {
+        cx = bx; cy = by; f = k1; r = IBM_REGION_VERTEX;
+      } else {
+        const double t = num / den;
+        cx = ax + t * ex; cy = ay + t * ey; f = kk; r = IBM_REGION_FACE;
+      }
+      const double ddx = px - cx, ddy = py - cy;
+      const double d2 = ddx * ddx + ddy * ddy;
+      if (d2 < best) {
+        best = d2; bseg = kk; bfeat = f; breg = r; bcx = cx; bcy = cy;
+      }
+    }
+    int win = block_argmin128(best, bseg, s_v, s_i, s_s);
+    if ((int)threadIdx.x == win) {
+      s_n[0] = bfeat;
+      s_n[1] = breg;
+      s_d[0] = bcx;
+      s_d[1] = bcy;
+    }
+    __syncthreads();
+    const int feat = s_n[0];
+    const int region = s_n[1];
+    const double ccx = s_d[0], ccy = s_d[1];
+    double nx, ny;
+    if (region == IBM_REGION_FACE) {
+      nx = g.snx[feat];
+      ny = g.sny[feat];
     } else {
-      const double t = num / den;
-      cx = ax + t * ex; cy = ay + t * ey; f = kk; r = IBM_REGION_FACE;
+      nx = g.vnx[feat];
+      ny = g.vny[feat];
     }
-    const double ddx = px - cx, ddy = py - cy;
-    const double d2 = ddx * ddx + ddy * ddy;
-    if (d2 < best) {
-      best = d2; bseg = kk; bfeat = f; breg = r; bcx = cx; bcy = cy;
+    // boundary point on the line along the local normal (Sec. 4.3)
+    const bool ghost = kind > 0;
+    double bs_best = INFINITY, bs_s = 0.0;
+    int bs_seg = 0x7fffffff;
+    for (int kk = threadIdx.x; kk < nv; kk += 128) {
+      const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
+      const double ax = g.vx[kk], ay = g.vy[kk];
+      const double ex = g.vx[k1] - ax, ey = g.vy[k1] - ay;
+      const double den = ex * ny - ey * nx;
+      if (den == 0.0) continue;
+      const double wx = px - ax, wy = py - ay;
+      const double u = (wx * ny - wy * nx) / den;
+      if (u < 0.0 || u > 1.0) continue;
+      const double sv = (wx * ey - wy * ex) / den;
+      if (ghost ? (sv < 0.0) : (sv > 0.0)) continue;
+      const double as = fabs(sv);
+      if (as < bs_best) {
+        bs_best = as; bs_s = sv; bs_seg = kk;
+      }
+    }
+    win = block_argmin128(bs_best, bs_seg, s_v, s_i, s_s);
+    if ((int)threadIdx.x == win) {
+      s_d[2] = bs_best;
+      s_d[3] = bs_s;
+    }
+    __syncthreads();
+    const double found_abs = s_d[2];
+    const double bsv = s_d[3];
+    if (threadIdx.x == 0) {
+      ibm_stencil s = s0;
+      double bx, by, xi_node;
+      int fb;
+      if (found_abs < INFINITY) {
+        bx = px + bsv * nx;
+        by = py + bsv * ny;
+        xi_node = -bsv;
+        fb = 0;
+      } else {
+        const double ddx = px - ccx, ddy = py - ccy;
+        const double d = sqrt(ddx * ddx + ddy * ddy);
+        bx = ccx;
+        by = ccy;
+        xi_node = ghost ? -d : d;
+        fb = 1;
+      }
+      double xi_probe;
+      if (kind == 0) {
+        xi_probe = xi_node + k.h;
+      } else {
+        xi_probe = -xi_node;
+        if (xi_probe < 0.5 * k.dmin) xi_probe = 0.5 * k.dmin;
+      }
+      const unsigned allowed = kind == 0 ? ALLOW_FLUID : ALLOW_FLUID_IB;
+      int i0 = 0, j0 = 0, mask = 0, nstep = 0;
+      double w[4];
+      for (;;) {
+        double X = bx + xi_probe * nx, Y = by + xi_probe * ny;
+        mask = interp_square(k, tag, X, Y, allowed, &i0, &j0, w);
+        if (mask != 0 || nstep == 3) break;
+        xi_probe = xi_probe + k.dmin;
+        nstep++;
+      }
+      if (mask == 0) atomicOr(&ds->err, ERR_STENCIL);
+      s.feature = feat;
+      s.region = fb ? IBM_REGION_FALLBACK : region;
+      s.i0 = i0;
+      s.j0 = j0;
+      s.mask = mask;
+      s.nstep = nstep;
+      s.nx = nx;
+      s.ny = ny;
+      s.bx = bx;
+      s.by = by;
+      s.xi_node = xi_node;
+      s.xi_probe = xi_probe;
+      for (int q = 0; q < 4; q++) s.w[q] = w[q];
+      st[e] = s;
+      if (rs) {
+        RStencil32 r;
+        r.cell = (int)cidx(k, s.cell % k.nx, s.cell / k.nx);
+        r.corner = s.mask ? (int)cidx(k, s.i0, s.j0) : 0;
+        r.ccell = s.mask ? s.j0 * k.nx + s.i0 : 0;
+        r.mask = s.mask | (s.kind == 0 ? 16 : 0);  // bit 4: IB node
+        r.ratio = (float)(s.xi_node / s.xi_probe);
+        r.dxi = (float)(s.xi_probe - s.xi_node);
+        r.nx = (float)s.nx;
+        r.ny = (float)s.ny;
+        for (int q = 0; q < 4; q++) r.w[q] = (float)s.w[q];
+        rs[e] = r;
+        sid[s.cell] = e;
+      }
+    }
+    __syncthreads();  // shared memory is reused by the next entry
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused per-classification geometry for bodies of up to FUSED_MAX_VERTS
+// vertices (see launch_fused_geometry).
+// ---------------------------------------------------------------------------
+
+// clipped cell rectangle [ilo, ihi] x [jlo, jhi]; empty if ilo > ihi or jlo > jhi
+__device__ __forceinline__ void clip_rect(const Consts &k, int r[4]) {
+  r[0] = max(r[0], 0);
+  r[1] = min(r[1], k.nx - 1);
+  r[2] = max(r[2], 0);
+  r[3] = min(r[3], k.ny - 1);
+}
+
+// (1) pose + ray-parity classification of the cells of urect = (current
+// bounding-box cells, 3-cell margin) united with the previous rectangle.
+// Every block poses the vertices into shared memory and reduces the box
+// itself (exact operations, identical in every block); block 0 publishes
+// them.  One warp per cell, grid-stride over the rectangle.
+__global__ void __launch_bounds__(256) k_pose_classify(Consts k, Geom g, uint8_t *__restrict__ solid,
+                                                       DevState *ds) {
+  extern __shared__ double sv[];  // x[nv] then y[nv]
+  __shared__ double X[2];
+  __shared__ double wb[8][4];
+  __shared__ double bb[4];
+  __shared__ int rect[4];
+  const int nv = g.nv;
+  if (threadIdx.x == 0) {
+    double V[2], A[2], P[2];
+    motion_at(k.motion, ds->t, P, V, A);
+    X[0] = P[0];
+    X[1] = P[1];
+  }
+  __syncthreads();
+  double b[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const double x = g.vref[2 * v] + X[0], y = g.vref[2 * v + 1] + X[1];
+    sv[v] = x;
+    sv[nv + v] = y;
+    if (blockIdx.x == 0) {
+      g.vx[v] = x;
+      g.vy[v] = y;
+    }
+    b[0] = fmin(b[0], x);
+    b[1] = fmax(b[1], x);
+    b[2] = fmin(b[2], y);
+    b[3] = fmax(b[3], y);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    b[0] = fmin(b[0], __shfl_xor_sync(0xffffffffu, b[0], off));
+    b[1] = fmax(b[1], __shfl_xor_sync(0xffffffffu, b[1], off));
+    b[2] = fmin(b[2], __shfl_xor_sync(0xffffffffu, b[2], off));
+    b[3] = fmax(b[3], __shfl_xor_sync(0xffffffffu, b[3], off));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int q = 0; q < 4; q++) wb[warp][q] = b[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; w++) {
+      b[0] = fmin(b[0], wb[w][0]);
+      b[1] = fmax(b[1], wb[w][1]);
+      b[2] = fmin(b[2], wb[w][2]);
+      b[3] = fmax(b[3], wb[w][3]);
+    }
+    int bc[4];
+    bc[0] = (int)floor((b[0] - k.x0) / k.dx - 0.5) - 3;
+    bc[1] = (int)ceil((b[1] - k.x0) / k.dx - 0.5) + 3;
+    bc[2] = (int)floor((b[2] - k.y0) / k.dy - 0.5) - 3;
+    bc[3] = (int)ceil((b[3] - k.y0) / k.dy - 0.5) + 3;
+    int r[4] = {bc[0], bc[1], bc[2], bc[3]};
+    clip_rect(k, r);
+    if (ds->prect_valid) {
+      const bool empty = r[0] > r[1] || r[2] > r[3];
+      const int *p = ds->prect;
+      if (p[0] <= p[1] && p[2] <= p[3]) {
+        if (empty) {
+          for (int q = 0; q < 4; q++) r[q] = p[q];
+        } else {
+          r[0] = min(r[0], p[0]);
+          r[1] = max(r[1], p[1]);
+          r[2] = min(r[2], p[2]);
+          r[3] = max(r[3], p[3]);
+        }
+      }
+    }
+    for (int q = 0; q < 4; q++) {
+      bb[q] = b[q];
+      rect[q] = r[q];
+    }
+    if (blockIdx.x == 0) {
+      ds->pos[0] = X[0];
+      ds->pos[1] = X[1];
+      for (int q = 0; q < 4; q++) {
+        ds->bbox[q] = b[q];
+        ds->bcell[q] = bc[q];
+        ds->urect[q] = r[q];
+      }
     }
   }
-  int src = warp_argmin(best, bseg);
-  const int feat = __shfl_sync(0xffffffffu, bfeat, src);
-  const int region = __shfl_sync(0xffffffffu, breg, src);
-  const double ccx = __shfl_sync(0xffffffffu, bcx, src);
-  const double ccy = __shfl_sync(0xffffffffu, bcy, src);
-  double nx, ny;
-  if (region == IBM_REGION_FACE) {
-    nx = g.snx[feat];
-    ny = g.sny[feat];
-  } else {
-    nx = g.vnx[feat];
-    ny = g.vny[feat];
+  __syncthreads();
+  if (rect[0] > rect[1] || rect[2] > rect[3]) return;
+  const int W = rect[1] - rect[0] + 1, H = rect[3] - rect[2] + 1;
+  const long long ncells = (long long)W * H;
+  const double b0 = bb[0], b1 = bb[1], b2 = bb[2], b3 = bb[3];
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + warp; c < ncells; c += nwarps) {
+    const int i = rect[0] + (int)(c % W), j = rect[2] + (int)(c / W);
+    const double px = k.x0 + ((double)i + 0.5) * k.dx;
+    const double py = k.y0 + ((double)j + 0.5) * k.dy;
+    int odd = 0;
+    if (!(px < b0 || px > b1 || py < b2 || py > b3)) {
+      for (int e = lane; e < nv; e += 32) {
+        const int e1 = (e + 1 == nv) ? 0 : e + 1;
+        const double ax = sv[e], ay = sv[nv + e], bx = sv[e1], by = sv[nv + e1];
+        if ((ay > py) != (by > py)) {
+          double t1 = py - ay;
+          double t2 = bx - ax;
+          double t3 = by - ay;
+          double xint = ax + (t1 * t2) / t3;
+          if (xint > px) odd ^= 1;
+        }
+      }
+      odd = __popc(__ballot_sync(0xffffffffu, odd)) & 1;
+    }
+    if (lane == 0) solid[j * k.nx + i] = (uint8_t)odd;
   }
-  // boundary point on the line along the local normal (Sec. 4.3)
-  const bool ghost = kind > 0;
-  double bs_best = INFINITY, bs_s = 0.0;
-  int bs_seg = 0x7fffffff;
-  for (int kk = lane; kk < nv; kk += 32) {
-    const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
-    const double ax = g.vx[kk], ay = g.vy[kk];
-    const double ex = g.vx[k1] - ax, ey = g.vy[k1] - ay;
-    const double den = ex * ny - ey * nx;
-    if (den == 0.0) continue;
-    const double wx = px - ax, wy = py - ay;
-    const double u = (wx * ny - wy * nx) / den;
-    if (u < 0.0 || u > 1.0) continue;
-    const double sv = (wx * ey - wy * ex) / den;
-    if (ghost ? (sv < 0.0) : (sv > 0.0)) continue;
-    const double as = fabs(sv);
-    if (as < bs_best) {
-      bs_best = as; bs_s = sv; bs_seg = kk;
+}
+
+// does the tile's loaded range [lo, hi] (before domain mapping) along one axis
+// reach the cells [blo, bhi]?  (A periodic side that the range crosses wraps
+// it: yes.)
+__device__ __forceinline__ bool tile_axis_reaches(int lo, int hi, int n, int bc_lo, int bc_hi, int blo, int bhi) {
+  if ((lo < 0 && bc_lo == IBM_BC_PERIODIC) || (hi >= n && bc_hi == IBM_BC_PERIODIC)) return true;
+  lo = max(lo, 0);
+  hi = min(hi, n - 1);
+  return lo <= bhi && hi >= blo;
+}
+
+// tag rule of tag_of on a staged copy of the solid flags: rows ey0.., columns
+// ex0.. of width ew (the rectangle plus the 3-cell reach of the rule)
+__device__ __forceinline__ uint8_t tag_of_staged(const Consts &k, const uint8_t *ss, int ex0, int ey0, int ew, int i,
+                                                 int j) {
+  const int nx = k.nx, ny = k.ny;
+#define SOL(ii, jj) ss[((jj)-ey0) * ew + ((ii)-ex0)]
+  if (!SOL(i, j)) {
+    bool ib = (i + 1 < nx && SOL(i + 1, j)) || (i > 0 && SOL(i - 1, j)) || (j + 1 < ny && SOL(i, j + 1)) ||
+              (j > 0 && SOL(i, j - 1));
+    return ib ? IB : FLUID;
+  }
+  for (int d = 1; d <= 3; d++) {
+    if ((i + d < nx && !SOL(i + d, j)) || (i - d >= 0 && !SOL(i - d, j)) || (j + d < ny && !SOL(i, j + d)) ||
+        (j - d >= 0 && !SOL(i, j - d)))
+      return (uint8_t)(G1 + d - 1);
+  }
+#undef SOL
+  return SOLID;
+}
+
+// (2) one block of 1024 threads over urect: tags (and sid reset), the
+// row-major IB / G1-G3 lists, then the body-tile flags of every stage tile and
+// their ascending list.  Rectangles of up to STAGED_CELLS cells (with the
+// rule's 3-cell reach) work on shared-memory copies of the solid flags and
+// tags; cells outside urect are fluid (invariant), so no other tag is read.
+// Ends by recording the current rectangle for the next classification.
+constexpr int STAGED_CELLS = 16384;
+__global__ void __launch_bounds__(1024) k_tags_lists(Consts k, const uint8_t *__restrict__ solid,
+                                                     uint8_t *__restrict__ tag, int *__restrict__ sid,
+                                                     ibm_stencil *__restrict__ st, int cap,
+                                                     uint8_t *__restrict__ tile_body, int *__restrict__ body_tiles,
+                                                     int body_cap, DevState *ds) {
+  __shared__ uint8_t s_sol[STAGED_CELLS];
+  __shared__ uint8_t s_tag[STAGED_CELLS];
+  __shared__ int wc[32][4];
+  __shared__ int tot[4], run[4], off[4];
+  __shared__ int wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = ds->urect[0], r1 = ds->urect[1], r2 = ds->urect[2], r3 = ds->urect[3];
+  const int W = r0 <= r1 && r2 <= r3 ? r1 - r0 + 1 : 0, H = W ? r3 - r2 + 1 : 0;
+  const int n = W * H;
+  const int ex0 = max(r0 - 3, 0), ex1 = min(r1 + 3, k.nx - 1), ey0 = max(r2 - 3, 0), ey1 = min(r3 + 3, k.ny - 1);
+  const int ew = ex1 - ex0 + 1, eh = ey1 - ey0 + 1;
+  const bool staged = n > 0 && ew * eh <= STAGED_CELLS;
+  if (staged)
+    for (int m = tid; m < ew * eh; m += 1024) s_sol[m] = solid[(ey0 + m / ew) * k.nx + ex0 + m % ew];
+  __syncthreads();
+  // pass 1: tags, counts per kind
+  int cnt[4] = {0, 0, 0, 0};
+  for (int m = tid; m < n; m += 1024) {
+    const int i = r0 + m % W, j = r2 + m / W;
+    const uint8_t t = staged ? tag_of_staged(k, s_sol, ex0, ey0, ew, i, j) : tag_of(k, solid, i, j);
+    tag[j * k.nx + i] = t;
+    if (staged) s_tag[m] = t;
+    if (sid) sid[j * k.nx + i] = -1;
+    const int q = list_kind(t);
+    if (q >= 0) cnt[q]++;
+  }
+  for (int q = 0; q < 4; q++) {
+    int v = cnt[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wc[warp][q] = v;
+  }
+  __syncthreads();
+  if (tid < 4) {
+    int v = 0;
+    for (int w = 0; w < 32; w++) v += wc[w][tid];
+    tot[tid] = v;
+    run[tid] = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int o = 0;
+    for (int q = 0; q < 4; q++) {
+      off[q] = o;
+      ds->count[q] = tot[q];
+      ds->offset[q] = o;
+      o += tot[q];
+    }
+    ds->offset[4] = o;
+    if (o > cap) atomicOr(&ds->err, ERR_CAPACITY);
+  }
+  __syncthreads();
+  // pass 2: scatter in row-major order, 1024 cells at a time
+  const unsigned lt = (1u << lane) - 1u;
+  for (int base = 0; base < n; base += 1024) {
+    const int m = base + tid;
+    int kind = -1, cell = 0;
+    if (m < n) {
+      const int i = r0 + m % W, j = r2 + m / W;
+      cell = j * k.nx + i;
+      kind = list_kind(staged ? s_tag[m] : tag[cell]);
+    }
+    int rank = 0;
+    for (int q = 0; q < 4; q++) {
+      const unsigned msk = __ballot_sync(0xffffffffu, kind == q);
+      if (lane == 0) wc[warp][q] = __popc(msk);
+      if (kind == q) rank = __popc(msk & lt);
+    }
+    __syncthreads();
+    if (kind >= 0) {
+      int before = 0;
+      for (int w = 0; w < warp; w++) before += wc[w][kind];
+      const int pos = off[kind] + run[kind] + before + rank;
+      if (pos < cap) {
+        st[pos].cell = cell;
+        st[pos].kind = kind;
+      }
+    }
+    __syncthreads();
+    if (tid < 4) {
+      int v = 0;
+      for (int w = 0; w < 32; w++) v += wc[w][tid];
+      run[tid] += v;
+    }
+    __syncthreads();
+  }
+  // body-tile flags (one warp per tile; tiles out of reach of the body's cells skipped) and their list
+  if (tile_body) {
+    constexpr int T = STAGE_TILE, HX = T + 2 * NG, HY = T + 2 * NG;
+    const int ntx = (k.nx + T - 1) / T, nt = ntx * ((k.ny + T - 1) / T);
+    const int nty = (k.ny + T - 1) / T;
+    const int bl = ds->bcell[0], bh = ds->bcell[1], cl = ds->bcell[2], ch = ds->bcell[3];
+    for (int t = tid; t < nt; t += 1024) tile_body[t] = 0;
+    __syncthreads();
+    // tiles whose loaded range can reach the body's cells: a conservative range of tile columns and rows
+    // (every tile along an axis whose sides are periodic), then the exact test
+    int tx0 = 0, tx1 = ntx - 1, ty0 = 0, ty1 = nty - 1;
+    if (k.bc[0] != IBM_BC_PERIODIC && k.bc[1] != IBM_BC_PERIODIC) {
+      tx0 = max(0, (max(bl, 0) - NG) / T - 1);
+      tx1 = min(ntx - 1, (min(bh, k.nx - 1) + NG) / T + 1);
+    }
+    if (k.bc[2] != IBM_BC_PERIODIC && k.bc[3] != IBM_BC_PERIODIC) {
+      ty0 = max(0, (max(cl, 0) - NG) / T - 1);
+      ty1 = min(nty - 1, (min(ch, k.ny - 1) + NG) / T + 1);
+    }
+    const int cw = tx1 - tx0 + 1, ncand = n > 0 && tx0 <= tx1 && ty0 <= ty1 ? cw * (ty1 - ty0 + 1) : 0;
+    for (int c = warp; c < ncand; c += 32) {
+      const int tx = tx0 + c % cw, ty = ty0 + c / cw;
+      const int t = ty * ntx + tx, i0 = tx * T, j0 = ty * T;
+      bool hit = false;
+      if (tile_axis_reaches(i0 - NG, i0 + T + NG - 1, k.nx, k.bc[0], k.bc[1], bl, bh) &&
+          tile_axis_reaches(j0 - NG, j0 + T + NG - 1, k.ny, k.bc[2], k.bc[3], cl, ch)) {
+        for (int m = lane; m < HX * HY; m += 32) {
+          int gi = i0 - NG + m % HX, gj = j0 - NG + m / HX;
+          if (!halo_map(k, gi, gj)) continue;
+          if (gi < r0 || gi > r1 || gj < r2 || gj > r3) continue;  // fluid outside the rectangle
+          const uint8_t tg = staged ? s_tag[(gj - r2) * W + (gi - r0)] : tag[gj * k.nx + gi];
+          hit |= (tg == IB || tg >= G1);
+        }
+        hit = __any_sync(0xffffffffu, hit);
+      }
+      if (lane == 0 && hit) tile_body[t] = 1;
+    }
+    __syncthreads();
+    // ascending list of the flagged tiles: per-thread runs, warp-shuffle scan, scan of the warp totals
+    const int per = (nt + 1023) / 1024;
+    const int t0 = tid * per, t1 = min(nt, t0 + per);
+    int c = 0;
+    for (int t = t0; t < t1; t++) c += tile_body[t];
+    int inc = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      int w = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += v;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    int pos = inc - c + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int t = t0; t < t1; t++)
+      if (tile_body[t]) {
+        if (pos < body_cap) body_tiles[pos] = t;
+        pos++;
+      }
+    if (tid == 0) {
+      const int total = wsum[31];
+      ds->nbody_tiles = min(total, body_cap);
+      if (total > body_cap) atomicOr(&ds->err, ERR_CAPACITY);
     }
   }
-  src = warp_argmin(bs_best, bs_seg);
-  const double found_abs = __shfl_sync(0xffffffffu, bs_best, src);
-  const double bsv = __shfl_sync(0xffffffffu, bs_s, src);
-  if (lane != 0) return;
-  double bx, by, xi_node;
-  int fb;
-  if (found_abs < INFINITY) {
-    bx = px + bsv * nx;
-    by = py + bsv * ny;
-    xi_node = -bsv;
-    fb = 0;
-  } else {
-    const double ddx = px - ccx, ddy = py - ccy;
-    const double d = sqrt(ddx * ddx + ddy * ddy);
-    bx = ccx;
-    by = ccy;
-    xi_node = ghost ? -d : d;
-    fb = 1;
+  if (tid == 0) {
+    int r[4] = {ds->bcell[0], ds->bcell[1], ds->bcell[2], ds->bcell[3]};
+    clip_rect(k, r);
+    for (int q = 0; q < 4; q++) ds->prect[q] = r[q];
+    ds->prect_valid = 1;
   }
-  double xi_probe;
-  if (kind == 0) {
-    xi_probe = xi_node + k.h;
-  } else {
-    xi_probe = -xi_node;
-    if (xi_probe < 0.5 * k.dmin) xi_probe = 0.5 * k.dmin;
+}
+
+int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_t *tag, ibm_stencil *st, int cap,
+                          RStencil32 *rs, int *sid, uint8_t *tile_body, int *body_tiles, int body_cap, int maxw,
+                          int maxh, DevState *ds, cudaStream_t s) {
+  const long long warps = (long long)(maxw + 8) * (maxh + 8);
+  const int blocks = (int)std::min<long long>(std::max<long long>((warps + 7) / 8, 1), 4096);
+  k_pose_classify<<<blocks, 256, 2 * sizeof(double) * g.nv, s>>>(k, g, solid, ds);
+  k_tags_lists<<<1, 1024, 0, s>>>(k, solid, tag, sid, st, cap, tile_body, body_tiles, body_cap, ds);
+  int nl = 2;
+  if (cap > 0) {
+    k_stencils<<<(unsigned)min(cap, 4 * 152), 128, 0, s>>>(k, g, tag, st, cap, ds, rs, sid);
+    nl++;
   }
-  const unsigned allowed = kind == 0 ? ALLOW_FLUID : ALLOW_FLUID_IB;
-  int i0 = 0, j0 = 0, mask = 0, nstep = 0;
-  double w[4];
-  for (;;) {
-    double X = bx + xi_probe * nx, Y = by + xi_probe * ny;
-    mask = interp_square(k, tag, X, Y, allowed, &i0, &j0, w);
-    if (mask != 0 || nstep == 3) break;
-    xi_probe = xi_probe + k.dmin;
-    nstep++;
-  }
-  if (mask == 0) atomicOr(&ds->err, ERR_STENCIL);
-  s.feature = feat;
-  s.region = fb ? IBM_REGION_FALLBACK : region;
-  s.i0 = i0;
-  s.j0 = j0;
-  s.mask = mask;
-  s.nstep = nstep;
-  s.nx = nx;
-  s.ny = ny;
-  s.bx = bx;
-  s.by = by;
-  s.xi_node = xi_node;
-  s.xi_probe = xi_probe;
-  for (int q = 0; q < 4; q++) s.w[q] = w[q];
-  st[e] = s;
+  return nl;
 }
 
 void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
                      cudaStream_t s) {
   if (cap <= 0) return;
-  k_stencils<<<(unsigned)(((long long)cap * 32 + 127) / 128), 128, 0, s>>>(k, g, tag, st, cap, ds);
+  k_stencils<<<(unsigned)min(cap, 4 * 152), 128, 0, s>>>(k, g, tag, st, cap, ds, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------

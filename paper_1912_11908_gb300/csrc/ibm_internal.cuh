@@ -9,6 +9,7 @@
 namespace ibm {
 
 constexpr int NG = 3;  // halo / ghost layers for the five-point WENO stencil (Sec. 5)
+constexpr int STAGE_TILE = 16;  // stage kernels: square tiles of STAGE_TILE x STAGE_TILE cells
 
 enum : uint8_t { FLUID = 0, SOLID = 1, IB = 2, G1 = 3, G2 = 4, G3 = 5 };
 
@@ -27,6 +28,10 @@ struct DevState {
   int pad;
   double pos[2];                 // body displacement at the last classification
   double bbox[4];                // xmin, xmax, ymin, ymax of the current pose
+  int bcell[4];                  // cell index range ilo, ihi, jlo, jhi of centres in bbox, widened by 3 cells
+  int urect[4];                  // cells re-classified this step: bcell (clipped) united with prect
+  int prect[4];                  // bcell (clipped) of the previous classification
+  int prect_valid;               // 0 before the first classification
   double force[4];               // Cd, Cl, Fx, Fy
   long long steps;
 };
@@ -144,6 +149,8 @@ __device__ inline void motion_at(const Motion &m, double t, double X[2], double 
   }
 }
 
+struct RStencil32;
+
 // ---- launchers (geometry.cu) ----
 void launch_normals(int nv, const double *v, double *snx, double *sny, double *vnx, double *vny, cudaStream_t s);
 void launch_pose(const Consts &k, const Geom &g, DevState *ds, cudaStream_t s);
@@ -154,6 +161,19 @@ void launch_tags(const Consts &k, const uint8_t *solid, uint8_t *tag, int *block
                  ibm_stencil *st, cudaStream_t s, int *nlaunch);
 void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
                      cudaStream_t s);
+// Geometry of one classification for bodies of at most FUSED_MAX_VERTS
+// vertices, restricted to the cells the body can occupy: (1) pose and
+// ray-parity classification of the cells of the previous and current
+// bounding-box rectangles, (2) one block: tags, row-major IB / G1-G3 lists,
+// reset of the cell -> stencil map, body-tile flags and list, (3) stencils,
+// with their compact FP32 form and the cell -> stencil map when rs != NULL.
+// Invariant: outside the rectangle last processed every cell is fluid,
+// untagged and unlisted (solid, tag and sid are cleared at creation).  Same
+// results as the unrestricted kernels.  Returns the kernels launched.
+constexpr int FUSED_MAX_VERTS = 1024;
+int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_t *tag, ibm_stencil *st, int cap,
+                          RStencil32 *rs, int *sid, uint8_t *tile_body, int *body_tiles, int body_cap, int maxw,
+                          int maxh, DevState *ds, cudaStream_t s);
 // A: FP64 state, absolute conserved (pert = false) or perturbation (pert = true)
 void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, bool pert,
                        DevState *ds, cudaStream_t s);
@@ -193,8 +213,11 @@ void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 
                              const DevState *ds, cudaStream_t s);
 // Tiles of the stage kernel whose cells or 3-cell halo hold IB / ghost nodes
 // ("body tiles"): flag per tile and a compact list (capacity body_cap).
+// has_body = false: no vertices (every tile plain; ds->bbox unused).
+// (Cases with a body of at most FUSED_MAX_VERTS vertices build their tile
+// lists inside launch_fused_geometry instead.)
 void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, int *body_tiles, int body_cap,
-                       DevState *ds, cudaStream_t s);
+                       DevState *ds, bool has_body, cudaStream_t s);
 int stage_tiles(const Consts &k);
 struct PertConsts {  // FP32 copies of the free-stream constants
   float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin, vis, cp;

@@ -130,7 +130,7 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
 // the FP64 kernel.  Stage 3 accumulates U^{n+1} in FP64 and refreshes the
 // FP32 mirror of U^{n+1}.
 // ---------------------------------------------------------------------------
-constexpr int TX = 16, TY = 16, HX = TX + 2 * NG, HY = TY + 2 * NG;
+constexpr int TX = STAGE_TILE, TY = STAGE_TILE, HX = TX + 2 * NG, HY = TY + 2 * NG;
 
 // spectral radius of the CFL rule for one cell of the FP32 mirror
 __device__ __forceinline__ float cfl_lambda(const Consts &k, const PertConsts &c, const float m[4]) {
