@@ -302,9 +302,11 @@ def run_ours(args, rank, world):
     if not args.skip_serving and rank == 0:
         from paper_1912_11908_gb300 import workloads as W
         mix0 = W.serving_mix(args.serve_requests)
+        ndual = sum(1 for r in mix0 if r["spec"]["time_scheme"] == W.TIME_DUAL)
         serving = {"workload": "serving mix: %d seeded requests (cylinder / NACA00xx / wedge, static or oscillating, "
-                               "M 0.001-2, Re 40-1e4, grids 64x64-1024x512, FP32-bulk SSP-RK3, %d steps each), "
-                               "Poisson arrivals mean 50 ms" % (args.serve_requests, mix0[0]["nsteps"]),
+                               "M 0.001-2, Re 40-1e4, grids 64x64-1024x512, FP32-bulk; %d explicit requests of 500 "
+                               "SSP-RK3 steps, %d at M <= 0.01 of 10 dual-time steps x 30 sub-iterations), "
+                               "Poisson arrivals mean 50 ms" % (args.serve_requests, args.serve_requests - ndual, ndual),
                    "slots": args.serve_slots, "steps_per_chunk": args.serve_chunk,
                    "memory_budget": "80% of free device memory",
                    "modes": {"batched": "size-class groups, one plain-tile and one body-tile launch per RK stage over "
@@ -389,8 +391,8 @@ def run_serving(ibm, W, n, slots, chunk, burst, mode):
     Poisson mode submits each request when its arrival time has passed;
     burst mode submits all of them at once.  Latency (time to solution) runs
     from the arrival to the retirement of the request; throughput counts grid
-    cells x 3 stages x steps of all requests over the span from the first
-    arrival to the last retirement.
+    cells x stages x steps of all requests (dual time: 3 pseudo stages per
+    sub-iteration) over the span from the first arrival to the last retirement.
     """
     reqs = W.serving_mix(n)
     srv = ibm.Server(max_active=slots, steps_per_chunk=chunk, mode=mode)
@@ -423,7 +425,8 @@ def run_serving(ibm, W, n, slots, chunk, burst, mode):
             continue
         lat.append(r["finish_s"] - r["submit_s"] + lag[rid])
         sp = reqs[kk]["spec"]
-        work += sp["nx"] * sp["ny"] * 3 * r["steps_done"]
+        stages = 3 * sp["subiters"] if sp["time_scheme"] == W.TIME_DUAL else 3
+        work += sp["nx"] * sp["ny"] * stages * r["steps_done"]
     srv.close()
     lat.sort()
 

@@ -110,11 +110,14 @@ def random_polygon(rng, n, center=(0.0, 0.0), rmin=0.3, rmax=1.0):
     return np.stack([center[0] + r * np.cos(a), center[1] + r * np.sin(a)], axis=1)
 
 
-def serving_mix(n=512, seed=20191224, mean_interarrival_s=0.05, nsteps=200):
+def serving_mix(n=512, seed=20191224, mean_interarrival_s=0.05, nsteps=500, dual_mach=0.01, dual_steps=10,
+                subiters=30):
     """Request mix for the request loop: bodies, motions, Mach, Re and grids drawn from a seed.
 
-    Each entry: arrival time (Poisson process), case spec (FP32-bulk, SSP-RK3)
-    and the number of explicit steps the request asks for.
+    Each entry: arrival time (Poisson process), case spec (FP32-bulk) and the
+    number of steps the request asks for: `nsteps` explicit SSP-RK3 steps, or,
+    at M <= dual_mach, `dual_steps` dual-time physical steps of dt = 0.5 h with
+    `subiters` sub-iterations (explicit steps would be acoustically limited).
     """
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(mean_interarrival_s, n))
@@ -137,8 +140,10 @@ def serving_mix(n=512, seed=20191224, mean_interarrival_s=0.05, nsteps=200):
         # square cells; at least 12 body lengths along x and 3 across, body 4 lengths from the inflow
         h = max(12.0 / gx, 3.0 / gy)
         dom = (-4.0, -4.0 + gx * h, -0.5 * gy * h, 0.5 * gy * h)
-        reqs.append(dict(arrival_s=float(t[k]), nsteps=int(nsteps), spec=case_spec(
+        dual = mach <= dual_mach
+        kw = dict(time_scheme=TIME_DUAL, dt_phys=0.5 * h, subiters=subiters) if dual else {}
+        reqs.append(dict(arrival_s=float(t[k]), nsteps=int(dual_steps if dual else nsteps), spec=case_spec(
             verts, gx, gy, dom, mach, re, FAR if mach < 1.0 else SUPERSONIC,
             motion=MOTION_SIN if osc else MOTION_STATIC, amp=(0.0, 0.2) if osc else (0.0, 0.0),
-            freq=0.16 if osc else 0.0, precision=PREC_FP32_BULK, name="req%03d" % k)))
+            freq=0.16 if osc else 0.0, precision=PREC_FP32_BULK, name="req%03d" % k, **kw)))
     return reqs
