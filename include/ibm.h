@@ -207,6 +207,14 @@ ibm_status ibm_profile_read(ibm_case *c, double *ms, int64_t *launches, int n_gr
  * (IBM_ESTATE afterwards). */
 ibm_status ibm_autotune(ibm_case *c, int enable);
 
+/* FP32-bulk explicit stages: stage the loaded region (tile + 3-cell halo) of
+ * every tile that needs no domain-halo mapping into shared memory with one TMA
+ * tensor copy (cp.async.bulk.tensor) per tile instead of per-thread loads
+ * (default on where the driver provides the tensor-map encoder).  The values
+ * loaded are the same, so results do not depend on the choice.  enable = 0
+ * uses per-thread loads for every tile. */
+ibm_status ibm_use_tma(ibm_case *c, int enable);
+
 /* Replay each step from a CUDA graph captured on first use (default on);
  * enable = 0 launches every kernel directly. */
 ibm_status ibm_use_graphs(ibm_case *c, int enable);

@@ -36,6 +36,9 @@ struct ibm_case {
   uint8_t *tile_body = nullptr;  // FP32-bulk: stage tiles that rebuild IB / ghost nodes
   int *body_tiles = nullptr;
   int body_cap = 0;
+  CUtensorMap tmap[3];              // FP32-bulk: tensor maps of M, F1, F2 for the TMA tile staging
+  bool have_tmap = false;           // tensor maps built
+  bool use_tma = true;              // stage interior tiles with TMA (ibm_use_tma)
   int plain_variant[2] = {-1, -1};  // FP32-bulk: register budget of the plain stage kernel for stage 1 and for
                                     // stages 2-3 (-1: not tuned yet)
   bool autotune = true;
@@ -408,6 +411,10 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
         if (cudaMemsetAsync(p, 0, 4 * plane * sizeof(float), s) != cudaSuccess) rs = fail(IBM_ECUDA, "memset failed");
     }
     c->launches += (c->B ? 3 : 1) + (c->Wn ? 2 : 0);
+    if (c->precision == IBM_PREC_FP32_BULK) {
+      float *const arrays[3] = {c->M, c->F1, c->F2};
+      c->have_tmap = make_stage_tmaps(k, arrays, c->tmap);
+    }
 
   } while (0);
   if (rs != IBM_OK) {
@@ -548,7 +555,8 @@ static int enqueue_step(ibm_case *c) {
       cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
       launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->tile_body,
                        c->body_tiles, c->body_cap, c->ds, fuse_cfl, s, c->sb,
-                       c->plain_variant[st == 1 ? 0 : 1] < 0 ? 0 : c->plain_variant[st == 1 ? 0 : 1], true);
+                       c->plain_variant[st == 1 ? 0 : 1] < 0 ? 0 : c->plain_variant[st == 1 ? 0 : 1], true,
+                       c->have_tmap && c->use_tma ? &c->tmap[st - 1] : nullptr);
       cudaEventRecord(c->ev_join, c->sb);
       cudaStreamWaitEvent(s, c->ev_join, 0);
       if (c->body_cap > 0) nl += 1;
@@ -595,7 +603,8 @@ static ibm_status tune_plain_variant(ibm_case *c) {
     cudaEventRecord(c->ev_fork, s);
     cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
     launch_stage_f32(c->k, stage, c->M, stage == 1 ? c->M : c->F1, stage == 1 ? c->F1 : c->F2, c->A, c->tag, c->sid,
-                     c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, s, c->sb, v, true);
+                     c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, s, c->sb, v, true,
+                     c->have_tmap && c->use_tma ? &c->tmap[stage - 1] : nullptr);
     cudaEventRecord(c->ev_join, c->sb);
     cudaStreamWaitEvent(s, c->ev_join, 0);
   };
@@ -740,6 +749,17 @@ extern "C" ibm_status ibm_autotune(ibm_case *c, int enable) {
   return IBM_OK;
 }
 
+extern "C" ibm_status ibm_use_tma(ibm_case *c, int enable) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  if (c->graph) {  // the captured step holds the old choice
+    CU(cudaStreamSynchronize(c->stream));
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->use_tma = enable != 0;
+  return IBM_OK;
+}
+
 extern "C" ibm_status ibm_use_graphs(ibm_case *c, int enable) {
   if (!c) return fail(IBM_EINVAL, "case is NULL");
   c->use_graphs = enable != 0;
@@ -785,6 +805,7 @@ static ibm_status sync_and_check(ibm_case *c) {
   if (c->hds->err & ERR_CAPACITY)
     return fail(IBM_ECAPACITY, "IB/ghost list overflow: %d nodes, capacity %d", c->hds->offset[4], c->cap);
   if (c->hds->err & ERR_STENCIL) return fail(IBM_ESTENCIL, "an IB/ghost node found no valid interpolation corner");
+  if (c->hds->err & ERR_TIMEOUT) return fail(IBM_ECUDA, "a bounded device wait for a TMA tile copy gave up");
   return IBM_OK;
 }
 

@@ -1,6 +1,9 @@
 // FP32-bulk flow kernels of one case: conversions between the FP64 master and
 // the FP32 mirror, the CFL reduction, compact stencils, body-tile lists and
 // the stage kernels (per-tile code in stage32.cuh).
+#include <cstring>
+#include <mutex>
+
 #include "stage32.cuh"
 
 namespace ibm {
@@ -123,9 +126,10 @@ __global__ void __launch_bounds__(256, MINB) k_stage_f32(Consts k, PertConsts c,
                                                    const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
                                                    const uint8_t *__restrict__ tile_body,
                                                    const int *__restrict__ body_tiles, DevState *ds, bool fuse_cfl,
-                                                   unsigned int ncfl) {
-  stage_tile<STAGE, BODY>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, fuse_cfl, ncfl,
-                          (int)blockIdx.x);
+                                                   unsigned int ncfl, const __grid_constant__ CUtensorMap tmap,
+                                                   int use_tma) {
+  stage_tile<STAGE, BODY, false, true>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, fuse_cfl, ncfl,
+                                       (int)blockIdx.x, DualPtrs{}, use_tma ? &tmap : nullptr);
 }
 
 int stage_tiles(const Consts &k) { return ((k.nx + TX - 1) / TX) * ((k.ny + TY - 1) / TY); }
@@ -211,30 +215,65 @@ void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, 
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
                       const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                       const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
-                      cudaStream_t sb, int plain_variant, bool with_body) {
+                      cudaStream_t sb, int plain_variant, bool with_body, const CUtensorMap *tmap) {
   PertConsts c = pert_consts(k);
   const int nt = stage_tiles(k);
   const int nb = body_cap > 0 ? body_cap : 0;
   const unsigned int ncfl = (unsigned int)(nt + nb);
-#define IBM_STAGE_PAIR(S)                                                                                      \
-  do {                                                                                                         \
-    if (nb && with_body)                                                                                       \
-      k_stage_f32<S, true, 0><<<nb, 256, 0, sb>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, \
-                                                  fuse_cfl, ncfl);                                             \
-    if (plain_variant == 1)                                                                                    \
-      k_stage_f32<S, false, 5><<<nt, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, \
-                                                  fuse_cfl, ncfl);                                             \
-    else if (plain_variant == 2)                                                                               \
-      k_stage_f32<S, false, 4><<<nt, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, \
-                                                  fuse_cfl, ncfl);                                             \
-    else                                                                                                       \
-      k_stage_f32<S, false, 0><<<nt, 256, 0, s>>>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, \
-                                                  fuse_cfl, ncfl);                                             \
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof tm);
+  if (tmap) tm = *tmap;
+  const int ut = tmap ? 1 : 0;
+#define IBM_ARGS k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, fuse_cfl, ncfl, tm, ut
+#define IBM_STAGE_PAIR(S)                                                      \
+  do {                                                                         \
+    if (nb && with_body) k_stage_f32<S, true, 0><<<nb, 256, 0, sb>>>(IBM_ARGS); \
+    if (plain_variant == 1)                                                    \
+      k_stage_f32<S, false, 5><<<nt, 256, 0, s>>>(IBM_ARGS);                   \
+    else if (plain_variant == 2)                                               \
+      k_stage_f32<S, false, 4><<<nt, 256, 0, s>>>(IBM_ARGS);                   \
+    else                                                                       \
+      k_stage_f32<S, false, 0><<<nt, 256, 0, s>>>(IBM_ARGS);                   \
   } while (0)
   if (stage == 1) IBM_STAGE_PAIR(1);
   else if (stage == 2) IBM_STAGE_PAIR(2);
   else IBM_STAGE_PAIR(3);
 #undef IBM_STAGE_PAIR
+#undef IBM_ARGS
+}
+
+// Tensor maps of the three FP32 stage inputs (mirror of U^n, U^(1), U^(2)) for
+// the TMA tile staging: 3-D tensors (pitch, rows, 4 planes) of floats, box
+// TMA_W x HY x 4.  The encoder is the driver's cuTensorMapEncodeTiled, looked
+// up through the runtime (no link-time dependence on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool make_stage_tmaps(const Consts &k, float *const arrays[3], CUtensorMap out[3]) {
+  static std::once_flag once;
+  static EncodeTiledFn encode = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = (EncodeTiledFn)p;
+    cudaGetLastError();
+  });
+  if (!encode || k.pitch < TMA_W || k.rows < HY) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)k.pitch, (cuuint64_t)k.rows, 4};
+  const cuuint64_t strides[2] = {(cuuint64_t)k.pitch * sizeof(float), (cuuint64_t)k.plane * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)TMA_W, (cuuint32_t)HY, 4};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int q = 0; q < 3; q++) {
+    if (encode(&out[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, arrays[q], dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
 }
 
 }  // namespace ibm

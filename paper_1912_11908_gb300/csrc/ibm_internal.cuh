@@ -1,6 +1,7 @@
 // Internal declarations of the sm_103a immersed-boundary library (not installed).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the encoder is looked up at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,6 +44,7 @@ constexpr int RECON_ONE_BLOCK_MAX = 1 << 16;
 
 constexpr int ERR_CAPACITY = 1;
 constexpr int ERR_STENCIL = 2;
+constexpr int ERR_TIMEOUT = 4;  // a bounded device wait (TMA completion) gave up
 
 // body motion (prescribed translation)
 struct Motion {
@@ -258,7 +260,11 @@ constexpr int PLAIN_VARIANTS = 3;
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
                       const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                       const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
-                      cudaStream_t sb, int plain_variant, bool with_body);
+                      cudaStream_t sb, int plain_variant, bool with_body, const CUtensorMap *tmap);
+// Tensor maps of the FP32 stage inputs arrays[0..2] (pitch x rows x 4 planes)
+// for the TMA staging of interior tiles (tmap above); false if the driver
+// offers no encoder or the grid is too small for a box.
+bool make_stage_tmaps(const Consts &k, float *const arrays[3], CUtensorMap out[3]);
 // Dual-time pseudo stage (1..3) in FP32-bulk form: residual of the FP32
 // mirror In32, FP64 point-implicit update of the iterate In64 into Out64 (and
 // its mirror Out32); D holds the sub-iteration's starting iterate, Wn / Wm

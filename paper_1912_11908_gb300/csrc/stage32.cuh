@@ -18,6 +18,8 @@
 // U^n).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
+
 #include "ibm_internal.cuh"
 
 namespace ibm {
@@ -131,6 +133,49 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
 // FP32 mirror of U^{n+1}.
 // ---------------------------------------------------------------------------
 constexpr int TX = STAGE_TILE, TY = STAGE_TILE, HX = TX + 2 * NG, HY = TY + 2 * NG;
+
+// ---------------------------------------------------------------------------
+// TMA staging of a tile (Blackwell bulk tensor copy, inline PTX).  The FP32
+// arrays are 3-D tensors (padded column, padded row, variable plane); the
+// loaded region of an interior tile is the box of TMA_W x HY x 4 floats at
+// padded (i0, j0, 0) -- i0 is a multiple of the tile width, so the copy
+// starts on a 64-byte boundary.  One elected thread arms an mbarrier with the
+// box's byte count and issues the copy; the block waits on the barrier.
+// ---------------------------------------------------------------------------
+constexpr int TMA_W = (HX + 3) / 4 * 4;  // box width: HX rounded up to a multiple of 16 bytes
+constexpr unsigned TMA_BYTES = 4u * HY * TMA_W * sizeof(float);
+constexpr int TMA_WAIT_LIMIT = 1 << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_arm_and_load(float *dst, const CUtensorMap *map, int x, int y,
+                                                 unsigned long long *mbar) {
+  const unsigned m = smem_u32(mbar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(m) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(TMA_BYTES) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(0), "r"(m)
+      : "memory");
+}
+
+// wait for phase 0 of the barrier; false if the bounded wait gave up
+__device__ __forceinline__ bool tma_wait(unsigned long long *mbar) {
+  const unsigned m = smem_u32(mbar);
+  for (int it = 0; it < TMA_WAIT_LIMIT; it++) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(m)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 
 // spectral radius of the CFL rule for one cell of the FP32 mirror
 __device__ __forceinline__ float cfl_lambda(const Consts &k, const PertConsts &c, const float m[4]) {
@@ -329,17 +374,29 @@ static __device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts
 // DUAL: a pseudo stage of dual time -- preconditioned faces, wall motion at
 // t + dt_phys, FP64 point-implicit update (dp; D holds the sub-iteration's
 // start, Out receives the FP32 mirror of the new iterate).
-template <int STAGE, bool BODY, bool DUAL = false>
+// TMA: the kernel may stage interior tiles with a tensor copy (tmap: tensor
+// map of In; NULL loads every tile with per-thread loads).
+template <int STAGE, bool BODY, bool DUAL = false, bool TMA = false>
 __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c, float *Mn,
                                            const float *__restrict__ In, float *Out, double *D,
                                            const uint8_t *__restrict__ tag, const int *__restrict__ sid,
                                            const RStencil32 *__restrict__ rs, const uint8_t *__restrict__ tile_body,
                                            const int *__restrict__ body_tiles, DevState *ds, bool fuse_cfl,
-                                           unsigned int ncfl, int blk, const DualPtrs &dp = DualPtrs{}) {
+                                           unsigned int ncfl, int blk, const DualPtrs &dp = DualPtrs{},
+                                           const CUtensorMap *tmap = nullptr) {
+  // face states share their storage with the TMA box (U' planes), which is consumed, behind a barrier,
+  // before the WENO phase writes the first face state
+  constexpr int NFX = 4 * TY * (TX + 1), NFY = 4 * (TY + 1) * TX;
+  static_assert(!TMA || 4 * HY * TMA_W <= 2 * (NFX + NFY), "TMA box must fit in the face-state storage");
+  __shared__ alignas(128) float s_face[2 * (NFX + NFY)];
+  __shared__ alignas(8) unsigned long long s_mbar;
   __shared__ float sq[4][HY][HX];  // rho', u, v, p'
   __shared__ float sT[HY][HX];     // T'
-  __shared__ float fLx[4][TY][TX + 1], fRx[4][TY][TX + 1];  // x-face states; fLx then holds the x flux
-  __shared__ float fLy[4][TY + 1][TX], fRy[4][TY + 1][TX];  // y-face states; fLy then holds the y flux
+  float(*fLx)[TY][TX + 1] = reinterpret_cast<float(*)[TY][TX + 1]>(s_face);  // x-face states; fLx then x flux
+  float(*fRx)[TY][TX + 1] = reinterpret_cast<float(*)[TY][TX + 1]>(s_face + NFX);
+  float(*fLy)[TY + 1][TX] = reinterpret_cast<float(*)[TY + 1][TX]>(s_face + 2 * NFX);  // y-face states; then y flux
+  float(*fRy)[TY + 1][TX] = reinterpret_cast<float(*)[TY + 1][TX]>(s_face + 2 * NFX + NFY);
+  float(*s_raw)[HY][TMA_W] = reinterpret_cast<float(*)[HY][TMA_W]>(s_face);  // TMA box
   __shared__ float wm[4];
   __shared__ float lred[8];
   const int ntx = (k.nx + TX - 1) / TX;
@@ -385,7 +442,11 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     wm[2] = (float)Acc[0];
     wm[3] = (float)Acc[1];
   }
+  // interior tile (the loaded region needs no domain mapping): one tensor copy stages it
+  const bool tma = TMA && tmap != nullptr && i0 >= NG && j0 >= NG && i0 + TX + NG <= k.nx && j0 + TY + NG <= k.ny;
+  if (TMA && tma && threadIdx.x == 0) tma_arm_and_load(s_face, tmap, i0, j0, &s_mbar);
   __syncthreads();
+  if (TMA && tma && !tma_wait(&s_mbar) && threadIdx.x == 0) atomicOr(&ds->err, ERR_TIMEOUT);
 
   const long long P = k.plane;
   // body tiles: every IB / ghost node of the loaded region, with its stencil staged in shared memory
@@ -401,7 +462,25 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     int gi = i0 - NG + a, gj = j0 - NG + b;
     float q[4] = {0.f, c.ux, c.uy, 0.f};  // (p', u, v, T'); free stream: zero perturbation
     float dr = 0.f;
-    if (halo_map(k, gi, gj)) {
+    if (TMA && tma) {
+      float u, v, pp, Tp;
+      dr = s_raw[0][b][a];
+      pert_prim(c, dr, s_raw[1][b][a], s_raw[2][b][a], s_raw[3][b][a], u, v, pp, Tp);
+      q[0] = pp;
+      q[1] = u;
+      q[2] = v;
+      q[3] = Tp;
+      if (BODY) {
+        const int e = sid[gj * k.nx + gi];
+        if (e >= 0) {
+          const int slot = atomicAdd(&s_nrb, 1);
+          if (slot < RB_MAX) {
+            s_rbm[slot] = m;
+            s_rbe[slot] = e;
+          }
+        }
+      }
+    } else if (halo_map(k, gi, gj)) {
       const long long id = cidx(k, gi, gj);
       int e = -1;
       if (BODY) e = sid[gj * k.nx + gi];
