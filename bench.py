@@ -153,6 +153,22 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(value, dist, device):
+    """Largest value over the ranks of the process group (a replica job takes as long as its slowest rank);
+    the value itself when there is no process group."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Aggregate throughput of a weak-scaling replica run: the units of all ranks over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def _time_steps(case, torch, flush, K, stream):
     """Device time of K steps, one CUDA-event pair per step on the case stream, L2 flushed in between."""
     total = 0.0
@@ -206,14 +222,10 @@ def run_ours(args, rank, world):
         t_dev_ms = _time_steps(case, torch, flush, args.steps, stream)
     barrier()
     launches = case.launches() - n0
-    if dist:
-        t = torch.tensor([t_dev_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev_ms = float(t.item())
+    t_dev_ms = max_over_ranks(t_dev_ms, dist, "cuda")
     is_dual = spec["time_scheme"] == 1
     stages_per_step = 3 * spec["subiters"] if is_dual else 3
-    units = cells * stages_per_step * args.steps * world
-    value = units / (t_dev_ms * 1e-3) / 1e6
+    value = whole_job_rate(cells * stages_per_step * args.steps, world, t_dev_ms * 1e-3) / 1e6
 
     # live kernel timing for the roofline: the same steps with CUDA events around every kernel group
     case.profile(True)
@@ -330,12 +342,8 @@ def run_ours(args, rank, world):
         case.set_state_from_ptr(host.data_ptr(), host.numel() * 8, False)
         case.step(1)
         case.forces_into(forces.data_ptr())
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": cells * stages_per_step * ke * world / t_e2e / 1e6, "unit": "Mcell-updates/s",
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": whole_job_rate(cells * stages_per_step * ke, world, t_e2e) / 1e6, "unit": "Mcell-updates/s",
            "h2d_bytes_per_step": int(host.numel() * 8), "d2h_bytes_per_step": int(forces.numel() * 8),
            "steps": ke}
 
