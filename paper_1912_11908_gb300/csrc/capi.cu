@@ -26,6 +26,7 @@ struct ibm_case {
          *vny = nullptr;
   double *A = nullptr, *B = nullptr, *C = nullptr;  // FP64 conserved: state, stage arrays (FP64 mode)
   double *Wn = nullptr, *Wm = nullptr;               // dual time: states at time levels n and n-1
+  double *Q0 = nullptr;                              // FP32-bulk dual time: (p', u, v, T') of the sub-iteration start
   float *M = nullptr, *F1 = nullptr, *F2 = nullptr;  // FP32-bulk: perturbation mirror and stage arrays
   double *stage64 = nullptr;  // FP32-bulk: absolute-variable staging for ibm_get_state (allocated on first use)
   uint8_t *solid = nullptr, *tag = nullptr;
@@ -200,11 +201,12 @@ static size_t carve(ibm_case *c, char *base) {
     take(&c->M, 4 * plane);
     take(&c->F1, 4 * plane);
     take(&c->F2, 4 * plane);
-    if (k.dual) {  // FP64 pseudo-stage iterates and time levels
+    if (k.dual) {  // FP64 pseudo-stage iterates, time levels, primitives of the sub-iteration's start
       take(&c->B, 4 * plane);
       take(&c->C, 4 * plane);
       take(&c->Wn, 4 * plane);
       take(&c->Wm, 4 * plane);
+      take(&c->Q0, 4 * plane);
     }
     take(&c->rst, (size_t)(c->cap > 0 ? c->cap : 1));
     take(&c->sid, ncell);
@@ -240,6 +242,8 @@ static void init_case(ibm_case *c, const ibm_geometry *geo, const ibm_grid *gr, 
   k.pinf = 1.0 / (fl->gamma * fl->mach * fl->mach);
   k.R = k.pinf;
   k.cp = k.gamma * k.R / (k.gamma - 1.0);
+  k.iR = 1.0 / k.R;
+  k.ig1 = 1.0 / (k.gamma - 1.0);
   k.mu = fl->re > 0.0 ? 1.0 / fl->re : 0.0;
   k.kappa = k.mu * k.cp / fl->prandtl;
   k.prandtl = fl->prandtl;
@@ -263,6 +267,7 @@ static void init_case(ibm_case *c, const ibm_geometry *geo, const ibm_grid *gr, 
   k.dual = fl->time_scheme == IBM_TIME_DUAL;
   k.subiters = fl->subiters;
   k.dt_phys = fl->dt_phys;
+  k.idt_phys = fl->dt_phys > 0.0 ? 1.0 / fl->dt_phys : 0.0;
   k.cfl_tau = fl->cfl_tau;
   c->g.nv = geo->nverts;
   c->cap = list_capacity(geo, gr);
@@ -505,8 +510,8 @@ static int enqueue_step(ibm_case *c) {
           prof_mark(c, 0, true);
           cudaEventRecord(c->ev_fork, s);
           cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
-          launch_dual_f32(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->Wn, c->Wm, c->tag,
-                          c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, s, c->sb);
+          launch_dual_f32(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->Wn, c->Wm, c->Q0,
+                          c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, s, c->sb);
           cudaEventRecord(c->ev_join, c->sb);
           cudaStreamWaitEvent(s, c->ev_join, 0);
           prof_mark(c, 0, false);

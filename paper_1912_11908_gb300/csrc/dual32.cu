@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(256) k_dual_f32(Consts k, PertConsts c, const 
 }
 
 void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,
-                     double *Out64, const double *Wn, const double *Wm, const uint8_t *tag, const int *sid,
+                     double *Out64, const double *Wn, const double *Wm, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
                      DevState *ds, cudaStream_t s, cudaStream_t sb) {
   PertConsts c = pert_consts(k);
@@ -33,6 +33,7 @@ void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32
   dp.Out64 = Out64;
   dp.Wn = Wn;
   dp.Wm = Wm;
+  dp.Q0 = Q0;
 #define IBM_DUAL_PAIR(S)                                                                                          \
   do {                                                                                                            \
     if (nb)                                                                                                       \

@@ -67,6 +67,8 @@ struct Consts {
   int subiters;     // dual time: sub-iterations per physical step
   double dt_phys;   // dual time: physical step
   double cfl_tau;   // dual time: pseudo-time CFL number
+  double iR, ig1;   // 1/R and 1/(gamma - 1)
+  double idt_phys;  // dual time: 1/dt_phys
 };
 
 // Bounded low-Mach preconditioning: reference velocity never below c/3.
@@ -268,9 +270,10 @@ bool make_stage_tmaps(const Consts &k, float *const arrays[3], CUtensorMap out[3
 // Dual-time pseudo stage (1..3) in FP32-bulk form: residual of the FP32
 // mirror In32, FP64 point-implicit update of the iterate In64 into Out64 (and
 // its mirror Out32); D holds the sub-iteration's starting iterate, Wn / Wm
-// the time levels n and n-1 (all FP64 perturbations).  Body tiles on sb.
+// the time levels n and n-1 (all FP64 perturbations); stage 1 stores the
+// starting iterate's primitives in Q0 for stages 2 and 3.  Body tiles on sb.
 void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,
-                     double *Out64, const double *Wn, const double *Wm, const uint8_t *tag, const int *sid,
+                     double *Out64, const double *Wn, const double *Wm, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
                      DevState *ds, cudaStream_t s, cudaStream_t sb);
 // The same two kernels over a group's block table: the plain kernel (stream s) covers tiles
