@@ -215,6 +215,25 @@ ibm_status ibm_autotune(ibm_case *c, int enable);
  * uses per-thread loads for every tile. */
 ibm_status ibm_use_tma(ibm_case *c, int enable);
 
+/* FP32-bulk explicit steps: run the three SSP-RK3 stages of a step (Sec. 2)
+ * as one persistent launch instead of one plain-tile and one body-tile launch
+ * per stage (default off).  Blocks take (stage, tile) items in order; a
+ * tile's next stage starts as soon as the tiles within two tiles of it have
+ * finished the previous one, so stages overlap across the grid.  Each tile
+ * runs the same arithmetic as in the per-stage launches (separately compiled:
+ * results agree to FP32 rounding).  On GB300 it matches the per-stage
+ * launches on grids of about one wave of tiles per stage and is slower on
+ * larger ones.  A dependency wait that gives up (it cannot, short of a fault)
+ * makes the next sync report IBM_ECUDA. */
+ibm_status ibm_use_persistent(ibm_case *c, int enable);
+
+/* Blocks of the persistent step kernel: 0 (default) = as many as are resident
+ * at once on the device; a smaller number (at least 1; larger values are
+ * clipped to the default) runs fewer items concurrently -- 1 runs every
+ * (stage, tile) item in order on one block.  The result does not depend on
+ * it. */
+ibm_status ibm_persistent_grid(ibm_case *c, int blocks);
+
 /* Replay each step from a CUDA graph captured on first use (default on);
  * enable = 0 launches every kernel directly. */
 ibm_status ibm_use_graphs(ibm_case *c, int enable);

@@ -15,6 +15,7 @@ template <int STAGE, bool BODY>
 __global__ void __launch_bounds__(256, BODY ? 1 : 6) k_stage_f32_batch(const __grid_constant__ StageBatch b) {
   const int *start = BODY ? b.body_start : b.plain_start;
   const int total = start[b.n];
+  __shared__ TileSmem sm;
   for (int e = blockIdx.x; e < total; e += gridDim.x) {
     int q = 0;
     while (q + 1 < b.n && start[q + 1] <= e) q++;
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(256, BODY ? 1 : 6) k_stage_f32_batch(const __g
     const float *In = STAGE == 1 ? sc.M : (STAGE == 2 ? sc.F1 : sc.F2);
     float *Out = STAGE == 1 ? sc.F1 : (STAGE == 2 ? sc.F2 : nullptr);
     stage_tile<STAGE, BODY>(sc.k, sc.c, sc.M, In, Out, sc.D, sc.tag, sc.sid, sc.rs, sc.tile_body, sc.body_tiles,
-                            sc.ds, sc.fuse_cfl != 0, sc.ncfl, e - start[q]);
+                            sc.ds, sc.fuse_cfl != 0, sc.ncfl, e - start[q], sm);
     __syncthreads();  // shared memory is reused by the next entry
   }
 }

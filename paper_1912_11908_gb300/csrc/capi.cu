@@ -42,6 +42,10 @@ struct ibm_case {
   bool use_tma = true;              // stage interior tiles with TMA (ibm_use_tma)
   int plain_variant[2] = {-1, -1};  // FP32-bulk: register budget of the plain stage kernel for stage 1 and for
                                     // stages 2-3 (-1: not tuned yet)
+  unsigned int *sch_words = nullptr;  // FP32-bulk explicit: schedule of the persistent step kernel (StepSched)
+  bool use_persist = false;           // one persistent launch per step (ibm_use_persistent)
+  int step_variant = 0;               // register budget of the persistent kernel
+  int step_grid = 0;                  // its grid (0: not computed yet)
   bool autotune = true;
   int box_w = 0, box_h = 0;      // cells spanned by the body's bounding box (any pose), for classification
   cudaStream_t sb = nullptr;     // FP32-bulk: stream of the body-tile kernels (forked from / joined to stream)
@@ -212,6 +216,7 @@ static size_t carve(ibm_case *c, char *base) {
     take(&c->sid, ncell);
     take(&c->tile_body, (size_t)stage_tiles(k));
     take(&c->body_tiles, (size_t)(c->body_cap > 0 ? c->body_cap : 1));
+    if (!k.dual) take(&c->sch_words, step_sched_bytes(k) / sizeof(unsigned int));
   }
   take(&c->solid, ncell);
   take(&c->tag, ncell);
@@ -401,7 +406,8 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
     // fluid, untagged and unlisted everywhere (the geometry kernels keep that outside the body's rectangle)
     if (cudaMemcpyAsync(c->ds, c->hds, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(c->tag, 0, ncell, s) != cudaSuccess || cudaMemsetAsync(c->solid, 0, ncell, s) != cudaSuccess ||
-        (c->sid && cudaMemsetAsync(c->sid, 0xff, ncell * sizeof(int), s) != cudaSuccess)) {
+        (c->sid && cudaMemsetAsync(c->sid, 0xff, ncell * sizeof(int), s) != cudaSuccess) ||
+        (c->sch_words && cudaMemsetAsync(c->sch_words, 0, step_sched_bytes(k), s) != cudaSuccess)) {
       rs = fail(IBM_ECUDA, "state initialisation failed");
       break;
     }
@@ -484,6 +490,11 @@ static bool fused_cfl(const ibm_case *c) {
          !c->k.dual;
 }
 
+// the explicit FP32-bulk step runs as one persistent launch
+static bool persistent_step(const ibm_case *c) {
+  return c->use_persist && c->sch_words && c->precision == IBM_PREC_FP32_BULK && !c->k.dual;
+}
+
 // one explicit step on the case stream (kernels only; graph-capturable)
 static int enqueue_step(ibm_case *c) {
   cudaStream_t s = c->stream;
@@ -539,6 +550,16 @@ static int enqueue_step(ibm_case *c) {
   if (f64) launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
   else if (!fuse_cfl) launch_dt_f32(c->k, c->M, c->tag, c->ds, s, &nl);
   prof_mark(c, 3, false);
+  if (!f64 && persistent_step(c)) {
+    // the three stages in one launch (the end of the step and the next dt included)
+    if (!c->step_grid) c->step_grid = step_f32_grid(c->k, c->step_variant);
+    prof_mark(c, 0, true);
+    launch_step_f32(c->k, c->M, c->F1, c->F2, c->A, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles,
+                    c->body_cap, c->ds, reinterpret_cast<StepSched *>(c->sch_words), fuse_cfl,
+                    c->have_tmap && c->use_tma ? c->tmap : nullptr, c->step_variant, c->step_grid, 1, 3, s);
+    prof_mark(c, 0, false);
+    return nl + 1;
+  }
   double *in64[3] = {c->A, c->B, c->C};
   double *out64[3] = {c->B, c->C, c->A};
   float *in32[3] = {c->M, c->F1, c->F2};
@@ -686,7 +707,7 @@ extern "C" ibm_status ibm_step(ibm_case *c, int nsteps) {
     c->launches += nl;
     c->dt_valid = true;
   }
-  if (c->plain_variant[0] < 0) {
+  if (c->plain_variant[0] < 0 && !persistent_step(c)) {
     ibm_status r = tune_plain_variant(c);
     if (r != IBM_OK) return r;
   }
@@ -762,6 +783,29 @@ extern "C" ibm_status ibm_use_tma(ibm_case *c, int enable) {
     c->graph = nullptr;
   }
   c->use_tma = enable != 0;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_use_persistent(ibm_case *c, int enable) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  if (c->graph) {  // the captured step holds the old choice
+    CU(cudaStreamSynchronize(c->stream));
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->use_persist = enable != 0;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_persistent_grid(ibm_case *c, int blocks) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  if (blocks < 0) return fail(IBM_EINVAL, "blocks < 0");
+  if (c->graph) {
+    CU(cudaStreamSynchronize(c->stream));
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->step_grid = blocks > 0 ? std::min(blocks, step_f32_grid(c->k, c->step_variant)) : 0;
   return IBM_OK;
 }
 

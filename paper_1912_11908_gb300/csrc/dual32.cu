@@ -16,8 +16,9 @@ __global__ void __launch_bounds__(256) k_dual_f32(Consts k, PertConsts c, const 
                                                   const uint8_t *__restrict__ tile_body,
                                                   const int *__restrict__ body_tiles, DevState *ds, unsigned int ncfl,
                                                   DualPtrs dp) {
+  __shared__ TileSmem sm;
   stage_tile<STAGE, BODY, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body, body_tiles, ds, false, ncfl,
-                                (int)blockIdx.x, dp);
+                                (int)blockIdx.x, sm, dp);
 }
 
 void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,

@@ -128,8 +128,9 @@ __global__ void __launch_bounds__(256, MINB) k_stage_f32(Consts k, PertConsts c,
                                                    const int *__restrict__ body_tiles, DevState *ds, bool fuse_cfl,
                                                    unsigned int ncfl, const __grid_constant__ CUtensorMap tmap,
                                                    int use_tma) {
+  __shared__ TileSmem sm;
   stage_tile<STAGE, BODY, false, true>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, fuse_cfl, ncfl,
-                                       (int)blockIdx.x, DualPtrs{}, use_tma ? &tmap : nullptr);
+                                       (int)blockIdx.x, sm, DualPtrs{}, use_tma ? &tmap : nullptr);
 }
 
 int stage_tiles(const Consts &k) { return ((k.nx + TX - 1) / TX) * ((k.ny + TY - 1) / TY); }

@@ -35,6 +35,9 @@ struct DevState {
   int prect_valid;               // 0 before the first classification
   double force[4];               // Cd, Cl, Fx, Fy
   long long steps;
+  double dt_next;                // persistent step kernel: dt of the next step, applied when the step ends
+  float dtf_next;
+  int pad2;
 };
 
 // IB / ghost lists up to this capacity are rebuilt by a single 1024-thread
@@ -119,15 +122,22 @@ __device__ __forceinline__ double stage_time(const DevState *ds, int stage) {
 // Last block of a CFL reduction: turn the maximum spectral radius into dt and
 // reset the reduction state for the next step.  Call from thread 0 after the
 // block's atomicMax; nblocks = blocks taking part (of one or more kernels).
-__device__ __forceinline__ void finish_cfl(const Consts &k, DevState *ds, unsigned int nblocks) {
+// defer: store dt as the next step's (dt_next), for a kernel that still reads
+// the current dt.
+__device__ __forceinline__ void finish_cfl(const Consts &k, DevState *ds, unsigned int nblocks, bool defer = false) {
   __threadfence();
   const unsigned int ticket = atomicAdd(&ds->done, 1u);
   if (ticket == nblocks - 1) {
     __threadfence();
     const unsigned long long bits = atomicAdd(&ds->lmax_bits, 0ull);
     const double dt = k.cfl / __longlong_as_double((long long)bits);
-    ds->dt = dt;
-    ds->dtf = (float)dt;
+    if (defer) {
+      ds->dt_next = dt;
+      ds->dtf_next = (float)dt;
+    } else {
+      ds->dt = dt;
+      ds->dtf = (float)dt;
+    }
     ds->lmax_bits = 0ull;
     ds->done = 0u;
   }
@@ -267,6 +277,31 @@ void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, fl
 // for the TMA staging of interior tiles (tmap above); false if the driver
 // offers no encoder or the grid is too small for a box.
 bool make_stage_tmaps(const Consts &k, float *const arrays[3], CUtensorMap out[3]);
+// Persistent step kernel (step32.cu): the three SSP-RK3 stages of one
+// explicit FP32-bulk step in one launch.  Blocks take (stage, tile) items in
+// order from one counter: per stage the body tiles first (list order), then
+// the other tiles (row-major); the item of stage s > 1 first waits until
+// every tile within two tile columns and rows (wrapping across periodic
+// sides) has finished stage s - 1.  Completion counts are epoch-based (3 x
+// launches before + stages done), so only the claim counter is reset between
+// launches; the last block to leave ends the step (t += dt, step count, next
+// dt of the fused CFL) and rearms it.
+struct StepSched {
+  unsigned int next;    // next item to hand out
+  unsigned int exited;  // blocks that have left the item loop
+  unsigned int epoch;   // launches completed
+  unsigned int pad;
+  // followed by one completion count per tile
+};
+constexpr int STEP_VARIANTS = 2;  // register budget: 0 -> 40 registers (six blocks per SM), 1 -> 48 (five)
+size_t step_sched_bytes(const Consts &k);
+// grid of the persistent kernel: resident blocks per SM x SMs, at most 3 x tiles
+int step_f32_grid(const Consts &k, int variant);
+// tmaps: tensor maps of M, F1, F2 (NULL: per-thread tile loads)
+cudaError_t launch_step_f32(const Consts &k, float *M, float *F1, float *F2, double *D, const uint8_t *tag,
+                            const int *sid, const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles,
+                            int body_cap, DevState *ds, StepSched *sch, bool fuse_cfl, const CUtensorMap *tmaps,
+                            int variant, int grid, int s_first, int s_last, cudaStream_t s);
 // Dual-time pseudo stage (1..3) in FP32-bulk form: residual of the FP32
 // mirror In32, FP64 point-implicit update of the iterate In64 into Out64 (and
 // its mirror Out32); D holds the sub-iteration's starting iterate, Wn / Wm

@@ -134,6 +134,25 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
 // FP32 mirror of U^{n+1}.
 // ---------------------------------------------------------------------------
 constexpr int TX = STAGE_TILE, TY = STAGE_TILE, HX = TX + 2 * NG, HY = TY + 2 * NG;
+constexpr int NFX = 4 * TY * (TX + 1), NFY = 4 * (TY + 1) * TX;  // x-face and y-face values of a tile
+constexpr int RB_MAX = 192;  // IB / ghost nodes a body tile's loaded region may hold
+
+// Shared memory of one tile.  face holds, in turn: the TMA box of the tile's
+// stage input, the stencils of the region's IB / ghost nodes (body tiles),
+// the WENO face states, the face fluxes; each use ends behind a barrier
+// before the next begins.
+struct TileSmem {
+  alignas(128) float face[2 * (NFX + NFY)];
+  float sq[4][HY][HX];  // rho', u, v, p' of the loaded region
+  float sT[HY][HX];     // T'
+  unsigned long long mbar;
+  unsigned int mbar_phase;  // persistent kernel: parity of the barrier's next phase (barrier initialised once)
+  float wm[4];    // wall velocity and acceleration at the stage time
+  float lred[8];  // per-warp maxima of the CFL reduction
+  int nrb;        // listed IB / ghost nodes (body tiles)
+  int rbm[RB_MAX], rbe[RB_MAX];
+};
+static_assert(RB_MAX * sizeof(RStencil32) <= sizeof(float) * 2 * (NFX + NFY), "node stencils fit the face storage");
 
 // ---------------------------------------------------------------------------
 // TMA staging of a tile (Blackwell bulk tensor copy, inline PTX).  The FP32
@@ -149,11 +168,14 @@ constexpr int TMA_WAIT_LIMIT = 1 << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void tma_arm_and_load(float *dst, const CUtensorMap *map, int x, int y,
-                                                 unsigned long long *mbar) {
-  const unsigned m = smem_u32(mbar);
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(m) : "memory");
+__device__ __forceinline__ void tma_init(unsigned long long *mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// arm the (initialised) barrier with the box's byte count and issue the copy
+__device__ __forceinline__ void tma_load(float *dst, const CUtensorMap *map, int x, int y, unsigned long long *mbar) {
+  const unsigned m = smem_u32(mbar);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(TMA_BYTES) : "memory");
   asm volatile(
@@ -163,15 +185,15 @@ __device__ __forceinline__ void tma_arm_and_load(float *dst, const CUtensorMap *
       : "memory");
 }
 
-// wait for phase 0 of the barrier; false if the bounded wait gave up
-__device__ __forceinline__ bool tma_wait(unsigned long long *mbar) {
+// wait for the completion of the barrier's phase with the given parity; false if the bounded wait gave up
+__device__ __forceinline__ bool tma_wait(unsigned long long *mbar, unsigned parity) {
   const unsigned m = smem_u32(mbar);
   for (int it = 0; it < TMA_WAIT_LIMIT; it++) {
     unsigned ok;
     asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
         : "=r"(ok)
-        : "r"(m)
+        : "r"(m), "r"(parity)
         : "memory");
     if (ok) return true;
   }
@@ -190,7 +212,7 @@ __device__ __forceinline__ float cfl_lambda(const Consts &k, const PertConsts &c
 // block maximum of lam (all 256 threads call), then the grid-wide maximum and
 // dt through the last-block pattern
 __device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float *red, DevState *ds,
-                                              unsigned int nblocks) {
+                                              unsigned int nblocks, bool defer) {
   for (int off = 16; off > 0; off >>= 1) lam = fmaxf(lam, __shfl_xor_sync(0xffffffffu, lam, off));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lam;
   __syncthreads();
@@ -198,8 +220,16 @@ __device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float 
     float m = red[0];
     for (int w = 1; w < 8; w++) m = fmaxf(m, red[w]);
     atomicMax(&ds->lmax_bits, (unsigned long long)__double_as_longlong((double)m));
-    finish_cfl(k, ds, nblocks);
+    finish_cfl(k, ds, nblocks, defer);
   }
+}
+
+// load of a value that other blocks of the same launch may have written (CG:
+// through L2, never the non-coherent read-only path)
+template <bool CG, class T>
+__device__ __forceinline__ T ld_stage(const T *p) {
+  if (CG) return __ldcg(p);
+  return *p;
 }
 
 // ---------------------------------------------------------------------------
@@ -210,10 +240,12 @@ __device__ __forceinline__ void cfl_block_max(const Consts &k, float lam, float 
 // region, then all ghost nodes, reading corners from shared memory and only
 // corners outside the region from the stage input.
 // ---------------------------------------------------------------------------
+template <bool CG = false>
 __device__ __forceinline__ void raw_prim(const PertConsts &c, const float *U, long long id, long long P,
                                          float q[4]) {
   float u, v, pp, Tp;
-  pert_prim(c, U[id], U[id + P], U[id + 2 * P], U[id + 3 * P], u, v, pp, Tp);
+  pert_prim(c, ld_stage<CG>(U + id), ld_stage<CG>(U + id + P), ld_stage<CG>(U + id + 2 * P),
+            ld_stage<CG>(U + id + 3 * P), u, v, pp, Tp);
   q[0] = pp;
   q[1] = u;
   q[2] = v;
@@ -231,13 +263,14 @@ __device__ __forceinline__ void wall_bc(const PertConsts &c, const RStencil32 &s
   q[3] = qp[3];
 }
 
+template <bool CG>
 static __device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts &c, const float *U,
-                                        const RStencil32 &s, const float *wm, float q[4]) {
+                                               const RStencil32 &s, const float *wm, float q[4]) {
   float qp[4] = {0.f, 0.f, 0.f, 0.f};
   for (int b = 0; b < 4; b++) {
     if (!(s.mask >> b & 1)) continue;  // bits 0-3: valid corners (bit 4: IB node)
     float cq[4];
-    raw_prim(c, U, s.corner + (b & 1) + (b >> 1) * k.pitch, k.plane, cq);
+    raw_prim<CG>(c, U, s.corner + (b & 1) + (b >> 1) * k.pitch, k.plane, cq);
     for (int v = 0; v < 4; v++) qp[v] += s.w[b] * cq[v];
   }
   wall_bc(c, s, qp, wm, q);
@@ -260,35 +293,40 @@ static __device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts
 // start, Out receives the FP32 mirror of the new iterate).
 // TMA: the kernel may stage interior tiles with a tensor copy (tmap: tensor
 // map of In; NULL loads every tile with per-thread loads).
-template <int STAGE, bool BODY, bool DUAL = false, bool TMA = false>
+// PERSIST: the tile's stage inside the persistent step kernel -- blk is the
+// tile itself; In, D and the stage arrays may have been written by other
+// blocks of the same launch (coherent loads); stage times come from t and dt,
+// which stay fixed during the launch; the step's end (t, step count) and the
+// next dt are left to the kernel.
+// sm: the block's shared memory.
+template <int STAGE, bool BODY, bool DUAL = false, bool TMA = false, bool PERSIST = false>
 __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c, float *Mn,
                                            const float *__restrict__ In, float *Out, double *D,
-                                           const uint8_t *__restrict__ tag, const int *__restrict__ sid,
-                                           const RStencil32 *__restrict__ rs, const uint8_t *__restrict__ tile_body,
-                                           const int *__restrict__ body_tiles, DevState *ds, bool fuse_cfl,
-                                           unsigned int ncfl, int blk, const DualPtrs &dp = DualPtrs{},
-                                           const CUtensorMap *tmap = nullptr) {
-  // face states share their storage with the TMA box (U' planes), which is consumed, behind a barrier,
-  // before the WENO phase writes the first face state
-  constexpr int NFX = 4 * TY * (TX + 1), NFY = 4 * (TY + 1) * TX;
+                                           const uint8_t *__restrict__ tag,
+                                           const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
+                                           const uint8_t *__restrict__ tile_body, const int *__restrict__ body_tiles,
+                                           DevState *ds, bool fuse_cfl, unsigned int ncfl, int blk, TileSmem &sm,
+                                           const DualPtrs &dp = DualPtrs{}, const CUtensorMap *tmap = nullptr) {
   static_assert(!TMA || 4 * HY * TMA_W <= 2 * (NFX + NFY), "TMA box must fit in the face-state storage");
-  __shared__ alignas(128) float s_face[2 * (NFX + NFY)];
-  __shared__ alignas(8) unsigned long long s_mbar;
-  __shared__ float sq[4][HY][HX];  // rho', u, v, p'
-  __shared__ float sT[HY][HX];     // T'
+  float *s_face = sm.face;
+  unsigned long long &s_mbar = sm.mbar;
+  float(&sq)[4][HY][HX] = sm.sq;
+  float(&sT)[HY][HX] = sm.sT;
   float(*fLx)[TY][TX + 1] = reinterpret_cast<float(*)[TY][TX + 1]>(s_face);  // x-face states; fLx then x flux
   float(*fRx)[TY][TX + 1] = reinterpret_cast<float(*)[TY][TX + 1]>(s_face + NFX);
   float(*fLy)[TY + 1][TX] = reinterpret_cast<float(*)[TY + 1][TX]>(s_face + 2 * NFX);  // y-face states; then y flux
   float(*fRy)[TY + 1][TX] = reinterpret_cast<float(*)[TY + 1][TX]>(s_face + 2 * NFX + NFY);
   float(*s_raw)[HY][TMA_W] = reinterpret_cast<float(*)[HY][TMA_W]>(s_face);  // TMA box
-  __shared__ float wm[4];
-  __shared__ float lred[8];
+  float *wm = sm.wm;
+  float *lred = sm.lred;
   const int ntx = (k.nx + TX - 1) / TX;
   // every block reads dt before any block can finish the fused CFL reduction
   const double dtd = ds->dt;
   const float dt = ds->dtf;
   int tile;
-  if (BODY) {
+  if (PERSIST) {
+    tile = blk;
+  } else if (BODY) {
     tile = blk < ds->nbody_tiles ? body_tiles[blk] : -1;
   } else {
     tile = tile_body[blk] ? -1 : blk;
@@ -303,7 +341,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     }
   }
   if (tile < 0) {
-    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds, ncfl);
+    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds, ncfl, PERSIST);
     return;
   }
   const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
@@ -315,12 +353,14 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
   // stages 1 and 3 also keep the IB / ghost nodes of U^n current; stage 2 only needs fluid cells
   const bool work = STAGE == 2 ? fluid : (mytag != SOLID);
   if (!__syncthreads_or(work)) {
-    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds, ncfl);
+    if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds, ncfl, PERSIST);
     return;
   }
   if (BODY && threadIdx.x == 0) {
     double X[2], V[2], Acc[2];
-    motion_at(k.motion, DUAL ? ds->t + k.dt_phys : (STAGE == 1 ? ds->t : ds->tst[STAGE - 2]), X, V, Acc);
+    const double ts = DUAL ? ds->t + k.dt_phys
+                           : (PERSIST ? stage_time(ds, STAGE) : (STAGE == 1 ? ds->t : ds->tst[STAGE - 2]));
+    motion_at(k.motion, ts, X, V, Acc);
     wm[0] = (float)V[0];
     wm[1] = (float)V[1];
     wm[2] = (float)Acc[0];
@@ -328,17 +368,25 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
   }
   // interior tile (the loaded region needs no domain mapping): one tensor copy stages it
   const bool tma = TMA && tmap != nullptr && i0 >= NG && j0 >= NG && i0 + TX + NG <= k.nx && j0 + TY + NG <= k.ny;
-  if (TMA && tma && threadIdx.x == 0) tma_arm_and_load(s_face, tmap, i0, j0, &s_mbar);
+  if (TMA && tma && threadIdx.x == 0) {
+    if (PERSIST) {
+      // the box may hold values other blocks of this launch wrote: order the tensor copy after them
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    } else {
+      tma_init(&s_mbar);
+    }
+    tma_load(s_face, tmap, i0, j0, &s_mbar);
+  }
   __syncthreads();
-  if (TMA && tma && !tma_wait(&s_mbar) && threadIdx.x == 0) atomicOr(&ds->err, ERR_TIMEOUT);
+  if (TMA && tma && !tma_wait(&s_mbar, PERSIST ? sm.mbar_phase : 0u) && threadIdx.x == 0)
+    atomicOr(&ds->err, ERR_TIMEOUT);
 
   const long long P = k.plane;
-  // body tiles: every IB / ghost node of the loaded region, with its stencil staged in shared memory
-  constexpr int RB_MAX = 192;
-  __shared__ int s_nrb;
-  __shared__ int s_rbm[BODY ? RB_MAX : 1];
-  __shared__ int s_rbe[BODY ? RB_MAX : 1];
-  __shared__ RStencil32 s_rs[BODY ? RB_MAX : 1];
+  // body tiles: every IB / ghost node of the loaded region, with its stencil staged in shared memory (in the
+  // face storage, after the TMA box has been consumed)
+  int &s_nrb = sm.nrb;
+  int *s_rbm = sm.rbm, *s_rbe = sm.rbe;
+  RStencil32 *s_rs = reinterpret_cast<RStencil32 *>(s_face);
   if (BODY && threadIdx.x == 0) s_nrb = 0;
   if (BODY) __syncthreads();
   for (int m = threadIdx.x; m < HX * HY; m += 256) {
@@ -368,8 +416,8 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
       const long long id = cidx(k, gi, gj);
       int e = -1;
       if (BODY) e = sid[gj * k.nx + gi];
-      dr = In[id];
-      raw_prim(c, In, id, P, q);
+      dr = ld_stage<PERSIST>(In + id);
+      raw_prim<PERSIST>(c, In, id, P, q);
       if (BODY && e >= 0) {
         const int slot = atomicAdd(&s_nrb, 1);
         if (slot < RB_MAX) {
@@ -385,37 +433,53 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     sT[b][a] = q[3];
   }
   __syncthreads();
+  // every thread has waited on this phase: the next tile's copy completes the other parity
+  if (PERSIST && TMA && tma && threadIdx.x == 0) sm.mbar_phase ^= 1u;
   if (BODY) {
     const int nrb = min(s_nrb, RB_MAX);
     for (int r = threadIdx.x; r < nrb; r += 256) s_rs[r] = rs[s_rbe[r]];
     __syncthreads();
     // rebuild the listed nodes in place: IB nodes, barrier, ghost nodes (whose image points may use IB
     // nodes); corners inside the loaded region come from shared memory
+    // four lanes per node, one stencil corner each, so that corners outside the loaded region (chains of
+    // dependent global loads) overlap; the node's first lane sums the corners in stencil order
     for (int pass = 0; pass < 2; pass++) {
-      for (int r = threadIdx.x; r < nrb; r += 256) {
-        const RStencil32 &st = s_rs[r];
-        const bool is_ib = (st.mask & 16) != 0;
-        if (is_ib != (pass == 0) || !(st.mask & 15)) continue;
-        const int m = s_rbm[r], a = m % HX, b = m / HX;
-        float qp[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int cq = 0; cq < 4; cq++) {
-          if (!(st.mask >> cq & 1)) continue;
-          const int cn = st.ccell + (cq & 1) + (cq >> 1) * k.nx;
-          const int la = cn % k.nx - (i0 - NG), lb = cn / k.nx - (j0 - NG);
-          float v4[4];
-          if (la >= 0 && la < HX && lb >= 0 && lb < HY) {
-            v4[0] = sq[3][lb][la];
-            v4[1] = sq[1][lb][la];
-            v4[2] = sq[2][lb][la];
-            v4[3] = sT[lb][la];
-          } else {
-            // corner outside the loaded region: fluid value, or an IB node rebuilt from its own stencil
-            const int e2 = pass == 1 ? sid[cn] : -1;
-            if (e2 >= 0 && (rs[e2].mask & 15)) rebuild_ib(k, c, In, rs[e2], wm, v4);
-            else raw_prim(c, In, st.corner + (cq & 1) + (cq >> 1) * k.pitch, P, v4);
+      for (int t0 = 0; t0 < 4 * nrb; t0 += 256) {  // block-uniform: every lane takes part in the shuffles
+        const int r = (t0 + (int)threadIdx.x) >> 2, cq = threadIdx.x & 3;
+        bool node = false;
+        float v4[4] = {0.f, 0.f, 0.f, 0.f};
+        if (r < nrb) {
+          const RStencil32 &st = s_rs[r];
+          node = ((st.mask & 16) != 0) == (pass == 0) && (st.mask & 15);
+          if (node && (st.mask >> cq & 1)) {
+            const int cn = st.ccell + (cq & 1) + (cq >> 1) * k.nx;
+            const int la = cn % k.nx - (i0 - NG), lb = cn / k.nx - (j0 - NG);
+            if (la >= 0 && la < HX && lb >= 0 && lb < HY) {
+              v4[0] = sq[3][lb][la];
+              v4[1] = sq[1][lb][la];
+              v4[2] = sq[2][lb][la];
+              v4[3] = sT[lb][la];
+            } else {
+              // corner outside the loaded region: fluid value, or an IB node rebuilt from its own stencil
+              const int e2 = pass == 1 ? sid[cn] : -1;
+              if (e2 >= 0 && (rs[e2].mask & 15)) rebuild_ib<PERSIST>(k, c, In, rs[e2], wm, v4);
+              else raw_prim<PERSIST>(c, In, st.corner + (cq & 1) + (cq >> 1) * k.pitch, P, v4);
+            }
           }
-          for (int v = 0; v < 4; v++) qp[v] += st.w[cq] * v4[v];
         }
+        const int lane0 = (int)(threadIdx.x & 31) & ~3;
+        float qp[4] = {0.f, 0.f, 0.f, 0.f};
+        const unsigned int mask = r < nrb ? (unsigned int)s_rs[r].mask : 0u;
+        for (int j = 0; j < 4; j++) {
+          const float wj = r < nrb ? s_rs[r].w[j] : 0.f;
+          for (int v = 0; v < 4; v++) {
+            const float x = __shfl_sync(0xffffffffu, v4[v], lane0 + j);
+            if (mask >> j & 1) qp[v] += wj * x;
+          }
+        }
+        if (!node || cq != 0) continue;
+        const RStencil32 &st = s_rs[r];
+        const int m = s_rbm[r], a = m % HX, b = m / HX;
         float q[4];
         wall_bc(c, st, qp, wm, q);
         sq[0][b][a] = (q[0] - c.R * q[3]) / (c.R * (1.f + q[3]));
@@ -569,14 +633,15 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     } else if (STAGE == 1) {
       for (int v = 0; v < 4; v++) Out[id + v * P] = Mn[id + v * P] + dt * L[v];
     } else if (STAGE == 2) {
-      for (int v = 0; v < 4; v++) Out[id + v * P] = 0.75f * Mn[id + v * P] + 0.25f * (In[id + v * P] + dt * L[v]);
+      for (int v = 0; v < 4; v++)
+        Out[id + v * P] = 0.75f * Mn[id + v * P] + 0.25f * (ld_stage<PERSIST>(In + id + v * P) + dt * L[v]);
     } else {
       // FP64 accumulation: dU^{n+1} = dU^n + (double)[2/3 ((dU^(2) - dU^n) + dt L)]
       float mnew[4];
       for (int v = 0; v < 4; v++) {
         const long long o = id + v * P;
-        const float inc = (2.f / 3.f) * ((In[o] - Mn[o]) + dt * L[v]);
-        const double dn = D[o] + (double)inc;
+        const float inc = (2.f / 3.f) * ((ld_stage<PERSIST>(In + o) - Mn[o]) + dt * L[v]);
+        const double dn = ld_stage<PERSIST>(D + o) + (double)inc;
         D[o] = dn;
         mnew[v] = (float)dn;
         Mn[o] = mnew[v];
@@ -585,10 +650,10 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     }
   } else if (!DUAL && BODY && STAGE == 3 && inside && mytag != SOLID) {
     // IB / ghost node: the mirror of U^{n+1} takes the value rebuilt at stage 1
-    for (int v = 0; v < 4; v++) Mn[id + v * P] = (float)D[id + v * P];
+    for (int v = 0; v < 4; v++) Mn[id + v * P] = (float)ld_stage<PERSIST>(D + id + v * P);
   }
   // one call site for the whole block (the reduction has a barrier)
-  if (STAGE == 3 && fuse_cfl) cfl_block_max(k, lam, lred, ds, ncfl);
+  if (STAGE == 3 && fuse_cfl) cfl_block_max(k, lam, lred, ds, ncfl, PERSIST);
 }
 
 

@@ -60,7 +60,8 @@ EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_
            "ibm_sync", "ibm_destroy_case", "ibm_case_device_bytes", "ibm_launch_count", "ibm_last_error",
            "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs", "ibm_tag_nodes_noalloc",
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
-           "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats", "ibm_autotune", "ibm_use_tma"]
+           "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats", "ibm_autotune", "ibm_use_tma",
+           "ibm_use_persistent", "ibm_persistent_grid"]
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 SERVE_BATCHED, SERVE_AUTOTUNE = 1, 2
 SERVER_STATS = ["group_graphs", "group_steps", "group_kernels", "autotune_runs", "capture_us"]
@@ -102,6 +103,10 @@ def load():
     L.ibm_autotune.restype = ip
     L.ibm_use_tma.argtypes = [vp, ip]
     L.ibm_use_tma.restype = ip
+    L.ibm_use_persistent.argtypes = [vp, ip]
+    L.ibm_use_persistent.restype = ip
+    L.ibm_persistent_grid.argtypes = [vp, ip]
+    L.ibm_persistent_grid.restype = ip
     L.ibm_tag_nodes_noalloc.argtypes = [ctypes.POINTER(ibm_grid), vp, ip, vp, vp, ctypes.c_int32, vp, vp]
     L.ibm_tag_nodes_noalloc.restype = ip
     L.ibm_server_create.argtypes = [sz, ip, ip, ctypes.POINTER(vp)]
@@ -281,6 +286,12 @@ class Case:
 
     def use_tma(self, enable):
         _check(lib().ibm_use_tma(self.h, int(enable)))
+
+    def use_persistent(self, enable):
+        _check(lib().ibm_use_persistent(self.h, int(enable)))
+
+    def persistent_grid(self, blocks):
+        _check(lib().ibm_persistent_grid(self.h, int(blocks)))
 
     def use_graphs(self, enable):
         _check(lib().ibm_use_graphs(self.h, 1 if enable else 0))
