@@ -91,14 +91,19 @@ def source_sha256(files):
     return h.hexdigest()
 
 
-def _traffic(summary):
-    """DRAM bytes per launch from a committed ncu summary (profiles/*.json), if the kernel source is unchanged."""
+def _traffic(summary, grid, stage_launch=None):
+    """DRAM bytes per launch from a committed ncu summary (profiles/*.json), if the kernel source is unchanged
+    and the summary covers this grid and the launch form in use."""
     p = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     if d.get("source_sha256") != source_sha256(d.get("sources", [])):
+        return None
+    if list(d.get("grid", [])) != list(grid):
+        return None
+    if stage_launch is not None and "stage_launch" in d and (d["stage_launch"] > 0) != (stage_launch > 0):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -204,6 +209,8 @@ def run_ours(args, rank, world):
 
     spec = _spec(args.workload, args.precision, args.grid)
     case = ibm.Case(spec, stream=stream.cuda_stream)
+    if args.stage_launch is not None and args.precision == "fp32_bulk":
+        case.stage_launches(args.stage_launch)
     case.classify()
     cells = _active_cells(case)
     case.step(args.warmup)
@@ -242,7 +249,9 @@ def run_ours(args, rank, world):
     achieved = bytes_per_launch / (stage_avg_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     if args.precision == "fp32_bulk":
-        traffic = _traffic("k_dual_f32_naca1024x512.json" if is_dual else "k_stage_f32_wedge768x384.json")
+        grid = (spec["nx"], spec["ny"])
+        traffic = (_traffic("k_dual_f32_naca1024x512.json", grid) if is_dual
+                   else _traffic("k_stage_f32_wedge768x384.json", grid, case.stage_launch()))
     else:
         traffic = None
     flops_per_launch = (DUAL_FP64_FLOPS_PER_CELL if is_dual else FLOPS_PER_CELL_STAGE) * spec["nx"] * spec["ny"]
@@ -253,7 +262,8 @@ def run_ours(args, rank, world):
         rl_src = "derived: FP32 peak / 64 (GB300 FP64 rate)"
     else:
         rl_bound, rl_peak = "alu", fp32_peak_tflops()
-        rl_kernel = "k_stage_f32 (plain + body tiles)" if args.precision == "fp32_bulk" else "k_stage_f64"
+        rl_kernel = ("k_stage_f32_one (plain and body tiles in one launch per stage)" if case.stage_launch() > 0
+                     else "k_stage_f32 (plain + body tiles)") if args.precision == "fp32_bulk" else "k_stage_f64"
         rl_src = "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
 
     # plain FP64 path on the same workload and GPU
@@ -370,7 +380,7 @@ def run_ours(args, rank, world):
                    "time_scheme": "dual time (BDF2, %d sub-iterations)" % spec["subiters"] if is_dual else "SSP-RK3",
                    "l2": "flushed between timed steps (512 MiB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU", "cuda_graphs": True,
-                   "autotuned_plain_variants": list(case.tuning())},
+                   "autotuned_plain_variants": list(case.tuning()), "stage_launch": case.stage_launch()},
         "roofline": {"bound": rl_bound, "kernel": rl_kernel, "achieved": achieved_tf, "peak": rl_peak, "unit": "TFLOP/s",
                      "frac": achieved_tf / rl_peak, "peak_source": rl_src,
                      "flops_per_launch": flops_per_launch, "traffic": traffic, "avg_launch_ms": stage_avg_ms,
@@ -507,6 +517,8 @@ def main():
     ap.add_argument("--workload", default="wedge_768x384", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32_bulk", choices=["fp32_bulk", "fp64"])
     ap.add_argument("--grid", default=None, help="override the workload grid, e.g. 3072x1536 (profiling)")
+    ap.add_argument("--stage-launch", type=int, default=None, choices=[0, 1, 2],
+                    help="pin the launch form of the FP32-bulk explicit stages (default: the autotuner's pick)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-dual", action="store_true")

@@ -44,6 +44,9 @@ struct ibm_case {
                                     // stages 2-3 (-1: not tuned yet)
   unsigned int *sch_words = nullptr;  // FP32-bulk explicit: schedule of the persistent step kernel (StepSched)
   bool use_persist = false;           // one persistent launch per step (ibm_use_persistent)
+  int stage_launch = 2;               // FP32-bulk explicit stages: 0 plain + body kernels on two streams, 1 one
+                                      // kernel, 2 one kernel chained by programmatic launch (ibm_stage_launches)
+  bool launch_pinned = false;         // stage_launch set by the caller (else the autotuner picks 0 or 2)
   int step_variant = 0;               // register budget of the persistent kernel
   int step_grid = 0;                  // its grid (0: not computed yet)
   bool autotune = true;
@@ -574,14 +577,19 @@ static int enqueue_step(ibm_case *c) {
     // inside the stage kernel's tile load; the end of the step (t += dt) is
     // folded into stage 3
     prof_mark(c, 0, true);
+    const int pv = c->plain_variant[st == 1 ? 0 : 1] < 0 ? 0 : c->plain_variant[st == 1 ? 0 : 1];
     if (f64) launch_stage_f64(c->k, st, c->A, in64[st - 1], out64[st - 1], c->tag, c->ds, s);
-    else {
+    else if (c->stage_launch > 0) {
+      // one launch for all tiles of the stage (body-tile slots first)
+      launch_stage_f32_one(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->tile_body,
+                           c->body_tiles, c->body_cap, c->ds, fuse_cfl, pv,
+                           c->have_tmap && c->use_tma ? &c->tmap[st - 1] : nullptr, c->stage_launch == 2, s);
+    } else {
       // body tiles run on a forked stream, concurrently with the plain tiles
       cudaEventRecord(c->ev_fork, s);
       cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
       launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->tile_body,
-                       c->body_tiles, c->body_cap, c->ds, fuse_cfl, s, c->sb,
-                       c->plain_variant[st == 1 ? 0 : 1] < 0 ? 0 : c->plain_variant[st == 1 ? 0 : 1], true,
+                       c->body_tiles, c->body_cap, c->ds, fuse_cfl, s, c->sb, pv, true,
                        c->have_tmap && c->use_tma ? &c->tmap[st - 1] : nullptr);
       cudaEventRecord(c->ev_join, c->sb);
       cudaStreamWaitEvent(s, c->ev_join, 0);
@@ -602,7 +610,10 @@ static int enqueue_step(ibm_case *c) {
 // stage-1 array) and write the stage arrays, the stage times, and U^n on IB /
 // ghost nodes with the values the step's own stage 1 writes again.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;
+struct Tuned {
+  int v1, v2, launch;
+};
+static std::map<std::tuple<int, int, int, int>, Tuned> g_tuned;
 
 static ibm_status tune_plain_variant(ibm_case *c) {
   if (c->precision != IBM_PREC_FP32_BULK || c->plain_variant[0] >= 0) return IBM_OK;
@@ -610,62 +621,88 @@ static ibm_status tune_plain_variant(ibm_case *c) {
     c->plain_variant[0] = c->plain_variant[1] = 0;
     return IBM_OK;
   }
-  const auto key = std::make_tuple(c->device, c->k.nx, c->k.ny);
+  // candidates: the register budgets of the launch form the caller pinned, or of both forms (two-stream plain and
+  // body kernels; one kernel per stage with programmatic launch)
+  const auto key = std::make_tuple(c->device, c->k.nx, c->k.ny, c->launch_pinned ? c->stage_launch : -1);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      c->plain_variant[0] = it->second.first;
-      c->plain_variant[1] = it->second.second;
+      c->plain_variant[0] = it->second.v1;
+      c->plain_variant[1] = it->second.v2;
+      c->stage_launch = it->second.launch;
       return IBM_OK;
     }
+  }
+  int forms[2] = {c->stage_launch, -1}, nforms = 1;
+  if (!c->launch_pinned) {
+    forms[0] = 2;
+    forms[1] = 0;
+    nforms = 2;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   const bool fuse = fused_cfl(c);
   cudaStream_t s = c->stream;
-  auto pair = [&](int stage, int v) {
+  auto pair = [&](int stage, int v, int form) {
+    const CUtensorMap *tm = c->have_tmap && c->use_tma ? &c->tmap[stage - 1] : nullptr;
+    if (form > 0) {
+      launch_stage_f32_one(c->k, stage, c->M, stage == 1 ? c->M : c->F1, stage == 1 ? c->F1 : c->F2, c->A, c->tag,
+                           c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, v, tm, form == 2, s);
+      return;
+    }
     cudaEventRecord(c->ev_fork, s);
     cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
     launch_stage_f32(c->k, stage, c->M, stage == 1 ? c->M : c->F1, stage == 1 ? c->F1 : c->F2, c->A, c->tag, c->sid,
-                     c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, s, c->sb, v, true,
-                     c->have_tmap && c->use_tma ? &c->tmap[stage - 1] : nullptr);
+                     c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, s, c->sb, v, true, tm);
     cudaEventRecord(c->ev_join, c->sb);
     cudaStreamWaitEvent(s, c->ev_join, 0);
   };
   constexpr int ROUNDS = 3, REPS = 5;
-  float best[2][PLAIN_VARIANTS];
-  for (int st = 0; st < 2; st++)
-    for (int v = 0; v < PLAIN_VARIANTS; v++) best[st][v] = 1e30f;
-  pair(1, 0);  // stage-1 array for the stage-2 timings
-  long long nl = 0;
+  float best[2][2][PLAIN_VARIANTS];  // form, stage, variant
+  for (int f = 0; f < 2; f++)
+    for (int st = 0; st < 2; st++)
+      for (int v = 0; v < PLAIN_VARIANTS; v++) best[f][st][v] = 1e30f;
+  pair(1, 0, forms[0]);  // stage-1 array for the stage-2 timings
+  long long nl = 1 + (c->body_cap > 0 && forms[0] == 0);
   cudaError_t e = cudaSuccess;
   for (int round = 0; round < ROUNDS && e == cudaSuccess; round++)
-    for (int st = 0; st < 2 && e == cudaSuccess; st++)
-      for (int v = 0; v < PLAIN_VARIANTS && e == cudaSuccess; v++) {
-        pair(st + 1, v);  // warm-up
-        cudaEventRecord(e0, s);
-        for (int rep = 0; rep < REPS; rep++) pair(st + 1, v);
-        cudaEventRecord(e1, s);
-        nl += (REPS + 1) * (1 + (c->body_cap > 0));
-        float ms = 0.f;
-        e = cudaEventSynchronize(e1);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess && ms < best[st][v]) best[st][v] = ms;
-      }
+    for (int f = 0; f < nforms && e == cudaSuccess; f++)
+      for (int st = 0; st < 2 && e == cudaSuccess; st++)
+        for (int v = 0; v < PLAIN_VARIANTS && e == cudaSuccess; v++) {
+          pair(st + 1, v, forms[f]);  // warm-up
+          cudaEventRecord(e0, s);
+          for (int rep = 0; rep < REPS; rep++) pair(st + 1, v, forms[f]);
+          cudaEventRecord(e1, s);
+          nl += (REPS + 1) * (1 + (c->body_cap > 0 && forms[f] == 0));
+          float ms = 0.f;
+          e = cudaEventSynchronize(e1);
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e == cudaSuccess && ms < best[f][st][v]) best[f][st][v] = ms;
+        }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return fail(IBM_ECUDA, "autotuning failed: %s", cudaGetErrorString(e));
-  for (int st = 0; st < 2; st++) {
-    int b = 0;
-    for (int v = 1; v < PLAIN_VARIANTS; v++)
-      if (best[st][v] < best[st][b]) b = v;
-    c->plain_variant[st] = b;
+  // per form the best budget per stage group; the form with the shorter step (stage 3 runs stage 2's choice)
+  int pick[2][2];
+  float step_ms[2];
+  for (int f = 0; f < nforms; f++) {
+    for (int st = 0; st < 2; st++) {
+      int b = 0;
+      for (int v = 1; v < PLAIN_VARIANTS; v++)
+        if (best[f][st][v] < best[f][st][b]) b = v;
+      pick[f][st] = b;
+    }
+    step_ms[f] = best[f][0][pick[f][0]] + 2.f * best[f][1][pick[f][1]];
   }
-  c->launches += nl + 1 + (c->body_cap > 0);
+  const int fb = nforms == 2 && step_ms[1] < step_ms[0] ? 1 : 0;
+  c->stage_launch = forms[fb];
+  c->plain_variant[0] = pick[fb][0];
+  c->plain_variant[1] = pick[fb][1];
+  c->launches += nl;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tuned[key] = std::make_pair(c->plain_variant[0], c->plain_variant[1]);
+  g_tuned[key] = Tuned{c->plain_variant[0], c->plain_variant[1], c->stage_launch};
   return IBM_OK;
 }
 
@@ -794,6 +831,20 @@ extern "C" ibm_status ibm_use_persistent(ibm_case *c, int enable) {
     c->graph = nullptr;
   }
   c->use_persist = enable != 0;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_stage_launches(ibm_case *c, int mode) {
+  if (!c) return fail(IBM_EINVAL, "case is NULL");
+  if (mode < 0 || mode > 2) return fail(IBM_EINVAL, "mode must be 0, 1 or 2");
+  if (c->graph) {  // the captured step holds the old choice
+    CU(cudaStreamSynchronize(c->stream));
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if ((mode > 0) != (c->stage_launch > 0)) c->plain_variant[0] = c->plain_variant[1] = -1;  // other kernels: retune
+  c->stage_launch = mode;
+  c->launch_pinned = true;
   return IBM_OK;
 }
 
@@ -945,6 +996,12 @@ extern "C" ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t byt
         return fail(IBM_EINVAL, "IBM_TUNING: host int32[2] destination");
       const int32_t v[2] = {c->plain_variant[0], c->plain_variant[1]};
       std::memcpy(dst, v, sizeof v);
+      break;
+    }
+    case IBM_STAGE_LAUNCH: {
+      if (bytes < sizeof(int32_t) || dst_on_device) return fail(IBM_EINVAL, "IBM_STAGE_LAUNCH: host int32 destination");
+      const int32_t v = c->precision == IBM_PREC_FP32_BULK && !c->k.dual ? c->stage_launch : -1;
+      std::memcpy(dst, &v, sizeof v);
       break;
     }
     default:

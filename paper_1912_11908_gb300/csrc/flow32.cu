@@ -133,6 +133,31 @@ __global__ void __launch_bounds__(256, MINB) k_stage_f32(Consts k, PertConsts c,
                                        (int)blockIdx.x, sm, DualPtrs{}, use_tma ? &tmap : nullptr);
 }
 
+// All tiles of a stage in one launch: blocks [0, nb) are body-tile slots
+// (dispatched first: they carry the node rebuilds, the longest chains), the
+// rest one block per tile (tiles in the body list return at once).  With
+// programmatic dependent launch the next stage's launch may begin once every
+// block of this one has started; its blocks then wait at the top for this
+// grid to complete and its stores to become visible, so the next stage's
+// blocks are resident when the tail of this one ends.
+template <int STAGE, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_stage_f32_one(Consts k, PertConsts c, float *Mn, const float *__restrict__ In, float *Out, double *D,
+                    const uint8_t *__restrict__ tag, const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
+                    const uint8_t *__restrict__ tile_body, const int *__restrict__ body_tiles, int nb, DevState *ds,
+                    bool fuse_cfl, unsigned int ncfl, const __grid_constant__ CUtensorMap tmap, int use_tma) {
+  __shared__ TileSmem sm;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int b = (int)blockIdx.x;
+  if (b < nb)
+    stage_tile<STAGE, true, false, true>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, fuse_cfl,
+                                         ncfl, b, sm, DualPtrs{}, use_tma ? &tmap : nullptr);
+  else
+    stage_tile<STAGE, false, false, true>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds, fuse_cfl,
+                                          ncfl, b - nb, sm, DualPtrs{}, use_tma ? &tmap : nullptr);
+}
+
 int stage_tiles(const Consts &k) { return ((k.nx + TX - 1) / TX) * ((k.ny + TY - 1) / TY); }
 
 // does the tile's loaded range [lo, hi] (before domain mapping) along one axis
@@ -241,6 +266,37 @@ void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, fl
   else IBM_STAGE_PAIR(3);
 #undef IBM_STAGE_PAIR
 #undef IBM_ARGS
+}
+
+cudaError_t launch_stage_f32_one(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
+                                 const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
+                                 const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, int plain_variant,
+                                 const CUtensorMap *tmap, bool pdl, cudaStream_t s) {
+  const PertConsts c = pert_consts(k);
+  const int nt = stage_tiles(k);
+  const int nb = body_cap > 0 ? body_cap : 0;
+  const unsigned int ncfl = (unsigned int)(nt + nb);
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof tm);
+  if (tmap) tm = *tmap;
+  const int ut = tmap ? 1 : 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned int)(nt + nb));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+#define IBM_ONE(S, MB)                                                                                        \
+  cudaLaunchKernelEx(&cfg, k_stage_f32_one<S, MB>, k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, nb, \
+                     ds, fuse_cfl, ncfl, tm, ut)
+#define IBM_ONE_V(S) (plain_variant == 1 ? IBM_ONE(S, 5) : plain_variant == 2 ? IBM_ONE(S, 4) : IBM_ONE(S, 6))
+  cudaError_t e = stage == 1 ? IBM_ONE_V(1) : stage == 2 ? IBM_ONE_V(2) : IBM_ONE_V(3);
+#undef IBM_ONE_V
+#undef IBM_ONE
+  return e;
 }
 
 // Tensor maps of the three FP32 stage inputs (mirror of U^n, U^(1), U^(2)) for

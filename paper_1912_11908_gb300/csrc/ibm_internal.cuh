@@ -273,6 +273,13 @@ void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, fl
                       const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                       const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
                       cudaStream_t sb, int plain_variant, bool with_body, const CUtensorMap *tmap);
+// The same stage as one launch on stream s: body-tile slots first, then one
+// block per tile (no second stream); pdl: launch with programmatic dependent
+// launch, so that the launch overlaps the tail of the preceding stage kernel.
+cudaError_t launch_stage_f32_one(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
+                                 const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
+                                 const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, int plain_variant,
+                                 const CUtensorMap *tmap, bool pdl, cudaStream_t s);
 // Tensor maps of the FP32 stage inputs arrays[0..2] (pitch x rows x 4 planes)
 // for the TMA staging of interior tiles (tmap above); false if the driver
 // offers no encoder or the grid is too small for a box.

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libibm_gb300.so")
 
 IBM_OK, IBM_EINVAL, IBM_ENOMEM, IBM_ECAPACITY, IBM_ESTENCIL, IBM_ECUDA, IBM_ESTATE = range(7)
-IBM_STATE_FP64, IBM_TAGS, IBM_LIST_COUNTS, IBM_STENCILS, IBM_TIME, IBM_STEPS, IBM_TUNING = range(7)
+IBM_STATE_FP64, IBM_TAGS, IBM_LIST_COUNTS, IBM_STENCILS, IBM_TIME, IBM_STEPS, IBM_TUNING, IBM_STAGE_LAUNCH = range(8)
 STATUS_NAMES = {0: "IBM_OK", 1: "IBM_EINVAL", 2: "IBM_ENOMEM", 3: "IBM_ECAPACITY", 4: "IBM_ESTENCIL",
                 5: "IBM_ECUDA", 6: "IBM_ESTATE"}
 
@@ -61,7 +61,7 @@ EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_
            "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs", "ibm_tag_nodes_noalloc",
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
            "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats", "ibm_autotune", "ibm_use_tma",
-           "ibm_use_persistent", "ibm_persistent_grid"]
+           "ibm_use_persistent", "ibm_persistent_grid", "ibm_stage_launches"]
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 SERVE_BATCHED, SERVE_AUTOTUNE = 1, 2
 SERVER_STATS = ["group_graphs", "group_steps", "group_kernels", "autotune_runs", "capture_us"]
@@ -107,6 +107,8 @@ def load():
     L.ibm_use_persistent.restype = ip
     L.ibm_persistent_grid.argtypes = [vp, ip]
     L.ibm_persistent_grid.restype = ip
+    L.ibm_stage_launches.argtypes = [vp, ip]
+    L.ibm_stage_launches.restype = ip
     L.ibm_tag_nodes_noalloc.argtypes = [ctypes.POINTER(ibm_grid), vp, ip, vp, vp, ctypes.c_int32, vp, vp]
     L.ibm_tag_nodes_noalloc.restype = ip
     L.ibm_server_create.argtypes = [sz, ip, ip, ctypes.POINTER(vp)]
@@ -278,6 +280,12 @@ class Case:
     def autotune(self, enable):
         _check(lib().ibm_autotune(self.h, int(enable)))
 
+    def stage_launch(self):
+        """Launch form of the FP32-bulk explicit stages (0..2; -1 for FP64 or dual time)."""
+        out = np.zeros(1, np.int32)
+        _check(lib().ibm_get_state(self.h, IBM_STAGE_LAUNCH, out.ctypes.data_as(ctypes.c_void_p), 4, 0))
+        return int(out[0])
+
     def tuning(self):
         """Register-budget variants of the plain stage kernel: (stage 1, stages 2-3)."""
         out = np.zeros(2, np.int32)
@@ -292,6 +300,9 @@ class Case:
 
     def persistent_grid(self, blocks):
         _check(lib().ibm_persistent_grid(self.h, int(blocks)))
+
+    def stage_launches(self, mode):
+        _check(lib().ibm_stage_launches(self.h, int(mode)))
 
     def use_graphs(self, enable):
         _check(lib().ibm_use_graphs(self.h, 1 if enable else 0))

@@ -113,10 +113,12 @@ def test_autotuned_register_budgets_agree(ibm):
     b.step(40)
     v = b.tuning()
     assert all(0 <= x <= 2 for x in v)
+    assert b.stage_launch() in (0, 2)
     c = ibm.Case(spec)
     c.use_persistent(False)
     c.step(1)
     assert c.tuning() == v
+    assert c.stage_launch() == b.stage_launch()
     fa, fb = a.forces(), b.forces()
     np.testing.assert_allclose(fb, fa, rtol=1e-5, atol=1e-5 * np.abs(fa).max())
     with pytest.raises(ibm.IbmError):
@@ -224,3 +226,29 @@ def test_persistent_step_without_graphs(ibm):
     b.step(20)
     np.testing.assert_array_equal(a.state(), b.state())
     np.testing.assert_array_equal(a.time(), b.time())
+
+
+@pytest.mark.parametrize("name,spec_fn", PERSIST_CASES, ids=[c[0] for c in PERSIST_CASES])
+def test_stage_launch_forms(ibm, name, spec_fn):
+    """One kernel per stage chained by programmatic dependent launch (blocks of the next stage resident and
+    waiting while the previous stage finishes) gives bit for bit what the same kernel gives launched plainly;
+    the two-stream plain / body kernels (compiled separately) agree to FP32 rounding."""
+    spec = spec_fn()
+    runs = {}
+    for mode in (0, 1, 2):
+        c = ibm.Case(spec)
+        c.autotune(False)
+        c.stage_launches(mode)
+        c.step(30)
+        runs[mode] = (c.state(), c.forces(), c.time(), c.tags())
+    np.testing.assert_array_equal(runs[2][0], runs[1][0])
+    np.testing.assert_array_equal(runs[2][1], runs[1][1])
+    np.testing.assert_array_equal(runs[2][2], runs[1][2])
+    assert _rel_state_diff(runs[2][0], runs[0][0], runs[0][3]) <= 1e-4
+    np.testing.assert_allclose(runs[2][1], runs[0][1], rtol=1e-5, atol=1e-5 * np.abs(runs[0][1]).max())
+
+
+def test_stage_launch_mode_checked(ibm):
+    c = ibm.Case(W.wedge_m2_re1e4(64, 32, precision=W.PREC_FP32_BULK))
+    with pytest.raises(ibm.IbmError):
+        c.stage_launches(3)
