@@ -501,39 +501,35 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     }
     if (threadIdx.x == 0 && s_nrb > RB_MAX) atomicOr(&ds->err, ERR_CAPACITY);
   }
-  // WENO5 per cell: x windows for local columns 2..TX+3 of interior rows,
-  // y windows for local rows 2..TY+3 of interior columns
-  constexpr int NXW = (TX + 2) * TY, NYW = TX * (TY + 2);
-  for (int m = threadIdx.x; m < NXW + NYW; m += 256) {
-    const bool xdir = m < NXW;
-    const int mm = xdir ? m : m - NXW;
-    int ccol, crow;
-    if (xdir) {
-      ccol = 2 + mm % (TX + 2);
-      crow = NG + mm / (TX + 2);
-    } else {
-      ccol = NG + mm % TX;
-      crow = 2 + mm / TX;
-    }
-    for (int v = 0; v < 4; v++) {
-      float f0, f1, f2, f3, f4;
-      if (xdir) {
-        const float *s = &sq[v][crow][ccol - 2];
-        f0 = s[0]; f1 = s[1]; f2 = s[2]; f3 = s[3]; f4 = s[4];
-      } else {
-        f0 = sq[v][crow - 2][ccol]; f1 = sq[v][crow - 1][ccol]; f2 = sq[v][crow][ccol];
-        f3 = sq[v][crow + 1][ccol]; f4 = sq[v][crow + 2][ccol];
-      }
+  // WENO5 (Sec. 3) along lines: an item is one variable of one interior tile row (x) or column (y) and one of
+  // its two halves -- nine consecutive window centres, local 2..10 or 11..19, the cells whose faces the tile
+  // needs.  The smoothness indicators are written with the second differences d2 and first differences g of the
+  // line, beta_0 = 13/12 d2(c-1)^2 + 1/4 (d2(c-1) + 2 g(c-1))^2, beta_1 = 13/12 d2(c)^2 + 1/4 (g(c-1) + g(c))^2,
+  // beta_2 = 13/12 d2(c+1)^2 + 1/4 (d2(c+1) - 2 g(c))^2 with g(j) = f(j+1) - f(j), so that each centre loads one
+  // value and forms one new squared second difference, shared by three windows.  The three candidate
+  // polynomials and the nonlinear weights of a window give the left state at its right face and, mirrored, the
+  // right state at its left face.
+  static_assert(TX == 16 && TY == 16, "one item per thread: 2 directions x 16 lines x 4 variables x 2 halves");
+  {
+    const int u = threadIdx.x & 127;
+    const bool xdir = threadIdx.x < 128;
+    const int half = u & 1, line = (u >> 1) & 15, v = u >> 5;
+    const float *lp = xdir ? &sq[v][NG + line][0] : &sq[v][0][NG + line];
+    const int ls = xdir ? 1 : HX;  // stride along the line
+    const int p0 = 2 + 9 * half;
+    float f0 = lp[(p0 - 2) * ls], f1 = lp[(p0 - 1) * ls], f2 = lp[p0 * ls], f3 = lp[(p0 + 1) * ls];
+    float d2m = f0 - 2.f * f1 + f2, d2c = f1 - 2.f * f2 + f3;  // second differences centred at c - 1 and c
+    float am = (13.f / 12.f) * d2m * d2m, ac = (13.f / 12.f) * d2c * d2c;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+      const int pc = p0 + i;
+      const float f4 = lp[(pc + 2) * ls];
+      const float d2p = f2 - 2.f * f3 + f4, ap = (13.f / 12.f) * d2p * d2p;
+      const float gm = f2 - f1, g0 = f3 - f2;
+      const float bb0 = d2m + 2.f * gm, bb1 = gm + g0, bb2 = d2p - 2.f * g0;
       const float eps = 1e-6f;
-      float aa = f0 - 2.f * f1 + f2, bb = f0 - 4.f * f1 + 3.f * f2;
-      const float b0 = (13.f / 12.f) * aa * aa + 0.25f * bb * bb;
-      aa = f1 - 2.f * f2 + f3;
-      bb = f1 - f3;
-      const float b1 = (13.f / 12.f) * aa * aa + 0.25f * bb * bb;
-      aa = f2 - 2.f * f3 + f4;
-      bb = 3.f * f2 - 4.f * f3 + f4;
-      const float b2 = (13.f / 12.f) * aa * aa + 0.25f * bb * bb;
-      const float e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+      const float e0 = eps + (am + 0.25f * bb0 * bb0), e1 = eps + (ac + 0.25f * bb1 * bb1),
+                  e2 = eps + (ap + 0.25f * bb2 * bb2);
       const float e01 = e0 * e1, e12 = e1 * e2, e02 = e0 * e2;
       const float s01 = e01 * e01, s12 = e12 * e12, s02 = e02 * e02;
       // left state at the cell's right face: weights (0.1, 0.6, 0.3) / e_k^2
@@ -549,14 +545,20 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
       const float ra0 = 0.1f * s01, ra1 = 0.6f * s02, ra2 = 0.3f * s12;
       const float qR = __fdividef(ra0 * r0 + ra1 * r1 + ra2 * r2, 6.f * (ra0 + ra1 + ra2));
       if (xdir) {
-        const int row = crow - NG;
-        if (ccol - 2 <= TX) fLx[v][row][ccol - 2] = qL;  // face between ccol and ccol+1
-        if (ccol >= 3) fRx[v][row][ccol - 3] = qR;        // face between ccol-1 and ccol
+        if (pc - 2 <= TX) fLx[v][line][pc - 2] = qL;  // face between pc and pc+1
+        if (pc >= 3) fRx[v][line][pc - 3] = qR;        // face between pc-1 and pc
       } else {
-        const int col = ccol - NG;
-        if (crow - 2 <= TY) fLy[v][crow - 2][col] = qL;
-        if (crow >= 3) fRy[v][crow - 3][col] = qR;
+        if (pc - 2 <= TY) fLy[v][pc - 2][line] = qL;
+        if (pc >= 3) fRy[v][pc - 3][line] = qR;
       }
+      f0 = f1;
+      f1 = f2;
+      f2 = f3;
+      f3 = f4;
+      d2m = d2c;
+      d2c = d2p;
+      am = ac;
+      ac = ap;
     }
   }
   __syncthreads();

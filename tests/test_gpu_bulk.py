@@ -194,10 +194,11 @@ def test_persistent_step_is_race_free(ibm, name, spec_fn, tma):
 
 @pytest.mark.parametrize("name,spec_fn", PERSIST_CASES, ids=[c[0] for c in PERSIST_CASES])
 def test_persistent_step_matches_per_stage_launches(ibm, name, spec_fn):
-    """The persistent step and the per-stage plain / body launches run the same per-tile code; the kernels are
-    compiled separately (different register budgets), so mul / add contraction may differ: after one step the
-    states agree to ~1 ulp of the FP32 increment, after 30 steps (shocks amplify) to 1e-4 of the deviation
-    scale, forces to 1e-5, time and the next dt to 1e-6."""
+    """The persistent step and the per-stage launches run the same per-tile code; the kernels are compiled
+    separately (different register budgets), so mul / add contraction may differ.  At a forming shock the WENO5
+    weights turn a 1-ulp difference of a smoothness indicator into a few ulp of the face state, so after one
+    step the states agree to 1e-5 of the deviation scale (FP32 rounding of the increments), after 30 steps to
+    1e-4, forces to 1e-5, time and the next dt to 1e-6."""
     spec = spec_fn()
     a = ibm.Case(spec)
     a.use_persistent(False)
@@ -207,7 +208,7 @@ def test_persistent_step_matches_per_stage_launches(ibm, name, spec_fn):
     for n in (1, 29):
         a.step(n)
         b.step(n)
-        tol = 1e-6 if n == 1 else 1e-4
+        tol = 1e-5 if n == 1 else 1e-4
         assert _rel_state_diff(b.state(), a.state(), a.tags()) <= tol
     fa, fb = a.forces(), b.forces()
     np.testing.assert_allclose(fb, fa, rtol=1e-5, atol=1e-5 * np.abs(fa).max())
