@@ -501,7 +501,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     }
     if (threadIdx.x == 0 && s_nrb > RB_MAX) atomicOr(&ds->err, ERR_CAPACITY);
   }
-  // WENO5 (Sec. 3) along lines: an item is one variable of one interior tile row (x) or column (y) and one of
+  // WENO5 (Sec. 2) along lines: an item is one variable of one interior tile row (x) or column (y) and one of
   // its two halves -- nine consecutive window centres, local 2..10 or 11..19, the cells whose faces the tile
   // needs.  The smoothness indicators are written with the second differences d2 and first differences g of the
   // line, beta_0 = 13/12 d2(c-1)^2 + 1/4 (d2(c-1) + 2 g(c-1))^2, beta_1 = 13/12 d2(c)^2 + 1/4 (g(c-1) + g(c))^2,
