@@ -15,7 +15,8 @@ namespace ibm {
 // from the energy row), so the energy rows of the Weiss-Smith matrices carry
 // H - H_inf instead of H and never cancel against H_inf; R' = -L is the FP32
 // residual, BDF' is formed from the FP64 iterates and time levels, the 4x4
-// system is solved exactly in FP64 through its structure (solve_precond),
+// system is solved in FP64 through its structure (solve_precond; the
+// reciprocal of its FP32 pseudo-time step coefficient in FP32),
 // Q' = (p', u, v, T') is updated and combined with the sub-iteration's start
 // as SSP-RK3 stage, and the new iterate is stored in FP64 with its FP32
 // mirror.
@@ -27,10 +28,12 @@ struct DualPtrs {
   double *Q0;            // (p', u, v, T') of the sub-iteration's start: written by stage 1, read by 2 and 3
 };
 
-// FP64 perturbation conserved -> (p', u, v, T')
+// FP64 perturbation conserved -> (p', u, v, T'); ir receives 1 / rho.  Reciprocals here are the
+// round-to-nearest FP64 reciprocal (the iterate's conversions stay exact to FP64 rounding).
 __device__ __forceinline__ void pert_prim64(const Consts &k, double dr, double dmx, double dmy, double W,
-                                            double q[4]) {
-  const double r = 1.0 + dr, ir = 1.0 / r;
+                                            double q[4], double &ir) {
+  const double r = 1.0 + dr;
+  ir = __drcp_rn(r);
   const double u = (k.uinf[0] + dmx) * ir, v = (k.uinf[1] + dmy) * ir;
   const double du = (dmx - dr * k.uinf[0]) * ir, dv = (dmy - dr * k.uinf[1]) * ir;
   const double dq = du * (u + k.uinf[0]) + dv * (v + k.uinf[1]);
@@ -45,7 +48,7 @@ __device__ __forceinline__ void pert_prim64(const Consts &k, double dr, double d
 // (p', u, v, T') -> FP64 perturbation conserved
 __device__ __forceinline__ void prim_pert64(const Consts &k, const double q[4], double w[4]) {
   const double pp = q[0], u = q[1], v = q[2], Tp = q[3];
-  const double dr = (pp - k.R * Tp) * k.iR / (1.0 + Tp);
+  const double dr = (pp - k.R * Tp) * k.iR * __drcp_rn(1.0 + Tp);
   const double dq = (u - k.uinf[0]) * (u + k.uinf[0]) + (v - k.uinf[1]) * (v + k.uinf[1]);
   const double ke = 0.5 * (dr * (u * u + v * v) + dq);
   w[0] = dr;
@@ -61,14 +64,20 @@ __device__ __forceinline__ void prim_pert64(const Consts &k, const double q[4], 
 // (after subtracting u, v times the first row) and the first and energy rows
 // leave a 2x2 system in dp, dT:
 //   tau dp + rho_T dT = S0/s,   -dp + rho cp dT = (S3 - dH S0)/s - rho (u du + v dv).
-__device__ __forceinline__ void solve_precond(double s, double tau, double r, double u, double v, double rT,
-                                              double cpv, double dH, const double S[4], double dQ[4]) {
-  const double is = 1.0 / s, irs = is / r;
+// is = 1/s, ir = 1/rho.  1/s scales the whole update (a pseudo-time step
+// size: it sets the path in pseudo time, not the fixed point, which the FP64
+// right-hand side S fixes) and is taken in FP32 like s itself.  The pivot
+// tau rho cp + rho_T is inverted in FP64: dp = rho cp dT - X is a small
+// difference of two terms of size X, so a relative error in 1/pivot would
+// reach dp multiplied by X / dp.
+__device__ __forceinline__ void solve_precond(double is, double tau, double r, double ir, double u, double v,
+                                              double rT, double cpv, double dH, const double S[4], double dQ[4]) {
+  const double irs = is * ir;
   const double du = (S[1] - u * S[0]) * irs;
   const double dv = (S[2] - v * S[0]) * irs;
   const double X = (S[3] - dH * S[0]) * is - r * (u * du + v * dv);
   const double Y = S[0] * is;
-  const double dT = (Y + tau * X) / (tau * r * cpv + rT);
+  const double dT = (Y + tau * X) * __drcp_rn(tau * r * cpv + rT);
   dQ[0] = r * cpv * dT - X;
   dQ[1] = du;
   dQ[2] = dv;
@@ -81,9 +90,9 @@ __device__ __forceinline__ void dual_update_cell(const Consts &k, const PertCons
                                                  const float L[4], const DualPtrs &dp,
                                                  float *Out32, bool bdf2) {
   const double idt = k.idt_phys;
-  double W[4], S[4], Qk[4];
+  double W[4], S[4], Qk[4], ir;
   for (int v = 0; v < 4; v++) W[v] = dp.In64[id + v * P];
-  pert_prim64(k, W[0], W[1], W[2], W[3], Qk);
+  pert_prim64(k, W[0], W[1], W[2], W[3], Qk, ir);
   for (int v = 0; v < 4; v++) {
     const long long o = id + v * P;
     const double tdt = bdf2 ? (3.0 * W[v] - 4.0 * dp.Wn[o] + dp.Wm[o]) * (0.5 * idt) : (W[v] - dp.Wn[o]) * idt;
@@ -110,7 +119,7 @@ __device__ __forceinline__ void dual_update_cell(const Consts &k, const PertCons
   const float tau = (thG * idtau + af * thJ) / sf;
   const double dH = k.cp * Qk[3] + 0.5 * ((u - k.uinf[0]) * (u + k.uinf[0]) + (v - k.uinf[1]) * (v + k.uinf[1]));
   double dQ[4];
-  solve_precond((double)sf, (double)tau, r, u, v, -(double)(rf * iTf), k.cp, dH, S, dQ);
+  solve_precond((double)(1.f / sf), (double)tau, r, ir, u, v, -(double)(rf * iTf), k.cp, dH, S, dQ);
   double Q0[4], Qn[4], Wo[4];
   if (STAGE == 1) {  // the stage starts from the sub-iteration's start: keep its primitives for stages 2 and 3
     for (int q = 0; q < 4; q++) dp.Q0[id + q * P] = Qk[q];
