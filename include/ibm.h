@@ -142,8 +142,8 @@ enum {
   IBM_TUNING = 6,       /* int32_t[2] (host only): register-budget variants of the FP32-bulk stage kernel
                            picked by the autotuner for stage 1 and for stages 2-3 (0..2; -1 before the first
                            step, or FP64) */
-  IBM_STAGE_LAUNCH = 7  /* int32_t (host only): launch form of the FP32-bulk explicit stages (0..2, see
-                           ibm_stage_launches; the autotuner's pick unless set; -1 for FP64 or dual time) */
+  IBM_STAGE_LAUNCH = 7  /* int32_t (host only): launch form of the FP32-bulk stages (0..2, see
+                           ibm_stage_launches; the autotuner's pick unless set; -1 for FP64) */
 };
 
 /* Create a case, initialised to the uniform free stream at t = 0 (no
@@ -217,15 +217,17 @@ ibm_status ibm_autotune(ibm_case *c, int enable);
  * uses per-thread loads for every tile. */
 ibm_status ibm_use_tma(ibm_case *c, int enable);
 
-/* FP32-bulk explicit stages (Sec. 2): how each stage is launched.
+/* FP32-bulk stages (Sec. 2; explicit stages and dual-time pseudo stages): how
+ * each stage is launched.
  *   0: a plain-tile kernel and a body-tile kernel on two streams;
  *   1: one kernel holding both, body-tile blocks first;
  *   2: as 1, each stage launched with programmatic dependent launch, so that
  *      its blocks are resident, waiting for the previous stage, while the
  *      previous stage's last blocks finish.
  * Unless this is called, the autotuner times forms 0 and 2 with their
- * register budgets on the case's first step and keeps the faster (IBM_STAGE_LAUNCH
- * reports it; without autotuning the form is 2).  Modes 1 and 2 run the same
+ * register budgets on an explicit case's first step and keeps the faster
+ * (IBM_STAGE_LAUNCH reports it; without autotuning, and for dual time, the
+ * form is 2).  Modes 1 and 2 run the same
  * kernel and give bit-identical results; mode 0's kernels are compiled
  * separately (results agree to FP32 rounding).  IBM_EINVAL for another mode. */
 ibm_status ibm_stage_launches(ibm_case *c, int mode);

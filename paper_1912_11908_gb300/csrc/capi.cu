@@ -522,14 +522,21 @@ static int enqueue_step(ibm_case *c) {
       for (int it = 0; it < c->k.subiters; it++)
         for (int st = 1; st <= 3; st++) {
           prof_mark(c, 0, true);
-          cudaEventRecord(c->ev_fork, s);
-          cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
-          launch_dual_f32(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->Wn, c->Wm, c->Q0,
-                          c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, s, c->sb);
-          cudaEventRecord(c->ev_join, c->sb);
-          cudaStreamWaitEvent(s, c->ev_join, 0);
+          if (c->stage_launch > 0) {  // one launch per pseudo stage (form 2: chained by programmatic launch)
+            launch_dual_f32_one(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->Wn, c->Wm,
+                                c->Q0, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds,
+                                c->stage_launch == 2, s);
+            nl += 1;
+          } else {
+            cudaEventRecord(c->ev_fork, s);
+            cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
+            launch_dual_f32(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->Wn, c->Wm,
+                            c->Q0, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, s, c->sb);
+            cudaEventRecord(c->ev_join, c->sb);
+            cudaStreamWaitEvent(s, c->ev_join, 0);
+            nl += 1 + (c->body_cap > 0);
+          }
           prof_mark(c, 0, false);
-          nl += 1 + (c->body_cap > 0);
         }
       launch_dual_end(c->k, c->ds, s);
       return nl + 1;
@@ -1004,7 +1011,7 @@ extern "C" ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t byt
     }
     case IBM_STAGE_LAUNCH: {
       if (bytes < sizeof(int32_t) || dst_on_device) return fail(IBM_EINVAL, "IBM_STAGE_LAUNCH: host int32 destination");
-      const int32_t v = c->precision == IBM_PREC_FP32_BULK && !c->k.dual ? c->stage_launch : -1;
+      const int32_t v = c->precision == IBM_PREC_FP32_BULK ? c->stage_launch : -1;
       std::memcpy(dst, &v, sizeof v);
       break;
     }

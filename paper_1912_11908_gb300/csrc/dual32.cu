@@ -21,6 +21,60 @@ __global__ void __launch_bounds__(256) k_dual_f32(Consts k, PertConsts c, const 
                                 (int)blockIdx.x, sm, dp);
 }
 
+// The same pseudo stage as one launch: body-tile slots [0, nb) first, then one
+// block per tile; with programmatic dependent launch its blocks are resident
+// while the previous pseudo stage's last blocks finish (they wait at the top
+// for it to complete).
+template <int STAGE>
+__global__ void __launch_bounds__(256) k_dual_f32_one(Consts k, PertConsts c, const float *__restrict__ In,
+                                                      float *Out32, double *D, const uint8_t *__restrict__ tag,
+                                                      const int *__restrict__ sid,
+                                                      const RStencil32 *__restrict__ rs,
+                                                      const uint8_t *__restrict__ tile_body,
+                                                      const int *__restrict__ body_tiles, int nb, DevState *ds,
+                                                      unsigned int ncfl, DualPtrs dp) {
+  __shared__ TileSmem sm;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int b = (int)blockIdx.x;
+  if (b < nb)
+    stage_tile<STAGE, true, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body, body_tiles, ds, false, ncfl,
+                                  b, sm, dp);
+  else
+    stage_tile<STAGE, false, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body, body_tiles, ds, false,
+                                   ncfl, b - nb, sm, dp);
+}
+
+cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, float *Out32, double *D,
+                                const double *In64, double *Out64, const double *Wn, const double *Wm, double *Q0,
+                                const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
+                                const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s) {
+  const PertConsts c = pert_consts(k);
+  const int nt = stage_tiles(k);
+  const int nb = body_cap > 0 ? body_cap : 0;
+  const unsigned int ncfl = (unsigned int)(nt + nb);
+  DualPtrs dp;
+  dp.In64 = In64;
+  dp.Out64 = Out64;
+  dp.Wn = Wn;
+  dp.Wm = Wm;
+  dp.Q0 = Q0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned int)(nt + nb));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+#define IBM_DUAL_ONE(S) \
+  cudaLaunchKernelEx(&cfg, k_dual_f32_one<S>, k, c, In32, Out32, D, tag, sid, rs, tile_body, body_tiles, nb, ds, ncfl, dp)
+  const cudaError_t e = stage == 1 ? IBM_DUAL_ONE(1) : stage == 2 ? IBM_DUAL_ONE(2) : IBM_DUAL_ONE(3);
+#undef IBM_DUAL_ONE
+  return e;
+}
+
 void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,
                      double *Out64, const double *Wn, const double *Wm, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,

@@ -1,6 +1,7 @@
 // FP32-bulk flow kernels of one case: conversions between the FP64 master and
 // the FP32 mirror, the CFL reduction, compact stencils, body-tile lists and
 // the stage kernels (per-tile code in stage32.cuh).
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -51,21 +52,27 @@ void launch_to_mirror(const Consts &k, const double *D, float *M, cudaStream_t s
 // of U^n; the last block converts the maximum into dt.
 __global__ void __launch_bounds__(256) k_dt_f32(Consts k, PertConsts c, const float *__restrict__ M,
                                                 const uint8_t *__restrict__ tag, DevState *ds) {
-  const int ncell = k.nx * k.ny;
+  // a warp on 32 cells of a row, the block's eight warps on eight rows, striding down the grid; the state is
+  // loaded whatever the tag and the loop unrolled, so that the loads of several rows leave together (few blocks:
+  // each block's maximum and completion are atomics on one address)
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
   const long long P = k.plane;
   const float idx = c.idx, idy = c.idy;
   const float vis = (float)((2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy)));
   float lmax = 0.f;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ncell; n += gridDim.x * blockDim.x) {
-    if (tag[n] != FLUID) continue;
-    const long long id = cidx(k, n % k.nx, n / k.nx);
-    float u, v, pp, Tp;
-    const float dr = M[id];
-    pert_prim(c, dr, M[id + P], M[id + 2 * P], M[id + 3 * P], u, v, pp, Tp);
-    const float r = 1.f + dr;
-    const float cs = sqrtf(c.gamma * (c.R + pp) / r);
-    const float lam = (fabsf(u) + cs) * idx + (fabsf(v) + cs) * idy + vis / r;
-    lmax = fmaxf(lmax, lam);
+  if (i < k.nx) {
+#pragma unroll 4
+    for (int j = blockIdx.y * 8 + (threadIdx.x >> 5); j < k.ny; j += gridDim.y * 8) {
+      const long long id = cidx(k, i, j);
+      const float dr = M[id], mx = M[id + P], my = M[id + 2 * P], w = M[id + 3 * P];
+      if (tag[j * k.nx + i] == FLUID) {
+        float u, v, pp, Tp;
+        pert_prim(c, dr, mx, my, w, u, v, pp, Tp);
+        const float r = 1.f + dr;
+        const float cs = sqrtf(c.gamma * (c.R + pp) / r);
+        lmax = fmaxf(lmax, (fabsf(u) + cs) * idx + (fabsf(v) + cs) * idy + vis / r);
+      }
+    }
   }
   for (int off = 16; off > 0; off >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
   __shared__ float wm[8];
@@ -82,9 +89,10 @@ __global__ void __launch_bounds__(256) k_dt_f32(Consts k, PertConsts c, const fl
 void launch_dt_f32(const Consts &k, const float *M, const uint8_t *tag, DevState *ds, cudaStream_t s,
                    int *nlaunch) {
   if (k.dt_fixed > 0.0) return;
-  const int ncell = k.nx * k.ny;
-  const int blocks = min((ncell + 255) / 256, 152 * 4);
-  k_dt_f32<<<blocks, 256, 0, s>>>(k, pert_consts(k), M, tag, ds);
+  // about two blocks per SM
+  const int gx = (k.nx + 31) / 32, rows8 = (k.ny + 7) / 8;
+  const int gy = std::max(1, std::min(rows8, (2 * 152 + gx - 1) / gx));
+  k_dt_f32<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(k, pert_consts(k), M, tag, ds);
   *nlaunch += 1;
 }
 

@@ -318,6 +318,12 @@ void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32
                      double *Out64, const double *Wn, const double *Wm, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
                      DevState *ds, cudaStream_t s, cudaStream_t sb);
+// The same pseudo stage as one launch on stream s (body-tile slots first);
+// pdl: chained to the previous launch by programmatic dependent launch.
+cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, float *Out32, double *D,
+                                const double *In64, double *Out64, const double *Wn, const double *Wm, double *Q0,
+                                const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
+                                const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s);
 // The same two kernels over a group's block table: the plain kernel (stream s) covers tiles
 // without IB / ghost nodes near them; the body kernel (stream sb, may run
 // concurrently) covers the listed body tiles and rebuilds IB and ghost nodes

@@ -281,7 +281,7 @@ class Case:
         _check(lib().ibm_autotune(self.h, int(enable)))
 
     def stage_launch(self):
-        """Launch form of the FP32-bulk explicit stages (0..2; -1 for FP64 or dual time)."""
+        """Launch form of the FP32-bulk stages (0..2; -1 for FP64)."""
         out = np.zeros(1, np.int32)
         _check(lib().ibm_get_state(self.h, IBM_STAGE_LAUNCH, out.ctypes.data_as(ctypes.c_void_p), 4, 0))
         return int(out[0])
