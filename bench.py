@@ -334,8 +334,9 @@ def run_ours(args, rank, world):
                                "Poisson arrivals mean 50 ms" % (args.serve_requests, args.serve_requests - ndual, ndual),
                    "slots": args.serve_slots, "steps_per_chunk": args.serve_chunk,
                    "memory_budget": "80% of free device memory",
-                   "modes": {"batched": "size-class groups, one plain-tile and one body-tile launch per RK stage over "
-                                        "the group's block table, group step in a CUDA graph, autotuned schedule",
+                   "modes": {"batched": "size-class groups, one launch per RK stage over the group's block table "
+                                        "(body-tile entries first, stages chained by programmatic launch), group step "
+                                        "in a CUDA graph, autotuned schedule",
                              "streams": "one stream and one step graph per case"}}
         bm = ibm.SERVE_BATCHED | ibm.SERVE_AUTOTUNE
         for name, mode in (("batched", bm), ("streams", 0)):

@@ -44,6 +44,53 @@ void launch_stage_f32_batch(const StageBatch &b, int stage, int plain_grid, int 
 #undef IBM_STAGE_PAIR
 }
 
+// All entries of a stage in one launch: the body-tile entries of every member
+// first (they carry the node rebuilds), then the plain-tile entries; blocks
+// walk the combined table with a grid stride.  Launched with programmatic
+// dependent launch, its blocks are resident while the previous stage's last
+// blocks finish (they wait at the top for it to complete).
+template <int STAGE>
+__global__ void __launch_bounds__(256, 6) k_stage_f32_batch_one(const __grid_constant__ StageBatch b) {
+  __shared__ TileSmem sm;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int nbody = b.body_start[b.n], total = nbody + b.plain_start[b.n];
+  for (int e = blockIdx.x; e < total; e += gridDim.x) {
+    const bool body = e < nbody;
+    const int *start = body ? b.body_start : b.plain_start;
+    const int ee = body ? e : e - nbody;
+    int q = 0;
+    while (q + 1 < b.n && start[q + 1] <= ee) q++;
+    const StageCase &sc = b.cs[q];
+    const float *In = STAGE == 1 ? sc.M : (STAGE == 2 ? sc.F1 : sc.F2);
+    float *Out = STAGE == 1 ? sc.F1 : (STAGE == 2 ? sc.F2 : nullptr);
+    if (body)
+      stage_tile<STAGE, true>(sc.k, sc.c, sc.M, In, Out, sc.D, sc.tag, sc.sid, sc.rs, sc.tile_body, sc.body_tiles,
+                              sc.ds, sc.fuse_cfl != 0, sc.ncfl, ee - start[q], sm);
+    else
+      stage_tile<STAGE, false>(sc.k, sc.c, sc.M, In, Out, sc.D, sc.tag, sc.sid, sc.rs, sc.tile_body, sc.body_tiles,
+                               sc.ds, sc.fuse_cfl != 0, sc.ncfl, ee - start[q], sm);
+    __syncthreads();  // shared memory is reused by the next entry
+  }
+}
+
+cudaError_t launch_stage_f32_batch_one(const StageBatch &b, int stage, int grid, bool pdl, cudaStream_t s) {
+  const int total = b.body_start[b.n] + b.plain_start[b.n];
+  if (total == 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned int)(grid > 0 && grid < total ? grid : total));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  if (stage == 1) return cudaLaunchKernelEx(&cfg, k_stage_f32_batch_one<1>, b);
+  if (stage == 2) return cudaLaunchKernelEx(&cfg, k_stage_f32_batch_one<2>, b);
+  return cudaLaunchKernelEx(&cfg, k_stage_f32_batch_one<3>, b);
+}
+
 void build_stage_batch(const StageCase *cases, int n, StageBatch *b) {
   b->n = n;
   b->plain_start[0] = b->body_start[0] = 0;

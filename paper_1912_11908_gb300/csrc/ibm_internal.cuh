@@ -366,6 +366,9 @@ void fill_stage_case(const Consts &k, float *M, float *F1, float *F2, double *D,
 // plain_grid / body_grid: blocks of the launch (<= 0 or >= the entries: one
 // block per entry; fewer: persistent blocks striding over the table).
 // with_body = false launches the plain-tile kernel only.
+// The same stage as one launch over the combined table (body-tile entries first); grid 0 = one block per
+// entry; pdl: chained to the previous launch by programmatic dependent launch.
+cudaError_t launch_stage_f32_batch_one(const StageBatch &b, int stage, int grid, bool pdl, cudaStream_t s);
 void launch_stage_f32_batch(const StageBatch &b, int stage, int plain_grid, int body_grid, cudaStream_t s,
                             cudaStream_t sb, bool with_body);
 

@@ -271,13 +271,10 @@ static ibm_status capture_group(ibm_server *s, Group *g) {
       cudaStreamWaitEvent(g->s, a->join, 0);
     }
   }
+  // one launch per stage over the combined table, stages chained by programmatic launch
   for (int st = 1; st <= 3; st++) {
-    cudaEventRecord(g->fork, g->s);
-    cudaStreamWaitEvent(g->sb, g->fork, 0);
-    launch_stage_f32_batch(b, st, g->plain_grid, 0, g->s, g->sb, true);
-    cudaEventRecord(g->join_b, g->sb);
-    cudaStreamWaitEvent(g->s, g->join_b, 0);
-    nk += (b.plain_start[b.n] > 0) + (b.body_start[b.n] > 0);
+    launch_stage_f32_batch_one(b, st, g->plain_grid, true, g->s);
+    nk += (b.plain_start[b.n] + b.body_start[b.n] > 0);
   }
   cudaError_t e = cudaStreamEndCapture(g->s, &graph);
   if (e == cudaSuccess && g->graph) {
@@ -302,11 +299,12 @@ static ibm_status capture_group(ibm_server *s, Group *g) {
   return IBM_OK;
 }
 
-// Autotuner: time the plain-tile kernel of stage 1 over the group's table
-// under each candidate schedule and keep the fastest for this size class and
-// membership size.  Between steps that kernel is free of side effects on the
-// solution: it reads the mirror of U^n and writes only the stage-1 array and
-// the stage times, which the next step's stage 1 rewrites.
+// Autotuner: time stage 1 over the group's combined table under each
+// candidate schedule and keep the fastest for this size class and membership
+// size.  Between steps stage 1 is free of side effects on the solution: it
+// reads the mirror of U^n and writes the stage-1 array, the stage times and
+// U^n on IB / ghost nodes, all of which the next step's stage 1 rewrites with
+// the same values.
 static void autotune(ibm_server *s, Group *g) {
   int mclass = 0;
   while ((2 << mclass) <= (int)g->members.size()) mclass++;
@@ -316,16 +314,16 @@ static void autotune(ibm_server *s, Group *g) {
     g->plain_grid = it->second;
     return;
   }
-  const int entries = g->batch->plain_start[g->batch->n];
+  const int entries = g->batch->plain_start[g->batch->n] + g->batch->body_start[g->batch->n];
   const int cands[3] = {0, 6 * s->nsms, 3 * s->nsms};
   int best = 0;
   float best_ms = 1e30f;
   for (int ci = 0; ci < 3; ci++) {
     const int grid = cands[ci];
     if (ci > 0 && grid >= entries) continue;
-    launch_stage_f32_batch(*g->batch, 1, grid, 0, g->s, g->sb, false);  // warm-up
+    launch_stage_f32_batch_one(*g->batch, 1, grid, true, g->s);  // warm-up
     cudaEventRecord(g->t0, g->s);
-    for (int rep = 0; rep < 3; rep++) launch_stage_f32_batch(*g->batch, 1, grid, 0, g->s, g->sb, false);
+    for (int rep = 0; rep < 3; rep++) launch_stage_f32_batch_one(*g->batch, 1, grid, true, g->s);
     cudaEventRecord(g->t1, g->s);
     cudaEventSynchronize(g->t1);
     float ms = 0.f;
