@@ -6,49 +6,15 @@
 
 namespace ibm {
 
-// One launch per stage for all member cases of a group.  Blocks walk the block
-// table with a grid stride, so a grid smaller than the table makes the launch
-// persistent.  Per entry the block runs the per-tile code of the case the
-// entry falls in (the same source as the single-case kernel; the two kernels
-// are compiled separately, so FP32 roundings may differ between them).
-template <int STAGE, bool BODY>
-__global__ void __launch_bounds__(256, BODY ? 1 : 6) k_stage_f32_batch(const __grid_constant__ StageBatch b) {
-  const int *start = BODY ? b.body_start : b.plain_start;
-  const int total = start[b.n];
-  __shared__ TileSmem sm;
-  for (int e = blockIdx.x; e < total; e += gridDim.x) {
-    int q = 0;
-    while (q + 1 < b.n && start[q + 1] <= e) q++;
-    const StageCase &sc = b.cs[q];
-    const float *In = STAGE == 1 ? sc.M : (STAGE == 2 ? sc.F1 : sc.F2);
-    float *Out = STAGE == 1 ? sc.F1 : (STAGE == 2 ? sc.F2 : nullptr);
-    stage_tile<STAGE, BODY>(sc.k, sc.c, sc.M, In, Out, sc.D, sc.tag, sc.sid, sc.rs, sc.tile_body, sc.body_tiles,
-                            sc.ds, sc.fuse_cfl != 0, sc.ncfl, e - start[q], sm);
-    __syncthreads();  // shared memory is reused by the next entry
-  }
-}
-
-void launch_stage_f32_batch(const StageBatch &b, int stage, int plain_grid, int body_grid, cudaStream_t s,
-                            cudaStream_t sb, bool with_body) {
-  const int nplain = b.plain_start[b.n], nbody = with_body ? b.body_start[b.n] : 0;
-  const int gp = plain_grid > 0 && plain_grid < nplain ? plain_grid : nplain;
-  const int gb = body_grid > 0 && body_grid < nbody ? body_grid : nbody;
-#define IBM_STAGE_PAIR(S)                                          \
-  do {                                                             \
-    if (gb > 0) k_stage_f32_batch<S, true><<<gb, 256, 0, sb>>>(b); \
-    if (gp > 0) k_stage_f32_batch<S, false><<<gp, 256, 0, s>>>(b); \
-  } while (0)
-  if (stage == 1) IBM_STAGE_PAIR(1);
-  else if (stage == 2) IBM_STAGE_PAIR(2);
-  else IBM_STAGE_PAIR(3);
-#undef IBM_STAGE_PAIR
-}
-
 // All entries of a stage in one launch: the body-tile entries of every member
 // first (they carry the node rebuilds), then the plain-tile entries; blocks
-// walk the combined table with a grid stride.  Launched with programmatic
-// dependent launch, its blocks are resident while the previous stage's last
-// blocks finish (they wait at the top for it to complete).
+// walk the combined table with a grid stride, so a grid smaller than the
+// table makes the launch persistent.  Per entry the block runs the per-tile
+// code of the case the entry falls in (the same source as the single-case
+// kernels; compiled separately, so FP32 roundings may differ between them).
+// Launched with programmatic dependent launch, its blocks are resident while
+// the previous stage's last blocks finish (they wait at the top for it to
+// complete).
 template <int STAGE>
 __global__ void __launch_bounds__(256, 6) k_stage_f32_batch_one(const __grid_constant__ StageBatch b) {
   __shared__ TileSmem sm;

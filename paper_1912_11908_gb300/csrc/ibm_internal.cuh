@@ -362,15 +362,11 @@ void build_stage_batch(const StageCase *cases, int n, StageBatch *b);
 void fill_stage_case(const Consts &k, float *M, float *F1, float *F2, double *D, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
                      DevState *ds, bool fuse_cfl, StageCase *out);
-// Stage `stage` of every case of the table: body entries on sb, plain entries on s.
-// plain_grid / body_grid: blocks of the launch (<= 0 or >= the entries: one
-// block per entry; fewer: persistent blocks striding over the table).
-// with_body = false launches the plain-tile kernel only.
-// The same stage as one launch over the combined table (body-tile entries first); grid 0 = one block per
-// entry; pdl: chained to the previous launch by programmatic dependent launch.
+// Stage `stage` of every case of the table as one launch over the combined
+// table (body-tile entries first).  grid: blocks of the launch (<= 0 or >= the
+// entries: one block per entry; fewer: persistent blocks striding over the
+// table); pdl: chained to the previous launch by programmatic dependent launch.
 cudaError_t launch_stage_f32_batch_one(const StageBatch &b, int stage, int grid, bool pdl, cudaStream_t s);
-void launch_stage_f32_batch(const StageBatch &b, int stage, int plain_grid, int body_grid, cudaStream_t s,
-                            cudaStream_t sb, bool with_body);
 
 // ---- batching support (capi.cu), used by the request loop (serve.cu) ----
 // FP32-bulk explicit RK3 cases advance through batched stage launches.

@@ -76,8 +76,8 @@ struct Active {
 struct Group {
   int bucket = 0;
   std::vector<Active *> members;
-  cudaStream_t s = nullptr, sb = nullptr;
-  cudaEvent_t fork = nullptr, join_b = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool dirty = true;
   long long graph_kernels = 0;
@@ -115,9 +115,8 @@ struct ibm_server {
 
 static void group_destroy(Group *g) {
   if (g->graph) cudaGraphExecDestroy(g->graph);
-  for (cudaEvent_t e : {g->fork, g->join_b, g->done, g->t0, g->t1})
+  for (cudaEvent_t e : {g->fork, g->done, g->t0, g->t1})
     if (e) cudaEventDestroy(e);
-  if (g->sb) cudaStreamDestroy(g->sb);
   if (g->s) cudaStreamDestroy(g->s);
   delete g->batch;
   delete g;
@@ -128,12 +127,9 @@ static Group *group_create(int bucket) {
   if (!g) return nullptr;
   g->bucket = bucket;
   g->batch = new (std::nothrow) StageBatch();
-  int lo = 0, hi = 0;
-  cudaDeviceGetStreamPriorityRange(&lo, &hi);
   cudaError_t e = g->batch ? cudaSuccess : cudaErrorMemoryAllocation;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->s, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g->sb, cudaStreamNonBlocking, hi);
-  for (cudaEvent_t *ev : {&g->fork, &g->join_b, &g->done})
+  for (cudaEvent_t *ev : {&g->fork, &g->done})
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&g->t0);
   if (e == cudaSuccess) e = cudaEventCreate(&g->t1);
@@ -249,7 +245,7 @@ static void build_table(Group *g) {
 }
 
 // Capture one step of the group: pre-stage work of each member on its own
-// stream, then the three batched stages (body entries on sb, plain on s).
+// stream, then the three batched stages (one launch each over the combined table).
 static ibm_status capture_group(ibm_server *s, Group *g) {
   build_table(g);
   const StageBatch &b = *g->batch;
