@@ -48,12 +48,12 @@ BYTES_PER_CELL_STAGE = {"fp32_bulk": 179.0 / 3.0, "fp64": 259.0 / 3.0}
 # 110 per face (x 2), viscous 40 per face (x 2), primitives 25, update 20
 FLOPS_PER_CELL_STAGE = 91 * 8 + 110 * 2 + 40 * 2 + 25 + 20
 # dual time, FP32-bulk: algorithmic DRAM bytes per cell and pseudo stage (FP32 tile 16 + tag 1 + FP64 iterate
-# 32 + primitives of the sub-iteration start 32 (written at stage 1, read at stages 2 and 3) + time levels n,
-# n-1 64 + FP64 output 32 + FP32 mirror 16) and FP64 flops per cell and pseudo stage of the point-implicit update
-# (counted from the formulas, FMA = 2, a division = 1: BDF2 term 25, conversion to primitives 32, enthalpy 10,
-# structured solve 26, stage combination 16, conversion back 28, misc 1)
-DUAL_BYTES_PER_CELL_STAGE = 193.0
-DUAL_FP64_FLOPS_PER_CELL = 138
+# 32 + primitives of the sub-iteration start 32 (written at stage 1, read at stages 2 and 3) + the physical step's
+# BDF part 32 + FP64 output 32 + FP32 mirror 16) and FP64 flops per cell and pseudo stage of the point-implicit
+# update (counted from the formulas, FMA = 2, a division = 1: BDF2 term 13, conversion to primitives 32, enthalpy
+# 10, structured solve 26, stage combination 16, conversion back 28, misc 1)
+DUAL_BYTES_PER_CELL_STAGE = 161.0
+DUAL_FP64_FLOPS_PER_CELL = 126
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
 def fp32_peak_tflops(sm_mhz=2070.0):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12

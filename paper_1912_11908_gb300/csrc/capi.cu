@@ -26,6 +26,7 @@ struct ibm_case {
          *vny = nullptr;
   double *A = nullptr, *B = nullptr, *C = nullptr;  // FP64 conserved: state, stage arrays (FP64 mode)
   double *Wn = nullptr, *Wm = nullptr;               // dual time: states at time levels n and n-1
+  double *G = nullptr;  // FP32-bulk dual time: the step's constant part of the BDF term (in place of W^{n-1})
   double *Q0 = nullptr;                              // FP32-bulk dual time: (p', u, v, T') of the sub-iteration start
   float *M = nullptr, *F1 = nullptr, *F2 = nullptr;  // FP32-bulk: perturbation mirror and stage arrays
   double *stage64 = nullptr;  // FP32-bulk: absolute-variable staging for ibm_get_state (allocated on first use)
@@ -208,11 +209,11 @@ static size_t carve(ibm_case *c, char *base) {
     take(&c->M, 4 * plane);
     take(&c->F1, 4 * plane);
     take(&c->F2, 4 * plane);
-    if (k.dual) {  // FP64 pseudo-stage iterates, time levels, primitives of the sub-iteration's start
+    if (k.dual) {  // FP64 pseudo-stage iterates, time level n, BDF part, primitives of the sub-iteration's start
       take(&c->B, 4 * plane);
       take(&c->C, 4 * plane);
       take(&c->Wn, 4 * plane);
-      take(&c->Wm, 4 * plane);
+      take(&c->G, 4 * plane);
       take(&c->Q0, 4 * plane);
     }
     take(&c->rst, (size_t)(c->cap > 0 ? c->cap : 1));
@@ -424,7 +425,8 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
       for (float *p : {c->M, c->F1, c->F2})
         if (cudaMemsetAsync(p, 0, 4 * plane * sizeof(float), s) != cudaSuccess) rs = fail(IBM_ECUDA, "memset failed");
     }
-    c->launches += (c->B ? 3 : 1) + (c->Wn ? 2 : 0);
+    for (double *w : {c->A, c->B, c->C, c->Wn, c->Wm})
+      if (w) c->launches += 1;
     if (c->precision == IBM_PREC_FP32_BULK) {
       float *const arrays[3] = {c->M, c->F1, c->F2};
       c->have_tmap = make_stage_tmaps(k, arrays, c->tmap);
@@ -510,12 +512,12 @@ static int enqueue_step(ibm_case *c) {
   }
   if (c->k.dual) {
     // dual time: W^{n-1} <- W^n <- W, then sub-iterations of three pseudo stages at t + dt
-    const size_t bytes = 4 * (size_t)c->k.plane * sizeof(double);
-    cudaMemcpyAsync(c->Wm, c->Wn, bytes, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(c->Wn, c->A, bytes, cudaMemcpyDeviceToDevice, s);
     double *din[3] = {c->A, c->B, c->C};
     double *dout[3] = {c->B, c->C, c->A};
     if (c->precision == IBM_PREC_FP32_BULK) {
+      // the time levels enter the pseudo stages only through the BDF part G, formed once per physical step
+      launch_dual_levels(c->k, c->A, c->Wn, c->G, c->ds, s);
+      nl += 1;
       // FP32 residual of the mirror, FP64 point-implicit update; IB / ghost nodes rebuilt in the tile loads
       float *fin[3] = {c->M, c->F1, c->F2};
       float *fout[3] = {c->F1, c->F2, c->M};
@@ -523,15 +525,15 @@ static int enqueue_step(ibm_case *c) {
         for (int st = 1; st <= 3; st++) {
           prof_mark(c, 0, true);
           if (c->stage_launch > 0) {  // one launch per pseudo stage (form 2: chained by programmatic launch)
-            launch_dual_f32_one(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->Wn, c->Wm,
-                                c->Q0, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds,
+            launch_dual_f32_one(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->G, c->Q0,
+                                c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds,
                                 c->stage_launch == 2, s);
             nl += 1;
           } else {
             cudaEventRecord(c->ev_fork, s);
             cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
-            launch_dual_f32(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->Wn, c->Wm,
-                            c->Q0, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, s, c->sb);
+            launch_dual_f32(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->G, c->Q0,
+                            c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, s, c->sb);
             cudaEventRecord(c->ev_join, c->sb);
             cudaStreamWaitEvent(s, c->ev_join, 0);
             nl += 1 + (c->body_cap > 0);
@@ -541,6 +543,9 @@ static int enqueue_step(ibm_case *c) {
       launch_dual_end(c->k, c->ds, s);
       return nl + 1;
     }
+    const size_t bytes = 4 * (size_t)c->k.plane * sizeof(double);
+    cudaMemcpyAsync(c->Wm, c->Wn, bytes, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->Wn, c->A, bytes, cudaMemcpyDeviceToDevice, s);
     for (int it = 0; it < c->k.subiters; it++)
       for (int st = 1; st <= 3; st++) {
         prof_mark(c, 1, true);

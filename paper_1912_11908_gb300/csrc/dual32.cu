@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_dual_f32_one(Consts k, PertConsts c, co
 }
 
 cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, float *Out32, double *D,
-                                const double *In64, double *Out64, const double *Wn, const double *Wm, double *Q0,
+                                const double *In64, double *Out64, const double *G, double *Q0,
                                 const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                                 const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s) {
   const PertConsts c = pert_consts(k);
@@ -56,8 +56,7 @@ cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, f
   DualPtrs dp;
   dp.In64 = In64;
   dp.Out64 = Out64;
-  dp.Wn = Wn;
-  dp.Wm = Wm;
+  dp.G = G;
   dp.Q0 = Q0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned int)(nt + nb));
@@ -75,8 +74,24 @@ cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, f
   return e;
 }
 
+// Start of a physical step: one thread per FP64 word of the 4-plane state.
+__global__ void __launch_bounds__(256) k_dual_levels(long long n, double idt, const double *__restrict__ A,
+                                                     double *__restrict__ Wn, double *__restrict__ G,
+                                                     const DevState *__restrict__ ds) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double wn = Wn[i], a = A[i];  // W^{n-1} and W^n of the new step
+  G[i] = ds->steps > 0 ? (wn - 4.0 * a) * (0.5 * idt) : -a * idt;
+  Wn[i] = a;
+}
+
+void launch_dual_levels(const Consts &k, const double *A, double *Wn, double *G, const DevState *ds, cudaStream_t s) {
+  const long long n = 4 * k.plane;
+  k_dual_levels<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, k.idt_phys, A, Wn, G, ds);
+}
+
 void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,
-                     double *Out64, const double *Wn, const double *Wm, double *Q0, const uint8_t *tag, const int *sid,
+                     double *Out64, const double *G, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
                      DevState *ds, cudaStream_t s, cudaStream_t sb) {
   PertConsts c = pert_consts(k);
@@ -86,8 +101,7 @@ void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32
   DualPtrs dp;
   dp.In64 = In64;
   dp.Out64 = Out64;
-  dp.Wn = Wn;
-  dp.Wm = Wm;
+  dp.G = G;
   dp.Q0 = Q0;
 #define IBM_DUAL_PAIR(S)                                                                                          \
   do {                                                                                                            \

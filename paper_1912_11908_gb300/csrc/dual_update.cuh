@@ -14,7 +14,8 @@ namespace ibm {
 // in perturbation variables W' = T W (T subtracts H_inf times the mass row
 // from the energy row), so the energy rows of the Weiss-Smith matrices carry
 // H - H_inf instead of H and never cancel against H_inf; R' = -L is the FP32
-// residual, BDF' is formed from the FP64 iterates and time levels, the 4x4
+// residual, BDF' is formed from the FP64 iterate and the time levels' part
+// fixed for the physical step (formed once per step), the 4x4
 // system is solved in FP64 through its structure (solve_precond; the
 // reciprocal of its FP32 pseudo-time step coefficient in FP32),
 // Q' = (p', u, v, T') is updated and combined with the sub-iteration's start
@@ -22,10 +23,11 @@ namespace ibm {
 // mirror.
 // ---------------------------------------------------------------------------
 struct DualPtrs {
-  const double *In64;    // FP64 iterate the stage starts from (perturbation)
-  double *Out64;         // FP64 iterate it produces
-  const double *Wn, *Wm; // FP64 states at time levels n and n-1 (perturbation)
-  double *Q0;            // (p', u, v, T') of the sub-iteration's start: written by stage 1, read by 2 and 3
+  const double *In64;  // FP64 iterate the stage starts from (perturbation)
+  double *Out64;       // FP64 iterate it produces
+  const double *G;     // the physical step's constant part of the BDF term: (W^{n-1} - 4 W^n) / (2 dt), or
+                       // -W^n / dt on the first step (perturbation)
+  double *Q0;          // (p', u, v, T') of the sub-iteration's start: written by stage 1, read by 2 and 3
 };
 
 // FP64 perturbation conserved -> (p', u, v, T'); ir receives 1 / rho.  Reciprocals here are the
@@ -90,13 +92,13 @@ __device__ __forceinline__ void dual_update_cell(const Consts &k, const PertCons
                                                  const float L[4], const DualPtrs &dp,
                                                  float *Out32, bool bdf2) {
   const double idt = k.idt_phys;
+  const double aw = bdf2 ? 1.5 * idt : idt;  // coefficient of the iterate in the BDF term
   double W[4], S[4], Qk[4], ir;
   for (int v = 0; v < 4; v++) W[v] = dp.In64[id + v * P];
   pert_prim64(k, W[0], W[1], W[2], W[3], Qk, ir);
   for (int v = 0; v < 4; v++) {
-    const long long o = id + v * P;
-    const double tdt = bdf2 ? (3.0 * W[v] - 4.0 * dp.Wn[o] + dp.Wm[o]) * (0.5 * idt) : (W[v] - dp.Wn[o]) * idt;
-    S[v] = (double)L[v] - tdt;  // -(R' + BDF') with R' = -L
+    const double tdt = aw * W[v] + dp.G[id + v * P];  // BDF2 (3 W - 4 W^n + W^{n-1}) / (2 dt), BDF1 (W - W^n) / dt
+    S[v] = (double)L[v] - tdt;                         // -(R' + BDF') with R' = -L
   }
   // pseudo-time coefficients (local dtau, preconditioning parameter) in FP32: they set the pseudo-time path,
   // not the fixed point R' + BDF' = 0

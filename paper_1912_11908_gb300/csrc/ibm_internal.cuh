@@ -311,23 +311,28 @@ cudaError_t launch_step_f32(const Consts &k, float *M, float *F1, float *F2, dou
                             int variant, int grid, int s_first, int s_last, cudaStream_t s);
 // Dual-time pseudo stage (1..3) in FP32-bulk form: residual of the FP32
 // mirror In32, FP64 point-implicit update of the iterate In64 into Out64 (and
-// its mirror Out32); D holds the sub-iteration's starting iterate, Wn / Wm
-// the time levels n and n-1 (all FP64 perturbations); stage 1 stores the
-// starting iterate's primitives in Q0 for stages 2 and 3.  Body tiles on sb.
+// its mirror Out32); D holds the sub-iteration's starting iterate, G the
+// physical step's constant part of the BDF term (launch_dual_levels; all FP64
+// perturbations); stage 1 stores the starting iterate's primitives in Q0 for
+// stages 2 and 3.  Body tiles on sb.
 void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,
-                     double *Out64, const double *Wn, const double *Wm, double *Q0, const uint8_t *tag, const int *sid,
+                     double *Out64, const double *G, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
                      DevState *ds, cudaStream_t s, cudaStream_t sb);
+// Start of a physical step of FP32-bulk dual time: W^n <- A and, from the
+// previous W^n (W^{n-1} of the new step), G = (W^{n-1} - 4 W^n) / (2 dt)
+// (BDF2), or G = -W^n / dt on the first step (BDF1), over the whole padded
+// state (4 planes).
+void launch_dual_levels(const Consts &k, const double *A, double *Wn, double *G, const DevState *ds, cudaStream_t s);
 // The same pseudo stage as one launch on stream s (body-tile slots first);
 // pdl: chained to the previous launch by programmatic dependent launch.
 cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, float *Out32, double *D,
-                                const double *In64, double *Out64, const double *Wn, const double *Wm, double *Q0,
+                                const double *In64, double *Out64, const double *G, double *Q0,
                                 const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                                 const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s);
-// The same two kernels over a group's block table: the plain kernel (stream s) covers tiles
-// without IB / ghost nodes near them; the body kernel (stream sb, may run
-// concurrently) covers the listed body tiles and rebuilds IB and ghost nodes
-// from rs / sid while it loads a tile (no separate reconstruction launch).
+// One member case of a group's block table (the request loop's batched
+// stages: body-tile entries rebuild IB and ghost nodes from rs / sid while
+// they load a tile, plain-tile entries cover the other tiles).
 struct StageCase {
   Consts k;
   PertConsts c;
