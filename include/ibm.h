@@ -251,6 +251,18 @@ ibm_status ibm_use_persistent(ibm_case *c, int enable);
  * it. */
 ibm_status ibm_persistent_grid(ibm_case *c, int blocks);
 
+/* Self-check of the FP32 <-> FP64 conversions that the FP32-bulk dual-time
+ * update (Sec. 2) performs on the integer bits of IEEE 754 values (off the
+ * FP64 pipe, which bounds that update): on the current device, compares them
+ * with the hardware conversions for every binary32 bit pattern except the
+ * subnormals (which the FP32 arithmetic flushes to zero) and for 2^30
+ * pseudo-random binary64 patterns, one in four an exact rounding tie, with
+ * exponents from below to above the binary32 range.  *checked receives the
+ * number of values compared, *mismatched those that differ in any bit (NaN
+ * against NaN counts as equal); both host pointers.  Synchronous; takes about
+ * a second.  IBM_EINVAL for a NULL pointer, IBM_ECUDA if a CUDA call fails. */
+ibm_status ibm_check_float_conversions(uint64_t *checked, uint64_t *mismatched);
+
 /* Replay each step from a CUDA graph captured on first use (default on);
  * enable = 0 launches every kernel directly. */
 ibm_status ibm_use_graphs(ibm_case *c, int enable);

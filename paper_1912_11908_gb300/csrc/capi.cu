@@ -876,6 +876,16 @@ extern "C" ibm_status ibm_persistent_grid(ibm_case *c, int blocks) {
   return IBM_OK;
 }
 
+extern "C" ibm_status ibm_check_float_conversions(uint64_t *checked, uint64_t *mismatched) {
+  if (!checked || !mismatched) return fail(IBM_EINVAL, "ibm_check_float_conversions: NULL output");
+  unsigned long long n = 0, bad = 0;
+  const cudaError_t e = check_float_conversions(&n, &bad);
+  if (e != cudaSuccess) return fail(IBM_ECUDA, "conversion check failed: %s", cudaGetErrorString(e));
+  *checked = n;
+  *mismatched = bad;
+  return IBM_OK;
+}
+
 extern "C" ibm_status ibm_use_graphs(ibm_case *c, int enable) {
   if (!c) return fail(IBM_EINVAL, "case is NULL");
   c->use_graphs = enable != 0;

@@ -117,4 +117,61 @@ void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32
 #undef IBM_DUAL_PAIR
 }
 
+// Self-check of f32_to_f64 / f64_to_f32 against the hardware conversions of
+// this module: every FP32 bit pattern but the subnormals (which the FP32
+// arithmetic flushes to zero), and 2^30 FP64 patterns from a counter-based
+// generator (splitmix64) with exponents from below to above the FP32 range and
+// one in four low words an exact rounding tie.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ bool same_double(double a, double b) {
+  return (a != a && b != b) || __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool same_float(float a, float b) {
+  return (a != a && b != b) || __float_as_uint(a) == __float_as_uint(b);
+}
+
+__global__ void __launch_bounds__(256) k_check_conversions(unsigned long long n64, unsigned long long *bad) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long nbad = 0;
+  for (unsigned long long i = t; i < (1ull << 32); i += stride) {
+    const unsigned int b = (unsigned int)i;
+    if (((b >> 23) & 0xffu) == 0u && (b & 0x7fffffu) != 0u) continue;  // FP32 subnormal
+    const float f = __uint_as_float(b);
+    nbad += !same_double(f32_to_f64(f), (double)f);
+  }
+  for (unsigned long long i = t; i < n64; i += stride) {
+    const unsigned long long r = mix64(i), q = mix64(i ^ 0x5851f42d4c957f2dull);
+    const unsigned int e = 860u + (unsigned int)(r % 330u);  // binary64 exponent field 860 .. 1189
+    const unsigned int hi = ((unsigned int)(r >> 32) & 0x80000000u) | (e << 20) | ((unsigned int)q & 0xfffffu);
+    unsigned int lo = (unsigned int)(q >> 32);
+    if ((r >> 20 & 3u) == 0u) lo = (lo & 0xe0000000u) | 0x10000000u;  // exact tie
+    const double d = __hiloint2double((int)hi, (int)lo);
+    nbad += !same_float(f64_to_f32(d), (float)d);
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+cudaError_t check_float_conversions(unsigned long long *checked, unsigned long long *mismatched) {
+  unsigned long long *bad = nullptr;
+  cudaError_t e = cudaMalloc(&bad, sizeof *bad);
+  if (e != cudaSuccess) return e;
+  const unsigned long long n64 = 1ull << 30;
+  e = cudaMemset(bad, 0, sizeof *bad);
+  if (e == cudaSuccess) {
+    k_check_conversions<<<152 * 8, 256>>>(n64, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(mismatched, bad, sizeof *bad, cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  *checked = (1ull << 32) - 2ull * ((1ull << 23) - 1ull) + n64;
+  return e;
+}
+
 }  // namespace ibm

@@ -30,6 +30,27 @@ struct DualPtrs {
   double *Q0;          // (p', u, v, T') of the sub-iteration's start: written by stage 1, read by 2 and 3
 };
 
+// IEEE 754 binary32 <-> binary64 conversions done on the integer bits, off the
+// FP64 pipe (which bounds the pseudo stage).  f32_to_f64 is exact for every
+// normal and zero value (the FP32 arithmetic here flushes subnormals to
+// zero); f64_to_f32 rounds to nearest, ties to even, for results in the
+// normal FP32 range and leaves anything else to the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int b = __float_as_uint(f), e = (b >> 23) & 0xffu;
+  if (e == 0xffu) return (double)f;  // infinity or NaN
+  const unsigned int hi = (b & 0x80000000u) | (e ? ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3) : 0u);
+  return __hiloint2double((int)hi, (int)(e ? b << 29 : 0u));
+}
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned int hi = (unsigned int)__double2hiint(d), lo = (unsigned int)__double2loint(d);
+  const unsigned int e = (hi >> 20) & 0x7ffu;
+  if (e - 897u >= 254u) return (float)d;  // outside the normal FP32 exponent range: hardware conversion
+  unsigned int f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned int rest = lo & 0x1fffffffu;  // the 29 dropped mantissa bits
+  f += (rest > 0x10000000u) | ((rest == 0x10000000u) & (f & 1u));
+  return __uint_as_float(f);
+}
+
 // FP64 perturbation conserved -> (p', u, v, T'); ir receives 1 / rho.  Reciprocals here are the
 // round-to-nearest FP64 reciprocal (the iterate's conversions stay exact to FP64 rounding).
 __device__ __forceinline__ void pert_prim64(const Consts &k, double dr, double dmx, double dmy, double W,
@@ -98,14 +119,14 @@ __device__ __forceinline__ void dual_update_cell(const Consts &k, const PertCons
   pert_prim64(k, W[0], W[1], W[2], W[3], Qk, ir);
   for (int v = 0; v < 4; v++) {
     const double tdt = aw * W[v] + dp.G[id + v * P];  // BDF2 (3 W - 4 W^n + W^{n-1}) / (2 dt), BDF1 (W - W^n) / dt
-    S[v] = (double)L[v] - tdt;                         // -(R' + BDF') with R' = -L
+    S[v] = f32_to_f64(L[v]) - tdt;                     // -(R' + BDF') with R' = -L
   }
   // pseudo-time coefficients (local dtau, preconditioning parameter) in FP32: they set the pseudo-time path,
   // not the fixed point R' + BDF' = 0
   const double r = 1.0 + W[0], u = Qk[1], v = Qk[2];
-  const float rf = (float)r, irf = 1.f / rf, uf = (float)u, vf = (float)v;
-  const float Tf = 1.f + (float)Qk[3], iTf = 1.f / Tf;
-  const float csf = sqrtf(c.gamma * (c.R + (float)Qk[0]) * irf), icsf = 1.f / csf;
+  const float rf = f64_to_f32(r), irf = 1.f / rf, uf = f64_to_f32(u), vf = f64_to_f32(v);
+  const float Tf = 1.f + f64_to_f32(Qk[3]), iTf = 1.f / Tf;
+  const float csf = sqrtf(c.gamma * (c.R + f64_to_f32(Qk[0])) * irf), icsf = 1.f / csf;
   const float Vm = sqrtf(uf * uf + vf * vf);
   float Ur = fmaxf(fmaxf(Vm, 1.f), c.mu * irf / c.dmin);
   Ur = fminf(fmaxf(Ur, (float)UR_FLOOR * csf), csf);
@@ -114,14 +135,14 @@ __device__ __forceinline__ void dual_update_cell(const Consts &k, const PertCons
   const float om = 1.f - mr2;
   const float cp_ = 0.5f * sqrtf(om * om * Vm * Vm + 4.f * Ur * Ur);
   const float lam = (up + cp_) * (c.idx + c.idy) + c.vis * irf;
-  const float idtau = lam / (float)k.cfl_tau;
-  const float af = bdf2 ? 1.5f * (float)idt : (float)idt;
+  const float idtau = lam / c.cfl_tau;
+  const float af = bdf2 ? 1.5f * c.idt_phys : c.idt_phys;
   const float thG = 1.f / (Ur * Ur) + iTf / c.cp, thJ = iTf / c.R;
   const float sf = idtau + af;
   const float tau = (thG * idtau + af * thJ) / sf;
   const double dH = k.cp * Qk[3] + 0.5 * ((u - k.uinf[0]) * (u + k.uinf[0]) + (v - k.uinf[1]) * (v + k.uinf[1]));
   double dQ[4];
-  solve_precond((double)(1.f / sf), (double)tau, r, ir, u, v, -(double)(rf * iTf), k.cp, dH, S, dQ);
+  solve_precond(f32_to_f64(1.f / sf), f32_to_f64(tau), r, ir, u, v, -f32_to_f64(rf * iTf), k.cp, dH, S, dQ);
   double Q0[4], Qn[4], Wo[4];
   if (STAGE == 1) {  // the stage starts from the sub-iteration's start: keep its primitives for stages 2 and 3
     for (int q = 0; q < 4; q++) dp.Q0[id + q * P] = Qk[q];
@@ -135,7 +156,7 @@ __device__ __forceinline__ void dual_update_cell(const Consts &k, const PertCons
   prim_pert64(k, Qn, Wo);
   for (int q = 0; q < 4; q++) {
     dp.Out64[id + q * P] = Wo[q];
-    Out32[id + q * P] = (float)Wo[q];
+    Out32[id + q * P] = f64_to_f32(Wo[q]);
   }
 }
 

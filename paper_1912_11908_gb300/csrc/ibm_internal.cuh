@@ -235,6 +235,7 @@ void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, 
 int stage_tiles(const Consts &k);
 struct PertConsts {  // FP32 copies of the free-stream constants
   float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin, vis, cp;
+  float cfl_tau, idt_phys;  // dual time: pseudo-time CFL number, 1 / physical dt
 };
 
 __host__ inline PertConsts pert_consts(const Consts &k) {
@@ -253,6 +254,8 @@ __host__ inline PertConsts pert_consts(const Consts &k) {
   c.dmin = (float)k.dmin;
   c.vis = (float)((2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy)));
   c.cp = (float)k.cp;
+  c.cfl_tau = (float)k.cfl_tau;
+  c.idt_phys = (float)k.idt_phys;
   return c;
 }
 
@@ -319,6 +322,9 @@ void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32
                      double *Out64, const double *G, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
                      DevState *ds, cudaStream_t s, cudaStream_t sb);
+// Self-check of the dual update's integer-bit FP32 <-> FP64 conversions
+// against the hardware conversions (synchronous, default stream).
+cudaError_t check_float_conversions(unsigned long long *checked, unsigned long long *mismatched);
 // Start of a physical step of FP32-bulk dual time: W^n <- A and, from the
 // previous W^n (W^{n-1} of the new step), G = (W^{n-1} - 4 W^n) / (2 dt)
 // (BDF2), or G = -W^n / dt on the first step (BDF1), over the whole padded

@@ -61,7 +61,8 @@ EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_
            "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs", "ibm_tag_nodes_noalloc",
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
            "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats", "ibm_autotune", "ibm_use_tma",
-           "ibm_use_persistent", "ibm_persistent_grid", "ibm_stage_launches"]
+           "ibm_use_persistent", "ibm_persistent_grid", "ibm_stage_launches",
+           "ibm_check_float_conversions"]
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 SERVE_BATCHED, SERVE_AUTOTUNE = 1, 2
 SERVER_STATS = ["group_graphs", "group_steps", "group_kernels", "autotune_runs", "capture_us"]
@@ -109,6 +110,8 @@ def load():
     L.ibm_persistent_grid.restype = ip
     L.ibm_stage_launches.argtypes = [vp, ip]
     L.ibm_stage_launches.restype = ip
+    L.ibm_check_float_conversions.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    L.ibm_check_float_conversions.restype = ip
     L.ibm_tag_nodes_noalloc.argtypes = [ctypes.POINTER(ibm_grid), vp, ip, vp, vp, ctypes.c_int32, vp, vp]
     L.ibm_tag_nodes_noalloc.restype = ip
     L.ibm_server_create.argtypes = [sz, ip, ip, ctypes.POINTER(vp)]
@@ -182,6 +185,14 @@ def ibm_tag_nodes_noalloc(spec, d_verts, nverts, d_tags, d_cells, capacity, d_co
     _check(lib().ibm_tag_nodes_noalloc(ctypes.byref(gr), ctypes.c_void_p(d_verts), int(nverts),
                                        ctypes.c_void_p(d_tags), ctypes.c_void_p(d_cells), int(capacity),
                                        ctypes.c_void_p(d_counts), ctypes.c_void_p(stream) if stream else None))
+
+
+def check_float_conversions():
+    """(values compared, mismatches) of the dual-time update's integer-bit FP32 <-> FP64 conversions against the
+    hardware conversions on the current device."""
+    n, bad = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib().ibm_check_float_conversions(ctypes.byref(n), ctypes.byref(bad)))
+    return int(n.value), int(bad.value)
 
 
 def case_device_bytes(spec):

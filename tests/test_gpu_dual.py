@@ -168,3 +168,12 @@ def test_bulk_dual_launch_forms(ibm):
     np.testing.assert_array_equal(runs[2][0], runs[1][0])
     np.testing.assert_array_equal(runs[2][1], runs[1][1])
     np.testing.assert_allclose(runs[2][1], runs[0][1], rtol=1e-5, atol=1e-5 * np.abs(runs[0][1]).max())
+
+
+def test_integer_bit_conversions_match_hardware(ibm):
+    """The dual-time update converts FP32 <-> FP64 on the integer bits of the IEEE 754 formats (the FP64 pipe
+    bounds it): every binary32 value but the flushed subnormals, and 2^30 binary64 patterns including exact
+    rounding ties and exponents outside the binary32 range, convert exactly as the hardware does."""
+    n, bad = ibm.check_float_conversions()
+    assert n == (1 << 32) - 2 * ((1 << 23) - 1) + (1 << 30)
+    assert bad == 0
