@@ -321,6 +321,26 @@ def run_ours(args, rank, world):
                   "unit": "Mcell-updates/s", "ms_per_step": tm / km, "steps": km,
                   "geometry_ms_per_step": mprof["geometry"][0] / 10, "stage_ms_per_step": mprof["residual_stage"][0] / 10}
         cm.close()
+        # cylinder crossing gas at rest at M_D = 1.2 (Re 300, 80 x 16 diameters at D/40, FP32-bulk): the
+        # supersonic moving-body pressure condition in every stage's node rebuild
+        sspec = W.moving_cylinder_supersonic(1.2, precision=W.PREC_FP32_BULK)
+        cs = ibm.Case(sspec, stream=stream.cuda_stream)
+        cs.classify()
+        scells = _active_cells(cs)
+        cs.step(5)
+        ks = 50
+        ts = _time_steps(cs, torch, flush, ks, stream)
+        cs.profile(True)
+        cs.profile_read()
+        cs.step(10)
+        sprof = cs.profile_read()
+        cs.profile(False)
+        moving["supersonic"] = {"workload": sspec["name"], "precision": "fp32_bulk",
+                                "value": scells * 3 * ks / (ts * 1e-3) / 1e6, "unit": "Mcell-updates/s",
+                                "ms_per_step": ts / ks, "steps": ks,
+                                "geometry_ms_per_step": sprof["geometry"][0] / 10,
+                                "stage_ms_per_step": sprof["residual_stage"][0] / 10}
+        cs.close()
 
     # serving mix through the request loop: Poisson arrivals (latency) and all at once (throughput)
     serving = None

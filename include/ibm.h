@@ -129,6 +129,8 @@ typedef struct {
   double bx, by;    /* boundary point P' */
   double xi_node, xi_probe;
   double w[4];      /* interpolation weights, 0 on invalid corners */
+  double curv;      /* signed curvature 1/R of the surface at P' (convex > 0): linear along the segment holding
+                       P' between the end vertices' Menger curvatures (Eq. 7, supersonic moving bodies) */
 } ibm_stencil;
 
 /* what for ibm_get_state */

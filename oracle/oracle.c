@@ -30,6 +30,7 @@ struct orc_case {
   double *vx, *vy;         /* vertices at the current pose */
   double *snx, *sny;       /* outward segment normals */
   double *vnx, *vny;       /* vertex pseudo-normals */
+  double *vk;              /* signed curvature at each vertex (convex > 0) */
   double dx, dy, h, dmin;
   double R, cp, mu, kappa, pinf;
   double Uinf[4];
@@ -153,6 +154,19 @@ static void build_normals(orc_case *c) {
       c->vnx[k] = c->snx[k];
       c->vny[k] = c->sny[k];
     }
+  }
+  /* Local curvature for the supersonic moving-body condition (Eq. 7): at vertex k the signed Menger curvature */
+  /* of (k-1, k, k+1), 2 (e1 x e2) / (|e1| |e2| |e1 + e2|), positive for a left (convex) turn of the CCW      */
+  /* polyline; on a regular polygon inscribed in a circle of radius r it is exactly 1/r.                     */
+  for (int k = 0; k < nv; k++) {
+    int km = (k == 0) ? nv - 1 : k - 1, k1 = (k + 1 == nv) ? 0 : k + 1;
+    double e1x = c->vref[2 * k] - c->vref[2 * km], e1y = c->vref[2 * k + 1] - c->vref[2 * km + 1];
+    double e2x = c->vref[2 * k1] - c->vref[2 * k], e2y = c->vref[2 * k1 + 1] - c->vref[2 * k + 1];
+    double l1 = sqrt(e1x * e1x + e1y * e1y), l2 = sqrt(e2x * e2x + e2y * e2y);
+    double sx = e1x + e2x, sy = e1y + e2y;
+    double l3 = sqrt(sx * sx + sy * sy);
+    double den = l1 * l2 * l3;
+    c->vk[k] = den > 0.0 ? 2.0 * (e1x * e2y - e1y * e2x) / den : 0.0;
   }
 }
 
@@ -304,10 +318,11 @@ static void build_tags(orc_case *c, const uint8_t *solid) {
 /* the normal (positive in the fluid).                                       */
 /* ------------------------------------------------------------------------- */
 static void boundary_point(const orc_case *c, double px, double py, double nx, double ny, int is_ghost,
-                           double ccx, double ccy, double *bx, double *by, double *xi_node, int *fallback) {
+                           double ccx, double ccy, double *bx, double *by, double *xi_node, int *fallback,
+                           int *seg, double *useg) {
   int nv = c->p.nv;
-  double best = INFINITY, bs = 0.0;
-  int found = 0;
+  double best = INFINITY, bs = 0.0, bu = 0.0;
+  int found = 0, bk = -1;
   for (int k = 0; k < nv; k++) {
     int k1 = (k + 1 == nv) ? 0 : k + 1;
     double ax = c->vx[k], ay = c->vy[k];
@@ -321,9 +336,11 @@ static void boundary_point(const orc_case *c, double px, double py, double nx, d
     if (is_ghost ? (s < 0.0) : (s > 0.0)) continue;
     double as = fabs(s);
     if (as < best) {
-      best = as; bs = s; found = 1;
+      best = as; bs = s; bu = u; bk = k; found = 1;
     }
   }
+  *seg = bk;
+  *useg = bu;
   if (found) {
     *bx = px + bs * nx;
     *by = py + bs * ny;
@@ -359,9 +376,24 @@ static void build_stencil(orc_case *c, int cell, int kind, orc_stencil *s) {
   } else {
     nx = c->vnx[feat]; ny = c->vny[feat];
   }
-  double bx, by, xi_node;
-  int fb;
-  boundary_point(c, px, py, nx, ny, kind > 0, ccx, ccy, &bx, &by, &xi_node, &fb);
+  double bx, by, xi_node, useg;
+  int fb, seg;
+  boundary_point(c, px, py, nx, ny, kind > 0, ccx, ccy, &bx, &by, &xi_node, &fb, &seg, &useg);
+  /* curvature at P' (Eq. 7): linear between the end-vertex curvatures of the segment holding P', or the     */
+  /* vertex curvature when P' falls back to a closest vertex                                                  */
+  double curv;
+  if (fb && region == ORC_REGION_VERTEX) {
+    curv = c->vk[feat];
+  } else {
+    if (fb) { /* P' is the foot point on segment feat */
+      int k1 = (feat + 1 == p->nv) ? 0 : feat + 1;
+      double ex = c->vx[k1] - c->vx[feat], ey = c->vy[k1] - c->vy[feat];
+      seg = feat;
+      useg = ((ccx - c->vx[feat]) * ex + (ccy - c->vy[feat]) * ey) / (ex * ex + ey * ey);
+    }
+    int k1 = (seg + 1 == p->nv) ? 0 : seg + 1;
+    curv = (1.0 - useg) * c->vk[seg] + useg * c->vk[k1];
+  }
   double xi_probe;
   if (kind == 0) {
     xi_probe = xi_node + c->h;              /* probe one diagonal spacing beyond the IB node */
@@ -394,6 +426,7 @@ static void build_stencil(orc_case *c, int cell, int kind, orc_stencil *s) {
   s->by = by;
   s->xi_node = xi_node;
   s->xi_probe = xi_probe;
+  s->curv = curv;
 }
 
 int orc_classify(orc_case *c) {
@@ -462,12 +495,16 @@ static inline void prim_to_cons(const orc_case *c, const double q[4], double U[4
 /* Sec. 4.4-4.6 and Sec. 5: IB and ghost reconstruction at stage time t.     */
 /* Velocity is Dirichlet (Eq. 4): linear along the normal through the wall   */
 /* value at P' and the interpolated probe value.  Pressure is Neumann        */
-/* (Eq. 5-6): dp/dn = -rho n.a_wall; temperature is adiabatic (Eq. 8).       */
+/* (Eq. 5-6): dp/dn = -rho n.a_wall; for a body moving faster than sound     */
+/* relative to the free stream, the normal force balance of Eq. 7, read in   */
+/* the sign convention of Eq. 6: dp/dn = rho u_t^2 / R - rho n.a_wall, with   */
+/* u_t the tangential velocity relative to the wall at the probe and 1/R the */
+/* stencil's curvature.  Temperature is adiabatic (Eq. 8).                   */
 /* IB nodes first (their probes use fluid nodes only), then all ghost layers */
 /* (their image points may use the freshly updated IB nodes).                */
 /* ------------------------------------------------------------------------- */
 static void reconstruct_set(orc_case *c, double *const U[4], const orc_stencil *s, int n, const double Vw[2],
-                            const double Aw[2]) {
+                            const double Aw[2], int supersonic) {
   for (int e = 0; e < n; e++) {
     const orc_stencil *st = &s[e];
     if (st->mask == 0) continue;
@@ -483,6 +520,10 @@ static void reconstruct_set(orc_case *c, double *const U[4], const orc_stencil *
     double q[4];
     double rho_p = qp[0] / (c->R * qp[3]);
     double g = -rho_p * (st->nx * Aw[0] + st->ny * Aw[1]);
+    if (supersonic) {
+      double ut = -(qp[1] - Vw[0]) * st->ny + (qp[2] - Vw[1]) * st->nx;
+      g = g + rho_p * ut * ut * st->curv;
+    }
     q[0] = qp[0] - (st->xi_probe - st->xi_node) * g;
     q[1] = Vw[0] + (qp[1] - Vw[0]) * ratio;
     q[2] = Vw[1] + (qp[2] - Vw[1]) * ratio;
@@ -494,11 +535,20 @@ static void reconstruct_set(orc_case *c, double *const U[4], const orc_stencil *
   }
 }
 
+/* Eq. 7 applies to a moving body whose speed relative to the free stream exceeds the free-stream sound speed  */
+/* (c_inf^2 = gamma p_inf / rho_inf = gamma R).                                                                  */
+static int supersonic_motion(const orc_case *c, const double V[2]) {
+  if (c->p.motion == ORC_MOTION_STATIC) return 0;
+  double rx = V[0] - c->p.uinf[0], ry = V[1] - c->p.uinf[1];
+  return rx * rx + ry * ry > c->p.gamma * c->R;
+}
+
 static void reconstruct(orc_case *c, double *const U[4], double t) {
   double X[2], V[2], Acc[2];
   motion_at(&c->p, t, X, V, Acc);
-  reconstruct_set(c, U, c->list[0], c->nlist[0], V, Acc);
-  for (int k = 1; k < 4; k++) reconstruct_set(c, U, c->list[k], c->nlist[k], V, Acc);
+  int sup = supersonic_motion(c, V);
+  reconstruct_set(c, U, c->list[0], c->nlist[0], V, Acc, sup);
+  for (int k = 1; k < 4; k++) reconstruct_set(c, U, c->list[k], c->nlist[k], V, Acc, sup);
 }
 
 void orc_reconstruct(orc_case *c, double t) {
@@ -1053,6 +1103,7 @@ orc_case *orc_create(const orc_params *pp) {
   c->sny = calloc(nv > 0 ? nv : 1, sizeof(double));
   c->vnx = calloc(nv > 0 ? nv : 1, sizeof(double));
   c->vny = calloc(nv > 0 ? nv : 1, sizeof(double));
+  c->vk = calloc(nv > 0 ? nv : 1, sizeof(double));
   if (nv > 0) build_normals(c);
   {
     double X[2], V[2], Acc[2];
@@ -1105,7 +1156,7 @@ void orc_destroy(orc_case *c) {
     free(c->Wn[v]); free(c->Wm[v]);
   }
   for (int k = 0; k < 4; k++) free(c->list[k]);
-  free(c->tag); free(c->vref); free(c->vx); free(c->vy); free(c->snx); free(c->sny); free(c->vnx); free(c->vny);
+  free(c->tag); free(c->vref); free(c->vx); free(c->vy); free(c->snx); free(c->sny); free(c->vnx); free(c->vny); free(c->vk);
   free(c);
 }
 

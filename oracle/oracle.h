@@ -78,6 +78,7 @@ typedef struct {
   double xi_node;    /* signed distance of the node from P' along the normal */
   double xi_probe;   /* signed distance of the probe / image point from P' */
   double w[4];       /* interpolation weights (0 for invalid corners) */
+  double curv;       /* signed curvature 1/R of the surface at P' (convex > 0; Eq. 7) */
 } orc_stencil;
 
 typedef struct orc_case orc_case;

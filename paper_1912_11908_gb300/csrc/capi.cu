@@ -23,7 +23,7 @@ struct ibm_case {
   int precision = IBM_PREC_FP64;
   // device memory
   double *vref = nullptr, *vx = nullptr, *vy = nullptr, *snx = nullptr, *sny = nullptr, *vnx = nullptr,
-         *vny = nullptr;
+         *vny = nullptr, *vk = nullptr;
   double *A = nullptr, *B = nullptr, *C = nullptr;  // FP64 conserved: state, stage arrays (FP64 mode)
   double *Wn = nullptr, *Wm = nullptr;               // dual time: states at time levels n and n-1
   double *G = nullptr;  // FP32-bulk dual time: the step's constant part of the BDF term (in place of W^{n-1})
@@ -197,6 +197,7 @@ static size_t carve(ibm_case *c, char *base) {
   take(&c->sny, nv);
   take(&c->vnx, nv);
   take(&c->vny, nv);
+  take(&c->vk, nv);
   take(&c->A, 4 * plane);
   if (c->precision == IBM_PREC_FP64) {
     take(&c->B, 4 * plane);
@@ -390,6 +391,7 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   c->g.sny = c->sny;
   c->g.vnx = c->vnx;
   c->g.vny = c->vny;
+  c->g.vk = c->vk;
 
   ibm_status rs = IBM_OK;
   do {
@@ -398,7 +400,7 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
         rs = fail(IBM_ECUDA, "vertex upload failed");
         break;
       }
-      launch_normals(nv, c->vref, c->snx, c->sny, c->vnx, c->vny, s);
+      launch_normals(nv, c->vref, c->snx, c->sny, c->vnx, c->vny, c->vk, s);
       c->launches++;
     }
     std::memset(c->hds, 0, sizeof(DevState));

@@ -56,11 +56,15 @@ void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *d
 // from their stencils.  Primitives p, u, v, T are interpolated at the probe
 // / image point; velocity is Dirichlet (Eq. 4), linear along the normal
 // through the wall velocity at P'; pressure is Neumann with
-// dp/dn = -rho n.a_wall (Eq. 5-6); temperature is adiabatic (Eq. 8).
+// dp/dn = -rho n.a_wall (Eq. 5-6), plus, for a body moving faster than the
+// free-stream sound speed, the centripetal term rho u_t^2 kappa of the normal
+// momentum balance (Eq. 7, in the sign convention of Eq. 6; u_t is the
+// velocity tangential to the wall relative to it at the probe, kappa the
+// signed curvature at P'); temperature is adiabatic (Eq. 8).
 // One thread per list entry; in place on the stage array.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const ibm_stencil &s, const double V[2],
-                                              const double Acc[2]) {
+                                              const double Acc[2], bool sup) {
   if (s.mask == 0) return;
   double qp[4] = {0.0, 0.0, 0.0, 0.0};
   for (int q = 0; q < 4; q++) {
@@ -76,7 +80,11 @@ __device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const 
   }
   const double ratio = s.xi_node / s.xi_probe;
   const double rho_p = qp[0] / (k.R * qp[3]);
-  const double g = -rho_p * (s.nx * Acc[0] + s.ny * Acc[1]);
+  double g = -rho_p * (s.nx * Acc[0] + s.ny * Acc[1]);
+  if (sup) {
+    const double ut = -(qp[1] - V[0]) * s.ny + (qp[2] - V[1]) * s.nx;
+    g = g + rho_p * ut * ut * s.curv;
+  }
   const double p = qp[0] - (s.xi_probe - s.xi_node) * g;
   const double u = V[0] + (qp[1] - V[0]) * ratio;
   const double v = V[1] + (qp[2] - V[1]) * ratio;
@@ -94,10 +102,11 @@ __global__ void __launch_bounds__(1024) k_recon1_f64(Consts k, double *U, const 
                                                      int cap, const DevState *__restrict__ ds, int stage) {
   double X[2], V[2], Acc[2];
   motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
+  const bool sup = supersonic_motion(k, V);
   const int nib = min(ds->offset[1], cap), tot = min(ds->offset[4], cap);
-  for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc);
+  for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup);
   __syncthreads();
-  for (int e = nib + threadIdx.x; e < tot; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc);
+  for (int e = nib + threadIdx.x; e < tot; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup);
 }
 
 // many blocks, one pass (0: IB nodes, 1: ghost nodes) per launch
@@ -109,7 +118,7 @@ __global__ void __launch_bounds__(128) k_recon_f64(Consts k, double *U, const ib
   if (e >= hi) return;
   double X[2], V[2], Acc[2];
   motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
-  recon_one_f64(k, U, st[e], V, Acc);
+  recon_one_f64(k, U, st[e], V, Acc, supersonic_motion(k, V));
 }
 
 void launch_recon_f64(const Consts &k, double *U, const ibm_stencil *st, int cap, const DevState *ds, int stage,

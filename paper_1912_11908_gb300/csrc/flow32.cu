@@ -113,6 +113,7 @@ __global__ void k_compact_stencils(Consts k, const ibm_stencil *__restrict__ st,
   r.nx = (float)s.nx;
   r.ny = (float)s.ny;
   for (int q = 0; q < 4; q++) r.w[q] = (float)s.w[q];
+  r.curv = (float)s.curv;
   rs[e] = r;
   sid[s.cell] = e;
 }

@@ -21,10 +21,14 @@ namespace ibm {
 // to k+1; its outward normal is the travel direction turned clockwise.  The
 // 2-D vertex pseudo-normal weights its two incident segments equally (each
 // incident "face" enters Eq. 2 / Eq. 3 with the same weight) and is
-// normalised.  One thread per vertex.
+// normalised.  The vertex also gets the local curvature of the supersonic
+// moving-body condition (Eq. 7): the signed Menger curvature of its two
+// incident segments, 2 (e1 x e2) / (|e1| |e2| |e1 + e2|), positive for a left
+// (convex) turn of the CCW polyline (1/r exactly on a regular polygon
+// inscribed in a circle of radius r).  One thread per vertex.
 // ---------------------------------------------------------------------------
 __global__ void k_normals(int nv, const double *__restrict__ v, double *snx, double *sny, double *vnx,
-                          double *vny) {
+                          double *vny, double *vk) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nv) return;
   int k1 = (k + 1 == nv) ? 0 : k + 1;
@@ -48,12 +52,17 @@ __global__ void k_normals(int nv, const double *__restrict__ v, double *snx, dou
     vnx[k] = nx;
     vny[k] = ny;
   }
+  // curvature: e1 = previous segment (fx, fy), e2 = own segment (ex, ey)
+  double cx = fx + ex, cy = fy + ey;
+  double L3 = sqrt(cx * cx + cy * cy);
+  double den = Lm * L * L3;
+  vk[k] = den > 0.0 ? 2.0 * (fx * ey - fy * ex) / den : 0.0;
 }
 
-void launch_normals(int nv, const double *v, double *snx, double *sny, double *vnx, double *vny,
+void launch_normals(int nv, const double *v, double *snx, double *sny, double *vnx, double *vny, double *vk,
                     cudaStream_t s) {
   if (nv <= 0) return;
-  k_normals<<<(nv + 127) / 128, 128, 0, s>>>(nv, v, snx, sny, vnx, vny);
+  k_normals<<<(nv + 127) / 128, 128, 0, s>>>(nv, v, snx, sny, vnx, vny, vk);
 }
 
 // ---------------------------------------------------------------------------
@@ -410,8 +419,8 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
                                                   RStencil32 *__restrict__ rs, int *__restrict__ sid) {
   __shared__ double s_v[4];
   __shared__ int s_i[4], s_s[4];
-  __shared__ double s_d[4];
-  __shared__ int s_n[2];
+  __shared__ double s_d[5];
+  __shared__ int s_n[3];
   const int total = min(ds->offset[4], cap);
   for (int e = blockIdx.x; e < total; e += gridDim.x) {
     const ibm_stencil s0 = st[e];
@@ -467,7 +476,7 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
     }
     // boundary point on the line along the local normal (Sec. 4.3)
     const bool ghost = kind > 0;
-    double bs_best = INFINITY, bs_s = 0.0;
+    double bs_best = INFINITY, bs_s = 0.0, bs_u = 0.0;
     int bs_seg = 0x7fffffff;
     for (int kk = threadIdx.x; kk < nv; kk += 128) {
       const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
@@ -482,13 +491,15 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
       if (ghost ? (sv < 0.0) : (sv > 0.0)) continue;
       const double as = fabs(sv);
       if (as < bs_best) {
-        bs_best = as; bs_s = sv; bs_seg = kk;
+        bs_best = as; bs_s = sv; bs_u = u; bs_seg = kk;
       }
     }
     win = block_argmin128(bs_best, bs_seg, s_v, s_i, s_s);
     if ((int)threadIdx.x == win) {
       s_d[2] = bs_best;
       s_d[3] = bs_s;
+      s_d[4] = bs_u;
+      s_n[2] = bs_seg;
     }
     __syncthreads();
     const double found_abs = s_d[2];
@@ -528,6 +539,24 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
         nstep++;
       }
       if (mask == 0) atomicOr(&ds->err, ERR_STENCIL);
+      // curvature at P' (Eq. 7): linear between the end-vertex curvatures of the segment holding P', or the
+      // vertex curvature when P' falls back to a closest vertex
+      double curv;
+      if (fb && region == IBM_REGION_VERTEX) {
+        curv = g.vk[feat];
+      } else {
+        int sg = s_n[2];
+        double uu = s_d[4];
+        if (fb) {  // P' is the foot point on segment feat
+          const int f1 = (feat + 1 == nv) ? 0 : feat + 1;
+          const double ex = g.vx[f1] - g.vx[feat], ey = g.vy[f1] - g.vy[feat];
+          sg = feat;
+          uu = ((ccx - g.vx[feat]) * ex + (ccy - g.vy[feat]) * ey) / (ex * ex + ey * ey);
+        }
+        const int s1 = (sg + 1 == nv) ? 0 : sg + 1;
+        curv = (1.0 - uu) * g.vk[sg] + uu * g.vk[s1];
+      }
+      s.curv = curv;
       s.feature = feat;
       s.region = fb ? IBM_REGION_FALLBACK : region;
       s.i0 = i0;
@@ -553,6 +582,7 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
         r.nx = (float)s.nx;
         r.ny = (float)s.ny;
         for (int q = 0; q < 4; q++) r.w[q] = (float)s.w[q];
+        r.curv = (float)s.curv;
         rs[e] = r;
         sid[s.cell] = e;
       }

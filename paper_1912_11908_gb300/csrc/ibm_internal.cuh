@@ -83,6 +83,7 @@ struct Geom {
   const double *vref;   // 2*nv reference vertices
   double *vx, *vy;      // current pose
   const double *snx, *sny, *vnx, *vny;
+  const double *vk;     // signed curvature at each vertex (convex > 0)
 };
 
 __host__ __device__ inline long long cidx(const Consts &k, int i, int j) {
@@ -163,10 +164,20 @@ __device__ inline void motion_at(const Motion &m, double t, double X[2], double 
   }
 }
 
+// Eq. 7 holds for a moving body whose speed relative to the free stream
+// exceeds the free-stream sound speed (c_inf^2 = gamma p_inf / rho_inf =
+// gamma R in the nondimensional gas).
+__device__ inline bool supersonic_motion(const Consts &k, const double V[2]) {
+  if (k.motion.kind == IBM_MOTION_STATIC) return false;
+  const double rx = V[0] - k.uinf[0], ry = V[1] - k.uinf[1];
+  return rx * rx + ry * ry > k.gamma * k.R;
+}
+
 struct RStencil32;
 
 // ---- launchers (geometry.cu) ----
-void launch_normals(int nv, const double *v, double *snx, double *sny, double *vnx, double *vny, cudaStream_t s);
+void launch_normals(int nv, const double *v, double *snx, double *sny, double *vnx, double *vny, double *vk,
+                    cudaStream_t s);
 void launch_pose(const Consts &k, const Geom &g, DevState *ds, cudaStream_t s);
 // maxw x maxh: upper bound (cells) of the body's bounding box for any pose
 void launch_classify(const Consts &k, const Geom &g, uint8_t *solid, const DevState *ds, int maxw, int maxh,
@@ -215,6 +226,7 @@ struct RStencil32 {
   float nx, ny;
   int ccell;    // interior index j0*nx + i0 of corner (i0, j0)
   float w[4];
+  float curv;   // signed surface curvature at P' (supersonic moving-body condition, Eq. 7)
 };
 
 // FP32-bulk path (flow32.cu).  The FP64 state D of this mode holds the

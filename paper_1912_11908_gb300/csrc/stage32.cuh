@@ -147,7 +147,7 @@ struct TileSmem {
   float sT[HY][HX];     // T'
   unsigned long long mbar;
   unsigned int mbar_phase;  // persistent kernel: parity of the barrier's next phase (barrier initialised once)
-  float wm[4];    // wall velocity and acceleration at the stage time
+  float wm[5];    // wall velocity and acceleration at the stage time; 1 if Eq. 7 applies (else 0)
   float lred[8];  // per-warp maxima of the CFL reduction
   int nrb;        // listed IB / ghost nodes (body tiles)
   int rbm[RB_MAX], rbe[RB_MAX];
@@ -254,9 +254,14 @@ __device__ __forceinline__ void raw_prim(const PertConsts &c, const float *U, lo
 
 __device__ __forceinline__ void wall_bc(const PertConsts &c, const RStencil32 &s, const float qp[4], const float *wm,
                                         float q[4]) {
-  // wm = (Vx, Vy, Ax, Ay) at the stage time
+  // wm = (Vx, Vy, Ax, Ay, supersonic) at the stage time; Neumann pressure (Eq. 5-6), plus the centripetal
+  // term rho u_t^2 kappa of Eq. 7 (u_t tangential to the wall, relative to it, at the probe)
   const float rho_p = 1.f + (qp[0] - c.R * qp[3]) / (c.R * (1.f + qp[3]));
-  const float g = -rho_p * (s.nx * wm[2] + s.ny * wm[3]);
+  float g = -rho_p * (s.nx * wm[2] + s.ny * wm[3]);
+  if (wm[4] != 0.f) {
+    const float ut = -(qp[1] - wm[0]) * s.ny + (qp[2] - wm[1]) * s.nx;
+    g = g + rho_p * ut * ut * s.curv;
+  }
   q[0] = qp[0] - s.dxi * g;
   q[1] = wm[0] + (qp[1] - wm[0]) * s.ratio;
   q[2] = wm[1] + (qp[2] - wm[1]) * s.ratio;
@@ -365,6 +370,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     wm[1] = (float)V[1];
     wm[2] = (float)Acc[0];
     wm[3] = (float)Acc[1];
+    wm[4] = supersonic_motion(k, V) ? 1.f : 0.f;
   }
   // interior tile (the loaded region needs no domain mapping): one tensor copy stages it
   const bool tma = TMA && tmap != nullptr && i0 >= NG && j0 >= NG && i0 + TX + NG <= k.nx && j0 + TY + NG <= k.ny;

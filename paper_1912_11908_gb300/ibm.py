@@ -47,7 +47,7 @@ STENCIL_DTYPE = np.dtype([
     ("cell", "<i4"), ("feature", "<i4"), ("region", "<i4"), ("i0", "<i4"), ("j0", "<i4"),
     ("mask", "<i4"), ("nstep", "<i4"), ("kind", "<i4"),
     ("nx", "<f8"), ("ny", "<f8"), ("bx", "<f8"), ("by", "<f8"),
-    ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (4,)),
+    ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (4,)), ("curv", "<f8"),
 ])
 
 class ibm_result(ctypes.Structure):

@@ -94,6 +94,27 @@ def oscillating_cylinder_m02_re185(nx=1024, ny=512, **kw):
                      amp=(0.0, 0.2), freq=0.16, name="osc_cylinder_M0.2_Re185_%dx%d" % (nx, ny), **kw)
 
 
+def moving_cylinder_supersonic(mach_d=1.2, nx=3200, ny=640, length=80.0, height=16.0, start=1.5, **kw):
+    """Cylinder moving at constant supersonic speed through gas at rest (Sec. 8.2.3): speed 1 along -x, Mach
+    and Reynolds numbers (300) on that speed, domain length x height diameters, centre `start` diameters from
+    the right side at mid-height; the wake leaves through the left side, the bow shock through the top and
+    bottom (zero-gradient), the gas ahead is at rest.  The paper's case runs along +x on a stretched grid with
+    D/80 near the body; this one uses a uniform grid (D/40 by default)."""
+    verts = cylinder(256, 1.0, center=(length - start, 0.5 * height))
+    bc = (BC_OUTFLOW, BC_FREESTREAM, BC_OUTFLOW, BC_OUTFLOW)
+    return case_spec(verts, nx, ny, (0.0, length, 0.0, height), mach_d, 300.0, bc, uinf=(0.0, 0.0),
+                     motion=MOTION_CONST, vel=(-1.0, 0.0), name="moving_cylinder_M%g_Re300_%dx%d" % (mach_d, nx, ny),
+                     **kw)
+
+
+def stationary_cylinder_supersonic(mach_d=1.2, nx=1600, ny=640, length=40.0, height=16.0, upstream=8.0, **kw):
+    """Galilean counterpart of moving_cylinder_supersonic: the cylinder at rest, the stream at speed 1 along +x
+    at the same Mach and Reynolds numbers; `upstream` diameters of domain ahead of the centre."""
+    verts = cylinder(256, 1.0, center=(upstream, 0.5 * height))
+    return case_spec(verts, nx, ny, (0.0, length, 0.0, height), mach_d, 300.0, SUPERSONIC,
+                     name="stationary_cylinder_M%g_Re300_%dx%d" % (mach_d, nx, ny), **kw)
+
+
 def naca0012_a5_m0001(nx=2048, ny=1024, **kw):
     """NACA0012 at 5 deg, 400 vertices, M=0.001, Re=1000, 2048x1024 over [-4,8]x[-3,3]; dual time, 30 sub-iterations."""
     dx = 12.0 / nx
