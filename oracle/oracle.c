@@ -499,7 +499,9 @@ static inline void prim_to_cons(const orc_case *c, const double q[4], double U[4
 /* relative to the free stream, the normal force balance of Eq. 7, read in   */
 /* the sign convention of Eq. 6: dp/dn = rho u_t^2 / R - rho n.a_wall, with   */
 /* u_t the tangential velocity relative to the wall at the probe and 1/R the */
-/* stencil's curvature.  Temperature is adiabatic (Eq. 8).                   */
+/* stencil's curvature.  Temperature is adiabatic (Eq. 8).  With rho =       */
+/* p / (R T) and T fixed along the normal, the pressure condition is a       */
+/* linear ODE in p, integrated exactly from the probe to the node.           */
 /* IB nodes first (their probes use fluid nodes only), then all ghost layers */
 /* (their image points may use the freshly updated IB nodes).                */
 /* ------------------------------------------------------------------------- */
@@ -518,13 +520,14 @@ static void reconstruct_set(orc_case *c, double *const U[4], const orc_stencil *
     }
     double ratio = st->xi_node / st->xi_probe;
     double q[4];
-    double rho_p = qp[0] / (c->R * qp[3]);
-    double g = -rho_p * (st->nx * Aw[0] + st->ny * Aw[1]);
+    /* dp/dn = rho G with G = -n.a_wall (+ u_t^2 kappa); rho = p / (R T) and T fixed along the normal (Eq. 8), */
+    /* so the condition integrates exactly from the probe to the node: p = p_probe exp(-(xi_p - xi_n) G / (R T)) */
+    double G = -(st->nx * Aw[0] + st->ny * Aw[1]);
     if (supersonic) {
       double ut = -(qp[1] - Vw[0]) * st->ny + (qp[2] - Vw[1]) * st->nx;
-      g = g + rho_p * ut * ut * st->curv;
+      G = G + ut * ut * st->curv;
     }
-    q[0] = qp[0] - (st->xi_probe - st->xi_node) * g;
+    q[0] = qp[0] * exp(-(st->xi_probe - st->xi_node) * G / (c->R * qp[3]));
     q[1] = Vw[0] + (qp[1] - Vw[0]) * ratio;
     q[2] = Vw[1] + (qp[2] - Vw[1]) * ratio;
     q[3] = qp[3];
@@ -1030,8 +1033,11 @@ int orc_step(orc_case *c, int nsteps) {
 /* ------------------------------------------------------------------------- */
 /* Sec. 6, Eq. 9: force on the body.  Midpoint rule per segment; surface     */
 /* pressure and wall shear from the probe one diagonal spacing out along the */
-/* segment normal (inverse-distance weighted as in Sec. 4.6).  The free-     */
-/* stream pressure is subtracted (its closed-surface integral is zero).      */
+/* segment normal (inverse-distance weighted as in Sec. 4.6); the pressure  */
+/* is carried to the wall by the wall condition of the reconstruction (Eq.   */
+/* 6-8, curvature at the segment midpoint = mean of its vertex values).     */
+/* The free-stream pressure is subtracted (its closed-surface integral is   */
+/* zero).                                                                    */
 /* Compensated (Kahan) summation.                                            */
 /* ------------------------------------------------------------------------- */
 void orc_forces(orc_case *c, double out[4]) {
@@ -1039,6 +1045,7 @@ void orc_forces(orc_case *c, double out[4]) {
   if (!c->classified) orc_classify(c);
   double X[2], V[2], Acc[2];
   motion_at(p, c->t, X, V, Acc);
+  int sup = supersonic_motion(c, V);
   double sx = 0, cx = 0, sy = 0, cy = 0;
   for (int k = 0; k < p->nv; k++) {
     int k1 = (k + 1 == p->nv) ? 0 : k + 1;
@@ -1065,9 +1072,13 @@ void orc_forces(orc_case *c, double out[4]) {
       cons_to_prim(c, c->A[0][id], c->A[1][id], c->A[2][id], c->A[3][id], qk);
       for (int v = 0; v < 4; v++) qp[v] += w[kk] * qk[v];
     }
-    double rho_p = qp[0] / (c->R * qp[3]);
-    double gn = -rho_p * (nx * Acc[0] + ny * Acc[1]);
-    double ps = qp[0] - xi * gn;
+    /* wall pressure: the probe's, carried to the surface by the wall condition of the reconstruction */
+    double G = -(nx * Acc[0] + ny * Acc[1]);
+    if (sup) {
+      double ut = (qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty;
+      G = G + ut * ut * (0.5 * (c->vk[k] + c->vk[k1]));
+    }
+    double ps = qp[0] * exp(-xi * G / (c->R * qp[3]));
     double tau = c->mu * ((qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty) / xi;
     double fx = (-(ps - c->pinf) * nx + tau * tx) * L;
     double fy = (-(ps - c->pinf) * ny + tau * ty) * L;

@@ -60,7 +60,8 @@ void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *d
 // free-stream sound speed, the centripetal term rho u_t^2 kappa of the normal
 // momentum balance (Eq. 7, in the sign convention of Eq. 6; u_t is the
 // velocity tangential to the wall relative to it at the probe, kappa the
-// signed curvature at P'); temperature is adiabatic (Eq. 8).
+// signed curvature at P'); temperature is adiabatic (Eq. 8), which makes the
+// pressure condition a linear ODE in p along the normal, integrated exactly.
 // One thread per list entry; in place on the stage array.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const ibm_stencil &s, const double V[2],
@@ -79,13 +80,14 @@ __device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const 
     qp[3] += w * (p / (r * k.R));
   }
   const double ratio = s.xi_node / s.xi_probe;
-  const double rho_p = qp[0] / (k.R * qp[3]);
-  double g = -rho_p * (s.nx * Acc[0] + s.ny * Acc[1]);
+  // dp/dn = rho G with rho = p / (R T) and T fixed along the normal (Eq. 8): integrated exactly from the
+  // probe to the node, p = p_probe exp(-(xi_p - xi_n) G / (R T)), positive however coarse the grid
+  double G = -(s.nx * Acc[0] + s.ny * Acc[1]);
   if (sup) {
     const double ut = -(qp[1] - V[0]) * s.ny + (qp[2] - V[1]) * s.nx;
-    g = g + rho_p * ut * ut * s.curv;
+    G = G + ut * ut * s.curv;
   }
-  const double p = qp[0] - (s.xi_probe - s.xi_node) * g;
+  const double p = qp[0] * exp(-(s.xi_probe - s.xi_node) * G / (k.R * qp[3]));
   const double u = V[0] + (qp[1] - V[0]) * ratio;
   const double v = V[1] + (qp[2] - V[1]) * ratio;
   const double T = qp[3];

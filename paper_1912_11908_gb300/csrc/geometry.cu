@@ -949,14 +949,17 @@ void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_ste
 // ---------------------------------------------------------------------------
 // Sec. 6, Eq. 9: force on the body, midpoint rule per segment; surface
 // pressure and wall shear from a probe one diagonal spacing out along the
-// segment normal (inverse-distance weighted, Sec. 4.6); free-stream pressure
-// subtracted.  One block; fixed-order tree reduction (deterministic).
+// segment normal (inverse-distance weighted, Sec. 4.6), the pressure carried
+// to the wall by the reconstruction's wall condition (Eq. 6-8, curvature at
+// the segment midpoint); free-stream pressure subtracted.  One block;
+// fixed-order tree reduction (deterministic).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint8_t *__restrict__ tag,
                                                     const double *__restrict__ A, bool pert, DevState *ds) {
   __shared__ double rx[256], ry[256];
   double V[2], Acc[2], X[2];
   motion_at(k.motion, ds->t, X, V, Acc);
+  const bool sup = supersonic_motion(k, V);
   double sx = 0.0, sy = 0.0;
   for (int e = threadIdx.x; e < g.nv; e += blockDim.x) {
     int e1 = (e + 1 == g.nv) ? 0 : e + 1;
@@ -993,9 +996,13 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
       qp[2] += w[q] * v;
       qp[3] += w[q] * T;
     }
-    double rho_p = qp[0] / (k.R * qp[3]);
-    double gn = -rho_p * (nx * Acc[0] + ny * Acc[1]);
-    double ps = qp[0] - xi * gn;
+    // wall pressure: the probe's, carried to the surface by the wall condition of the reconstruction
+    double G = -(nx * Acc[0] + ny * Acc[1]);
+    if (sup) {
+      double ut = (qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty;
+      G = G + ut * ut * (0.5 * (g.vk[e] + g.vk[e1]));
+    }
+    double ps = qp[0] * exp(-xi * G / (k.R * qp[3]));
     double tau = k.mu * ((qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty) / xi;
     sx += (-(ps - k.pinf) * nx + tau * tx) * L;
     sy += (-(ps - k.pinf) * ny + tau * ty) * L;

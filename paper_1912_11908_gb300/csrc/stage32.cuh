@@ -254,15 +254,16 @@ __device__ __forceinline__ void raw_prim(const PertConsts &c, const float *U, lo
 
 __device__ __forceinline__ void wall_bc(const PertConsts &c, const RStencil32 &s, const float qp[4], const float *wm,
                                         float q[4]) {
-  // wm = (Vx, Vy, Ax, Ay, supersonic) at the stage time; Neumann pressure (Eq. 5-6), plus the centripetal
-  // term rho u_t^2 kappa of Eq. 7 (u_t tangential to the wall, relative to it, at the probe)
-  const float rho_p = 1.f + (qp[0] - c.R * qp[3]) / (c.R * (1.f + qp[3]));
-  float g = -rho_p * (s.nx * wm[2] + s.ny * wm[3]);
+  // wm = (Vx, Vy, Ax, Ay, supersonic) at the stage time.  Neumann pressure dp/dn = rho G (Eq. 5-6), G = -n.a
+  // plus the centripetal u_t^2 kappa of Eq. 7 (u_t tangential to the wall, relative to it, at the probe); with
+  // rho = p / (R T) and T fixed along the normal (Eq. 8) it integrates to p = p_probe exp(-dxi G / (R T)),
+  // here in perturbation form p' = p'_probe + (R + p'_probe) expm1(...) so that p' keeps its digits
+  float G = -(s.nx * wm[2] + s.ny * wm[3]);
   if (wm[4] != 0.f) {
     const float ut = -(qp[1] - wm[0]) * s.ny + (qp[2] - wm[1]) * s.nx;
-    g = g + rho_p * ut * ut * s.curv;
+    G = G + ut * ut * s.curv;
   }
-  q[0] = qp[0] - s.dxi * g;
+  q[0] = qp[0] + (c.R + qp[0]) * expm1f(-s.dxi * G / (c.R * (1.f + qp[3])));
   q[1] = wm[0] + (qp[1] - wm[0]) * s.ratio;
   q[2] = wm[1] + (qp[2] - wm[1]) * s.ratio;
   q[3] = qp[3];
