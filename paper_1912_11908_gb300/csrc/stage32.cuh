@@ -263,7 +263,8 @@ __device__ __forceinline__ void wall_bc(const PertConsts &c, const RStencil32 &s
     const float ut = -(qp[1] - wm[0]) * s.ny + (qp[2] - wm[1]) * s.nx;
     G = G + ut * ut * s.curv;
   }
-  q[0] = qp[0] + (c.R + qp[0]) * expm1f(-s.dxi * G / (c.R * (1.f + qp[3])));
+  // (static body: G = 0 and p'_node = p'_probe exactly, without the exponential)
+  q[0] = G != 0.f ? qp[0] + (c.R + qp[0]) * expm1f(-s.dxi * G / (c.R * (1.f + qp[3]))) : qp[0];
   q[1] = wm[0] + (qp[1] - wm[0]) * s.ratio;
   q[2] = wm[1] + (qp[2] - wm[1]) * s.ratio;
   q[3] = qp[3];
