@@ -341,6 +341,27 @@ def run_ours(args, rank, world):
                                 "geometry_ms_per_step": sprof["geometry"][0] / 10,
                                 "stage_ms_per_step": sprof["residual_stage"][0] / 10}
         cs.close()
+        # planar shock (Mach 1.5) driving a cylinder free to translate (Sec. 8.2.6, 656 x 656, FP32-bulk): force
+        # and body update every step on top of the re-classification
+        kspec = W.shock_driven_cylinder(precision=W.PREC_FP32_BULK)
+        ck = ibm.Case(kspec, stream=stream.cuda_stream)
+        ck.set_state(W.shock_initial_state(kspec))
+        ck.classify()
+        kcells = _active_cells(ck)
+        ck.step(5)
+        kk = 50
+        tk = _time_steps(ck, torch, flush, kk, stream)
+        ck.profile(True)
+        ck.profile_read()
+        ck.step(10)
+        kprof = ck.profile_read()
+        ck.profile(False)
+        moving["shock_driven"] = {"workload": kspec["name"], "precision": "fp32_bulk",
+                                  "value": kcells * 3 * kk / (tk * 1e-3) / 1e6, "unit": "Mcell-updates/s",
+                                  "ms_per_step": tk / kk, "steps": kk,
+                                  "geometry_and_force_ms_per_step": kprof["geometry"][0] / 10,
+                                  "stage_ms_per_step": kprof["residual_stage"][0] / 10}
+        ck.close()
 
     # serving mix through the request loop: Poisson arrivals (latency) and all at once (throughput)
     serving = None

@@ -62,8 +62,11 @@ typedef enum {
 enum { IBM_TAG_FLUID = 0, IBM_TAG_SOLID = 1, IBM_TAG_IB = 2, IBM_TAG_G1 = 3, IBM_TAG_G2 = 4, IBM_TAG_G3 = 5 };
 /* domain sides, in ibm_grid.bc order: x-low, x-high, y-low, y-high */
 enum { IBM_BC_FREESTREAM = 0, IBM_BC_OUTFLOW = 1, IBM_BC_PERIODIC = 2 };
-/* prescribed body motion: displacement X(t) = amp sin(2 pi freq t) (SIN) or vel t (CONST) */
-enum { IBM_MOTION_STATIC = 0, IBM_MOTION_SIN = 1, IBM_MOTION_CONST = 2 };
+/* body motion: prescribed displacement X(t) = amp sin(2 pi freq t) (SIN) or vel t (CONST), or translation
+ * under the fluid force (COUPLED, Sec. 6, Eq. 10): initial velocity vel, mass per unit depth `mass`; each step
+ * the force at its start sets a constant acceleration F / mass for the step, the position advances by
+ * U dt + dt^2 F / (2 mass) and the velocity by dt F / mass (explicit RK3 only) */
+enum { IBM_MOTION_STATIC = 0, IBM_MOTION_SIN = 1, IBM_MOTION_CONST = 2, IBM_MOTION_COUPLED = 3 };
 /* arithmetic: FP64 throughout, or FP32 bulk (stage values and fluxes in FP32
  * on perturbations from the free stream, FP64 state accumulation) */
 enum { IBM_PREC_FP64 = 0, IBM_PREC_FP32_BULK = 1 };
@@ -109,7 +112,8 @@ typedef struct {
   int kind;         /* IBM_MOTION_* */
   double amp[2];
   double freq;
-  double vel[2];
+  double vel[2];    /* CONST: velocity; COUPLED: initial velocity */
+  double mass;      /* COUPLED: body mass per unit depth (> 0), in units of rho_inf L^2 */
 } ibm_motion;
 
 /* One IB or ghost node and its reconstruction stencil (Sec. 4.1-4.6, Sec. 5).
@@ -144,8 +148,11 @@ enum {
   IBM_TUNING = 6,       /* int32_t[2] (host only): register-budget variants of the FP32-bulk stage kernel
                            picked by the autotuner for stage 1 and for stages 2-3 (0..2; -1 before the first
                            step, or FP64) */
-  IBM_STAGE_LAUNCH = 7  /* int32_t (host only): launch form of the FP32-bulk stages (0..2, see
+  IBM_STAGE_LAUNCH = 7, /* int32_t (host only): launch form of the FP32-bulk stages (0..2, see
                            ibm_stage_launches; the autotuner's pick unless set; -1 for FP64) */
+  IBM_BODY = 8          /* double[6]: body displacement x, y and velocity u, v at the current time, and the
+                           force per unit depth Fx, Fy that set the last step's acceleration (COUPLED; zeros
+                           otherwise) */
 };
 
 /* Create a case, initialised to the uniform free stream at t = 0 (no

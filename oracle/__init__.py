@@ -19,7 +19,7 @@ SOURCES = [os.path.join(HERE, "oracle.c")]
 
 FLUID, SOLID, IB, G1, G2, G3 = range(6)
 BC_FREESTREAM, BC_OUTFLOW, BC_PERIODIC = range(3)
-MOTION_STATIC, MOTION_SIN, MOTION_CONST = range(3)
+MOTION_STATIC, MOTION_SIN, MOTION_CONST, MOTION_COUPLED = range(4)
 
 
 def build(force=False):
@@ -45,7 +45,7 @@ class _Params(ctypes.Structure):
         ("uinf", ctypes.c_double * 2), ("dt_fixed", ctypes.c_double), ("ref_len", ctypes.c_double),
         ("nv", ctypes.c_int), ("verts", ctypes.POINTER(ctypes.c_double)),
         ("motion", ctypes.c_int), ("amp", ctypes.c_double * 2), ("freq", ctypes.c_double),
-        ("vel", ctypes.c_double * 2),
+        ("vel", ctypes.c_double * 2), ("mass", ctypes.c_double),
         ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("dt_phys", ctypes.c_double),
         ("cfl_tau", ctypes.c_double),
     ]
@@ -81,6 +81,7 @@ def lib():
         L.orc_list_len.restype = ip
         L.orc_get_list.argtypes = [vp, ip, vp]
         L.orc_forces.argtypes = [vp, vp]
+        L.orc_body.argtypes = [vp, vp]
         L.orc_time.argtypes = [vp]
         L.orc_time.restype = dp
         L.orc_last_dt.argtypes = [vp]
@@ -131,6 +132,7 @@ class Case:
         P.amp[0], P.amp[1] = amp
         P.freq = s.get("freq", 0.0)
         P.vel[0], P.vel[1] = vel
+        P.mass = s.get("mass", 0.0)
         P.time_scheme = s.get("time_scheme", 0)
         P.subiters = s.get("subiters", 30)
         P.dt_phys = s.get("dt_phys", 0.0)
@@ -178,6 +180,13 @@ class Case:
 
     def time(self):
         return lib().orc_time(self.h)
+
+    def body(self):
+        """Body displacement (x, y), velocity (u, v) and the force per unit depth (Fx, Fy) that set the last
+        step's acceleration (coupled motion, Eq. 10)."""
+        out = np.zeros(6, np.float64)
+        lib().orc_body(self.h, _ptr(out))
+        return out
 
     def last_dt(self):
         return lib().orc_last_dt(self.h)

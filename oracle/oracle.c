@@ -49,17 +49,30 @@ struct orc_case {
   int classified;
   int nerr;
   double pos[2];           /* body displacement at the classification time */
+  /* body free to translate under the fluid force (Eq. 10): displacement, velocity and acceleration at bt, */
+  /* the start of the current step, and the force that set the acceleration                                */
+  double bX[2], bV[2], bA[2], bF[2], bt;
 };
 
 static inline int fidx(const orc_case *c, int i, int j) { return (j + NG) * c->W + (i + NG); }
 
 /* ------------------------------------------------------------------------- */
 /* body motion: prescribed translation (Sec. 8.2.2 oscillating cylinder;     */
-/* constant-velocity translation for the Galilean check of Sec. 8.2.3)       */
+/* constant-velocity translation for the Galilean check of Sec. 8.2.3), or   */
+/* translation under the fluid force (Sec. 6, Eq. 10): within a step the     */
+/* body moves with the constant acceleration set at the step's start         */
 /* ------------------------------------------------------------------------- */
-static void motion_at(const orc_params *p, double t, double X[2], double V[2], double Acc[2]) {
+static void motion_at(const orc_case *c, double t, double X[2], double V[2], double Acc[2]) {
+  const orc_params *p = &c->p;
   X[0] = X[1] = V[0] = V[1] = Acc[0] = Acc[1] = 0.0;
-  if (p->motion == ORC_MOTION_SIN) {
+  if (p->motion == ORC_MOTION_COUPLED) {
+    double tau = t - c->bt;
+    for (int k = 0; k < 2; k++) {
+      Acc[k] = c->bA[k];
+      V[k] = c->bV[k] + tau * c->bA[k];
+      X[k] = c->bX[k] + tau * c->bV[k] + 0.5 * tau * tau * c->bA[k];
+    }
+  } else if (p->motion == ORC_MOTION_SIN) {
     double w = 2.0 * M_PI * p->freq;
     double s = sin(w * t), co = cos(w * t);
     for (int k = 0; k < 2; k++) {
@@ -433,7 +446,7 @@ int orc_classify(orc_case *c) {
   const orc_params *p = &c->p;
   int nx = p->nx, ny = p->ny, nc = nx * ny;
   double X[2], V[2], Acc[2];
-  motion_at(p, c->t, X, V, Acc);
+  motion_at(c, c->t, X, V, Acc);
   c->pos[0] = X[0];
   c->pos[1] = X[1];
   for (int k = 0; k < p->nv; k++) {
@@ -548,7 +561,7 @@ static int supersonic_motion(const orc_case *c, const double V[2]) {
 
 static void reconstruct(orc_case *c, double *const U[4], double t) {
   double X[2], V[2], Acc[2];
-  motion_at(&c->p, t, X, V, Acc);
+  motion_at(c, t, X, V, Acc);
   int sup = supersonic_motion(c, V);
   reconstruct_set(c, U, c->list[0], c->nlist[0], V, Acc, sup);
   for (int k = 1; k < 4; k++) reconstruct_set(c, U, c->list[k], c->nlist[k], V, Acc, sup);
@@ -1013,6 +1026,16 @@ int orc_step(orc_case *c, int nsteps) {
   }
   for (int s = 0; s < nsteps; s++) {
     if (!c->classified || c->p.motion != ORC_MOTION_STATIC) orc_classify(c);
+    if (c->p.motion == ORC_MOTION_COUPLED) {
+      /* Eq. 10: the force on the body at t^n (its wall pressure carried with the previous acceleration) */
+      /* sets the acceleration of the step                                                                */
+      double f[4];
+      orc_forces(c, f);
+      for (int k = 0; k < 2; k++) {
+        c->bF[k] = f[2 + k];
+        c->bA[k] = f[2 + k] / c->p.mass;
+      }
+    }
     double dt = compute_dt(c);
     double t = c->t;
     double ts[3] = {t, t + dt, t + 0.5 * dt};
@@ -1026,8 +1049,25 @@ int orc_step(orc_case *c, int nsteps) {
     }
     c->t = t + dt;
     c->last_dt = dt;
+    if (c->p.motion == ORC_MOTION_COUPLED) {
+      /* Eq. 10 with the position advanced by the constant-acceleration step (the printed update lacks the */
+      /* factor 1/2 of the step's (dt)^2 term): x += U dt + dt^2 F / (2 M), U += dt F / M                   */
+      for (int k = 0; k < 2; k++) {
+        c->bX[k] = c->bX[k] + dt * c->bV[k] + 0.5 * dt * dt * c->bA[k];
+        c->bV[k] = c->bV[k] + dt * c->bA[k];
+      }
+      c->bt = c->t;
+    }
   }
   return c->nerr;
+}
+
+void orc_body(const orc_case *c, double out[6]) {
+  for (int k = 0; k < 2; k++) {
+    out[k] = c->bX[k];
+    out[2 + k] = c->bV[k];
+    out[4 + k] = c->bF[k];
+  }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1044,7 +1084,7 @@ void orc_forces(orc_case *c, double out[4]) {
   const orc_params *p = &c->p;
   if (!c->classified) orc_classify(c);
   double X[2], V[2], Acc[2];
-  motion_at(p, c->t, X, V, Acc);
+  motion_at(c, c->t, X, V, Acc);
   int sup = supersonic_motion(c, V);
   double sx = 0, cx = 0, sy = 0, cy = 0;
   for (int k = 0; k < p->nv; k++) {
@@ -1118,7 +1158,13 @@ orc_case *orc_create(const orc_params *pp) {
   if (nv > 0) build_normals(c);
   {
     double X[2], V[2], Acc[2];
-    motion_at(p, 0.0, X, V, Acc);
+    for (int k = 0; k < 2; k++) {
+      c->bX[k] = 0.0;
+      c->bV[k] = p->motion == ORC_MOTION_COUPLED ? p->vel[k] : 0.0;
+      c->bA[k] = c->bF[k] = 0.0;
+    }
+    c->bt = 0.0;
+    motion_at(c, 0.0, X, V, Acc);
     for (int k = 0; k < nv; k++) {
       c->vx[k] = c->vref[2 * k] + X[0];
       c->vy[k] = c->vref[2 * k + 1] + X[1];

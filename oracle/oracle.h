@@ -42,7 +42,7 @@ extern "C" {
 enum { ORC_FLUID = 0, ORC_SOLID = 1, ORC_IB = 2, ORC_G1 = 3, ORC_G2 = 4, ORC_G3 = 5 };
 /* domain sides: 0 x-low, 1 x-high, 2 y-low, 3 y-high */
 enum { ORC_BC_FREESTREAM = 0, ORC_BC_OUTFLOW = 1, ORC_BC_PERIODIC = 2 };
-enum { ORC_MOTION_STATIC = 0, ORC_MOTION_SIN = 1, ORC_MOTION_CONST = 2 };
+enum { ORC_MOTION_STATIC = 0, ORC_MOTION_SIN = 1, ORC_MOTION_CONST = 2, ORC_MOTION_COUPLED = 3 };
 enum { ORC_REGION_FACE = 0, ORC_REGION_VERTEX = 1, ORC_REGION_FALLBACK = 2 };
 enum { ORC_TIME_RK3 = 0, ORC_TIME_DUAL = 1 };
 
@@ -57,7 +57,8 @@ typedef struct {
   int nv;                  /* body vertices (closed CCW polyline); 0 = no body */
   const double *verts;     /* 2*nv, interleaved x,y; copied */
   int motion;
-  double amp[2], freq, vel[2];
+  double amp[2], freq, vel[2];  /* COUPLED: vel = initial body velocity */
+  double mass;                  /* COUPLED: body mass per unit depth (Eq. 10); RK3 only */
   int time_scheme;         /* ORC_TIME_RK3 or ORC_TIME_DUAL */
   int subiters;            /* dual time: pseudo-time sub-iterations per physical step */
   double dt_phys;          /* dual time: physical time step */
@@ -94,6 +95,7 @@ int orc_list_len(const orc_case *c, int kind);           /* 0 IB, 1..3 G1..G3 */
 void orc_get_list(const orc_case *c, int kind, orc_stencil *dst);
 void orc_forces(orc_case *c, double out[4]);             /* Cd, Cl, Fx, Fy */
 double orc_time(const orc_case *c);
+void orc_body(const orc_case *c, double out[6]);         /* displacement x, y; velocity u, v; last force Fx, Fy */
 double orc_last_dt(const orc_case *c);
 void orc_reconstruct(orc_case *c, double t);             /* IB + ghost fill at time t (one call of the stage step) */
 void orc_vertex_normals(const orc_case *c, double *dst); /* 2*nv */

@@ -168,7 +168,12 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
   if (!(fl->cfl > 0) && !(fl->dt_fixed > 0)) return fail(IBM_EINVAL, "cfl or dt_fixed must be positive");
   if (fl->precision != IBM_PREC_FP64 && fl->precision != IBM_PREC_FP32_BULK)
     return fail(IBM_EINVAL, "bad precision");
-  if (mo && (mo->kind < IBM_MOTION_STATIC || mo->kind > IBM_MOTION_CONST)) return fail(IBM_EINVAL, "bad motion");
+  if (mo && (mo->kind < IBM_MOTION_STATIC || mo->kind > IBM_MOTION_COUPLED)) return fail(IBM_EINVAL, "bad motion");
+  if (mo && mo->kind == IBM_MOTION_COUPLED) {
+    if (!(mo->mass > 0)) return fail(IBM_EINVAL, "a body moving under the fluid force needs mass > 0");
+    if (fl->time_scheme != IBM_TIME_RK3) return fail(IBM_EINVAL, "a body moving under the fluid force needs RK3");
+    if (geo->nverts == 0) return fail(IBM_EINVAL, "a body moving under the fluid force needs a body");
+  }
   if (fl->time_scheme != IBM_TIME_RK3 && fl->time_scheme != IBM_TIME_DUAL) return fail(IBM_EINVAL, "bad time scheme");
   if (fl->time_scheme == IBM_TIME_DUAL) {
     if (!(fl->dt_phys > 0) || !(fl->cfl_tau > 0) || fl->subiters < 1)
@@ -274,6 +279,7 @@ static void init_case(ibm_case *c, const ibm_geometry *geo, const ibm_grid *gr, 
     k.motion.vel[d] = mo ? mo->vel[d] : 0.0;
   }
   k.motion.freq = mo ? mo->freq : 0.0;
+  k.motion.mass = mo && mo->kind == IBM_MOTION_COUPLED ? mo->mass : 0.0;
   k.dual = fl->time_scheme == IBM_TIME_DUAL;
   k.subiters = fl->subiters;
   k.dt_phys = fl->dt_phys;
@@ -404,6 +410,8 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
       c->launches++;
     }
     std::memset(c->hds, 0, sizeof(DevState));
+    if (k.motion.kind == IBM_MOTION_COUPLED)
+      for (int d = 0; d < 2; d++) c->hds->bV[d] = k.motion.vel[d];  // at rest where it starts, moving at vel
     if (k.dt_fixed > 0.0 || k.dual) {
       c->hds->dt = k.dual ? k.dt_phys : k.dt_fixed;
       c->hds->dtf = (float)c->hds->dt;
@@ -563,6 +571,13 @@ static int enqueue_step(ibm_case *c) {
   }
   const bool f64 = c->precision == IBM_PREC_FP64;
   const bool fuse_cfl = fused_cfl(c);
+  const bool coupled = c->k.motion.kind == IBM_MOTION_COUPLED;
+  if (coupled) {  // Eq. 10: the force at the start of the step sets the body's acceleration for the step
+    prof_mark(c, 4, true);
+    launch_forces_f64(c->k, c->g, c->tag, c->A, !f64, c->ds, s, true);
+    prof_mark(c, 4, false);
+    nl += 1;
+  }
   prof_mark(c, 3, true);
   if (f64) launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
   else if (!fuse_cfl) launch_dt_f32(c->k, c->M, c->tag, c->ds, s, &nl);
@@ -575,6 +590,10 @@ static int enqueue_step(ibm_case *c) {
                     c->body_cap, c->ds, reinterpret_cast<StepSched *>(c->sch_words), fuse_cfl,
                     c->have_tmap && c->use_tma ? c->tmap : nullptr, c->step_variant, c->step_grid, 1, 3, s);
     prof_mark(c, 0, false);
+    if (coupled) {
+      launch_body_end(c->ds, s);
+      nl += 1;
+    }
     return nl + 1;
   }
   double *in64[3] = {c->A, c->B, c->C};
@@ -610,6 +629,12 @@ static int enqueue_step(ibm_case *c) {
       if (c->body_cap > 0) nl += 1;
     }
     prof_mark(c, 0, false);
+    nl += 1;
+  }
+  if (coupled) {  // Eq. 10: position and velocity over the step (t has advanced in stage 3)
+    prof_mark(c, 5, true);
+    launch_body_end(c->ds, s);
+    prof_mark(c, 5, false);
     nl += 1;
   }
   return nl;
@@ -784,7 +809,11 @@ extern "C" ibm_status ibm_step(ibm_case *c, int nsteps) {
 
 namespace ibm {
 
-bool case_batchable(const ibm_case *c) { return c->precision == IBM_PREC_FP32_BULK && !c->k.dual; }
+// batched groups run the explicit stages only: dual time and bodies moving under the fluid force (whose
+// steps add the force and the body update) advance on their own streams
+bool case_batchable(const ibm_case *c) {
+  return c->precision == IBM_PREC_FP32_BULK && !c->k.dual && c->k.motion.kind != IBM_MOTION_COUPLED;
+}
 
 ibm_status case_prepare_batch(ibm_case *c) {
   if (!c->classified) {
@@ -1032,6 +1061,15 @@ extern "C" ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t byt
       if (bytes < sizeof(int32_t) || dst_on_device) return fail(IBM_EINVAL, "IBM_STAGE_LAUNCH: host int32 destination");
       const int32_t v = c->precision == IBM_PREC_FP32_BULK ? c->stage_launch : -1;
       std::memcpy(dst, &v, sizeof v);
+      break;
+    }
+    case IBM_BODY: {
+      if (bytes < 6 * sizeof(double)) return fail(IBM_EINVAL, "dst too small");
+      const double b[6] = {h.bX[0], h.bX[1], h.bV[0], h.bV[1], h.bF[0], h.bF[1]};
+      if (dst_on_device) {
+        CU(cudaMemcpyAsync(dst, b, sizeof b, cudaMemcpyHostToDevice, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+      } else std::memcpy(dst, b, sizeof b);
       break;
     }
     default:

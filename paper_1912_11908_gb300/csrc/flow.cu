@@ -103,7 +103,7 @@ __device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const 
 __global__ void __launch_bounds__(1024) k_recon1_f64(Consts k, double *U, const ibm_stencil *__restrict__ st,
                                                      int cap, const DevState *__restrict__ ds, int stage) {
   double X[2], V[2], Acc[2];
-  motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
+  body_motion(k, ds, stage_time(ds, stage), X, V, Acc);
   const bool sup = supersonic_motion(k, V);
   const int nib = min(ds->offset[1], cap), tot = min(ds->offset[4], cap);
   for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup);
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128) k_recon_f64(Consts k, double *U, const ib
   const int e = lo + blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= hi) return;
   double X[2], V[2], Acc[2];
-  motion_at(k.motion, stage_time(ds, stage), X, V, Acc);
+  body_motion(k, ds, stage_time(ds, stage), X, V, Acc);
   recon_one_f64(k, U, st[e], V, Acc, supersonic_motion(k, V));
 }
 

@@ -73,7 +73,7 @@ __global__ void k_pose(Consts k, Geom g, DevState *ds) {
   __shared__ double X[2];
   if (threadIdx.x == 0) {
     double V[2], A[2], P[2];
-    motion_at(k.motion, ds->t, P, V, A);
+    body_motion(k, ds, ds->t, P, V, A);
     X[0] = P[0];
     X[1] = P[1];
     ds->pos[0] = P[0];
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(256) k_pose_classify(Consts k, Geom g, uint8_t
   const int nv = g.nv;
   if (threadIdx.x == 0) {
     double V[2], A[2], P[2];
-    motion_at(k.motion, ds->t, P, V, A);
+    body_motion(k, ds, ds->t, P, V, A);
     X[0] = P[0];
     X[1] = P[1];
   }
@@ -955,10 +955,11 @@ void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_ste
 // fixed-order tree reduction (deterministic).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint8_t *__restrict__ tag,
-                                                    const double *__restrict__ A, bool pert, DevState *ds) {
+                                                    const double *__restrict__ A, bool pert, DevState *ds,
+                                                    bool set_accel) {
   __shared__ double rx[256], ry[256];
   double V[2], Acc[2], X[2];
-  motion_at(k.motion, ds->t, X, V, Acc);
+  body_motion(k, ds, ds->t, X, V, Acc);
   const bool sup = supersonic_motion(k, V);
   double sx = 0.0, sy = 0.0;
   for (int e = threadIdx.x; e < g.nv; e += blockDim.x) {
@@ -1023,13 +1024,32 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
     ds->force[1] = ry[0] / q;
     ds->force[2] = rx[0];
     ds->force[3] = ry[0];
+    if (set_accel) {  // Eq. 10: this force sets the body's acceleration for the step
+      ds->bF[0] = rx[0];
+      ds->bF[1] = ry[0];
+      ds->bA[0] = rx[0] / k.motion.mass;
+      ds->bA[1] = ry[0] / k.motion.mass;
+    }
   }
 }
 
 void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, bool pert,
-                       DevState *ds, cudaStream_t s) {
-  k_forces_f64<<<1, 256, 0, s>>>(k, g, tag, A, pert, ds);
+                       DevState *ds, cudaStream_t s, bool set_accel) {
+  k_forces_f64<<<1, 256, 0, s>>>(k, g, tag, A, pert, ds, set_accel);
 }
+
+// Sec. 6, Eq. 10: end of a step of a body translating under the fluid force.  The step's constant
+// acceleration carries position and velocity over the step (dt of the step; t already advanced).
+__global__ void k_body_end(DevState *ds) {
+  const double dt = ds->dt;
+  for (int d = 0; d < 2; d++) {
+    ds->bX[d] = ds->bX[d] + dt * ds->bV[d] + 0.5 * dt * dt * ds->bA[d];
+    ds->bV[d] = ds->bV[d] + dt * ds->bA[d];
+  }
+  ds->bt = ds->t;
+}
+
+void launch_body_end(DevState *ds, cudaStream_t s) { k_body_end<<<1, 1, 0, s>>>(ds); }
 
 }  // namespace ibm
 

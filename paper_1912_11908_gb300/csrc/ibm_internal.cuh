@@ -38,6 +38,9 @@ struct DevState {
   double dt_next;                // persistent step kernel: dt of the next step, applied when the step ends
   float dtf_next;
   int pad2;
+  // body free to translate under the fluid force (Eq. 10): displacement, velocity and acceleration at bt, the
+  // start of the current step, and the force that set the acceleration
+  double bX[2], bV[2], bA[2], bF[2], bt;
 };
 
 // IB / ghost lists up to this capacity are rebuilt by a single 1024-thread
@@ -53,6 +56,7 @@ constexpr int ERR_TIMEOUT = 4;  // a bounded device wait (TMA completion) gave u
 struct Motion {
   int kind;
   double amp[2], freq, vel[2];
+  double mass;  // COUPLED: body mass per unit depth
 };
 
 // everything a kernel needs about the grid and the gas, passed by value
@@ -164,6 +168,23 @@ __device__ inline void motion_at(const Motion &m, double t, double X[2], double 
   }
 }
 
+// Body motion at time t: the prescribed forms, or, for a body translating
+// under the fluid force (Eq. 10), the constant-acceleration motion of the
+// current step from its start bt.
+__device__ inline void body_motion(const Consts &k, const DevState *ds, double t, double X[2], double V[2],
+                                   double A[2]) {
+  if (k.motion.kind == IBM_MOTION_COUPLED) {
+    const double tau = t - ds->bt;
+    for (int d = 0; d < 2; d++) {
+      A[d] = ds->bA[d];
+      V[d] = ds->bV[d] + tau * ds->bA[d];
+      X[d] = ds->bX[d] + tau * ds->bV[d] + 0.5 * tau * tau * ds->bA[d];
+    }
+    return;
+  }
+  motion_at(k.motion, t, X, V, A);
+}
+
 // Eq. 7 holds for a moving body whose speed relative to the free stream
 // exceeds the free-stream sound speed (c_inf^2 = gamma p_inf / rho_inf =
 // gamma R in the nondimensional gas).
@@ -200,8 +221,9 @@ int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_
                           RStencil32 *rs, int *sid, uint8_t *tile_body, int *body_tiles, int body_cap, int maxw,
                           int maxh, DevState *ds, cudaStream_t s);
 // A: FP64 state, absolute conserved (pert = false) or perturbation (pert = true)
+void launch_body_end(DevState *ds, cudaStream_t s);
 void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, bool pert,
-                       DevState *ds, cudaStream_t s);
+                       DevState *ds, cudaStream_t s, bool set_accel = false);
 
 // ---- launchers (flow.cu) ----
 void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch);

@@ -19,7 +19,8 @@
 // or a persistent grid striding over the table) by timing the candidates on
 // the group itself, once per size class and membership size.
 //
-// Other cases (FP64, dual time), and every case when batching is off, advance
+// Other cases (FP64, dual time, bodies moving under the fluid force), and every
+// case when batching is off, advance
 // on their own streams in chunks of steps replayed from their own graphs.
 //
 // A case that has taken all its steps is retired: its forces and time are

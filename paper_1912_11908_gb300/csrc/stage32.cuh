@@ -367,7 +367,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     double X[2], V[2], Acc[2];
     const double ts = DUAL ? ds->t + k.dt_phys
                            : (PERSIST ? stage_time(ds, STAGE) : (STAGE == 1 ? ds->t : ds->tst[STAGE - 2]));
-    motion_at(k.motion, ts, X, V, Acc);
+    body_motion(k, ds, ts, X, V, Acc);
     wm[0] = (float)V[0];
     wm[1] = (float)V[1];
     wm[2] = (float)Acc[0];

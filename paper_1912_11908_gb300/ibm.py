@@ -16,7 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libibm_gb300.so")
 
 IBM_OK, IBM_EINVAL, IBM_ENOMEM, IBM_ECAPACITY, IBM_ESTENCIL, IBM_ECUDA, IBM_ESTATE = range(7)
-IBM_STATE_FP64, IBM_TAGS, IBM_LIST_COUNTS, IBM_STENCILS, IBM_TIME, IBM_STEPS, IBM_TUNING, IBM_STAGE_LAUNCH = range(8)
+(IBM_STATE_FP64, IBM_TAGS, IBM_LIST_COUNTS, IBM_STENCILS, IBM_TIME, IBM_STEPS, IBM_TUNING, IBM_STAGE_LAUNCH,
+ IBM_BODY) = range(9)
 STATUS_NAMES = {0: "IBM_OK", 1: "IBM_EINVAL", 2: "IBM_ENOMEM", 3: "IBM_ECAPACITY", 4: "IBM_ESTENCIL",
                 5: "IBM_ECUDA", 6: "IBM_ESTATE"}
 
@@ -40,7 +41,7 @@ class ibm_flow(ctypes.Structure):
 
 class ibm_motion(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("amp", ctypes.c_double * 2), ("freq", ctypes.c_double),
-                ("vel", ctypes.c_double * 2)]
+                ("vel", ctypes.c_double * 2), ("mass", ctypes.c_double)]
 
 
 STENCIL_DTYPE = np.dtype([
@@ -176,6 +177,7 @@ def marshal(spec):
     mo.amp[0], mo.amp[1] = spec.get("amp", (0.0, 0.0))
     mo.freq = spec.get("freq", 0.0)
     mo.vel[0], mo.vel[1] = spec.get("vel", (0.0, 0.0))
+    mo.mass = spec.get("mass", 0.0)
     return verts, geo, gr, fl, mo
 
 
@@ -296,6 +298,13 @@ class Case:
         out = np.zeros(1, np.int32)
         _check(lib().ibm_get_state(self.h, IBM_STAGE_LAUNCH, out.ctypes.data_as(ctypes.c_void_p), 4, 0))
         return int(out[0])
+
+    def body(self):
+        """Body displacement (x, y), velocity (u, v) and the force per unit depth (Fx, Fy) that set the last
+        step's acceleration (motion under the fluid force, Eq. 10; zeros otherwise)."""
+        out = np.zeros(6, np.float64)
+        _check(lib().ibm_get_state(self.h, IBM_BODY, out.ctypes.data_as(ctypes.c_void_p), out.nbytes, 0))
+        return out
 
     def tuning(self):
         """Register-budget variants of the plain stage kernel: (stage 1, stages 2-3)."""

@@ -14,7 +14,7 @@ import math
 import numpy as np
 
 BC_FREESTREAM, BC_OUTFLOW, BC_PERIODIC = 0, 1, 2
-MOTION_STATIC, MOTION_SIN, MOTION_CONST = 0, 1, 2
+MOTION_STATIC, MOTION_SIN, MOTION_CONST, MOTION_COUPLED = 0, 1, 2, 3
 PREC_FP64, PREC_FP32_BULK = 0, 1
 TIME_RK3, TIME_DUAL = 0, 1
 
@@ -59,14 +59,14 @@ def wedge(half_angle_deg=15.0, chord=1.0):
 
 
 def case_spec(verts, nx, ny, domain, mach, re, bc, *, cfl=0.5, uinf=(1.0, 0.0), gamma=1.4, prandtl=0.72,
-              motion=MOTION_STATIC, amp=(0.0, 0.0), freq=0.0, vel=(0.0, 0.0), dt_fixed=0.0, ref_len=1.0,
+              motion=MOTION_STATIC, amp=(0.0, 0.0), freq=0.0, vel=(0.0, 0.0), mass=0.0, dt_fixed=0.0, ref_len=1.0,
               precision=PREC_FP64, time_scheme=TIME_RK3, subiters=30, dt_phys=0.0, cfl_tau=0.8, name=""):
     verts = np.zeros((0, 2)) if verts is None else np.ascontiguousarray(verts, np.float64)
     return dict(name=name, verts=verts, nx=int(nx), ny=int(ny), domain=tuple(float(v) for v in domain),
                 mach=float(mach), re=float(re), bc=tuple(int(b) for b in bc), cfl=float(cfl),
                 uinf=tuple(float(u) for u in uinf), gamma=float(gamma), prandtl=float(prandtl),
                 motion=int(motion), amp=tuple(float(a) for a in amp), freq=float(freq),
-                vel=tuple(float(v) for v in vel), dt_fixed=float(dt_fixed), ref_len=float(ref_len),
+                vel=tuple(float(v) for v in vel), mass=float(mass), dt_fixed=float(dt_fixed), ref_len=float(ref_len),
                 precision=int(precision), time_scheme=int(time_scheme), subiters=int(subiters),
                 dt_phys=float(dt_phys), cfl_tau=float(cfl_tau))
 
@@ -113,6 +113,41 @@ def stationary_cylinder_supersonic(mach_d=1.2, nx=1600, ny=640, length=40.0, hei
     verts = cylinder(256, 1.0, center=(upstream, 0.5 * height))
     return case_spec(verts, nx, ny, (0.0, length, 0.0, height), mach_d, 300.0, SUPERSONIC,
                      name="stationary_cylinder_M%g_Re300_%dx%d" % (mach_d, nx, ny), **kw)
+
+
+def shock_driven_cylinder(nx=656, ny=656, mach_s=1.5, density_ratio=10.0, shock_x=0.5, **kw):
+    """Planar shock driving a cylinder free to translate (Sec. 8.2.6), in diameters (D = 0.1 m) and in units of
+    the pre-shock gas (density 1, sound speed 1: reference Mach 1, gas at rest).  Domain 4 x 4 diameters
+    (0.4 m), centre (1.5, 2) D, D/164 on the paper's 656 x 656 grid; shock Mach 1.5 starting at x = 0.5 D and
+    moving along +x; inviscid.  The cylinder's mass per unit depth is density_ratio times that of the gas it
+    displaces.  Sides: zero-gradient behind the shock (left) and across it (bottom, top), gas at rest ahead."""
+    verts = cylinder(256, 1.0, center=(1.5, 2.0))
+    spec = case_spec(verts, nx, ny, (0.0, 4.0, 0.0, 4.0), 1.0, 0.0, (BC_OUTFLOW, BC_FREESTREAM, BC_OUTFLOW, BC_OUTFLOW),
+                     uinf=(0.0, 0.0), motion=MOTION_COUPLED, mass=density_ratio * math.pi * 0.25,
+                     name="shock_driven_cylinder_Ms%g_%dx%d" % (mach_s, nx, ny), **kw)
+    spec["shock"] = (float(shock_x), float(mach_s))
+    return spec
+
+
+def shock_initial_state(spec):
+    """Conserved state [4][ny][nx] of a planar shock at x = x_s moving along +x at Mach M_s into gas at rest
+    (density 1, pressure p_inf = 1 / (gamma M^2) of the spec): the Rankine-Hugoniot state behind it,
+    rho1 = (g+1) Ms^2 / ((g-1) Ms^2 + 2), p1 = p_inf (1 + 2g (Ms^2 - 1) / (g+1)), u1 = Ms c (1 - 1/rho1)."""
+    xs, ms = spec["shock"]
+    g = spec["gamma"]
+    p0 = 1.0 / (g * spec["mach"] ** 2)
+    c0 = math.sqrt(g * p0)
+    r1 = (g + 1.0) * ms * ms / ((g - 1.0) * ms * ms + 2.0)
+    p1 = p0 * (1.0 + 2.0 * g * (ms * ms - 1.0) / (g + 1.0))
+    u1 = ms * c0 * (1.0 - 1.0 / r1)
+    nx, ny = spec["nx"], spec["ny"]
+    x0, x1, _, _ = spec["domain"]
+    xc = x0 + (np.arange(nx) + 0.5) * (x1 - x0) / nx
+    behind = np.broadcast_to(xc < xs, (ny, nx))
+    r = np.where(behind, r1, 1.0)
+    u = np.where(behind, u1, 0.0)
+    p = np.where(behind, p1, p0)
+    return np.stack([r, r * u, np.zeros_like(r), p / (g - 1.0) + 0.5 * r * u * u])
 
 
 def naca0012_a5_m0001(nx=2048, ny=1024, **kw):
