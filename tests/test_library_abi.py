@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1912_11908_gb300 import workloads as W
@@ -58,3 +59,68 @@ def test_device_bytes_estimate(ibm):
     cells = 768 * 384
     assert 96 * cells < fp64 < 140 * cells
     assert fp32 < fp64
+
+
+def test_coupled_motion_arguments_rejected_without_gpu(ibm):
+    """A body moving under the fluid force needs a positive mass, the explicit scheme and a body."""
+    L = ibm.lib()
+    spec = W.shock_driven_cylinder(64, 64)
+    for bad in (dict(spec, mass=0.0), dict(spec, mass=-1.0), dict(spec, time_scheme=W.TIME_DUAL, dt_phys=0.01),
+                dict(spec, verts=np.zeros((0, 2))), dict(spec, motion=4)):
+        verts, geo, gr, fl, mo = ibm.marshal(bad)
+        h = ctypes.c_void_p()
+        st = L.ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), None,
+                               ctypes.byref(h))
+        assert st == ibm.IBM_EINVAL, bad
+        assert not h.value
+
+
+def _header_enums():
+    txt = open(os.path.join(ROOT, "include", "ibm.h")).read()
+    out = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", txt, re.S):
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        for name, val in re.findall(r"(IBM_\w+)\s*=\s*(\d+)", body):
+            out[name] = int(val)
+    return out
+
+
+def test_header_constants_match_the_binding(ibm):
+    """Every enum value the binding and the input generators use equals the header's."""
+    h = _header_enums()
+    for name in ("IBM_OK", "IBM_EINVAL", "IBM_ECAPACITY", "IBM_ESTENCIL", "IBM_STATE_FP64", "IBM_TAGS",
+                 "IBM_LIST_COUNTS", "IBM_STENCILS", "IBM_TIME", "IBM_STEPS", "IBM_TUNING", "IBM_STAGE_LAUNCH",
+                 "IBM_BODY"):
+        assert getattr(ibm, name) == h[name], name
+    pairs = {"MOTION_STATIC": "IBM_MOTION_STATIC", "MOTION_SIN": "IBM_MOTION_SIN", "MOTION_CONST": "IBM_MOTION_CONST",
+             "MOTION_COUPLED": "IBM_MOTION_COUPLED", "PREC_FP64": "IBM_PREC_FP64",
+             "PREC_FP32_BULK": "IBM_PREC_FP32_BULK", "TIME_RK3": "IBM_TIME_RK3", "TIME_DUAL": "IBM_TIME_DUAL",
+             "BC_FREESTREAM": "IBM_BC_FREESTREAM", "BC_OUTFLOW": "IBM_BC_OUTFLOW", "BC_PERIODIC": "IBM_BC_PERIODIC"}
+    for py, c in pairs.items():
+        assert getattr(W, py) == h[c], py
+
+
+def test_struct_layouts_match_the_header(ibm, tmp_path):
+    """sizeof and field offsets of the ABI structs, as a C compiler lays them out from the header, equal the
+    binding's ctypes layouts (a field added on one side only fails here)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {"ibm_geometry": ibm.ibm_geometry, "ibm_grid": ibm.ibm_grid, "ibm_flow": ibm.ibm_flow,
+               "ibm_motion": ibm.ibm_motion, "ibm_result": ibm.ibm_result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ibm.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f in cls._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert int(got["%s.%s" % (name, f[0])]) == getattr(cls, f[0]).offset, (name, f[0])
