@@ -45,7 +45,7 @@ class _Params(ctypes.Structure):
         ("uinf", ctypes.c_double * 2), ("dt_fixed", ctypes.c_double), ("ref_len", ctypes.c_double),
         ("nv", ctypes.c_int), ("verts", ctypes.POINTER(ctypes.c_double)),
         ("motion", ctypes.c_int), ("amp", ctypes.c_double * 2), ("freq", ctypes.c_double),
-        ("vel", ctypes.c_double * 2), ("mass", ctypes.c_double),
+        ("vel", ctypes.c_double * 2), ("mass", ctypes.c_double), ("ib_mode", ctypes.c_int),
         ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("dt_phys", ctypes.c_double),
         ("cfl_tau", ctypes.c_double),
     ]
@@ -133,6 +133,7 @@ class Case:
         P.freq = s.get("freq", 0.0)
         P.vel[0], P.vel[1] = vel
         P.mass = s.get("mass", 0.0)
+        P.ib_mode = s.get("ib_mode", 0)
         P.time_scheme = s.get("time_scheme", 0)
         P.subiters = s.get("subiters", 30)
         P.dt_phys = s.get("dt_phys", 0.0)

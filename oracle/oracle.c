@@ -56,6 +56,11 @@ struct orc_case {
 
 static inline int fidx(const orc_case *c, int i, int j) { return (j + NG) * c->W + (i + NG); }
 
+/* nodes the flux update advances: fluid nodes, and IB nodes when they are not rebuilt */
+static inline int advanced(const orc_case *c, uint8_t tag) {
+  return tag == ORC_FLUID || (tag == ORC_IB && c->p.ib_mode == ORC_IB_ADVANCE);
+}
+
 /* ------------------------------------------------------------------------- */
 /* body motion: prescribed translation (Sec. 8.2.2 oscillating cylinder;     */
 /* constant-velocity translation for the Galilean check of Sec. 8.2.3), or   */
@@ -563,7 +568,7 @@ static void reconstruct(orc_case *c, double *const U[4], double t) {
   double X[2], V[2], Acc[2];
   motion_at(c, t, X, V, Acc);
   int sup = supersonic_motion(c, V);
-  reconstruct_set(c, U, c->list[0], c->nlist[0], V, Acc, sup);
+  if (c->p.ib_mode != ORC_IB_ADVANCE) reconstruct_set(c, U, c->list[0], c->nlist[0], V, Acc, sup);
   for (int k = 1; k < 4; k++) reconstruct_set(c, U, c->list[k], c->nlist[k], V, Acc, sup);
 }
 
@@ -831,7 +836,7 @@ static void stage_update(orc_case *c, int stage, double *const Un[4], double *co
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < ny; j++)
     for (int i = 0; i < nx; i++) {
-      if (c->tag[j * nx + i] != ORC_FLUID) continue;
+      if (!advanced(c, c->tag[j * nx + i])) continue;
       int m = fidx(c, i, j), mw = fidx(c, i - 1, j), ms = fidx(c, i, j - 1);
       for (int v = 0; v < 4; v++) {
         double L = -((c->fx[v][m] - c->fx[v][mw]) / c->dx + (c->fy[v][m] - c->fy[v][ms]) / c->dy);
@@ -852,7 +857,7 @@ static double compute_dt(orc_case *c) {
   double lmax = 0.0, g = p->gamma;
   for (int j = 0; j < p->ny; j++)
     for (int i = 0; i < p->nx; i++) {
-      if (c->tag[j * p->nx + i] != ORC_FLUID) continue;
+      if (!advanced(c, c->tag[j * p->nx + i])) continue;
       int m = fidx(c, i, j);
       double q[4];
       cons_to_prim(c, c->A[0][m], c->A[1][m], c->A[2][m], c->A[3][m], q);
@@ -949,7 +954,7 @@ static void dual_update(orc_case *c, int stage, double *const In[4], double *con
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < ny; j++)
     for (int i = 0; i < nx; i++) {
-      if (c->tag[j * nx + i] != ORC_FLUID) continue;
+      if (!advanced(c, c->tag[j * nx + i])) continue;
       int m = fidx(c, i, j), mw = fidx(c, i - 1, j), ms = fidx(c, i, j - 1);
       double W[4], Q[4], S[4];
       for (int v = 0; v < 4; v++) W[v] = In[v][m];

@@ -43,6 +43,11 @@ enum { ORC_FLUID = 0, ORC_SOLID = 1, ORC_IB = 2, ORC_G1 = 3, ORC_G2 = 4, ORC_G3 
 /* domain sides: 0 x-low, 1 x-high, 2 y-low, 3 y-high */
 enum { ORC_BC_FREESTREAM = 0, ORC_BC_OUTFLOW = 1, ORC_BC_PERIODIC = 2 };
 enum { ORC_MOTION_STATIC = 0, ORC_MOTION_SIN = 1, ORC_MOTION_CONST = 2, ORC_MOTION_COUPLED = 3 };
+/* IB nodes: rebuilt from their probes every stage (Sec. 4.4-4.6, the fluid-side nodes of Fig. 1 / Fig. 6),   */
+/* or advanced by the flux update like fluid nodes, the wall then imposed by the rebuilt ghost layers alone    */
+/* (Sec. 5's field extension).  The second holds normal shocks on blunt bodies where the first lets the mass   */
+/* the upwind flux carries into a rebuilt node vanish (M >= 2 stagnation).                                     */
+enum { ORC_IB_REBUILD = 0, ORC_IB_ADVANCE = 1 };
 enum { ORC_REGION_FACE = 0, ORC_REGION_VERTEX = 1, ORC_REGION_FALLBACK = 2 };
 enum { ORC_TIME_RK3 = 0, ORC_TIME_DUAL = 1 };
 
@@ -59,6 +64,7 @@ typedef struct {
   int motion;
   double amp[2], freq, vel[2];  /* COUPLED: vel = initial body velocity */
   double mass;                  /* COUPLED: body mass per unit depth (Eq. 10); RK3 only */
+  int ib_mode;                  /* ORC_IB_REBUILD or ORC_IB_ADVANCE */
   int time_scheme;         /* ORC_TIME_RK3 or ORC_TIME_DUAL */
   int subiters;            /* dual time: pseudo-time sub-iterations per physical step */
   double dt_phys;          /* dual time: physical time step */

@@ -175,6 +175,7 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
     if (geo->nverts == 0) return fail(IBM_EINVAL, "a body moving under the fluid force needs a body");
   }
   if (fl->time_scheme != IBM_TIME_RK3 && fl->time_scheme != IBM_TIME_DUAL) return fail(IBM_EINVAL, "bad time scheme");
+  if (fl->ib_mode != IBM_IB_REBUILD) return fail(IBM_EINVAL, "only IBM_IB_REBUILD is built on the GPU");
   if (fl->time_scheme == IBM_TIME_DUAL) {
     if (!(fl->dt_phys > 0) || !(fl->cfl_tau > 0) || fl->subiters < 1)
       return fail(IBM_EINVAL, "dual time needs dt_phys > 0, cfl_tau > 0, subiters >= 1");

@@ -35,7 +35,7 @@ class ibm_flow(ctypes.Structure):
     _fields_ = [("mach", ctypes.c_double), ("re", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("prandtl", ctypes.c_double), ("cfl", ctypes.c_double), ("uinf", ctypes.c_double * 2),
                 ("dt_fixed", ctypes.c_double), ("ref_len", ctypes.c_double), ("precision", ctypes.c_int),
-                ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("ib_mode", ctypes.c_int),
                 ("dt_phys", ctypes.c_double), ("cfl_tau", ctypes.c_double)]
 
 
@@ -172,6 +172,7 @@ def marshal(spec):
     fl.subiters = spec.get("subiters", 30)
     fl.dt_phys = spec.get("dt_phys", 0.0)
     fl.cfl_tau = spec.get("cfl_tau", 0.8)
+    fl.ib_mode = spec.get("ib_mode", W.IB_REBUILD)
     mo = ibm_motion()
     mo.kind = spec.get("motion", W.MOTION_STATIC)
     mo.amp[0], mo.amp[1] = spec.get("amp", (0.0, 0.0))

@@ -95,7 +95,8 @@ def test_header_constants_match_the_binding(ibm):
     pairs = {"MOTION_STATIC": "IBM_MOTION_STATIC", "MOTION_SIN": "IBM_MOTION_SIN", "MOTION_CONST": "IBM_MOTION_CONST",
              "MOTION_COUPLED": "IBM_MOTION_COUPLED", "PREC_FP64": "IBM_PREC_FP64",
              "PREC_FP32_BULK": "IBM_PREC_FP32_BULK", "TIME_RK3": "IBM_TIME_RK3", "TIME_DUAL": "IBM_TIME_DUAL",
-             "BC_FREESTREAM": "IBM_BC_FREESTREAM", "BC_OUTFLOW": "IBM_BC_OUTFLOW", "BC_PERIODIC": "IBM_BC_PERIODIC"}
+             "BC_FREESTREAM": "IBM_BC_FREESTREAM", "BC_OUTFLOW": "IBM_BC_OUTFLOW", "BC_PERIODIC": "IBM_BC_PERIODIC",
+             "IB_REBUILD": "IBM_IB_REBUILD", "IB_ADVANCE": "IBM_IB_ADVANCE"}
     for py, c in pairs.items():
         assert getattr(W, py) == h[c], py
 
@@ -124,3 +125,13 @@ def test_struct_layouts_match_the_header(ibm, tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for f in cls._fields_:
             assert int(got["%s.%s" % (name, f[0])]) == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_ib_advance_mode_is_oracle_only(ibm):
+    """IBM_IB_ADVANCE is defined by the oracle; the library refuses it instead of ignoring it."""
+    L = ibm.lib()
+    verts, geo, gr, fl, mo = ibm.marshal(dict(W.cylinder_m02_re40(64, 32), ib_mode=W.IB_ADVANCE))
+    h = ctypes.c_void_p()
+    st = L.ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), None,
+                           ctypes.byref(h))
+    assert st == ibm.IBM_EINVAL and not h.value
