@@ -175,7 +175,9 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
     if (geo->nverts == 0) return fail(IBM_EINVAL, "a body moving under the fluid force needs a body");
   }
   if (fl->time_scheme != IBM_TIME_RK3 && fl->time_scheme != IBM_TIME_DUAL) return fail(IBM_EINVAL, "bad time scheme");
-  if (fl->ib_mode != IBM_IB_REBUILD) return fail(IBM_EINVAL, "only IBM_IB_REBUILD is built on the GPU");
+  if (fl->ib_mode != IBM_IB_REBUILD && fl->ib_mode != IBM_IB_ADVANCE) return fail(IBM_EINVAL, "bad ib_mode");
+  if (fl->ib_mode == IBM_IB_ADVANCE && fl->precision != IBM_PREC_FP64)
+    return fail(IBM_EINVAL, "IBM_IB_ADVANCE is built for the FP64 path only");
   if (fl->time_scheme == IBM_TIME_DUAL) {
     if (!(fl->dt_phys > 0) || !(fl->cfl_tau > 0) || fl->subiters < 1)
       return fail(IBM_EINVAL, "dual time needs dt_phys > 0, cfl_tau > 0, subiters >= 1");
@@ -282,6 +284,7 @@ static void init_case(ibm_case *c, const ibm_geometry *geo, const ibm_grid *gr, 
   k.motion.freq = mo ? mo->freq : 0.0;
   k.motion.mass = mo && mo->kind == IBM_MOTION_COUPLED ? mo->mass : 0.0;
   k.dual = fl->time_scheme == IBM_TIME_DUAL;
+  k.ib_advance = fl->ib_mode == IBM_IB_ADVANCE;
   k.subiters = fl->subiters;
   k.dt_phys = fl->dt_phys;
   k.idt_phys = fl->dt_phys > 0.0 ? 1.0 / fl->dt_phys : 0.0;

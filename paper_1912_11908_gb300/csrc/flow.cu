@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(256) k_dt(Consts k, const double *__restrict__
   double lmax = 0.0;
   const double vis = (2.0 * k.gamma * k.mu / k.prandtl) * (1.0 / (k.dx * k.dx) + 1.0 / (k.dy * k.dy));
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ncell; n += gridDim.x * blockDim.x) {
-    if (tag[n] != FLUID) continue;
+    if (tag[n] != FLUID && !(k.ib_advance && tag[n] == IB)) continue;
     long long id = cidx(k, n % k.nx, n / k.nx);
     double r = A[id], u = A[id + k.plane] / r, v = A[id + 2 * k.plane] / r;
     double p = (k.gamma - 1.0) * (A[id + 3 * k.plane] - 0.5 * r * (u * u + v * v));
@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(1024) k_recon1_f64(Consts k, double *U, const 
   body_motion(k, ds, stage_time(ds, stage), X, V, Acc);
   const bool sup = supersonic_motion(k, V);
   const int nib = min(ds->offset[1], cap), tot = min(ds->offset[4], cap);
-  for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup);
+  if (!k.ib_advance)  // IB nodes rebuilt (else advanced by the flux update)
+    for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup);
   __syncthreads();
   for (int e = nib + threadIdx.x; e < tot; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup);
 }
@@ -132,9 +133,12 @@ void launch_recon_f64(const Consts &k, double *U, const ibm_stencil *st, int cap
     return;
   }
   int blocks = (cap + 127) / 128;
-  k_recon_f64<<<blocks, 128, 0, s>>>(k, U, st, cap, ds, stage, 0);
+  if (!k.ib_advance) {  // IB nodes rebuilt (else advanced by the flux update)
+    k_recon_f64<<<blocks, 128, 0, s>>>(k, U, st, cap, ds, stage, 0);
+    *nlaunch += 1;
+  }
   k_recon_f64<<<blocks, 128, 0, s>>>(k, U, st, cap, ds, stage, 1);
-  *nlaunch += 2;
+  *nlaunch += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -313,7 +317,8 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int ci = i0 + tx, cj = j0 + ty;
   const bool inside = ci < k.nx && cj < k.ny;
-  const bool fluid = inside && tag[cj * k.nx + ci] == FLUID;
+  // cells the flux update advances: fluid cells, and IB nodes when the ghost layers alone impose the wall
+  const bool fluid = inside && (tag[cj * k.nx + ci] == FLUID || (k.ib_advance && tag[cj * k.nx + ci] == IB));
   const double dt = ds->dt;
   if (!DUAL && STAGE == 3 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     // end of the step (no other kernel of this stage reads t)
