@@ -70,7 +70,7 @@ enum { IBM_MOTION_STATIC = 0, IBM_MOTION_SIN = 1, IBM_MOTION_CONST = 2, IBM_MOTI
 /* arithmetic: FP64 throughout, or FP32 bulk (stage values and fluxes in FP32
  * on perturbations from the free stream, FP64 state accumulation) */
 enum { IBM_PREC_FP64 = 0, IBM_PREC_FP32_BULK = 1 };
-/* IB nodes (ibm_flow.ib_mode): rebuilt every stage, or advanced by the flux update (FP64 only) */
+/* IB nodes (ibm_flow.ib_mode): rebuilt every stage, or advanced by the flux update */
 enum { IBM_IB_REBUILD = 0, IBM_IB_ADVANCE = 1 };
 /* time stepping: explicit SSP-RK3 with the CFL rule, or dual time (Sec. 2):
  * three-point (BDF2) physical-time derivative, preconditioned pseudo time,
@@ -107,7 +107,7 @@ typedef struct {
   int subiters;     /* dual time: pseudo-time sub-iterations per physical step (>= 1) */
   int ib_mode;      /* IBM_IB_REBUILD: IB nodes rebuilt from their probes every stage (Sec. 4.4-4.6);
                        IBM_IB_ADVANCE: IB nodes advanced by the flux update, the wall imposed by the ghost
-                       layers alone (Sec. 5) -- FP64 precision only (IBM_EINVAL with FP32 bulk) */
+                       layers alone (Sec. 5) -- not with FP32-bulk dual time (IBM_EINVAL) */
   double dt_phys;   /* dual time: physical time step (> 0) */
   double cfl_tau;   /* dual time: pseudo-time CFL number (> 0) */
 } ibm_flow;

@@ -176,8 +176,8 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
   }
   if (fl->time_scheme != IBM_TIME_RK3 && fl->time_scheme != IBM_TIME_DUAL) return fail(IBM_EINVAL, "bad time scheme");
   if (fl->ib_mode != IBM_IB_REBUILD && fl->ib_mode != IBM_IB_ADVANCE) return fail(IBM_EINVAL, "bad ib_mode");
-  if (fl->ib_mode == IBM_IB_ADVANCE && fl->precision != IBM_PREC_FP64)
-    return fail(IBM_EINVAL, "IBM_IB_ADVANCE is built for the FP64 path only");
+  if (fl->ib_mode == IBM_IB_ADVANCE && fl->precision != IBM_PREC_FP64 && fl->time_scheme == IBM_TIME_DUAL)
+    return fail(IBM_EINVAL, "IBM_IB_ADVANCE is not built for FP32-bulk dual time");
   if (fl->time_scheme == IBM_TIME_DUAL) {
     if (!(fl->dt_phys > 0) || !(fl->cfl_tau > 0) || fl->subiters < 1)
       return fail(IBM_EINVAL, "dual time needs dt_phys > 0, cfl_tau > 0, subiters >= 1");

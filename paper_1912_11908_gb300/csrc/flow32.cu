@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256) k_dt_f32(Consts k, PertConsts c, const fl
     for (int j = blockIdx.y * 8 + (threadIdx.x >> 5); j < k.ny; j += gridDim.y * 8) {
       const long long id = cidx(k, i, j);
       const float dr = M[id], mx = M[id + P], my = M[id + 2 * P], w = M[id + 3 * P];
-      if (tag[j * k.nx + i] == FLUID) {
+      if (tag[j * k.nx + i] == FLUID || (k.ib_advance && tag[j * k.nx + i] == IB)) {
         float u, v, pp, Tp;
         pert_prim(c, dr, mx, my, w, u, v, pp, Tp);
         const float r = 1.f + dr;

@@ -71,7 +71,7 @@ struct Consts {
   int bc[4];
   Motion motion;
   int dual;         // dual time stepping (preconditioned pseudo time, BDF2 physical time)
-  int ib_advance;   // IB nodes advanced by the flux update (FP64 path); the ghost layers alone impose the wall
+  int ib_advance;   // IB nodes advanced by the flux update; the ghost layers alone impose the wall
   int subiters;     // dual time: sub-iterations per physical step
   double dt_phys;   // dual time: physical step
   double cfl_tau;   // dual time: pseudo-time CFL number

@@ -356,7 +356,8 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
   const int ci = i0 + tx, cj = j0 + ty;
   const bool inside = ci < k.nx && cj < k.ny;
   const uint8_t mytag = inside ? tag[cj * k.nx + ci] : (uint8_t)SOLID;
-  const bool fluid = mytag == FLUID;
+  // cells the flux update advances: fluid cells, and IB nodes when the ghost layers alone impose the wall
+  const bool fluid = mytag == FLUID || (k.ib_advance && mytag == IB);
   // stages 1 and 3 also keep the IB / ghost nodes of U^n current; stage 2 only needs fluid cells
   const bool work = STAGE == 2 ? fluid : (mytag != SOLID);
   if (!__syncthreads_or(work)) {
@@ -451,7 +452,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     // nodes); corners inside the loaded region come from shared memory
     // four lanes per node, one stencil corner each, so that corners outside the loaded region (chains of
     // dependent global loads) overlap; the node's first lane sums the corners in stencil order
-    for (int pass = 0; pass < 2; pass++) {
+    for (int pass = k.ib_advance ? 1 : 0; pass < 2; pass++) {  // IB nodes (pass 0) unless advanced
       for (int t0 = 0; t0 < 4 * nrb; t0 += 256) {  // block-uniform: every lane takes part in the shuffles
         const int r = (t0 + (int)threadIdx.x) >> 2, cq = threadIdx.x & 3;
         bool node = false;
@@ -470,7 +471,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
             } else {
               // corner outside the loaded region: fluid value, or an IB node rebuilt from its own stencil
               const int e2 = pass == 1 ? sid[cn] : -1;
-              if (e2 >= 0 && (rs[e2].mask & 15)) rebuild_ib<PERSIST>(k, c, In, rs[e2], wm, v4);
+              if (!k.ib_advance && e2 >= 0 && (rs[e2].mask & 15)) rebuild_ib<PERSIST>(k, c, In, rs[e2], wm, v4);
               else raw_prim<PERSIST>(c, In, st.corner + (cq & 1) + (cq >> 1) * k.pitch, P, v4);
             }
           }

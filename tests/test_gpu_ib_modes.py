@@ -41,3 +41,28 @@ def test_ib_advance_fp64_parity(ibm, orc, name, spec_fn, nsteps):
     err = _state_err(g.state(), o.state(), o.tags())
     assert err <= 1e-10, err
     np.testing.assert_allclose(g.forces(), o.forces(), rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("name,spec_fn,nsteps", [
+    ("cylinder_M2_192x96", lambda p: W.stationary_cylinder_supersonic(2.0, 192, 96, length=24.0, height=12.0,
+                                                                     upstream=6.0, ib_mode=W.IB_ADVANCE,
+                                                                     precision=p), 150),
+    ("osc_cylinder_128x64", lambda p: dict(W.oscillating_cylinder_m02_re185(128, 64, ib_mode=W.IB_ADVANCE,
+                                                                            precision=p),
+                                           amp=(0.0, 0.6), freq=0.5), 60),
+])
+def test_ib_advance_fp32_bulk_vs_fp64_oracle(ibm, orc, name, spec_fn, nsteps):
+    """FP32-bulk body tiles skip the IB rebuild and advance IB nodes: forces within 1e-3 of the FP64 oracle,
+    state within 1e-3 of the deviation scale."""
+    g, o = ibm.Case(spec_fn(W.PREC_FP32_BULK)), orc.Case(spec_fn(W.PREC_FP64))
+    g.step(nsteps)
+    o.step(nsteps)
+    np.testing.assert_array_equal(g.tags(), o.tags())
+    fg, fo = g.forces(), o.forces()
+    assert abs(fg[0] - fo[0]) <= 1e-3 and abs(fg[1] - fo[1]) <= 1e-3, (fg, fo)
+    a, b = g.state(), o.state()
+    live = (o.tags() == 0) | (o.tags() == 2)
+    for k in range(4):
+        ref = b[k][live]
+        dev = np.abs(ref - np.median(ref)).max() + 1e-300
+        assert np.abs(a[k][live] - ref).max() <= 1e-3 * dev, k

@@ -127,11 +127,11 @@ def test_struct_layouts_match_the_header(ibm, tmp_path):
             assert int(got["%s.%s" % (name, f[0])]) == getattr(cls, f[0]).offset, (name, f[0])
 
 
-def test_ib_advance_mode_refused_on_the_fp32_bulk_path(ibm):
-    """IBM_IB_ADVANCE is built for the FP64 path; the FP32-bulk path refuses it instead of ignoring it."""
+def test_ib_advance_mode_refused_with_fp32_bulk_dual_time(ibm):
+    """IBM_IB_ADVANCE is not built for FP32-bulk dual time; the library refuses it instead of ignoring it."""
     L = ibm.lib()
     verts, geo, gr, fl, mo = ibm.marshal(dict(W.cylinder_m02_re40(64, 32, precision=W.PREC_FP32_BULK),
-                                              ib_mode=W.IB_ADVANCE))
+                                              ib_mode=W.IB_ADVANCE, time_scheme=W.TIME_DUAL, dt_phys=0.01))
     h = ctypes.c_void_p()
     st = L.ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), None,
                            ctypes.byref(h))
