@@ -518,7 +518,48 @@ def cpu_baseline(args, cells_gpu=None, sample_s=10.0, max_steps=400):
         n += 1
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": cells * 3 * n / t / 1e6, "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
-            "sample": "%d RK3 steps of %s after 1 warm-up step (%.1f s)" % (n, spec["name"], t)}
+            "sample": "%d RK3 steps of %s after 1 warm-up step (%.1f s)" % (n, spec["name"], t),
+            "cpu_model": _cpu_model(), "nproc": os.cpu_count(),
+            "single_core": _oracle_single_core(args.workload)}
+
+
+def _cpu_model():
+    """The host CPU's model line from /proc/cpuinfo (x86 "model name"; Arm implementer / part), else the machine."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        for key in ("model name", "Model", "CPU part"):
+            for line in info.splitlines():
+                if line.startswith(key):
+                    val = line.split(":", 1)[1].strip()
+                    return "%s %s" % (platform.machine(), val) if key == "CPU part" else val
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def _oracle_single_core(workload, sample_s=3.0, max_steps=100):
+    """The oracle on one host core (OMP_NUM_THREADS=1 in a child process), a short sample; None if it fails."""
+    code = ("import sys, time; sys.path.insert(0, %r)\n"
+            "import oracle, bench\n"
+            "spec = bench._spec(%r, 'fp64')\n"
+            "oracle.build()\n"
+            "c = oracle.Case(spec)\n"
+            "c.step(1)\n"
+            "cells = int((c.tags() != 1).sum())\n"
+            "n, t = 0, 0.0\n"
+            "while t < %r and n < %d:\n"
+            "    t0 = time.perf_counter(); c.step(1); t += time.perf_counter() - t0; n += 1\n"
+            "print(cells * 3 * n / t / 1e6, n, t)\n") % (ROOT, workload, sample_s, max_steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+        v, n, t = out.stdout.split()
+        return {"value": float(v), "unit": "Mcell-updates/s", "cores": 1,
+                "sample": "%s RK3 steps (%.1f s)" % (n, float(t))}
+    except Exception:
+        return None
 
 
 def run_reference(args, rank, world):
