@@ -111,25 +111,30 @@ def _mean_drag(case, t_end, t_avg, chunk=50):
             return float(np.mean(samples)), float(np.std(samples))
 
 
-def test_galilean_invariance_moving_vs_stationary(ibm):
-    """Sec. 8.2.3 at M_D = 1.2, Re_D = 300: the mean drag over t = 24-30 of the cylinder moving through gas at
-    rest (40 x 12 diameters) against that of the cylinder at rest in the stream (24 x 12 diameters), at D/16
-    and D/32.  The wall conditions differ between the two by design: the moving body's carries the Eq. 7
-    gradient over the probe distance, the body at rest (Eq. 6) none, so the two drags differ by a first-order
-    term in h.  Measured with the oracle: -6.83% at D/16, -3.38% at D/32.  Bounds: the difference halves with
-    h (ratio <= 0.6), and its extrapolation to h = 0 (2 d_32 - d_16, measured 0.07%) is within 1%."""
+@pytest.mark.parametrize("mach_d,ib_mode,extrap_bound", [(1.2, W.IB_REBUILD, 0.01), (2.0, W.IB_ADVANCE, 0.02)])
+def test_galilean_invariance_moving_vs_stationary(ibm, mach_d, ib_mode, extrap_bound):
+    """Sec. 8.2.3, Re_D = 300: the mean drag over t = 24-30 of the cylinder moving through gas at rest (40 x 12
+    diameters) against that of the cylinder at rest in the stream (24 x 12 diameters), at D/16 and D/32.  The
+    wall conditions differ between the two by design: the moving body's carries the Eq. 7 gradient over the
+    probe distance, the body at rest (Eq. 6) none, so the two drags differ by a first-order term in h.
+    Measured with the oracle: M_D 1.2, -6.83% at D/16, -3.38% at D/32, extrapolated (2 d_32 - d_16) 0.07%;
+    M_D 2.0 with IB nodes advanced by the flux update (the rebuilt nodes do not hold the bow shock there),
+    -6.23% and -2.47%, extrapolated 1.3%.  Bounds: the difference shrinks like h (ratio <= 0.6) and its
+    extrapolation to h = 0 is within 1% (M 1.2) or 2% (M 2)."""
     t_end, t_avg = 30.0, 6.0
     d = {}
     for res in (16, 32):
-        mv = ibm.Case(W.moving_cylinder_supersonic(1.2, 40 * res, 12 * res, length=40.0, height=12.0, start=4.0))
-        st = ibm.Case(W.stationary_cylinder_supersonic(1.2, 24 * res, 12 * res, length=24.0, height=12.0,
-                                                       upstream=6.0))
+        mv = ibm.Case(W.moving_cylinder_supersonic(mach_d, 40 * res, 12 * res, length=40.0, height=12.0, start=4.0,
+                                                   ib_mode=ib_mode))
+        st = ibm.Case(W.stationary_cylinder_supersonic(mach_d, 24 * res, 12 * res, length=24.0, height=12.0,
+                                                       upstream=6.0, ib_mode=ib_mode))
         cd_m, sd_m = _mean_drag(mv, t_end, t_avg)
         cd_s, sd_s = _mean_drag(st, t_end, t_avg)
-        print("D/%d  Cd moving %.5f (+-%.5f)  stationary %.5f (+-%.5f)" % (res, cd_m, sd_m, cd_s, sd_s))
-        assert 1.3 < cd_s < 1.8  # cylinder at M 1.2, Re 300: bow shock and wake
+        print("M_D=%g D/%d  Cd moving %.5f (+-%.5f)  stationary %.5f (+-%.5f)" % (mach_d, res, cd_m, sd_m, cd_s,
+                                                                                  sd_s))
+        assert 1.3 < cd_s < 1.8  # cylinder at M 1.2-2, Re 300: bow shock and wake
         d[res] = (cd_m - cd_s) / cd_s
         mv.close()
         st.close()
     assert abs(d[32]) <= 0.6 * abs(d[16]), d
-    assert abs(2.0 * d[32] - d[16]) <= 0.01, d
+    assert abs(2.0 * d[32] - d[16]) <= extrap_bound, d
