@@ -19,7 +19,7 @@ SOURCES = [os.path.join(HERE, "oracle.c")]
 
 FLUID, SOLID, IB, G1, G2, G3 = range(6)
 BC_FREESTREAM, BC_OUTFLOW, BC_PERIODIC = range(3)
-MOTION_STATIC, MOTION_SIN, MOTION_CONST, MOTION_COUPLED = range(4)
+MOTION_STATIC, MOTION_SIN, MOTION_CONST, MOTION_COUPLED, MOTION_PITCH = range(5)
 
 
 def build(force=False):
@@ -46,6 +46,7 @@ class _Params(ctypes.Structure):
         ("nv", ctypes.c_int), ("verts", ctypes.POINTER(ctypes.c_double)),
         ("motion", ctypes.c_int), ("amp", ctypes.c_double * 2), ("freq", ctypes.c_double),
         ("vel", ctypes.c_double * 2), ("mass", ctypes.c_double), ("ib_mode", ctypes.c_int),
+        ("pivot", ctypes.c_double * 2), ("pitch_mean", ctypes.c_double), ("pitch_amp", ctypes.c_double),
         ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("dt_phys", ctypes.c_double),
         ("cfl_tau", ctypes.c_double),
     ]
@@ -134,6 +135,9 @@ class Case:
         P.vel[0], P.vel[1] = vel
         P.mass = s.get("mass", 0.0)
         P.ib_mode = s.get("ib_mode", 0)
+        P.pivot[0], P.pivot[1] = s.get("pivot", (0.0, 0.0))
+        P.pitch_mean = s.get("pitch_mean", 0.0)
+        P.pitch_amp = s.get("pitch_amp", 0.0)
         P.time_scheme = s.get("time_scheme", 0)
         P.subiters = s.get("subiters", 30)
         P.dt_phys = s.get("dt_phys", 0.0)

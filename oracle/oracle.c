@@ -52,6 +52,7 @@ struct orc_case {
   /* body free to translate under the fluid force (Eq. 10): displacement, velocity and acceleration at bt, */
   /* the start of the current step, and the force that set the acceleration                                */
   double bX[2], bV[2], bA[2], bF[2], bt;
+  double *snx0, *sny0, *vnx0, *vny0;  /* PITCH: normals of the reference pose */
 };
 
 static inline int fidx(const orc_case *c, int i, int j) { return (j + NG) * c->W + (i + NG); }
@@ -91,6 +92,34 @@ static void motion_at(const orc_case *c, double t, double X[2], double V[2], dou
       V[k] = p->vel[k];
     }
   }
+}
+
+/* pitching rotation (Sec. 7.2): body angle theta = -alpha(t) (counter-clockwise positive), its rate and     */
+/* its acceleration                                                                                         */
+static void pitch_at(const orc_case *c, double t, double *th, double *om, double *al) {
+  const orc_params *p = &c->p;
+  double w = 2.0 * M_PI * p->freq;
+  *th = -(p->pitch_mean - p->pitch_amp * cos(w * t));
+  *om = -p->pitch_amp * w * sin(w * t);
+  *al = -p->pitch_amp * w * w * cos(w * t);
+}
+
+/* wall velocity and acceleration at the surface point (px, py): the translation's, plus for a pitching body  */
+/* the rigid rotation about the pivot, V = om x r and A = al x r - om^2 r                                      */
+static void wall_kin(const orc_case *c, double t, double px, double py, const double V0[2], const double A0[2],
+                     double V[2], double A[2]) {
+  if (c->p.motion != ORC_MOTION_PITCH) {
+    V[0] = V0[0]; V[1] = V0[1];
+    A[0] = A0[0]; A[1] = A0[1];
+    return;
+  }
+  double th, om, al;
+  pitch_at(c, t, &th, &om, &al);
+  double rx = px - c->p.pivot[0], ry = py - c->p.pivot[1];
+  V[0] = V0[0] - om * ry;
+  V[1] = V0[1] + om * rx;
+  A[0] = A0[0] - al * ry - om * om * rx;
+  A[1] = A0[1] + al * rx - om * om * ry;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -454,9 +483,25 @@ int orc_classify(orc_case *c) {
   motion_at(c, c->t, X, V, Acc);
   c->pos[0] = X[0];
   c->pos[1] = X[1];
-  for (int k = 0; k < p->nv; k++) {
-    c->vx[k] = c->vref[2 * k] + X[0];
-    c->vy[k] = c->vref[2 * k + 1] + X[1];
+  if (p->motion == ORC_MOTION_PITCH) {
+    /* rotate the reference pose and its normals about the pivot */
+    double th, om, al;
+    pitch_at(c, c->t, &th, &om, &al);
+    double cs = cos(th), sn = sin(th);
+    for (int k = 0; k < p->nv; k++) {
+      double rx = c->vref[2 * k] - p->pivot[0], ry = c->vref[2 * k + 1] - p->pivot[1];
+      c->vx[k] = p->pivot[0] + (cs * rx - sn * ry);
+      c->vy[k] = p->pivot[1] + (sn * rx + cs * ry);
+      c->snx[k] = cs * c->snx0[k] - sn * c->sny0[k];
+      c->sny[k] = sn * c->snx0[k] + cs * c->sny0[k];
+      c->vnx[k] = cs * c->vnx0[k] - sn * c->vny0[k];
+      c->vny[k] = sn * c->vnx0[k] + cs * c->vny0[k];
+    }
+  } else {
+    for (int k = 0; k < p->nv; k++) {
+      c->vx[k] = c->vref[2 * k] + X[0];
+      c->vy[k] = c->vref[2 * k + 1] + X[1];
+    }
   }
   uint8_t *solid = calloc(nc, 1);
   if (p->nv > 0) {
@@ -523,11 +568,13 @@ static inline void prim_to_cons(const orc_case *c, const double q[4], double U[4
 /* IB nodes first (their probes use fluid nodes only), then all ghost layers */
 /* (their image points may use the freshly updated IB nodes).                */
 /* ------------------------------------------------------------------------- */
-static void reconstruct_set(orc_case *c, double *const U[4], const orc_stencil *s, int n, const double Vw[2],
-                            const double Aw[2], int supersonic) {
+static void reconstruct_set(orc_case *c, double *const U[4], const orc_stencil *s, int n, const double Vb[2],
+                            const double Ab[2], int supersonic, double t) {
   for (int e = 0; e < n; e++) {
     const orc_stencil *st = &s[e];
     if (st->mask == 0) continue;
+    double Vw[2], Aw[2];
+    wall_kin(c, t, st->bx, st->by, Vb, Ab, Vw, Aw);  /* the wall's motion at P' */
     double qp[4] = {0, 0, 0, 0};
     for (int k = 0; k < 4; k++) {
       if (!(st->mask >> k & 1)) continue;
@@ -568,8 +615,8 @@ static void reconstruct(orc_case *c, double *const U[4], double t) {
   double X[2], V[2], Acc[2];
   motion_at(c, t, X, V, Acc);
   int sup = supersonic_motion(c, V);
-  if (c->p.ib_mode != ORC_IB_ADVANCE) reconstruct_set(c, U, c->list[0], c->nlist[0], V, Acc, sup);
-  for (int k = 1; k < 4; k++) reconstruct_set(c, U, c->list[k], c->nlist[k], V, Acc, sup);
+  if (c->p.ib_mode != ORC_IB_ADVANCE) reconstruct_set(c, U, c->list[0], c->nlist[0], V, Acc, sup, t);
+  for (int k = 1; k < 4; k++) reconstruct_set(c, U, c->list[k], c->nlist[k], V, Acc, sup, t);
 }
 
 void orc_reconstruct(orc_case *c, double t) {
@@ -1118,13 +1165,15 @@ void orc_forces(orc_case *c, double out[4]) {
       for (int v = 0; v < 4; v++) qp[v] += w[kk] * qk[v];
     }
     /* wall pressure: the probe's, carried to the surface by the wall condition of the reconstruction */
-    double G = -(nx * Acc[0] + ny * Acc[1]);
+    double Vs[2], As[2];
+    wall_kin(c, c->t, mx, my, V, Acc, Vs, As);  /* the wall's motion at the segment midpoint */
+    double G = -(nx * As[0] + ny * As[1]);
     if (sup) {
-      double ut = (qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty;
+      double ut = (qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty;
       G = G + ut * ut * (0.5 * (c->vk[k] + c->vk[k1]));
     }
     double ps = qp[0] * exp(-xi * G / (c->R * qp[3]));
-    double tau = c->mu * ((qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty) / xi;
+    double tau = c->mu * ((qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty) / xi;
     double fx = (-(ps - c->pinf) * nx + tau * tx) * L;
     double fy = (-(ps - c->pinf) * ny + tau * ty) * L;
     double y1 = fx - cx, t1 = sx + y1;
@@ -1161,6 +1210,16 @@ orc_case *orc_create(const orc_params *pp) {
   c->vny = calloc(nv > 0 ? nv : 1, sizeof(double));
   c->vk = calloc(nv > 0 ? nv : 1, sizeof(double));
   if (nv > 0) build_normals(c);
+  if (nv > 0 && p->motion == ORC_MOTION_PITCH) {  /* reference normals, rotated at every classification */
+    c->snx0 = malloc(nv * sizeof(double));
+    c->sny0 = malloc(nv * sizeof(double));
+    c->vnx0 = malloc(nv * sizeof(double));
+    c->vny0 = malloc(nv * sizeof(double));
+    memcpy(c->snx0, c->snx, nv * sizeof(double));
+    memcpy(c->sny0, c->sny, nv * sizeof(double));
+    memcpy(c->vnx0, c->vnx, nv * sizeof(double));
+    memcpy(c->vny0, c->vny, nv * sizeof(double));
+  }
   {
     double X[2], V[2], Acc[2];
     for (int k = 0; k < 2; k++) {
@@ -1219,6 +1278,7 @@ void orc_destroy(orc_case *c) {
   }
   for (int k = 0; k < 4; k++) free(c->list[k]);
   free(c->tag); free(c->vref); free(c->vx); free(c->vy); free(c->snx); free(c->sny); free(c->vnx); free(c->vny); free(c->vk);
+  free(c->snx0); free(c->sny0); free(c->vnx0); free(c->vny0);
   free(c);
 }
 

@@ -42,7 +42,7 @@ extern "C" {
 enum { ORC_FLUID = 0, ORC_SOLID = 1, ORC_IB = 2, ORC_G1 = 3, ORC_G2 = 4, ORC_G3 = 5 };
 /* domain sides: 0 x-low, 1 x-high, 2 y-low, 3 y-high */
 enum { ORC_BC_FREESTREAM = 0, ORC_BC_OUTFLOW = 1, ORC_BC_PERIODIC = 2 };
-enum { ORC_MOTION_STATIC = 0, ORC_MOTION_SIN = 1, ORC_MOTION_CONST = 2, ORC_MOTION_COUPLED = 3 };
+enum { ORC_MOTION_STATIC = 0, ORC_MOTION_SIN = 1, ORC_MOTION_CONST = 2, ORC_MOTION_COUPLED = 3, ORC_MOTION_PITCH = 4 };
 /* IB nodes: rebuilt from their probes every stage (Sec. 4.4-4.6, the fluid-side nodes of Fig. 1 / Fig. 6),   */
 /* or advanced by the flux update like fluid nodes, the wall then imposed by the rebuilt ghost layers alone    */
 /* (Sec. 5's field extension).  The second holds normal shocks on blunt bodies where the first lets the mass   */
@@ -65,6 +65,9 @@ typedef struct {
   double amp[2], freq, vel[2];  /* COUPLED: vel = initial body velocity */
   double mass;                  /* COUPLED: body mass per unit depth (Eq. 10); RK3 only */
   int ib_mode;                  /* ORC_IB_REBUILD or ORC_IB_ADVANCE */
+  /* PITCH (Sec. 7.2): rotation about `pivot`, angle of attack alpha(t) = pitch_mean - pitch_amp cos(2 pi freq t) */
+  /* (radians, nose up = clockwise); the given vertices are the body at alpha = 0                                 */
+  double pivot[2], pitch_mean, pitch_amp;
   int time_scheme;         /* ORC_TIME_RK3 or ORC_TIME_DUAL */
   int subiters;            /* dual time: pseudo-time sub-iterations per physical step */
   double dt_phys;          /* dual time: physical time step */

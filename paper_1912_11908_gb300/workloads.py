@@ -14,7 +14,7 @@ import math
 import numpy as np
 
 BC_FREESTREAM, BC_OUTFLOW, BC_PERIODIC = 0, 1, 2
-MOTION_STATIC, MOTION_SIN, MOTION_CONST, MOTION_COUPLED = 0, 1, 2, 3
+MOTION_STATIC, MOTION_SIN, MOTION_CONST, MOTION_COUPLED, MOTION_PITCH = 0, 1, 2, 3, 4  # PITCH: CPU oracle only
 PREC_FP64, PREC_FP32_BULK = 0, 1
 IB_REBUILD, IB_ADVANCE = 0, 1
 TIME_RK3, TIME_DUAL = 0, 1
@@ -150,6 +150,19 @@ def shock_initial_state(spec):
     u = np.where(behind, u1, 0.0)
     p = np.where(behind, p1, p0)
     return np.stack([r, r * u, np.zeros_like(r), p / (g - 1.0) + 0.5 * r * u * u])
+
+
+def pitching_naca0012(nx=425, ny=317, mean_deg=30.0, amp_deg=15.0, freq=0.1, mach=0.006, re=3000.0, **kw):
+    """NACA0012 pitching about mid-chord (Sec. 7.2): alpha(t) = mean - amp cos(2 pi f t), reduced frequency
+    f* = f C / U = 0.1, Re 3000, M 0.006, domain 40C x 30C on the paper's 425 x 317 nodes (here uniform cells).
+    The vertices are the airfoil at alpha = 0; the pose rotates them about the pivot (0.5, 0).  Dual time
+    (explicit steps would be acoustically limited at this Mach number)."""
+    kw.setdefault("time_scheme", TIME_DUAL)
+    kw.setdefault("dt_phys", 0.5 * 40.0 / nx)
+    spec = case_spec(naca00xx(0.12, 400, 0.0), nx, ny, (-10.0, 30.0, -15.0, 15.0), mach, re, FAR,
+                     motion=MOTION_PITCH, freq=freq, name="pitching_naca0012_%dx%d" % (nx, ny), **kw)
+    spec.update(pivot=(0.5, 0.0), pitch_mean=math.radians(mean_deg), pitch_amp=math.radians(amp_deg))
+    return spec
 
 
 def naca0012_a5_m0001(nx=2048, ny=1024, **kw):
