@@ -47,6 +47,7 @@ class _Params(ctypes.Structure):
         ("motion", ctypes.c_int), ("amp", ctypes.c_double * 2), ("freq", ctypes.c_double),
         ("vel", ctypes.c_double * 2), ("mass", ctypes.c_double), ("ib_mode", ctypes.c_int),
         ("pivot", ctypes.c_double * 2), ("pitch_mean", ctypes.c_double), ("pitch_amp", ctypes.c_double),
+        ("scheme", ctypes.c_int),
         ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("dt_phys", ctypes.c_double),
         ("cfl_tau", ctypes.c_double),
     ]
@@ -92,6 +93,8 @@ def lib():
         L.orc_closest.argtypes = [vp, dp, dp, vp, vp, vp, vp, vp]
         L.orc_classify_points.argtypes = [ip, vp, ip, vp, vp]
         L.orc_weno5.argtypes = [vp]
+        L.orc_tvd2.argtypes = [vp]
+        L.orc_tvd2.restype = dp
         L.orc_weno5.restype = dp
         L.orc_ldfss_xflux.argtypes = [vp, vp, dp, dp, dp, vp]
         L.orc_euler_xflux.argtypes = [vp, dp, dp, vp]
@@ -138,6 +141,7 @@ class Case:
         P.pivot[0], P.pivot[1] = s.get("pivot", (0.0, 0.0))
         P.pitch_mean = s.get("pitch_mean", 0.0)
         P.pitch_amp = s.get("pitch_amp", 0.0)
+        P.scheme = s.get("scheme", 0)
         P.time_scheme = s.get("time_scheme", 0)
         P.subiters = s.get("subiters", 30)
         P.dt_phys = s.get("dt_phys", 0.0)
@@ -224,6 +228,11 @@ def classify_points(verts, pts):
 def weno5(f):
     f = np.ascontiguousarray(f, np.float64)
     return lib().orc_weno5(_ptr(f))
+
+
+def tvd2(f):
+    f = np.ascontiguousarray(f, np.float64)
+    return lib().orc_tvd2(_ptr(f))
 
 
 def ldfss_xflux(qL, qR, gamma, R, mr2=1.0):

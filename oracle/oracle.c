@@ -656,6 +656,20 @@ static void domain_bc(orc_case *c, double *const U[4]) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Sec. 2: second-order TVD reconstruction (MUSCL with the minmod limiter;   */
+/* the paper names the scheme, not its limiter).  f = values at i-1..i+1;    */
+/* returns the left-biased value at face i+1/2: f_i + 1/2 minmod of the two  */
+/* one-sided differences.                                                    */
+/* ------------------------------------------------------------------------- */
+double orc_tvd2(const double f[3]) {
+  double a = f[1] - f[0], b = f[2] - f[1];
+  double m = 0.0;
+  if (a > 0.0 && b > 0.0) m = a < b ? a : b;
+  else if (a < 0.0 && b < 0.0) m = a > b ? a : b;
+  return f[1] + 0.5 * m;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Sec. 2: fifth-order WENO (Jiang-Shu smoothness indicators, linear weights */
 /* 1/10, 6/10, 3/10, eps = 1e-6).  f = values at i-2..i+2; returns the       */
 /* left-biased value at face i+1/2.                                          */
@@ -791,8 +805,15 @@ static double face_mr2(const orc_case *c, const double qL[4], const double qR[4]
  * Reading: the paper iterates (p, u, v, w, T) but does not say which set WENO
  * acts on; (rho, u, v, p) keeps a density wave at fifth order because every
  * flux component is affine in rho when u and p are uniform. */
-static void face_states(const double s[6][4], double qL[4], double qR[4]) {
+static void face_states(const orc_case *c, const double s[6][4], double qL[4], double qR[4]) {
   for (int v = 0; v < 4; v++) {
+    if (c->p.scheme == ORC_SCHEME_TVD2) {
+      double fl[3] = {s[1][v], s[2][v], s[3][v]};
+      double fr[3] = {s[4][v], s[3][v], s[2][v]};
+      qL[v] = orc_tvd2(fl);
+      qR[v] = orc_tvd2(fr);
+      continue;
+    }
     double fl[5] = {s[0][v], s[1][v], s[2][v], s[3][v], s[4][v]};
     double fr[5] = {s[5][v], s[4][v], s[3][v], s[2][v], s[1][v]};
     qL[v] = orc_weno5(fl);
@@ -830,7 +851,7 @@ static void residual_faces(orc_case *c, double *const U[4]) {
       for (int k = 0; k < 6; k++)
         for (int v = 0; v < 4; v++) s[k][v] = Q[v][fidx(c, i - 2 + k, j)];
       double qL[4], qR[4], F[4];
-      face_states(s, qL, qR);
+      face_states(c, s, qL, qR);
       ldfss(qL, qR, 1.0, 0.0, g, R, cpv, face_mr2(c, qL, qR, c->dx), F);
       int a = fidx(c, i, j), b = fidx(c, i + 1, j);
       int an = fidx(c, i, j + 1), as = fidx(c, i, j - 1), bn = fidx(c, i + 1, j + 1), bs = fidx(c, i + 1, j - 1);
@@ -854,7 +875,7 @@ static void residual_faces(orc_case *c, double *const U[4]) {
       for (int k = 0; k < 6; k++)
         for (int v = 0; v < 4; v++) s[k][v] = Q[v][fidx(c, i, j - 2 + k)];
       double qL[4], qR[4], F[4];
-      face_states(s, qL, qR);
+      face_states(c, s, qL, qR);
       ldfss(qL, qR, 0.0, 1.0, g, R, cpv, face_mr2(c, qL, qR, c->dy), F);
       int a = fidx(c, i, j), b = fidx(c, i, j + 1);
       int ae = fidx(c, i + 1, j), aw = fidx(c, i - 1, j), be = fidx(c, i + 1, j + 1), bw = fidx(c, i - 1, j + 1);

@@ -48,6 +48,7 @@ enum { ORC_MOTION_STATIC = 0, ORC_MOTION_SIN = 1, ORC_MOTION_CONST = 2, ORC_MOTI
 /* (Sec. 5's field extension).  The second holds normal shocks on blunt bodies where the first lets the mass   */
 /* the upwind flux carries into a rebuilt node vanish (M >= 2 stagnation).                                     */
 enum { ORC_IB_REBUILD = 0, ORC_IB_ADVANCE = 1 };
+enum { ORC_SCHEME_WENO5 = 0, ORC_SCHEME_TVD2 = 1 };
 enum { ORC_REGION_FACE = 0, ORC_REGION_VERTEX = 1, ORC_REGION_FALLBACK = 2 };
 enum { ORC_TIME_RK3 = 0, ORC_TIME_DUAL = 1 };
 
@@ -68,6 +69,7 @@ typedef struct {
   /* PITCH (Sec. 7.2): rotation about `pivot`, angle of attack alpha(t) = pitch_mean - pitch_amp cos(2 pi freq t) */
   /* (radians, nose up = clockwise); the given vertices are the body at alpha = 0                                 */
   double pivot[2], pitch_mean, pitch_amp;
+  int scheme;                   /* ORC_SCHEME_WENO5 or ORC_SCHEME_TVD2 (Sec. 2: either reconstruction) */
   int time_scheme;         /* ORC_TIME_RK3 or ORC_TIME_DUAL */
   int subiters;            /* dual time: pseudo-time sub-iterations per physical step */
   double dt_phys;          /* dual time: physical time step */
@@ -114,6 +116,7 @@ void orc_closest(const orc_case *c, double px, double py, int32_t *feature, int3
 /* pure kernels exposed for pins; flux states are (rho, u, v, p) */
 void orc_classify_points(int nv, const double *verts, int np, const double *pts, uint8_t *solid);
 double orc_weno5(const double f[5]);
+double orc_tvd2(const double f[3]);
 void orc_ldfss_xflux(const double qL[4], const double qR[4], double gamma, double R,
                      double mr2_fixed, double flux[4]);
 void orc_euler_xflux(const double q[4], double gamma, double R, double flux[4]);

@@ -173,6 +173,8 @@ def marshal(spec):
     fl.dt_phys = spec.get("dt_phys", 0.0)
     fl.cfl_tau = spec.get("cfl_tau", 0.8)
     fl.ib_mode = spec.get("ib_mode", W.IB_REBUILD)
+    if spec.get("scheme", W.SCHEME_WENO5) != W.SCHEME_WENO5:
+        raise ValueError("the GPU library builds the WENO5 reconstruction only")
     mo = ibm_motion()
     mo.kind = spec.get("motion", W.MOTION_STATIC)
     mo.amp[0], mo.amp[1] = spec.get("amp", (0.0, 0.0))
