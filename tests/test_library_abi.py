@@ -136,3 +136,9 @@ def test_ib_advance_mode_refused_with_fp32_bulk_dual_time(ibm):
     st = L.ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), None,
                            ctypes.byref(h))
     assert st == ibm.IBM_EINVAL and not h.value
+
+
+def test_binding_refuses_the_oracle_only_reconstruction(ibm):
+    """The TVD-2 reconstruction exists in the oracle only: the binding refuses it instead of ignoring it."""
+    with pytest.raises(ValueError):
+        ibm.marshal(dict(W.cylinder_m02_re40(64, 32), scheme=W.SCHEME_TVD2))
