@@ -92,6 +92,7 @@ def lib():
         L.orc_vertex_normals.argtypes = [vp, vp]
         L.orc_closest.argtypes = [vp, dp, dp, vp, vp, vp, vp, vp]
         L.orc_classify_points.argtypes = [ip, vp, ip, vp, vp]
+        L.orc_classify_points_3d.argtypes = [ip, vp, ip, vp, ip, vp, vp]
         L.orc_weno5.argtypes = [vp]
         L.orc_tvd2.argtypes = [vp]
         L.orc_tvd2.restype = dp
@@ -215,6 +216,17 @@ class Case:
         lib().orc_closest(self.h, x, y, ctypes.byref(f), ctypes.byref(r), ctypes.byref(cx), ctypes.byref(cy),
                           ctypes.byref(d2))
         return f.value, r.value, cx.value, cy.value, d2.value
+
+
+def classify_points_3d(verts, tris, pts):
+    """Ray-casting classification against a closed triangulated surface (1 = solid)."""
+    verts = np.ascontiguousarray(verts, np.float64).reshape(-1, 3)
+    tris = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
+    pts = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
+    out = np.zeros(pts.shape[0], np.uint8)
+    lib().orc_classify_points_3d(verts.shape[0], _ptr(verts), tris.shape[0], _ptr(tris), pts.shape[0], _ptr(pts),
+                                 _ptr(out))
+    return out
 
 
 def classify_points(verts, pts):

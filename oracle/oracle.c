@@ -173,6 +173,60 @@ void orc_classify_points(int nv, const double *verts, int np, const double *pts,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Sec. 3.2, 3-D: ray casting against a closed triangulated surface with the  */
+/* Moller-Trumbore ray/triangle test (barycentric u, v and distance t from a  */
+/* 3x3 system solved by Cramer's rule).  Reading: a ray through an edge or a  */
+/* vertex can count twice (inclusive barycentric bounds) or not at all, so    */
+/* three fixed rays (+x and two oblique directions) are cast and the parity   */
+/* of the majority decides; nodes outside the axis-aligned bounding box are   */
+/* fluid.                                                                     */
+/* ------------------------------------------------------------------------- */
+static int ray_parity_3d(int ntri, const double *v, const int *tri, const double o[3], const double d[3]) {
+  int hits = 0;
+  for (int f = 0; f < ntri; f++) {
+    const double *a = v + 3 * tri[3 * f], *b = v + 3 * tri[3 * f + 1], *c = v + 3 * tri[3 * f + 2];
+    double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double pv[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2], d[0] * e2[1] - d[1] * e2[0]};
+    double det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+    if (det == 0.0) continue; /* ray parallel to the triangle's plane */
+    double tv[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
+    double u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) / det;
+    if (u < 0.0 || u > 1.0) continue;
+    double qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
+    double w = (d[0] * qv[0] + d[1] * qv[1] + d[2] * qv[2]) / det;
+    if (w < 0.0 || u + w > 1.0) continue;
+    double t = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) / det;
+    if (t > 0.0) hits++;
+  }
+  return hits & 1;
+}
+
+void orc_classify_points_3d(int nv, const double *verts, int ntri, const int *tris, int np, const double *pts,
+                            uint8_t *solid) {
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int k = 0; k < nv; k++)
+    for (int a = 0; a < 3; a++) {
+      if (verts[3 * k + a] < lo[a]) lo[a] = verts[3 * k + a];
+      if (verts[3 * k + a] > hi[a]) hi[a] = verts[3 * k + a];
+    }
+  /* +x and two oblique unit directions with irrational-looking components (no grid or mesh alignment) */
+  static const double dirs[3][3] = {{1.0, 0.0, 0.0},
+                                    {0.5773502691896258, 0.5773502691896258, -0.5773502691896258},
+                                    {-0.2672612419124244, 0.5345224838248488, 0.8017837257372732}};
+  for (int n = 0; n < np; n++) {
+    const double *o = pts + 3 * n;
+    if (o[0] < lo[0] || o[0] > hi[0] || o[1] < lo[1] || o[1] > hi[1] || o[2] < lo[2] || o[2] > hi[2]) {
+      solid[n] = 0;
+      continue;
+    }
+    int votes = 0;
+    for (int r = 0; r < 3; r++) votes += ray_parity_3d(ntri, verts, tris, o, dirs[r]);
+    solid[n] = (uint8_t)(votes >= 2);
+  }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Sec. 4.2: pseudo-normals.  Segment k runs from vertex k to k+1 of a CCW   */
 /* polyline; its outward normal is the travel direction turned clockwise.    */
 /* In 2-D each vertex has two incident segments that enter Eq. 2 with equal  */

@@ -115,6 +115,9 @@ void orc_closest(const orc_case *c, double px, double py, int32_t *feature, int3
 
 /* pure kernels exposed for pins; flux states are (rho, u, v, p) */
 void orc_classify_points(int nv, const double *verts, int np, const double *pts, uint8_t *solid);
+/* 3-D: closed triangulated surface (verts 3*nv, outward-oriented triangles 3*ntri), points 3*np */
+void orc_classify_points_3d(int nv, const double *verts, int ntri, const int *tris, int np, const double *pts,
+                            uint8_t *solid);
 double orc_weno5(const double f[5]);
 double orc_tvd2(const double f[3]);
 void orc_ldfss_xflux(const double qL[4], const double qR[4], double gamma, double R,

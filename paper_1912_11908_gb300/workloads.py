@@ -175,6 +175,32 @@ def naca0012_a5_m0001(nx=2048, ny=1024, **kw):
                      name="naca0012_a5_M0.001_Re1000_%dx%d" % (nx, ny), **kw)
 
 
+def uv_sphere(n_lat=21, n_lon=30, radius=1.0, center=(0.0, 0.0, 0.0)):
+    """Closed triangulated sphere (Appendix A: 1200 triangles for 21 x 30): two poles and n_lat - 1 rings of
+    n_lon vertices; triangles counter-clockwise seen from outside."""
+    verts = [(0.0, 0.0, radius)]
+    for i in range(1, n_lat):
+        th = math.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2.0 * math.pi * j / n_lon
+            verts.append((radius * math.sin(th) * math.cos(ph), radius * math.sin(th) * math.sin(ph),
+                          radius * math.cos(th)))
+    verts.append((0.0, 0.0, -radius))
+    south = len(verts) - 1
+    ring = lambda i, j: 1 + (i - 1) * n_lon + (j % n_lon)  # noqa: E731
+    tris = []
+    for j in range(n_lon):
+        tris.append((0, ring(1, j), ring(1, j + 1)))
+    for i in range(1, n_lat - 1):
+        for j in range(n_lon):
+            a, b, c, d = ring(i, j), ring(i, j + 1), ring(i + 1, j), ring(i + 1, j + 1)
+            tris.append((a, c, d))
+            tris.append((a, d, b))
+    for j in range(n_lon):
+        tris.append((south, ring(n_lat - 1, j + 1), ring(n_lat - 1, j)))
+    return np.array(verts) + np.array(center), np.array(tris, dtype=np.int32)
+
+
 def random_polygon(rng, n, center=(0.0, 0.0), rmin=0.3, rmax=1.0):
     """Star-shaped random polygon (CCW) for brute-force classification checks."""
     a = np.sort(rng.uniform(0.0, 2.0 * math.pi, n))
