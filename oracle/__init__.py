@@ -93,6 +93,7 @@ def lib():
         L.orc_closest.argtypes = [vp, dp, dp, vp, vp, vp, vp, vp]
         L.orc_classify_points.argtypes = [ip, vp, ip, vp, vp]
         L.orc_classify_points_3d.argtypes = [ip, vp, ip, vp, ip, vp, vp]
+        L.orc_closest_3d.argtypes = [ip, vp, ip, vp, ip, vp, vp, vp, vp]
         L.orc_weno5.argtypes = [vp]
         L.orc_tvd2.argtypes = [vp]
         L.orc_tvd2.restype = dp
@@ -227,6 +228,19 @@ def classify_points_3d(verts, tris, pts):
     lib().orc_classify_points_3d(verts.shape[0], _ptr(verts), tris.shape[0], _ptr(tris), pts.shape[0], _ptr(pts),
                                  _ptr(out))
     return out
+
+
+def closest_3d(verts, tris, pts):
+    """Closest surface point, its pseudo-normal and the feature kind (0 face, 1 edge, 2 vertex) per point."""
+    verts = np.ascontiguousarray(verts, np.float64).reshape(-1, 3)
+    tris = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
+    pts = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
+    cp = np.zeros_like(pts)
+    nrm = np.zeros_like(pts)
+    kind = np.zeros(pts.shape[0], np.int32)
+    lib().orc_closest_3d(verts.shape[0], _ptr(verts), tris.shape[0], _ptr(tris), pts.shape[0], _ptr(pts), _ptr(cp),
+                         _ptr(nrm), _ptr(kind))
+    return cp, nrm, kind
 
 
 def classify_points(verts, pts):

@@ -227,6 +227,123 @@ void orc_classify_points_3d(int nv, const double *verts, int ntri, const int *tr
 }
 
 /* ------------------------------------------------------------------------- */
+/* Sec. 4.1-4.2, 3-D: closest feature of a closed triangulated surface and    */
+/* its pseudo-normal.  Faces carry their unit normals; a vertex the angle-    */
+/* weighted sum of the normals of its faces (Eq. 2); an edge the sum of its   */
+/* two faces' normals (Eq. 3, equal weights), all normalised.  The closest    */
+/* point on a triangle is the plane projection when it falls inside, else     */
+/* the nearest point of the three edges (a vertex when the edge parameter is  */
+/* clamped to an end).  The search is exhaustive; ties keep the lowest        */
+/* triangle index.  kind: 0 face, 1 edge, 2 vertex.                           */
+/* ------------------------------------------------------------------------- */
+static void sub3(const double *a, const double *b, double *r) { r[0] = a[0] - b[0]; r[1] = a[1] - b[1]; r[2] = a[2] - b[2]; }
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double *a, const double *b, double *r) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+static void unit3(double *a) {
+  double L = sqrt(dot3(a, a));
+  if (L > 0.0) { a[0] /= L; a[1] /= L; a[2] /= L; }
+}
+
+void orc_closest_3d(int nv, const double *v, int ntri, const int *tri, int np, const double *pts, double *cp,
+                    double *nrm, int32_t *kind) {
+  double *fn = calloc((size_t)3 * ntri, sizeof(double)), *vn = calloc((size_t)3 * nv, sizeof(double));
+  /* face normals and angle-weighted vertex sums */
+  for (int f = 0; f < ntri; f++) {
+    const int *t = tri + 3 * f;
+    double e1[3], e2[3];
+    sub3(v + 3 * t[1], v + 3 * t[0], e1);
+    sub3(v + 3 * t[2], v + 3 * t[0], e2);
+    cross3(e1, e2, fn + 3 * f);
+    unit3(fn + 3 * f);
+    for (int k = 0; k < 3; k++) {
+      double a[3], b[3];
+      sub3(v + 3 * t[(k + 1) % 3], v + 3 * t[k], a);
+      sub3(v + 3 * t[(k + 2) % 3], v + 3 * t[k], b);
+      double ang = acos(fmax(-1.0, fmin(1.0, dot3(a, b) / sqrt(dot3(a, a) * dot3(b, b)))));
+      for (int d = 0; d < 3; d++) vn[3 * t[k] + d] += ang * fn[3 * f + d];
+    }
+  }
+  for (int k = 0; k < nv; k++) unit3(vn + 3 * k);
+  for (int n = 0; n < np; n++) {
+    const double *P = pts + 3 * n;
+    double best = INFINITY, bc[3] = {0, 0, 0};
+    int bf = -1, bk = 0, be = 0, bv = 0;
+    for (int f = 0; f < ntri; f++) {
+      const int *t = tri + 3 * f;
+      const double *A = v + 3 * t[0];
+      double e1[3], e2[3], w[3];
+      sub3(v + 3 * t[1], A, e1);
+      sub3(v + 3 * t[2], A, e2);
+      sub3(P, A, w);
+      /* plane projection in barycentric form: solve the 2x2 normal equations */
+      double a11 = dot3(e1, e1), a12 = dot3(e1, e2), a22 = dot3(e2, e2), b1 = dot3(w, e1), b2 = dot3(w, e2);
+      double det = a11 * a22 - a12 * a12;
+      double s = (b1 * a22 - b2 * a12) / det, r = (a11 * b2 - a12 * b1) / det;
+      double q[3];
+      int fk = 0, fe = 0, fv = 0;
+      if (s >= 0.0 && r >= 0.0 && s + r <= 1.0) {
+        for (int d = 0; d < 3; d++) q[d] = A[d] + s * e1[d] + r * e2[d];
+      } else {
+        double dmin = INFINITY;
+        for (int k = 0; k < 3; k++) {
+          const double *E0 = v + 3 * t[k], *E1 = v + 3 * t[(k + 1) % 3];
+          double ed[3], pw[3];
+          sub3(E1, E0, ed);
+          sub3(P, E0, pw);
+          double u = dot3(pw, ed) / dot3(ed, ed);
+          int vert = -1;
+          if (u <= 0.0) { u = 0.0; vert = t[k]; }
+          else if (u >= 1.0) { u = 1.0; vert = t[(k + 1) % 3]; }
+          double x[3] = {E0[0] + u * ed[0], E0[1] + u * ed[1], E0[2] + u * ed[2]}, dd[3];
+          sub3(P, x, dd);
+          double d2 = dot3(dd, dd);
+          if (d2 < dmin) {
+            dmin = d2;
+            q[0] = x[0]; q[1] = x[1]; q[2] = x[2];
+            fk = vert >= 0 ? 2 : 1;
+            fe = k;
+            fv = vert;
+          }
+        }
+      }
+      double dq[3];
+      sub3(P, q, dq);
+      double d2 = dot3(dq, dq);
+      if (d2 < best) {
+        best = d2;
+        bf = f; bk = fk; be = fe; bv = fv;
+        bc[0] = q[0]; bc[1] = q[1]; bc[2] = q[2];
+      }
+    }
+    double nn[3] = {0, 0, 0};
+    if (bk == 0) {
+      for (int d = 0; d < 3; d++) nn[d] = fn[3 * bf + d];
+    } else if (bk == 2) {
+      for (int d = 0; d < 3; d++) nn[d] = vn[3 * bv + d];
+    } else {
+      /* edge (i, j) of face bf: the neighbouring face holds (j, i) */
+      int i = tri[3 * bf + be], j = tri[3 * bf + (be + 1) % 3], g = -1;
+      for (int f = 0; f < ntri && g < 0; f++)
+        for (int k = 0; k < 3; k++)
+          if (tri[3 * f + k] == j && tri[3 * f + (k + 1) % 3] == i) { g = f; break; }
+      for (int d = 0; d < 3; d++) nn[d] = fn[3 * bf + d] + (g >= 0 ? fn[3 * g + d] : 0.0);
+      unit3(nn);
+    }
+    for (int d = 0; d < 3; d++) {
+      cp[3 * n + d] = bc[d];
+      nrm[3 * n + d] = nn[d];
+    }
+    kind[n] = bk;
+  }
+  free(fn);
+  free(vn);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Sec. 4.2: pseudo-normals.  Segment k runs from vertex k to k+1 of a CCW   */
 /* polyline; its outward normal is the travel direction turned clockwise.    */
 /* In 2-D each vertex has two incident segments that enter Eq. 2 with equal  */

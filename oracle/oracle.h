@@ -118,6 +118,9 @@ void orc_classify_points(int nv, const double *verts, int np, const double *pts,
 /* 3-D: closed triangulated surface (verts 3*nv, outward-oriented triangles 3*ntri), points 3*np */
 void orc_classify_points_3d(int nv, const double *verts, int ntri, const int *tris, int np, const double *pts,
                             uint8_t *solid);
+/* 3-D closest point cp (3*np), pseudo-normal nrm (3*np) and feature kind (0 face, 1 edge, 2 vertex) */
+void orc_closest_3d(int nv, const double *verts, int ntri, const int *tris, int np, const double *pts, double *cp,
+                    double *nrm, int32_t *kind);
 double orc_weno5(const double f[5]);
 double orc_tvd2(const double f[3]);
 void orc_ldfss_xflux(const double qL[4], const double qR[4], double gamma, double R,

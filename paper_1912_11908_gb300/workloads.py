@@ -201,6 +201,20 @@ def uv_sphere(n_lat=21, n_lon=30, radius=1.0, center=(0.0, 0.0, 0.0)):
     return np.array(verts) + np.array(center), np.array(tris, dtype=np.int32)
 
 
+def box_mesh(lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """Closed triangulated box: 8 corners, two triangles per face, counter-clockwise seen from outside (sharp
+    edges and corners for the pseudo-normal checks of Sec. 4.2)."""
+    x0, y0, z0 = lo
+    x1, y1, z1 = hi
+    verts = np.array([(x0, y0, z0), (x1, y0, z0), (x1, y1, z0), (x0, y1, z0),
+                      (x0, y0, z1), (x1, y0, z1), (x1, y1, z1), (x0, y1, z1)], dtype=np.float64)
+    quads = [(0, 3, 2, 1), (4, 5, 6, 7), (0, 1, 5, 4), (2, 3, 7, 6), (1, 2, 6, 5), (0, 4, 7, 3)]
+    tris = []
+    for a, b, c, d in quads:
+        tris += [(a, b, c), (a, c, d)]
+    return verts, np.array(tris, dtype=np.int32)
+
+
 def random_polygon(rng, n, center=(0.0, 0.0), rmin=0.3, rmax=1.0):
     """Star-shaped random polygon (CCW) for brute-force classification checks."""
     a = np.sort(rng.uniform(0.0, 2.0 * math.pi, n))

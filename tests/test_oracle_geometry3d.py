@@ -55,3 +55,42 @@ def test_rays_through_vertices_and_edges(orc):
     solid = orc.classify_points_3d(verts, tris, pts[keep])
     np.testing.assert_array_equal(solid, (wind[keep] > 0.5).astype(np.uint8))
     assert 0 < solid.sum() < keep.sum()  # both sides are exercised
+
+
+def test_pseudo_normal_sign_matches_inside_near_sharp_edges(orc):
+    """Angle-weighted vertex and edge pseudo-normals (Eq. 2, 3): near every face, edge and corner of a box and
+    of the sphere, sign((X - C).n) < 0 exactly for the points inside (the property that makes the signed
+    distance consistent at sharp features, Sec. 4.2)."""
+    rng = np.random.default_rng(13)
+    for verts, tris in (W.box_mesh((0.1, 0.2, 0.3), (0.9, 0.7, 1.1)), W.uv_sphere(21, 30, 0.5)):
+        idx = rng.integers(0, len(verts), 600)
+        pts = np.concatenate([verts[idx] + rng.normal(scale=0.05, size=(600, 3)),
+                              verts[tris[rng.integers(0, len(tris), 600)]].mean(axis=1)
+                              + rng.normal(scale=0.05, size=(600, 3))])
+        cp, nrm, kind = orc.closest_3d(verts, tris, pts)
+        wind = _winding(verts, tris, pts)
+        d = np.einsum("pi,pi->p", pts - cp, nrm)
+        ok = np.linalg.norm(pts - cp, axis=1) > 1e-9
+        assert ok.sum() > 1100
+        np.testing.assert_array_equal((d < 0)[ok], (wind > 0.5)[ok])
+        assert set(np.unique(kind[ok])) == {0, 1, 2}  # faces, edges and vertices all exercised
+
+
+def test_closest_point_against_dense_sampling(orc):
+    verts, tris = W.uv_sphere(11, 16, 1.0)
+    g = np.linspace(0.0, 1.0, 41)
+    S, T = np.meshgrid(g, g)
+    keep = S + T <= 1.0
+    s, t = S[keep], T[keep]
+    samples = np.concatenate([verts[f[0]] + s[:, None] * (verts[f[1]] - verts[f[0]])
+                              + t[:, None] * (verts[f[2]] - verts[f[0]]) for f in tris])
+    rng = np.random.default_rng(5)
+    pts = rng.normal(size=(150, 3))
+    pts *= rng.uniform(0.5, 1.5, (150, 1)) / np.linalg.norm(pts, axis=1, keepdims=True)
+    cp, _, _ = orc.closest_3d(verts, tris, pts)
+    dist = np.linalg.norm(pts - cp, axis=1)
+    for k in range(len(pts)):
+        dmin = np.min(np.linalg.norm(samples - pts[k], axis=1))
+        assert dist[k] <= dmin + 1e-12
+        assert dist[k] >= dmin - 0.02  # sampling resolution (edge length / 40)
+        assert np.min(np.linalg.norm(samples - cp[k], axis=1)) < 0.02  # the point lies on the surface
