@@ -94,6 +94,7 @@ def lib():
         L.orc_classify_points.argtypes = [ip, vp, ip, vp, vp]
         L.orc_classify_points_3d.argtypes = [ip, vp, ip, vp, ip, vp, vp]
         L.orc_closest_3d.argtypes = [ip, vp, ip, vp, ip, vp, vp, vp, vp]
+        L.orc_tags_3d.argtypes = [ip, ip, ip, vp, vp]
         L.orc_weno5.argtypes = [vp]
         L.orc_tvd2.argtypes = [vp]
         L.orc_tvd2.restype = dp
@@ -227,6 +228,15 @@ def classify_points_3d(verts, tris, pts):
     out = np.zeros(pts.shape[0], np.uint8)
     lib().orc_classify_points_3d(verts.shape[0], _ptr(verts), tris.shape[0], _ptr(tris), pts.shape[0], _ptr(pts),
                                  _ptr(out))
+    return out
+
+
+def tags_3d(solid):
+    """Node tags of a [nz][ny][nx] lattice from its solid flags (IB = fluid with a solid 6-neighbour, G1..G3)."""
+    solid = np.ascontiguousarray(solid, np.uint8)
+    nz, ny, nx = solid.shape
+    out = np.zeros_like(solid)
+    lib().orc_tags_3d(nx, ny, nz, _ptr(solid), _ptr(out))
     return out
 
 

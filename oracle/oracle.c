@@ -227,6 +227,43 @@ void orc_classify_points_3d(int nv, const double *verts, int ntri, const int *tr
 }
 
 /* ------------------------------------------------------------------------- */
+/* Sec. 3.2 and Sec. 5, 3-D: node tags from the solid flags of an nx x ny x   */
+/* nz lattice (x fastest): IB = fluid node with a solid 6-neighbour; G1..G3 = */
+/* solid node whose nearest non-solid node along a grid line is 1, 2 or 3     */
+/* nodes away; other solid nodes stay SOLID.                                  */
+/* ------------------------------------------------------------------------- */
+void orc_tags_3d(int nx, int ny, int nz, const uint8_t *solid, uint8_t *tags) {
+  static const int dirs[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        size_t n = ((size_t)k * ny + j) * nx + i;
+        if (!solid[n]) {
+          int ib = 0;
+          for (int d = 0; d < 6 && !ib; d++) {
+            int a = i + dirs[d][0], b = j + dirs[d][1], c = k + dirs[d][2];
+            if (a >= 0 && a < nx && b >= 0 && b < ny && c >= 0 && c < nz && solid[((size_t)c * ny + b) * nx + a]) ib = 1;
+          }
+          tags[n] = ib ? ORC_IB : ORC_FLUID;
+          continue;
+        }
+        tags[n] = ORC_SOLID;
+        for (int s = 1; s <= 3; s++) {
+          int hit = 0;
+          for (int d = 0; d < 6 && !hit; d++) {
+            int a = i + s * dirs[d][0], b = j + s * dirs[d][1], c = k + s * dirs[d][2];
+            if (a >= 0 && a < nx && b >= 0 && b < ny && c >= 0 && c < nz && !solid[((size_t)c * ny + b) * nx + a])
+              hit = 1;
+          }
+          if (hit) {
+            tags[n] = (uint8_t)(ORC_G1 + s - 1);
+            break;
+          }
+        }
+      }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Sec. 4.1-4.2, 3-D: closest feature of a closed triangulated surface and    */
 /* its pseudo-normal.  Faces carry their unit normals; a vertex the angle-    */
 /* weighted sum of the normals of its faces (Eq. 2); an edge the sum of its   */

@@ -118,6 +118,8 @@ void orc_classify_points(int nv, const double *verts, int np, const double *pts,
 /* 3-D: closed triangulated surface (verts 3*nv, outward-oriented triangles 3*ntri), points 3*np */
 void orc_classify_points_3d(int nv, const double *verts, int ntri, const int *tris, int np, const double *pts,
                             uint8_t *solid);
+/* 3-D node tags (ORC_FLUID .. ORC_G3) of an nx*ny*nz lattice, x fastest, from its solid flags */
+void orc_tags_3d(int nx, int ny, int nz, const uint8_t *solid, uint8_t *tags);
 /* 3-D closest point cp (3*np), pseudo-normal nrm (3*np) and feature kind (0 face, 1 edge, 2 vertex) */
 void orc_closest_3d(int nv, const double *verts, int ntri, const int *tris, int np, const double *pts, double *cp,
                     double *nrm, int32_t *kind);

@@ -94,3 +94,54 @@ def test_closest_point_against_dense_sampling(orc):
         assert dist[k] <= dmin + 1e-12
         assert dist[k] >= dmin - 0.02  # sampling resolution (edge length / 40)
         assert np.min(np.linalg.norm(samples - cp[k], axis=1)) < 0.02  # the point lies on the surface
+
+
+def _tags_by_definition_3d(solid):
+    """Tags written out from the definitions with array shifts: IB = fluid with a solid 6-neighbour; G_s = solid
+    with a non-solid node s steps away along some axis and none closer."""
+    nz, ny, nx = solid.shape
+    pad = np.pad(solid, 3, constant_values=0).astype(bool)
+    inner = (slice(3, 3 + nz), slice(3, 3 + ny), slice(3, 3 + nx))
+
+    def shifted(s, axis):
+        sl = [slice(3, 3 + nz), slice(3, 3 + ny), slice(3, 3 + nx)]
+        sl[axis] = slice(3 + s, 3 + s + solid.shape[axis])
+        return pad[tuple(sl)]
+
+    # outside the lattice counts as neither solid (for IB) nor non-solid (for ghosts)
+    valid = np.pad(np.ones_like(solid, bool), 3, constant_values=False)
+
+    def in_lattice(s, axis):
+        sl = [slice(3, 3 + nz), slice(3, 3 + ny), slice(3, 3 + nx)]
+        sl[axis] = slice(3 + s, 3 + s + solid.shape[axis])
+        return valid[tuple(sl)]
+
+    s0 = pad[inner]
+    tags = np.where(s0, 1, 0).astype(np.uint8)
+    nb_solid = np.zeros_like(s0)
+    for axis in range(3):
+        for s in (1, -1):
+            nb_solid |= shifted(s, axis) & in_lattice(s, axis)
+    tags[~s0 & nb_solid] = 2
+    done = ~s0
+    for step in (1, 2, 3):
+        hit = np.zeros_like(s0)
+        for axis in range(3):
+            for s in (step, -step):
+                hit |= ~shifted(s, axis) & in_lattice(s, axis)
+        new = s0 & ~done & hit
+        tags[new] = 2 + step
+        done |= new
+    return tags
+
+
+def test_tags_3d_by_definition(orc):
+    verts, tris = W.uv_sphere(21, 30, 0.35, (0.5, 0.5, 0.5))
+    g = (np.arange(40) + 0.5) / 40
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    solid = orc.classify_points_3d(verts, tris, pts).reshape(40, 40, 40)
+    tags = orc.tags_3d(solid)
+    np.testing.assert_array_equal(tags, _tags_by_definition_3d(solid))
+    counts = np.bincount(tags.ravel(), minlength=6)
+    assert all(counts[k] > 500 for k in (2, 3, 4, 5)), counts
