@@ -83,6 +83,7 @@ def lib():
         L.orc_list_len.restype = ip
         L.orc_get_list.argtypes = [vp, ip, vp]
         L.orc_forces.argtypes = [vp, vp]
+        L.orc_surface.argtypes = [vp, vp, vp]
         L.orc_body.argtypes = [vp, vp]
         L.orc_time.argtypes = [vp]
         L.orc_time.restype = dp
@@ -189,6 +190,15 @@ class Case:
         out = np.zeros(4, np.float64)
         lib().orc_forces(self.h, _ptr(out))
         return out
+
+    def surface(self):
+        """Per segment (Eq. 9 integrand at the midpoints): pressure coefficient (p_s - p_inf) / (rho U^2 / 2)
+        and skin-friction coefficient tau / (rho U^2 / 2); NaN where no probe square was found."""
+        n = self._verts.shape[0]
+        cp = np.zeros(n, np.float64)
+        cf = np.zeros(n, np.float64)
+        lib().orc_surface(self.h, _ptr(cp), _ptr(cf))
+        return cp, cf
 
     def time(self):
         return lib().orc_time(self.h)

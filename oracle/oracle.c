@@ -940,9 +940,12 @@ static void ldfss(const double qL[4], const double qR[4], double nxf, double nyf
   double MhP = Mh * (1.0 - (dp + adp) / (2.0 * rL * cs * cs));
   double MhM = Mh * (1.0 - (-dp + adp) / (2.0 * rR * cs * cs));
   double Cp = CVL - MhP, Cm = CVR + MhM;
-  /* pressure split: with low-Mach scaling (mr2 < 1) it uses the physical Mach
-   * numbers un/c (reading: the split with the scaled Mach numbers made the
-   * preconditioned pseudo-time iteration diverge below M = 0.01) */
+  /* pressure split with the physical face Mach numbers un/c.  With low-Mach scaling (mr2 < 1) its        */
+  /* dissipative part -- the departure of D_L p_L + D_R p_R from the face mean, about (3/4) rho c (uL - uR) */
+  /* at low Mach -- is scaled by fa = c'/c, so that it acts like rho c' (uL - uR) with c' of the order of  */
+  /* the flow speed (reading: the paper only names the scheme; the unscaled split keeps O(M) pressure     */
+  /* fluctuations and loses the incompressible limit, the split in the scaled Mach numbers un/c' raises   */
+  /* that term by c/c' and made the pseudo-time iteration diverge).  mr2 = 1 gives plain LDFSS(0).        */
   double pL_ = ML, pR_ = MR, paL = aL, paR = aR, pbL = bL, pbR = bR;
   if (mr2 < 1.0) {
     pL_ = unL / cb;
@@ -959,6 +962,10 @@ static void ldfss(const double qL[4], const double qR[4], double nxf, double nyf
   double DR = paR * (1.0 + pbR) - pbR * PmR;
   double mL = rL * cs * Cp, mR = rR * cs * Cm;
   double ph = DL * pL + DR * pR;
+  if (mr2 < 1.0) {
+    double fa = cs / cb;
+    ph = 0.5 * (pL + pR) + fa * ((DL - 0.5) * pL + (DR - 0.5) * pR);
+  }
   F[0] = mL + mR;
   F[1] = mL * uL + mR * uR + ph * nxf;
   F[2] = mL * vL + mR * vR + ph * nyf;
@@ -984,12 +991,9 @@ void orc_euler_xflux(const double q[4], double gamma, double R, double flux[4]) 
 /* Low-Mach preconditioning parameter at a face.  Only the dual-time scheme,
  * whose pseudo-time derivative carries the preconditioning matrix, scales the
  * dissipation; explicit physical-time stepping uses plain LDFSS (Mr^2 = 1).
- * Reference velocity Ur = min(c, max(|V|, U_ref, nu/dn, c/3)), Mr^2 = (Ur/c)^2
- * with face-averaged c, |V| and rho.  Reading: the floor c/3 bounds the
- * preconditioning; with lower floors (c/5 and below, or U_ref alone) the
- * explicit pseudo-time iteration diverged next to an immersed body at
- * M <= 0.01 (and without a body below M = 0.003). */
-#define UR_FLOOR (1.0 / 3.0)
+ * Reference velocity Ur = min(c, max(|V|, U_ref, nu/dn)), Mr^2 = (Ur/c)^2
+ * with face-averaged c, |V| and rho (Weiss-Smith; no lower bound tied to c,
+ * so that the dissipation follows the flow speed as M -> 0). */
 static double face_mr2(const orc_case *c, const double qL[4], const double qR[4], double dn) {
   if (!c->precond) return 1.0;
   double g = c->p.gamma;
@@ -1001,7 +1005,6 @@ static double face_mr2(const orc_case *c, const double qL[4], const double qR[4]
   double Ur = Vm;
   if (1.0 > Ur) Ur = 1.0;
   if (vis > Ur) Ur = vis;
-  if (UR_FLOOR * cb > Ur) Ur = UR_FLOOR * cb;
   if (cb < Ur) Ur = cb;
   double m = (Ur / cb) * (Ur / cb);
   return m < 1.0 ? m : 1.0;
@@ -1163,7 +1166,7 @@ static double compute_dt(orc_case *c) {
 /*   rows [T, 0, 0, rT], [T u, r, 0, rT u], [T v, 0, r, rT v],                */
 /*        [T H - 1, r u, r v, rT H + r cp]                                   */
 /* with rT = -r/T and T = 1/Ur^2 - rT/(r cp) (Gamma) or 1/(R T) (dW/dQ).       */
-/* Ur = min(c, max(|V|, U_ref, nu/dmin, c/3)); local dtau = CFL_tau / [(|u'|+c') */
+/* Ur = min(c, max(|V|, U_ref, nu/dmin)); local dtau = CFL_tau / [(|u'|+c') */
 /* (1/dx + 1/dy) + 2 gamma mu/(Pr r)(1/dx^2 + 1/dy^2)], u', c' the           */
 /* eigenvalue terms of the preconditioned system.  The 4x4 system is solved  */
 /* by Gaussian elimination with partial pivoting.                            */
@@ -1246,7 +1249,6 @@ static void dual_update(orc_case *c, int stage, double *const In[4], double *con
       double Ur = Vm;
       if (1.0 > Ur) Ur = 1.0;
       if (c->mu / r / c->dmin > Ur) Ur = c->mu / r / c->dmin;
-      if (UR_FLOOR * cs > Ur) Ur = UR_FLOOR * cs;
       if (cs < Ur) Ur = cs;
       double mr2 = (Ur / cs) * (Ur / cs);
       double up = 0.5 * Vm * (1.0 + mr2);
@@ -1361,6 +1363,53 @@ void orc_body(const orc_case *c, double out[6]) {
 /* zero).                                                                    */
 /* Compensated (Kahan) summation.                                            */
 /* ------------------------------------------------------------------------- */
+/* Eq. 9 integrand on segment k: unit tangent and normal, length, wall      */
+/* pressure ps and wall shear tau at the midpoint.  Returns 0 when no probe */
+/* square is found (the segment is then left out of the sums).             */
+static int surface_segment(orc_case *c, int k, const double V[2], const double Acc[2], int sup, double *ps_o,
+                           double *tau_o, double *L_o, double *tx_o, double *ty_o) {
+  const orc_params *p = &c->p;
+  int k1 = (k + 1 == p->nv) ? 0 : k + 1;
+  double ax = c->vx[k], ay = c->vy[k];
+  double ex = c->vx[k1] - ax, ey = c->vy[k1] - ay;
+  double L = sqrt(ex * ex + ey * ey);
+  double tx = ex / L, ty = ey / L;
+  double nx = ty, ny = -tx;
+  double mx = ax + 0.5 * ex, my = ay + 0.5 * ey;
+  double xi = c->h, w[4];
+  int32_t i0, j0;
+  int mask = 0;
+  for (int st = 0; st <= 3; st++) {
+    mask = interp_square(c, mx + xi * nx, my + xi * ny, ALLOW_FLUID, &i0, &j0, w);
+    if (mask) break;
+    if (st < 3) xi = xi + c->dmin;
+  }
+  if (!mask) return 0;
+  double qp[4] = {0, 0, 0, 0};
+  for (int kk = 0; kk < 4; kk++) {
+    if (!(mask >> kk & 1)) continue;
+    int id = fidx(c, i0 + (kk & 1), j0 + (kk >> 1));
+    double qk[4];
+    cons_to_prim(c, c->A[0][id], c->A[1][id], c->A[2][id], c->A[3][id], qk);
+    for (int v = 0; v < 4; v++) qp[v] += w[kk] * qk[v];
+  }
+  /* wall pressure: the probe's, carried to the surface by the wall condition of the reconstruction */
+  double Vs[2], As[2];
+  wall_kin(c, c->t, mx, my, V, Acc, Vs, As);  /* the wall's motion at the segment midpoint */
+  double G = -(nx * As[0] + ny * As[1]);
+  if (sup) {
+    double ut = (qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty;
+    G = G + ut * ut * (0.5 * (c->vk[k] + c->vk[k1]));
+  }
+  /* wall shear: the tangential velocity relative to the wall over the probe distance */
+  *ps_o = qp[0] * exp(-xi * G / (c->R * qp[3]));
+  *tau_o = c->mu * ((qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty) / xi;
+  *L_o = L;
+  *tx_o = tx;
+  *ty_o = ty;
+  return 1;
+}
+
 void orc_forces(orc_case *c, double out[4]) {
   const orc_params *p = &c->p;
   if (!c->classified) orc_classify(c);
@@ -1369,40 +1418,9 @@ void orc_forces(orc_case *c, double out[4]) {
   int sup = supersonic_motion(c, V);
   double sx = 0, cx = 0, sy = 0, cy = 0;
   for (int k = 0; k < p->nv; k++) {
-    int k1 = (k + 1 == p->nv) ? 0 : k + 1;
-    double ax = c->vx[k], ay = c->vy[k];
-    double ex = c->vx[k1] - ax, ey = c->vy[k1] - ay;
-    double L = sqrt(ex * ex + ey * ey);
-    double tx = ex / L, ty = ey / L;
+    double ps, tau, L, tx, ty;
+    if (!surface_segment(c, k, V, Acc, sup, &ps, &tau, &L, &tx, &ty)) continue;
     double nx = ty, ny = -tx;
-    double mx = ax + 0.5 * ex, my = ay + 0.5 * ey;
-    double xi = c->h, w[4];
-    int32_t i0, j0;
-    int mask = 0;
-    for (int st = 0; st <= 3; st++) {
-      mask = interp_square(c, mx + xi * nx, my + xi * ny, ALLOW_FLUID, &i0, &j0, w);
-      if (mask) break;
-      if (st < 3) xi = xi + c->dmin;
-    }
-    if (!mask) continue;
-    double qp[4] = {0, 0, 0, 0};
-    for (int kk = 0; kk < 4; kk++) {
-      if (!(mask >> kk & 1)) continue;
-      int id = fidx(c, i0 + (kk & 1), j0 + (kk >> 1));
-      double qk[4];
-      cons_to_prim(c, c->A[0][id], c->A[1][id], c->A[2][id], c->A[3][id], qk);
-      for (int v = 0; v < 4; v++) qp[v] += w[kk] * qk[v];
-    }
-    /* wall pressure: the probe's, carried to the surface by the wall condition of the reconstruction */
-    double Vs[2], As[2];
-    wall_kin(c, c->t, mx, my, V, Acc, Vs, As);  /* the wall's motion at the segment midpoint */
-    double G = -(nx * As[0] + ny * As[1]);
-    if (sup) {
-      double ut = (qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty;
-      G = G + ut * ut * (0.5 * (c->vk[k] + c->vk[k1]));
-    }
-    double ps = qp[0] * exp(-xi * G / (c->R * qp[3]));
-    double tau = c->mu * ((qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty) / xi;
     double fx = (-(ps - c->pinf) * nx + tau * tx) * L;
     double fy = (-(ps - c->pinf) * ny + tau * ty) * L;
     double y1 = fx - cx, t1 = sx + y1;
@@ -1417,6 +1435,27 @@ void orc_forces(orc_case *c, double out[4]) {
   out[1] = sy / qref;
   out[2] = sx;
   out[3] = sy;
+}
+
+/* Surface distributions of Eq. 9 per segment: pressure coefficient       */
+/* (ps - p_inf) / (rho_inf U^2 / 2) and skin-friction coefficient          */
+/* tau / (rho_inf U^2 / 2) at the segment midpoints; NaN where no probe.   */
+void orc_surface(orc_case *c, double *cp, double *cf) {
+  const orc_params *p = &c->p;
+  if (!c->classified) orc_classify(c);
+  double X[2], V[2], Acc[2];
+  motion_at(c, c->t, X, V, Acc);
+  int sup = supersonic_motion(c, V);
+  for (int k = 0; k < p->nv; k++) {
+    double ps, tau, L, tx, ty;
+    if (!surface_segment(c, k, V, Acc, sup, &ps, &tau, &L, &tx, &ty)) {
+      cp[k] = NAN;
+      cf[k] = NAN;
+      continue;
+    }
+    cp[k] = (ps - c->pinf) / 0.5;
+    cf[k] = tau / 0.5;
+  }
 }
 
 /* ------------------------------------------------------------------------- */

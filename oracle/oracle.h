@@ -105,6 +105,8 @@ void orc_get_tags(const orc_case *c, uint8_t *dst);      /* [ny][nx] */
 int orc_list_len(const orc_case *c, int kind);           /* 0 IB, 1..3 G1..G3 */
 void orc_get_list(const orc_case *c, int kind, orc_stencil *dst);
 void orc_forces(orc_case *c, double out[4]);             /* Cd, Cl, Fx, Fy */
+/* Eq. 9 per segment: surface pressure and skin-friction coefficients at the segment midpoints (NaN where no probe). */
+void orc_surface(orc_case *c, double *cp, double *cf);
 double orc_time(const orc_case *c);
 void orc_body(const orc_case *c, double out[6]);         /* displacement x, y; velocity u, v; last force Fx, Fy */
 double orc_last_dt(const orc_case *c);

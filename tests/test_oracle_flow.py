@@ -428,7 +428,11 @@ def test_dual_time_advects_entropy_wave_without_pressure(orc, M):
 
 
 def test_dual_time_quiescent_body_and_free_stream(orc):
-    """Gas at rest around a body and a uniform stream are exact solutions of the dual-time scheme too."""
+    """Gas at rest around a body and a uniform stream are exact solutions of the dual-time scheme too, up to
+    rounding.  The rounding of the pressure, eps p_inf, moves the velocity through the preconditioned
+    impedance rho U_r (U_r = U_ref = 1 here) by about eps p_inf per pseudo step, so momentum is bounded by
+    1e-14 p_inf (7e-11 at M = 0.01; measured 2e-12), the other components by 1e-12 of their size."""
+    pinf = 1.0 / (GAMMA * 0.01 ** 2)
     for uinf in ((0.0, 0.0), (1.0, 0.0)):
         spec = W.case_spec(W.naca00xx(0.12, 200, 10.0), 96, 48, (-0.5, 1.5, -0.5, 0.5), 0.01, 500.0, W.FAR,
                            uinf=uinf, time_scheme=W.TIME_DUAL, dt_phys=0.01, subiters=10)
@@ -440,7 +444,10 @@ def test_dual_time_quiescent_body_and_free_stream(orc):
         U1 = c.state()
         live = c.tags() != 1
         for k in range(4):
-            assert np.abs(U1[k] - U0[k])[live].max() <= 1e-12 * max(1.0, np.abs(U0[k]).max()), (uinf, k)
+            bound = 1e-12 * max(1.0, np.abs(U0[k]).max())
+            if k in (1, 2):
+                bound = max(bound, 1e-14 * pinf)
+            assert np.abs(U1[k] - U0[k])[live].max() <= bound, (uinf, k)
 
 
 def test_dual_time_cylinder_low_mach_is_stable(orc):
@@ -458,6 +465,35 @@ def test_dual_time_cylinder_low_mach_is_stable(orc):
     assert u[fl].max() < 1.5 and u[fl].min() > -0.5
     cd = c.forces()[0]
     assert 1.0 < cd < 3.0, cd
+
+
+def test_dual_time_incompressible_limit(orc):
+    """Low-Mach preconditioning (Sec. 2) exists so that the discrete solution tends to the incompressible one
+    as M -> 0, the compressibility corrections of the pressure being of order M^2.  Cylinder at Re 40 (D/8,
+    20 physical steps of dt = 0.0625 with 30 sub-iterations) at M = 0.1, 0.01 and 0.001:
+    (i) the M = 0.01 and M = 0.001 solutions agree: drag and lift within 1e-3, surface Cp and Cf within 1e-3
+        in L-inf (measured 8.5e-5, 1.6e-7, 1.1e-4, 1e-5).  An upwind dissipation scaled by the sound speed
+        rather than the flow speed leaves O(M) pressure fluctuations and fails by orders of magnitude (with
+        the pressure split's dissipation unscaled, Cd was 1.5 at M = 0.01 and 7.0 at M = 0.001);
+    (ii) the differences shrink like M^2: the ratio of the (0.1, 0.01) difference to the (0.01, 0.001) one is
+        near (0.1^2 - 0.01^2) / (0.01^2 - 0.001^2) = 100 for Cd and for surface Cp (accepted: 30 to 300)."""
+    res = {}
+    for M in (0.1, 0.01, 0.001):
+        spec = W.case_spec(W.cylinder(256), 160, 96, (-6.0, 14.0, -6.0, 6.0), M, 40.0, W.FAR,
+                           time_scheme=W.TIME_DUAL, dt_phys=0.0625, subiters=30)
+        c = orc.Case(spec)
+        c.step(20)
+        f = c.forces()
+        cp, cf = c.surface()
+        assert np.all(np.isfinite(cp)) and np.all(np.isfinite(cf))
+        res[M] = (f, cp, cf)
+    (f1, cp1, cf1), (f2, cp2, cf2), (f3, cp3, cf3) = res[0.1], res[0.01], res[0.001]
+    assert 1.0 < f3[0] < 3.0, f3
+    assert abs(f2[0] - f3[0]) < 1e-3 and abs(f2[1] - f3[1]) < 1e-3, (f2, f3)
+    assert np.abs(cp2 - cp3).max() < 1e-3 and np.abs(cf2 - cf3).max() < 1e-3
+    ratio_cd = abs(f1[0] - f2[0]) / abs(f2[0] - f3[0])
+    ratio_cp = np.abs(cp1 - cp2).max() / np.abs(cp2 - cp3).max()
+    assert 30.0 < ratio_cd < 300.0 and 30.0 < ratio_cp < 300.0, (ratio_cd, ratio_cp)
 
 
 # ---------------------------------------------------------------- TVD-2 (Sec. 2, the second reconstruction)

@@ -260,3 +260,61 @@ def test_force_integral_uniform_and_linear_pressure(orc):
     fx = -g * h * np.sum(nrm[:, 0] * nrm[:, 1] * L)
     assert abs(F[2] - fx) < 1e-12
     assert abs(F[3] / fy - 1.0) < 1e-2, (F, fy)
+
+
+def _shear_layer_case(orc, vel, gammas, re=50.0, segs_per_face=4):
+    """Rectangle whose faces sit a quarter cell from the nearest outside node row (sides (n + 1/2) dx), so that
+    every force probe one diagonal spacing out has four FLUID corners; outside each face, within the face's
+    strip, the gas slides parallel to the face with u = V + gamma_k d t_k (d the distance from the face)."""
+    n = 128
+    d = 4.0 / n
+    lo, hi = -2.0 + 47.75 * d, -2.0 + 80.25 * d  # nodes at lo - d/4 and hi + d/4 are the first outside rows
+    corners = [(lo, lo), (hi, lo), (hi, hi), (lo, hi)]
+    verts = []
+    for k in range(4):
+        a, b = np.array(corners[k]), np.array(corners[(k + 1) % 4])
+        for s in range(segs_per_face):
+            verts.append(a + (b - a) * s / segs_per_face)
+    verts = np.array(verts)
+    motion = dict(motion=W.MOTION_CONST, vel=vel) if any(vel) else {}
+    spec = W.case_spec(verts, n, n, (-2.0, 2.0, -2.0, 2.0), 0.2, re, W.FAR, **motion)
+    c = orc.Case(spec)
+    xc = -2.0 + (np.arange(n) + 0.5) * d
+    X, Y = np.meshgrid(xc, xc)
+    u = np.full_like(X, vel[0])
+    v = np.full_like(X, vel[1])
+    tang = [(1.0, 0.0), (0.0, 1.0), (-1.0, 0.0), (0.0, -1.0)]  # CCW: bottom, right, top, left
+    inx, iny = (X >= lo) & (X <= hi), (Y >= lo) & (Y <= hi)
+    dist = [np.where(inx & (Y < lo), lo - Y, -1.0), np.where(iny & (X > hi), X - hi, -1.0),
+            np.where(inx & (Y > hi), Y - hi, -1.0), np.where(iny & (X < lo), lo - X, -1.0)]
+    for k in range(4):
+        m = dist[k] > 0.0
+        u[m] += gammas[k] * dist[k][m] * tang[k][0]
+        v[m] += gammas[k] * dist[k][m] * tang[k][1]
+    r = np.ones_like(X)
+    pinf = 1.0 / (1.4 * 0.04)
+    c.set_state(np.stack([r, r * u, r * v, pinf / 0.4 + 0.5 * r * (u * u + v * v)]))
+    face_of_seg = np.repeat(np.arange(4), segs_per_face)
+    L = (hi - lo) / segs_per_face
+    mu = 1.0 / re
+    F = mu * L * segs_per_face * sum(gammas[k] * np.array(tang[k]) for k in range(4))
+    return c, face_of_seg, mu, F
+
+
+def test_force_integral_wall_shear_closed_form(orc):
+    """Eq. 9's viscous term: in a gas sliding along each face of a rectangle with u_t = gamma_k d (a linear
+    shear layer, exact wall shear mu gamma_k), every segment's skin friction is 2 mu gamma_k / (rho U^2) and the
+    net force is mu L sum_k gamma_k t_k: the traction acts along +t where the gas outruns the wall.  Shear rates
+    of both signs and different sizes per face, a body at rest and one translating at constant velocity with
+    the gas carried along (only the velocity relative to the wall shears), two Reynolds numbers.  A sign,
+    factor, probe-distance or relative-velocity error in tau_w = mu (u_P - U_wall).t / h fails it."""
+    for vel in ((0.0, 0.0), (0.3, -0.2)):
+        for re, gammas in ((50.0, (1.0, -2.0, 0.5, -1.5)), (400.0, (-0.7, 0.3, 2.0, 1.1))):
+            c, face, mu, F = _shear_layer_case(orc, vel, gammas, re)
+            cp, cf = c.surface()
+            assert np.all(np.isfinite(cf))
+            np.testing.assert_allclose(cf, 2.0 * mu * np.array(gammas)[face], rtol=1e-12, atol=1e-14)
+            np.testing.assert_allclose(cp, 0.0, atol=1e-9)
+            f = c.forces()
+            np.testing.assert_allclose(f[2:], F, rtol=1e-12, atol=1e-14)
+            np.testing.assert_allclose(f[:2], F / 0.5, rtol=1e-12, atol=1e-14)
