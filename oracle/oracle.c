@@ -174,30 +174,58 @@ void orc_classify_points(int nv, const double *verts, int np, const double *pts,
 
 /* ------------------------------------------------------------------------- */
 /* Sec. 3.2, 3-D: ray casting against a closed triangulated surface with the  */
-/* Moller-Trumbore ray/triangle test (barycentric u, v and distance t from a  */
-/* 3x3 system solved by Cramer's rule).  Reading: a ray through an edge or a  */
-/* vertex can count twice (inclusive barycentric bounds) or not at all, so    */
-/* three fixed rays (+x and two oblique directions) are cast and the parity   */
-/* of the majority decides; nodes outside the axis-aligned bounding box are   */
-/* fluid.                                                                     */
+/* Moller-Trumbore ray/triangle test: the ray hits a triangle when the       */
+/* barycentric coordinates of its crossing with the triangle's plane are    */
+/* all non-negative and the crossing lies ahead of the node.  For a ray      */
+/* along a coordinate axis the unnormalised barycentric coordinates are the */
+/* three edge functions of the triangle projected along the ray,            */
+/*   E_ab(P) = (b_u - a_u)(P_v - a_v) - (b_v - a_v)(P_u - a_u),             */
+/* each divided by the projected area; (u, v) the other two coordinates in  */
+/* cyclic order.  Reading (the paper is silent on rays through an edge or a */
+/* vertex, where inclusive bounds count a crossing twice and exclusive ones */
+/* not at all): every edge function is evaluated with the edge's endpoints  */
+/* in increasing vertex index, so the two triangles sharing an edge see     */
+/* exactly opposite values, and a zero takes the sign of a symbolic shift   */
+/* of the node by (eps, eps^2) in (u, v), i.e. the sign of -(b_v - a_v),    */
+/* else of (b_u - a_u).  Each edge and vertex crossing is then counted once */
+/* and one ray decides; three rays (+x, +y, +z) vote, so that a node within */
+/* rounding of a face (where the "ahead" test t > 0 is decided by rounding) */
+/* is still classified by the majority.  Nodes outside the axis-aligned     */
+/* bounding box are fluid.                                                  */
 /* ------------------------------------------------------------------------- */
-static int ray_parity_3d(int ntri, const double *v, const int *tri, const double o[3], const double d[3]) {
+static int edge_sign(const double *pa, int ia, const double *pb, int ib, const double P[3], int u, int v) {
+  int flip = 1;
+  if (ib < ia) { /* canonical order: lower vertex index first */
+    const double *t = pa;
+    pa = pb;
+    pb = t;
+    flip = -1;
+  }
+  double du = pb[u] - pa[u], dv = pb[v] - pa[v];
+  double e = du * (P[v] - pa[v]) - dv * (P[u] - pa[u]);
+  int sg = e > 0.0 ? 1 : (e < 0.0 ? -1 : 0);
+  if (sg == 0) sg = -dv > 0.0 ? 1 : (-dv < 0.0 ? -1 : 0);
+  if (sg == 0) sg = du > 0.0 ? 1 : (du < 0.0 ? -1 : 0);
+  return flip * sg;
+}
+
+static int ray_parity_3d(int ntri, const double *vtx, const int *tri, const double o[3], int axis) {
+  const int u = (axis + 1) % 3, v = (axis + 2) % 3;
   int hits = 0;
   for (int f = 0; f < ntri; f++) {
-    const double *a = v + 3 * tri[3 * f], *b = v + 3 * tri[3 * f + 1], *c = v + 3 * tri[3 * f + 2];
+    const int i0 = tri[3 * f], i1 = tri[3 * f + 1], i2 = tri[3 * f + 2];
+    const double *a = vtx + 3 * i0, *b = vtx + 3 * i1, *c = vtx + 3 * i2;
+    int s0 = edge_sign(a, i0, b, i1, o, u, v);
+    int s1 = edge_sign(b, i1, c, i2, o, u, v);
+    int s2 = edge_sign(c, i2, a, i0, o, u, v);
+    if (s0 == 0 || s0 != s1 || s1 != s2) continue; /* outside the projected triangle (or degenerate edge) */
+    /* crossing ahead of the node: t = n.(a - o) / n_axis > 0, n = (b - a) x (c - a) */
     double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
     double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-    double pv[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2], d[0] * e2[1] - d[1] * e2[0]};
-    double det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
-    if (det == 0.0) continue; /* ray parallel to the triangle's plane */
-    double tv[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
-    double u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) / det;
-    if (u < 0.0 || u > 1.0) continue;
-    double qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
-    double w = (d[0] * qv[0] + d[1] * qv[1] + d[2] * qv[2]) / det;
-    if (w < 0.0 || u + w > 1.0) continue;
-    double t = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) / det;
-    if (t > 0.0) hits++;
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    if (n[axis] == 0.0) continue; /* plane parallel to the ray */
+    double num = n[0] * (a[0] - o[0]) + n[1] * (a[1] - o[1]) + n[2] * (a[2] - o[2]);
+    if ((num > 0.0 && n[axis] > 0.0) || (num < 0.0 && n[axis] < 0.0)) hits++;
   }
   return hits & 1;
 }
@@ -210,10 +238,6 @@ void orc_classify_points_3d(int nv, const double *verts, int ntri, const int *tr
       if (verts[3 * k + a] < lo[a]) lo[a] = verts[3 * k + a];
       if (verts[3 * k + a] > hi[a]) hi[a] = verts[3 * k + a];
     }
-  /* +x and two oblique unit directions with irrational-looking components (no grid or mesh alignment) */
-  static const double dirs[3][3] = {{1.0, 0.0, 0.0},
-                                    {0.5773502691896258, 0.5773502691896258, -0.5773502691896258},
-                                    {-0.2672612419124244, 0.5345224838248488, 0.8017837257372732}};
   for (int n = 0; n < np; n++) {
     const double *o = pts + 3 * n;
     if (o[0] < lo[0] || o[0] > hi[0] || o[1] < lo[1] || o[1] > hi[1] || o[2] < lo[2] || o[2] > hi[2]) {
@@ -221,7 +245,7 @@ void orc_classify_points_3d(int nv, const double *verts, int ntri, const int *tr
       continue;
     }
     int votes = 0;
-    for (int r = 0; r < 3; r++) votes += ray_parity_3d(ntri, verts, tris, o, dirs[r]);
+    for (int r = 0; r < 3; r++) votes += ray_parity_3d(ntri, verts, tris, o, r);
     solid[n] = (uint8_t)(votes >= 2);
   }
 }
