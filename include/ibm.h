@@ -188,6 +188,23 @@ ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, int src_on_
  * with C = F / (1/2 rho_inf U_ref^2 ref_len).  Synchronises. */
 ibm_status ibm_forces(ibm_case *c, double out[4]);
 
+/* Surface distributions at the current time (Sec. 6, the integrand of Eq. 9): for each of the body's nseg
+ * segments (segment e runs from vertex e to vertex e + 1 of the current pose) the wall pressure coefficient
+ * cp[e] = (p_s - p_inf) / (rho_inf U_ref^2 / 2) and the skin-friction coefficient cf[e] = tau_w /
+ * (rho_inf U_ref^2 / 2) at its midpoint, evaluated exactly as ibm_forces evaluates them (p_s the probe
+ * pressure carried to the wall by the wall condition, tau_w = mu (u_P - U_wall).t / h); NaN where no probe
+ * square was found.  cp, cf: host arrays of nseg doubles (caller-owned).  IBM_EINVAL unless nseg equals the
+ * body's vertex count.  Synchronises. */
+ibm_status ibm_surface(ibm_case *c, double *cp, double *cf, int nseg);
+
+/* Measured arithmetic ceiling (no counterpart in the paper; the rooflines of the ALU-bound kernels are
+ * taken against it): one launch of iters fused multiply-adds per recurrence, 8 independent recurrences per
+ * thread, 4 blocks of 256 threads per SM, in FP32 (fp64 = 0) or FP64 (fp64 = 1) on the current device,
+ * after a short warm-up launch.  flops_per_s = 2 x FMAs / the launch's CUDA-event time, ms = that time.
+ * Allocates and frees a small output buffer; synchronises the device's legacy default stream.
+ * IBM_EINVAL for iters <= 0 or NULL outputs. */
+ibm_status ibm_fma_peak(int fp64, long long iters, double *flops_per_s, double *ms);
+
 /* Wait for the case's stream; report asynchronous errors. */
 ibm_status ibm_sync(ibm_case *c);
 
@@ -306,9 +323,12 @@ const char *ibm_last_error(void);
  * Asynchronous on cuda_stream (NULL = legacy default stream).  Sizes beyond
  * the limits return IBM_EINVAL before any GPU work.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
- * share the one array, so calls that overlap on the GPU (other streams,
- * other host threads) race and must be serialised by the caller. */
+ * device current; make that first call before any stream capture.  The
+ * address is kept for the life of the process: after cudaDeviceReset (or any
+ * teardown of the device's primary context) it is stale, so do not call this
+ * entry point on that device again in the same process.  All calls share the
+ * one array, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
 ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, int nverts, uint8_t *d_tags,
                                  int32_t *d_cells, int32_t capacity, int32_t *d_counts, void *cuda_stream);
 

@@ -24,6 +24,7 @@ struct ibm_case {
   // device memory
   double *vref = nullptr, *vx = nullptr, *vy = nullptr, *snx = nullptr, *sny = nullptr, *vnx = nullptr,
          *vny = nullptr, *vk = nullptr;
+  double *surf = nullptr;  // per segment (Cp, Cf) of the last ibm_surface call
   double *A = nullptr, *B = nullptr, *C = nullptr;  // FP64 conserved: state, stage arrays (FP64 mode)
   double *Wn = nullptr, *Wm = nullptr;               // dual time: states at time levels n and n-1
   double *G = nullptr;  // FP32-bulk dual time: the step's constant part of the BDF term (in place of W^{n-1})
@@ -206,6 +207,7 @@ static size_t carve(ibm_case *c, char *base) {
   take(&c->vnx, nv);
   take(&c->vny, nv);
   take(&c->vk, nv);
+  take(&c->surf, 2 * nv);
   take(&c->A, 4 * plane);
   if (c->precision == IBM_PREC_FP64) {
     take(&c->B, 4 * plane);
@@ -1115,6 +1117,21 @@ extern "C" ibm_status ibm_forces(ibm_case *c, double out[4]) {
   ibm_status r = sync_and_check(c);
   for (int q = 0; q < 4; q++) out[q] = c->hds->force[q];
   return r;
+}
+
+extern "C" ibm_status ibm_surface(ibm_case *c, double *cp, double *cf, int nseg) {
+  if (!c || !cp || !cf) return fail(IBM_EINVAL, "case or output is NULL");
+  if (nseg != c->g.nv) return fail(IBM_EINVAL, "nseg %d differs from the body's %d segments", nseg, c->g.nv);
+  if (c->g.nv <= 0) return IBM_OK;
+  if (!c->classified) {
+    ibm_status r = do_classify(c);
+    if (r != IBM_OK) return r;
+  }
+  launch_forces_f64(c->k, c->g, c->tag, c->A, c->precision == IBM_PREC_FP32_BULK, c->ds, c->stream, false, c->surf);
+  c->launches++;
+  CU(cudaMemcpyAsync(cp, c->surf, (size_t)nseg * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(cf, c->surf + nseg, (size_t)nseg * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return sync_and_check(c);
 }
 
 extern "C" ibm_status ibm_destroy_case(ibm_case *c) {

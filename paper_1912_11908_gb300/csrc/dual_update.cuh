@@ -129,7 +129,7 @@ __device__ __forceinline__ void dual_update_cell(const Consts &k, const PertCons
   const float csf = sqrtf(c.gamma * (c.R + f64_to_f32(Qk[0])) * irf), icsf = 1.f / csf;
   const float Vm = sqrtf(uf * uf + vf * vf);
   float Ur = fmaxf(fmaxf(Vm, 1.f), c.mu * irf / c.dmin);
-  Ur = fminf(fmaxf(Ur, (float)UR_FLOOR * csf), csf);
+  Ur = fminf(Ur, csf);
   const float mr2 = (Ur * icsf) * (Ur * icsf);
   const float up = 0.5f * Vm * (1.f + mr2);
   const float om = 1.f - mr2;

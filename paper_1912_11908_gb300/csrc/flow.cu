@@ -203,7 +203,7 @@ __device__ __forceinline__ void ldfss_f64(double rL, double unL, double utL, dou
   const double MhM = Mh * (1.0 - (adp - dp) * ic2 / rR);
   const double Cp = CVL - MhP, Cm = CVR + MhM;
   double DL, DR;
-  if (PRE && mr2 < 1.0) {  // pressure split with the physical Mach numbers
+  if (PRE && mr2 < 1.0) {  // pressure split with the physical Mach numbers (its dissipation scaled below)
     const double ic = 1.0 / cb;
     const double mL = unL * ic, mR = unR * ic;
     const double paL = mL >= 0.0 ? 1.0 : 0.0, paR = mR >= 0.0 ? 0.0 : 1.0;
@@ -219,8 +219,14 @@ __device__ __forceinline__ void ldfss_f64(double rL, double unL, double utL, dou
     DR = aR * (1.0 + bR) - bR * PmR;
   }
   const double mL = rL * cs * Cp, mR = rR * cs * Cm;
+  double ph = DL * pL + DR * pR;
+  if (PRE && mr2 < 1.0) {
+    // low-Mach scaling: the split's departure from the face mean (its rho c du dissipation) times c'/c
+    const double fa = cs / cb;
+    ph = 0.5 * (pL + pR) + fa * ((DL - 0.5) * pL + (DR - 0.5) * pR);
+  }
   F[0] = mL + mR;
-  F[1] = mL * unL + mR * unR + DL * pL + DR * pR;
+  F[1] = mL * unL + mR * unR + ph;
   F[2] = mL * utL + mR * utR;
   F[3] = mL * HL + mR * HR;
 }
@@ -239,7 +245,7 @@ __device__ __forceinline__ void ldfss_f64(double rL, double unL, double utL, dou
 constexpr int TX = 16, TY = 16, HX = TX + 2 * NG, HY = TY + 2 * NG;
 
 // Low-Mach preconditioning parameter at a face (dual time): reference velocity
-// Ur = min(c, max(|V|, U_ref, nu/dn, c/3)) from face-averaged c, |V|, rho;
+// Ur = min(c, max(|V|, U_ref, nu/dn)) from face-averaged c, |V|, rho;
 // returns Mr^2 = (Ur/c)^2.  States (rho, u, v, p).
 __device__ __forceinline__ double face_mr2(const Consts &k, const double qL[4], const double qR[4], double dn) {
   const double cb = 0.5 * (sqrt(k.gamma * qL[3] / qL[0]) + sqrt(k.gamma * qR[3] / qR[0]));
@@ -247,7 +253,6 @@ __device__ __forceinline__ double face_mr2(const Consts &k, const double qL[4], 
   const double Vm = sqrt(ub * ub + vb * vb);
   const double rb = 0.5 * (qL[0] + qR[0]);
   double Ur = fmax(fmax(Vm, 1.0), k.mu / rb / dn);
-  Ur = fmax(Ur, UR_FLOOR * cb);
   Ur = fmin(Ur, cb);
   const double m = (Ur / cb) * (Ur / cb);
   return fmin(m, 1.0);
@@ -461,7 +466,7 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
   const double cs = sqrt(k.gamma * pr / r);
   const double Vm = sqrt(iu * iu + iv * iv);
   double Ur = fmax(fmax(Vm, 1.0), k.mu / r / k.dmin);
-  Ur = fmin(fmax(Ur, UR_FLOOR * cs), cs);
+  Ur = fmin(Ur, cs);
   const double mr2 = (Ur / cs) * (Ur / cs);
   const double up = 0.5 * Vm * (1.0 + mr2);
   const double om = 1.0 - mr2;

@@ -8,6 +8,7 @@
 // no contraction, so tags, lists and stencils are reproducible bit for bit by
 // any IEEE implementation that performs the same operations in the same
 // order.  No transcendental function is used on these paths.
+#include <math_constants.h>
 #include <mutex>
 
 #include <algorithm>
@@ -956,7 +957,7 @@ void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_ste
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint8_t *__restrict__ tag,
                                                     const double *__restrict__ A, bool pert, DevState *ds,
-                                                    bool set_accel) {
+                                                    bool set_accel, double *__restrict__ surf) {
   __shared__ double rx[256], ry[256];
   double V[2], Acc[2], X[2];
   body_motion(k, ds, ds->t, X, V, Acc);
@@ -977,7 +978,10 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
       if (mask) break;
       if (stp < 3) xi = xi + k.dmin;
     }
-    if (!mask) continue;
+    if (!mask) {
+      if (surf) surf[e] = surf[g.nv + e] = CUDART_NAN;
+      continue;
+    }
     double qp[4] = {0.0, 0.0, 0.0, 0.0};
     for (int q = 0; q < 4; q++) {
       if (!(mask >> q & 1)) continue;
@@ -1005,6 +1009,10 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
     }
     double ps = qp[0] * exp(-xi * G / (k.R * qp[3]));
     double tau = k.mu * ((qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty) / xi;
+    if (surf) {  // Eq. 9 integrand: (p_s - p_inf) / (rho_inf U^2 / 2), tau / (rho_inf U^2 / 2)
+      surf[e] = (ps - k.pinf) / 0.5;
+      surf[g.nv + e] = tau / 0.5;
+    }
     sx += (-(ps - k.pinf) * nx + tau * tx) * L;
     sy += (-(ps - k.pinf) * ny + tau * ty) * L;
   }
@@ -1034,8 +1042,8 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
 }
 
 void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, bool pert,
-                       DevState *ds, cudaStream_t s, bool set_accel) {
-  k_forces_f64<<<1, 256, 0, s>>>(k, g, tag, A, pert, ds, set_accel);
+                       DevState *ds, cudaStream_t s, bool set_accel, double *surf) {
+  k_forces_f64<<<1, 256, 0, s>>>(k, g, tag, A, pert, ds, set_accel, surf);
 }
 
 // Sec. 6, Eq. 10: end of a step of a body translating under the fluid force.  The step's constant

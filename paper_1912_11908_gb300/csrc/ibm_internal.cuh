@@ -79,8 +79,6 @@ struct Consts {
   double idt_phys;  // dual time: 1/dt_phys
 };
 
-// Bounded low-Mach preconditioning: reference velocity never below c/3.
-constexpr double UR_FLOOR = 1.0 / 3.0;
 
 // geometry arrays (device)
 struct Geom {
@@ -223,8 +221,9 @@ int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_
                           int maxh, DevState *ds, cudaStream_t s);
 // A: FP64 state, absolute conserved (pert = false) or perturbation (pert = true)
 void launch_body_end(DevState *ds, cudaStream_t s);
+// surf (optional): per segment the pressure and skin-friction coefficients, surf[e] and surf[nv + e]
 void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, bool pert,
-                       DevState *ds, cudaStream_t s, bool set_accel = false);
+                       DevState *ds, cudaStream_t s, bool set_accel = false, double *surf = nullptr);
 
 // ---- launchers (flow.cu) ----
 void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch);

@@ -58,9 +58,10 @@ __device__ __forceinline__ void prim_pert(const PertConsts &c, float pp, float u
 //
 // PRE (dual time, Sec. 2): the low-Mach numerical sound speed
 // c' = 1/2 sqrt((1 - Mr^2)^2 un^2 + 4 Mr^2 c^2), Mr^2 = (Ur/c)^2 with
-// Ur = min(c, max(|V|, U_ref, nu/dn, c/3)) from face averages (idn = 1/dn),
-// scales the mass-flux (dissipation) part; the pressure split keeps the
-// physical face Mach numbers, as in the FP64 path.
+// Ur = min(c, max(|V|, U_ref, nu/dn)) from face averages (idn = 1/dn),
+// scales the mass-flux (dissipation) part; the pressure split takes the
+// physical face Mach numbers and its departure from the face mean (the
+// rho c du dissipation) is scaled by c'/c, as in the FP64 path.
 template <bool PRE = false>
 __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float unL, float utL, float ppL,
                                            float drR, float unR, float utR, float ppR, float un_inf, float ut_inf,
@@ -79,7 +80,7 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
     const float Vm = sqrtf(ub * ub + vb * vb);
     const float rb = 0.5f * (rL + rR);
     float Ur = fmaxf(fmaxf(Vm, 1.f), c.mu / rb * idn);
-    Ur = fminf(fmaxf(Ur, (float)UR_FLOOR * cb), cb);
+    Ur = fminf(Ur, cb);
     mr2 = fminf((Ur / cb) * (Ur / cb), 1.f);
     const float om = 1.f - mr2;
     cs = 0.5f * sqrtf(om * om * ub * ub + 4.f * mr2 * cb * cb);
@@ -122,8 +123,14 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
     Dm1 = (subL && subR) ? 0.25f * (MR - ML) * (MR * MR + MR * ML + ML * ML - 3.f) : (DL + DR - 1.f);
   }
   const float mL = rL * cs * Cp, mR = rR * cs * Cm;
+  // p_inf (D_L + D_R - 1) + D_L p'_L + D_R p'_R; with low-Mach scaling the departure from the face mean
+  // 1/2 (p'_L + p'_R) is scaled by c'/c
   F[0] = mL + mR;
-  F[1] = mL * unL + mR * unR + c.R * Dm1 + DL * ppL + DR * ppR;
+  if (PRE && mr2 < 1.f)
+    F[1] = mL * unL + mR * unR +
+           (0.5f * (ppL + ppR) + (cs / cb) * (c.R * Dm1 + (DL - 0.5f) * ppL + (DR - 0.5f) * ppR));
+  else
+    F[1] = mL * unL + mR * unR + c.R * Dm1 + DL * ppL + DR * ppR;
   F[2] = mL * utL + mR * utR;
   F[3] = mL * HL + mR * HR;
 }

@@ -58,12 +58,13 @@ class ibm_result(ctypes.Structure):
 
 
 EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state", "ibm_forces",
+           "ibm_surface",
            "ibm_sync", "ibm_destroy_case", "ibm_case_device_bytes", "ibm_launch_count", "ibm_last_error",
            "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs", "ibm_tag_nodes_noalloc",
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
            "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats", "ibm_autotune", "ibm_use_tma",
            "ibm_use_persistent", "ibm_persistent_grid", "ibm_stage_launches",
-           "ibm_check_float_conversions"]
+           "ibm_check_float_conversions", "ibm_fma_peak"]
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 SERVE_BATCHED, SERVE_AUTOTUNE = 1, 2
 SERVER_STATS = ["group_graphs", "group_steps", "group_kernels", "autotune_runs", "capture_us"]
@@ -90,6 +91,9 @@ def load():
     L.ibm_get_state.argtypes = [vp, ip, vp, sz, ip]
     L.ibm_set_state.argtypes = [vp, vp, sz, ip]
     L.ibm_forces.argtypes = [vp, vp]
+    L.ibm_surface.argtypes = [vp, vp, vp, ip]
+    L.ibm_fma_peak.argtypes = [ip, ctypes.c_longlong, vp, vp]
+    L.ibm_fma_peak.restype = ip
     L.ibm_sync.argtypes = [vp]
     L.ibm_destroy_case.argtypes = [vp]
     L.ibm_case_device_bytes.argtypes = [ctypes.POINTER(ibm_geometry), ctypes.POINTER(ibm_grid),
@@ -128,7 +132,7 @@ def load():
                  "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats"):
         getattr(L, name).restype = ip
     for name in ("ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state",
-                 "ibm_forces", "ibm_sync", "ibm_destroy_case", "ibm_profile_enable", "ibm_profile_read",
+                 "ibm_forces", "ibm_surface", "ibm_sync", "ibm_destroy_case", "ibm_profile_enable", "ibm_profile_read",
                  "ibm_use_graphs"):
         getattr(L, name).restype = ip
     return L
@@ -182,6 +186,13 @@ def marshal(spec):
     mo.vel[0], mo.vel[1] = spec.get("vel", (0.0, 0.0))
     mo.mass = spec.get("mass", 0.0)
     return verts, geo, gr, fl, mo
+
+
+def fma_peak(fp64, iters):
+    """Measured FMA rate of the current device: (flop/s, launch ms) for FP32 (fp64 False) or FP64."""
+    f, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().ibm_fma_peak(int(bool(fp64)), int(iters), ctypes.byref(f), ctypes.byref(ms)))
+    return f.value, ms.value
 
 
 def ibm_tag_nodes_noalloc(spec, d_verts, nverts, d_tags, d_cells, capacity, d_counts, stream=None):
@@ -285,6 +296,14 @@ class Case:
         out = np.zeros(4, np.float64)
         _check(lib().ibm_forces(self.h, out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    def surface(self):
+        """Per segment (Eq. 9 integrand at the midpoints): pressure and skin-friction coefficients."""
+        n = int(self.spec["verts"].shape[0])
+        cp = np.zeros(n, np.float64)
+        cf = np.zeros(n, np.float64)
+        _check(lib().ibm_surface(self.h, cp.ctypes.data_as(ctypes.c_void_p), cf.ctypes.data_as(ctypes.c_void_p), n))
+        return cp, cf
 
     def forces_into(self, ptr):
         """Forces written to caller memory at ptr (host, 4 doubles)."""

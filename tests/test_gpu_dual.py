@@ -1,7 +1,8 @@
 """Dual time stepping on the GPU (FP64 and FP32-bulk) against the FP64 oracle.
 
 BDF2 physical time, preconditioned point-implicit pseudo time in three stages per sub-iteration, FP64 4x4 solve per
-cell (Sec. 2).  Bar: state within 1e-10 relative after several physical steps; tags / stencils as for RK3.
+cell (Sec. 2).  Bar: FP64 state within 1e-10 relative after several physical steps, or within four times the
+oracle's own conditioning floor where that is larger (see ulp_floor); tags / stencils as for RK3.
 """
 import math
 
@@ -9,6 +10,7 @@ import numpy as np
 import pytest
 
 from paper_1912_11908_gb300 import workloads as W
+from flowmetrics import fp64_bar
 
 pytestmark = pytest.mark.gpu
 
@@ -39,9 +41,10 @@ def test_dual_cylinder_parity(ibm, orc, M):
     g.step(6)
     o.step(6)
     assert abs(g.time()[0] - o.time()) < 1e-12
-    err = _err(g.state(), o.state(), o.tags())
-    assert err <= 1e-10, err
-    np.testing.assert_allclose(g.forces(), o.forces(), rtol=1e-8, atol=1e-8)
+    err, bar = _err(g.state(), o.state(), o.tags()), fp64_bar(orc, spec, 6)
+    print("dual cylinder M %g: FP64 state %.2e (bar %.2e)" % (M, err, bar))
+    assert err <= bar, (err, bar)
+    np.testing.assert_allclose(g.forces(), o.forces(), rtol=1e-8, atol=max(1e-8, bar))
 
 
 def test_dual_naca_sharp_te_parity(ibm, orc):
@@ -51,8 +54,9 @@ def test_dual_naca_sharp_te_parity(ibm, orc):
     g.step(4)
     o.step(4)
     np.testing.assert_array_equal(g.tags(), o.tags())
-    err = _err(g.state(), o.state(), o.tags())
-    assert err <= 1e-10, err
+    err, bar = _err(g.state(), o.state(), o.tags()), fp64_bar(orc, spec, 4)
+    print("dual NACA sharp TE: FP64 state %.2e (bar %.2e)" % (err, bar))
+    assert err <= bar, (err, bar)
 
 
 def test_dual_entropy_wave_periodic(ibm, orc):
@@ -70,8 +74,9 @@ def test_dual_entropy_wave_periodic(ibm, orc):
     o.set_state(U)
     g.step(5)
     o.step(5)
-    err = _err(g.state(), o.state(), np.zeros((8, nx), np.uint8))
-    assert err <= 1e-10, err
+    err, bar = _err(g.state(), o.state(), np.zeros((8, nx), np.uint8)), fp64_bar(orc, spec, 5, U)
+    print("dual entropy wave: FP64 state %.2e (bar %.2e)" % (err, bar))
+    assert err <= bar, (err, bar)
 
 
 # ---- FP32-bulk dual time: FP32 perturbation residual, FP64 point-implicit update and iterates ----
@@ -97,14 +102,15 @@ def _bulk_vs_oracle(ibm, orc, spec, nsteps):
     return dp, du, df
 
 
-# Tolerances.  The FP32 residual carries face velocities to FP32 rounding (~6e-8 of U); the preconditioned
-# LDFSS dissipation scales velocity differences by rho c', and with the reference-velocity floor c/3 the
-# numerical sound speed is c' >= c/3 = 1/(3M) -- about 33 at M = 0.01 and 333 at M = 0.001 -- so the residual's
-# rounding floor is ~c' * 6e-8 of the dynamic scale and the solution error grows roughly like 1/M^2 (measured:
-# |dCd| 1e-5 at M = 0.01; at M = 0.001 on this 8-cells-per-diameter cylinder 1.2e-4, and 1.9e-3 with an earlier
-# ordering of the same FP32 operations -- the floor is rounding noise, amplified; 2.1e-4 on the NACA0012 case of
-# the M = 0.001 configuration, whose target is 1e-3).
-@pytest.mark.parametrize("M,force_tol", [(0.01, 1e-4), (0.001, 3e-3)])
+# Tolerances.  The FP32 residual carries face velocities to FP32 rounding (~6e-8 of U) and pressure perturbations
+# to ~6e-8 of their own size (the perturbation form keeps p_inf = 1/(gamma M^2) out of every FP32 sum).  The
+# preconditioned LDFSS dissipation scales velocity differences by rho c' with c' of the order of the reference
+# velocity U_r = max(|V|, U_ref, nu/dn) -- independent of M -- so the rounding floor of the residual is ~1e-7 of
+# the dynamic scale at any Mach number; the pseudo-time coefficients (FP32) change the path of the sub-iterations
+# but not their fixed point.  Bounds: |dCd|, |dCl| <= 1e-4 at M = 0.01 and the configuration's 1e-3 at
+# M = 0.001 (a coarse 8-cells-per-diameter cylinder, 10 sub-iterations: the pseudo iteration is far from converged,
+# so FP32 rounding of the path is not damped out).
+@pytest.mark.parametrize("M,force_tol", [(0.01, 1e-4), (0.001, 1e-3)])
 def test_bulk_dual_cylinder_vs_fp64_oracle(ibm, orc, M, force_tol):
     nx, ny = 96, 48
     spec = W.case_spec(W.cylinder(128), nx, ny, (-3.0, 9.0, -3.0, 3.0), M, 40.0, W.FAR, time_scheme=W.TIME_DUAL,
