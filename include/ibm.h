@@ -65,8 +65,12 @@ enum { IBM_BC_FREESTREAM = 0, IBM_BC_OUTFLOW = 1, IBM_BC_PERIODIC = 2 };
 /* body motion: prescribed displacement X(t) = amp sin(2 pi freq t) (SIN) or vel t (CONST), or translation
  * under the fluid force (COUPLED, Sec. 6, Eq. 10): initial velocity vel, mass per unit depth `mass`; each step
  * the force at its start sets a constant acceleration F / mass for the step, the position advances by
- * U dt + dt^2 F / (2 mass) and the velocity by dt F / mass (explicit RK3 only) */
-enum { IBM_MOTION_STATIC = 0, IBM_MOTION_SIN = 1, IBM_MOTION_CONST = 2, IBM_MOTION_COUPLED = 3 };
+ * U dt + dt^2 F / (2 mass) and the velocity by dt F / mass (explicit RK3 only), or pitching about a pivot
+ * (PITCH, Sec. 7.2): incidence alpha(t) = pitch_mean - pitch_amp cos(2 pi freq t), nose up = clockwise, so the
+ * body (given at zero incidence) is turned by -alpha(t) about `pivot`, its normals with it; the wall's velocity
+ * and acceleration at a surface point r from the pivot are those of the rigid rotation, omega x r and
+ * domega/dt x r - omega^2 r */
+enum { IBM_MOTION_STATIC = 0, IBM_MOTION_SIN = 1, IBM_MOTION_CONST = 2, IBM_MOTION_COUPLED = 3, IBM_MOTION_PITCH = 4 };
 /* arithmetic: FP64 throughout, or FP32 bulk (stage values and fluxes in FP32
  * on perturbations from the free stream, FP64 state accumulation) */
 enum { IBM_PREC_FP64 = 0, IBM_PREC_FP32_BULK = 1 };
@@ -75,8 +79,13 @@ enum { IBM_IB_REBUILD = 0, IBM_IB_ADVANCE = 1 };
 /* time stepping: explicit SSP-RK3 with the CFL rule, or dual time (Sec. 2):
  * three-point (BDF2) physical-time derivative, preconditioned pseudo time,
  * each sub-iteration one point-implicit three-stage pseudo step with a 4x4
- * FP64 solve per cell; low-Mach scaling bounded at Ur >= c/3 */
+ * FP64 solve per cell; low-Mach scaling with the reference velocity
+ * Ur = min(c, max(|V|, U_ref, nu/dx)) */
 enum { IBM_TIME_RK3 = 0, IBM_TIME_DUAL = 1 };
+/* face reconstruction of the inviscid flux (Sec. 2): fifth-order WENO (Jiang-Shu), or the second-order TVD
+ * scheme read as MUSCL with the minmod limiter, f_i + 1/2 minmod(f_i - f_{i-1}, f_{i+1} - f_i), on the same
+ * variables (rho, u, v, p) */
+enum { IBM_SCHEME_WENO5 = 0, IBM_SCHEME_TVD2 = 1 };
 /* stencil regions (Sec. 4.1): closest feature is a segment interior or a
  * vertex; FALLBACK = the line along the local normal met no segment on the
  * surface side, the boundary point is the closest point */
@@ -107,9 +116,10 @@ typedef struct {
   int subiters;     /* dual time: pseudo-time sub-iterations per physical step (>= 1) */
   int ib_mode;      /* IBM_IB_REBUILD: IB nodes rebuilt from their probes every stage (Sec. 4.4-4.6);
                        IBM_IB_ADVANCE: IB nodes advanced by the flux update, the wall imposed by the ghost
-                       layers alone (Sec. 5) -- not with FP32-bulk dual time (IBM_EINVAL) */
+                       layers alone (Sec. 5) */
   double dt_phys;   /* dual time: physical time step (> 0) */
   double cfl_tau;   /* dual time: pseudo-time CFL number (> 0) */
+  int scheme;       /* IBM_SCHEME_* */
 } ibm_flow;
 
 typedef struct {
@@ -118,6 +128,8 @@ typedef struct {
   double freq;
   double vel[2];    /* CONST: velocity; COUPLED: initial velocity */
   double mass;      /* COUPLED: body mass per unit depth (> 0), in units of rho_inf L^2 */
+  double pivot[2];  /* PITCH: centre of rotation */
+  double pitch_mean, pitch_amp;  /* PITCH: mean incidence and amplitude (radians) */
 } ibm_motion;
 
 /* One IB or ghost node and its reconstruction stencil (Sec. 4.1-4.6, Sec. 5).
@@ -197,6 +209,85 @@ ibm_status ibm_forces(ibm_case *c, double out[4]);
  * body's vertex count.  Synchronises. */
 ibm_status ibm_surface(ibm_case *c, double *cp, double *cf, int nseg);
 
+/* ---- 3-D immersed-boundary pre-processing (Sec. 3.2, Sec. 4.1-4.2; Appendix A) ----
+ *
+ * A closed, consistently oriented triangulated surface (each directed edge in
+ * one face, its reverse in the neighbouring face; counter-clockwise seen from
+ * outside) against a uniform lattice of nx * ny * nz nodes over [lo, hi]: node
+ * (i, j, k) sits at lo + (index + 1/2) (hi - lo) / n along each axis, node
+ * index (k ny + j) nx + i.  One classification runs, on the body's stream:
+ *   - ray casting (Sec. 3.2): nodes outside the surface's axis-aligned
+ *     bounding box are fluid; inside it, rays along +x, +y and +z each count
+ *     their crossings with the Moller-Trumbore barycentric test, written as
+ *     the three edge functions of the face projected along the ray, every edge
+ *     evaluated with its endpoints in increasing vertex index and a zero value
+ *     resolved by a symbolic shift of the node, so that a crossing through an
+ *     edge or a vertex counts exactly once; a node is solid when at least two
+ *     of the three crossing counts are odd;
+ *   - tagging over the 6-neighbourhood: IB = fluid node with a solid
+ *     neighbour; G1..G3 = solid node whose nearest non-solid node along a
+ *     lattice line is 1..3 nodes away (IBM_TAG_*);
+ *   - ordered lists: the IB nodes, then G1, G2, G3, each in node-index order;
+ *   - closest feature of every listed node (Sec. 4.1): exhaustive over the
+ *     faces, the plane projection when it falls inside a face, else the
+ *     nearest point of its edges; equal distances keep the lowest face; and
+ *     its pseudo-normal (Sec. 4.2): the face normal, the angle-weighted vertex
+ *     normal (Eq. 2) or the normalised sum of the two faces' normals at an edge
+ *     (Eq. 3), all pointing out of the body.
+ * The computation uses IEEE basic operations and sqrt only (face and vertex
+ * normals, which need acos, are formed once on the host at creation), so its
+ * results are reproducible bit for bit.  The 3-D flow solver is not built: a
+ * body can be classified, not stepped. */
+typedef struct ibm_body3d ibm_body3d;
+
+typedef struct {
+  int nx, ny, nz;   /* lattice nodes per axis, each >= 1, product < 2^31 */
+  double lo[3], hi[3];
+} ibm_grid3d;
+
+enum { IBM_FEATURE_FACE = 0, IBM_FEATURE_EDGE = 1, IBM_FEATURE_VERTEX = 2 };
+
+/* one listed node and its closest surface feature */
+typedef struct {
+  int32_t node;      /* node index (k ny + j) nx + i */
+  int32_t tri;       /* face holding the closest point */
+  int32_t kind;      /* IBM_FEATURE_* */
+  int32_t reserved;
+  double cp[3];      /* closest point on the surface */
+  double n[3];       /* unit pseudo-normal of the feature, out of the body */
+} ibm_closest3d;
+
+/* what for ibm_body3d_get */
+enum {
+  IBM_3D_TAGS = 0,     /* uint8_t[nz][ny][nx] */
+  IBM_3D_COUNTS = 1,   /* int32_t[4]: #IB, #G1, #G2, #G3 */
+  IBM_3D_NODES = 2,    /* int32_t[#IB + #G1 + #G2 + #G3]: node indices, IB first, each class in index order */
+  IBM_3D_CLOSEST = 3   /* ibm_closest3d[#IB + #G1 + #G2 + #G3], in the order of IBM_3D_NODES */
+};
+
+/* Copy a surface (verts: 3*nverts doubles, tris: 3*ntris vertex indices; host
+ * memory, copied) to the device and form its face normals, angle-weighted
+ * vertex normals and edge neighbours.  cuda_stream: a cudaStream_t or NULL
+ * (the body then creates its own).  IBM_EINVAL for fewer than 4 vertices or
+ * faces or an index out of range, IBM_ENOMEM / IBM_ECUDA on device errors. */
+ibm_status ibm_body3d_create(const double *verts, int nverts, const int32_t *tris, int ntris, void *cuda_stream,
+                             ibm_body3d **out);
+
+/* Classify the lattice, tag it, build the lists and the closest features
+ * (five kernels, asynchronous on the body's stream).  Device buffers are
+ * (re)allocated when the lattice size changes; the lists hold the nodes
+ * within three nodes of the bounding box.  IBM_EINVAL for an empty or
+ * oversized lattice. */
+ibm_status ibm_body3d_classify(ibm_body3d *b, const ibm_grid3d *grid);
+
+/* Copy a result of the last classification to host memory (synchronises the
+ * body's stream).  IBM_ESTATE before any classification; IBM_ECAPACITY (after
+ * copying what fits) if the lists overflowed. */
+ibm_status ibm_body3d_get(ibm_body3d *b, int what, void *dst, size_t bytes);
+
+/* Release the body's device memory (and its own stream).  NULL is a no-op. */
+ibm_status ibm_body3d_destroy(ibm_body3d *b);
+
 /* Measured arithmetic ceiling (no counterpart in the paper; the rooflines of the ALU-bound kernels are
  * taken against it): one launch of iters fused multiply-adds per recurrence, 8 independent recurrences per
  * thread, 4 blocks of 256 threads per SM, in FP32 (fp64 = 0) or FP64 (fp64 = 1) on the current device,
@@ -244,7 +335,11 @@ ibm_status ibm_autotune(ibm_case *c, int enable);
  * tensor copy (cp.async.bulk.tensor) per tile instead of per-thread loads
  * (default on where the driver provides the tensor-map encoder).  The values
  * loaded are the same, so results do not depend on the choice.  enable = 0
- * uses per-thread loads for every tile. */
+ * uses per-thread loads for every tile.  The wait for a copy is bounded by
+ * about a second of the GPU's global timer; a block whose copy has not
+ * completed by then waits once more (bounded), leaves its tile unprocessed and
+ * flags the case: the next synchronising call returns IBM_ECUDA and the
+ * state of that step is invalid. */
 ibm_status ibm_use_tma(ibm_case *c, int enable);
 
 /* FP32-bulk stages (Sec. 2; explicit stages and dual-time pseudo stages): how

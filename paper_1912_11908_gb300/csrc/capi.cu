@@ -25,6 +25,7 @@ struct ibm_case {
   double *vref = nullptr, *vx = nullptr, *vy = nullptr, *snx = nullptr, *sny = nullptr, *vnx = nullptr,
          *vny = nullptr, *vk = nullptr;
   double *surf = nullptr;  // per segment (Cp, Cf) of the last ibm_surface call
+  double *rsnx = nullptr, *rsny = nullptr, *rvnx = nullptr, *rvny = nullptr;  // PITCH: reference-pose normals
   double *A = nullptr, *B = nullptr, *C = nullptr;  // FP64 conserved: state, stage arrays (FP64 mode)
   double *Wn = nullptr, *Wm = nullptr;               // dual time: states at time levels n and n-1
   double *G = nullptr;  // FP32-bulk dual time: the step's constant part of the BDF term (in place of W^{n-1})
@@ -113,15 +114,36 @@ static ibm_status fail(ibm_status s, const char *fmt, ...) {
 
 // Upper bound of IB + ghost nodes: every listed node lies within one cell
 // (IB) or three cells (ghost) of the body's bounding box, whatever the pose.
-static int list_capacity(const ibm_geometry *geo, const ibm_grid *gr) {
-  if (!geo || geo->nverts <= 0) return 0;
-  double xmin = geo->verts[0], xmax = xmin, ymin = geo->verts[1], ymax = ymin;
+// Axis-aligned box holding the body in every pose it can take: its vertex box (a translating body's pose only
+// shifts it), or for a pitching body the disc its vertices sweep about the pivot.
+static void body_extent(const ibm_geometry *geo, const ibm_motion *mo, double &xmin, double &xmax, double &ymin,
+                        double &ymax) {
+  xmin = xmax = geo->verts[0];
+  ymin = ymax = geo->verts[1];
   for (int v = 1; v < geo->nverts; v++) {
     xmin = fmin(xmin, geo->verts[2 * v]);
     xmax = fmax(xmax, geo->verts[2 * v]);
     ymin = fmin(ymin, geo->verts[2 * v + 1]);
     ymax = fmax(ymax, geo->verts[2 * v + 1]);
   }
+  if (mo && mo->kind == IBM_MOTION_PITCH) {
+    double r2 = 0.0;
+    for (int v = 0; v < geo->nverts; v++) {
+      const double rx = geo->verts[2 * v] - mo->pivot[0], ry = geo->verts[2 * v + 1] - mo->pivot[1];
+      r2 = fmax(r2, rx * rx + ry * ry);
+    }
+    const double r = sqrt(r2);
+    xmin = mo->pivot[0] - r;
+    xmax = mo->pivot[0] + r;
+    ymin = mo->pivot[1] - r;
+    ymax = mo->pivot[1] + r;
+  }
+}
+
+static int list_capacity(const ibm_geometry *geo, const ibm_grid *gr, const ibm_motion *mo) {
+  if (!geo || geo->nverts <= 0) return 0;
+  double xmin, xmax, ymin, ymax;
+  body_extent(geo, mo, xmin, xmax, ymin, ymax);
   double dx = (gr->hi[0] - gr->lo[0]) / gr->nx, dy = (gr->hi[1] - gr->lo[1]) / gr->ny;
   long long w = (long long)ceil((xmax - xmin) / dx) + 10;
   long long h = (long long)ceil((ymax - ymin) / dy) + 10;
@@ -136,15 +158,10 @@ static size_t pitch_of(int nx) { return (size_t)((nx + 2 * NG + 31) / 32 * 32); 
 // Upper bound of stage tiles (16x16) whose cells or 3-cell halo can hold IB /
 // ghost nodes: tiles meeting the body's bounding box grown by 4 cells, for any
 // pose (plus one tile per axis for the offset against the tile grid).
-static int body_tile_capacity(const ibm_geometry *geo, const ibm_grid *gr, int ntiles) {
+static int body_tile_capacity(const ibm_geometry *geo, const ibm_grid *gr, const ibm_motion *mo, int ntiles) {
   if (!geo || geo->nverts <= 0) return 0;
-  double xmin = geo->verts[0], xmax = xmin, ymin = geo->verts[1], ymax = ymin;
-  for (int v = 1; v < geo->nverts; v++) {
-    xmin = fmin(xmin, geo->verts[2 * v]);
-    xmax = fmax(xmax, geo->verts[2 * v]);
-    ymin = fmin(ymin, geo->verts[2 * v + 1]);
-    ymax = fmax(ymax, geo->verts[2 * v + 1]);
-  }
+  double xmin, xmax, ymin, ymax;
+  body_extent(geo, mo, xmin, xmax, ymin, ymax);
   double dx = (gr->hi[0] - gr->lo[0]) / gr->nx, dy = (gr->hi[1] - gr->lo[1]) / gr->ny;
   long long w = ((long long)ceil((xmax - xmin) / dx) + 8 + 15) / 16 + 2;
   long long h = ((long long)ceil((ymax - ymin) / dy) + 8 + 15) / 16 + 2;
@@ -169,7 +186,8 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
   if (!(fl->cfl > 0) && !(fl->dt_fixed > 0)) return fail(IBM_EINVAL, "cfl or dt_fixed must be positive");
   if (fl->precision != IBM_PREC_FP64 && fl->precision != IBM_PREC_FP32_BULK)
     return fail(IBM_EINVAL, "bad precision");
-  if (mo && (mo->kind < IBM_MOTION_STATIC || mo->kind > IBM_MOTION_COUPLED)) return fail(IBM_EINVAL, "bad motion");
+  if (mo && (mo->kind < IBM_MOTION_STATIC || mo->kind > IBM_MOTION_PITCH)) return fail(IBM_EINVAL, "bad motion");
+  if (mo && mo->kind == IBM_MOTION_PITCH && geo->nverts == 0) return fail(IBM_EINVAL, "a pitching motion needs a body");
   if (mo && mo->kind == IBM_MOTION_COUPLED) {
     if (!(mo->mass > 0)) return fail(IBM_EINVAL, "a body moving under the fluid force needs mass > 0");
     if (fl->time_scheme != IBM_TIME_RK3) return fail(IBM_EINVAL, "a body moving under the fluid force needs RK3");
@@ -177,8 +195,7 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
   }
   if (fl->time_scheme != IBM_TIME_RK3 && fl->time_scheme != IBM_TIME_DUAL) return fail(IBM_EINVAL, "bad time scheme");
   if (fl->ib_mode != IBM_IB_REBUILD && fl->ib_mode != IBM_IB_ADVANCE) return fail(IBM_EINVAL, "bad ib_mode");
-  if (fl->ib_mode == IBM_IB_ADVANCE && fl->precision != IBM_PREC_FP64 && fl->time_scheme == IBM_TIME_DUAL)
-    return fail(IBM_EINVAL, "IBM_IB_ADVANCE is not built for FP32-bulk dual time");
+  if (fl->scheme != IBM_SCHEME_WENO5 && fl->scheme != IBM_SCHEME_TVD2) return fail(IBM_EINVAL, "bad scheme");
   if (fl->time_scheme == IBM_TIME_DUAL) {
     if (!(fl->dt_phys > 0) || !(fl->cfl_tau > 0) || fl->subiters < 1)
       return fail(IBM_EINVAL, "dual time needs dt_phys > 0, cfl_tau > 0, subiters >= 1");
@@ -208,6 +225,12 @@ static size_t carve(ibm_case *c, char *base) {
   take(&c->vny, nv);
   take(&c->vk, nv);
   take(&c->surf, 2 * nv);
+  if (k.motion.kind == IBM_MOTION_PITCH) {
+    take(&c->rsnx, nv);
+    take(&c->rsny, nv);
+    take(&c->rvnx, nv);
+    take(&c->rvny, nv);
+  }
   take(&c->A, 4 * plane);
   if (c->precision == IBM_PREC_FP64) {
     take(&c->B, 4 * plane);
@@ -285,23 +308,22 @@ static void init_case(ibm_case *c, const ibm_geometry *geo, const ibm_grid *gr, 
   }
   k.motion.freq = mo ? mo->freq : 0.0;
   k.motion.mass = mo && mo->kind == IBM_MOTION_COUPLED ? mo->mass : 0.0;
+  for (int d = 0; d < 2; d++) k.motion.pivot[d] = mo && mo->kind == IBM_MOTION_PITCH ? mo->pivot[d] : 0.0;
+  k.motion.pmean = mo && mo->kind == IBM_MOTION_PITCH ? mo->pitch_mean : 0.0;
+  k.motion.pamp = mo && mo->kind == IBM_MOTION_PITCH ? mo->pitch_amp : 0.0;
   k.dual = fl->time_scheme == IBM_TIME_DUAL;
   k.ib_advance = fl->ib_mode == IBM_IB_ADVANCE;
+  k.tvd2 = fl->scheme == IBM_SCHEME_TVD2;
   k.subiters = fl->subiters;
   k.dt_phys = fl->dt_phys;
   k.idt_phys = fl->dt_phys > 0.0 ? 1.0 / fl->dt_phys : 0.0;
   k.cfl_tau = fl->cfl_tau;
   c->g.nv = geo->nverts;
-  c->cap = list_capacity(geo, gr);
-  if (c->precision == IBM_PREC_FP32_BULK) c->body_cap = body_tile_capacity(geo, gr, stage_tiles(k));
+  c->cap = list_capacity(geo, gr, mo);
+  if (c->precision == IBM_PREC_FP32_BULK) c->body_cap = body_tile_capacity(geo, gr, mo, stage_tiles(k));
   if (geo->nverts > 0) {
-    double xmin = geo->verts[0], xmax = xmin, ymin = geo->verts[1], ymax = ymin;
-    for (int v = 1; v < geo->nverts; v++) {
-      xmin = fmin(xmin, geo->verts[2 * v]);
-      xmax = fmax(xmax, geo->verts[2 * v]);
-      ymin = fmin(ymin, geo->verts[2 * v + 1]);
-      ymax = fmax(ymax, geo->verts[2 * v + 1]);
-    }
+    double xmin, xmax, ymin, ymax;
+    body_extent(geo, mo, xmin, xmax, ymin, ymax);
     c->box_w = (int)fmin((double)k.nx, ceil((xmax - xmin) / k.dx) + 4);
     c->box_h = (int)fmin((double)k.ny, ceil((ymax - ymin) / k.dy) + 4);
   }
@@ -404,6 +426,11 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   c->g.vnx = c->vnx;
   c->g.vny = c->vny;
   c->g.vk = c->vk;
+  const bool pitching = k.motion.kind == IBM_MOTION_PITCH;
+  c->g.rsnx = pitching ? c->rsnx : nullptr;
+  c->g.rsny = pitching ? c->rsny : nullptr;
+  c->g.rvnx = pitching ? c->rvnx : nullptr;
+  c->g.rvny = pitching ? c->rvny : nullptr;
 
   ibm_status rs = IBM_OK;
   do {
@@ -412,7 +439,12 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
         rs = fail(IBM_ECUDA, "vertex upload failed");
         break;
       }
-      launch_normals(nv, c->vref, c->snx, c->sny, c->vnx, c->vny, c->vk, s);
+      // normals of the reference pose: the current pose's for a translating body; a pitching body's pose
+      // kernel rotates them into the current arrays at every classification
+      if (pitching)
+        launch_normals(nv, c->vref, c->rsnx, c->rsny, c->rvnx, c->rvny, c->vk, s);
+      else
+        launch_normals(nv, c->vref, c->snx, c->sny, c->vnx, c->vny, c->vk, s);
       c->launches++;
     }
     std::memset(c->hds, 0, sizeof(DevState));

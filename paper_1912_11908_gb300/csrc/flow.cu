@@ -64,9 +64,11 @@ void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *d
 // pressure condition a linear ODE in p along the normal, integrated exactly.
 // One thread per list entry; in place on the stage array.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const ibm_stencil &s, const double V[2],
-                                              const double Acc[2], bool sup) {
+__device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const ibm_stencil &s, const double Vb[2],
+                                              const double Ab[2], bool sup, double t) {
   if (s.mask == 0) return;
+  double V[2], Acc[2];
+  wall_kin(k, t, s.bx, s.by, Vb, Ab, V, Acc);  // the wall's motion at P'
   double qp[4] = {0.0, 0.0, 0.0, 0.0};
   for (int q = 0; q < 4; q++) {
     if (!(s.mask >> q & 1)) continue;
@@ -103,13 +105,14 @@ __device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const 
 __global__ void __launch_bounds__(1024) k_recon1_f64(Consts k, double *U, const ibm_stencil *__restrict__ st,
                                                      int cap, const DevState *__restrict__ ds, int stage) {
   double X[2], V[2], Acc[2];
-  body_motion(k, ds, stage_time(ds, stage), X, V, Acc);
+  const double ts = stage_time(ds, stage);
+  body_motion(k, ds, ts, X, V, Acc);
   const bool sup = supersonic_motion(k, V);
   const int nib = min(ds->offset[1], cap), tot = min(ds->offset[4], cap);
   if (!k.ib_advance)  // IB nodes rebuilt (else advanced by the flux update)
-    for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup);
+    for (int e = threadIdx.x; e < nib; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup, ts);
   __syncthreads();
-  for (int e = nib + threadIdx.x; e < tot; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup);
+  for (int e = nib + threadIdx.x; e < tot; e += blockDim.x) recon_one_f64(k, U, st[e], V, Acc, sup, ts);
 }
 
 // many blocks, one pass (0: IB nodes, 1: ghost nodes) per launch
@@ -120,8 +123,9 @@ __global__ void __launch_bounds__(128) k_recon_f64(Consts k, double *U, const ib
   const int e = lo + blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= hi) return;
   double X[2], V[2], Acc[2];
-  body_motion(k, ds, stage_time(ds, stage), X, V, Acc);
-  recon_one_f64(k, U, st[e], V, Acc, supersonic_motion(k, V));
+  const double ts = stage_time(ds, stage);
+  body_motion(k, ds, ts, X, V, Acc);
+  recon_one_f64(k, U, st[e], V, Acc, supersonic_motion(k, V), ts);
 }
 
 void launch_recon_f64(const Consts &k, double *U, const ibm_stencil *st, int cap, const DevState *ds, int stage,
@@ -164,6 +168,16 @@ __device__ __forceinline__ R weno5(R f0, R f1, R f2, R f3, R f4) {
   R e01 = e0 * e1, e12 = e1 * e2, e02 = e0 * e2;
   R a0 = R(0.1) * e12 * e12, a1 = R(0.6) * e02 * e02, a2 = R(0.3) * e01 * e01;
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// Sec. 2, the second-order TVD scheme: MUSCL with the minmod limiter; value at the face right of f1
+template <typename R>
+__device__ __forceinline__ R tvd2(R f0, R f1, R f2) {
+  const R a = f1 - f0, b = f2 - f1;
+  R m = R(0);
+  if (a > R(0) && b > R(0)) m = a < b ? a : b;
+  else if (a < R(0) && b < R(0)) m = a > b ? a : b;
+  return f1 + R(0.5) * m;
 }
 
 // ---------------------------------------------------------------------------
@@ -371,8 +385,13 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
     double qL[4], qR[4];
     for (int v = 0; v < 4; v++) {
       const double *s = &sq[v][b][f];
-      qL[v] = weno5(s[0], s[1], s[2], s[3], s[4]);
-      qR[v] = weno5(s[5], s[4], s[3], s[2], s[1]);
+      if (k.tvd2) {
+        qL[v] = tvd2(s[1], s[2], s[3]);
+        qR[v] = tvd2(s[4], s[3], s[2]);
+      } else {
+        qL[v] = weno5(s[0], s[1], s[2], s[3], s[4]);
+        qR[v] = weno5(s[5], s[4], s[3], s[2], s[1]);
+      }
     }
     if (!(qL[0] > 0.0) || !(qL[3] > 0.0) || !(qR[0] > 0.0) || !(qR[3] > 0.0)) {
       for (int v = 0; v < 4; v++) {
@@ -405,8 +424,13 @@ __global__ void __launch_bounds__(256) k_stage_f64(Consts k, const double *Un, c
     for (int v = 0; v < 4; v++) {
       const double s0 = sq[v][f][a], s1 = sq[v][f + 1][a], s2 = sq[v][f + 2][a];
       const double s3 = sq[v][f + 3][a], s4 = sq[v][f + 4][a], s5 = sq[v][f + 5][a];
-      qL[v] = weno5(s0, s1, s2, s3, s4);
-      qR[v] = weno5(s5, s4, s3, s2, s1);
+      if (k.tvd2) {
+        qL[v] = tvd2(s1, s2, s3);
+        qR[v] = tvd2(s4, s3, s2);
+      } else {
+        qL[v] = weno5(s0, s1, s2, s3, s4);
+        qR[v] = weno5(s5, s4, s3, s2, s1);
+      }
     }
     if (!(qL[0] > 0.0) || !(qL[3] > 0.0) || !(qR[0] > 0.0) || !(qR[3] > 0.0)) {
       for (int v = 0; v < 4; v++) {

@@ -114,6 +114,9 @@ __global__ void k_compact_stencils(Consts k, const ibm_stencil *__restrict__ st,
   r.ny = (float)s.ny;
   for (int q = 0; q < 4; q++) r.w[q] = (float)s.w[q];
   r.curv = (float)s.curv;
+  const bool pitching = k.motion.kind == IBM_MOTION_PITCH;
+  r.rx = pitching ? (float)(s.bx - k.motion.pivot[0]) : 0.f;
+  r.ry = pitching ? (float)(s.by - k.motion.pivot[1]) : 0.f;
   rs[e] = r;
   sid[s.cell] = e;
 }

@@ -66,15 +66,51 @@ void launch_normals(int nv, const double *v, double *snx, double *sny, double *v
   k_normals<<<(nv + 127) / 128, 128, 0, s>>>(nv, v, snx, sny, vnx, vny, vk);
 }
 
+// Pose of vertex v: the reference vertex shifted by the translation X, or for a pitching body (Sec. 7.2) turned
+// about the pivot by the body angle whose cosine and sine are cs, sn.
+__device__ __forceinline__ void pose_vertex(const Consts &k, const Geom &g, int v, const double X[2], double cs,
+                                            double sn, double &x, double &y) {
+  if (k.motion.kind == IBM_MOTION_PITCH) {
+    const double rx = g.vref[2 * v] - k.motion.pivot[0], ry = g.vref[2 * v + 1] - k.motion.pivot[1];
+    x = k.motion.pivot[0] + (cs * rx - sn * ry);
+    y = k.motion.pivot[1] + (sn * rx + cs * ry);
+  } else {
+    x = g.vref[2 * v] + X[0];
+    y = g.vref[2 * v + 1] + X[1];
+  }
+}
+
+// a pitching body's segment and vertex normals: the reference pose's, turned with the body
+__device__ __forceinline__ void pose_normals(const Geom &g, int v, double cs, double sn) {
+  g.snx[v] = cs * g.rsnx[v] - sn * g.rsny[v];
+  g.sny[v] = sn * g.rsnx[v] + cs * g.rsny[v];
+  g.vnx[v] = cs * g.rvnx[v] - sn * g.rvny[v];
+  g.vny[v] = sn * g.rvnx[v] + cs * g.rvny[v];
+}
+
+// translation X and, for a pitching body, cos / sin of the body angle at the start of the step
+__device__ __forceinline__ void pose_params(const Consts &k, const DevState *ds, double X[2], double &cs,
+                                            double &sn) {
+  double V[2], A[2];
+  body_motion(k, ds, ds->t, X, V, A);
+  cs = 1.0;
+  sn = 0.0;
+  if (k.motion.kind == IBM_MOTION_PITCH) {
+    double th, om, al;
+    pitch_at(k.motion, ds->t, &th, &om, &al);
+    sincos(th, &sn, &cs);
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Body pose at the start of the step (prescribed translation) and its
-// axis-aligned bounding box.  One block.
+// Body pose at the start of the step (prescribed translation or pitching) and
+// its axis-aligned bounding box.  One block.
 // ---------------------------------------------------------------------------
 __global__ void k_pose(Consts k, Geom g, DevState *ds) {
-  __shared__ double X[2];
+  __shared__ double X[2], rot[2];
   if (threadIdx.x == 0) {
-    double V[2], A[2], P[2];
-    body_motion(k, ds, ds->t, P, V, A);
+    double P[2];
+    pose_params(k, ds, P, rot[0], rot[1]);
     X[0] = P[0];
     X[1] = P[1];
     ds->pos[0] = P[0];
@@ -84,9 +120,11 @@ __global__ void k_pose(Consts k, Geom g, DevState *ds) {
   // each thread keeps the extremes of its own vertices; then warp and block reductions (min / max are exact)
   double b[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
   for (int v = threadIdx.x; v < g.nv; v += blockDim.x) {
-    const double x = g.vref[2 * v] + X[0], y = g.vref[2 * v + 1] + X[1];
+    double x, y;
+    pose_vertex(k, g, v, X, rot[0], rot[1], x, y);
     g.vx[v] = x;
     g.vy[v] = y;
+    if (k.motion.kind == IBM_MOTION_PITCH) pose_normals(g, v, rot[0], rot[1]);
     b[0] = fmin(b[0], x);
     b[1] = fmax(b[1], x);
     b[2] = fmin(b[2], y);
@@ -584,6 +622,9 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
         r.ny = (float)s.ny;
         for (int q = 0; q < 4; q++) r.w[q] = (float)s.w[q];
         r.curv = (float)s.curv;
+        const bool pitching = k.motion.kind == IBM_MOTION_PITCH;  // P' relative to the pivot (wall motion)
+        r.rx = pitching ? (float)(s.bx - k.motion.pivot[0]) : 0.f;
+        r.ry = pitching ? (float)(s.by - k.motion.pivot[1]) : 0.f;
         rs[e] = r;
         sid[s.cell] = e;
       }
@@ -613,26 +654,28 @@ __device__ __forceinline__ void clip_rect(const Consts &k, int r[4]) {
 __global__ void __launch_bounds__(256) k_pose_classify(Consts k, Geom g, uint8_t *__restrict__ solid,
                                                        DevState *ds) {
   extern __shared__ double sv[];  // x[nv] then y[nv]
-  __shared__ double X[2];
+  __shared__ double X[2], rot[2];
   __shared__ double wb[8][4];
   __shared__ double bb[4];
   __shared__ int rect[4];
   const int nv = g.nv;
   if (threadIdx.x == 0) {
-    double V[2], A[2], P[2];
-    body_motion(k, ds, ds->t, P, V, A);
+    double P[2];
+    pose_params(k, ds, P, rot[0], rot[1]);
     X[0] = P[0];
     X[1] = P[1];
   }
   __syncthreads();
   double b[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-    const double x = g.vref[2 * v] + X[0], y = g.vref[2 * v + 1] + X[1];
+    double x, y;
+    pose_vertex(k, g, v, X, rot[0], rot[1], x, y);
     sv[v] = x;
     sv[nv + v] = y;
     if (blockIdx.x == 0) {
       g.vx[v] = x;
       g.vy[v] = y;
+      if (k.motion.kind == IBM_MOTION_PITCH) pose_normals(g, v, rot[0], rot[1]);
     }
     b[0] = fmin(b[0], x);
     b[1] = fmax(b[1], x);
@@ -1002,13 +1045,15 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
       qp[3] += w[q] * T;
     }
     // wall pressure: the probe's, carried to the surface by the wall condition of the reconstruction
-    double G = -(nx * Acc[0] + ny * Acc[1]);
+    double Vs[2], As[2];
+    wall_kin(k, ds->t, mx, my, V, Acc, Vs, As);  // the wall's motion at the segment midpoint
+    double G = -(nx * As[0] + ny * As[1]);
     if (sup) {
-      double ut = (qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty;
+      double ut = (qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty;
       G = G + ut * ut * (0.5 * (g.vk[e] + g.vk[e1]));
     }
     double ps = qp[0] * exp(-xi * G / (k.R * qp[3]));
-    double tau = k.mu * ((qp[1] - V[0]) * tx + (qp[2] - V[1]) * ty) / xi;
+    double tau = k.mu * ((qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty) / xi;
     if (surf) {  // Eq. 9 integrand: (p_s - p_inf) / (rho_inf U^2 / 2), tau / (rho_inf U^2 / 2)
       surf[e] = (ps - k.pinf) / 0.5;
       surf[g.nv + e] = tau / 0.5;

@@ -57,6 +57,7 @@ struct Motion {
   int kind;
   double amp[2], freq, vel[2];
   double mass;  // COUPLED: body mass per unit depth
+  double pivot[2], pmean, pamp;  // PITCH: centre of rotation, mean incidence and amplitude
 };
 
 // everything a kernel needs about the grid and the gas, passed by value
@@ -77,6 +78,7 @@ struct Consts {
   double cfl_tau;   // dual time: pseudo-time CFL number
   double iR, ig1;   // 1/R and 1/(gamma - 1)
   double idt_phys;  // dual time: 1/dt_phys
+  int tvd2;         // face reconstruction: TVD-2 (MUSCL, minmod) instead of WENO5
 };
 
 
@@ -85,7 +87,8 @@ struct Geom {
   int nv;
   const double *vref;   // 2*nv reference vertices
   double *vx, *vy;      // current pose
-  const double *snx, *sny, *vnx, *vny;
+  double *snx, *sny, *vnx, *vny;   // segment and vertex normals of the current pose
+  const double *rsnx, *rsny, *rvnx, *rvny;  // PITCH: normals of the reference pose (rotated into snx ...)
   const double *vk;     // signed curvature at each vertex (convex > 0)
 };
 
@@ -165,6 +168,36 @@ __device__ inline void motion_at(const Motion &m, double t, double X[2], double 
       V[d] = m.vel[d];
     }
   }
+}
+
+// Pitching (Sec. 7.2): body angle theta = -alpha(t) (counter-clockwise positive), its rate and acceleration.
+__device__ inline void pitch_at(const Motion &m, double t, double *th, double *om, double *al) {
+  const double w = 2.0 * 3.14159265358979323846 * m.freq;
+  double s, c;
+  sincos(w * t, &s, &c);
+  *th = -(m.pmean - m.pamp * c);
+  *om = -m.pamp * w * s;
+  *al = -m.pamp * w * w * c;
+}
+
+// Wall velocity and acceleration at the surface point (px, py): the body's translation, plus for a pitching
+// body the rigid rotation about the pivot, V = om x r and A = al x r - om^2 r (r from the pivot).
+__device__ inline void wall_kin(const Consts &k, double t, double px, double py, const double V0[2],
+                                const double A0[2], double V[2], double A[2]) {
+  if (k.motion.kind != IBM_MOTION_PITCH) {
+    V[0] = V0[0];
+    V[1] = V0[1];
+    A[0] = A0[0];
+    A[1] = A0[1];
+    return;
+  }
+  double th, om, al;
+  pitch_at(k.motion, t, &th, &om, &al);
+  const double rx = px - k.motion.pivot[0], ry = py - k.motion.pivot[1];
+  V[0] = V0[0] - om * ry;
+  V[1] = V0[1] + om * rx;
+  A[0] = A0[0] - al * ry - om * om * rx;
+  A[1] = A0[1] + al * rx - om * om * ry;
 }
 
 // Body motion at time t: the prescribed forms, or, for a body translating
@@ -249,6 +282,7 @@ struct RStencil32 {
   int ccell;    // interior index j0*nx + i0 of corner (i0, j0)
   float w[4];
   float curv;   // signed surface curvature at P' (supersonic moving-body condition, Eq. 7)
+  float rx, ry; // P' relative to the pivot of a pitching body (0 otherwise)
 };
 
 // FP32-bulk path (flow32.cu).  The FP64 state D of this mode holds the
@@ -270,6 +304,7 @@ int stage_tiles(const Consts &k);
 struct PertConsts {  // FP32 copies of the free-stream constants
   float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin, vis, cp;
   float cfl_tau, idt_phys;  // dual time: pseudo-time CFL number, 1 / physical dt
+  int tvd2;                 // face reconstruction: TVD-2 instead of WENO5
 };
 
 __host__ inline PertConsts pert_consts(const Consts &k) {
@@ -290,6 +325,7 @@ __host__ inline PertConsts pert_consts(const Consts &k) {
   c.cp = (float)k.cp;
   c.cfl_tau = (float)k.cfl_tau;
   c.idt_phys = (float)k.idt_phys;
+  c.tvd2 = k.tvd2;
   return c;
 }
 

@@ -154,7 +154,8 @@ struct TileSmem {
   float sT[HY][HX];     // T'
   unsigned long long mbar;
   unsigned int mbar_phase;  // persistent kernel: parity of the barrier's next phase (barrier initialised once)
-  float wm[5];    // wall velocity and acceleration at the stage time; 1 if Eq. 7 applies (else 0)
+  float wm[7];    // wall velocity and acceleration at the stage time; 1 if Eq. 7 applies (else 0); the rotation
+                  // rate and its rate of change of a pitching body (else 0)
   float lred[8];  // per-warp maxima of the CFL reduction
   int nrb;        // listed IB / ghost nodes (body tiles)
   int rbm[RB_MAX], rbe[RB_MAX];
@@ -171,7 +172,10 @@ static_assert(RB_MAX * sizeof(RStencil32) <= sizeof(float) * 2 * (NFX + NFY), "n
 // ---------------------------------------------------------------------------
 constexpr int TMA_W = (HX + 3) / 4 * 4;  // box width: HX rounded up to a multiple of 16 bytes
 constexpr unsigned TMA_BYTES = 4u * HY * TMA_W * sizeof(float);
-constexpr int TMA_WAIT_LIMIT = 1 << 22;
+// a tile's copy completes within microseconds; a wait gives up after about a second of %globaltimer (the
+// iteration count is only a backstop: the time a try_wait suspends is implementation-defined)
+constexpr unsigned long long TMA_WAIT_NS = 1ull << 30;
+constexpr unsigned TMA_WAIT_BACKSTOP = 1u << 28;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -192,10 +196,18 @@ __device__ __forceinline__ void tma_load(float *dst, const CUtensorMap *map, int
       : "memory");
 }
 
-// wait for the completion of the barrier's phase with the given parity; false if the bounded wait gave up
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for the completion of the barrier's phase with the given parity; false if it has not completed within
+// TMA_WAIT_NS
 __device__ __forceinline__ bool tma_wait(unsigned long long *mbar, unsigned parity) {
   const unsigned m = smem_u32(mbar);
-  for (int it = 0; it < TMA_WAIT_LIMIT; it++) {
+  unsigned long long t0 = 0;
+  for (unsigned it = 0; it < TMA_WAIT_BACKSTOP; it++) {
     unsigned ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -203,6 +215,11 @@ __device__ __forceinline__ bool tma_wait(unsigned long long *mbar, unsigned pari
         : "r"(m), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 63) == 0) {
+      const unsigned long long t = globaltimer_ns();
+      if (it == 0) t0 = t;
+      else if (t - t0 > TMA_WAIT_NS) return false;
+    }
   }
   return false;
 }
@@ -261,19 +278,24 @@ __device__ __forceinline__ void raw_prim(const PertConsts &c, const float *U, lo
 
 __device__ __forceinline__ void wall_bc(const PertConsts &c, const RStencil32 &s, const float qp[4], const float *wm,
                                         float q[4]) {
-  // wm = (Vx, Vy, Ax, Ay, supersonic) at the stage time.  Neumann pressure dp/dn = rho G (Eq. 5-6), G = -n.a
-  // plus the centripetal u_t^2 kappa of Eq. 7 (u_t tangential to the wall, relative to it, at the probe); with
-  // rho = p / (R T) and T fixed along the normal (Eq. 8) it integrates to p = p_probe exp(-dxi G / (R T)),
-  // here in perturbation form p' = p'_probe + (R + p'_probe) expm1(...) so that p' keeps its digits
-  float G = -(s.nx * wm[2] + s.ny * wm[3]);
+  // wm = (Vx, Vy, Ax, Ay, supersonic, omega, domega/dt) at the stage time: the wall's motion at P' is the
+  // body's translation plus, for a pitching body, omega x r and domega/dt x r - omega^2 r with r = P' - pivot
+  // (zero terms otherwise).  Neumann pressure dp/dn = rho G (Eq. 5-6), G = -n.a plus the centripetal
+  // u_t^2 kappa of Eq. 7 (u_t tangential to the wall, relative to it, at the probe); with rho = p / (R T) and
+  // T fixed along the normal (Eq. 8) it integrates to p = p_probe exp(-dxi G / (R T)), here in perturbation
+  // form p' = p'_probe + (R + p'_probe) expm1(...) so that p' keeps its digits
+  const float om = wm[5], al = wm[6];
+  const float Vx = wm[0] - om * s.ry, Vy = wm[1] + om * s.rx;
+  const float Ax = wm[2] - al * s.ry - om * om * s.rx, Ay = wm[3] + al * s.rx - om * om * s.ry;
+  float G = -(s.nx * Ax + s.ny * Ay);
   if (wm[4] != 0.f) {
-    const float ut = -(qp[1] - wm[0]) * s.ny + (qp[2] - wm[1]) * s.nx;
+    const float ut = -(qp[1] - Vx) * s.ny + (qp[2] - Vy) * s.nx;
     G = G + ut * ut * s.curv;
   }
   // (static body: G = 0 and p'_node = p'_probe exactly, without the exponential)
   q[0] = G != 0.f ? qp[0] + (c.R + qp[0]) * expm1f(-s.dxi * G / (c.R * (1.f + qp[3]))) : qp[0];
-  q[1] = wm[0] + (qp[1] - wm[0]) * s.ratio;
-  q[2] = wm[1] + (qp[2] - wm[1]) * s.ratio;
+  q[1] = Vx + (qp[1] - Vx) * s.ratio;
+  q[2] = Vy + (qp[2] - Vy) * s.ratio;
   q[3] = qp[3];
 }
 
@@ -381,6 +403,10 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     wm[2] = (float)Acc[0];
     wm[3] = (float)Acc[1];
     wm[4] = supersonic_motion(k, V) ? 1.f : 0.f;
+    double th = 0.0, om = 0.0, al = 0.0;
+    if (k.motion.kind == IBM_MOTION_PITCH) pitch_at(k.motion, ts, &th, &om, &al);
+    wm[5] = (float)om;
+    wm[6] = (float)al;
   }
   // interior tile (the loaded region needs no domain mapping): one tensor copy stages it
   const bool tma = TMA && tmap != nullptr && i0 >= NG && j0 >= NG && i0 + TX + NG <= k.nx && j0 + TY + NG <= k.ny;
@@ -394,8 +420,20 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     tma_load(s_face, tmap, i0, j0, &s_mbar);
   }
   __syncthreads();
-  if (TMA && tma && !tma_wait(&s_mbar, PERSIST ? sm.mbar_phase : 0u) && threadIdx.x == 0)
-    atomicOr(&ds->err, ERR_TIMEOUT);
+  if (TMA && tma) {
+    const unsigned parity = PERSIST ? sm.mbar_phase : 0u;
+    if (__syncthreads_or(!tma_wait(&s_mbar, parity))) {
+      // the copy has not completed and may still write the box: wait for it once more (bounded), then leave
+      // the tile without touching shared memory or outputs.  The step's state is invalid; the error flag makes
+      // the next synchronising call report it.
+      if (threadIdx.x == 0) {
+        atomicOr(&ds->err, ERR_TIMEOUT);
+        tma_wait(&s_mbar, parity);
+        if (STAGE == 3 && fuse_cfl) finish_cfl(k, ds, ncfl, PERSIST);
+      }
+      return;
+    }
+  }
 
   const long long P = k.plane;
   // body tiles: every IB / ghost node of the loaded region, with its stencil staged in shared memory (in the
@@ -526,7 +564,37 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
   // polynomials and the nonlinear weights of a window give the left state at its right face and, mirrored, the
   // right state at its left face.
   static_assert(TX == 16 && TY == 16, "one item per thread: 2 directions x 16 lines x 4 variables x 2 halves");
-  {
+  if (c.tvd2) {
+    // the second-order TVD scheme (Sec. 2): MUSCL with the minmod limiter over the same items; differences
+    // of perturbations equal differences of the variables, so the limiter sees what it would in absolute form
+    const int u = threadIdx.x & 127;
+    const bool xdir = threadIdx.x < 128;
+    const int half = u & 1, line = (u >> 1) & 15, v = u >> 5;
+    const float *lp = xdir ? &sq[v][NG + line][0] : &sq[v][0][NG + line];
+    const int ls = xdir ? 1 : HX;
+    const int p0 = 2 + 9 * half;
+    float f1 = lp[(p0 - 1) * ls], f2 = lp[p0 * ls];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+      const int pc = p0 + i;
+      const float f3 = lp[(pc + 1) * ls];
+      const float a = f2 - f1, b = f3 - f2;
+      // minmod(a, b) for the left state at the right face, minmod(-b, -a) = -minmod(a, b) for the right state
+      float m = 0.f;
+      if (a > 0.f && b > 0.f) m = a < b ? a : b;
+      else if (a < 0.f && b < 0.f) m = a > b ? a : b;
+      const float qL = f2 + 0.5f * m, qR = f2 - 0.5f * m;
+      if (xdir) {
+        if (pc - 2 <= TX) fLx[v][line][pc - 2] = qL;
+        if (pc >= 3) fRx[v][line][pc - 3] = qR;
+      } else {
+        if (pc - 2 <= TY) fLy[v][pc - 2][line] = qL;
+        if (pc >= 3) fRy[v][pc - 3][line] = qR;
+      }
+      f1 = f2;
+      f2 = f3;
+    }
+  } else {
     const int u = threadIdx.x & 127;
     const bool xdir = threadIdx.x < 128;
     const int half = u & 1, line = (u >> 1) & 15, v = u >> 5;

@@ -36,12 +36,13 @@ class ibm_flow(ctypes.Structure):
                 ("prandtl", ctypes.c_double), ("cfl", ctypes.c_double), ("uinf", ctypes.c_double * 2),
                 ("dt_fixed", ctypes.c_double), ("ref_len", ctypes.c_double), ("precision", ctypes.c_int),
                 ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("ib_mode", ctypes.c_int),
-                ("dt_phys", ctypes.c_double), ("cfl_tau", ctypes.c_double)]
+                ("dt_phys", ctypes.c_double), ("cfl_tau", ctypes.c_double), ("scheme", ctypes.c_int)]
 
 
 class ibm_motion(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("amp", ctypes.c_double * 2), ("freq", ctypes.c_double),
-                ("vel", ctypes.c_double * 2), ("mass", ctypes.c_double)]
+                ("vel", ctypes.c_double * 2), ("mass", ctypes.c_double), ("pivot", ctypes.c_double * 2),
+                ("pitch_mean", ctypes.c_double), ("pitch_amp", ctypes.c_double)]
 
 
 STENCIL_DTYPE = np.dtype([
@@ -50,6 +51,16 @@ STENCIL_DTYPE = np.dtype([
     ("nx", "<f8"), ("ny", "<f8"), ("bx", "<f8"), ("by", "<f8"),
     ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (4,)), ("curv", "<f8"),
 ])
+
+class ibm_grid3d(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3)]
+
+
+CLOSEST3D_DTYPE = np.dtype([("node", "<i4"), ("tri", "<i4"), ("kind", "<i4"), ("reserved", "<i4"),
+                            ("cp", "<f8", (3,)), ("n", "<f8", (3,))])
+IBM_3D_TAGS, IBM_3D_COUNTS, IBM_3D_NODES, IBM_3D_CLOSEST = range(4)
+
 
 class ibm_result(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64), ("state", ctypes.c_int32), ("status", ctypes.c_int32),
@@ -64,7 +75,8 @@ EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
            "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats", "ibm_autotune", "ibm_use_tma",
            "ibm_use_persistent", "ibm_persistent_grid", "ibm_stage_launches",
-           "ibm_check_float_conversions", "ibm_fma_peak"]
+           "ibm_check_float_conversions", "ibm_fma_peak", "ibm_body3d_create", "ibm_body3d_classify",
+           "ibm_body3d_get", "ibm_body3d_destroy"]
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 SERVE_BATCHED, SERVE_AUTOTUNE = 1, 2
 SERVER_STATS = ["group_graphs", "group_steps", "group_kernels", "autotune_runs", "capture_us"]
@@ -94,6 +106,12 @@ def load():
     L.ibm_surface.argtypes = [vp, vp, vp, ip]
     L.ibm_fma_peak.argtypes = [ip, ctypes.c_longlong, vp, vp]
     L.ibm_fma_peak.restype = ip
+    L.ibm_body3d_create.argtypes = [vp, ip, vp, ip, vp, vp]
+    L.ibm_body3d_classify.argtypes = [vp, vp]
+    L.ibm_body3d_get.argtypes = [vp, ip, vp, ctypes.c_size_t]
+    L.ibm_body3d_destroy.argtypes = [vp]
+    for name in ("ibm_body3d_create", "ibm_body3d_classify", "ibm_body3d_get", "ibm_body3d_destroy"):
+        getattr(L, name).restype = ip
     L.ibm_sync.argtypes = [vp]
     L.ibm_destroy_case.argtypes = [vp]
     L.ibm_case_device_bytes.argtypes = [ctypes.POINTER(ibm_geometry), ctypes.POINTER(ibm_grid),
@@ -177,14 +195,16 @@ def marshal(spec):
     fl.dt_phys = spec.get("dt_phys", 0.0)
     fl.cfl_tau = spec.get("cfl_tau", 0.8)
     fl.ib_mode = spec.get("ib_mode", W.IB_REBUILD)
-    if spec.get("scheme", W.SCHEME_WENO5) != W.SCHEME_WENO5:
-        raise ValueError("the GPU library builds the WENO5 reconstruction only")
+    fl.scheme = spec.get("scheme", W.SCHEME_WENO5)
     mo = ibm_motion()
     mo.kind = spec.get("motion", W.MOTION_STATIC)
     mo.amp[0], mo.amp[1] = spec.get("amp", (0.0, 0.0))
     mo.freq = spec.get("freq", 0.0)
     mo.vel[0], mo.vel[1] = spec.get("vel", (0.0, 0.0))
     mo.mass = spec.get("mass", 0.0)
+    mo.pivot[0], mo.pivot[1] = spec.get("pivot", (0.0, 0.0))
+    mo.pitch_mean = spec.get("pitch_mean", 0.0)
+    mo.pitch_amp = spec.get("pitch_amp", 0.0)
     return verts, geo, gr, fl, mo
 
 
@@ -422,3 +442,48 @@ class Server:
                 return
             if sleep_s:
                 time.sleep(sleep_s)
+
+
+class Body3D:
+    """A closed triangulated surface on the device (ibm_body3d_*): 3-D classification, tagging, ordered lists
+    and closest features with pseudo-normals on a uniform lattice (Sec. 3.2, 4.1-4.2)."""
+
+    def __init__(self, verts, tris, stream=None):
+        self.verts = np.ascontiguousarray(verts, np.float64).reshape(-1, 3)
+        self.tris = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
+        h = ctypes.c_void_p()
+        _check(lib().ibm_body3d_create(self.verts.ctypes.data_as(ctypes.c_void_p), self.verts.shape[0],
+                                       self.tris.ctypes.data_as(ctypes.c_void_p), self.tris.shape[0],
+                                       ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+        self.h = h
+        self.shape = None
+
+    def classify(self, n, lo, hi):
+        """n = (nx, ny, nz) lattice nodes over [lo, hi] (asynchronous)."""
+        g = ibm_grid3d(int(n[0]), int(n[1]), int(n[2]), (ctypes.c_double * 3)(*lo), (ctypes.c_double * 3)(*hi))
+        _check(lib().ibm_body3d_classify(self.h, ctypes.byref(g)))
+        self.shape = (int(n[2]), int(n[1]), int(n[0]))
+
+    def _get(self, what, arr):
+        _check(lib().ibm_body3d_get(self.h, what, arr.ctypes.data_as(ctypes.c_void_p), arr.nbytes))
+        return arr
+
+    def tags(self):
+        return self._get(IBM_3D_TAGS, np.empty(self.shape, np.uint8))
+
+    def counts(self):
+        return self._get(IBM_3D_COUNTS, np.zeros(4, np.int32))
+
+    def nodes(self):
+        return self._get(IBM_3D_NODES, np.zeros(int(self.counts().sum()), np.int32))
+
+    def closest(self):
+        return self._get(IBM_3D_CLOSEST, np.zeros(int(self.counts().sum()), CLOSEST3D_DTYPE))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ibm_body3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -27,6 +27,19 @@ def theta_beta_m(M, theta, g=GAMMA):
     return beta, 1.0 + 2.0 * g / (g + 1) * (Mn * Mn - 1)
 
 
+def theta_from_beta(M, beta, g=GAMMA):
+    """Wedge angle (deg) whose attached oblique shock stands at beta (radians): the theta-beta-M relation solved
+    for theta."""
+    t = 2.0 / math.tan(beta) * (M * M * math.sin(beta) ** 2 - 1) / (M * M * (g + math.cos(2 * beta)) + 2)
+    return math.degrees(math.atan(t))
+
+
+def theta_from_ratio(M, ratio, g=GAMMA):
+    """Wedge angle (deg) whose weak oblique shock has the pressure ratio p2/p1 = ratio."""
+    Mn2 = 1.0 + (ratio - 1.0) * (g + 1) / (2.0 * g)
+    return theta_from_beta(M, math.asin(math.sqrt(Mn2) / M), g)
+
+
 def wedge_shock(U, tags, spec, xs=(0.45, 0.55, 0.65, 0.75)):
     """Angle (deg) and pressure ratio of the shock above the wedge's upper face: on each column x in xs the
     height where p crosses the mean of the free-stream and theta-beta-M post-shock pressures (linear between

@@ -62,11 +62,13 @@ def test_device_bytes_estimate(ibm):
 
 
 def test_coupled_motion_arguments_rejected_without_gpu(ibm):
-    """A body moving under the fluid force needs a positive mass, the explicit scheme and a body."""
+    """A body moving under the fluid force needs a positive mass, the explicit scheme and a body; an unknown
+    motion kind and a pitching motion without a body are rejected too."""
     L = ibm.lib()
     spec = W.shock_driven_cylinder(64, 64)
     for bad in (dict(spec, mass=0.0), dict(spec, mass=-1.0), dict(spec, time_scheme=W.TIME_DUAL, dt_phys=0.01),
-                dict(spec, verts=np.zeros((0, 2))), dict(spec, motion=4)):
+                dict(spec, verts=np.zeros((0, 2))), dict(spec, motion=99),
+                dict(spec, motion=W.MOTION_PITCH, verts=np.zeros((0, 2)))):
         verts, geo, gr, fl, mo = ibm.marshal(bad)
         h = ctypes.c_void_p()
         st = L.ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), None,
@@ -96,9 +98,12 @@ def test_header_constants_match_the_binding(ibm):
              "MOTION_COUPLED": "IBM_MOTION_COUPLED", "PREC_FP64": "IBM_PREC_FP64",
              "PREC_FP32_BULK": "IBM_PREC_FP32_BULK", "TIME_RK3": "IBM_TIME_RK3", "TIME_DUAL": "IBM_TIME_DUAL",
              "BC_FREESTREAM": "IBM_BC_FREESTREAM", "BC_OUTFLOW": "IBM_BC_OUTFLOW", "BC_PERIODIC": "IBM_BC_PERIODIC",
-             "IB_REBUILD": "IBM_IB_REBUILD", "IB_ADVANCE": "IBM_IB_ADVANCE"}
+             "IB_REBUILD": "IBM_IB_REBUILD", "IB_ADVANCE": "IBM_IB_ADVANCE", "MOTION_PITCH": "IBM_MOTION_PITCH",
+             "SCHEME_WENO5": "IBM_SCHEME_WENO5", "SCHEME_TVD2": "IBM_SCHEME_TVD2"}
     for py, c in pairs.items():
         assert getattr(W, py) == h[c], py
+    for name in ("IBM_3D_TAGS", "IBM_3D_COUNTS", "IBM_3D_NODES", "IBM_3D_CLOSEST"):
+        assert getattr(ibm, name) == h[name], name
 
 
 def test_struct_layouts_match_the_header(ibm, tmp_path):
@@ -109,7 +114,7 @@ def test_struct_layouts_match_the_header(ibm, tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("no C compiler")
     structs = {"ibm_geometry": ibm.ibm_geometry, "ibm_grid": ibm.ibm_grid, "ibm_flow": ibm.ibm_flow,
-               "ibm_motion": ibm.ibm_motion, "ibm_result": ibm.ibm_result}
+               "ibm_motion": ibm.ibm_motion, "ibm_result": ibm.ibm_result, "ibm_grid3d": ibm.ibm_grid3d}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ibm.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (name, name))
@@ -127,18 +132,11 @@ def test_struct_layouts_match_the_header(ibm, tmp_path):
             assert int(got["%s.%s" % (name, f[0])]) == getattr(cls, f[0]).offset, (name, f[0])
 
 
-def test_ib_advance_mode_refused_with_fp32_bulk_dual_time(ibm):
-    """IBM_IB_ADVANCE is not built for FP32-bulk dual time; the library refuses it instead of ignoring it."""
+def test_unknown_reconstruction_rejected(ibm):
+    """ibm_flow.scheme other than WENO5 / TVD-2 is refused by the library (no silent default)."""
     L = ibm.lib()
-    verts, geo, gr, fl, mo = ibm.marshal(dict(W.cylinder_m02_re40(64, 32, precision=W.PREC_FP32_BULK),
-                                              ib_mode=W.IB_ADVANCE, time_scheme=W.TIME_DUAL, dt_phys=0.01))
+    verts, geo, gr, fl, mo = ibm.marshal(dict(W.cylinder_m02_re40(64, 32), scheme=7))
     h = ctypes.c_void_p()
     st = L.ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), None,
                            ctypes.byref(h))
     assert st == ibm.IBM_EINVAL and not h.value
-
-
-def test_binding_refuses_the_oracle_only_reconstruction(ibm):
-    """The TVD-2 reconstruction exists in the oracle only: the binding refuses it instead of ignoring it."""
-    with pytest.raises(ValueError):
-        ibm.marshal(dict(W.cylinder_m02_re40(64, 32), scheme=W.SCHEME_TVD2))

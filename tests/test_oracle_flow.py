@@ -12,6 +12,7 @@ import math
 import numpy as np
 import pytest
 
+from flowmetrics import wedge_shock
 from paper_1912_11908_gb300 import workloads as W
 
 GAMMA = 1.4
@@ -322,36 +323,20 @@ def _theta_beta_m(M, theta, g=GAMMA):
 
 @pytest.mark.slow
 def test_wedge_oblique_shock_theta_beta_m(orc):
-    """M=2 over the 15 deg wedge: the attached weak oblique shock.  Its slope between x = 0.45 and 0.75
-    gives the shock angle, the plateau behind it the pressure ratio (theta-beta-M and the normal-shock
-    relations).  The slope is measured, not the position: the no-slip immersed boundary shifts the
-    effective leading edge by a few cells."""
+    """M=2 over the 15 deg wedge (IB nodes advanced, the workload's treatment): the steady attached weak oblique
+    shock.  Its slope between x = 0.45 and 0.75 gives the shock angle, the plateau behind it the pressure ratio,
+    against theta-beta-M and the normal-shock relations within 1 deg and 3% (measured on this 384x192 grid at
+    t = 4: 45.3 deg, p2/p1 -2%).  The flow starts impulsively: the shock over that stretch of the wedge settles
+    only after t = 3.5 (at t = 2 it still stands 1 deg short and moving)."""
     nx, ny = 384, 192
-    c = orc.Case(W.wedge_m2_re1e4(nx, ny))
-    while c.time() < 2.0:
-        c.step(50)
-    r, u, v, p = cons_to_prim(c.state())
-    tags = c.tags()
-    xc = -1.0 + (np.arange(nx) + 0.5) * (4.0 / nx)
-    yc = -1.0 + (np.arange(ny) + 0.5) * (2.0 / ny)
+    spec = W.wedge_m2_re1e4(nx, ny)
+    c = orc.Case(spec)
+    while c.time() < 4.0:
+        c.step(100)
+    beta, ratio = wedge_shock(c.state(), c.tags(), spec)
     beta_e, pr_e = _theta_beta_m(2.0, math.radians(15.0))
-    p1 = 1.0 / (GAMMA * 4.0)
-    mid = p1 * (1.0 + pr_e) / 2.0
-    xs, ys, plateau = [], [], []
-    for xt in (0.45, 0.55, 0.65, 0.75):
-        i = int(np.argmin(np.abs(xc - xt)))
-        col = p[:, i]
-        j = max(jj for jj in range(ny - 1) if col[jj] >= mid and col[jj + 1] < mid)
-        ys.append(yc[j] + (col[j] - mid) / (col[j] - col[j + 1]) * (yc[j + 1] - yc[j]))
-        xs.append(xc[i])
-        wall = max(jj for jj in range(ny) if tags[jj, i] != 0)
-        plateau.append(np.median(col[wall + 3:j - 2]) / p1)
-    slope = np.polyfit(xs, ys, 1)[0]
-    # tolerances of a 384x192 grid (about 26 cells across the wedge base); the full-size run on the
-    # GPU checks the same relation more tightly
-    assert abs(math.degrees(math.atan(slope)) - math.degrees(beta_e)) < 3.0, (math.degrees(math.atan(slope)),
-                                                                              math.degrees(beta_e))
-    assert abs(np.median(plateau) / pr_e - 1.0) < 0.10, (plateau, pr_e)
+    assert abs(beta - math.degrees(beta_e)) < 1.0, (beta, math.degrees(beta_e))
+    assert abs(ratio / pr_e - 1.0) < 0.03, (ratio, pr_e)
 
 
 # ---------------------------------------------------------------- dual time (Sec. 2)

@@ -60,6 +60,30 @@ def test_noalloc_tagging_matches_classify_twice(env):
         assert (cells.cpu().numpy()[n:] == -1).all()
 
 
+def test_noalloc_list_overflow_keeps_totals(env):
+    """Capacity below the number of listed nodes: d_counts still holds the full totals, the first `capacity`
+    entries are the reference list's, and nothing past capacity is written (a guard region stays untouched)."""
+    torch, ibm = env
+    spec = W.cylinder_m02_re40(150, 70)
+    tags_ref, counts_ref, cells_ref = _reference(ibm, spec)
+    n = int(counts_ref.sum())
+    cap = n // 2
+    guard = 256
+    verts = torch.tensor(np.ascontiguousarray(spec["verts"]).ravel(), dtype=torch.float64, device="cuda")
+    tags = torch.full((spec["ny"], spec["nx"]), 255, dtype=torch.uint8, device="cuda")
+    cells = torch.full((cap + guard,), -7, dtype=torch.int32, device="cuda")
+    counts = torch.zeros(4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ibm.ibm_tag_nodes_noalloc(spec, verts.data_ptr(), spec["verts"].shape[0], tags.data_ptr(), cells.data_ptr(),
+                              cap, counts.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(counts.cpu().numpy(), counts_ref)
+    np.testing.assert_array_equal(tags.cpu().numpy(), tags_ref)
+    out = cells.cpu().numpy()
+    np.testing.assert_array_equal(out[:cap], cells_ref[:cap])
+    assert (out[cap:] == -7).all()
+
+
 def test_noalloc_rejects_oversize(env):
     torch, ibm = env
     spec = W.cylinder_m02_re40(4096, 2048)  # 8.4 M cells > 4,194,304
