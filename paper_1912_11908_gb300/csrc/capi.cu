@@ -383,6 +383,7 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   ibm_case *c = new (std::nothrow) ibm_case();
   if (!c) return fail(IBM_ENOMEM, "host allocation failed");
   cudaGetDevice(&c->device);
+  prepare_geometry_kernels();
   c->stream = (cudaStream_t)stream;
   if (!c->stream) {
     if (cudaStreamCreate(&c->stream) != cudaSuccess) {
@@ -545,7 +546,7 @@ static bool fused_cfl(const ibm_case *c) {
 
 // the explicit FP32-bulk step runs as one persistent launch
 static bool persistent_step(const ibm_case *c) {
-  return c->use_persist && c->sch_words && c->precision == IBM_PREC_FP32_BULK && !c->k.dual;
+  return c->use_persist && c->sch_words && c->precision == IBM_PREC_FP32_BULK && !c->k.dual && !c->k.tvd2;
 }
 
 // one explicit step on the case stream (kernels only; graph-capturable)
@@ -850,7 +851,7 @@ namespace ibm {
 // batched groups run the explicit stages only: dual time and bodies moving under the fluid force (whose
 // steps add the force and the body update) advance on their own streams
 bool case_batchable(const ibm_case *c) {
-  return c->precision == IBM_PREC_FP32_BULK && !c->k.dual && c->k.motion.kind != IBM_MOTION_COUPLED;
+  return c->precision == IBM_PREC_FP32_BULK && !c->k.dual && c->k.motion.kind != IBM_MOTION_COUPLED && !c->k.tvd2;
 }
 
 ibm_status case_prepare_batch(ibm_case *c) {

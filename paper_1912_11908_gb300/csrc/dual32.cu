@@ -45,6 +45,27 @@ __global__ void __launch_bounds__(256) k_dual_f32_one(Consts k, PertConsts c, co
                                    ncfl, b - nb, sm, dp);
 }
 
+// the same with the TVD-2 reconstruction compiled in (every launch form of a TVD-2 case)
+template <int STAGE>
+__global__ void __launch_bounds__(256) k_dual_f32_tvd(Consts k, PertConsts c, const float *__restrict__ In,
+                                                      float *Out32, double *D, const uint8_t *__restrict__ tag,
+                                                      const int *__restrict__ sid,
+                                                      const RStencil32 *__restrict__ rs,
+                                                      const uint8_t *__restrict__ tile_body,
+                                                      const int *__restrict__ body_tiles, int nb, DevState *ds,
+                                                      unsigned int ncfl, DualPtrs dp) {
+  __shared__ TileSmem sm;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int b = (int)blockIdx.x;
+  if (b < nb)
+    stage_tile<STAGE, true, true, false, false, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body,
+                                                      body_tiles, ds, false, ncfl, b, sm, dp);
+  else
+    stage_tile<STAGE, false, true, false, false, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body,
+                                                       body_tiles, ds, false, ncfl, b - nb, sm, dp);
+}
+
 cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, float *Out32, double *D,
                                 const double *In64, double *Out64, const double *G, double *Q0,
                                 const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
@@ -67,9 +88,14 @@ cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, f
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = pdl ? 1 : 0;
-#define IBM_DUAL_ONE(S) \
-  cudaLaunchKernelEx(&cfg, k_dual_f32_one<S>, k, c, In32, Out32, D, tag, sid, rs, tile_body, body_tiles, nb, ds, ncfl, dp)
-  const cudaError_t e = stage == 1 ? IBM_DUAL_ONE(1) : stage == 2 ? IBM_DUAL_ONE(2) : IBM_DUAL_ONE(3);
+#define IBM_DUAL_ONE(K, S) \
+  cudaLaunchKernelEx(&cfg, K<S>, k, c, In32, Out32, D, tag, sid, rs, tile_body, body_tiles, nb, ds, ncfl, dp)
+  const cudaError_t e = k.tvd2 ? (stage == 1   ? IBM_DUAL_ONE(k_dual_f32_tvd, 1)
+                                  : stage == 2 ? IBM_DUAL_ONE(k_dual_f32_tvd, 2)
+                                               : IBM_DUAL_ONE(k_dual_f32_tvd, 3))
+                               : (stage == 1   ? IBM_DUAL_ONE(k_dual_f32_one, 1)
+                                  : stage == 2 ? IBM_DUAL_ONE(k_dual_f32_one, 2)
+                                               : IBM_DUAL_ONE(k_dual_f32_one, 3));
 #undef IBM_DUAL_ONE
   return e;
 }
@@ -94,6 +120,11 @@ void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32
                      double *Out64, const double *G, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
                      DevState *ds, cudaStream_t s, cudaStream_t sb) {
+  if (k.tvd2) {  // the TVD-2 kernel holds plain and body tiles: one launch on the case stream
+    launch_dual_f32_one(k, stage, In32, Out32, D, In64, Out64, G, Q0, tag, sid, rs, tile_body, body_tiles, body_cap,
+                        ds, false, s);
+    return;
+  }
   PertConsts c = pert_consts(k);
   const int nt = stage_tiles(k);
   const int nb = body_cap > 0 ? body_cap : 0;

@@ -170,6 +170,27 @@ __global__ void __launch_bounds__(256, MINB)
                                           ncfl, b - nb, sm, DualPtrs{}, use_tma ? &tmap : nullptr);
 }
 
+// The same stage with the TVD-2 reconstruction (Sec. 2) compiled in: a case with that scheme takes this kernel
+// in every launch form (the two-stream form runs it as one launch on the case stream).
+template <int STAGE>
+__global__ void __launch_bounds__(256, 6)
+    k_stage_f32_tvd(Consts k, PertConsts c, float *Mn, const float *__restrict__ In, float *Out, double *D,
+                    const uint8_t *__restrict__ tag, const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
+                    const uint8_t *__restrict__ tile_body, const int *__restrict__ body_tiles, int nb, DevState *ds,
+                    bool fuse_cfl, unsigned int ncfl, const __grid_constant__ CUtensorMap tmap, int use_tma) {
+  __shared__ TileSmem sm;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int b = (int)blockIdx.x;
+  if (b < nb)
+    stage_tile<STAGE, true, false, true, false, true>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds,
+                                                      fuse_cfl, ncfl, b, sm, DualPtrs{}, use_tma ? &tmap : nullptr);
+  else
+    stage_tile<STAGE, false, false, true, false, true>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles,
+                                                       ds, fuse_cfl, ncfl, b - nb, sm, DualPtrs{},
+                                                       use_tma ? &tmap : nullptr);
+}
+
 int stage_tiles(const Consts &k) { return ((k.nx + TX - 1) / TX) * ((k.ny + TY - 1) / TY); }
 
 // does the tile's loaded range [lo, hi] (before domain mapping) along one axis
@@ -254,6 +275,11 @@ void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, fl
                       const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                       const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
                       cudaStream_t sb, int plain_variant, bool with_body, const CUtensorMap *tmap) {
+  if (k.tvd2) {  // the TVD-2 kernel holds plain and body tiles: one launch on the case stream
+    launch_stage_f32_one(k, stage, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, with_body ? body_cap : 0, ds,
+                         fuse_cfl, plain_variant, tmap, false, s);
+    return;
+  }
   PertConsts c = pert_consts(k);
   const int nt = stage_tiles(k);
   const int nb = body_cap > 0 ? body_cap : 0;
@@ -305,7 +331,12 @@ cudaError_t launch_stage_f32_one(const Consts &k, int stage, float *Mn, const fl
   cudaLaunchKernelEx(&cfg, k_stage_f32_one<S, MB>, k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, nb, \
                      ds, fuse_cfl, ncfl, tm, ut)
 #define IBM_ONE_V(S) (plain_variant == 1 ? IBM_ONE(S, 5) : plain_variant == 2 ? IBM_ONE(S, 4) : IBM_ONE(S, 6))
-  cudaError_t e = stage == 1 ? IBM_ONE_V(1) : stage == 2 ? IBM_ONE_V(2) : IBM_ONE_V(3);
+#define IBM_TVD(S)                                                                                           \
+  cudaLaunchKernelEx(&cfg, k_stage_f32_tvd<S>, k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, nb, ds, \
+                     fuse_cfl, ncfl, tm, ut)
+  cudaError_t e = k.tvd2 ? (stage == 1 ? IBM_TVD(1) : stage == 2 ? IBM_TVD(2) : IBM_TVD(3))
+                         : (stage == 1 ? IBM_ONE_V(1) : stage == 2 ? IBM_ONE_V(2) : IBM_ONE_V(3));
+#undef IBM_TVD
 #undef IBM_ONE_V
 #undef IBM_ONE
   return e;

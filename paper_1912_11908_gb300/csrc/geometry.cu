@@ -453,6 +453,25 @@ __device__ __forceinline__ int block_argmin128(double v, int idx, double *sv, in
 // a sequential scan.
 // rs / sid (optional): the FP32 compact form of each stencil and the cell ->
 // stencil map of the FP32-bulk reconstruction.
+// Pruning (bodies of up to STENCIL_PRUNE_MAX vertices): every segment's
+// bounding circle in FP32 (centre, half length plus a margin of 1e-5 of the
+// coordinates' size, far above FP32 rounding) bounds the distance from the
+// node to the segment from below and above; a segment whose lower bound
+// exceeds the smallest upper bound cannot hold the closest point, and one
+// whose lower bound exceeds the |s| of a crossing already found cannot hold a
+// nearer boundary point (the crossing lies on the segment).  The searches run
+// the exact FP64 tests on the others only, so the result is the exhaustive
+// search's, bit for bit.
+constexpr int STENCIL_PRUNE_MAX = 2048;
+__device__ __forceinline__ float block_min128f(float v, float *sf) {
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = fminf(fminf(sf[0], sf[1]), fminf(sf[2], sf[3]));
+  __syncthreads();
+  return v;
+}
+
 __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_t *__restrict__ tag,
                                                   ibm_stencil *__restrict__ st, int cap, DevState *ds,
                                                   RStencil32 *__restrict__ rs, int *__restrict__ sid) {
@@ -460,18 +479,47 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
   __shared__ int s_i[4], s_s[4];
   __shared__ double s_d[5];
   __shared__ int s_n[3];
+  __shared__ float s_f[4];
+  extern __shared__ float s_sb[];  // per segment: centre x, y and radius (half length plus the margin), FP32
   const int total = min(ds->offset[4], cap);
+  const int nv = g.nv;
+  const bool prune = nv <= STENCIL_PRUNE_MAX;
+  if (prune && (int)blockIdx.x < total) {
+    for (int kk = threadIdx.x; kk < nv; kk += 128) {
+      const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
+      const double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
+      const double cx = 0.5 * (ax + bx), cy = 0.5 * (ay + by);
+      const double hl = 0.5 * sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+      s_sb[3 * kk] = (float)cx;
+      s_sb[3 * kk + 1] = (float)cy;
+      s_sb[3 * kk + 2] = (float)(hl + 1e-5 * (1.0 + fabs(cx) + fabs(cy) + hl));
+    }
+    __syncthreads();
+  }
   for (int e = blockIdx.x; e < total; e += gridDim.x) {
     const ibm_stencil s0 = st[e];
     const int kind = s0.kind;
     const int i = s0.cell % k.nx, j = s0.cell / k.nx;
     const double px = k.x0 + ((double)i + 0.5) * k.dx;
     const double py = k.y0 + ((double)j + 0.5) * k.dy;
-    const int nv = g.nv;
+    const float pxf = (float)px, pyf = (float)py;
+    // the smallest upper bound of the node's distance to a segment
+    float ub = INFINITY;
+    if (prune) {
+      for (int kk = threadIdx.x; kk < nv; kk += 128) {
+        const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
+        ub = fminf(ub, sqrtf(dx * dx + dy * dy) + s_sb[3 * kk + 2]);
+      }
+      ub = block_min128f(ub, s_f);
+    }
     // closest feature (Sec. 4.1)
     double best = INFINITY, bcx = 0.0, bcy = 0.0;
     int bseg = 0x7fffffff, bfeat = 0, breg = 0;
     for (int kk = threadIdx.x; kk < nv; kk += 128) {
+      if (prune) {
+        const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
+        if (sqrtf(dx * dx + dy * dy) - s_sb[3 * kk + 2] > ub) continue;
+      }
       const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
       const double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
       const double ex = bx - ax, ey = by - ay;
@@ -513,24 +561,42 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
       nx = g.vnx[feat];
       ny = g.vny[feat];
     }
-    // boundary point on the line along the local normal (Sec. 4.3)
+    // boundary point on the line along the local normal (Sec. 4.3): first the segments that can hold the
+    // closest point, then, beyond them, those that can hold a crossing no farther than the best found (all of
+    // them if none was found)
     const bool ghost = kind > 0;
     double bs_best = INFINITY, bs_s = 0.0, bs_u = 0.0;
     int bs_seg = 0x7fffffff;
-    for (int kk = threadIdx.x; kk < nv; kk += 128) {
-      const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
-      const double ax = g.vx[kk], ay = g.vy[kk];
-      const double ex = g.vx[k1] - ax, ey = g.vy[k1] - ay;
-      const double den = ex * ny - ey * nx;
-      if (den == 0.0) continue;
-      const double wx = px - ax, wy = py - ay;
-      const double u = (wx * ny - wy * nx) / den;
-      if (u < 0.0 || u > 1.0) continue;
-      const double sv = (wx * ey - wy * ex) / den;
-      if (ghost ? (sv < 0.0) : (sv > 0.0)) continue;
-      const double as = fabs(sv);
-      if (as < bs_best) {
-        bs_best = as; bs_s = sv; bs_u = u; bs_seg = kk;
+    float bound = INFINITY;
+    for (int pass = 0; pass < (prune ? 2 : 1); pass++) {
+      if (pass == 1) {
+        const int w2 = block_argmin128(bs_best, bs_seg, s_v, s_i, s_s);
+        if ((int)threadIdx.x == w2) s_d[2] = bs_best;
+        __syncthreads();
+        const double found = s_d[2];
+        __syncthreads();
+        bound = found < INFINITY ? (float)found * (1.f + 1e-6f) : INFINITY;
+      }
+      for (int kk = threadIdx.x; kk < nv; kk += 128) {
+        if (prune) {
+          const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
+          const float lb = sqrtf(dx * dx + dy * dy) - s_sb[3 * kk + 2];
+          if (pass == 0 ? lb > ub : (lb <= ub || lb > bound)) continue;
+        }
+        const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
+        const double ax = g.vx[kk], ay = g.vy[kk];
+        const double ex = g.vx[k1] - ax, ey = g.vy[k1] - ay;
+        const double den = ex * ny - ey * nx;
+        if (den == 0.0) continue;
+        const double wx = px - ax, wy = py - ay;
+        const double u = (wx * ny - wy * nx) / den;
+        if (u < 0.0 || u > 1.0) continue;
+        const double sv = (wx * ey - wy * ex) / den;
+        if (ghost ? (sv < 0.0) : (sv > 0.0)) continue;
+        const double as = fabs(sv);
+        if (as < bs_best || (as == bs_best && kk < bs_seg)) {
+          bs_best = as; bs_s = sv; bs_u = u; bs_seg = kk;
+        }
       }
     }
     win = block_argmin128(bs_best, bs_seg, s_v, s_i, s_s);
@@ -638,6 +704,8 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
 // vertices (see launch_fused_geometry).
 // ---------------------------------------------------------------------------
 
+constexpr int ROW_XMAX = 64;  // crossings of one row kept in shared memory by the fused classification
+
 // clipped cell rectangle [ilo, ihi] x [jlo, jhi]; empty if ilo > ihi or jlo > jhi
 __device__ __forceinline__ void clip_rect(const Consts &k, int r[4]) {
   r[0] = max(r[0], 0);
@@ -737,30 +805,68 @@ __global__ void __launch_bounds__(256) k_pose_classify(Consts k, Geom g, uint8_t
   __syncthreads();
   if (rect[0] > rect[1] || rect[2] > rect[3]) return;
   const int W = rect[1] - rect[0] + 1, H = rect[3] - rect[2] + 1;
-  const long long ncells = (long long)W * H;
   const double b0 = bb[0], b1 = bb[1], b2 = bb[2], b3 = bb[3];
-  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + warp; c < ncells; c += nwarps) {
-    const int i = rect[0] + (int)(c % W), j = rect[2] + (int)(c / W);
-    const double px = k.x0 + ((double)i + 0.5) * k.dx;
+  const int nwarps = (int)gridDim.x * (blockDim.x >> 5);
+  // one warp per row of the rectangle: a segment's crossing abscissa depends only on the row's ordinate, so
+  // the lanes find the crossings of the row once (the same operations as a per-cell test, hence the same bits)
+  // and every cell of the row counts those right of its centre; a row with more than ROW_XMAX crossings
+  // falls back to testing every segment per cell
+  __shared__ double xs[8][ROW_XMAX];
+  for (int r = (int)blockIdx.x * (blockDim.x >> 5) + warp; r < H; r += nwarps) {
+    const int j = rect[2] + r;
     const double py = k.y0 + ((double)j + 0.5) * k.dy;
-    int odd = 0;
-    if (!(px < b0 || px > b1 || py < b2 || py > b3)) {
-      for (int e = lane; e < nv; e += 32) {
-        const int e1 = (e + 1 == nv) ? 0 : e + 1;
-        const double ax = sv[e], ay = sv[nv + e], bx = sv[e1], by = sv[nv + e1];
-        if ((ay > py) != (by > py)) {
-          double t1 = py - ay;
-          double t2 = bx - ax;
-          double t3 = by - ay;
-          double xint = ax + (t1 * t2) / t3;
-          if (xint > px) odd ^= 1;
+    int nx_ = 0;  // crossings of the row found so far (warp-uniform)
+    bool overflow = false;
+    const bool row_in = !(py < b2 || py > b3);
+    if (row_in) {
+      for (int e0 = 0; e0 < nv; e0 += 32) {
+        const int e = e0 + lane;
+        bool cross = false;
+        double xint = 0.0;
+        if (e < nv) {
+          const int e1 = (e + 1 == nv) ? 0 : e + 1;
+          const double ax = sv[e], ay = sv[nv + e], bx = sv[e1], by = sv[nv + e1];
+          if ((ay > py) != (by > py)) {
+            double t1 = py - ay;
+            double t2 = bx - ax;
+            double t3 = by - ay;
+            xint = ax + (t1 * t2) / t3;
+            cross = true;
+          }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, cross);
+        const int pos = nx_ + __popc(m & ((1u << lane) - 1u));
+        if (cross && pos < ROW_XMAX) xs[warp][pos] = xint;
+        nx_ += __popc(m);
+      }
+      overflow = nx_ > ROW_XMAX;
+    }
+    __syncwarp();
+    for (int i = rect[0] + lane; i <= rect[1]; i += 32) {
+      const double px = k.x0 + ((double)i + 0.5) * k.dx;
+      int odd = 0;
+      if (row_in && !(px < b0 || px > b1)) {
+        if (!overflow) {
+          for (int q = 0; q < nx_; q++) odd ^= xs[warp][q] > px ? 1 : 0;
+        } else {
+          for (int e = 0; e < nv; e++) {
+            const int e1 = (e + 1 == nv) ? 0 : e + 1;
+            const double ax = sv[e], ay = sv[nv + e], bx = sv[e1], by = sv[nv + e1];
+            if ((ay > py) != (by > py)) {
+              double t1 = py - ay;
+              double t2 = bx - ax;
+              double t3 = by - ay;
+              double xint = ax + (t1 * t2) / t3;
+              if (xint > px) odd ^= 1;
+            }
+          }
         }
       }
-      odd = __popc(__ballot_sync(0xffffffffu, odd)) & 1;
+      solid[j * k.nx + i] = (uint8_t)odd;
     }
-    if (lane == 0) solid[j * k.nx + i] = (uint8_t)odd;
+    __syncwarp();
   }
+  (void)W;
 }
 
 // does the tile's loaded range [lo, hi] (before domain mapping) along one axis
@@ -795,18 +901,22 @@ __device__ __forceinline__ uint8_t tag_of_staged(const Consts &k, const uint8_t 
 
 // (2) one block of 1024 threads over urect: tags (and sid reset), the
 // row-major IB / G1-G3 lists, then the body-tile flags of every stage tile and
-// their ascending list.  Rectangles of up to STAGED_CELLS cells (with the
-// rule's 3-cell reach) work on shared-memory copies of the solid flags and
-// tags; cells outside urect are fluid (invariant), so no other tag is read.
-// Ends by recording the current rectangle for the next classification.
-constexpr int STAGED_CELLS = 16384;
+// their ascending list.  Rectangles of up to staged_cap cells (with the rule's
+// 3-cell reach; dynamic shared memory sized from the body's pose-independent
+// box) work on shared-memory copies of the solid flags and tags; cells
+// outside urect are fluid (invariant), so no other tag is read.  The lists
+// are ranked with one block-wide scan: every thread owns a contiguous chunk of
+// the rectangle (row-major), counts its nodes per class, takes its offsets
+// from an exclusive scan of the counts and writes its nodes in order.  Ends by
+// recording the current rectangle for the next classification.
+constexpr int STAGED_CELLS_MAX = 100 * 1024;  // 200 KB of shared memory for the two staged byte arrays
 __global__ void __launch_bounds__(1024) k_tags_lists(Consts k, const uint8_t *__restrict__ solid,
                                                      uint8_t *__restrict__ tag, int *__restrict__ sid,
                                                      ibm_stencil *__restrict__ st, int cap,
                                                      uint8_t *__restrict__ tile_body, int *__restrict__ body_tiles,
-                                                     int body_cap, DevState *ds) {
-  __shared__ uint8_t s_sol[STAGED_CELLS];
-  __shared__ uint8_t s_tag[STAGED_CELLS];
+                                                     int body_cap, DevState *ds, int staged_cap) {
+  extern __shared__ uint8_t s_dyn[];
+  uint8_t *s_sol = s_dyn, *s_tag = s_dyn + staged_cap;
   __shared__ int wc[32][4];
   __shared__ int tot[4], run[4], off[4];
   __shared__ int wsum[32];
@@ -816,7 +926,7 @@ __global__ void __launch_bounds__(1024) k_tags_lists(Consts k, const uint8_t *__
   const int n = W * H;
   const int ex0 = max(r0 - 3, 0), ex1 = min(r1 + 3, k.nx - 1), ey0 = max(r2 - 3, 0), ey1 = min(r3 + 3, k.ny - 1);
   const int ew = ex1 - ex0 + 1, eh = ey1 - ey0 + 1;
-  const bool staged = n > 0 && ew * eh <= STAGED_CELLS;
+  const bool staged = n > 0 && ew * eh <= staged_cap && n <= staged_cap;
   if (staged)
     for (int m = tid; m < ew * eh; m += 1024) s_sol[m] = solid[(ey0 + m / ew) * k.nx + ex0 + m % ew];
   __syncthreads();
@@ -856,40 +966,49 @@ __global__ void __launch_bounds__(1024) k_tags_lists(Consts k, const uint8_t *__
     if (o > cap) atomicOr(&ds->err, ERR_CAPACITY);
   }
   __syncthreads();
-  // pass 2: scatter in row-major order, 1024 cells at a time
-  const unsigned lt = (1u << lane) - 1u;
-  for (int base = 0; base < n; base += 1024) {
-    const int m = base + tid;
-    int kind = -1, cell = 0;
-    if (m < n) {
-      const int i = r0 + m % W, j = r2 + m / W;
-      cell = j * k.nx + i;
-      kind = list_kind(staged ? s_tag[m] : tag[cell]);
-    }
-    int rank = 0;
-    for (int q = 0; q < 4; q++) {
-      const unsigned msk = __ballot_sync(0xffffffffu, kind == q);
-      if (lane == 0) wc[warp][q] = __popc(msk);
-      if (kind == q) rank = __popc(msk & lt);
-    }
-    __syncthreads();
-    if (kind >= 0) {
-      int before = 0;
-      for (int w = 0; w < warp; w++) before += wc[w][kind];
-      const int pos = off[kind] + run[kind] + before + rank;
-      if (pos < cap) {
-        st[pos].cell = cell;
-        st[pos].kind = kind;
-      }
-    }
-    __syncthreads();
-    if (tid < 4) {
-      int v = 0;
-      for (int w = 0; w < 32; w++) v += wc[w][tid];
-      run[tid] += v;
-    }
-    __syncthreads();
+  // pass 2: every thread owns the contiguous chunk [m0, m1) of the rectangle (row-major); its nodes of each
+  // class follow those of the threads before it
+  const int chunk = (n + 1023) / 1024, m0 = min(n, tid * chunk), m1 = min(n, m0 + chunk);
+  int own[4] = {0, 0, 0, 0};
+  for (int m = m0; m < m1; m++) {
+    const int q = list_kind(staged ? s_tag[m] : tag[(r2 + m / W) * k.nx + r0 + m % W]);
+    if (q >= 0) own[q]++;
   }
+  // exclusive scan of the four counts over the block: within the warp by shuffles, then over the warp totals
+  int before[4];
+  for (int q = 0; q < 4; q++) {
+    int v = own[q];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    before[q] = v - own[q];
+    if (lane == 31) wc[warp][q] = v;
+  }
+  __syncthreads();
+  if (tid < 4) {  // exclusive scan of the warp totals of class tid (32 values)
+    int acc = 0;
+    for (int w = 0; w < 32; w++) {
+      const int x = wc[w][tid];
+      wc[w][tid] = acc;
+      acc += x;
+    }
+  }
+  __syncthreads();
+  int pos[4];
+  for (int q = 0; q < 4; q++) pos[q] = off[q] + wc[warp][q] + before[q];
+  for (int m = m0; m < m1; m++) {
+    const int i = r0 + m % W, j = r2 + m / W, cell = j * k.nx + i;
+    const int q = list_kind(staged ? s_tag[m] : tag[cell]);
+    if (q < 0) continue;
+    const int p_ = pos[q]++;
+    if (p_ < cap) {
+      st[p_].cell = cell;
+      st[p_].kind = q;
+    }
+  }
+  (void)run;
+  __syncthreads();
   // body-tile flags (one warp per tile; tiles out of reach of the body's cells skipped) and their list
   if (tile_body) {
     constexpr int T = STAGE_TILE, HX = T + 2 * NG, HY = T + 2 * NG;
@@ -969,16 +1088,34 @@ __global__ void __launch_bounds__(1024) k_tags_lists(Consts k, const uint8_t *__
   }
 }
 
+// opt the one-block tag / list kernel into the dynamic shared memory its staging uses (once per process and
+// device, before any capture)
+void prepare_geometry_kernels() {
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+  cudaFuncSetAttribute(k_tags_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGED_CELLS_MAX);
+  done[dev] = true;
+}
+
 int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_t *tag, ibm_stencil *st, int cap,
                           RStencil32 *rs, int *sid, uint8_t *tile_body, int *body_tiles, int body_cap, int maxw,
                           int maxh, DevState *ds, cudaStream_t s) {
-  const long long warps = (long long)(maxw + 8) * (maxh + 8);
+  // one warp per row of the classification rectangle (at most the body's pose-independent height, the previous
+  // rectangle's and the margins)
+  const long long warps = 2LL * (maxh + 8);
   const int blocks = (int)std::min<long long>(std::max<long long>((warps + 7) / 8, 1), 4096);
   k_pose_classify<<<blocks, 256, 2 * sizeof(double) * g.nv, s>>>(k, g, solid, ds);
-  k_tags_lists<<<1, 1024, 0, s>>>(k, solid, tag, sid, st, cap, tile_body, body_tiles, body_cap, ds);
+  // staged copies of the rectangle (plus the tag rule's reach) in dynamic shared memory, sized for the body's
+  // pose-independent box with room for one step's motion; larger rectangles read global memory
+  const long long want = (long long)(maxw + 24) * (maxh + 24);
+  const int staged_cap = (int)std::min<long long>(want, STAGED_CELLS_MAX);
+  k_tags_lists<<<1, 1024, 2 * (size_t)staged_cap, s>>>(k, solid, tag, sid, st, cap, tile_body, body_tiles, body_cap,
+                                                       ds, staged_cap);
   int nl = 2;
   if (cap > 0) {
-    k_stencils<<<(unsigned)min(cap, 4 * 152), 128, 0, s>>>(k, g, tag, st, cap, ds, rs, sid);
+    k_stencils<<<(unsigned)min(cap, 4 * 152), 128, g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(
+        k, g, tag, st, cap, ds, rs, sid);
     nl++;
   }
   return nl;
@@ -987,7 +1124,8 @@ int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_
 void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
                      cudaStream_t s) {
   if (cap <= 0) return;
-  k_stencils<<<(unsigned)min(cap, 4 * 152), 128, 0, s>>>(k, g, tag, st, cap, ds, nullptr, nullptr);
+  k_stencils<<<(unsigned)min(cap, 4 * 152), 128, g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(
+      k, g, tag, st, cap, ds, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------

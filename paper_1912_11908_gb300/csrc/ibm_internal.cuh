@@ -239,6 +239,8 @@ void launch_tags(const Consts &k, const uint8_t *solid, uint8_t *tag, int *block
                  ibm_stencil *st, cudaStream_t s, int *nlaunch);
 void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
                      cudaStream_t s);
+// Opt the fused geometry kernels into the shared memory they use (once per device; before any capture).
+void prepare_geometry_kernels();
 // Geometry of one classification for bodies of at most FUSED_MAX_VERTS
 // vertices, restricted to the cells the body can occupy: (1) pose and
 // ray-parity classification of the cells of the previous and current
@@ -304,7 +306,6 @@ int stage_tiles(const Consts &k);
 struct PertConsts {  // FP32 copies of the free-stream constants
   float gamma, g1, gg, R, Hinf, ux, uy, mu, kappa, idx, idy, dmin, vis, cp;
   float cfl_tau, idt_phys;  // dual time: pseudo-time CFL number, 1 / physical dt
-  int tvd2;                 // face reconstruction: TVD-2 instead of WENO5
 };
 
 __host__ inline PertConsts pert_consts(const Consts &k) {
@@ -325,7 +326,6 @@ __host__ inline PertConsts pert_consts(const Consts &k) {
   c.cp = (float)k.cp;
   c.cfl_tau = (float)k.cfl_tau;
   c.idt_phys = (float)k.idt_phys;
-  c.tvd2 = k.tvd2;
   return c;
 }
 

@@ -335,7 +335,9 @@ static __device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts
 // which stay fixed during the launch; the step's end (t, step count) and the
 // next dt are left to the kernel.
 // sm: the block's shared memory.
-template <int STAGE, bool BODY, bool DUAL = false, bool TMA = false, bool PERSIST = false>
+// TVD: the second-order TVD reconstruction in place of WENO5 (Sec. 2), compiled into its own kernels so that
+// the WENO5 kernels carry no branch for it.
+template <int STAGE, bool BODY, bool DUAL = false, bool TMA = false, bool PERSIST = false, bool TVD = false>
 __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c, float *Mn,
                                            const float *__restrict__ In, float *Out, double *D,
                                            const uint8_t *__restrict__ tag,
@@ -392,6 +394,21 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
   if (!__syncthreads_or(work)) {
     if (STAGE == 3 && fuse_cfl && threadIdx.x == 0) finish_cfl(k, ds, ncfl, PERSIST);
     return;
+  }
+  // L2 prefetch of the operands the stage update reads at the end of the tile (the mirror of U^n; the stage
+  // input; the FP64 master at stage 3): one line per tile row and plane, issued before the tile's arithmetic
+  // so that those reads find L2 rather than DRAM after the L2 has turned over
+  if (!DUAL && threadIdx.x < 4 * TY) {
+    const int r = threadIdx.x % TY, v = threadIdx.x / TY;
+    if (j0 + r < k.ny) {
+      const long long o = cidx(k, i0, j0 + r) + v * k.plane;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(Mn + o));
+      if (STAGE >= 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(In + o));
+      if (STAGE == 3) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(D + o));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(D + o + 8));
+      }
+    }
   }
   if (BODY && threadIdx.x == 0) {
     double X[2], V[2], Acc[2];
@@ -564,7 +581,7 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
   // polynomials and the nonlinear weights of a window give the left state at its right face and, mirrored, the
   // right state at its left face.
   static_assert(TX == 16 && TY == 16, "one item per thread: 2 directions x 16 lines x 4 variables x 2 halves");
-  if (c.tvd2) {
+  if (TVD) {
     // the second-order TVD scheme (Sec. 2): MUSCL with the minmod limiter over the same items; differences
     // of perturbations equal differences of the variables, so the limiter sees what it would in absolute form
     const int u = threadIdx.x & 127;
