@@ -276,7 +276,9 @@ def run_ours(args, rank, world):
         traffic = None
     flops_per_launch = (DUAL_FP64_FLOPS_PER_CELL if is_dual else FLOPS_PER_CELL_STAGE) * spec["nx"] * spec["ny"]
     achieved_tf = flops_per_launch / (stage_avg_ms * 1e-3) / 1e12
-    fma = measure_fma_peaks(ibm, smi_index)
+    fma = measure_fma_peaks(ibm, smi_index) if not args.skip_peaks else None
+    if fma is None:  # profiling runs: the peaks of the last measured run are not needed
+        fma = {"fp32": {"tflops": float("nan")}, "fp64": {"tflops": float("nan")}, "clocks": None, "how": "skipped"}
     if is_dual:
         # the FP64 point-implicit update bounds the pseudo stage
         rl_bound, rl_peak = "fp64", fma["fp64"]["tflops"]
@@ -430,7 +432,7 @@ def run_ours(args, rank, world):
     # 3-D immersed-boundary pre-processing (Appendix A: a 1200-triangle sphere in a 40^3 lattice): classification,
     # tags, ordered lists, closest features and pseudo-normals, timed on the device
     geo3d = None
-    if rank == 0:
+    if rank == 0 and not args.skip_geometry3d:
         from paper_1912_11908_gb300 import workloads as W
         sv, st_ = W.uv_sphere(21, 30, 0.35, (0.5, 0.5, 0.5))
         b3 = ibm.Body3D(sv, st_, stream=stream.cuda_stream)
@@ -754,6 +756,8 @@ def main():
     ap.add_argument("--skip-moving", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-peaks", action="store_true", help="do not measure the FMA peaks (profiling runs)")
+    ap.add_argument("--skip-geometry3d", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=32)
     ap.add_argument("--serve-chunk", type=int, default=10)

@@ -497,7 +497,7 @@ static ibm_status do_classify(ibm_case *c) {
   if (c->g.nv > 0 && c->g.nv <= FUSED_MAX_VERTS) {
     // pose + classification, tags / lists / tile lists, stencils: three kernels over the body's rectangle
     nl += launch_fused_geometry(c->k, c->g, c->solid, c->tag, c->st, c->cap, c->rst, c->sid, c->tile_body,
-                                c->body_tiles, c->body_cap, c->box_w, c->box_h, c->ds, s);
+                                c->body_tiles, c->body_cap, c->box_w, c->box_h, c->ds, c->blockcounts, s);
     prof_mark(c, 4, false);
     c->launches += nl;
     c->classified = true;

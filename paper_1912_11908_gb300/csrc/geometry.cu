@@ -421,36 +421,11 @@ __device__ __forceinline__ int warp_argmin(double v, int idx) {
   return src;
 }
 
-// lexicographic (value, index) minimum across a 128-thread block; every
-// thread gets the winning thread's index.  sv / si / ss: 4-entry shared arrays
-__device__ __forceinline__ int block_argmin128(double v, int idx, double *sv, int *si, int *ss) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int src = warp_argmin(v, idx);
-  const double wv = __shfl_sync(0xffffffffu, v, src);
-  const int wi = __shfl_sync(0xffffffffu, idx, src);
-  if (lane == 0) {
-    sv[w] = wv;
-    si[w] = wi;
-    ss[w] = w * 32 + src;
-  }
-  __syncthreads();
-  double bv = sv[0];
-  int bi = si[0], bs = ss[0];
-  for (int q = 1; q < 4; q++)
-    if (sv[q] < bv || (sv[q] == bv && si[q] < bi)) {
-      bv = sv[q];
-      bi = si[q];
-      bs = ss[q];
-    }
-  __syncthreads();
-  return bs;
-}
-
-// Sec. 4.1-4.6, Sec. 5: one stencil per listed node, one 128-thread block per
-// node (blocks stride over the list).  The threads split the segments of the
-// two exhaustive searches (closest feature, boundary point); the block keeps
-// the (distance, segment) lexicographic minimum, which is the first minimum of
-// a sequential scan.
+// Sec. 4.1-4.6, Sec. 5: one stencil per listed node, one warp per node (four
+// per 128-thread block, blocks striding over the list).  The lanes split the
+// segments of the two searches (closest feature, boundary point); the warp
+// keeps the (distance, segment) lexicographic minimum, which is the first
+// minimum of a sequential scan.
 // rs / sid (optional): the FP32 compact form of each stencil and the cell ->
 // stencil map of the FP32-bulk reconstruction.
 // Pruning (bodies of up to STENCIL_PRUNE_MAX vertices): every segment's
@@ -463,28 +438,16 @@ __device__ __forceinline__ int block_argmin128(double v, int idx, double *sv, in
 // the exact FP64 tests on the others only, so the result is the exhaustive
 // search's, bit for bit.
 constexpr int STENCIL_PRUNE_MAX = 2048;
-__device__ __forceinline__ float block_min128f(float v, float *sf) {
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) sf[threadIdx.x >> 5] = v;
-  __syncthreads();
-  v = fminf(fminf(sf[0], sf[1]), fminf(sf[2], sf[3]));
-  __syncthreads();
-  return v;
-}
-
 __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_t *__restrict__ tag,
                                                   ibm_stencil *__restrict__ st, int cap, DevState *ds,
                                                   RStencil32 *__restrict__ rs, int *__restrict__ sid) {
-  __shared__ double s_v[4];
-  __shared__ int s_i[4], s_s[4];
-  __shared__ double s_d[5];
-  __shared__ int s_n[3];
-  __shared__ float s_f[4];
   extern __shared__ float s_sb[];  // per segment: centre x, y and radius (half length plus the margin), FP32
   const int total = min(ds->offset[4], cap);
   const int nv = g.nv;
   const bool prune = nv <= STENCIL_PRUNE_MAX;
-  if (prune && (int)blockIdx.x < total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if ((int)blockIdx.x * 4 >= total) return;
+  if (prune) {
     for (int kk = threadIdx.x; kk < nv; kk += 128) {
       const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
       const double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
@@ -496,7 +459,8 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
     }
     __syncthreads();
   }
-  for (int e = blockIdx.x; e < total; e += gridDim.x) {
+  // one warp per listed node, the lanes splitting the segments of the searches
+  for (int e = (int)blockIdx.x * 4 + warp; e < total; e += (int)gridDim.x * 4) {
     const ibm_stencil s0 = st[e];
     const int kind = s0.kind;
     const int i = s0.cell % k.nx, j = s0.cell / k.nx;
@@ -506,16 +470,16 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
     // the smallest upper bound of the node's distance to a segment
     float ub = INFINITY;
     if (prune) {
-      for (int kk = threadIdx.x; kk < nv; kk += 128) {
+      for (int kk = lane; kk < nv; kk += 32) {
         const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
         ub = fminf(ub, sqrtf(dx * dx + dy * dy) + s_sb[3 * kk + 2]);
       }
-      ub = block_min128f(ub, s_f);
+      for (int o = 16; o > 0; o >>= 1) ub = fminf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
     }
     // closest feature (Sec. 4.1)
     double best = INFINITY, bcx = 0.0, bcy = 0.0;
     int bseg = 0x7fffffff, bfeat = 0, breg = 0;
-    for (int kk = threadIdx.x; kk < nv; kk += 128) {
+    for (int kk = lane; kk < nv; kk += 32) {
       if (prune) {
         const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
         if (sqrtf(dx * dx + dy * dy) - s_sb[3 * kk + 2] > ub) continue;
@@ -542,17 +506,10 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
         best = d2; bseg = kk; bfeat = f; breg = r; bcx = cx; bcy = cy;
       }
     }
-    int win = block_argmin128(best, bseg, s_v, s_i, s_s);
-    if ((int)threadIdx.x == win) {
-      s_n[0] = bfeat;
-      s_n[1] = breg;
-      s_d[0] = bcx;
-      s_d[1] = bcy;
-    }
-    __syncthreads();
-    const int feat = s_n[0];
-    const int region = s_n[1];
-    const double ccx = s_d[0], ccy = s_d[1];
+    int win = warp_argmin(best, bseg);
+    const int feat = __shfl_sync(0xffffffffu, bfeat, win);
+    const int region = __shfl_sync(0xffffffffu, breg, win);
+    const double ccx = __shfl_sync(0xffffffffu, bcx, win), ccy = __shfl_sync(0xffffffffu, bcy, win);
     double nx, ny;
     if (region == IBM_REGION_FACE) {
       nx = g.snx[feat];
@@ -570,14 +527,11 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
     float bound = INFINITY;
     for (int pass = 0; pass < (prune ? 2 : 1); pass++) {
       if (pass == 1) {
-        const int w2 = block_argmin128(bs_best, bs_seg, s_v, s_i, s_s);
-        if ((int)threadIdx.x == w2) s_d[2] = bs_best;
-        __syncthreads();
-        const double found = s_d[2];
-        __syncthreads();
+        const int w2 = warp_argmin(bs_best, bs_seg);
+        const double found = __shfl_sync(0xffffffffu, bs_best, w2);
         bound = found < INFINITY ? (float)found * (1.f + 1e-6f) : INFINITY;
       }
-      for (int kk = threadIdx.x; kk < nv; kk += 128) {
+      for (int kk = lane; kk < nv; kk += 32) {
         if (prune) {
           const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
           const float lb = sqrtf(dx * dx + dy * dy) - s_sb[3 * kk + 2];
@@ -599,17 +553,12 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
         }
       }
     }
-    win = block_argmin128(bs_best, bs_seg, s_v, s_i, s_s);
-    if ((int)threadIdx.x == win) {
-      s_d[2] = bs_best;
-      s_d[3] = bs_s;
-      s_d[4] = bs_u;
-      s_n[2] = bs_seg;
-    }
-    __syncthreads();
-    const double found_abs = s_d[2];
-    const double bsv = s_d[3];
-    if (threadIdx.x == 0) {
+    win = warp_argmin(bs_best, bs_seg);
+    const double found_abs = __shfl_sync(0xffffffffu, bs_best, win);
+    const double bsv = __shfl_sync(0xffffffffu, bs_s, win);
+    const double bsu = __shfl_sync(0xffffffffu, bs_u, win);
+    const int bsg = __shfl_sync(0xffffffffu, bs_seg, win);
+    if (lane == 0) {
       ibm_stencil s = s0;
       double bx, by, xi_node;
       int fb;
@@ -650,8 +599,8 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
       if (fb && region == IBM_REGION_VERTEX) {
         curv = g.vk[feat];
       } else {
-        int sg = s_n[2];
-        double uu = s_d[4];
+        int sg = bsg;
+        double uu = bsu;
         if (fb) {  // P' is the foot point on segment feat
           const int f1 = (feat + 1 == nv) ? 0 : feat + 1;
           const double ex = g.vx[f1] - g.vx[feat], ey = g.vy[f1] - g.vy[feat];
@@ -695,7 +644,7 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
         sid[s.cell] = e;
       }
     }
-    __syncthreads();  // shared memory is reused by the next entry
+    __syncwarp();
   }
 }
 
@@ -1088,6 +1037,77 @@ __global__ void __launch_bounds__(1024) k_tags_lists(Consts k, const uint8_t *__
   }
 }
 
+// Bodies whose pose-independent box holds more than LARGE_RECT cells: the same tags and lists over many blocks.
+// Chunk c of the rectangle is its cells [c TAG_BLOCK, (c + 1) TAG_BLOCK) in row-major order; one block per
+// chunk (chunks past the rectangle count zero), then the block scan of launch_tags and a rectangle scatter; the
+// body-tile flags and list follow with launch_tile_lists.
+constexpr long long LARGE_RECT = 8192;
+__global__ void __launch_bounds__(TAG_BLOCK) k_rect_tags(Consts k, const uint8_t *__restrict__ solid,
+                                                         uint8_t *__restrict__ tag, int *__restrict__ sid,
+                                                         int *__restrict__ blockcounts, const DevState *ds) {
+  __shared__ int wc[TAG_BLOCK / 32][4];
+  const int r0 = ds->urect[0], r1 = ds->urect[1], r2 = ds->urect[2], r3 = ds->urect[3];
+  const int W = r0 <= r1 && r2 <= r3 ? r1 - r0 + 1 : 0, H = W ? r3 - r2 + 1 : 0;
+  const int m = blockIdx.x * TAG_BLOCK + threadIdx.x;
+  int kind = -1;
+  if (m < W * H) {
+    const int i = r0 + m % W, j = r2 + m / W;
+    const uint8_t t = tag_of(k, solid, i, j);
+    tag[j * k.nx + i] = t;
+    if (sid) sid[j * k.nx + i] = -1;
+    kind = list_kind(t);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < 4; q++) {
+    const unsigned b = __ballot_sync(0xffffffffu, kind == q);
+    if (lane == 0) wc[warp][q] = __popc(b);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    int v = 0;
+    for (int w = 0; w < TAG_BLOCK / 32; w++) v += wc[w][threadIdx.x];
+    blockcounts[4 * blockIdx.x + threadIdx.x] = v;
+  }
+}
+
+__global__ void __launch_bounds__(TAG_BLOCK) k_rect_scatter(Consts k, const uint8_t *__restrict__ tag,
+                                                            const int *__restrict__ blockoff, DevState *ds,
+                                                            ibm_stencil *__restrict__ st, int cap) {
+  __shared__ int wc[TAG_BLOCK / 32][4];
+  const int r0 = ds->urect[0], r1 = ds->urect[1], r2 = ds->urect[2], r3 = ds->urect[3];
+  const int W = r0 <= r1 && r2 <= r3 ? r1 - r0 + 1 : 0, H = W ? r3 - r2 + 1 : 0;
+  const int m = blockIdx.x * TAG_BLOCK + threadIdx.x;
+  int kind = -1, cell = 0;
+  if (m < W * H) {
+    cell = (r2 + m / W) * k.nx + r0 + m % W;
+    kind = list_kind(tag[cell]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int rank = 0;
+  for (int q = 0; q < 4; q++) {
+    const unsigned b = __ballot_sync(0xffffffffu, kind == q);
+    if (lane == 0) wc[warp][q] = __popc(b);
+    if (kind == q) rank = __popc(b & lt);
+  }
+  __syncthreads();
+  if (kind >= 0) {
+    int before = 0;
+    for (int w = 0; w < warp; w++) before += wc[w][kind];
+    const int pos = ds->offset[kind] + blockoff[blockIdx.x * 4 + kind] + before + rank;
+    if (pos < cap) {
+      st[pos].cell = cell;
+      st[pos].kind = kind;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the rectangle of this classification, for the next one
+    int r[4] = {ds->bcell[0], ds->bcell[1], ds->bcell[2], ds->bcell[3]};
+    clip_rect(k, r);
+    for (int q = 0; q < 4; q++) ds->prect[q] = r[q];
+    ds->prect_valid = 1;
+  }
+}
+
 // opt the one-block tag / list kernel into the dynamic shared memory its staging uses (once per process and
 // device, before any capture)
 void prepare_geometry_kernels() {
@@ -1100,7 +1120,7 @@ void prepare_geometry_kernels() {
 
 int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_t *tag, ibm_stencil *st, int cap,
                           RStencil32 *rs, int *sid, uint8_t *tile_body, int *body_tiles, int body_cap, int maxw,
-                          int maxh, DevState *ds, cudaStream_t s) {
+                          int maxh, DevState *ds, int *blockcounts, cudaStream_t s) {
   // one warp per row of the classification rectangle (at most the body's pose-independent height, the previous
   // rectangle's and the margins)
   const long long warps = 2LL * (maxh + 8);
@@ -1110,12 +1130,26 @@ int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_
   // pose-independent box with room for one step's motion; larger rectangles read global memory
   const long long want = (long long)(maxw + 24) * (maxh + 24);
   const int staged_cap = (int)std::min<long long>(want, STAGED_CELLS_MAX);
-  k_tags_lists<<<1, 1024, 2 * (size_t)staged_cap, s>>>(k, solid, tag, sid, st, cap, tile_body, body_tiles, body_cap,
-                                                       ds, staged_cap);
   int nl = 2;
+  if ((long long)maxw * maxh > LARGE_RECT && blockcounts) {
+    // one block per chunk of the grid's size (the block counts are sized for it), so that any rectangle is
+    // covered; blocks past the rectangle exit at once
+    const int nchunk = (int)(((long long)k.nx * k.ny + TAG_BLOCK - 1) / TAG_BLOCK);
+    k_rect_tags<<<nchunk, TAG_BLOCK, 0, s>>>(k, solid, tag, sid, blockcounts, ds);
+    k_scan_blocks<<<1, 1024, 0, s>>>(nchunk, blockcounts, ds, cap);
+    k_rect_scatter<<<nchunk, TAG_BLOCK, 0, s>>>(k, tag, blockcounts, ds, st, cap);
+    nl += 2;
+    if (tile_body) {
+      launch_tile_lists(k, tag, tile_body, body_tiles, body_cap, ds, true, s);
+      nl += 2;
+    }
+  } else {
+    k_tags_lists<<<1, 1024, 2 * (size_t)staged_cap, s>>>(k, solid, tag, sid, st, cap, tile_body, body_tiles,
+                                                         body_cap, ds, staged_cap);
+  }
   if (cap > 0) {
-    k_stencils<<<(unsigned)min(cap, 4 * 152), 128, g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(
-        k, g, tag, st, cap, ds, rs, sid);
+    k_stencils<<<(unsigned)min((cap + 3) / 4, 8 * 152), 128,
+                 g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(k, g, tag, st, cap, ds, rs, sid);
     nl++;
   }
   return nl;
@@ -1124,8 +1158,8 @@ int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_
 void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
                      cudaStream_t s) {
   if (cap <= 0) return;
-  k_stencils<<<(unsigned)min(cap, 4 * 152), 128, g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(
-      k, g, tag, st, cap, ds, nullptr, nullptr);
+  k_stencils<<<(unsigned)min((cap + 3) / 4, 8 * 152), 128,
+               g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(k, g, tag, st, cap, ds, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1136,15 +1170,20 @@ void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_ste
 // the segment midpoint); free-stream pressure subtracted.  One block;
 // fixed-order tree reduction (deterministic).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint8_t *__restrict__ tag,
-                                                    const double *__restrict__ A, bool pert, DevState *ds,
-                                                    bool set_accel, double *__restrict__ surf) {
-  __shared__ double rx[256], ry[256];
+// Eq. 9 over the body's segments: up to FORCE_BLOCKS blocks of FORCE_THREADS threads, one segment per thread
+// (blocks stride over longer bodies); each block sums its segments in a fixed tree order into a partial, and
+// the last block to finish adds the partials in block order, so the sum is deterministic
+constexpr int FORCE_THREADS = 64, FORCE_BLOCKS = 64;
+__global__ void __launch_bounds__(FORCE_THREADS) k_forces_f64(Consts k, Geom g, const uint8_t *__restrict__ tag,
+                                                              const double *__restrict__ A, bool pert, DevState *ds,
+                                                              bool set_accel, double *__restrict__ surf) {
+  __shared__ double rx[FORCE_THREADS], ry[FORCE_THREADS];
+  __shared__ bool last;
   double V[2], Acc[2], X[2];
   body_motion(k, ds, ds->t, X, V, Acc);
   const bool sup = supersonic_motion(k, V);
   double sx = 0.0, sy = 0.0;
-  for (int e = threadIdx.x; e < g.nv; e += blockDim.x) {
+  for (int e = blockIdx.x * FORCE_THREADS + threadIdx.x; e < g.nv; e += gridDim.x * FORCE_THREADS) {
     int e1 = (e + 1 == g.nv) ? 0 : e + 1;
     double ax = g.vx[e], ay = g.vy[e];
     double ex = g.vx[e1] - ax, ey = g.vy[e1] - ay;
@@ -1202,7 +1241,7 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
   rx[threadIdx.x] = sx;
   ry[threadIdx.x] = sy;
   __syncthreads();
-  for (int off = 128; off > 0; off >>= 1) {
+  for (int off = FORCE_THREADS / 2; off > 0; off >>= 1) {
     if (threadIdx.x < off) {
       rx[threadIdx.x] += rx[threadIdx.x + off];
       ry[threadIdx.x] += ry[threadIdx.x + off];
@@ -1210,23 +1249,38 @@ __global__ void __launch_bounds__(256) k_forces_f64(Consts k, Geom g, const uint
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double q = 0.5 * k.ref_len;
-    ds->force[0] = rx[0] / q;
-    ds->force[1] = ry[0] / q;
-    ds->force[2] = rx[0];
-    ds->force[3] = ry[0];
+    ds->fpart[2 * blockIdx.x] = rx[0];
+    ds->fpart[2 * blockIdx.x + 1] = ry[0];
+    __threadfence();
+    last = atomicAdd(&ds->fdone, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double fx = 0.0, fy = 0.0;
+    for (int b = 0; b < (int)gridDim.x; b++) {
+      fx += *(volatile double *)&ds->fpart[2 * b];
+      fy += *(volatile double *)&ds->fpart[2 * b + 1];
+    }
+    ds->fdone = 0;
+    const double q = 0.5 * k.ref_len;
+    ds->force[0] = fx / q;
+    ds->force[1] = fy / q;
+    ds->force[2] = fx;
+    ds->force[3] = fy;
     if (set_accel) {  // Eq. 10: this force sets the body's acceleration for the step
-      ds->bF[0] = rx[0];
-      ds->bF[1] = ry[0];
-      ds->bA[0] = rx[0] / k.motion.mass;
-      ds->bA[1] = ry[0] / k.motion.mass;
+      ds->bF[0] = fx;
+      ds->bF[1] = fy;
+      ds->bA[0] = fx / k.motion.mass;
+      ds->bA[1] = fy / k.motion.mass;
     }
   }
 }
 
 void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, bool pert,
                        DevState *ds, cudaStream_t s, bool set_accel, double *surf) {
-  k_forces_f64<<<1, 256, 0, s>>>(k, g, tag, A, pert, ds, set_accel, surf);
+  const int blocks = std::max(1, std::min(FORCE_BLOCKS, (g.nv + FORCE_THREADS - 1) / FORCE_THREADS));
+  k_forces_f64<<<blocks, FORCE_THREADS, 0, s>>>(k, g, tag, A, pert, ds, set_accel, surf);
 }
 
 // Sec. 6, Eq. 10: end of a step of a body translating under the fluid force.  The step's constant

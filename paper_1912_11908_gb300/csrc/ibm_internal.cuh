@@ -41,6 +41,10 @@ struct DevState {
   // body free to translate under the fluid force (Eq. 10): displacement, velocity and acceleration at bt, the
   // start of the current step, and the force that set the acceleration
   double bX[2], bV[2], bA[2], bF[2], bt;
+  // surface force (Eq. 9): per-block partial sums of the force kernel and the blocks finished (0 between calls)
+  double fpart[2 * 64];
+  unsigned int fdone;
+  int pad3;
 };
 
 // IB / ghost lists up to this capacity are rebuilt by a single 1024-thread
@@ -251,9 +255,10 @@ void prepare_geometry_kernels();
 // untagged and unlisted (solid, tag and sid are cleared at creation).  Same
 // results as the unrestricted kernels.  Returns the kernels launched.
 constexpr int FUSED_MAX_VERTS = 1024;
+// blockcounts: 4 ints per TAG_BLOCK cells of the grid (the multi-block lists of large bodies)
 int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_t *tag, ibm_stencil *st, int cap,
                           RStencil32 *rs, int *sid, uint8_t *tile_body, int *body_tiles, int body_cap, int maxw,
-                          int maxh, DevState *ds, cudaStream_t s);
+                          int maxh, DevState *ds, int *blockcounts, cudaStream_t s);
 // A: FP64 state, absolute conserved (pert = false) or perturbation (pert = true)
 void launch_body_end(DevState *ds, cudaStream_t s);
 // surf (optional): per segment the pressure and skin-friction coefficients, surf[e] and surf[nv + e]
