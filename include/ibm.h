@@ -432,7 +432,8 @@ ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, in
  * library facility built on the calls above.)
  *
  * A server queues solve requests -- body, grid, flow, motion and a number of
- * explicit steps -- and admits them in arrival order while fewer than
+ * steps (explicit steps, or physical steps in dual time) -- and admits them in
+ * arrival order while fewer than
  * max_active cases are running and the device bytes of the running cases
  * (ibm_case_device_bytes) plus the next request's stay within the budget.
  * Each admitted case owns its device state, tags and lists and a stream of
@@ -443,22 +444,28 @@ ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, in
  * goes to the next waiting request.  Cases share nothing on the device, so
  * a request gives the same result alone and in any mix.
  *
- * Batched mode (default) for FP32-bulk explicit RK3 requests: the requests
- * admitted in one pass form groups of up to 24 cases of similar size (grids
- * within a factor four in cells) and equal step counts; one step of a group is
- * one CUDA graph with the per-case pre-stage work (re-classification of moving
- * bodies, dt) on the cases' streams and, per RK stage, one launch of the
- * plain-tile kernel and one of the body-tile kernel over the block table of
- * all member cases.  A group's membership is fixed when it forms (its graph is
- * captured once and its members finish together); later arrivals form new
- * groups, which run beside the old ones.  With IBM_SERVE_AUTOTUNE the
- * plain-tile launch's schedule (one block per tile, or a persistent grid
- * striding over the table) is picked by timing the candidates on the group,
- * once per size class and membership size.  Other requests (FP64, dual time),
- * and all requests when batching is off, advance on their own streams as
- * described above.  Results do not depend on the mix; they are bit-identical
- * to a case stepped alone on the own-stream path and equal up to FP32
- * rounding in a group (its kernels are compiled separately).
+ * Batched mode (default) for FP32-bulk requests (explicit RK3 with any
+ * motion, including a body under the fluid force, or dual time; not TVD-2):
+ * the requests admitted in one pass form groups of up to 24 cases of similar
+ * size (grids within a factor four in cells), equal step counts and the same
+ * time scheme (dual time: equal sub-iteration counts).  One step of a group is
+ * one CUDA graph: the per-case work before the stages (re-classification of
+ * moving bodies, the force and acceleration of Eq. 10, dt, or the rotation of
+ * the dual-time levels) on the cases' streams; per RK stage, or per pseudo
+ * stage of every sub-iteration, one launch over the block table of all member
+ * cases; then the per-case work that ends the step (the body update of
+ * Eq. 10, the end of a dual-time step).  A group's membership is fixed when it
+ * forms (its graph is captured once and its members finish together); later
+ * arrivals form new groups, which run beside the old ones.  With
+ * IBM_SERVE_AUTOTUNE the stage launch's schedule of an explicit group whose
+ * bodies do not move under the fluid force (one block per tile, or a
+ * persistent grid striding over the table) is picked by timing the candidates
+ * on the group, once per size class and membership size.  Other requests
+ * (FP64, TVD-2), and all requests when batching is off, advance on their own
+ * streams as described above.  Results do not depend on the mix; they are
+ * bit-identical to a case stepped alone on the own-stream path and, for
+ * dual-time requests, in a group; explicit requests in a group are equal up
+ * to FP32 rounding (the group's stage kernel is compiled separately).
  *
  * The server is driven by the caller's thread: ibm_server_progress does one
  * non-blocking pass (retire finished cases, admit waiting requests, enqueue

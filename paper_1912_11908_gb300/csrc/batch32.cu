@@ -1,5 +1,6 @@
 // Block-table stage kernels of the request loop: one launch per RK stage over
-// all member cases of a group.  Kept in a module of their own: linked into the
+// all member cases of a group (the dual-time pseudo-stage form is in
+// dual32.cu, beside the single-case dual-time launch that shares it).  Kept in a module of their own: linked into the
 // single-case module, these kernels slowed the replay of single-case step
 // graphs by ~10% on GB300 (measured; kernel durations themselves unchanged).
 #include "stage32.cuh"
@@ -86,6 +87,8 @@ void fill_stage_case(const Consts &k, float *M, float *F1, float *F2, double *D,
   out->nb = body_cap > 0 ? body_cap : 0;
   out->fuse_cfl = fuse_cfl ? 1 : 0;
   out->ncfl = (unsigned int)(out->nt + out->nb);
+  out->B = out->C = out->Q0 = nullptr;
+  out->G = nullptr;
 }
 
 

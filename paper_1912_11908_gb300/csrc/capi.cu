@@ -56,6 +56,12 @@ struct ibm_case {
   int box_w = 0, box_h = 0;      // cells spanned by the body's bounding box (any pose), for classification
   cudaStream_t sb = nullptr;     // FP32-bulk: stream of the body-tile kernels (forked from / joined to stream)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // FP32-bulk per-step geometry: after the tags, the stencils run on sb and the force of a body under the fluid
+  // force on sf, beside the tile lists and dt on the case stream; joined before the stages
+  cudaStream_t sf = nullptr;
+  cudaEvent_t ev_tags = nullptr, ev_sten = nullptr, ev_force = nullptr;
+  bool geo_forked = false;   // stencils in flight on sb since the last classification
+  bool force_forked = false; // force in flight on sf
   int cap = 0;
   bool dt_valid = false;      // FP32-bulk static body: dt of the next step is already in DevState
   DevState *ds = nullptr;
@@ -355,7 +361,10 @@ static void free_case(ibm_case *c) {
     if (c->ev[q]) cudaEventDestroy(c->ev[q]);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (cudaEvent_t ev : {c->ev_tags, c->ev_sten, c->ev_force})
+    if (ev) cudaEventDestroy(ev);
   if (c->sb) cudaStreamDestroy(c->sb);
+  if (c->sf) cudaStreamDestroy(c->sf);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -413,6 +422,9 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
     e = cudaStreamCreateWithPriority(&c->sb, cudaStreamNonBlocking, prio_hi);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->sf, cudaStreamNonBlocking, prio_hi);
+    for (cudaEvent_t *ev : {&c->ev_tags, &c->ev_sten, &c->ev_force})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   }
   if (e != cudaSuccess) {
     free_case(c);
@@ -490,15 +502,51 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   return IBM_OK;
 }
 
-static ibm_status do_classify(ibm_case *c) {
+// the per-step geometry work forked by do_classify (stencils) and enqueue_force (force) joins the case stream
+static void geometry_join(ibm_case *c) {
+  if (c->geo_forked) {
+    cudaEventRecord(c->ev_sten, c->sb);
+    cudaStreamWaitEvent(c->stream, c->ev_sten, 0);
+    c->geo_forked = false;
+  }
+  if (c->force_forked) {
+    cudaEventRecord(c->ev_force, c->sf);
+    cudaStreamWaitEvent(c->stream, c->ev_force, 0);
+    c->force_forked = false;
+  }
+}
+
+// Eq. 9-10: the force at the start of the step sets the body's acceleration; beside the stencils when the
+// classification forked them (both read only the tags, the state and the pose)
+static int enqueue_force(ibm_case *c) {
+  const bool f64 = c->precision == IBM_PREC_FP64;
+  if (c->geo_forked) {
+    cudaStreamWaitEvent(c->sf, c->ev_tags, 0);
+    launch_forces_f64(c->k, c->g, c->tag, c->A, !f64, c->ds, c->sf, true);
+    c->force_forked = true;
+  } else {
+    launch_forces_f64(c->k, c->g, c->tag, c->A, !f64, c->ds, c->stream, true);
+  }
+  return 1;
+}
+
+// Classification of the current pose.  defer_join: a case with a side stream
+// leaves its stencils running there (geo_forked) for the caller to overlap
+// with other pre-stage work and join (geometry_join) before the stages.
+static ibm_status do_classify(ibm_case *c, bool defer_join = false) {
   cudaStream_t s = c->stream;
   int nl = 0;
   prof_mark(c, 4, true);
   if (c->g.nv > 0 && c->g.nv <= FUSED_MAX_VERTS) {
     // pose + classification, tags / lists / tile lists, stencils: three kernels over the body's rectangle
     nl += launch_fused_geometry(c->k, c->g, c->solid, c->tag, c->st, c->cap, c->rst, c->sid, c->tile_body,
-                                c->body_tiles, c->body_cap, c->box_w, c->box_h, c->ds, c->blockcounts, s);
-    prof_mark(c, 4, false);
+                                c->body_tiles, c->body_cap, c->box_w, c->box_h, c->ds, c->blockcounts, s, c->sb,
+                                c->ev_tags);
+    c->geo_forked = c->sb != nullptr && c->cap > 0;
+    if (!defer_join) {
+      geometry_join(c);
+      prof_mark(c, 4, false);
+    }
     c->launches += nl;
     c->classified = true;
     CU(cudaGetLastError());
@@ -525,7 +573,7 @@ static ibm_status do_classify(ibm_case *c) {
     launch_tile_lists(c->k, c->tag, c->tile_body, c->body_tiles, c->body_cap, c->ds, c->g.nv > 0, s);
     nl += 2;
   }
-  prof_mark(c, 4, false);
+  if (!defer_join) prof_mark(c, 4, false);
   c->launches += nl;
   c->classified = true;
   CU(cudaGetLastError());
@@ -553,12 +601,21 @@ static bool persistent_step(const ibm_case *c) {
 static int enqueue_step(ibm_case *c) {
   cudaStream_t s = c->stream;
   int nl = 0;
+  // with a side stream the classification's stencils (and the force of a body under the fluid force) overlap
+  // the other pre-stage work; the profile's geometry group then spans all of it, up to the join
+  bool geo_open = false;
   if (!c->classified || c->k.motion.kind != IBM_MOTION_STATIC) {
     int before = (int)c->launches;
-    do_classify(c);
+    geo_open = c->sb != nullptr;
+    do_classify(c, geo_open);
     nl += (int)c->launches - before;
     c->launches = before;
   }
+  auto join = [&]() {
+    geometry_join(c);
+    if (geo_open) prof_mark(c, 4, false);
+    geo_open = false;
+  };
   if (c->k.dual) {
     // dual time: W^{n-1} <- W^n <- W, then sub-iterations of three pseudo stages at t + dt
     double *din[3] = {c->A, c->B, c->C};
@@ -567,16 +624,29 @@ static int enqueue_step(ibm_case *c) {
       // the time levels enter the pseudo stages only through the BDF part G, formed once per physical step
       launch_dual_levels(c->k, c->A, c->Wn, c->G, c->ds, s);
       nl += 1;
+      join();
       // FP32 residual of the mirror, FP64 point-implicit update; IB / ghost nodes rebuilt in the tile loads
       float *fin[3] = {c->M, c->F1, c->F2};
       float *fout[3] = {c->F1, c->F2, c->M};
+      // one launch per pseudo stage: the block-table kernel of the request loop with this case alone in the
+      // table (so that a case gives the same bits alone and in a group), TVD-2 its own kernel
+      StageBatch *one = nullptr;
+      if (c->stage_launch > 0 && !c->k.tvd2) {
+        StageCase sc;
+        case_stage_desc(c, &sc);
+        one = new StageBatch();
+        build_stage_batch(&sc, 1, one);
+      }
       for (int it = 0; it < c->k.subiters; it++)
         for (int st = 1; st <= 3; st++) {
           prof_mark(c, 0, true);
           if (c->stage_launch > 0) {  // one launch per pseudo stage (form 2: chained by programmatic launch)
-            launch_dual_f32_one(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->G, c->Q0,
-                                c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds,
-                                c->stage_launch == 2, s);
+            if (one)
+              launch_dual_f32_batch_one(*one, st, 0, c->stage_launch == 2, s);
+            else
+              launch_dual_f32_tvd(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->G,
+                                  c->Q0, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds,
+                                  c->stage_launch == 2, s);
             nl += 1;
           } else {
             cudaEventRecord(c->ev_fork, s);
@@ -589,9 +659,11 @@ static int enqueue_step(ibm_case *c) {
           }
           prof_mark(c, 0, false);
         }
+      delete one;
       launch_dual_end(c->k, c->ds, s);
       return nl + 1;
     }
+    join();
     const size_t bytes = 4 * (size_t)c->k.plane * sizeof(double);
     cudaMemcpyAsync(c->Wm, c->Wn, bytes, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(c->Wn, c->A, bytes, cudaMemcpyDeviceToDevice, s);
@@ -612,15 +684,15 @@ static int enqueue_step(ibm_case *c) {
   const bool fuse_cfl = fused_cfl(c);
   const bool coupled = c->k.motion.kind == IBM_MOTION_COUPLED;
   if (coupled) {  // Eq. 10: the force at the start of the step sets the body's acceleration for the step
-    prof_mark(c, 4, true);
-    launch_forces_f64(c->k, c->g, c->tag, c->A, !f64, c->ds, s, true);
-    prof_mark(c, 4, false);
-    nl += 1;
+    if (!geo_open) prof_mark(c, 4, true);
+    nl += enqueue_force(c);
+    if (!geo_open) prof_mark(c, 4, false);
   }
-  prof_mark(c, 3, true);
+  if (!geo_open) prof_mark(c, 3, true);
   if (f64) launch_dt(c->k, c->A, c->tag, c->ds, s, &nl);
   else if (!fuse_cfl) launch_dt_f32(c->k, c->M, c->tag, c->ds, s, &nl);
-  prof_mark(c, 3, false);
+  if (!geo_open) prof_mark(c, 3, false);
+  join();
   if (!f64 && persistent_step(c)) {
     // the three stages in one launch (the end of the step and the next dt included)
     if (!c->step_grid) c->step_grid = step_f32_grid(c->k, c->step_variant);
@@ -850,9 +922,11 @@ namespace ibm {
 
 // batched groups run the explicit stages only: dual time and bodies moving under the fluid force (whose
 // steps add the force and the body update) advance on their own streams
-bool case_batchable(const ibm_case *c) {
-  return c->precision == IBM_PREC_FP32_BULK && !c->k.dual && c->k.motion.kind != IBM_MOTION_COUPLED && !c->k.tvd2;
-}
+bool case_batchable(const ibm_case *c) { return c->precision == IBM_PREC_FP32_BULK && !c->k.tvd2; }
+
+int case_subiters(const ibm_case *c) { return c->k.dual ? c->k.subiters : 0; }
+
+bool case_coupled(const ibm_case *c) { return c->k.motion.kind == IBM_MOTION_COUPLED; }
 
 ibm_status case_prepare_batch(ibm_case *c) {
   if (!c->classified) {
@@ -871,19 +945,47 @@ ibm_status case_prepare_batch(ibm_case *c) {
 
 int case_enqueue_prestage(ibm_case *c) {
   int nl = 0;
+  bool geo_open = false;  // as in enqueue_step: the stencils (and force) overlap the rest, joined at the end
   if (c->k.motion.kind != IBM_MOTION_STATIC) {
     const long long before = c->launches;
-    do_classify(c);
+    geo_open = c->sb != nullptr;
+    do_classify(c, geo_open);
     nl += (int)(c->launches - before);
     c->launches = before;
   }
-  if (!fused_cfl(c)) launch_dt_f32(c->k, c->M, c->tag, c->ds, c->stream, &nl);
+  if (c->k.dual) {  // as in a dual-time step of the case alone: W^{n-1} <- W^n <- W and the BDF part
+    launch_dual_levels(c->k, c->A, c->Wn, c->G, c->ds, c->stream);
+    nl += 1;
+  } else {
+    if (c->k.motion.kind == IBM_MOTION_COUPLED) nl += enqueue_force(c);  // Eq. 10: the force at the step's start
+    if (!fused_cfl(c)) launch_dt_f32(c->k, c->M, c->tag, c->ds, c->stream, &nl);
+  }
+  geometry_join(c);
+  if (geo_open) prof_mark(c, 4, false);
   return nl;
+}
+
+int case_enqueue_poststage(ibm_case *c) {
+  if (c->k.dual) {
+    launch_dual_end(c->k, c->ds, c->stream);
+    return 1;
+  }
+  if (c->k.motion.kind == IBM_MOTION_COUPLED) {  // Eq. 10: position and velocity over the step
+    launch_body_end(c->ds, c->stream);
+    return 1;
+  }
+  return 0;
 }
 
 void case_stage_desc(const ibm_case *c, StageCase *out) {
   fill_stage_case(c->k, c->M, c->F1, c->F2, c->A, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap,
                   c->ds, fused_cfl(c), out);
+  if (c->k.dual) {
+    out->B = c->B;
+    out->C = c->C;
+    out->G = c->G;
+    out->Q0 = c->Q0;
+  }
 }
 
 cudaStream_t case_stream(const ibm_case *c) { return c->stream; }

@@ -21,31 +21,8 @@ __global__ void __launch_bounds__(256) k_dual_f32(Consts k, PertConsts c, const 
                                 (int)blockIdx.x, sm, dp);
 }
 
-// The same pseudo stage as one launch: body-tile slots [0, nb) first, then one
-// block per tile; with programmatic dependent launch its blocks are resident
-// while the previous pseudo stage's last blocks finish (they wait at the top
-// for it to complete).
-template <int STAGE>
-__global__ void __launch_bounds__(256) k_dual_f32_one(Consts k, PertConsts c, const float *__restrict__ In,
-                                                      float *Out32, double *D, const uint8_t *__restrict__ tag,
-                                                      const int *__restrict__ sid,
-                                                      const RStencil32 *__restrict__ rs,
-                                                      const uint8_t *__restrict__ tile_body,
-                                                      const int *__restrict__ body_tiles, int nb, DevState *ds,
-                                                      unsigned int ncfl, DualPtrs dp) {
-  __shared__ TileSmem sm;
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  const int b = (int)blockIdx.x;
-  if (b < nb)
-    stage_tile<STAGE, true, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body, body_tiles, ds, false, ncfl,
-                                  b, sm, dp);
-  else
-    stage_tile<STAGE, false, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body, body_tiles, ds, false,
-                                   ncfl, b - nb, sm, dp);
-}
-
-// the same with the TVD-2 reconstruction compiled in (every launch form of a TVD-2 case)
+// one launch of a TVD-2 case's pseudo stage: body-tile slots [0, nb) first, then one block per tile (every
+// launch form of a TVD-2 case)
 template <int STAGE>
 __global__ void __launch_bounds__(256) k_dual_f32_tvd(Consts k, PertConsts c, const float *__restrict__ In,
                                                       float *Out32, double *D, const uint8_t *__restrict__ tag,
@@ -66,7 +43,7 @@ __global__ void __launch_bounds__(256) k_dual_f32_tvd(Consts k, PertConsts c, co
                                                        body_tiles, ds, false, ncfl, b - nb, sm, dp);
 }
 
-cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, float *Out32, double *D,
+cudaError_t launch_dual_f32_tvd(const Consts &k, int stage, const float *In32, float *Out32, double *D,
                                 const double *In64, double *Out64, const double *G, double *Q0,
                                 const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                                 const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s) {
@@ -88,16 +65,68 @@ cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, f
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = pdl ? 1 : 0;
-#define IBM_DUAL_ONE(K, S) \
-  cudaLaunchKernelEx(&cfg, K<S>, k, c, In32, Out32, D, tag, sid, rs, tile_body, body_tiles, nb, ds, ncfl, dp)
-  const cudaError_t e = k.tvd2 ? (stage == 1   ? IBM_DUAL_ONE(k_dual_f32_tvd, 1)
-                                  : stage == 2 ? IBM_DUAL_ONE(k_dual_f32_tvd, 2)
-                                               : IBM_DUAL_ONE(k_dual_f32_tvd, 3))
-                               : (stage == 1   ? IBM_DUAL_ONE(k_dual_f32_one, 1)
-                                  : stage == 2 ? IBM_DUAL_ONE(k_dual_f32_one, 2)
-                                               : IBM_DUAL_ONE(k_dual_f32_one, 3));
-#undef IBM_DUAL_ONE
+#define IBM_DUAL_TVD(S) \
+  cudaLaunchKernelEx(&cfg, k_dual_f32_tvd<S>, k, c, In32, Out32, D, tag, sid, rs, tile_body, body_tiles, nb, ds, ncfl, dp)
+  const cudaError_t e = stage == 1 ? IBM_DUAL_TVD(1) : stage == 2 ? IBM_DUAL_TVD(2) : IBM_DUAL_TVD(3);
+#undef IBM_DUAL_TVD
   return e;
+}
+
+// Dual-time pseudo stage over a block table: per entry the per-tile code --
+// FP32 residual of the mirror, FP64 point-implicit update -- of the case the
+// entry falls in, with its stage arrays and FP64 iterates rotated over the
+// three pseudo stages (mirror -> F1 -> F2 -> mirror, D -> B -> C -> D).
+// Body-tile entries of every case first.  A case alone runs it with a table
+// of one entry (one block per tile), a group of dual-time cases with the
+// group's table, so a case's results are the same bits alone and in a group.
+// With programmatic dependent launch its blocks are resident while the
+// previous pseudo stage's last blocks finish (they wait at the top for it to
+// complete).
+template <int STAGE>
+__global__ void __launch_bounds__(256, 4) k_dual_f32_batch_one(const __grid_constant__ StageBatch b) {
+  __shared__ TileSmem sm;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int nbody = b.body_start[b.n], total = nbody + b.plain_start[b.n];
+  for (int e = blockIdx.x; e < total; e += gridDim.x) {
+    const bool body = e < nbody;
+    const int *start = body ? b.body_start : b.plain_start;
+    const int ee = body ? e : e - nbody;
+    int q = 0;
+    while (q + 1 < b.n && start[q + 1] <= ee) q++;
+    const StageCase &sc = b.cs[q];
+    const float *In = STAGE == 1 ? sc.M : (STAGE == 2 ? sc.F1 : sc.F2);
+    float *Out = STAGE == 1 ? sc.F1 : (STAGE == 2 ? sc.F2 : sc.M);
+    DualPtrs dp;
+    dp.In64 = STAGE == 1 ? sc.D : (STAGE == 2 ? sc.B : sc.C);
+    dp.Out64 = STAGE == 1 ? sc.B : (STAGE == 2 ? sc.C : sc.D);
+    dp.G = sc.G;
+    dp.Q0 = sc.Q0;
+    if (body)
+      stage_tile<STAGE, true, true>(sc.k, sc.c, nullptr, In, Out, sc.D, sc.tag, sc.sid, sc.rs, sc.tile_body,
+                                    sc.body_tiles, sc.ds, false, sc.ncfl, ee - start[q], sm, dp);
+    else
+      stage_tile<STAGE, false, true>(sc.k, sc.c, nullptr, In, Out, sc.D, sc.tag, sc.sid, sc.rs, sc.tile_body,
+                                     sc.body_tiles, sc.ds, false, sc.ncfl, ee - start[q], sm, dp);
+    __syncthreads();  // shared memory is reused by the next entry
+  }
+}
+
+cudaError_t launch_dual_f32_batch_one(const StageBatch &b, int stage, int grid, bool pdl, cudaStream_t s) {
+  const int total = b.body_start[b.n] + b.plain_start[b.n];
+  if (total == 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned int)(grid > 0 && grid < total ? grid : total));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  if (stage == 1) return cudaLaunchKernelEx(&cfg, k_dual_f32_batch_one<1>, b);
+  if (stage == 2) return cudaLaunchKernelEx(&cfg, k_dual_f32_batch_one<2>, b);
+  return cudaLaunchKernelEx(&cfg, k_dual_f32_batch_one<3>, b);
 }
 
 // Start of a physical step: one thread per FP64 word of the 4-plane state.
@@ -121,7 +150,7 @@ void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
                      DevState *ds, cudaStream_t s, cudaStream_t sb) {
   if (k.tvd2) {  // the TVD-2 kernel holds plain and body tiles: one launch on the case stream
-    launch_dual_f32_one(k, stage, In32, Out32, D, In64, Out64, G, Q0, tag, sid, rs, tile_body, body_tiles, body_cap,
+    launch_dual_f32_tvd(k, stage, In32, Out32, D, In64, Out64, G, Q0, tag, sid, rs, tile_body, body_tiles, body_cap,
                         ds, false, s);
     return;
   }

@@ -421,6 +421,151 @@ __device__ __forceinline__ int warp_argmin(double v, int idx) {
   return src;
 }
 
+// Sec. 4.1: the point of segment kk nearest (px, py) -- a vertex (region VERTEX, feature the vertex) or the
+// foot point (region FACE, feature the segment) -- and its squared distance
+__device__ __forceinline__ double seg_closest(const Geom &g, int kk, double px, double py, double *cxo, double *cyo,
+                                              int *fo, int *ro) {
+  const int k1 = (kk + 1 == g.nv) ? 0 : kk + 1;
+  const double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
+  const double ex = bx - ax, ey = by - ay;
+  const double wx = px - ax, wy = py - ay;
+  const double num = wx * ex + wy * ey;
+  const double den = ex * ex + ey * ey;
+  double cx, cy;
+  if (num <= 0.0) {
+    cx = ax; cy = ay; *fo = kk; *ro = IBM_REGION_VERTEX;
+  } else if (num >= den) {
+    cx = bx; cy = by; *fo = k1; *ro = IBM_REGION_VERTEX;
+  } else {
+    const double t = num / den;
+    cx = ax + t * ex; cy = ay + t * ey; *fo = kk; *ro = IBM_REGION_FACE;
+  }
+  *cxo = cx;
+  *cyo = cy;
+  const double ddx = px - cx, ddy = py - cy;
+  return ddx * ddx + ddy * ddy;
+}
+
+// Sec. 4.3: crossing of the line through (px, py) along (nx, ny) with segment kk, at parameter u on the
+// segment and signed distance sv along the normal, on the side the node's kind allows (a ghost node, inside
+// the body, finds the wall along the normal, sv >= 0; an IB node, in the fluid, against it, sv <= 0); false if
+// there is none
+__device__ __forceinline__ bool seg_crossing(const Geom &g, int kk, double px, double py, double nx, double ny,
+                                             bool ghost, double *uo, double *svo) {
+  const int k1 = (kk + 1 == g.nv) ? 0 : kk + 1;
+  const double ax = g.vx[kk], ay = g.vy[kk];
+  const double ex = g.vx[k1] - ax, ey = g.vy[k1] - ay;
+  const double den = ex * ny - ey * nx;
+  if (den == 0.0) return false;
+  const double wx = px - ax, wy = py - ay;
+  const double u = (wx * ny - wy * nx) / den;
+  if (u < 0.0 || u > 1.0) return false;
+  const double sv = (wx * ey - wy * ex) / den;
+  if (ghost ? (sv < 0.0) : (sv > 0.0)) return false;
+  *uo = u;
+  *svo = sv;
+  return true;
+}
+
+// The rest of one node's stencil once the closest feature (feat, region, foot point cc) and the boundary point
+// search (found_abs < inf: signed distance bsv at parameter bsu on segment bsg) are known: boundary point,
+// image / probe distance, interpolation square (Sec. 4.3-4.6), curvature at P' (Eq. 7); writes the record,
+// and with rs its compact FP32 form and the cell -> stencil map.
+__device__ __forceinline__ void stencil_tail(const Consts &k, const Geom &g, const uint8_t *__restrict__ tag,
+                                             DevState *ds, const ibm_stencil &s0, int e, double px, double py,
+                                             int feat, int region, double ccx, double ccy, double found_abs,
+                                             double bsv, double bsu, int bsg, double nx, double ny,
+                                             ibm_stencil *__restrict__ st, RStencil32 *__restrict__ rs,
+                                             int *__restrict__ sid) {
+  const int kind = s0.kind;
+  const bool ghost = kind > 0;
+  const int nv = g.nv;
+  ibm_stencil s = s0;
+  double bx, by, xi_node;
+  int fb;
+  if (found_abs < INFINITY) {
+    bx = px + bsv * nx;
+    by = py + bsv * ny;
+    xi_node = -bsv;
+    fb = 0;
+  } else {
+    const double ddx = px - ccx, ddy = py - ccy;
+    const double d = sqrt(ddx * ddx + ddy * ddy);
+    bx = ccx;
+    by = ccy;
+    xi_node = ghost ? -d : d;
+    fb = 1;
+  }
+  double xi_probe;
+  if (kind == 0) {
+    xi_probe = xi_node + k.h;
+  } else {
+    xi_probe = -xi_node;
+    if (xi_probe < 0.5 * k.dmin) xi_probe = 0.5 * k.dmin;
+  }
+  const unsigned allowed = kind == 0 ? ALLOW_FLUID : ALLOW_FLUID_IB;
+  int i0 = 0, j0 = 0, mask = 0, nstep = 0;
+  double w[4];
+  for (;;) {
+    double X = bx + xi_probe * nx, Y = by + xi_probe * ny;
+    mask = interp_square(k, tag, X, Y, allowed, &i0, &j0, w);
+    if (mask != 0 || nstep == 3) break;
+    xi_probe = xi_probe + k.dmin;
+    nstep++;
+  }
+  if (mask == 0) atomicOr(&ds->err, ERR_STENCIL);
+  // curvature at P' (Eq. 7): linear between the end-vertex curvatures of the segment holding P', or the
+  // vertex curvature when P' falls back to a closest vertex
+  double curv;
+  if (fb && region == IBM_REGION_VERTEX) {
+    curv = g.vk[feat];
+  } else {
+    int sg = bsg;
+    double uu = bsu;
+    if (fb) {  // P' is the foot point on segment feat
+      const int f1 = (feat + 1 == nv) ? 0 : feat + 1;
+      const double ex = g.vx[f1] - g.vx[feat], ey = g.vy[f1] - g.vy[feat];
+      sg = feat;
+      uu = ((ccx - g.vx[feat]) * ex + (ccy - g.vy[feat]) * ey) / (ex * ex + ey * ey);
+    }
+    const int s1 = (sg + 1 == nv) ? 0 : sg + 1;
+    curv = (1.0 - uu) * g.vk[sg] + uu * g.vk[s1];
+  }
+  s.curv = curv;
+  s.feature = feat;
+  s.region = fb ? IBM_REGION_FALLBACK : region;
+  s.i0 = i0;
+  s.j0 = j0;
+  s.mask = mask;
+  s.nstep = nstep;
+  s.nx = nx;
+  s.ny = ny;
+  s.bx = bx;
+  s.by = by;
+  s.xi_node = xi_node;
+  s.xi_probe = xi_probe;
+  for (int q = 0; q < 4; q++) s.w[q] = w[q];
+  st[e] = s;
+  if (rs) {
+    RStencil32 r;
+    r.cell = (int)cidx(k, s.cell % k.nx, s.cell / k.nx);
+    r.corner = s.mask ? (int)cidx(k, s.i0, s.j0) : 0;
+    r.ccell = s.mask ? s.j0 * k.nx + s.i0 : 0;
+    r.mask = s.mask | (s.kind == 0 ? 16 : 0);  // bit 4: IB node
+    r.ratio = (float)(s.xi_node / s.xi_probe);
+    r.dxi = (float)(s.xi_probe - s.xi_node);
+    r.nx = (float)s.nx;
+    r.ny = (float)s.ny;
+    for (int q = 0; q < 4; q++) r.w[q] = (float)s.w[q];
+    r.curv = (float)s.curv;
+    const bool pitching = k.motion.kind == IBM_MOTION_PITCH;  // P' relative to the pivot (wall motion)
+    r.rx = pitching ? (float)(s.bx - k.motion.pivot[0]) : 0.f;
+    r.ry = pitching ? (float)(s.by - k.motion.pivot[1]) : 0.f;
+    rs[e] = r;
+    sid[s.cell] = e;
+  }
+}
+
 // Sec. 4.1-4.6, Sec. 5: one stencil per listed node, one warp per node (four
 // per 128-thread block, blocks striding over the list).  The lanes split the
 // segments of the two searches (closest feature, boundary point); the warp
@@ -438,6 +583,7 @@ __device__ __forceinline__ int warp_argmin(double v, int idx) {
 // the exact FP64 tests on the others only, so the result is the exhaustive
 // search's, bit for bit.
 constexpr int STENCIL_PRUNE_MAX = 2048;
+
 __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_t *__restrict__ tag,
                                                   ibm_stencil *__restrict__ st, int cap, DevState *ds,
                                                   RStencil32 *__restrict__ rs, int *__restrict__ sid) {
@@ -484,24 +630,9 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
         const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
         if (sqrtf(dx * dx + dy * dy) - s_sb[3 * kk + 2] > ub) continue;
       }
-      const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
-      const double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
-      const double ex = bx - ax, ey = by - ay;
-      const double wx = px - ax, wy = py - ay;
-      const double num = wx * ex + wy * ey;
-      const double den = ex * ex + ey * ey;
       double cx, cy;
       int f, r;
-      if (num <= 0.0) {
-        cx = ax; cy = ay; f = kk; r = IBM_REGION_VERTEX;
-      } else if (num >= den) {
-        cx = bx; cy = by; f = k1; r = IBM_REGION_VERTEX;
-      } else {
-        const double t = num / den;
-        cx = ax + t * ex; cy = ay + t * ey; f = kk; r = IBM_REGION_FACE;
-      }
-      const double ddx = px - cx, ddy = py - cy;
-      const double d2 = ddx * ddx + ddy * ddy;
+      const double d2 = seg_closest(g, kk, px, py, &cx, &cy, &f, &r);
       if (d2 < best) {
         best = d2; bseg = kk; bfeat = f; breg = r; bcx = cx; bcy = cy;
       }
@@ -537,16 +668,8 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
           const float lb = sqrtf(dx * dx + dy * dy) - s_sb[3 * kk + 2];
           if (pass == 0 ? lb > ub : (lb <= ub || lb > bound)) continue;
         }
-        const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
-        const double ax = g.vx[kk], ay = g.vy[kk];
-        const double ex = g.vx[k1] - ax, ey = g.vy[k1] - ay;
-        const double den = ex * ny - ey * nx;
-        if (den == 0.0) continue;
-        const double wx = px - ax, wy = py - ay;
-        const double u = (wx * ny - wy * nx) / den;
-        if (u < 0.0 || u > 1.0) continue;
-        const double sv = (wx * ey - wy * ex) / den;
-        if (ghost ? (sv < 0.0) : (sv > 0.0)) continue;
+        double u, sv;
+        if (!seg_crossing(g, kk, px, py, nx, ny, ghost, &u, &sv)) continue;
         const double as = fabs(sv);
         if (as < bs_best || (as == bs_best && kk < bs_seg)) {
           bs_best = as; bs_s = sv; bs_u = u; bs_seg = kk;
@@ -558,94 +681,19 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
     const double bsv = __shfl_sync(0xffffffffu, bs_s, win);
     const double bsu = __shfl_sync(0xffffffffu, bs_u, win);
     const int bsg = __shfl_sync(0xffffffffu, bs_seg, win);
-    if (lane == 0) {
-      ibm_stencil s = s0;
-      double bx, by, xi_node;
-      int fb;
-      if (found_abs < INFINITY) {
-        bx = px + bsv * nx;
-        by = py + bsv * ny;
-        xi_node = -bsv;
-        fb = 0;
-      } else {
-        const double ddx = px - ccx, ddy = py - ccy;
-        const double d = sqrt(ddx * ddx + ddy * ddy);
-        bx = ccx;
-        by = ccy;
-        xi_node = ghost ? -d : d;
-        fb = 1;
-      }
-      double xi_probe;
-      if (kind == 0) {
-        xi_probe = xi_node + k.h;
-      } else {
-        xi_probe = -xi_node;
-        if (xi_probe < 0.5 * k.dmin) xi_probe = 0.5 * k.dmin;
-      }
-      const unsigned allowed = kind == 0 ? ALLOW_FLUID : ALLOW_FLUID_IB;
-      int i0 = 0, j0 = 0, mask = 0, nstep = 0;
-      double w[4];
-      for (;;) {
-        double X = bx + xi_probe * nx, Y = by + xi_probe * ny;
-        mask = interp_square(k, tag, X, Y, allowed, &i0, &j0, w);
-        if (mask != 0 || nstep == 3) break;
-        xi_probe = xi_probe + k.dmin;
-        nstep++;
-      }
-      if (mask == 0) atomicOr(&ds->err, ERR_STENCIL);
-      // curvature at P' (Eq. 7): linear between the end-vertex curvatures of the segment holding P', or the
-      // vertex curvature when P' falls back to a closest vertex
-      double curv;
-      if (fb && region == IBM_REGION_VERTEX) {
-        curv = g.vk[feat];
-      } else {
-        int sg = bsg;
-        double uu = bsu;
-        if (fb) {  // P' is the foot point on segment feat
-          const int f1 = (feat + 1 == nv) ? 0 : feat + 1;
-          const double ex = g.vx[f1] - g.vx[feat], ey = g.vy[f1] - g.vy[feat];
-          sg = feat;
-          uu = ((ccx - g.vx[feat]) * ex + (ccy - g.vy[feat]) * ey) / (ex * ex + ey * ey);
-        }
-        const int s1 = (sg + 1 == nv) ? 0 : sg + 1;
-        curv = (1.0 - uu) * g.vk[sg] + uu * g.vk[s1];
-      }
-      s.curv = curv;
-      s.feature = feat;
-      s.region = fb ? IBM_REGION_FALLBACK : region;
-      s.i0 = i0;
-      s.j0 = j0;
-      s.mask = mask;
-      s.nstep = nstep;
-      s.nx = nx;
-      s.ny = ny;
-      s.bx = bx;
-      s.by = by;
-      s.xi_node = xi_node;
-      s.xi_probe = xi_probe;
-      for (int q = 0; q < 4; q++) s.w[q] = w[q];
-      st[e] = s;
-      if (rs) {
-        RStencil32 r;
-        r.cell = (int)cidx(k, s.cell % k.nx, s.cell / k.nx);
-        r.corner = s.mask ? (int)cidx(k, s.i0, s.j0) : 0;
-        r.ccell = s.mask ? s.j0 * k.nx + s.i0 : 0;
-        r.mask = s.mask | (s.kind == 0 ? 16 : 0);  // bit 4: IB node
-        r.ratio = (float)(s.xi_node / s.xi_probe);
-        r.dxi = (float)(s.xi_probe - s.xi_node);
-        r.nx = (float)s.nx;
-        r.ny = (float)s.ny;
-        for (int q = 0; q < 4; q++) r.w[q] = (float)s.w[q];
-        r.curv = (float)s.curv;
-        const bool pitching = k.motion.kind == IBM_MOTION_PITCH;  // P' relative to the pivot (wall motion)
-        r.rx = pitching ? (float)(s.bx - k.motion.pivot[0]) : 0.f;
-        r.ry = pitching ? (float)(s.by - k.motion.pivot[1]) : 0.f;
-        rs[e] = r;
-        sid[s.cell] = e;
-      }
-    }
+    if (lane == 0)
+      stencil_tail(k, g, tag, ds, s0, e, px, py, feat, region, ccx, ccy, found_abs, bsv, bsu, bsg, nx, ny, st,
+                   rs, sid);
     __syncwarp();
   }
+}
+
+// stencils of the listed nodes: one warp per node, four per block, blocks striding over the list
+static void launch_stencil_kernel(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap,
+                                  DevState *ds, RStencil32 *rs, int *sid, cudaStream_t s) {
+  if (cap <= 0) return;
+  k_stencils<<<(unsigned)min((cap + 3) / 4, 8 * 152), 128,
+               g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(k, g, tag, st, cap, ds, rs, sid);
 }
 
 // ---------------------------------------------------------------------------
@@ -1120,7 +1168,8 @@ void prepare_geometry_kernels() {
 
 int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_t *tag, ibm_stencil *st, int cap,
                           RStencil32 *rs, int *sid, uint8_t *tile_body, int *body_tiles, int body_cap, int maxw,
-                          int maxh, DevState *ds, int *blockcounts, cudaStream_t s) {
+                          int maxh, DevState *ds, int *blockcounts, cudaStream_t s, cudaStream_t ss,
+                          cudaEvent_t ev_tags) {
   // one warp per row of the classification rectangle (at most the body's pose-independent height, the previous
   // rectangle's and the margins)
   const long long warps = 2LL * (maxh + 8);
@@ -1131,7 +1180,8 @@ int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_
   const long long want = (long long)(maxw + 24) * (maxh + 24);
   const int staged_cap = (int)std::min<long long>(want, STAGED_CELLS_MAX);
   int nl = 2;
-  if ((long long)maxw * maxh > LARGE_RECT && blockcounts) {
+  const bool large = (long long)maxw * maxh > LARGE_RECT && blockcounts;
+  if (large) {
     // one block per chunk of the grid's size (the block counts are sized for it), so that any rectangle is
     // covered; blocks past the rectangle exit at once
     const int nchunk = (int)(((long long)k.nx * k.ny + TAG_BLOCK - 1) / TAG_BLOCK);
@@ -1139,27 +1189,32 @@ int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_
     k_scan_blocks<<<1, 1024, 0, s>>>(nchunk, blockcounts, ds, cap);
     k_rect_scatter<<<nchunk, TAG_BLOCK, 0, s>>>(k, tag, blockcounts, ds, st, cap);
     nl += 2;
-    if (tile_body) {
-      launch_tile_lists(k, tag, tile_body, body_tiles, body_cap, ds, true, s);
-      nl += 2;
-    }
   } else {
     k_tags_lists<<<1, 1024, 2 * (size_t)staged_cap, s>>>(k, solid, tag, sid, st, cap, tile_body, body_tiles,
                                                          body_cap, ds, staged_cap);
   }
+  // the stencils need the tags and the ordered list only: with a side stream they run there, beside the tile
+  // lists (and whatever the caller enqueues next on s until it joins ss)
+  cudaStream_t sst = s;
+  if (ss && ev_tags && cap > 0) {
+    cudaEventRecord(ev_tags, s);
+    cudaStreamWaitEvent(ss, ev_tags, 0);
+    sst = ss;
+  }
   if (cap > 0) {
-    k_stencils<<<(unsigned)min((cap + 3) / 4, 8 * 152), 128,
-                 g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(k, g, tag, st, cap, ds, rs, sid);
+    launch_stencil_kernel(k, g, tag, st, cap, ds, rs, sid, sst);
     nl++;
+  }
+  if (large && tile_body) {
+    launch_tile_lists(k, tag, tile_body, body_tiles, body_cap, ds, true, s);
+    nl += 2;
   }
   return nl;
 }
 
 void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap, DevState *ds,
                      cudaStream_t s) {
-  if (cap <= 0) return;
-  k_stencils<<<(unsigned)min((cap + 3) / 4, 8 * 152), 128,
-               g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(k, g, tag, st, cap, ds, nullptr, nullptr);
+  launch_stencil_kernel(k, g, tag, st, cap, ds, nullptr, nullptr, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1173,7 +1228,7 @@ void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_ste
 // Eq. 9 over the body's segments: up to FORCE_BLOCKS blocks of FORCE_THREADS threads, one segment per thread
 // (blocks stride over longer bodies); each block sums its segments in a fixed tree order into a partial, and
 // the last block to finish adds the partials in block order, so the sum is deterministic
-constexpr int FORCE_THREADS = 64, FORCE_BLOCKS = 64;
+constexpr int FORCE_THREADS = 32, FORCE_BLOCKS = 64;
 __global__ void __launch_bounds__(FORCE_THREADS) k_forces_f64(Consts k, Geom g, const uint8_t *__restrict__ tag,
                                                               const double *__restrict__ A, bool pert, DevState *ds,
                                                               bool set_accel, double *__restrict__ surf) {

@@ -255,10 +255,13 @@ void prepare_geometry_kernels();
 // untagged and unlisted (solid, tag and sid are cleared at creation).  Same
 // results as the unrestricted kernels.  Returns the kernels launched.
 constexpr int FUSED_MAX_VERTS = 1024;
-// blockcounts: 4 ints per TAG_BLOCK cells of the grid (the multi-block lists of large bodies)
+// blockcounts: 4 ints per TAG_BLOCK cells of the grid (the multi-block lists of large bodies).  ss (with
+// ev_tags): a side stream for the stencils, forked from s once the tags and lists are enqueued; the caller
+// joins it to s before anything reads the stencils (null: everything on s).
 int launch_fused_geometry(const Consts &k, const Geom &g, uint8_t *solid, uint8_t *tag, ibm_stencil *st, int cap,
                           RStencil32 *rs, int *sid, uint8_t *tile_body, int *body_tiles, int body_cap, int maxw,
-                          int maxh, DevState *ds, int *blockcounts, cudaStream_t s);
+                          int maxh, DevState *ds, int *blockcounts, cudaStream_t s, cudaStream_t ss = nullptr,
+                          cudaEvent_t ev_tags = nullptr);
 // A: FP64 state, absolute conserved (pert = false) or perturbation (pert = true)
 void launch_body_end(DevState *ds, cudaStream_t s);
 // surf (optional): per segment the pressure and skin-friction coefficients, surf[e] and surf[nv + e]
@@ -405,9 +408,10 @@ cudaError_t check_float_conversions(unsigned long long *checked, unsigned long l
 // (BDF2), or G = -W^n / dt on the first step (BDF1), over the whole padded
 // state (4 planes).
 void launch_dual_levels(const Consts &k, const double *A, double *Wn, double *G, const DevState *ds, cudaStream_t s);
-// The same pseudo stage as one launch on stream s (body-tile slots first);
-// pdl: chained to the previous launch by programmatic dependent launch.
-cudaError_t launch_dual_f32_one(const Consts &k, int stage, const float *In32, float *Out32, double *D,
+// The same pseudo stage of a TVD-2 case as one launch on stream s (body-tile
+// slots first); pdl: chained to the previous launch by programmatic dependent
+// launch.  (Other cases take launch_dual_f32_batch_one with a table of one.)
+cudaError_t launch_dual_f32_tvd(const Consts &k, int stage, const float *In32, float *Out32, double *D,
                                 const double *In64, double *Out64, const double *G, double *Q0,
                                 const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                                 const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s);
@@ -428,6 +432,11 @@ struct StageCase {
   int nt, nb;          // stage tiles, body-tile slots
   int fuse_cfl;
   unsigned int ncfl;   // blocks of the fused CFL reduction (nt + nb)
+  // dual time only (null otherwise): the FP64 pseudo-stage iterates (D -> B -> C -> D), the BDF part of the
+  // physical step and the sub-iteration's start primitives
+  double *B, *C;
+  const double *G;
+  double *Q0;
 };
 
 // Block table of a batched stage launch over the member cases of a group,
@@ -453,18 +462,34 @@ void fill_stage_case(const Consts &k, float *M, float *F1, float *F2, double *D,
 // entries: one block per entry; fewer: persistent blocks striding over the
 // table); pdl: chained to the previous launch by programmatic dependent launch.
 cudaError_t launch_stage_f32_batch_one(const StageBatch &b, int stage, int grid, bool pdl, cudaStream_t s);
+// Dual-time pseudo stage `stage` of every (dual-time, not TVD-2) case of the
+// table as one launch over the combined table, with the same grid and pdl
+// meanings: the one-launch form of a dual-time case alone (a table of one) and
+// of a group of them.
+cudaError_t launch_dual_f32_batch_one(const StageBatch &b, int stage, int grid, bool pdl, cudaStream_t s);
 
 // ---- batching support (capi.cu), used by the request loop (serve.cu) ----
-// FP32-bulk explicit RK3 cases advance through batched stage launches.
+// FP32-bulk cases (explicit RK3 with any motion, or dual time) advance through
+// batched stage launches.
 bool case_batchable(const ibm_case *c);
+// sub-iterations per physical step of a dual-time case (0: explicit RK3)
+int case_subiters(const ibm_case *c);
+// the case's body moves under the fluid force (Eq. 10)
+bool case_coupled(const ibm_case *c);
 // Work that must precede batched steps, on the case stream: the first
 // classification and, for the fused CFL rule, the first dt (as ibm_step does
 // outside its graph).
 ibm_status case_prepare_batch(ibm_case *c);
 // Per-step work before the stages, on the case stream: re-classification and
-// stencils of a moving body, and dt unless stage 3 provides it.  Returns the
-// kernels enqueued (0: nothing to do).  Graph-capturable.
+// stencils of a moving body; for a body under the fluid force, the force and
+// the body's acceleration (Eq. 10); dt unless stage 3 provides it; for dual
+// time, the rotation of the time levels.  Returns the kernels enqueued (0:
+// nothing to do).  Graph-capturable.
 int case_enqueue_prestage(ibm_case *c);
+// Per-step work after the stages, on the case stream: the body update of
+// Eq. 10, or the end of a dual-time physical step.  Returns the kernels
+// enqueued.  Graph-capturable.
+int case_enqueue_poststage(ibm_case *c);
 void case_stage_desc(const ibm_case *c, StageCase *out);
 cudaStream_t case_stream(const ibm_case *c);
 void case_add_launches(ibm_case *c, long long n);

@@ -5,23 +5,25 @@
 // and are admitted while a slot and enough device memory are free; each
 // admitted case owns its device state, tags and lists.
 //
-// Batched mode (default) for FP32-bulk explicit RK3 cases: the requests
-// admitted in one pass of the loop form groups of cases of similar size (grids
-// within a factor four in cells) and equal step counts, up to MAX_BATCH cases
-// per group.  One step of a group is one CUDA graph: the per-case work that
-// precedes the stages (re-classification and stencils of moving bodies, dt)
-// forked onto the cases' own streams, then per RK stage ONE launch of the
-// plain-tile kernel and one of the body-tile kernel over the block table of all
-// member cases.  A group's membership is fixed when it forms, so its graph is
+// Batched mode (default) for FP32-bulk cases: the requests admitted in one
+// pass of the loop form groups of cases of similar size (grids within a factor
+// four in cells), equal step counts and the same time scheme (explicit RK3, or
+// dual time with equal sub-iteration counts), up to MAX_BATCH cases per group.
+// One step of a group is one CUDA graph: the per-case work that precedes the
+// stages (re-classification and stencils of moving bodies, the force and
+// acceleration of a body under the fluid force, dt, or the rotation of a
+// dual-time case's time levels) forked onto the cases' own streams, then per
+// RK stage (per pseudo stage of every sub-iteration) ONE launch over the block
+// table of all member cases, then the per-case work that ends the step (the
+// body update of Eq. 10, the end of a dual-time step), forked likewise.  A group's membership is fixed when it forms, so its graph is
 // captured once and its members finish together; requests that arrive later
 // form new groups, which run beside the old ones on their own streams.  A small
 // autotuner picks the plain-tile launch's schedule (one block per table entry,
 // or a persistent grid striding over the table) by timing the candidates on
 // the group itself, once per size class and membership size.
 //
-// Other cases (FP64, dual time, bodies moving under the fluid force), and every
-// case when batching is off, advance
-// on their own streams in chunks of steps replayed from their own graphs.
+// Other cases (FP64, TVD-2), and every case when batching is off, advance on
+// their own streams in chunks of steps replayed from their own graphs.
 //
 // A case that has taken all its steps is retired: its forces and time are
 // read, its memory freed, and the next waiting request can take the slot.
@@ -39,6 +41,7 @@
 #include <deque>
 #include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "ibm_internal.cuh"
@@ -72,10 +75,13 @@ struct Active {
   int launched = 0;            // steps enqueued so far
   Group *group = nullptr;
   bool prestage = false;       // has per-step work before the stages
+  bool poststage = false;      // has per-step work after the stages
 };
 
 struct Group {
   int bucket = 0;
+  int subiters = 0;  // dual-time sub-iterations per physical step (0: explicit RK3)
+  bool coupled = false;  // a member's body moves under the fluid force
   std::vector<Active *> members;
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
@@ -269,9 +275,30 @@ static ibm_status capture_group(ibm_server *s, Group *g) {
     }
   }
   // one launch per stage over the combined table, stages chained by programmatic launch
-  for (int st = 1; st <= 3; st++) {
-    launch_stage_f32_batch_one(b, st, g->plain_grid, true, g->s);
-    nk += (b.plain_start[b.n] + b.body_start[b.n] > 0);
+  const bool nonempty = b.plain_start[b.n] + b.body_start[b.n] > 0;
+  if (g->subiters > 0) {
+    for (int it = 0; it < g->subiters; it++)
+      for (int st = 1; st <= 3; st++) {
+        launch_dual_f32_batch_one(b, st, g->plain_grid, true, g->s);
+        nk += nonempty;
+      }
+  } else {
+    for (int st = 1; st <= 3; st++) {
+      launch_stage_f32_batch_one(b, st, g->plain_grid, true, g->s);
+      nk += nonempty;
+    }
+  }
+  bool any_post = false;
+  for (Active *a : g->members) any_post |= a->poststage;
+  if (any_post) {
+    cudaEventRecord(g->fork, g->s);
+    for (Active *a : g->members) {
+      if (!a->poststage) continue;
+      cudaStreamWaitEvent(a->stream, g->fork, 0);
+      nk += case_enqueue_poststage(a->c);
+      cudaEventRecord(a->join, a->stream);
+      cudaStreamWaitEvent(g->s, a->join, 0);
+    }
   }
   cudaError_t e = cudaStreamEndCapture(g->s, &graph);
   if (e == cudaSuccess && g->graph) {
@@ -301,8 +328,15 @@ static ibm_status capture_group(ibm_server *s, Group *g) {
 // size.  Between steps stage 1 is free of side effects on the solution: it
 // reads the mirror of U^n and writes the stage-1 array, the stage times and
 // U^n on IB / ghost nodes, all of which the next step's stage 1 rewrites with
-// the same values.
+// the same values.  Groups whose step reads those IB / ghost values before
+// stage 1 rewrites them (the force of a body under the fluid force) and
+// dual-time groups (a pseudo stage updates the FP64 iterates) keep one block
+// per table entry and are not timed.
 static void autotune(ibm_server *s, Group *g) {
+  if (g->subiters > 0 || g->coupled) {
+    g->plain_grid = 0;
+    return;
+  }
   int mclass = 0;
   while ((2 << mclass) <= (int)g->members.size()) mclass++;
   const int key = g->bucket * 16 + mclass;
@@ -362,7 +396,7 @@ extern "C" ibm_status ibm_server_progress(ibm_server *s, int *n_active, int *n_p
   // 2. admit waiting requests, in arrival order, while a slot and memory are free.  Batchable requests
   // admitted in this pass form new groups by (size class, steps): a group's membership is fixed when it
   // is formed, so its step graph is captured once and all its members finish together.
-  std::map<long long, Group *> forming;
+  std::map<std::tuple<int, int, int>, Group *> forming;
   while (!s->pending.empty() && (int)s->active.size() < s->max_active &&
          s->used + s->pending.front()->bytes <= s->budget) {
     Request *r = s->pending.front();
@@ -379,12 +413,13 @@ extern "C" ibm_status ibm_server_progress(ibm_server *s, int *n_active, int *n_p
     if (st == IBM_OK) st = batched ? case_prepare_batch(a->c) : ibm_classify(a->c);
     Group *g = nullptr;
     if (st == IBM_OK && batched) {
-      const long long key = (long long)bucket_of(r) << 32 | (long long)r->nsteps;
+      const auto key = std::make_tuple(bucket_of(r), case_subiters(a->c), r->nsteps);
       auto it = forming.find(key);
       if (it != forming.end() && (int)it->second->members.size() < MAX_BATCH) g = it->second;
       if (!g) {
         g = group_create(bucket_of(r));
         if (g) {
+          g->subiters = case_subiters(a->c);
           s->groups.push_back(g);
           forming[key] = g;
         } else {
@@ -414,9 +449,12 @@ extern "C" ibm_status ibm_server_progress(ibm_server *s, int *n_active, int *n_p
     if (g) {
       // the group's next step starts after the case's set-up work
       a->group = g;
-      // a moving body is re-classified and its dt reduced before the stages of every step; a static body's dt
-      // comes from stage 3 (or is fixed)
-      a->prestage = r->motion.kind != IBM_MOTION_STATIC;
+      // a moving body is re-classified and its dt reduced before the stages of every step (a body under the
+      // fluid force also takes the force first and is moved after them); a static body's dt comes from
+      // stage 3 (or is fixed); a dual-time step rotates the time levels first and advances t after them
+      a->prestage = r->motion.kind != IBM_MOTION_STATIC || g->subiters > 0;
+      a->poststage = case_coupled(a->c) || g->subiters > 0;
+      g->coupled |= case_coupled(a->c);
       g->members.push_back(a);
       g->dirty = true;
       cudaStreamWaitEvent(g->s, a->done, 0);

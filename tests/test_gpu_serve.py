@@ -1,18 +1,23 @@
-"""Request loop (ibm_server_*): continuous batching of independent cases.
+"""Request loop (ibm_server_*): continuous batching of independent cases -- explicit requests with any motion
+(a body under the fluid force included) and dual-time requests, each kind in block-table groups.
 
 Each request must give the same result in the mix as alone.  Cases share
 nothing on the device and every kernel of the step is deterministic (no
 floating-point atomics), so with one stream per case -- the same kernels as a
-case stepped alone -- forces and time are compared bit for bit.  Batched
-groups run the same per-tile source in a separately compiled block-table
-kernel, whose FP32 roundings (fused multiply-adds) may differ by an ulp per
-operation; over the <= 23 steps of these tests that moves time by ~1e-8
+case stepped alone -- forces and time are compared bit for bit, and so are
+dual-time requests in batched groups (a dual-time case alone runs the same
+block-table kernel with a table of one).  Batched explicit groups run the same
+per-tile source in a separately compiled block-table kernel, whose FP32
+roundings (fused multiply-adds) may differ by an ulp per operation; over the <= 23 steps of these tests that moves time by ~1e-8
 relative and forces by at most ~1e-6 of the largest force component (the
 largest measured, 1.1e-6, is on the lift of a body symmetric about the
 stream, whose exact value is zero: rounding noise that the flow amplifies).
-The tolerance is 1e-5 of the largest component.  The admission tests check
-the memory gate and the slot limit.
+The tolerance is 1e-5 of the largest component.  Batched groups are also
+checked against the FP64 oracle with the FP32-bulk bar (drag and lift within
+1e-3).  The admission tests check the memory gate and the slot limit.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -25,8 +30,8 @@ STEPS = 23
 RTOL_BATCHED = 1e-5
 
 
-def _same(r, f, t, mode):
-    if mode & ibm.SERVE_BATCHED:
+def _same(r, f, t, mode, spec):
+    if mode & ibm.SERVE_BATCHED and spec["time_scheme"] != W.TIME_DUAL:
         np.testing.assert_allclose(r["forces"], f, rtol=RTOL_BATCHED, atol=RTOL_BATCHED * np.abs(f).max())
         assert abs(r["t"] - t) <= RTOL_BATCHED * abs(t)
     else:
@@ -44,6 +49,12 @@ def _specs(n=10, max_cells=256 * 128):
     out = osc[:3] + sup[:2] + rest[: n - len(picked)]
     assert len(out) == n and osc and sup
     return out
+
+
+def _coupled(nx=128, ny=64, mach=0.4, name="coupled"):
+    """A cylinder free to translate in a uniform stream (Eq. 10), mass twice that of the gas it displaces."""
+    return W.case_spec(W.cylinder(256), nx, ny, (-8.0, 24.0, -8.0, 8.0), mach, 200.0, W.FAR,
+                       motion=W.MOTION_COUPLED, mass=2.0 * math.pi * 0.25, precision=W.PREC_FP32_BULK, name=name)
 
 
 def _alone(spec, nsteps):
@@ -75,18 +86,19 @@ MODES = [ibm.SERVE_BATCHED | ibm.SERVE_AUTOTUNE, ibm.SERVE_BATCHED, 0]
 
 @pytest.mark.parametrize("mode", MODES)
 def test_mix_results_identical_to_alone(mode):
-    specs = _specs()
+    specs = _specs(9) + [_coupled()]
+    assert any(s["time_scheme"] == W.TIME_DUAL for s in specs)
     ref = [_alone(s, STEPS) for s in specs]
     srv = ibm.Server(max_active=4, steps_per_chunk=7, mode=mode)
     try:
         ids = [srv.submit(s, STEPS) for s in specs]
         max_running = _drain(srv, cap=4)
         assert max_running >= 2, "no two cases ran together"
-        for rid, (f, t) in zip(ids, ref):
+        for rid, (f, t), spec in zip(ids, ref, specs):
             r = srv.poll(rid)
             assert r["state"] == ibm.REQ_DONE and r["status"] == 0, r
             assert r["steps_done"] == STEPS
-            _same(r, f, t, mode)
+            _same(r, f, t, mode, spec)
             assert r["submit_s"] <= r["start_s"] <= r["finish_s"]
         st = srv.stats()
         if mode & ibm.SERVE_BATCHED:
@@ -94,6 +106,41 @@ def test_mix_results_identical_to_alone(mode):
             assert (st["autotune_runs"] > 0) == bool(mode & ibm.SERVE_AUTOTUNE)
         else:
             assert st["group_steps"] == 0
+    finally:
+        srv.close()
+
+
+def test_batched_groups_against_oracle(orc):
+    """Batched results against the FP64 oracle (not only against the case alone): one explicit group with a
+    static, an oscillating, a free (Eq. 10) and a supersonic body, and one dual-time group at low Mach."""
+    P = W.PREC_FP32_BULK
+    cyl, dom = W.cylinder(256), (-8.0, 24.0, -8.0, 8.0)
+    explicit = [W.case_spec(cyl, 128, 64, dom, 0.3, 100.0, W.FAR, precision=P, name="static"),
+                W.case_spec(cyl, 128, 64, dom, 0.3, 100.0, W.FAR, motion=W.MOTION_SIN, amp=(0.0, 0.2), freq=0.16,
+                            precision=P, name="osc"),
+                _coupled(160, 64),
+                W.wedge_m2_re1e4(128, 64, precision=P)]
+    dual = [W.case_spec(cyl, 128, 64, dom, 0.01, 100.0, W.FAR, time_scheme=W.TIME_DUAL, dt_phys=0.125,
+                        subiters=10, precision=P, name="dual_cyl"),
+            W.case_spec(W.naca00xx(0.12, 400, 5.0), 160, 80, (-1.0, 3.0, -1.0, 1.0), 0.01, 500.0, W.FAR,
+                        time_scheme=W.TIME_DUAL, dt_phys=0.025, subiters=10, precision=P, name="dual_naca")]
+    jobs = [(s, 40) for s in explicit] + [(s, 4) for s in dual]
+    srv = ibm.Server(max_active=8, steps_per_chunk=10)
+    try:
+        ids = [srv.submit(s, n) for s, n in jobs]
+        assert _drain(srv, cap=8) == len(jobs)
+        st = srv.stats()
+        assert st["group_graphs"] >= 2 and st["group_steps"] > 0  # an explicit and a dual-time group
+        for rid, (spec, n) in zip(ids, jobs):
+            r = srv.poll(rid)
+            assert r["state"] == ibm.REQ_DONE and r["status"] == 0 and r["steps_done"] == n, r
+            o = orc.Case(dict(spec, precision=W.PREC_FP64))
+            o.step(n)
+            fo = o.forces()
+            d = np.abs(r["forces"][:2] - fo[:2])
+            print("%s: batched Cd, Cl %s oracle %s" % (spec["name"], r["forces"][:2], fo[:2]))
+            assert d.max() <= 1e-3, (spec["name"], d)
+            assert abs(r["t"] - o.time()) <= 1e-5 * o.time(), spec["name"]
     finally:
         srv.close()
 
@@ -110,10 +157,10 @@ def test_batched_group_of_many_cases():
     try:
         ids = [srv.submit(s, 11) for s in specs]
         assert _drain(srv, cap=30) == 30
-        for rid, (f, t) in zip(ids, ref):
+        for rid, (f, t), spec in zip(ids, ref, specs):
             r = srv.poll(rid)
             assert r["state"] == ibm.REQ_DONE, r
-            _same(r, f, t, MODES[0])
+            _same(r, f, t, MODES[0], spec)
         st = srv.stats()
         assert st["group_graphs"] >= 2  # 30 cases of one size class need two groups
     finally:
@@ -136,10 +183,10 @@ def test_requests_arriving_while_others_run(mode):
             srv.progress()
         _drain(srv, cap=3)
         assert overlapped
-        for rid, (f, t) in zip(ids, ref):
+        for rid, (f, t), spec in zip(ids, ref, specs):
             r = srv.poll(rid)
             assert r["state"] == ibm.REQ_DONE, r
-            _same(r, f, t, mode)
+            _same(r, f, t, mode, spec)
     finally:
         srv.close()
 
