@@ -24,6 +24,7 @@ struct ibm_case {
   // device memory
   double *vref = nullptr, *vx = nullptr, *vy = nullptr, *snx = nullptr, *sny = nullptr, *vnx = nullptr,
          *vny = nullptr, *vk = nullptr;
+  float *segb = nullptr;  // segment bounds of the current pose (stencil searches)
   double *surf = nullptr;  // per segment (Cp, Cf) of the last ibm_surface call
   double *rsnx = nullptr, *rsny = nullptr, *rvnx = nullptr, *rvny = nullptr;  // PITCH: reference-pose normals
   double *A = nullptr, *B = nullptr, *C = nullptr;  // FP64 conserved: state, stage arrays (FP64 mode)
@@ -230,6 +231,7 @@ static size_t carve(ibm_case *c, char *base) {
   take(&c->vnx, nv);
   take(&c->vny, nv);
   take(&c->vk, nv);
+  take(&c->segb, 3 * nv);
   take(&c->surf, 2 * nv);
   if (k.motion.kind == IBM_MOTION_PITCH) {
     take(&c->rsnx, nv);
@@ -439,6 +441,17 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   c->g.vnx = c->vnx;
   c->g.vny = c->vny;
   c->g.vk = c->vk;
+  c->g.sb = c->segb;
+  {  // stencil searches: half a warp per node when the body's nodes (about four layers along its perimeter)
+     // fill the GPU with whole-warp nodes, a whole warp otherwise
+    double perim = 0.0;
+    for (int v = 0; v < c->g.nv; v++) {
+      const int v1 = v + 1 == c->g.nv ? 0 : v + 1;
+      perim += std::hypot(geo->verts[2 * v1] - geo->verts[2 * v], geo->verts[2 * v1 + 1] - geo->verts[2 * v + 1]);
+    }
+    const double cells = perim / std::min(k.dx, k.dy);
+    c->g.stencil_lanes = 4.0 * cells >= 4.0 * 2 * 152 ? 16 : 32;
+  }
   const bool pitching = k.motion.kind == IBM_MOTION_PITCH;
   c->g.rsnx = pitching ? c->rsnx : nullptr;
   c->g.rsny = pitching ? c->rsny : nullptr;

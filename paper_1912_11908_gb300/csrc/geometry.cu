@@ -140,7 +140,11 @@ __global__ void k_pose(Consts k, Geom g, DevState *ds) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   if (lane == 0)
     for (int q = 0; q < 4; q++) wb[warp][q] = b[q];
-  __syncthreads();
+  __syncthreads();  // (also orders this block's pose writes before the segment bounds read them)
+  for (int v = threadIdx.x; v < g.nv; v += blockDim.x) {
+    const int v1 = v + 1 == g.nv ? 0 : v + 1;
+    segment_bound(g.vx[v], g.vy[v], g.vx[v1], g.vy[v1], g.sb + 3 * v);
+  }
   if (threadIdx.x == 0) {
     for (int w = 1; w < nw; w++) {
       b[0] = fmin(b[0], wb[w][0]);
@@ -405,22 +409,6 @@ __device__ int interp_square(const Consts &k, const uint8_t *__restrict__ tag, d
 constexpr unsigned ALLOW_FLUID = 1u << FLUID;
 constexpr unsigned ALLOW_FLUID_IB = (1u << FLUID) | (1u << IB);
 
-// lexicographic (value, index) minimum across a warp; every lane gets the winner's lane
-__device__ __forceinline__ int warp_argmin(double v, int idx) {
-  int src = threadIdx.x & 31;
-  for (int off = 16; off > 0; off >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
-    const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
-    const int os = __shfl_xor_sync(0xffffffffu, src, off);
-    if (ov < v || (ov == v && oi < idx)) {
-      v = ov;
-      idx = oi;
-      src = os;
-    }
-  }
-  return src;
-}
-
 // Sec. 4.1: the point of segment kk nearest (px, py) -- a vertex (region VERTEX, feature the vertex) or the
 // foot point (region FACE, feature the segment) -- and its squared distance
 __device__ __forceinline__ double seg_closest(const Geom &g, int kk, double px, double py, double *cxo, double *cyo,
@@ -566,11 +554,11 @@ __device__ __forceinline__ void stencil_tail(const Consts &k, const Geom &g, con
   }
 }
 
-// Sec. 4.1-4.6, Sec. 5: one stencil per listed node, one warp per node (four
-// per 128-thread block, blocks striding over the list).  The lanes split the
-// segments of the two searches (closest feature, boundary point); the warp
-// keeps the (distance, segment) lexicographic minimum, which is the first
-// minimum of a sequential scan.
+// Sec. 4.1-4.6, Sec. 5: one stencil per listed node, a group of NL lanes
+// per node (blocks striding over the list).  The lanes
+// split the segments of the two searches (closest feature, boundary point);
+// the group keeps the (distance, segment) lexicographic minimum, which is the
+// first minimum of a sequential scan.
 // rs / sid (optional): the FP32 compact form of each stencil and the cell ->
 // stencil map of the FP32-bulk reconstruction.
 // Pruning (bodies of up to STENCIL_PRUNE_MAX vertices): every segment's
@@ -584,30 +572,52 @@ __device__ __forceinline__ void stencil_tail(const Consts &k, const Geom &g, con
 // search's, bit for bit.
 constexpr int STENCIL_PRUNE_MAX = 2048;
 
+// Lanes per listed node: a whole warp, or half a warp (two nodes per warp).  Half a warp splits a node's
+// segments about as well (its candidates after pruning are a few neighbouring segments), and the FP64 work
+// that follows the searches, on the group's first lane, then shares its warp instructions with the other
+// node's: fewer FP64 warp instructions per node, which bounds the kernel when many nodes fill the GPU; with
+// few nodes the kernel is bound by one node's latency, which a whole warp keeps shorter.
+
+// group_argmin over aligned groups of NL lanes: the lane holding the (value, index) lexicographic minimum
+template <int NL>
+__device__ __forceinline__ int group_argmin(double v, int idx) {
+  int src = threadIdx.x & 31;
+  for (int off = NL / 2; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    const int os = __shfl_xor_sync(0xffffffffu, src, off);
+    if (ov < v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+      src = os;
+    }
+  }
+  return src;
+}
+
+template <int NL>
 __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_t *__restrict__ tag,
                                                   ibm_stencil *__restrict__ st, int cap, DevState *ds,
                                                   RStencil32 *__restrict__ rs, int *__restrict__ sid) {
-  extern __shared__ float s_sb[];  // per segment: centre x, y and radius (half length plus the margin), FP32
+  constexpr int STENCIL_NODES = 128 / NL;  // nodes per block in flight
+  extern __shared__ float s_sb[];  // per segment: centre x, y and bounding radius, FP32 (segment_bound)
   const int total = min(ds->offset[4], cap);
   const int nv = g.nv;
   const bool prune = nv <= STENCIL_PRUNE_MAX;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if ((int)blockIdx.x * 4 >= total) return;
-  if (prune) {
-    for (int kk = threadIdx.x; kk < nv; kk += 128) {
-      const int k1 = (kk + 1 == nv) ? 0 : kk + 1;
-      const double ax = g.vx[kk], ay = g.vy[kk], bx = g.vx[k1], by = g.vy[k1];
-      const double cx = 0.5 * (ax + bx), cy = 0.5 * (ay + by);
-      const double hl = 0.5 * sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
-      s_sb[3 * kk] = (float)cx;
-      s_sb[3 * kk + 1] = (float)cy;
-      s_sb[3 * kk + 2] = (float)(hl + 1e-5 * (1.0 + fabs(cx) + fabs(cy) + hl));
-    }
+  const int lane = threadIdx.x & 31, gl = lane % NL;
+  if ((int)blockIdx.x * STENCIL_NODES >= total) return;
+  if (prune) {  // the pose kernel's segment bounds of this pose
+    for (int kk = threadIdx.x; kk < 3 * nv; kk += 128) s_sb[kk] = g.sb[kk];
     __syncthreads();
   }
-  // one warp per listed node, the lanes splitting the segments of the searches
-  for (int e = (int)blockIdx.x * 4 + warp; e < total; e += (int)gridDim.x * 4) {
-    const ibm_stencil s0 = st[e];
+  // NL lanes per listed node splitting the segments of the searches; the loop runs alike for the whole warp
+  // (every lane takes part in the shuffles), a group past the end of the list idle inside it
+  for (int e0 = (int)blockIdx.x * STENCIL_NODES + (int)(threadIdx.x >> 5) * (32 / NL); e0 < total;
+       e0 += (int)gridDim.x * STENCIL_NODES) {
+    const int e = e0 + lane / NL;
+    const bool act = e < total;
+    ibm_stencil s0 = {};
+    if (act) s0 = st[e];
     const int kind = s0.kind;
     const int i = s0.cell % k.nx, j = s0.cell / k.nx;
     const double px = k.x0 + ((double)i + 0.5) * k.dx;
@@ -615,39 +625,43 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
     const float pxf = (float)px, pyf = (float)py;
     // the smallest upper bound of the node's distance to a segment
     float ub = INFINITY;
-    if (prune) {
-      for (int kk = lane; kk < nv; kk += 32) {
+    if (prune && act) {
+      for (int kk = gl; kk < nv; kk += NL) {
         const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
         ub = fminf(ub, sqrtf(dx * dx + dy * dy) + s_sb[3 * kk + 2]);
       }
-      for (int o = 16; o > 0; o >>= 1) ub = fminf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
     }
+    for (int o = NL / 2; o > 0; o >>= 1) ub = fminf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
     // closest feature (Sec. 4.1)
     double best = INFINITY, bcx = 0.0, bcy = 0.0;
     int bseg = 0x7fffffff, bfeat = 0, breg = 0;
-    for (int kk = lane; kk < nv; kk += 32) {
-      if (prune) {
-        const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
-        if (sqrtf(dx * dx + dy * dy) - s_sb[3 * kk + 2] > ub) continue;
-      }
-      double cx, cy;
-      int f, r;
-      const double d2 = seg_closest(g, kk, px, py, &cx, &cy, &f, &r);
-      if (d2 < best) {
-        best = d2; bseg = kk; bfeat = f; breg = r; bcx = cx; bcy = cy;
+    if (act) {
+      for (int kk = gl; kk < nv; kk += NL) {
+        if (prune) {
+          const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
+          if (sqrtf(dx * dx + dy * dy) - s_sb[3 * kk + 2] > ub) continue;
+        }
+        double cx, cy;
+        int f, r;
+        const double d2 = seg_closest(g, kk, px, py, &cx, &cy, &f, &r);
+        if (d2 < best) {
+          best = d2; bseg = kk; bfeat = f; breg = r; bcx = cx; bcy = cy;
+        }
       }
     }
-    int win = warp_argmin(best, bseg);
+    int win = group_argmin<NL>(best, bseg);
     const int feat = __shfl_sync(0xffffffffu, bfeat, win);
     const int region = __shfl_sync(0xffffffffu, breg, win);
     const double ccx = __shfl_sync(0xffffffffu, bcx, win), ccy = __shfl_sync(0xffffffffu, bcy, win);
-    double nx, ny;
-    if (region == IBM_REGION_FACE) {
-      nx = g.snx[feat];
-      ny = g.sny[feat];
-    } else {
-      nx = g.vnx[feat];
-      ny = g.vny[feat];
+    double nx = 0.0, ny = 0.0;
+    if (act) {
+      if (region == IBM_REGION_FACE) {
+        nx = g.snx[feat];
+        ny = g.sny[feat];
+      } else {
+        nx = g.vnx[feat];
+        ny = g.vny[feat];
+      }
     }
     // boundary point on the line along the local normal (Sec. 4.3): first the segments that can hold the
     // closest point, then, beyond them, those that can hold a crossing no farther than the best found (all of
@@ -658,11 +672,12 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
     float bound = INFINITY;
     for (int pass = 0; pass < (prune ? 2 : 1); pass++) {
       if (pass == 1) {
-        const int w2 = warp_argmin(bs_best, bs_seg);
+        const int w2 = group_argmin<NL>(bs_best, bs_seg);
         const double found = __shfl_sync(0xffffffffu, bs_best, w2);
         bound = found < INFINITY ? (float)found * (1.f + 1e-6f) : INFINITY;
       }
-      for (int kk = lane; kk < nv; kk += 32) {
+      if (!act) continue;
+      for (int kk = gl; kk < nv; kk += NL) {
         if (prune) {
           const float dx = pxf - s_sb[3 * kk], dy = pyf - s_sb[3 * kk + 1];
           const float lb = sqrtf(dx * dx + dy * dy) - s_sb[3 * kk + 2];
@@ -676,24 +691,27 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
         }
       }
     }
-    win = warp_argmin(bs_best, bs_seg);
+    win = group_argmin<NL>(bs_best, bs_seg);
     const double found_abs = __shfl_sync(0xffffffffu, bs_best, win);
     const double bsv = __shfl_sync(0xffffffffu, bs_s, win);
     const double bsu = __shfl_sync(0xffffffffu, bs_u, win);
     const int bsg = __shfl_sync(0xffffffffu, bs_seg, win);
-    if (lane == 0)
+    if (act && gl == 0)
       stencil_tail(k, g, tag, ds, s0, e, px, py, feat, region, ccx, ccy, found_abs, bsv, bsu, bsg, nx, ny, st,
                    rs, sid);
     __syncwarp();
   }
 }
 
-// stencils of the listed nodes: one warp per node, four per block, blocks striding over the list
+// stencils of the listed nodes: 128 / lanes per node per 128-thread block, blocks striding over the list
 static void launch_stencil_kernel(const Consts &k, const Geom &g, const uint8_t *tag, ibm_stencil *st, int cap,
                                   DevState *ds, RStencil32 *rs, int *sid, cudaStream_t s) {
   if (cap <= 0) return;
-  k_stencils<<<(unsigned)min((cap + 3) / 4, 8 * 152), 128,
-               g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0, s>>>(k, g, tag, st, cap, ds, rs, sid);
+  const size_t smem = g.nv <= STENCIL_PRUNE_MAX ? 3 * sizeof(float) * g.nv : 0;
+  if (g.stencil_lanes == 16)
+    k_stencils<16><<<(unsigned)min((cap + 7) / 8, 8 * 152), 128, smem, s>>>(k, g, tag, st, cap, ds, rs, sid);
+  else
+    k_stencils<32><<<(unsigned)min((cap + 3) / 4, 8 * 152), 128, smem, s>>>(k, g, tag, st, cap, ds, rs, sid);
 }
 
 // ---------------------------------------------------------------------------
@@ -757,6 +775,11 @@ __global__ void __launch_bounds__(256) k_pose_classify(Consts k, Geom g, uint8_t
   if (lane == 0)
     for (int q = 0; q < 4; q++) wb[warp][q] = b[q];
   __syncthreads();
+  if (blockIdx.x == 0)  // the stencil searches' segment bounds of this pose
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      const int v1 = v + 1 == nv ? 0 : v + 1;
+      segment_bound(sv[v], sv[nv + v], sv[v1], sv[nv + v1], g.sb + 3 * v);
+    }
   if (threadIdx.x == 0) {
     for (int w = 1; w < 8; w++) {
       b[0] = fmin(b[0], wb[w][0]);
@@ -1222,45 +1245,52 @@ void launch_stencils(const Consts &k, const Geom &g, const uint8_t *tag, ibm_ste
 // pressure and wall shear from a probe one diagonal spacing out along the
 // segment normal (inverse-distance weighted, Sec. 4.6), the pressure carried
 // to the wall by the reconstruction's wall condition (Eq. 6-8, curvature at
-// the segment midpoint); free-stream pressure subtracted.  One block;
-// fixed-order tree reduction (deterministic).
+// the segment midpoint); free-stream pressure subtracted.
 // ---------------------------------------------------------------------------
-// Eq. 9 over the body's segments: up to FORCE_BLOCKS blocks of FORCE_THREADS threads, one segment per thread
-// (blocks stride over longer bodies); each block sums its segments in a fixed tree order into a partial, and
-// the last block to finish adds the partials in block order, so the sum is deterministic
-constexpr int FORCE_THREADS = 32, FORCE_BLOCKS = 64;
+// Eq. 9 over the body's segments: four lanes per segment, each taking one corner of the probe's interpolation
+// square (the corners' conversions to primitives are the longest part of a segment's work), summed in corner
+// order by shuffles -- the values a single lane forms, a masked corner adding an exact zero.  The segment's
+// geometry and wall terms run on all four lanes alike.  One-warp blocks of FORCE_THREADS / 4 segments, up to
+// FORCE_BLOCKS blocks striding over longer bodies; each block sums its segments in a fixed shuffle-tree order
+// into a partial, and the last block to finish adds the partials in block order, so the sum is deterministic.
+constexpr int FORCE_THREADS = 32, FORCE_BLOCKS = 64, FORCE_SEGS = FORCE_THREADS / 4;
 __global__ void __launch_bounds__(FORCE_THREADS) k_forces_f64(Consts k, Geom g, const uint8_t *__restrict__ tag,
                                                               const double *__restrict__ A, bool pert, DevState *ds,
                                                               bool set_accel, double *__restrict__ surf) {
-  __shared__ double rx[FORCE_THREADS], ry[FORCE_THREADS];
   __shared__ bool last;
+  __shared__ double part[2 * FORCE_BLOCKS];
   double V[2], Acc[2], X[2];
   body_motion(k, ds, ds->t, X, V, Acc);
   const bool sup = supersonic_motion(k, V);
+  const int cq = threadIdx.x & 3, base = threadIdx.x & ~3;
   double sx = 0.0, sy = 0.0;
-  for (int e = blockIdx.x * FORCE_THREADS + threadIdx.x; e < g.nv; e += gridDim.x * FORCE_THREADS) {
-    int e1 = (e + 1 == g.nv) ? 0 : e + 1;
-    double ax = g.vx[e], ay = g.vy[e];
-    double ex = g.vx[e1] - ax, ey = g.vy[e1] - ay;
-    double L = sqrt(ex * ex + ey * ey);
-    double tx = ex / L, ty = ey / L;
-    double nx = ty, ny = -tx;
-    double mx = ax + 0.5 * ex, my = ay + 0.5 * ey;
-    double xi = k.h, w[4];
+  // the loop's trip count is the same for the whole warp (every lane takes part in the shuffles)
+  for (int e0 = blockIdx.x * FORCE_SEGS; e0 < g.nv; e0 += gridDim.x * FORCE_SEGS) {
+    const int e = e0 + (threadIdx.x >> 2);
+    const bool valid = e < g.nv;
+    const int e1 = (e + 1 >= g.nv) ? 0 : e + 1;
+    double L = 1.0, tx = 0.0, ty = 0.0, nx = 0.0, ny = 0.0, mx = 0.0, my = 0.0, xi = k.h, w[4];
     int i0 = 0, j0 = 0, mask = 0;
-    for (int stp = 0; stp <= 3; stp++) {
-      mask = interp_square(k, tag, mx + xi * nx, my + xi * ny, ALLOW_FLUID, &i0, &j0, w);
-      if (mask) break;
-      if (stp < 3) xi = xi + k.dmin;
+    if (valid) {
+      const double ax = g.vx[e], ay = g.vy[e];
+      const double ex = g.vx[e1] - ax, ey = g.vy[e1] - ay;
+      L = sqrt(ex * ex + ey * ey);
+      tx = ex / L;
+      ty = ey / L;
+      nx = ty;
+      ny = -tx;
+      mx = ax + 0.5 * ex;
+      my = ay + 0.5 * ey;
+      for (int stp = 0; stp <= 3; stp++) {
+        mask = interp_square(k, tag, mx + xi * nx, my + xi * ny, ALLOW_FLUID, &i0, &j0, w);
+        if (mask) break;
+        if (stp < 3) xi = xi + k.dmin;
+      }
     }
-    if (!mask) {
-      if (surf) surf[e] = surf[g.nv + e] = CUDART_NAN;
-      continue;
-    }
-    double qp[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int q = 0; q < 4; q++) {
-      if (!(mask >> q & 1)) continue;
-      long long id = cidx(k, i0 + (q & 1), j0 + (q >> 1));
+    // this lane's corner: w_q (p, u, v, T) at the corner's cell
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    if (mask >> cq & 1) {
+      const long long id = cidx(k, i0 + (cq & 1), j0 + (cq >> 1));
       double U0 = A[id], U1 = A[id + k.plane], U2 = A[id + 2 * k.plane], U3 = A[id + 3 * k.plane];
       if (pert) {  // perturbation state dU -> absolute conserved
         U3 = k.Uinf[3] + U3 + k.Hinf * U0;
@@ -1268,13 +1298,22 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_forces_f64(Consts k, Geom g, 
         U1 = k.Uinf[1] + U1;
         U2 = k.Uinf[2] + U2;
       }
-      double r = U0, u = U1 / r, v = U2 / r;
-      double pr = (k.gamma - 1.0) * (U3 - 0.5 * r * (u * u + v * v));
-      double T = pr / (r * k.R);
-      qp[0] += w[q] * pr;
-      qp[1] += w[q] * u;
-      qp[2] += w[q] * v;
-      qp[3] += w[q] * T;
+      const double r = U0, u = U1 / r, v = U2 / r;
+      const double pr = (k.gamma - 1.0) * (U3 - 0.5 * r * (u * u + v * v));
+      const double T = pr / (r * k.R);
+      const double wq = cq == 0 ? w[0] : cq == 1 ? w[1] : cq == 2 ? w[2] : w[3];
+      t[0] = wq * pr;
+      t[1] = wq * u;
+      t[2] = wq * v;
+      t[3] = wq * T;
+    }
+    double qp[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < 4; q++)
+      for (int m = 0; m < 4; m++) qp[m] += __shfl_sync(0xffffffffu, t[m], base + q);
+    if (!valid) continue;
+    if (!mask) {
+      if (surf && cq == 0) surf[e] = surf[g.nv + e] = CUDART_NAN;
+      continue;
     }
     // wall pressure: the probe's, carried to the surface by the wall condition of the reconstruction
     double Vs[2], As[2];
@@ -1284,8 +1323,9 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_forces_f64(Consts k, Geom g, 
       double ut = (qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty;
       G = G + ut * ut * (0.5 * (g.vk[e] + g.vk[e1]));
     }
-    double ps = qp[0] * exp(-xi * G / (k.R * qp[3]));
-    double tau = k.mu * ((qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty) / xi;
+    const double ps = qp[0] * exp(-xi * G / (k.R * qp[3]));
+    const double tau = k.mu * ((qp[1] - Vs[0]) * tx + (qp[2] - Vs[1]) * ty) / xi;
+    if (cq != 0) continue;
     if (surf) {  // Eq. 9 integrand: (p_s - p_inf) / (rho_inf U^2 / 2), tau / (rho_inf U^2 / 2)
       surf[e] = (ps - k.pinf) / 0.5;
       surf[g.nv + e] = tau / 0.5;
@@ -1293,29 +1333,30 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_forces_f64(Consts k, Geom g, 
     sx += (-(ps - k.pinf) * nx + tau * tx) * L;
     sy += (-(ps - k.pinf) * ny + tau * ty) * L;
   }
-  rx[threadIdx.x] = sx;
-  ry[threadIdx.x] = sy;
-  __syncthreads();
-  for (int off = FORCE_THREADS / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off) {
-      rx[threadIdx.x] += rx[threadIdx.x + off];
-      ry[threadIdx.x] += ry[threadIdx.x + off];
-    }
-    __syncthreads();
+  for (int off = 16; off > 0; off >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+    sy += __shfl_xor_sync(0xffffffffu, sy, off);
   }
   if (threadIdx.x == 0) {
-    ds->fpart[2 * blockIdx.x] = rx[0];
-    ds->fpart[2 * blockIdx.x + 1] = ry[0];
+    ds->fpart[2 * blockIdx.x] = sx;
+    ds->fpart[2 * blockIdx.x + 1] = sy;
     __threadfence();
     last = atomicAdd(&ds->fdone, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
+  if (!last) return;
+  // the last block: the partials loaded in parallel, then added in block order
+  __threadfence();
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += FORCE_THREADS) {
+    part[2 * b] = *(volatile double *)&ds->fpart[2 * b];
+    part[2 * b + 1] = *(volatile double *)&ds->fpart[2 * b + 1];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double fx = 0.0, fy = 0.0;
     for (int b = 0; b < (int)gridDim.x; b++) {
-      fx += *(volatile double *)&ds->fpart[2 * b];
-      fy += *(volatile double *)&ds->fpart[2 * b + 1];
+      fx += part[2 * b];
+      fy += part[2 * b + 1];
     }
     ds->fdone = 0;
     const double q = 0.5 * k.ref_len;
@@ -1334,7 +1375,7 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_forces_f64(Consts k, Geom g, 
 
 void launch_forces_f64(const Consts &k, const Geom &g, const uint8_t *tag, const double *A, bool pert,
                        DevState *ds, cudaStream_t s, bool set_accel, double *surf) {
-  const int blocks = std::max(1, std::min(FORCE_BLOCKS, (g.nv + FORCE_THREADS - 1) / FORCE_THREADS));
+  const int blocks = std::max(1, std::min(FORCE_BLOCKS, (g.nv + FORCE_SEGS - 1) / FORCE_SEGS));
   k_forces_f64<<<blocks, FORCE_THREADS, 0, s>>>(k, g, tag, A, pert, ds, set_accel, surf);
 }
 

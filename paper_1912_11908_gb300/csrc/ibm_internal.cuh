@@ -94,7 +94,21 @@ struct Geom {
   double *snx, *sny, *vnx, *vny;   // segment and vertex normals of the current pose
   const double *rsnx, *rsny, *rvnx, *rvny;  // PITCH: normals of the reference pose (rotated into snx ...)
   const double *vk;     // signed curvature at each vertex (convex > 0)
+  float *sb;            // per segment of the current pose, FP32: centre x, y and bounding radius (the stencil
+                        // searches' pruning bounds, written by the pose kernels)
+  int stencil_lanes;    // lanes per listed node of the stencil searches (16 or 32, from the body's size)
 };
+
+// The FP32 bounding circle of the segment (ax, ay) - (bx, by): centre, and half length plus a margin of 1e-5 of
+// the coordinates' size (far above FP32 rounding), so that FP32 distances to the centre bound the distance to
+// the segment from below and above.
+__device__ __forceinline__ void segment_bound(double ax, double ay, double bx, double by, float *out) {
+  const double cx = 0.5 * (ax + bx), cy = 0.5 * (ay + by);
+  const double hl = 0.5 * sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+  out[0] = (float)cx;
+  out[1] = (float)cy;
+  out[2] = (float)(hl + 1e-5 * (1.0 + fabs(cx) + fabs(cy) + hl));
+}
 
 __host__ __device__ inline long long cidx(const Consts &k, int i, int j) {
   return (long long)(j + NG) * k.pitch + (i + NG);
