@@ -49,7 +49,7 @@ class _Params(ctypes.Structure):
         ("pivot", ctypes.c_double * 2), ("pitch_mean", ctypes.c_double), ("pitch_amp", ctypes.c_double),
         ("scheme", ctypes.c_int),
         ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("dt_phys", ctypes.c_double),
-        ("cfl_tau", ctypes.c_double),
+        ("cfl_tau", ctypes.c_double), ("ib_interp", ctypes.c_int),
     ]
 
 
@@ -58,6 +58,7 @@ STENCIL_DTYPE = np.dtype([
     ("mask", "<i4"), ("nstep", "<i4"), ("kind", "<i4"),
     ("nx", "<f8"), ("ny", "<f8"), ("bx", "<f8"), ("by", "<f8"),
     ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (4,)), ("curv", "<f8"),
+    ("i0b", "<i4"), ("j0b", "<i4"), ("maskb", "<i4"), ("nstepb", "<i4"), ("xi_probe2", "<f8"), ("wb", "<f8", (4,)),
 ])
 
 _lib = None
@@ -78,6 +79,7 @@ def lib():
         L.orc_step.restype = ip
         L.orc_get_state.argtypes = [vp, vp]
         L.orc_set_state.argtypes = [vp, vp]
+        L.orc_set_time.argtypes = [vp, dp]
         L.orc_get_tags.argtypes = [vp, vp]
         L.orc_list_len.argtypes = [vp, ip]
         L.orc_list_len.restype = ip
@@ -150,6 +152,7 @@ class Case:
         P.subiters = s.get("subiters", 30)
         P.dt_phys = s.get("dt_phys", 0.0)
         P.cfl_tau = s.get("cfl_tau", 0.8)
+        P.ib_interp = s.get("ib_interp", 0)
         self._P = P
         self.h = lib().orc_create(ctypes.byref(P))
 
@@ -173,6 +176,9 @@ class Case:
         a = np.ascontiguousarray(a, dtype=np.float64)
         assert a.shape == (4, self.ny, self.nx)
         lib().orc_set_state(self.h, _ptr(a))
+
+    def set_time(self, t):
+        lib().orc_set_time(self.h, float(t))
 
     def tags(self):
         a = np.empty((self.ny, self.nx), np.uint8)

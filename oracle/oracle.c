@@ -706,6 +706,28 @@ static void build_stencil(orc_case *c, int cell, int kind, orc_stencil *s) {
   s->xi_node = xi_node;
   s->xi_probe = xi_probe;
   s->curv = curv;
+  /* QUADRATIC (Sec. 4.5, Sec. 5): a second probe / image point one diagonal spacing beyond the first, on the   */
+  /* same corner set and pushed out the same way while its square has no usable corner                          */
+  s->i0b = s->j0b = s->maskb = s->nstepb = 0;
+  s->xi_probe2 = 0.0;
+  for (int k = 0; k < 4; k++) s->wb[k] = 0.0;
+  if (p->ib_interp == ORC_INTERP_QUADRATIC && mask != 0) {
+    double xi2 = xi_probe + c->h;
+    int32_t ib = 0, jb = 0;
+    int maskb = 0, nstepb = 0;
+    for (;;) {
+      double X = bx + xi2 * nx, Y = by + xi2 * ny;
+      maskb = interp_square(c, X, Y, allowed, &ib, &jb, s->wb);
+      if (maskb != 0 || nstepb == 3) break;
+      xi2 = xi2 + c->dmin;
+      nstepb++;
+    }
+    s->i0b = ib;
+    s->j0b = jb;
+    s->maskb = maskb;
+    s->nstepb = nstepb;
+    s->xi_probe2 = xi2;
+  }
 }
 
 int orc_classify(orc_case *c) {
@@ -788,6 +810,7 @@ static inline void prim_to_cons(const orc_case *c, const double q[4], double U[4
 
 /* ------------------------------------------------------------------------- */
 /* Sec. 4.4-4.6 and Sec. 5: IB and ghost reconstruction at stage time t.     */
+/* (ORC_INTERP_QUADRATIC: the quadratic forms in the body of the loop.)      */
 /* Velocity is Dirichlet (Eq. 4): linear along the normal through the wall   */
 /* value at P' and the interpolated probe value.  Pressure is Neumann        */
 /* (Eq. 5-6): dp/dn = -rho n.a_wall; for a body moving faster than sound     */
@@ -815,19 +838,46 @@ static void reconstruct_set(orc_case *c, double *const U[4], const orc_stencil *
       cons_to_prim(c, U[0][id], U[1][id], U[2][id], U[3][id], qk);
       for (int v = 0; v < 4; v++) qp[v] += st->w[k] * qk[v];
     }
-    double ratio = st->xi_node / st->xi_probe;
     double q[4];
-    /* dp/dn = rho G with G = -n.a_wall (+ u_t^2 kappa); rho = p / (R T) and T fixed along the normal (Eq. 8), */
-    /* so the condition integrates exactly from the probe to the node: p = p_probe exp(-(xi_p - xi_n) G / (R T)) */
+    /* dp/dn = rho G with G = -n.a_wall (+ u_t^2 kappa) */
     double G = -(st->nx * Aw[0] + st->ny * Aw[1]);
     if (supersonic) {
       double ut = -(qp[1] - Vw[0]) * st->ny + (qp[2] - Vw[1]) * st->nx;
       G = G + ut * ut * st->curv;
     }
-    q[0] = qp[0] * exp(-(st->xi_probe - st->xi_node) * G / (c->R * qp[3]));
-    q[1] = Vw[0] + (qp[1] - Vw[0]) * ratio;
-    q[2] = Vw[1] + (qp[2] - Vw[1]) * ratio;
-    q[3] = qp[3];
+    if (c->p.ib_interp == ORC_INTERP_QUADRATIC && st->maskb != 0) {
+      /* the incompressible form (Sec. 4.5, Sec. 5): quadratics in the distance s along the normal through the */
+      /* wall condition at P' (s = 0) and the two probes (s1, s2), evaluated at the node (s_n; < 0 for a ghost) */
+      double qb[4] = {0, 0, 0, 0};
+      for (int k = 0; k < 4; k++) {
+        if (!(st->maskb >> k & 1)) continue;
+        int id = fidx(c, st->i0b + (k & 1), st->j0b + (k >> 1));
+        double qk[4];
+        cons_to_prim(c, U[0][id], U[1][id], U[2][id], U[3][id], qk);
+        for (int v = 0; v < 4; v++) qb[v] += st->wb[k] * qk[v];
+      }
+      double s1 = st->xi_probe, s2 = st->xi_probe2, sn = st->xi_node;
+      /* velocity, Dirichlet (Eq. 4): Lagrange quadratic through (0, V_w), (s1, q1), (s2, q2) */
+      double L1 = sn * (sn - s2) / (s1 * (s1 - s2));
+      double L2 = sn * (sn - s1) / (s2 * (s2 - s1));
+      q[1] = Vw[0] + (qp[1] - Vw[0]) * L1 + (qb[1] - Vw[0]) * L2;
+      q[2] = Vw[1] + (qp[2] - Vw[1]) * L1 + (qb[2] - Vw[1]) * L2;
+      /* temperature, adiabatic (Eq. 8), and pressure (Eq. 5-7): a + b s + c s^2 through the two probes with    */
+      /* the wall slope b given -- 0, and rho G with the density of the first probe                             */
+      double m = (sn * sn - s1 * s1) / (s2 * s2 - s1 * s1);
+      double b = qp[0] / (c->R * qp[3]) * G;
+      q[3] = qp[3] + (qb[3] - qp[3]) * m;
+      q[0] = qp[0] + (qb[0] - qp[0]) * m + b * ((sn - s1) - (s2 - s1) * m);
+    } else {
+      /* the compressible form: linear through the wall value and the probe for the velocity; T fixed along the */
+      /* normal (Eq. 8) and rho = p / (R T), so dp/dn = rho G integrates exactly from the probe to the node:     */
+      /* p = p_probe exp(-(xi_p - xi_n) G / (R T))                                                               */
+      double ratio = st->xi_node / st->xi_probe;
+      q[0] = qp[0] * exp(-(st->xi_probe - st->xi_node) * G / (c->R * qp[3]));
+      q[1] = Vw[0] + (qp[1] - Vw[0]) * ratio;
+      q[2] = Vw[1] + (qp[2] - Vw[1]) * ratio;
+      q[3] = qp[3];
+    }
     double Un[4];
     prim_to_cons(c, q, Un);
     int id = fidx(c, st->cell % c->p.nx, st->cell / c->p.nx);
@@ -1586,6 +1636,12 @@ void orc_set_state(orc_case *c, const double *src) {
   for (int v = 0; v < 4; v++)
     for (int j = 0; j < ny; j++)
       for (int i = 0; i < nx; i++) c->A[v][fidx(c, i, j)] = src[((size_t)v * ny + j) * nx + i];
+}
+
+/* tests: move the case to time t (the next classification poses the body there) */
+void orc_set_time(orc_case *c, double t) {
+  c->t = t;
+  c->classified = 0;
 }
 
 void orc_get_tags(const orc_case *c, uint8_t *dst) { memcpy(dst, c->tag, (size_t)c->p.nx * c->p.ny); }

@@ -27,6 +27,8 @@
  *   viscous flux         pinned: shear-wave and entropy-wave decay rates (Sec. 2)
  *   RK3 + residual       pinned: periodic mass/energy conservation, free-stream preservation
  *   IB reconstruction    pinned: linear-field exactness at a flat wall, quiescent body (Sec. 4.4-4.6, Sec. 5)
+ *   quadratic IB / ghost pinned: quadratic-profile exactness at a 45-degree wall whose probes and image points
+ *                        fall on cell centres, where the linear form is off (Sec. 4.5, Sec. 5)
  *   forces               pinned: zero force in uniform flow / uniform pressure (Sec. 6, Eq. 9)
  *   drag/lift values     parity unpinned (the paper prints none for these workloads)
  */
@@ -49,6 +51,10 @@ enum { ORC_MOTION_STATIC = 0, ORC_MOTION_SIN = 1, ORC_MOTION_CONST = 2, ORC_MOTI
 /* the upwind flux carries into a rebuilt node vanish (M >= 2 stagnation).                                     */
 enum { ORC_IB_REBUILD = 0, ORC_IB_ADVANCE = 1 };
 enum { ORC_SCHEME_WENO5 = 0, ORC_SCHEME_TVD2 = 1 };
+/* IB and ghost reconstruction along the local normal: linear through the wall and one probe / image point     */
+/* (the compressible form, Sec. 4.6 and Sec. 5), or quadratic through the wall and two probes / image points    */
+/* (the incompressible form, Sec. 4.5 and Sec. 5)                                                               */
+enum { ORC_INTERP_LINEAR = 0, ORC_INTERP_QUADRATIC = 1 };
 enum { ORC_REGION_FACE = 0, ORC_REGION_VERTEX = 1, ORC_REGION_FALLBACK = 2 };
 enum { ORC_TIME_RK3 = 0, ORC_TIME_DUAL = 1 };
 
@@ -74,6 +80,7 @@ typedef struct {
   int subiters;            /* dual time: pseudo-time sub-iterations per physical step */
   double dt_phys;          /* dual time: physical time step */
   double cfl_tau;          /* dual time: pseudo-time CFL number */
+  int ib_interp;           /* ORC_INTERP_LINEAR or ORC_INTERP_QUADRATIC */
 } orc_params;
 
 /* One immersed-boundary or ghost node and its reconstruction stencil. */
@@ -91,6 +98,11 @@ typedef struct {
   double xi_probe;   /* signed distance of the probe / image point from P' */
   double w[4];       /* interpolation weights (0 for invalid corners) */
   double curv;       /* signed curvature 1/R of the surface at P' (convex > 0; Eq. 7) */
+  /* QUADRATIC: the second probe / image point, one diagonal spacing beyond the first (mask2 = 0: none found, */
+  /* or LINEAR)                                                                                                */
+  int32_t i0b, j0b, maskb, nstepb;
+  double xi_probe2;
+  double wb[4];
 } orc_stencil;
 
 typedef struct orc_case orc_case;
@@ -101,6 +113,7 @@ int orc_classify(orc_case *c);                   /* geometry at the current time
 int orc_step(orc_case *c, int nsteps);           /* RK3 or dual-time physical steps; returns #stencil errors */
 void orc_get_state(const orc_case *c, double *dst);      /* [4][ny][nx] conserved */
 void orc_set_state(orc_case *c, const double *src);      /* [4][ny][nx] conserved */
+void orc_set_time(orc_case *c, double t);                /* tests: pose the body at t from the next classification */
 void orc_get_tags(const orc_case *c, uint8_t *dst);      /* [ny][nx] */
 int orc_list_len(const orc_case *c, int kind);           /* 0 IB, 1..3 G1..G3 */
 void orc_get_list(const orc_case *c, int kind, orc_stencil *dst);

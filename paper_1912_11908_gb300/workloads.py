@@ -18,6 +18,7 @@ MOTION_STATIC, MOTION_SIN, MOTION_CONST, MOTION_COUPLED, MOTION_PITCH = 0, 1, 2,
 PREC_FP64, PREC_FP32_BULK = 0, 1
 IB_REBUILD, IB_ADVANCE = 0, 1
 SCHEME_WENO5, SCHEME_TVD2 = 0, 1
+INTERP_LINEAR, INTERP_QUADRATIC = 0, 1  # IB / ghost reconstruction along the normal (ibm_flow.ib_interp)
 TIME_RK3, TIME_DUAL = 0, 1
 
 
@@ -63,7 +64,7 @@ def wedge(half_angle_deg=15.0, chord=1.0):
 def case_spec(verts, nx, ny, domain, mach, re, bc, *, cfl=0.5, uinf=(1.0, 0.0), gamma=1.4, prandtl=0.72,
               motion=MOTION_STATIC, amp=(0.0, 0.0), freq=0.0, vel=(0.0, 0.0), mass=0.0, dt_fixed=0.0, ref_len=1.0,
               precision=PREC_FP64, time_scheme=TIME_RK3, subiters=30, dt_phys=0.0, cfl_tau=0.8, ib_mode=IB_REBUILD,
-              scheme=SCHEME_WENO5, name=""):
+              scheme=SCHEME_WENO5, ib_interp=INTERP_LINEAR, name=""):
     verts = np.zeros((0, 2)) if verts is None else np.ascontiguousarray(verts, np.float64)
     return dict(name=name, verts=verts, nx=int(nx), ny=int(ny), domain=tuple(float(v) for v in domain),
                 mach=float(mach), re=float(re), bc=tuple(int(b) for b in bc), cfl=float(cfl),
@@ -71,7 +72,8 @@ def case_spec(verts, nx, ny, domain, mach, re, bc, *, cfl=0.5, uinf=(1.0, 0.0), 
                 motion=int(motion), amp=tuple(float(a) for a in amp), freq=float(freq),
                 vel=tuple(float(v) for v in vel), mass=float(mass), dt_fixed=float(dt_fixed), ref_len=float(ref_len),
                 precision=int(precision), time_scheme=int(time_scheme), subiters=int(subiters),
-                dt_phys=float(dt_phys), cfl_tau=float(cfl_tau), ib_mode=int(ib_mode), scheme=int(scheme))
+                dt_phys=float(dt_phys), cfl_tau=float(cfl_tau), ib_mode=int(ib_mode), scheme=int(scheme),
+                ib_interp=int(ib_interp))
 
 
 FAR = (BC_FREESTREAM, BC_OUTFLOW, BC_FREESTREAM, BC_FREESTREAM)
