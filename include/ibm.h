@@ -86,6 +86,16 @@ enum { IBM_TIME_RK3 = 0, IBM_TIME_DUAL = 1 };
  * scheme read as MUSCL with the minmod limiter, f_i + 1/2 minmod(f_i - f_{i-1}, f_{i+1} - f_i), on the same
  * variables (rho, u, v, p) */
 enum { IBM_SCHEME_WENO5 = 0, IBM_SCHEME_TVD2 = 1 };
+/* IB and ghost reconstruction along the local normal n (distance s from the boundary point P'):
+ *   LINEAR (default; the compressible form, Sec. 4.6 and Sec. 5): the velocity linear through the wall value and
+ *     the probe (IB node) or mirror image point (ghost node), the temperature the probe's (adiabatic, Eq. 8), the
+ *     pressure integrated from the probe under dp/dn = rho G with T fixed (Eq. 5-7);
+ *   QUADRATIC (the incompressible form, Sec. 4.5 and Sec. 5): a second probe one diagonal spacing beyond the first
+ *     (ibm_stencil *b fields) and quadratics in s through the wall condition and both probes -- Dirichlet velocity
+ *     (Eq. 4), zero wall slope for the temperature, wall slope rho G for the pressure with the first probe's
+ *     density -- evaluated at the node (s < 0 for a ghost node: extrapolation).  For smooth low-speed flow; the
+ *     paper keeps the linear form wherever shocks can reach the wall. */
+enum { IBM_INTERP_LINEAR = 0, IBM_INTERP_QUADRATIC = 1 };
 /* stencil regions (Sec. 4.1): closest feature is a segment interior or a
  * vertex; FALLBACK = the line along the local normal met no segment on the
  * surface side, the boundary point is the closest point */
@@ -120,6 +130,7 @@ typedef struct {
   double dt_phys;   /* dual time: physical time step (> 0) */
   double cfl_tau;   /* dual time: pseudo-time CFL number (> 0) */
   int scheme;       /* IBM_SCHEME_* */
+  int ib_interp;    /* IBM_INTERP_* */
 } ibm_flow;
 
 typedef struct {
@@ -151,6 +162,12 @@ typedef struct {
   double w[4];      /* interpolation weights, 0 on invalid corners */
   double curv;      /* signed curvature 1/R of the surface at P' (convex > 0): linear along the segment holding
                        P' between the end vertices' Menger curvatures (Eq. 7, supersonic moving bodies) */
+  /* IBM_INTERP_QUADRATIC: the second probe / image point, at xi_probe2 = xi_probe + one diagonal spacing (pushed
+   * out like the first while its square has no valid corner), its square and weights; all zero otherwise or when
+   * none was found (the node then takes the linear form) */
+  int32_t i0b, j0b, maskb, nstepb;
+  double xi_probe2;
+  double wb[4];
 } ibm_stencil;
 
 /* what for ibm_get_state */

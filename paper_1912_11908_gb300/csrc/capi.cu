@@ -37,6 +37,7 @@ struct ibm_case {
   int *blockcounts = nullptr;
   ibm_stencil *st = nullptr;
   RStencil32 *rst = nullptr;  // FP32-bulk: compact stencils
+  RStencilQ *rsq = nullptr;   // FP32-bulk, quadratic reconstruction: their quadratic part
   int *sid = nullptr;         // FP32-bulk: cell -> stencil index (-1 if none)
   uint8_t *tile_body = nullptr;  // FP32-bulk: stage tiles that rebuild IB / ghost nodes
   int *body_tiles = nullptr;
@@ -203,6 +204,8 @@ static ibm_status validate(const ibm_geometry *geo, const ibm_grid *gr, const ib
   if (fl->time_scheme != IBM_TIME_RK3 && fl->time_scheme != IBM_TIME_DUAL) return fail(IBM_EINVAL, "bad time scheme");
   if (fl->ib_mode != IBM_IB_REBUILD && fl->ib_mode != IBM_IB_ADVANCE) return fail(IBM_EINVAL, "bad ib_mode");
   if (fl->scheme != IBM_SCHEME_WENO5 && fl->scheme != IBM_SCHEME_TVD2) return fail(IBM_EINVAL, "bad scheme");
+  if (fl->ib_interp != IBM_INTERP_LINEAR && fl->ib_interp != IBM_INTERP_QUADRATIC)
+    return fail(IBM_EINVAL, "bad ib_interp");
   if (fl->time_scheme == IBM_TIME_DUAL) {
     if (!(fl->dt_phys > 0) || !(fl->cfl_tau > 0) || fl->subiters < 1)
       return fail(IBM_EINVAL, "dual time needs dt_phys > 0, cfl_tau > 0, subiters >= 1");
@@ -259,6 +262,7 @@ static size_t carve(ibm_case *c, char *base) {
       take(&c->Q0, 4 * plane);
     }
     take(&c->rst, (size_t)(c->cap > 0 ? c->cap : 1));
+    if (k.quad) take(&c->rsq, (size_t)(c->cap > 0 ? c->cap : 1));
     take(&c->sid, ncell);
     take(&c->tile_body, (size_t)stage_tiles(k));
     take(&c->body_tiles, (size_t)(c->body_cap > 0 ? c->body_cap : 1));
@@ -322,6 +326,7 @@ static void init_case(ibm_case *c, const ibm_geometry *geo, const ibm_grid *gr, 
   k.dual = fl->time_scheme == IBM_TIME_DUAL;
   k.ib_advance = fl->ib_mode == IBM_IB_ADVANCE;
   k.tvd2 = fl->scheme == IBM_SCHEME_TVD2;
+  k.quad = fl->ib_interp == IBM_INTERP_QUADRATIC;
   k.subiters = fl->subiters;
   k.dt_phys = fl->dt_phys;
   k.idt_phys = fl->dt_phys > 0.0 ? 1.0 / fl->dt_phys : 0.0;
@@ -442,6 +447,7 @@ extern "C" ibm_status ibm_create_case(const ibm_geometry *geo, const ibm_grid *g
   c->g.vny = c->vny;
   c->g.vk = c->vk;
   c->g.sb = c->segb;
+  c->g.rsq = c->rsq;
   {  // stencil searches: half a warp per node when the body's nodes (about four layers along its perimeter)
      // fill the GPU with whole-warp nodes, a whole warp otherwise
     double perim = 0.0;
@@ -578,7 +584,7 @@ static ibm_status do_classify(ibm_case *c, bool defer_join = false) {
     launch_stencils(c->k, c->g, c->tag, c->st, c->cap, c->ds, s);
     nl += 1;
     if (c->rst) {
-      launch_compact_stencils(c->k, c->st, c->rst, c->sid, c->cap, c->ds, s);
+      launch_compact_stencils(c->k, c->st, c->rst, c->rsq, c->sid, c->cap, c->ds, s);
       nl += 1;
     }
   }
@@ -607,7 +613,8 @@ static bool fused_cfl(const ibm_case *c) {
 
 // the explicit FP32-bulk step runs as one persistent launch
 static bool persistent_step(const ibm_case *c) {
-  return c->use_persist && c->sch_words && c->precision == IBM_PREC_FP32_BULK && !c->k.dual && !c->k.tvd2;
+  return c->use_persist && c->sch_words && c->precision == IBM_PREC_FP32_BULK && !c->k.dual && !c->k.tvd2 &&
+         !c->k.quad;
 }
 
 // one explicit step on the case stream (kernels only; graph-capturable)
@@ -644,7 +651,7 @@ static int enqueue_step(ibm_case *c) {
       // one launch per pseudo stage: the block-table kernel of the request loop with this case alone in the
       // table (so that a case gives the same bits alone and in a group), TVD-2 its own kernel
       StageBatch *one = nullptr;
-      if (c->stage_launch > 0 && !c->k.tvd2) {
+      if (c->stage_launch > 0 && !c->k.tvd2 && !c->k.quad) {
         StageCase sc;
         case_stage_desc(c, &sc);
         one = new StageBatch();
@@ -657,15 +664,16 @@ static int enqueue_step(ibm_case *c) {
             if (one)
               launch_dual_f32_batch_one(*one, st, 0, c->stage_launch == 2, s);
             else
-              launch_dual_f32_tvd(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->G,
+              launch_dual_f32_var(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->G,
                                   c->Q0, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds,
-                                  c->stage_launch == 2, s);
+                                  c->stage_launch == 2, s, c->rsq);
             nl += 1;
           } else {
             cudaEventRecord(c->ev_fork, s);
             cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
             launch_dual_f32(c->k, st, fin[st - 1], fout[st - 1], c->A, din[st - 1], dout[st - 1], c->G, c->Q0,
-                            c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, s, c->sb);
+                            c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, s, c->sb,
+                            c->rsq);
             cudaEventRecord(c->ev_join, c->sb);
             cudaStreamWaitEvent(s, c->ev_join, 0);
             nl += 1 + (c->body_cap > 0);
@@ -740,14 +748,15 @@ static int enqueue_step(ibm_case *c) {
       // one launch for all tiles of the stage (body-tile slots first)
       launch_stage_f32_one(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->tile_body,
                            c->body_tiles, c->body_cap, c->ds, fuse_cfl, pv,
-                           c->have_tmap && c->use_tma ? &c->tmap[st - 1] : nullptr, c->stage_launch == 2, s);
+                           c->have_tmap && c->use_tma ? &c->tmap[st - 1] : nullptr, c->stage_launch == 2, s,
+                           c->rsq);
     } else {
       // body tiles run on a forked stream, concurrently with the plain tiles
       cudaEventRecord(c->ev_fork, s);
       cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
       launch_stage_f32(c->k, st, c->M, in32[st - 1], out32[st - 1], c->A, c->tag, c->sid, c->rst, c->tile_body,
                        c->body_tiles, c->body_cap, c->ds, fuse_cfl, s, c->sb, pv, true,
-                       c->have_tmap && c->use_tma ? &c->tmap[st - 1] : nullptr);
+                       c->have_tmap && c->use_tma ? &c->tmap[st - 1] : nullptr, c->rsq);
       cudaEventRecord(c->ev_join, c->sb);
       cudaStreamWaitEvent(s, c->ev_join, 0);
       if (c->body_cap > 0) nl += 1;
@@ -814,13 +823,14 @@ static ibm_status tune_plain_variant(ibm_case *c) {
     const CUtensorMap *tm = c->have_tmap && c->use_tma ? &c->tmap[stage - 1] : nullptr;
     if (form > 0) {
       launch_stage_f32_one(c->k, stage, c->M, stage == 1 ? c->M : c->F1, stage == 1 ? c->F1 : c->F2, c->A, c->tag,
-                           c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, v, tm, form == 2, s);
+                           c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, v, tm, form == 2, s,
+                           c->rsq);
       return;
     }
     cudaEventRecord(c->ev_fork, s);
     cudaStreamWaitEvent(c->sb, c->ev_fork, 0);
     launch_stage_f32(c->k, stage, c->M, stage == 1 ? c->M : c->F1, stage == 1 ? c->F1 : c->F2, c->A, c->tag, c->sid,
-                     c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, s, c->sb, v, true, tm);
+                     c->rst, c->tile_body, c->body_tiles, c->body_cap, c->ds, fuse, s, c->sb, v, true, tm, c->rsq);
     cudaEventRecord(c->ev_join, c->sb);
     cudaStreamWaitEvent(s, c->ev_join, 0);
   };
@@ -935,7 +945,9 @@ namespace ibm {
 
 // batched groups run the explicit stages only: dual time and bodies moving under the fluid force (whose
 // steps add the force and the body update) advance on their own streams
-bool case_batchable(const ibm_case *c) { return c->precision == IBM_PREC_FP32_BULK && !c->k.tvd2; }
+bool case_batchable(const ibm_case *c) {
+  return c->precision == IBM_PREC_FP32_BULK && !c->k.tvd2 && !c->k.quad;
+}
 
 int case_subiters(const ibm_case *c) { return c->k.dual ? c->k.subiters : 0; }
 

@@ -21,32 +21,37 @@ __global__ void __launch_bounds__(256) k_dual_f32(Consts k, PertConsts c, const 
                                 (int)blockIdx.x, sm, dp);
 }
 
-// one launch of a TVD-2 case's pseudo stage: body-tile slots [0, nb) first, then one block per tile (every
-// launch form of a TVD-2 case)
-template <int STAGE>
-__global__ void __launch_bounds__(256) k_dual_f32_tvd(Consts k, PertConsts c, const float *__restrict__ In,
+// one launch of the pseudo stage of a case with the TVD-2 reconstruction and / or the quadratic IB / ghost
+// reconstruction compiled in: body-tile slots [0, nb) first, then one block per tile (every launch form of such
+// a case)
+template <int STAGE, bool TVD, bool QUAD>
+__global__ void __launch_bounds__(256) k_dual_f32_var(Consts k, PertConsts c, const float *__restrict__ In,
                                                       float *Out32, double *D, const uint8_t *__restrict__ tag,
                                                       const int *__restrict__ sid,
                                                       const RStencil32 *__restrict__ rs,
                                                       const uint8_t *__restrict__ tile_body,
                                                       const int *__restrict__ body_tiles, int nb, DevState *ds,
-                                                      unsigned int ncfl, DualPtrs dp) {
+                                                      unsigned int ncfl, DualPtrs dp,
+                                                      const RStencilQ *__restrict__ rsq) {
   __shared__ TileSmem sm;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int b = (int)blockIdx.x;
   if (b < nb)
-    stage_tile<STAGE, true, true, false, false, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body,
-                                                      body_tiles, ds, false, ncfl, b, sm, dp);
+    stage_tile<STAGE, true, true, false, false, TVD, QUAD>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body,
+                                                           body_tiles, ds, false, ncfl, b, sm, dp, nullptr, rsq);
   else
-    stage_tile<STAGE, false, true, false, false, true>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body,
-                                                       body_tiles, ds, false, ncfl, b - nb, sm, dp);
+    stage_tile<STAGE, false, true, false, false, TVD, QUAD>(k, c, nullptr, In, Out32, D, tag, sid, rs, tile_body,
+                                                            body_tiles, ds, false, ncfl, b - nb, sm, dp, nullptr,
+                                                            rsq);
 }
 
-cudaError_t launch_dual_f32_tvd(const Consts &k, int stage, const float *In32, float *Out32, double *D,
+cudaError_t launch_dual_f32_var(const Consts &k, int stage, const float *In32, float *Out32, double *D,
                                 const double *In64, double *Out64, const double *G, double *Q0,
                                 const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
-                                const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s) {
+                                const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s,
+                                const RStencilQ *rsq) {
+  if (k.quad && !rsq) return cudaErrorInvalidValue;  // the quadratic kernels read the second probes
   const PertConsts c = pert_consts(k);
   const int nt = stage_tiles(k);
   const int nb = body_cap > 0 ? body_cap : 0;
@@ -65,10 +70,15 @@ cudaError_t launch_dual_f32_tvd(const Consts &k, int stage, const float *In32, f
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = pdl ? 1 : 0;
-#define IBM_DUAL_TVD(S) \
-  cudaLaunchKernelEx(&cfg, k_dual_f32_tvd<S>, k, c, In32, Out32, D, tag, sid, rs, tile_body, body_tiles, nb, ds, ncfl, dp)
-  const cudaError_t e = stage == 1 ? IBM_DUAL_TVD(1) : stage == 2 ? IBM_DUAL_TVD(2) : IBM_DUAL_TVD(3);
-#undef IBM_DUAL_TVD
+#define IBM_DUAL_VAR(S, T, Q)                                                                                 \
+  cudaLaunchKernelEx(&cfg, k_dual_f32_var<S, T, Q>, k, c, In32, Out32, D, tag, sid, rs, tile_body, body_tiles, nb, \
+                     ds, ncfl, dp, rsq)
+#define IBM_DUAL_VAR_S(S)                                                                                       \
+  (k.tvd2 && k.quad ? IBM_DUAL_VAR(S, true, true)                                                              \
+                    : k.tvd2 ? IBM_DUAL_VAR(S, true, false) : IBM_DUAL_VAR(S, false, true))
+  const cudaError_t e = stage == 1 ? IBM_DUAL_VAR_S(1) : stage == 2 ? IBM_DUAL_VAR_S(2) : IBM_DUAL_VAR_S(3);
+#undef IBM_DUAL_VAR_S
+#undef IBM_DUAL_VAR
   return e;
 }
 
@@ -148,10 +158,10 @@ void launch_dual_levels(const Consts &k, const double *A, double *Wn, double *G,
 void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,
                      double *Out64, const double *G, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
-                     DevState *ds, cudaStream_t s, cudaStream_t sb) {
-  if (k.tvd2) {  // the TVD-2 kernel holds plain and body tiles: one launch on the case stream
-    launch_dual_f32_tvd(k, stage, In32, Out32, D, In64, Out64, G, Q0, tag, sid, rs, tile_body, body_tiles, body_cap,
-                        ds, false, s);
+                     DevState *ds, cudaStream_t s, cudaStream_t sb, const RStencilQ *rsq) {
+  if (k.tvd2 || k.quad) {  // the variant kernel holds plain and body tiles: one launch on the case stream
+    launch_dual_f32_var(k, stage, In32, Out32, D, In64, Out64, G, Q0, tag, sid, rs, tile_body, body_tiles, body_cap,
+                        ds, false, s, rsq);
     return;
   }
   PertConsts c = pert_consts(k);

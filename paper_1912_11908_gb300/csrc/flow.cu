@@ -64,35 +64,59 @@ void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *d
 // pressure condition a linear ODE in p along the normal, integrated exactly.
 // One thread per list entry; in place on the stage array.
 // ---------------------------------------------------------------------------
+// (p, u, v, T) interpolated at a probe from the valid corners of its square
+__device__ __forceinline__ void probe_f64(const Consts &k, const double *U, int i0, int j0, int mask,
+                                          const double w[4], double qp[4]) {
+  for (int q = 0; q < 4; q++) qp[q] = 0.0;
+  for (int q = 0; q < 4; q++) {
+    if (!(mask >> q & 1)) continue;
+    long long id = cidx(k, i0 + (q & 1), j0 + (q >> 1));
+    double r = U[id], u = U[id + k.plane] / r, v = U[id + 2 * k.plane] / r;
+    double p = (k.gamma - 1.0) * (U[id + 3 * k.plane] - 0.5 * r * (u * u + v * v));
+    qp[0] += w[q] * p;
+    qp[1] += w[q] * u;
+    qp[2] += w[q] * v;
+    qp[3] += w[q] * (p / (r * k.R));
+  }
+}
+
 __device__ __forceinline__ void recon_one_f64(const Consts &k, double *U, const ibm_stencil &s, const double Vb[2],
                                               const double Ab[2], bool sup, double t) {
   if (s.mask == 0) return;
   double V[2], Acc[2];
   wall_kin(k, t, s.bx, s.by, Vb, Ab, V, Acc);  // the wall's motion at P'
-  double qp[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int q = 0; q < 4; q++) {
-    if (!(s.mask >> q & 1)) continue;
-    long long id = cidx(k, s.i0 + (q & 1), s.j0 + (q >> 1));
-    double r = U[id], u = U[id + k.plane] / r, v = U[id + 2 * k.plane] / r;
-    double p = (k.gamma - 1.0) * (U[id + 3 * k.plane] - 0.5 * r * (u * u + v * v));
-    double w = s.w[q];
-    qp[0] += w * p;
-    qp[1] += w * u;
-    qp[2] += w * v;
-    qp[3] += w * (p / (r * k.R));
-  }
-  const double ratio = s.xi_node / s.xi_probe;
-  // dp/dn = rho G with rho = p / (R T) and T fixed along the normal (Eq. 8): integrated exactly from the
-  // probe to the node, p = p_probe exp(-(xi_p - xi_n) G / (R T)), positive however coarse the grid
+  double qp[4];
+  probe_f64(k, U, s.i0, s.j0, s.mask, s.w, qp);
+  // dp/dn = rho G (Eq. 5-7)
   double G = -(s.nx * Acc[0] + s.ny * Acc[1]);
   if (sup) {
     const double ut = -(qp[1] - V[0]) * s.ny + (qp[2] - V[1]) * s.nx;
     G = G + ut * ut * s.curv;
   }
-  const double p = qp[0] * exp(-(s.xi_probe - s.xi_node) * G / (k.R * qp[3]));
-  const double u = V[0] + (qp[1] - V[0]) * ratio;
-  const double v = V[1] + (qp[2] - V[1]) * ratio;
-  const double T = qp[3];
+  double p, u, v, T;
+  if (k.quad && s.maskb != 0) {
+    // quadratic form (Sec. 4.5, Sec. 5): quadratics in the distance s along the normal through the wall
+    // condition (s = 0) and the probes at s1, s2, evaluated at the node s_n -- Lagrange for the Dirichlet
+    // velocity, a + b s + c s^2 with the wall slope b given for T (0) and p (rho G, the first probe's density)
+    double qb[4];
+    probe_f64(k, U, s.i0b, s.j0b, s.maskb, s.wb, qb);
+    const double s1 = s.xi_probe, s2 = s.xi_probe2, sn = s.xi_node;
+    const double L1 = sn * (sn - s2) / (s1 * (s1 - s2)), L2 = sn * (sn - s1) / (s2 * (s2 - s1));
+    const double m = (sn * sn - s1 * s1) / (s2 * s2 - s1 * s1);
+    const double b = qp[0] / (k.R * qp[3]) * G;
+    u = V[0] + (qp[1] - V[0]) * L1 + (qb[1] - V[0]) * L2;
+    v = V[1] + (qp[2] - V[1]) * L1 + (qb[2] - V[1]) * L2;
+    T = qp[3] + (qb[3] - qp[3]) * m;
+    p = qp[0] + (qb[0] - qp[0]) * m + b * ((sn - s1) - (s2 - s1) * m);
+  } else {
+    // linear form: rho = p / (R T) and T fixed along the normal (Eq. 8), integrated exactly from the probe to
+    // the node, p = p_probe exp(-(xi_p - xi_n) G / (R T)), positive however coarse the grid
+    const double ratio = s.xi_node / s.xi_probe;
+    p = qp[0] * exp(-(s.xi_probe - s.xi_node) * G / (k.R * qp[3]));
+    u = V[0] + (qp[1] - V[0]) * ratio;
+    v = V[1] + (qp[2] - V[1]) * ratio;
+    T = qp[3];
+  }
   const double r = p / (k.R * T);
   const long long id = cidx(k, s.cell % k.nx, s.cell / k.nx);
   U[id] = r;

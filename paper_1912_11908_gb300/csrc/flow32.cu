@@ -99,7 +99,8 @@ void launch_dt_f32(const Consts &k, const float *M, const uint8_t *tag, DevState
 // FP32 copy of every IB / ghost stencil and the cell -> stencil map used by the
 // fused reconstruction (sid must be -1 on entry)
 __global__ void k_compact_stencils(Consts k, const ibm_stencil *__restrict__ st, RStencil32 *__restrict__ rs,
-                                   int *__restrict__ sid, int cap, const DevState *__restrict__ ds) {
+                                   RStencilQ *__restrict__ rsq, int *__restrict__ sid, int cap,
+                                   const DevState *__restrict__ ds) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= min(ds->offset[4], cap)) return;
   const ibm_stencil s = st[e];
@@ -119,13 +120,14 @@ __global__ void k_compact_stencils(Consts k, const ibm_stencil *__restrict__ st,
   r.ry = pitching ? (float)(s.by - k.motion.pivot[1]) : 0.f;
   rs[e] = r;
   sid[s.cell] = e;
+  if (rsq) rsq[e] = quad_stencil(k, s);
 }
 
-void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 *rs, int *sid, int cap,
-                             const DevState *ds, cudaStream_t s) {
+void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 *rs, RStencilQ *rsq, int *sid,
+                             int cap, const DevState *ds, cudaStream_t s) {
   cudaMemsetAsync(sid, 0xff, sizeof(int) * (size_t)k.nx * k.ny, s);
   if (cap <= 0) return;
-  k_compact_stencils<<<(cap + 127) / 128, 128, 0, s>>>(k, st, rs, sid, cap, ds);
+  k_compact_stencils<<<(cap + 127) / 128, 128, 0, s>>>(k, st, rs, rsq, sid, cap, ds);
 }
 
 // A case stepped on its own: one block per tile (plain) or body-tile slot.
@@ -170,25 +172,28 @@ __global__ void __launch_bounds__(256, MINB)
                                           ncfl, b - nb, sm, DualPtrs{}, use_tma ? &tmap : nullptr);
 }
 
-// The same stage with the TVD-2 reconstruction (Sec. 2) compiled in: a case with that scheme takes this kernel
-// in every launch form (the two-stream form runs it as one launch on the case stream).
-template <int STAGE>
+// The same stage with the TVD-2 reconstruction (Sec. 2) and / or the quadratic IB / ghost reconstruction
+// (Sec. 4.5, Sec. 5) compiled in: a case with either takes this kernel in every launch form (the two-stream
+// form runs it as one launch on the case stream), so that the default kernels carry neither.
+template <int STAGE, bool TVD, bool QUAD>
 __global__ void __launch_bounds__(256, 6)
-    k_stage_f32_tvd(Consts k, PertConsts c, float *Mn, const float *__restrict__ In, float *Out, double *D,
+    k_stage_f32_var(Consts k, PertConsts c, float *Mn, const float *__restrict__ In, float *Out, double *D,
                     const uint8_t *__restrict__ tag, const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
                     const uint8_t *__restrict__ tile_body, const int *__restrict__ body_tiles, int nb, DevState *ds,
-                    bool fuse_cfl, unsigned int ncfl, const __grid_constant__ CUtensorMap tmap, int use_tma) {
+                    bool fuse_cfl, unsigned int ncfl, const __grid_constant__ CUtensorMap tmap, int use_tma,
+                    const RStencilQ *__restrict__ rsq) {
   __shared__ TileSmem sm;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int b = (int)blockIdx.x;
   if (b < nb)
-    stage_tile<STAGE, true, false, true, false, true>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, ds,
-                                                      fuse_cfl, ncfl, b, sm, DualPtrs{}, use_tma ? &tmap : nullptr);
+    stage_tile<STAGE, true, false, true, false, TVD, QUAD>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles,
+                                                           ds, fuse_cfl, ncfl, b, sm, DualPtrs{},
+                                                           use_tma ? &tmap : nullptr, rsq);
   else
-    stage_tile<STAGE, false, false, true, false, true>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles,
-                                                       ds, fuse_cfl, ncfl, b - nb, sm, DualPtrs{},
-                                                       use_tma ? &tmap : nullptr);
+    stage_tile<STAGE, false, false, true, false, TVD, QUAD>(k, c, Mn, In, Out, D, tag, sid, rs, tile_body,
+                                                            body_tiles, ds, fuse_cfl, ncfl, b - nb, sm, DualPtrs{},
+                                                            use_tma ? &tmap : nullptr, rsq);
 }
 
 int stage_tiles(const Consts &k) { return ((k.nx + TX - 1) / TX) * ((k.ny + TY - 1) / TY); }
@@ -274,10 +279,11 @@ void launch_tile_lists(const Consts &k, const uint8_t *tag, uint8_t *tile_body, 
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
                       const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                       const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
-                      cudaStream_t sb, int plain_variant, bool with_body, const CUtensorMap *tmap) {
-  if (k.tvd2) {  // the TVD-2 kernel holds plain and body tiles: one launch on the case stream
+                      cudaStream_t sb, int plain_variant, bool with_body, const CUtensorMap *tmap,
+                      const RStencilQ *rsq) {
+  if (k.tvd2 || k.quad) {  // the variant kernel holds plain and body tiles: one launch on the case stream
     launch_stage_f32_one(k, stage, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, with_body ? body_cap : 0, ds,
-                         fuse_cfl, plain_variant, tmap, false, s);
+                         fuse_cfl, plain_variant, tmap, false, s, rsq);
     return;
   }
   PertConsts c = pert_consts(k);
@@ -309,7 +315,8 @@ void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, fl
 cudaError_t launch_stage_f32_one(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
                                  const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                                  const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, int plain_variant,
-                                 const CUtensorMap *tmap, bool pdl, cudaStream_t s) {
+                                 const CUtensorMap *tmap, bool pdl, cudaStream_t s, const RStencilQ *rsq) {
+  if (k.quad && !rsq) return cudaErrorInvalidValue;  // the quadratic kernels read the second probes
   const PertConsts c = pert_consts(k);
   const int nt = stage_tiles(k);
   const int nb = body_cap > 0 ? body_cap : 0;
@@ -331,12 +338,15 @@ cudaError_t launch_stage_f32_one(const Consts &k, int stage, float *Mn, const fl
   cudaLaunchKernelEx(&cfg, k_stage_f32_one<S, MB>, k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, nb, \
                      ds, fuse_cfl, ncfl, tm, ut)
 #define IBM_ONE_V(S) (plain_variant == 1 ? IBM_ONE(S, 5) : plain_variant == 2 ? IBM_ONE(S, 4) : IBM_ONE(S, 6))
-#define IBM_TVD(S)                                                                                           \
-  cudaLaunchKernelEx(&cfg, k_stage_f32_tvd<S>, k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, nb, ds, \
-                     fuse_cfl, ncfl, tm, ut)
-  cudaError_t e = k.tvd2 ? (stage == 1 ? IBM_TVD(1) : stage == 2 ? IBM_TVD(2) : IBM_TVD(3))
-                         : (stage == 1 ? IBM_ONE_V(1) : stage == 2 ? IBM_ONE_V(2) : IBM_ONE_V(3));
-#undef IBM_TVD
+#define IBM_VAR(S, T, Q)                                                                                       \
+  cudaLaunchKernelEx(&cfg, k_stage_f32_var<S, T, Q>, k, c, Mn, In, Out, D, tag, sid, rs, tile_body, body_tiles, nb, \
+                     ds, fuse_cfl, ncfl, tm, ut, rsq)
+#define IBM_VAR_S(S) \
+  (k.tvd2 && k.quad ? IBM_VAR(S, true, true) : k.tvd2 ? IBM_VAR(S, true, false) : IBM_VAR(S, false, true))
+  cudaError_t e = k.tvd2 || k.quad ? (stage == 1 ? IBM_VAR_S(1) : stage == 2 ? IBM_VAR_S(2) : IBM_VAR_S(3))
+                                   : (stage == 1 ? IBM_ONE_V(1) : stage == 2 ? IBM_ONE_V(2) : IBM_ONE_V(3));
+#undef IBM_VAR_S
+#undef IBM_VAR
 #undef IBM_ONE_V
 #undef IBM_ONE
   return e;

@@ -455,20 +455,47 @@ __device__ __forceinline__ bool seg_crossing(const Geom &g, int kk, double px, d
   return true;
 }
 
+// quadratic form (Sec. 4.5, Sec. 5): the second probe / image point one diagonal spacing beyond the first, on the
+// same corner set and pushed out the same way while its square has no usable corner (kept out of line: it is
+// compiled into every stencil kernel, most of whose cases take the linear form)
+static __device__ __noinline__ void second_probe(const Consts &k, const uint8_t *__restrict__ tag, double bx,
+                                                 double by, double nx, double ny, double xi_probe, unsigned allowed,
+                                                 ibm_stencil &s) {
+  double xi2 = xi_probe + k.h;
+  int ib = 0, jb = 0, maskb = 0, nstepb = 0;
+  for (;;) {
+    double X = bx + xi2 * nx, Y = by + xi2 * ny;
+    maskb = interp_square(k, tag, X, Y, allowed, &ib, &jb, s.wb);
+    if (maskb != 0 || nstepb == 3) break;
+    xi2 = xi2 + k.dmin;
+    nstepb++;
+  }
+  s.i0b = ib;
+  s.j0b = jb;
+  s.maskb = maskb;
+  s.nstepb = nstepb;
+  s.xi_probe2 = xi2;
+}
+
+// the FP32 quadratic part of a record (out of line, like second_probe)
+static __device__ __noinline__ void write_quad_stencil(const Consts &k, const ibm_stencil &s, RStencilQ *out) {
+  *out = quad_stencil(k, s);
+}
+
 // The rest of one node's stencil once the closest feature (feat, region, foot point cc) and the boundary point
 // search (found_abs < inf: signed distance bsv at parameter bsu on segment bsg) are known: boundary point,
 // image / probe distance, interpolation square (Sec. 4.3-4.6), curvature at P' (Eq. 7); writes the record,
 // and with rs its compact FP32 form and the cell -> stencil map.
 __device__ __forceinline__ void stencil_tail(const Consts &k, const Geom &g, const uint8_t *__restrict__ tag,
-                                             DevState *ds, const ibm_stencil &s0, int e, double px, double py,
+                                             DevState *ds, int e, double px, double py,
                                              int feat, int region, double ccx, double ccy, double found_abs,
                                              double bsv, double bsu, int bsg, double nx, double ny,
                                              ibm_stencil *__restrict__ st, RStencil32 *__restrict__ rs,
                                              int *__restrict__ sid) {
-  const int kind = s0.kind;
+  ibm_stencil s = st[e];  // the list entry: cell and kind
+  const int kind = s.kind;
   const bool ghost = kind > 0;
   const int nv = g.nv;
-  ibm_stencil s = s0;
   double bx, by, xi_node;
   int fb;
   if (found_abs < INFINITY) {
@@ -533,6 +560,12 @@ __device__ __forceinline__ void stencil_tail(const Consts &k, const Geom &g, con
   s.xi_node = xi_node;
   s.xi_probe = xi_probe;
   for (int q = 0; q < 4; q++) s.w[q] = w[q];
+  // quadratic form (Sec. 4.5, Sec. 5): the second probe / image point one diagonal spacing beyond the first, on the
+  // same corner set and pushed out the same way while its square has no usable corner
+  s.i0b = s.j0b = s.maskb = s.nstepb = 0;
+  s.xi_probe2 = 0.0;
+  for (int q = 0; q < 4; q++) s.wb[q] = 0.0;
+  if (k.quad && mask != 0) second_probe(k, tag, bx, by, nx, ny, xi_probe, allowed, s);
   st[e] = s;
   if (rs) {
     RStencil32 r;
@@ -551,6 +584,7 @@ __device__ __forceinline__ void stencil_tail(const Consts &k, const Geom &g, con
     r.ry = pitching ? (float)(s.by - k.motion.pivot[1]) : 0.f;
     rs[e] = r;
     sid[s.cell] = e;
+    if (g.rsq) write_quad_stencil(k, s, g.rsq + e);
   }
 }
 
@@ -616,10 +650,8 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
        e0 += (int)gridDim.x * STENCIL_NODES) {
     const int e = e0 + lane / NL;
     const bool act = e < total;
-    ibm_stencil s0 = {};
-    if (act) s0 = st[e];
-    const int kind = s0.kind;
-    const int i = s0.cell % k.nx, j = s0.cell / k.nx;
+    const int cell = act ? st[e].cell : 0, kind = act ? st[e].kind : 0;
+    const int i = cell % k.nx, j = cell / k.nx;
     const double px = k.x0 + ((double)i + 0.5) * k.dx;
     const double py = k.y0 + ((double)j + 0.5) * k.dy;
     const float pxf = (float)px, pyf = (float)py;
@@ -697,8 +729,8 @@ __global__ void __launch_bounds__(128) k_stencils(Consts k, Geom g, const uint8_
     const double bsu = __shfl_sync(0xffffffffu, bs_u, win);
     const int bsg = __shfl_sync(0xffffffffu, bs_seg, win);
     if (act && gl == 0)
-      stencil_tail(k, g, tag, ds, s0, e, px, py, feat, region, ccx, ccy, found_abs, bsv, bsu, bsg, nx, ny, st,
-                   rs, sid);
+      stencil_tail(k, g, tag, ds, e, px, py, feat, region, ccx, ccy, found_abs, bsv, bsu, bsg, nx, ny, st, rs,
+                   sid);
     __syncwarp();
   }
 }

@@ -83,10 +83,12 @@ struct Consts {
   double iR, ig1;   // 1/R and 1/(gamma - 1)
   double idt_phys;  // dual time: 1/dt_phys
   int tvd2;         // face reconstruction: TVD-2 (MUSCL, minmod) instead of WENO5
+  int quad;         // IB / ghost reconstruction: quadratic along the normal (IBM_INTERP_QUADRATIC)
 };
 
 
 // geometry arrays (device)
+struct RStencilQ;
 struct Geom {
   int nv;
   const double *vref;   // 2*nv reference vertices
@@ -97,6 +99,8 @@ struct Geom {
   float *sb;            // per segment of the current pose, FP32: centre x, y and bounding radius (the stencil
                         // searches' pruning bounds, written by the pose kernels)
   int stencil_lanes;    // lanes per listed node of the stencil searches (16 or 32, from the body's size)
+  RStencilQ *rsq;       // FP32-bulk with IBM_INTERP_QUADRATIC: the quadratic part of the compact stencils (else
+                        // null), written with them
 };
 
 // The FP32 bounding circle of the segment (ax, ay) - (bx, by): centre, and half length plus a margin of 1e-5 of
@@ -309,14 +313,46 @@ struct RStencil32 {
   float rx, ry; // P' relative to the pivot of a pitching body (0 otherwise)
 };
 
+// The quadratic reconstruction's part of a node's FP32 stencil (IBM_INTERP_QUADRATIC; a second array beside
+// the RStencil32 records, read only by the kernels compiled for that form): the second probe's square, and the
+// weights of the quadratics in the distance s along the normal, with s_n the node and s1, s2 the probes
+struct RStencilQ {
+  int corner;   // state index of corner (i0b, j0b)
+  int ccell;    // interior index j0b*nx + i0b
+  int mask;     // valid corners of the second square (0: none; the node takes the linear form)
+  float w[4];
+  float L1, L2; // Lagrange weights of the probes (Dirichlet velocity): s_n (s_n - s2) / (s1 (s1 - s2)), ...
+  float m;      // (s_n^2 - s1^2) / (s2^2 - s1^2): weight of the second probe in the zero-slope quadratic
+  float dq;     // (s_n - s1) - (s2 - s1) m: the pressure's change per unit wall slope
+};
+
+// the RStencilQ of a stencil record (weights from its FP64 distances)
+__device__ __forceinline__ RStencilQ quad_stencil(const Consts &k, const ibm_stencil &s) {
+  RStencilQ q;
+  q.mask = s.maskb;
+  q.corner = s.maskb ? (int)cidx(k, s.i0b, s.j0b) : 0;
+  q.ccell = s.maskb ? s.j0b * k.nx + s.i0b : 0;
+  for (int c = 0; c < 4; c++) q.w[c] = (float)s.wb[c];
+  q.L1 = q.L2 = q.m = q.dq = 0.f;
+  if (s.maskb) {
+    const double s1 = s.xi_probe, s2 = s.xi_probe2, sn = s.xi_node;
+    const double m = (sn * sn - s1 * s1) / (s2 * s2 - s1 * s1);
+    q.L1 = (float)(sn * (sn - s2) / (s1 * (s1 - s2)));
+    q.L2 = (float)(sn * (sn - s1) / (s2 * (s2 - s1)));
+    q.m = (float)m;
+    q.dq = (float)((sn - s1) - (s2 - s1) * m);
+  }
+  return q;
+}
+
 // FP32-bulk path (flow32.cu).  The FP64 state D of this mode holds the
 // perturbation dU from the free stream (same variables as the FP32 arrays).
 void launch_abs_to_pert64(const Consts &k, double *D, cudaStream_t s);          // in place
 void launch_pert_to_abs64(const Consts &k, const double *D, double *A, cudaStream_t s);
 void launch_to_mirror(const Consts &k, const double *D, float *M, cudaStream_t s);
 void launch_dt_f32(const Consts &k, const float *M, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch);
-void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 *rs, int *sid, int cap,
-                             const DevState *ds, cudaStream_t s);
+void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 *rs, RStencilQ *rsq, int *sid,
+                             int cap, const DevState *ds, cudaStream_t s);
 // Tiles of the stage kernel whose cells or 3-cell halo hold IB / ghost nodes
 // ("body tiles"): flag per tile and a compact list (capacity body_cap).
 // has_body = false: no vertices (every tile plain; ds->bbox unused).
@@ -367,14 +403,16 @@ constexpr int PLAIN_VARIANTS = 3;
 void launch_stage_f32(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
                       const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                       const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, cudaStream_t s,
-                      cudaStream_t sb, int plain_variant, bool with_body, const CUtensorMap *tmap);
+                      cudaStream_t sb, int plain_variant, bool with_body, const CUtensorMap *tmap,
+                      const RStencilQ *rsq = nullptr);
 // The same stage as one launch on stream s: body-tile slots first, then one
 // block per tile (no second stream); pdl: launch with programmatic dependent
 // launch, so that the launch overlaps the tail of the preceding stage kernel.
 cudaError_t launch_stage_f32_one(const Consts &k, int stage, float *Mn, const float *In, float *Out, double *D,
                                  const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
                                  const int *body_tiles, int body_cap, DevState *ds, bool fuse_cfl, int plain_variant,
-                                 const CUtensorMap *tmap, bool pdl, cudaStream_t s);
+                                 const CUtensorMap *tmap, bool pdl, cudaStream_t s,
+                                 const RStencilQ *rsq = nullptr);
 // Tensor maps of the FP32 stage inputs arrays[0..2] (pitch x rows x 4 planes)
 // for the TMA staging of interior tiles (tmap above); false if the driver
 // offers no encoder or the grid is too small for a box.
@@ -413,7 +451,7 @@ cudaError_t launch_step_f32(const Consts &k, float *M, float *F1, float *F2, dou
 void launch_dual_f32(const Consts &k, int stage, const float *In32, float *Out32, double *D, const double *In64,
                      double *Out64, const double *G, double *Q0, const uint8_t *tag, const int *sid,
                      const RStencil32 *rs, const uint8_t *tile_body, const int *body_tiles, int body_cap,
-                     DevState *ds, cudaStream_t s, cudaStream_t sb);
+                     DevState *ds, cudaStream_t s, cudaStream_t sb, const RStencilQ *rsq = nullptr);
 // Self-check of the dual update's integer-bit FP32 <-> FP64 conversions
 // against the hardware conversions (synchronous, default stream).
 cudaError_t check_float_conversions(unsigned long long *checked, unsigned long long *mismatched);
@@ -422,13 +460,16 @@ cudaError_t check_float_conversions(unsigned long long *checked, unsigned long l
 // (BDF2), or G = -W^n / dt on the first step (BDF1), over the whole padded
 // state (4 planes).
 void launch_dual_levels(const Consts &k, const double *A, double *Wn, double *G, const DevState *ds, cudaStream_t s);
-// The same pseudo stage of a TVD-2 case as one launch on stream s (body-tile
-// slots first); pdl: chained to the previous launch by programmatic dependent
-// launch.  (Other cases take launch_dual_f32_batch_one with a table of one.)
-cudaError_t launch_dual_f32_tvd(const Consts &k, int stage, const float *In32, float *Out32, double *D,
+// The same pseudo stage of a case with TVD-2 or the quadratic reconstruction
+// as one launch on stream s (body-tile slots first); pdl: chained to the
+// previous launch by programmatic dependent launch; rsq: the quadratic part
+// of the compact stencils (required with the quadratic form).  (Other cases
+// take launch_dual_f32_batch_one with a table of one.)
+cudaError_t launch_dual_f32_var(const Consts &k, int stage, const float *In32, float *Out32, double *D,
                                 const double *In64, double *Out64, const double *G, double *Q0,
                                 const uint8_t *tag, const int *sid, const RStencil32 *rs, const uint8_t *tile_body,
-                                const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s);
+                                const int *body_tiles, int body_cap, DevState *ds, bool pdl, cudaStream_t s,
+                                const RStencilQ *rsq = nullptr);
 // One member case of a group's block table (the request loop's batched
 // stages: body-tile entries rebuild IB and ghost nodes from rs / sid while
 // they load a tile, plain-tile entries cover the other tiles).

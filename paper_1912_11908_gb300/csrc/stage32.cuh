@@ -299,9 +299,32 @@ __device__ __forceinline__ void wall_bc(const PertConsts &c, const RStencil32 &s
   q[3] = qp[3];
 }
 
-template <bool CG>
+// The quadratic form (Sec. 4.5, Sec. 5; IBM_INTERP_QUADRATIC) of wall_bc: quadratics in the distance along the
+// normal through the wall condition and the probes' values qp (first) and qb (second) -- the Lagrange weights
+// for the Dirichlet velocity, zero wall slope for T', wall slope rho G for p' with the first probe's density --
+// in perturbation form (differences of perturbations are differences of the variables)
+__device__ __forceinline__ void wall_bc_quad(const PertConsts &c, const RStencil32 &s, const RStencilQ &t,
+                                             const float qp[4], const float qb[4], const float *wm, float q[4]) {
+  const float om = wm[5], al = wm[6];
+  const float Vx = wm[0] - om * s.ry, Vy = wm[1] + om * s.rx;
+  const float Ax = wm[2] - al * s.ry - om * om * s.rx, Ay = wm[3] + al * s.rx - om * om * s.ry;
+  float G = -(s.nx * Ax + s.ny * Ay);
+  if (wm[4] != 0.f) {
+    const float ut = -(qp[1] - Vx) * s.ny + (qp[2] - Vy) * s.nx;
+    G = G + ut * ut * s.curv;
+  }
+  const float b = (c.R + qp[0]) / (c.R * (1.f + qp[3])) * G;
+  q[0] = qp[0] + (qb[0] - qp[0]) * t.m + b * t.dq;
+  q[1] = Vx + (qp[1] - Vx) * t.L1 + (qb[1] - Vx) * t.L2;
+  q[2] = Vy + (qp[2] - Vy) * t.L1 + (qb[2] - Vy) * t.L2;
+  q[3] = qp[3] + (qb[3] - qp[3]) * t.m;
+}
+
+// An IB node outside a tile's loaded region, rebuilt from its own stencil (QUAD: and its second probe)
+template <bool CG, bool QUAD = false>
 static __device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts &c, const float *U,
-                                               const RStencil32 &s, const float *wm, float q[4]) {
+                                               const RStencil32 &s, const RStencilQ *t, const float *wm,
+                                               float q[4]) {
   float qp[4] = {0.f, 0.f, 0.f, 0.f};
   for (int b = 0; b < 4; b++) {
     if (!(s.mask >> b & 1)) continue;  // bits 0-3: valid corners (bit 4: IB node)
@@ -309,7 +332,18 @@ static __device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts
     raw_prim<CG>(c, U, s.corner + (b & 1) + (b >> 1) * k.pitch, k.plane, cq);
     for (int v = 0; v < 4; v++) qp[v] += s.w[b] * cq[v];
   }
-  wall_bc(c, s, qp, wm, q);
+  if (QUAD && t->mask) {
+    float qb[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int b = 0; b < 4; b++) {
+      if (!(t->mask >> b & 1)) continue;
+      float cq[4];
+      raw_prim<CG>(c, U, t->corner + (b & 1) + (b >> 1) * k.pitch, k.plane, cq);
+      for (int v = 0; v < 4; v++) qb[v] += t->w[b] * cq[v];
+    }
+    wall_bc_quad(c, s, *t, qp, qb, wm, q);
+  } else {
+    wall_bc(c, s, qp, wm, q);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -337,14 +371,16 @@ static __device__ __noinline__ void rebuild_ib(const Consts &k, const PertConsts
 // sm: the block's shared memory.
 // TVD: the second-order TVD reconstruction in place of WENO5 (Sec. 2), compiled into its own kernels so that
 // the WENO5 kernels carry no branch for it.
-template <int STAGE, bool BODY, bool DUAL = false, bool TMA = false, bool PERSIST = false, bool TVD = false>
+template <int STAGE, bool BODY, bool DUAL = false, bool TMA = false, bool PERSIST = false, bool TVD = false,
+          bool QUAD = false>
 __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c, float *Mn,
                                            const float *__restrict__ In, float *Out, double *D,
                                            const uint8_t *__restrict__ tag,
                                            const int *__restrict__ sid, const RStencil32 *__restrict__ rs,
                                            const uint8_t *__restrict__ tile_body, const int *__restrict__ body_tiles,
                                            DevState *ds, bool fuse_cfl, unsigned int ncfl, int blk, TileSmem &sm,
-                                           const DualPtrs &dp = DualPtrs{}, const CUtensorMap *tmap = nullptr) {
+                                           const DualPtrs &dp = DualPtrs{}, const CUtensorMap *tmap = nullptr,
+                                           const RStencilQ *__restrict__ rsq = nullptr) {
   static_assert(!TMA || 4 * HY * TMA_W <= 2 * (NFX + NFY), "TMA box must fit in the face-state storage");
   float *s_face = sm.face;
   unsigned long long &s_mbar = sm.mbar;
@@ -533,8 +569,30 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
             } else {
               // corner outside the loaded region: fluid value, or an IB node rebuilt from its own stencil
               const int e2 = pass == 1 ? sid[cn] : -1;
-              if (!k.ib_advance && e2 >= 0 && (rs[e2].mask & 15)) rebuild_ib<PERSIST>(k, c, In, rs[e2], wm, v4);
+              if (!k.ib_advance && e2 >= 0 && (rs[e2].mask & 15))
+                rebuild_ib<PERSIST, QUAD>(k, c, In, rs[e2], QUAD ? rsq + e2 : nullptr, wm, v4);
               else raw_prim<PERSIST>(c, In, st.corner + (cq & 1) + (cq >> 1) * k.pitch, P, v4);
+            }
+          }
+        }
+        // quadratic form: the same lane also takes its corner of the second probe's square
+        const RStencilQ *tq = nullptr;
+        float v4b[4] = {0.f, 0.f, 0.f, 0.f};
+        if (QUAD && r < nrb && node) {
+          tq = rsq + s_rbe[r];
+          if (tq->mask >> cq & 1) {
+            const int cn = tq->ccell + (cq & 1) + (cq >> 1) * k.nx;
+            const int la = cn % k.nx - (i0 - NG), lb = cn / k.nx - (j0 - NG);
+            if (la >= 0 && la < HX && lb >= 0 && lb < HY) {
+              v4b[0] = sq[3][lb][la];
+              v4b[1] = sq[1][lb][la];
+              v4b[2] = sq[2][lb][la];
+              v4b[3] = sT[lb][la];
+            } else {
+              const int e2 = pass == 1 ? sid[cn] : -1;
+              if (!k.ib_advance && e2 >= 0 && (rs[e2].mask & 15))
+                rebuild_ib<PERSIST, QUAD>(k, c, In, rs[e2], rsq + e2, wm, v4b);
+              else raw_prim<PERSIST>(c, In, tq->corner + (cq & 1) + (cq >> 1) * k.pitch, P, v4b);
             }
           }
         }
@@ -548,11 +606,23 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
             if (mask >> j & 1) qp[v] += wj * x;
           }
         }
+        float qb[4] = {0.f, 0.f, 0.f, 0.f};
+        if (QUAD) {
+          const unsigned int maskb = tq ? (unsigned int)tq->mask : 0u;
+          for (int j = 0; j < 4; j++) {
+            const float wj = tq ? tq->w[j] : 0.f;
+            for (int v = 0; v < 4; v++) {
+              const float x = __shfl_sync(0xffffffffu, v4b[v], lane0 + j);
+              if (maskb >> j & 1) qb[v] += wj * x;
+            }
+          }
+        }
         if (!node || cq != 0) continue;
         const RStencil32 &st = s_rs[r];
         const int m = s_rbm[r], a = m % HX, b = m / HX;
         float q[4];
-        wall_bc(c, st, qp, wm, q);
+        if (QUAD && tq->mask) wall_bc_quad(c, st, *tq, qp, qb, wm, q);
+        else wall_bc(c, st, qp, wm, q);
         sq[0][b][a] = (q[0] - c.R * q[3]) / (c.R * (1.f + q[3]));
         sq[1][b][a] = q[1];
         sq[2][b][a] = q[2];

@@ -36,7 +36,8 @@ class ibm_flow(ctypes.Structure):
                 ("prandtl", ctypes.c_double), ("cfl", ctypes.c_double), ("uinf", ctypes.c_double * 2),
                 ("dt_fixed", ctypes.c_double), ("ref_len", ctypes.c_double), ("precision", ctypes.c_int),
                 ("time_scheme", ctypes.c_int), ("subiters", ctypes.c_int), ("ib_mode", ctypes.c_int),
-                ("dt_phys", ctypes.c_double), ("cfl_tau", ctypes.c_double), ("scheme", ctypes.c_int)]
+                ("dt_phys", ctypes.c_double), ("cfl_tau", ctypes.c_double), ("scheme", ctypes.c_int),
+                ("ib_interp", ctypes.c_int)]
 
 
 class ibm_motion(ctypes.Structure):
@@ -50,6 +51,7 @@ STENCIL_DTYPE = np.dtype([
     ("mask", "<i4"), ("nstep", "<i4"), ("kind", "<i4"),
     ("nx", "<f8"), ("ny", "<f8"), ("bx", "<f8"), ("by", "<f8"),
     ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (4,)), ("curv", "<f8"),
+    ("i0b", "<i4"), ("j0b", "<i4"), ("maskb", "<i4"), ("nstepb", "<i4"), ("xi_probe2", "<f8"), ("wb", "<f8", (4,)),
 ])
 
 class ibm_grid3d(ctypes.Structure):
@@ -196,6 +198,7 @@ def marshal(spec):
     fl.cfl_tau = spec.get("cfl_tau", 0.8)
     fl.ib_mode = spec.get("ib_mode", W.IB_REBUILD)
     fl.scheme = spec.get("scheme", W.SCHEME_WENO5)
+    fl.ib_interp = spec.get("ib_interp", W.INTERP_LINEAR)
     mo = ibm_motion()
     mo.kind = spec.get("motion", W.MOTION_STATIC)
     mo.amp[0], mo.amp[1] = spec.get("amp", (0.0, 0.0))

@@ -60,7 +60,7 @@ def test_tags_lists_stencils_bit_exact(ibm, orc, name):
     counts = g.counts()
     assert [int(c) for c in counts] == [len(o.stencils(k)) for k in range(4)]
     gs, os_ = g.stencils(), _oracle_stencils(o)
-    assert gs.dtype.itemsize == os_.dtype.itemsize == 120
+    assert gs.dtype.itemsize == os_.dtype.itemsize == 176
     assert gs.tobytes() == os_.tobytes()
 
 

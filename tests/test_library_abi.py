@@ -99,7 +99,8 @@ def test_header_constants_match_the_binding(ibm):
              "PREC_FP32_BULK": "IBM_PREC_FP32_BULK", "TIME_RK3": "IBM_TIME_RK3", "TIME_DUAL": "IBM_TIME_DUAL",
              "BC_FREESTREAM": "IBM_BC_FREESTREAM", "BC_OUTFLOW": "IBM_BC_OUTFLOW", "BC_PERIODIC": "IBM_BC_PERIODIC",
              "IB_REBUILD": "IBM_IB_REBUILD", "IB_ADVANCE": "IBM_IB_ADVANCE", "MOTION_PITCH": "IBM_MOTION_PITCH",
-             "SCHEME_WENO5": "IBM_SCHEME_WENO5", "SCHEME_TVD2": "IBM_SCHEME_TVD2"}
+             "SCHEME_WENO5": "IBM_SCHEME_WENO5", "SCHEME_TVD2": "IBM_SCHEME_TVD2",
+             "INTERP_LINEAR": "IBM_INTERP_LINEAR", "INTERP_QUADRATIC": "IBM_INTERP_QUADRATIC"}
     for py, c in pairs.items():
         assert getattr(W, py) == h[c], py
     for name in ("IBM_3D_TAGS", "IBM_3D_COUNTS", "IBM_3D_NODES", "IBM_3D_CLOSEST"):
@@ -120,6 +121,9 @@ def test_struct_layouts_match_the_header(ibm, tmp_path):
         lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (name, name))
         for f in cls._fields_:
             lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    for f in ibm.STENCIL_DTYPE.names:  # the stencil record is read into a numpy structured array
+        lines.append('  printf("ibm_stencil.%s %%zu\\n", offsetof(ibm_stencil, %s));' % (f, f))
+    lines.append('  printf("ibm_stencil %zu\\n", sizeof(ibm_stencil));')
     lines.append("  return 0;\n}")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -130,13 +134,18 @@ def test_struct_layouts_match_the_header(ibm, tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for f in cls._fields_:
             assert int(got["%s.%s" % (name, f[0])]) == getattr(cls, f[0]).offset, (name, f[0])
+    assert int(got["ibm_stencil"]) == ibm.STENCIL_DTYPE.itemsize
+    for f in ibm.STENCIL_DTYPE.names:
+        assert int(got["ibm_stencil.%s" % f]) == ibm.STENCIL_DTYPE.fields[f][1], f
 
 
 def test_unknown_reconstruction_rejected(ibm):
-    """ibm_flow.scheme other than WENO5 / TVD-2 is refused by the library (no silent default)."""
+    """ibm_flow.scheme other than WENO5 / TVD-2, and ib_interp other than linear / quadratic, are refused by
+    the library (no silent default)."""
     L = ibm.lib()
-    verts, geo, gr, fl, mo = ibm.marshal(dict(W.cylinder_m02_re40(64, 32), scheme=7))
-    h = ctypes.c_void_p()
-    st = L.ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), None,
-                           ctypes.byref(h))
-    assert st == ibm.IBM_EINVAL and not h.value
+    for bad in (dict(scheme=7), dict(ib_interp=5), dict(ib_interp=-1)):
+        verts, geo, gr, fl, mo = ibm.marshal(dict(W.cylinder_m02_re40(64, 32), **bad))
+        h = ctypes.c_void_p()
+        st = L.ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), None,
+                               ctypes.byref(h))
+        assert st == ibm.IBM_EINVAL and not h.value, bad
