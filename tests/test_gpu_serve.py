@@ -145,6 +145,31 @@ def test_batched_groups_against_oracle(orc):
         srv.close()
 
 
+def test_tvd2_and_quadratic_requests_in_a_batched_mix():
+    """Requests the group kernels are not compiled for (TVD-2, the quadratic reconstruction) run on their own
+    streams beside batched groups, and give the bits they give alone."""
+    base = [s for s in _specs(6) if s["time_scheme"] == W.TIME_RK3][:3]
+    odd = [dict(base[0], scheme=W.SCHEME_TVD2, name="tvd2"), dict(base[1], ib_interp=W.INTERP_QUADRATIC, name="quad"),
+           dict(base[2], scheme=W.SCHEME_TVD2, ib_interp=W.INTERP_QUADRATIC, name="tvd2_quad")]
+    specs = base + odd
+    ref = [_alone(s, STEPS) for s in specs]
+    srv = ibm.Server(max_active=6, steps_per_chunk=7)
+    try:
+        ids = [srv.submit(s, STEPS) for s in specs]
+        _drain(srv, cap=6)
+        for q, (rid, (f, t), spec) in enumerate(zip(ids, ref, specs)):
+            r = srv.poll(rid)
+            assert r["state"] == ibm.REQ_DONE and r["status"] == 0, r
+            if q >= len(base):  # on its own stream: the kernels of the case alone
+                np.testing.assert_array_equal(r["forces"], f)
+                assert r["t"] == t
+            else:
+                _same(r, f, t, MODES[0], spec)
+        assert srv.stats()["group_steps"] > 0
+    finally:
+        srv.close()
+
+
 def test_batched_group_of_many_cases():
     """A full group (more cases than one group holds) of equal-size requests, batched vs alone."""
     # 64x64 and 128x64 grids share a size class: 30 cases fill one group and start a second
