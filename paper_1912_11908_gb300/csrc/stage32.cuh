@@ -688,33 +688,37 @@ __device__ __forceinline__ void stage_tile(const Consts &k, const PertConsts &c,
     const float *lp = xdir ? &sq[v][NG + line][0] : &sq[v][0][NG + line];
     const int ls = xdir ? 1 : HX;  // stride along the line
     const int p0 = 2 + 9 * half;
+    // the indicators are written as e_k = eps + beta_k = [eps + 13/12 d2^2] + (b_k / 2)^2: eps rides in the
+    // sliding 13/12 d2^2 terms and the first-difference combinations are halved, so each e_k is one FMA
+    const float eps = 1e-6f;
     float f0 = lp[(p0 - 2) * ls], f1 = lp[(p0 - 1) * ls], f2 = lp[p0 * ls], f3 = lp[(p0 + 1) * ls];
     float d2m = f0 - 2.f * f1 + f2, d2c = f1 - 2.f * f2 + f3;  // second differences centred at c - 1 and c
-    float am = (13.f / 12.f) * d2m * d2m, ac = (13.f / 12.f) * d2c * d2c;
+    float am = fmaf((13.f / 12.f) * d2m, d2m, eps), ac = fmaf((13.f / 12.f) * d2c, d2c, eps);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
       const int pc = p0 + i;
       const float f4 = lp[(pc + 2) * ls];
-      const float d2p = f2 - 2.f * f3 + f4, ap = (13.f / 12.f) * d2p * d2p;
+      const float d2p = f2 - 2.f * f3 + f4, ap = fmaf((13.f / 12.f) * d2p, d2p, eps);
       const float gm = f2 - f1, g0 = f3 - f2;
-      const float bb0 = d2m + 2.f * gm, bb1 = gm + g0, bb2 = d2p - 2.f * g0;
-      const float eps = 1e-6f;
-      const float e0 = eps + (am + 0.25f * bb0 * bb0), e1 = eps + (ac + 0.25f * bb1 * bb1),
-                  e2 = eps + (ap + 0.25f * bb2 * bb2);
+      const float hb0 = fmaf(0.5f, d2m, gm), hb1 = 0.5f * (gm + g0), hb2 = fmaf(0.5f, d2p, -g0);
+      const float e0 = fmaf(hb0, hb0, am), e1 = fmaf(hb1, hb1, ac), e2 = fmaf(hb2, hb2, ap);
       const float e01 = e0 * e1, e12 = e1 * e2, e02 = e0 * e2;
       const float s01 = e01 * e01, s12 = e12 * e12, s02 = e02 * e02;
-      // left state at the cell's right face: weights (0.1, 0.6, 0.3) / e_k^2
-      const float l0 = 2.f * f0 - 7.f * f1 + 11.f * f2;
-      const float l1 = -f1 + 5.f * f2 + 2.f * f3;
-      const float l2 = 2.f * f2 + 5.f * f3 - f4;
-      const float la0 = 0.1f * s12, la1 = 0.6f * s02, la2 = 0.3f * s01;
-      const float qL = __fdividef(la0 * l0 + la1 * l1 + la2 * l2, 6.f * (la0 + la1 + la2));
+      // left state at the cell's right face: the candidates (2 f0 - 7 f1 + 11 f2, -f1 + 5 f2 + 2 f3,
+      // 2 f2 + 5 f3 - f4) / 6 with the linear weights (0.1, 0.6, 0.3) folded into their coefficients, the
+      // nonlinear weights d_k / e_k^2 cleared of their common denominator (s12 for k = 0, s02, s01)
+      const float hf2 = 0.5f * f2;
+      const float l0 = (1.f / 30.f) * f0 - (7.f / 60.f) * f1 + (11.f / 60.f) * f2;
+      const float l1 = fmaf(-0.1f, f1, fmaf(0.2f, f3, hf2));
+      const float l2 = 0.1f * f2 + 0.25f * f3 - 0.05f * f4;
+      const float qL = __fdividef(fmaf(s12, l0, fmaf(s02, l1, s01 * l2)),
+                                  fmaf(0.1f, s12, fmaf(0.6f, s02, 0.3f * s01)));
       // right state at the cell's left face: mirrored window, indicators reversed
-      const float r0 = 2.f * f4 - 7.f * f3 + 11.f * f2;
-      const float r1 = -f3 + 5.f * f2 + 2.f * f1;
-      const float r2 = 2.f * f2 + 5.f * f1 - f0;
-      const float ra0 = 0.1f * s01, ra1 = 0.6f * s02, ra2 = 0.3f * s12;
-      const float qR = __fdividef(ra0 * r0 + ra1 * r1 + ra2 * r2, 6.f * (ra0 + ra1 + ra2));
+      const float r0 = (1.f / 30.f) * f4 - (7.f / 60.f) * f3 + (11.f / 60.f) * f2;
+      const float r1 = fmaf(-0.1f, f3, fmaf(0.2f, f1, hf2));
+      const float r2 = 0.1f * f2 + 0.25f * f1 - 0.05f * f0;
+      const float qR = __fdividef(fmaf(s01, r0, fmaf(s02, r1, s12 * r2)),
+                                  fmaf(0.1f, s01, fmaf(0.6f, s02, 0.3f * s12)));
       if (xdir) {
         if (pc - 2 <= TX) fLx[v][line][pc - 2] = qL;  // face between pc and pc+1
         if (pc >= 3) fRx[v][line][pc - 3] = qR;        // face between pc-1 and pc
