@@ -87,16 +87,15 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
   }
   const float ics = 1.f / cs;
   const float ML = unL * ics, MR = unR * ics;
-  const float aL = ML >= 0.f ? 1.f : 0.f;
-  const float aR = MR >= 0.f ? 0.f : 1.f;
+  // the split functions' subsonic / supersonic branches as selects: alpha = 1 (0) for M >= 0 (< 0) on the
+  // left, the reverse on the right; beta = -1 subsonic, 0 supersonic
   const bool subL = fabsf(ML) < 1.f, subR = fabsf(MR) < 1.f;
-  const float bL = subL ? -1.f : 0.f, bR = subR ? -1.f : 0.f;
   const float MpL = 0.25f * (ML + 1.f) * (ML + 1.f);
   const float MmR = -0.25f * (MR - 1.f) * (MR - 1.f);
-  const float CVL = aL * (1.f + bL) * ML - bL * MpL;
-  const float CVR = aR * (1.f + bR) * MR - bR * MmR;
+  const float CVL = subL ? MpL : fmaxf(ML, 0.f);
+  const float CVR = subR ? MmR : fminf(MR, 0.f);
   const float sq = sqrtf(0.5f * (ML * ML + MR * MR)) - 1.f;
-  const float Mh = 0.25f * bL * bR * sq * sq;
+  const float Mh = subL && subR ? 0.25f * sq * sq : 0.f;
   const float dp = ppL - ppR, adp = fabsf(dp);
   const float ic2 = 0.5f * ics * ics;
   const float MhP = Mh * (1.f - (dp + adp) * ic2 * irL);
@@ -107,19 +106,17 @@ __device__ __forceinline__ void ldfss_pert(const PertConsts &c, float drL, float
     // pressure split with the physical face Mach numbers
     const float icb = 1.f / cb;
     const float pML = unL * icb, pMR = unR * icb;
-    const float paL = pML >= 0.f ? 1.f : 0.f, paR = pMR >= 0.f ? 0.f : 1.f;
     const bool psL = fabsf(pML) < 1.f, psR = fabsf(pMR) < 1.f;
-    const float pbL = psL ? -1.f : 0.f, pbR = psR ? -1.f : 0.f;
     const float PpL = 0.25f * (pML + 1.f) * (pML + 1.f) * (2.f - pML);
     const float PmR = 0.25f * (pMR - 1.f) * (pMR - 1.f) * (2.f + pMR);
-    DL = paL * (1.f + pbL) - pbL * PpL;
-    DR = paR * (1.f + pbR) - pbR * PmR;
+    DL = psL ? PpL : (pML >= 0.f ? 1.f : 0.f);
+    DR = psR ? PmR : (pMR >= 0.f ? 0.f : 1.f);
     Dm1 = (psL && psR) ? 0.25f * (pMR - pML) * (pMR * pMR + pMR * pML + pML * pML - 3.f) : (DL + DR - 1.f);
   } else {
     const float PpL = MpL * (2.f - ML);
     const float PmR = -MmR * (2.f + MR);
-    DL = aL * (1.f + bL) - bL * PpL;
-    DR = aR * (1.f + bR) - bR * PmR;
+    DL = subL ? PpL : (ML >= 0.f ? 1.f : 0.f);
+    DR = subR ? PmR : (MR >= 0.f ? 0.f : 1.f);
     Dm1 = (subL && subR) ? 0.25f * (MR - ML) * (MR * MR + MR * ML + ML * ML - 3.f) : (DL + DR - 1.f);
   }
   const float mL = rL * cs * Cp, mR = rR * cs * Cm;
