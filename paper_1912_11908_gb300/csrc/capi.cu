@@ -62,6 +62,7 @@ struct ibm_case {
   // force on sf, beside the tile lists and dt on the case stream; joined before the stages
   cudaStream_t sf = nullptr;
   cudaEvent_t ev_tags = nullptr, ev_sten = nullptr, ev_force = nullptr;
+  StageBatch *one = nullptr;  // FP32-bulk dual time: the one-case block table of its pseudo-stage launches
   bool geo_forked = false;   // stencils in flight on sb since the last classification
   bool force_forked = false; // force in flight on sf
   int cap = 0;
@@ -360,6 +361,7 @@ extern "C" size_t ibm_case_device_bytes(const ibm_geometry *geo, const ibm_grid 
 // retired while other cases run.
 static void free_case(ibm_case *c) {
   if (!c) return;
+  delete c->one;
   if (c->stage64) cudaFreeAsync(c->stage64, c->stream);
   if (c->arena) cudaFreeAsync(c->arena, c->stream);
   delete c->hds;
@@ -649,18 +651,24 @@ static int enqueue_step(ibm_case *c) {
       float *fin[3] = {c->M, c->F1, c->F2};
       float *fout[3] = {c->F1, c->F2, c->M};
       // one launch per pseudo stage: the block-table kernel of the request loop with this case alone in the
-      // table (so that a case gives the same bits alone and in a group), TVD-2 its own kernel
-      StageBatch *one = nullptr;
+      // table (so that a case gives the same bits alone and in a group); TVD-2 and the quadratic reconstruction
+      // their own kernels.  The table (kernel parameters; its pointers fixed for the case's life) is built once.
+      const StageBatch *one = nullptr;
       if (c->stage_launch > 0 && !c->k.tvd2 && !c->k.quad) {
-        StageCase sc;
-        case_stage_desc(c, &sc);
-        one = new StageBatch();
-        build_stage_batch(&sc, 1, one);
+        if (!c->one) {
+          StageCase sc;
+          case_stage_desc(c, &sc);
+          c->one = new (std::nothrow) StageBatch();
+          if (c->one) build_stage_batch(&sc, 1, c->one);
+        }
+        one = c->one;
       }
       for (int it = 0; it < c->k.subiters; it++)
         for (int st = 1; st <= 3; st++) {
           prof_mark(c, 0, true);
-          if (c->stage_launch > 0) {  // one launch per pseudo stage (form 2: chained by programmatic launch)
+          // one launch per pseudo stage (form 2: chained by programmatic launch); the two-stream form otherwise,
+          // and if the table could not be allocated
+          if (c->stage_launch > 0 && (one || c->k.tvd2 || c->k.quad)) {
             if (one)
               launch_dual_f32_batch_one(*one, st, 0, c->stage_launch == 2, s);
             else
@@ -680,7 +688,6 @@ static int enqueue_step(ibm_case *c) {
           }
           prof_mark(c, 0, false);
         }
-      delete one;
       launch_dual_end(c->k, c->ds, s);
       return nl + 1;
     }
