@@ -686,7 +686,37 @@ def cpu_baseline(args, cells_gpu=None, sample_s=10.0, max_steps=400):
     return {"value": cells * 3 * n / t / 1e6, "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
             "sample": "%d RK3 steps of %s after 1 warm-up step (%.1f s)" % (n, spec["name"], t),
             "cpu_model": _cpu_model(), "nproc": os.cpu_count(),
-            "single_core": _oracle_single_core(args.workload)}
+            "single_core": _oracle_single_core(args.workload),
+            "geometry3d_single_core": None if args.skip_geometry3d else _oracle_geometry3d_single_core()}
+
+
+def _oracle_geometry3d_single_core(n=40):
+    """The oracle's 3-D pre-processing of Appendix A's sphere (1200 triangles) in n^3 lattice nodes on one host
+    core (OMP_NUM_THREADS=1 in a child process): classification, tags, ordered lists, closest features and
+    pseudo-normals of the listed nodes, as the device path computes them; None if it fails."""
+    code = ("import sys, time; sys.path.insert(0, %r)\n"
+            "import numpy as np, oracle\n"
+            "from paper_1912_11908_gb300 import workloads as W\n"
+            "oracle.build()\n"
+            "v, t = W.uv_sphere(21, 30, 0.35, (0.5, 0.5, 0.5))\n"
+            "ax = (np.arange(%d) + 0.5) / %d\n"
+            "Z, Y, X = np.meshgrid(ax, ax, ax, indexing='ij')\n"
+            "pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)\n"
+            "t0 = time.perf_counter()\n"
+            "solid = oracle.classify_points_3d(v, t, pts).reshape(%d, %d, %d)\n"
+            "flat = oracle.tags_3d(solid).ravel()\n"
+            "nodes = np.concatenate([np.nonzero(flat == k)[0] for k in (2, 3, 4, 5)])\n"
+            "oracle.closest_3d(v, t, pts[nodes])\n"
+            "print(time.perf_counter() - t0, len(nodes), len(t))\n") % (ROOT, n, n, n, n, n)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        sec, nodes, ntri = out.stdout.split()
+        return {"workload": "Appendix A sphere, %s triangles, %d^3 lattice nodes" % (ntri, n), "s": float(sec),
+                "listed_nodes": int(nodes), "cores": 1,
+                "stages": "classification, tags, lists, closest features and pseudo-normals"}
+    except Exception:
+        return None
 
 
 def _cpu_model():
