@@ -462,10 +462,12 @@ ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, in
  * a request gives the same result alone and in any mix.
  *
  * Batched mode (default) for FP32-bulk requests (explicit RK3 with any
- * motion, including a body under the fluid force, or dual time; not TVD-2):
+ * motion, including a body under the fluid force, and either reconstruction
+ * and IB form; dual time with WENO5 and the linear IB form):
  * the requests admitted in one pass form groups of up to 24 cases of similar
- * size (grids within a factor four in cells), equal step counts and the same
- * time scheme (dual time: equal sub-iteration counts).  One step of a group is
+ * size (grids within a factor four in cells), equal step counts, the same
+ * time scheme (dual time: equal sub-iteration counts) and the same scheme and
+ * IB form.  One step of a group is
  * one CUDA graph: the per-case work before the stages (re-classification of
  * moving bodies, the force and acceleration of Eq. 10, dt, or the rotation of
  * the dual-time levels) on the cases' streams; per RK stage, or per pseudo
@@ -478,9 +480,9 @@ ibm_status ibm_tag_nodes_noalloc(const ibm_grid *grid, const double *d_verts, in
  * bodies do not move under the fluid force (one block per tile, or a
  * persistent grid striding over the table) is picked by timing the candidates
  * on the group, once per size class and membership size.  Other requests
- * (FP64, TVD-2), and all requests when batching is off, advance on their own
- * streams as described above.  Results do not depend on the mix; they are
- * bit-identical to a case stepped alone on the own-stream path and, for
+ * (FP64; dual time with TVD-2 or the quadratic IB form), and all requests
+ * when batching is off, advance on their own streams as described above.
+ * Results do not depend on the mix; they are bit-identical to a case stepped alone on the own-stream path and, for
  * dual-time requests, in a group; explicit requests in a group are equal up
  * to FP32 rounding (the group's stage kernel is compiled separately).
  *

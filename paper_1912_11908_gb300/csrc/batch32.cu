@@ -16,7 +16,9 @@ namespace ibm {
 // Launched with programmatic dependent launch, its blocks are resident while
 // the previous stage's last blocks finish (they wait at the top for it to
 // complete).
-template <int STAGE>
+// TVD / QUAD: the TVD-2 reconstruction and / or the quadratic IB / ghost reconstruction compiled in (a group
+// holds cases of one variant)
+template <int STAGE, bool TVD, bool QUAD>
 __global__ void __launch_bounds__(256, 6) k_stage_f32_batch_one(const __grid_constant__ StageBatch b) {
   __shared__ TileSmem sm;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -32,11 +34,15 @@ __global__ void __launch_bounds__(256, 6) k_stage_f32_batch_one(const __grid_con
     const float *In = STAGE == 1 ? sc.M : (STAGE == 2 ? sc.F1 : sc.F2);
     float *Out = STAGE == 1 ? sc.F1 : (STAGE == 2 ? sc.F2 : nullptr);
     if (body)
-      stage_tile<STAGE, true>(sc.k, sc.c, sc.M, In, Out, sc.D, sc.tag, sc.sid, sc.rs, sc.tile_body, sc.body_tiles,
-                              sc.ds, sc.fuse_cfl != 0, sc.ncfl, ee - start[q], sm);
+      stage_tile<STAGE, true, false, false, false, TVD, QUAD>(sc.k, sc.c, sc.M, In, Out, sc.D, sc.tag, sc.sid, sc.rs,
+                                                              sc.tile_body, sc.body_tiles, sc.ds, sc.fuse_cfl != 0,
+                                                              sc.ncfl, ee - start[q], sm, DualPtrs{}, nullptr,
+                                                              sc.rsq);
     else
-      stage_tile<STAGE, false>(sc.k, sc.c, sc.M, In, Out, sc.D, sc.tag, sc.sid, sc.rs, sc.tile_body, sc.body_tiles,
-                               sc.ds, sc.fuse_cfl != 0, sc.ncfl, ee - start[q], sm);
+      stage_tile<STAGE, false, false, false, false, TVD, QUAD>(sc.k, sc.c, sc.M, In, Out, sc.D, sc.tag, sc.sid,
+                                                               sc.rs, sc.tile_body, sc.body_tiles, sc.ds,
+                                                               sc.fuse_cfl != 0, sc.ncfl, ee - start[q], sm,
+                                                               DualPtrs{}, nullptr, sc.rsq);
     __syncthreads();  // shared memory is reused by the next entry
   }
 }
@@ -53,9 +59,18 @@ cudaError_t launch_stage_f32_batch_one(const StageBatch &b, int stage, int grid,
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = pdl ? 1 : 0;
-  if (stage == 1) return cudaLaunchKernelEx(&cfg, k_stage_f32_batch_one<1>, b);
-  if (stage == 2) return cudaLaunchKernelEx(&cfg, k_stage_f32_batch_one<2>, b);
-  return cudaLaunchKernelEx(&cfg, k_stage_f32_batch_one<3>, b);
+  const bool tvd = b.cs[0].k.tvd2 != 0, quad = b.cs[0].k.quad != 0;
+  if (quad)
+    for (int q = 0; q < b.n; q++)
+      if (!b.cs[q].rsq) return cudaErrorInvalidValue;  // the quadratic kernels read the second probes
+#define IBM_BATCH(S, T, Q) cudaLaunchKernelEx(&cfg, k_stage_f32_batch_one<S, T, Q>, b)
+#define IBM_BATCH_S(S)                                                                                          \
+  (tvd ? (quad ? IBM_BATCH(S, true, true) : IBM_BATCH(S, true, false))                                          \
+       : (quad ? IBM_BATCH(S, false, true) : IBM_BATCH(S, false, false)))
+  const cudaError_t e = stage == 1 ? IBM_BATCH_S(1) : stage == 2 ? IBM_BATCH_S(2) : IBM_BATCH_S(3);
+#undef IBM_BATCH_S
+#undef IBM_BATCH
+  return e;
 }
 
 void build_stage_batch(const StageCase *cases, int n, StageBatch *b) {
@@ -89,6 +104,7 @@ void fill_stage_case(const Consts &k, float *M, float *F1, float *F2, double *D,
   out->ncfl = (unsigned int)(out->nt + out->nb);
   out->B = out->C = out->Q0 = nullptr;
   out->G = nullptr;
+  out->rsq = nullptr;
 }
 
 

@@ -953,8 +953,11 @@ namespace ibm {
 // batched groups run the explicit stages only: dual time and bodies moving under the fluid force (whose
 // steps add the force and the body update) advance on their own streams
 bool case_batchable(const ibm_case *c) {
-  return c->precision == IBM_PREC_FP32_BULK && !c->k.tvd2 && !c->k.quad;
+  // dual-time groups are compiled for WENO5 and the linear reconstruction only
+  return c->precision == IBM_PREC_FP32_BULK && !(c->k.dual && (c->k.tvd2 || c->k.quad));
 }
+
+int case_variant(const ibm_case *c) { return (c->k.tvd2 ? 1 : 0) | (c->k.quad ? 2 : 0); }
 
 int case_subiters(const ibm_case *c) { return c->k.dual ? c->k.subiters : 0; }
 
@@ -1012,6 +1015,7 @@ int case_enqueue_poststage(ibm_case *c) {
 void case_stage_desc(const ibm_case *c, StageCase *out) {
   fill_stage_case(c->k, c->M, c->F1, c->F2, c->A, c->tag, c->sid, c->rst, c->tile_body, c->body_tiles, c->body_cap,
                   c->ds, fused_cfl(c), out);
+  out->rsq = c->rsq;
   if (c->k.dual) {
     out->B = c->B;
     out->C = c->C;

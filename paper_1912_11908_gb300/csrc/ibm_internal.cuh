@@ -492,6 +492,7 @@ struct StageCase {
   double *B, *C;
   const double *G;
   double *Q0;
+  const RStencilQ *rsq;  // quadratic reconstruction: the quadratic part of the compact stencils (else null)
 };
 
 // Block table of a batched stage launch over the member cases of a group,
@@ -524,11 +525,14 @@ cudaError_t launch_stage_f32_batch_one(const StageBatch &b, int stage, int grid,
 cudaError_t launch_dual_f32_batch_one(const StageBatch &b, int stage, int grid, bool pdl, cudaStream_t s);
 
 // ---- batching support (capi.cu), used by the request loop (serve.cu) ----
-// FP32-bulk cases (explicit RK3 with any motion, or dual time) advance through
+// FP32-bulk cases (explicit RK3 with any motion and either reconstruction,
+// or dual time with WENO5 and the linear reconstruction) advance through
 // batched stage launches.
 bool case_batchable(const ibm_case *c);
 // sub-iterations per physical step of a dual-time case (0: explicit RK3)
 int case_subiters(const ibm_case *c);
+// the stage kernels' variant a case needs: bit 0 TVD-2, bit 1 quadratic reconstruction (a group holds one)
+int case_variant(const ibm_case *c);
 // the case's body moves under the fluid force (Eq. 10)
 bool case_coupled(const ibm_case *c);
 // Work that must precede batched steps, on the case stream: the first

@@ -7,8 +7,10 @@
 //
 // Batched mode (default) for FP32-bulk cases: the requests admitted in one
 // pass of the loop form groups of cases of similar size (grids within a factor
-// four in cells), equal step counts and the same time scheme (explicit RK3, or
-// dual time with equal sub-iteration counts), up to MAX_BATCH cases per group.
+// four in cells), equal step counts, the same time scheme (explicit RK3, or
+// dual time with equal sub-iteration counts) and the same stage-kernel variant
+// (WENO5 or TVD-2, linear or quadratic reconstruction; dual-time groups the
+// first of each), up to MAX_BATCH cases per group.
 // One step of a group is one CUDA graph: the per-case work that precedes the
 // stages (re-classification and stencils of moving bodies, the force and
 // acceleration of a body under the fluid force, dt, or the rotation of a
@@ -22,8 +24,9 @@
 // or a persistent grid striding over the table) by timing the candidates on
 // the group itself, once per size class and membership size.
 //
-// Other cases (FP64, TVD-2), and every case when batching is off, advance on
-// their own streams in chunks of steps replayed from their own graphs.
+// Other cases (FP64; dual time with TVD-2 or the quadratic reconstruction),
+// and every case when batching is off, advance on their own streams in chunks
+// of steps replayed from their own graphs.
 //
 // A case that has taken all its steps is retired: its forces and time are
 // read, its memory freed, and the next waiting request can take the slot.
@@ -396,7 +399,7 @@ extern "C" ibm_status ibm_server_progress(ibm_server *s, int *n_active, int *n_p
   // 2. admit waiting requests, in arrival order, while a slot and memory are free.  Batchable requests
   // admitted in this pass form new groups by (size class, steps): a group's membership is fixed when it
   // is formed, so its step graph is captured once and all its members finish together.
-  std::map<std::tuple<int, int, int>, Group *> forming;
+  std::map<std::tuple<int, int, int, int>, Group *> forming;
   while (!s->pending.empty() && (int)s->active.size() < s->max_active &&
          s->used + s->pending.front()->bytes <= s->budget) {
     Request *r = s->pending.front();
@@ -413,7 +416,7 @@ extern "C" ibm_status ibm_server_progress(ibm_server *s, int *n_active, int *n_p
     if (st == IBM_OK) st = batched ? case_prepare_batch(a->c) : ibm_classify(a->c);
     Group *g = nullptr;
     if (st == IBM_OK && batched) {
-      const auto key = std::make_tuple(bucket_of(r), case_subiters(a->c), r->nsteps);
+      const auto key = std::make_tuple(bucket_of(r), case_subiters(a->c), case_variant(a->c), r->nsteps);
       auto it = forming.find(key);
       if (it != forming.end() && (int)it->second->members.size() < MAX_BATCH) g = it->second;
       if (!g) {

@@ -145,27 +145,44 @@ def test_batched_groups_against_oracle(orc):
         srv.close()
 
 
-def test_tvd2_and_quadratic_requests_in_a_batched_mix():
-    """Requests the group kernels are not compiled for (TVD-2, the quadratic reconstruction) run on their own
-    streams beside batched groups, and give the bits they give alone."""
+def test_tvd2_and_quadratic_requests_batch():
+    """Explicit requests with the TVD-2 reconstruction and / or the quadratic IB reconstruction form groups of
+    their own variant (the group kernel is compiled for each), and give what they give alone up to FP32 rounding;
+    a dual-time request with either runs on its own stream, bit for bit."""
     base = [s for s in _specs(6) if s["time_scheme"] == W.TIME_RK3][:3]
     odd = [dict(base[0], scheme=W.SCHEME_TVD2, name="tvd2"), dict(base[1], ib_interp=W.INTERP_QUADRATIC, name="quad"),
            dict(base[2], scheme=W.SCHEME_TVD2, ib_interp=W.INTERP_QUADRATIC, name="tvd2_quad")]
-    specs = base + odd
-    ref = [_alone(s, STEPS) for s in specs]
+    dual_q = dict(W.case_spec(W.cylinder(128), 96, 48, (-3.0, 9.0, -3.0, 3.0), 0.01, 40.0, W.FAR,
+                              time_scheme=W.TIME_DUAL, dt_phys=0.125, subiters=5, precision=W.PREC_FP32_BULK),
+                  ib_interp=W.INTERP_QUADRATIC, name="dual_quad")
+    # the variant requests alone in a server: they run in groups
+    ref = [_alone(s, STEPS) for s in odd]
     srv = ibm.Server(max_active=6, steps_per_chunk=7)
     try:
-        ids = [srv.submit(s, STEPS) for s in specs]
+        ids = [srv.submit(s, STEPS) for s in odd]
         _drain(srv, cap=6)
-        for q, (rid, (f, t), spec) in enumerate(zip(ids, ref, specs)):
+        assert srv.stats()["group_graphs"] >= len(odd)  # one group per variant
+        for rid, (f, t), spec in zip(ids, ref, odd):
             r = srv.poll(rid)
             assert r["state"] == ibm.REQ_DONE and r["status"] == 0, r
-            if q >= len(base):  # on its own stream: the kernels of the case alone
+            _same(r, f, t, MODES[0], spec)
+    finally:
+        srv.close()
+    # mixed with plain requests and a dual-time request with the quadratic reconstruction
+    specs = base + odd + [dual_q]
+    ref = [_alone(s, 4 if s is dual_q else STEPS) for s in specs]
+    srv = ibm.Server(max_active=8, steps_per_chunk=7)
+    try:
+        ids = [srv.submit(s, 4 if s is dual_q else STEPS) for s in specs]
+        _drain(srv, cap=8)
+        for rid, (f, t), spec in zip(ids, ref, specs):
+            r = srv.poll(rid)
+            assert r["state"] == ibm.REQ_DONE and r["status"] == 0, r
+            if spec is dual_q:  # on its own stream: the kernels of the case alone
                 np.testing.assert_array_equal(r["forces"], f)
                 assert r["t"] == t
             else:
                 _same(r, f, t, MODES[0], spec)
-        assert srv.stats()["group_steps"] > 0
     finally:
         srv.close()
 
