@@ -1260,14 +1260,14 @@ extern "C" ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, 
   if (!c || !src) return fail(IBM_EINVAL, "case or src is NULL");
   const size_t ncell = (size_t)c->k.nx * c->k.ny;
   if (bytes < 4 * ncell * sizeof(double)) return fail(IBM_EINVAL, "src too small");
-  ibm_status q = copy_state(c, nullptr, (const double *)src, false, src_on_device);
-  if (q != IBM_OK) return q;
-  if (c->M) {
-    launch_abs_to_pert64(c->k, c->A, c->stream);
-    launch_to_mirror(c->k, c->A, c->M, c->stream);
-    c->launches += 2;
-    c->dt_valid = false;
-  }
+  // one contiguous copy into a device staging buffer (the full bandwidth of the host link, where a pitched copy
+  // into the padded layout moves row by row), then one kernel: layout, perturbation form and FP32 mirror
+  if (!c->stage64) CU(cudaMallocAsync((void **)&c->stage64, 4 * (size_t)c->k.plane * sizeof(double), c->stream));
+  CU(cudaMemcpyAsync(c->stage64, src, 4 * ncell * sizeof(double),
+                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  launch_set_state(c->k, c->stage64, c->A, c->M, c->stream);
+  c->launches += 1;
+  if (c->M) c->dt_valid = false;
   if (!src_on_device) CU(cudaStreamSynchronize(c->stream));
   CU(cudaGetLastError());
   return IBM_OK;

@@ -64,6 +64,37 @@ void launch_dt(const Consts &k, const double *A, const uint8_t *tag, DevState *d
 // pressure condition a linear ODE in p along the normal, integrated exactly.
 // One thread per list entry; in place on the stage array.
 // ---------------------------------------------------------------------------
+// A state written by the caller ([4][ny][nx] absolute conserved, contiguous, already on the device) into the
+// case's padded layout: FP64 as given, or -- FP32-bulk, M != null -- as the perturbation from the free stream
+// (dU = U - U_inf, the energy row less H_inf d rho) with its FP32 mirror.  One thread per cell.
+__global__ void k_set_state(Consts k, const double *__restrict__ U, double *__restrict__ A, float *__restrict__ M) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ncell = (long long)k.nx * k.ny;
+  if (n >= ncell) return;
+  const long long id = cidx(k, (int)(n % k.nx), (int)(n / k.nx)), P = k.plane;
+  double u0 = U[n], u1 = U[n + ncell], u2 = U[n + 2 * ncell], u3 = U[n + 3 * ncell];
+  if (M) {
+    const double d = u0 - 1.0;
+    u0 = d;
+    u1 = u1 - k.Uinf[1];
+    u2 = u2 - k.Uinf[2];
+    u3 = (u3 - k.Uinf[3]) - k.Hinf * d;
+    M[id] = (float)u0;
+    M[id + P] = (float)u1;
+    M[id + 2 * P] = (float)u2;
+    M[id + 3 * P] = (float)u3;
+  }
+  A[id] = u0;
+  A[id + P] = u1;
+  A[id + 2 * P] = u2;
+  A[id + 3 * P] = u3;
+}
+
+void launch_set_state(const Consts &k, const double *U, double *A, float *M, cudaStream_t s) {
+  const long long ncell = (long long)k.nx * k.ny;
+  k_set_state<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(k, U, A, M);
+}
+
 // (p, u, v, T) interpolated at a probe from the valid corners of its square
 __device__ __forceinline__ void probe_f64(const Consts &k, const double *U, int i0, int j0, int mask,
                                           const double w[4], double qp[4]) {
