@@ -441,7 +441,8 @@ def run_ours(args, rank, world):
     barrier()
     t0 = time.perf_counter()
     for _ in range(ke):
-        case.set_state_from_ptr(host.data_ptr(), host.numel() * 8, False)
+        # upload (asynchronous: the pinned buffer stays unchanged), one step, forces back (the one host wait)
+        case.set_state_from_ptr(host.data_ptr(), host.numel() * 8, False, wait=False)
         case.step(1)
         case.forces_into(forces.data_ptr())
     t_e2e = max_over_ranks(time.perf_counter() - t0, dist, "cuda")

@@ -213,6 +213,13 @@ ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t bytes, int dst
  * copied before the call returns. */
 ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, int src_on_device);
 
+/* As ibm_set_state, asynchronous for host sources too: the copy is enqueued
+ * on the case stream and the caller keeps src unchanged (and, for a host
+ * source, page-locked if it wants the copy to overlap) until the next
+ * synchronising call (ibm_forces, ibm_get_state, ibm_sync).  Lets a caller
+ * upload, step and read forces with one host synchronisation per step. */
+ibm_status ibm_set_state_async(ibm_case *c, const void *src, size_t bytes, int src_on_device);
+
 /* Surface force at the current time (Sec. 6, Eq. 9): out = {Cd, Cl, Fx, Fy}
  * with C = F / (1/2 rho_inf U_ref^2 ref_len).  Synchronises. */
 ibm_status ibm_forces(ibm_case *c, double out[4]);

@@ -1256,7 +1256,7 @@ extern "C" ibm_status ibm_get_state(ibm_case *c, int what, void *dst, size_t byt
   return r;
 }
 
-extern "C" ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, int src_on_device) {
+static ibm_status set_state(ibm_case *c, const void *src, size_t bytes, int src_on_device, bool wait_for_host) {
   if (!c || !src) return fail(IBM_EINVAL, "case or src is NULL");
   const size_t ncell = (size_t)c->k.nx * c->k.ny;
   if (bytes < 4 * ncell * sizeof(double)) return fail(IBM_EINVAL, "src too small");
@@ -1268,9 +1268,17 @@ extern "C" ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, 
   launch_set_state(c->k, c->stage64, c->A, c->M, c->stream);
   c->launches += 1;
   if (c->M) c->dt_valid = false;
-  if (!src_on_device) CU(cudaStreamSynchronize(c->stream));
+  if (!src_on_device && wait_for_host) CU(cudaStreamSynchronize(c->stream));
   CU(cudaGetLastError());
   return IBM_OK;
+}
+
+extern "C" ibm_status ibm_set_state(ibm_case *c, const void *src, size_t bytes, int src_on_device) {
+  return set_state(c, src, bytes, src_on_device, true);
+}
+
+extern "C" ibm_status ibm_set_state_async(ibm_case *c, const void *src, size_t bytes, int src_on_device) {
+  return set_state(c, src, bytes, src_on_device, false);
 }
 
 extern "C" ibm_status ibm_forces(ibm_case *c, double out[4]) {

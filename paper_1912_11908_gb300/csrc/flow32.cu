@@ -1,6 +1,7 @@
-// FP32-bulk flow kernels of one case: conversions between the FP64 master and
-// the FP32 mirror, the CFL reduction, compact stencils, body-tile lists and
-// the stage kernels (per-tile code in stage32.cuh).
+// FP32-bulk flow kernels of one case: the FP64 master's perturbation form back
+// to absolute variables, the CFL reduction, compact stencils, body-tile lists
+// and the stage kernels (per-tile code in stage32.cuh).  (A state written by
+// the caller takes k_set_state of flow.cu.)
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -9,18 +10,7 @@
 
 namespace ibm {
 
-// FP64 absolute conserved <-> FP64 perturbation, in place / out of place
-__global__ void k_abs_to_pert64(Consts k, double *D) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= k.plane) return;
-  const long long P = k.plane;
-  const double d = D[n] - 1.0;
-  D[n] = d;
-  D[n + P] = D[n + P] - k.Uinf[1];
-  D[n + 2 * P] = D[n + 2 * P] - k.Uinf[2];
-  D[n + 3 * P] = (D[n + 3 * P] - k.Uinf[3]) - k.Hinf * d;
-}
-
+// FP64 perturbation -> FP64 absolute conserved
 __global__ void k_pert_to_abs64(Consts k, const double *__restrict__ D, double *__restrict__ A) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= k.plane) return;
@@ -32,20 +22,8 @@ __global__ void k_pert_to_abs64(Consts k, const double *__restrict__ D, double *
   A[n + 3 * P] = k.Uinf[3] + D[n + 3 * P] + k.Hinf * d;
 }
 
-__global__ void k_to_mirror(Consts k, const double *__restrict__ D, float *__restrict__ M) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= 4 * k.plane) return;
-  M[n] = (float)D[n];
-}
-
-void launch_abs_to_pert64(const Consts &k, double *D, cudaStream_t s) {
-  k_abs_to_pert64<<<(unsigned)((k.plane + 255) / 256), 256, 0, s>>>(k, D);
-}
 void launch_pert_to_abs64(const Consts &k, const double *D, double *A, cudaStream_t s) {
   k_pert_to_abs64<<<(unsigned)((k.plane + 255) / 256), 256, 0, s>>>(k, D, A);
-}
-void launch_to_mirror(const Consts &k, const double *D, float *M, cudaStream_t s) {
-  k_to_mirror<<<(unsigned)((4 * k.plane + 255) / 256), 256, 0, s>>>(k, D, M);
 }
 
 // CFL rule (same expression as the FP64 path) evaluated in FP32 on the mirror

@@ -347,12 +347,10 @@ __device__ __forceinline__ RStencilQ quad_stencil(const Consts &k, const ibm_ste
 
 // FP32-bulk path (flow32.cu).  The FP64 state D of this mode holds the
 // perturbation dU from the free stream (same variables as the FP32 arrays).
-void launch_abs_to_pert64(const Consts &k, double *D, cudaStream_t s);          // in place
 // U ([4][ny][nx] absolute conserved, contiguous, on the device) into A's padded layout; with M (FP32-bulk) as
 // the perturbation from the free stream and its FP32 mirror
 void launch_set_state(const Consts &k, const double *U, double *A, float *M, cudaStream_t s);
 void launch_pert_to_abs64(const Consts &k, const double *D, double *A, cudaStream_t s);
-void launch_to_mirror(const Consts &k, const double *D, float *M, cudaStream_t s);
 void launch_dt_f32(const Consts &k, const float *M, const uint8_t *tag, DevState *ds, cudaStream_t s, int *nlaunch);
 void launch_compact_stencils(const Consts &k, const ibm_stencil *st, RStencil32 *rs, RStencilQ *rsq, int *sid,
                              int cap, const DevState *ds, cudaStream_t s);

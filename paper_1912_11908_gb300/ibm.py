@@ -70,8 +70,8 @@ class ibm_result(ctypes.Structure):
                 ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
 
 
-EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state", "ibm_forces",
-           "ibm_surface",
+EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state", "ibm_set_state_async",
+           "ibm_forces", "ibm_surface",
            "ibm_sync", "ibm_destroy_case", "ibm_case_device_bytes", "ibm_launch_count", "ibm_last_error",
            "ibm_profile_enable", "ibm_profile_read", "ibm_use_graphs", "ibm_tag_nodes_noalloc",
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_poll",
@@ -104,6 +104,7 @@ def load():
     L.ibm_step.argtypes = [vp, ip]
     L.ibm_get_state.argtypes = [vp, ip, vp, sz, ip]
     L.ibm_set_state.argtypes = [vp, vp, sz, ip]
+    L.ibm_set_state_async.argtypes = [vp, vp, sz, ip]
     L.ibm_forces.argtypes = [vp, vp]
     L.ibm_surface.argtypes = [vp, vp, vp, ip]
     L.ibm_fma_peak.argtypes = [ip, ctypes.c_longlong, vp, vp]
@@ -152,7 +153,7 @@ def load():
                  "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats"):
         getattr(L, name).restype = ip
     for name in ("ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_set_state",
-                 "ibm_forces", "ibm_surface", "ibm_sync", "ibm_destroy_case", "ibm_profile_enable", "ibm_profile_read",
+                 "ibm_set_state_async", "ibm_forces", "ibm_surface", "ibm_sync", "ibm_destroy_case", "ibm_profile_enable", "ibm_profile_read",
                  "ibm_use_graphs"):
         getattr(L, name).restype = ip
     return L
@@ -293,8 +294,10 @@ class Case:
         assert a.shape == (4, self.ny, self.nx)
         _check(lib().ibm_set_state(self.h, a.ctypes.data_as(ctypes.c_void_p), a.nbytes, 0))
 
-    def set_state_from_ptr(self, ptr, nbytes, on_device):
-        _check(lib().ibm_set_state(self.h, ctypes.c_void_p(ptr), nbytes, 1 if on_device else 0))
+    def set_state_from_ptr(self, ptr, nbytes, on_device, wait=True):
+        """wait=False: ibm_set_state_async (the source must stay unchanged until the next synchronising call)."""
+        f = lib().ibm_set_state if wait else lib().ibm_set_state_async
+        _check(f(self.h, ctypes.c_void_p(ptr), nbytes, 1 if on_device else 0))
 
     def tags(self):
         return self._get(IBM_TAGS, np.empty((self.ny, self.nx), np.uint8))

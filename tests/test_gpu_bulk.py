@@ -253,3 +253,22 @@ def test_stage_launch_mode_checked(ibm):
     c = ibm.Case(W.wedge_m2_re1e4(64, 32, precision=W.PREC_FP32_BULK))
     with pytest.raises(ibm.IbmError):
         c.stage_launches(3)
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32_BULK])
+def test_set_state_async_matches_set_state(ibm, precision):
+    """ibm_set_state_async enqueues the same copy and conversion as ibm_set_state without waiting for the host
+    buffer: stepping from either gives the same bits (the buffer is left unchanged until the forces are read)."""
+    spec = W.cylinder_m02_re40(96, 48, precision=precision)
+    src = ibm.Case(spec)
+    src.step(30)
+    U = np.ascontiguousarray(src.state())
+    res = []
+    for wait in (True, False):
+        c = ibm.Case(spec)
+        c.classify()
+        c.set_state_from_ptr(U.ctypes.data, U.nbytes, False, wait=wait)
+        c.step(20)
+        res.append((c.forces(), c.state()))
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_array_equal(res[0][1], res[1][1])
