@@ -1,4 +1,4 @@
-"""FP64 CPU oracle (ctypes wrapper over ``oracle.c``).
+"""FP64 CPU oracle (ctypes wrapper over ``oracle.c`` and, for the 3-D flow, ``oracle3d.c``).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
 leg of the benchmark are the only callers.  The CUDA library never imports,
@@ -15,7 +15,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
-SOURCES = [os.path.join(HERE, "oracle.c")]
+SOURCES = [os.path.join(HERE, "oracle.c"), os.path.join(HERE, "oracle3d.c")]
 
 FLUID, SOLID, IB, G1, G2, G3 = range(6)
 BC_FREESTREAM, BC_OUTFLOW, BC_PERIODIC = range(3)
@@ -52,6 +52,24 @@ class _Params(ctypes.Structure):
         ("cfl_tau", ctypes.c_double), ("ib_interp", ctypes.c_int),
     ]
 
+
+class _Params3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("bc", ctypes.c_int * 6),
+        ("mach", ctypes.c_double), ("re", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("prandtl", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("uinf", ctypes.c_double * 3), ("dt_fixed", ctypes.c_double), ("ref_area", ctypes.c_double),
+        ("nv", ctypes.c_int), ("ntri", ctypes.c_int),
+        ("verts", ctypes.POINTER(ctypes.c_double)), ("tris", ctypes.POINTER(ctypes.c_int)),
+    ]
+
+
+STENCIL3_DTYPE = np.dtype([
+    ("node", "<i4"), ("kind", "<i4"), ("region", "<i4"), ("nstep", "<i4"),
+    ("i0", "<i4"), ("j0", "<i4"), ("k0", "<i4"), ("mask", "<i4"),
+    ("n", "<f8", (3,)), ("b", "<f8", (3,)), ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (8,)),
+])
 
 STENCIL_DTYPE = np.dtype([
     ("cell", "<i4"), ("feature", "<i4"), ("region", "<i4"), ("i0", "<i4"), ("j0", "<i4"),
@@ -108,6 +126,25 @@ def lib():
         L.orc_dwdq.argtypes = [vp, dp, dp, vp]
         L.orc_solve4.argtypes = [vp, vp, vp]
         L.orc_solve4.restype = ip
+        L.orc3_create.restype = vp
+        L.orc3_create.argtypes = [ctypes.POINTER(_Params3)]
+        L.orc3_destroy.argtypes = [vp]
+        L.orc3_classify.argtypes = [vp]
+        L.orc3_classify.restype = ip
+        L.orc3_step.argtypes = [vp, ip]
+        L.orc3_step.restype = ip
+        L.orc3_reconstruct.argtypes = [vp]
+        L.orc3_get_state.argtypes = [vp, vp]
+        L.orc3_set_state.argtypes = [vp, vp]
+        L.orc3_get_tags.argtypes = [vp, vp]
+        L.orc3_list_len.argtypes = [vp, ip]
+        L.orc3_list_len.restype = ip
+        L.orc3_get_list.argtypes = [vp, ip, vp]
+        L.orc3_forces.argtypes = [vp, vp]
+        L.orc3_time.argtypes = [vp]
+        L.orc3_time.restype = dp
+        L.orc3_last_dt.argtypes = [vp]
+        L.orc3_last_dt.restype = dp
         _lib = L
     return _lib
 
@@ -234,6 +271,84 @@ class Case:
         lib().orc_closest(self.h, x, y, ctypes.byref(f), ctypes.byref(r), ctypes.byref(cx), ctypes.byref(cy),
                           ctypes.byref(d2))
         return f.value, r.value, cx.value, cy.value, d2.value
+
+
+class Case3D:
+    """One 3-D oracle case (static closed triangulated body, SSP-RK3); ``spec`` is a dict from
+    ``workloads.case3d_spec``."""
+
+    def __init__(self, spec):
+        s = spec
+        self.spec = spec
+        self.nx, self.ny, self.nz = s["n"]
+        self._verts = np.ascontiguousarray(s["verts"], np.float64).reshape(-1, 3)
+        self._tris = np.ascontiguousarray(s["tris"], np.int32).reshape(-1, 3)
+        P = _Params3()
+        P.nx, P.ny, P.nz = s["n"]
+        for a in range(3):
+            P.lo[a], P.hi[a] = s["lo"][a], s["hi"][a]
+            P.uinf[a] = s["uinf"][a]
+        for k in range(6):
+            P.bc[k] = s["bc"][k]
+        P.mach, P.re, P.gamma, P.prandtl, P.cfl = s["mach"], s["re"], s["gamma"], s["prandtl"], s["cfl"]
+        P.dt_fixed = s["dt_fixed"]
+        P.ref_area = s["ref_area"]
+        P.nv, P.ntri = self._verts.shape[0], self._tris.shape[0]
+        if P.ntri:
+            P.verts = self._verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            P.tris = self._tris.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        self._P = P
+        self.h = lib().orc3_create(ctypes.byref(P))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc3_destroy(self.h)
+            self.h = None
+
+    def classify(self):
+        return lib().orc3_classify(self.h)
+
+    def step(self, n):
+        return lib().orc3_step(self.h, n)
+
+    def reconstruct(self):
+        lib().orc3_reconstruct(self.h)
+
+    def state(self):
+        a = np.empty((5, self.nz, self.ny, self.nx), np.float64)
+        lib().orc3_get_state(self.h, _ptr(a))
+        return a
+
+    def set_state(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        assert a.shape == (5, self.nz, self.ny, self.nx)
+        lib().orc3_set_state(self.h, _ptr(a))
+
+    def tags(self):
+        a = np.empty((self.nz, self.ny, self.nx), np.uint8)
+        lib().orc3_get_tags(self.h, _ptr(a))
+        return a
+
+    def stencils(self, kind=None):
+        """The stencils of one list (0 IB, 1..3 G1..G3), or of all four in that order."""
+        if kind is None:
+            return np.concatenate([self.stencils(k) for k in range(4)])
+        n = lib().orc3_list_len(self.h, kind)
+        a = np.zeros(n, STENCIL3_DTYPE)
+        if n:
+            lib().orc3_get_list(self.h, kind, _ptr(a))
+        return a
+
+    def forces(self):
+        out = np.zeros(6, np.float64)
+        lib().orc3_forces(self.h, _ptr(out))
+        return out
+
+    def time(self):
+        return lib().orc3_time(self.h)
+
+    def last_dt(self):
+        return lib().orc3_last_dt(self.h)
 
 
 def classify_points_3d(verts, tris, pts):

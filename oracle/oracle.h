@@ -31,6 +31,10 @@
  *                        fall on cell centres, where the linear form is off (Sec. 4.5, Sec. 5)
  *   forces               pinned: zero force in uniform flow / uniform pressure (Sec. 6, Eq. 9)
  *   drag/lift values     parity unpinned (the paper prints none for these workloads)
+ *   3-D residual + RK3   pinned: a field constant along one axis reproduces the 2-D oracle bit for bit in each
+ *                        of the three coordinate planes (oracle3d.c)
+ *   3-D IB / ghost       pinned: linear profiles at axis-aligned and oblique plane walls, quiescent sphere
+ *   3-D forces           pinned: linear pressure field on a closed polyhedron (divergence theorem, Eq. 9)
  */
 #ifndef IBM_ORACLE_H
 #define IBM_ORACLE_H
@@ -147,6 +151,55 @@ void orc_euler_xflux(const double q[4], double gamma, double R, double flux[4]);
 void orc_precond_matrix(const double Q[4], double gamma, double R, double Ur, double out[16]);
 void orc_dwdq(const double Q[4], double gamma, double R, double out[16]);
 int orc_solve4(const double A[16], const double b[4], double x[4]);
+
+/* ------------------------------------------------------------------------------------------------------ */
+/* 3-D flow (oracle3d.c): one uniform block of nx * ny * nz cells with a static closed triangulated body,     */
+/* explicit SSP-RK3, the compressible (linear) IB / ghost form.  State (rho, rho u, rho v, rho w, rho E).     */
+/* domain sides in bc order: x-low, x-high, y-low, y-high, z-low, z-high                                      */
+/* ------------------------------------------------------------------------------------------------------ */
+typedef struct {
+  int nx, ny, nz;          /* cells */
+  double lo[3], hi[3];     /* domain */
+  int bc[6];
+  double mach, re, gamma, prandtl, cfl;  /* re <= 0: inviscid */
+  double uinf[3];
+  double dt_fixed;         /* > 0: use this time step instead of the CFL rule */
+  double ref_area;         /* force normalisation area */
+  int nv, ntri;            /* body: 0 = none */
+  const double *verts;     /* 3*nv; copied */
+  const int *tris;         /* 3*ntri, counter-clockwise seen from outside; copied */
+} orc3_params;
+
+/* One IB or ghost node of the 3-D lattice and its reconstruction stencil. */
+typedef struct {
+  int32_t node;      /* (k ny + j) nx + i */
+  int32_t kind;      /* 0 IB, 1..3 ghost layer */
+  int32_t region;    /* closest feature: 0 face, 1 edge, 2 vertex */
+  int32_t nstep;     /* probe push-outs taken */
+  int32_t i0, j0, k0;/* lowest corner of the interpolation cube */
+  int32_t mask;      /* bit b: corner (i0 + (b & 1), j0 + (b >> 1 & 1), k0 + (b >> 2)) valid */
+  double n[3];       /* local normal (pseudo-normal of the closest feature, out of the body) */
+  double b[3];       /* boundary point P' */
+  double xi_node;    /* signed distance of the node from P' along n */
+  double xi_probe;   /* signed distance of the probe / image point from P' */
+  double w[8];       /* interpolation weights (0 for invalid corners) */
+} orc3_stencil;
+
+typedef struct orc3_case orc3_case;
+
+orc3_case *orc3_create(const orc3_params *p);
+void orc3_destroy(orc3_case *c);
+int orc3_classify(orc3_case *c);                    /* returns #stencil errors */
+int orc3_step(orc3_case *c, int nsteps);            /* SSP-RK3 steps; returns #stencil errors */
+void orc3_reconstruct(orc3_case *c);                /* IB + ghost fill of the current state (one stage's) */
+void orc3_get_state(const orc3_case *c, double *dst);    /* [5][nz][ny][nx] */
+void orc3_set_state(orc3_case *c, const double *src);    /* [5][nz][ny][nx] */
+void orc3_get_tags(const orc3_case *c, uint8_t *dst);    /* [nz][ny][nx] */
+int orc3_list_len(const orc3_case *c, int kind);
+void orc3_get_list(const orc3_case *c, int kind, orc3_stencil *dst);
+void orc3_forces(orc3_case *c, double out[6]);      /* Cx, Cy, Cz, Fx, Fy, Fz */
+double orc3_time(const orc3_case *c);
+double orc3_last_dt(const orc3_case *c);
 
 #ifdef __cplusplus
 }

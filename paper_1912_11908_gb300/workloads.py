@@ -220,6 +220,30 @@ def box_mesh(lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
     return verts, np.array(tris, dtype=np.int32)
 
 
+def case3d_spec(verts, tris, n, lo, hi, mach, re, bc, *, cfl=0.5, uinf=(1.0, 0.0, 0.0), gamma=1.4, prandtl=0.72,
+                dt_fixed=0.0, ref_area=1.0, name=""):
+    """A 3-D case: nx * ny * nz cells over [lo, hi], a static closed triangulated body (verts None: no body),
+    domain sides in the order x-low, x-high, y-low, y-high, z-low, z-high."""
+    if verts is None:
+        verts, tris = np.zeros((0, 3)), np.zeros((0, 3), np.int32)
+    return dict(name=name, verts=np.ascontiguousarray(verts, np.float64).reshape(-1, 3),
+                tris=np.ascontiguousarray(tris, np.int32).reshape(-1, 3), n=tuple(int(v) for v in n),
+                lo=tuple(float(v) for v in lo), hi=tuple(float(v) for v in hi), mach=float(mach), re=float(re),
+                bc=tuple(int(b) for b in bc), cfl=float(cfl), uinf=tuple(float(u) for u in uinf), gamma=float(gamma),
+                prandtl=float(prandtl), dt_fixed=float(dt_fixed), ref_area=float(ref_area))
+
+
+FAR3D = (BC_FREESTREAM, BC_OUTFLOW) + (BC_FREESTREAM,) * 4
+
+
+def sphere_m03_re100(nx=192, ny=96, nz=96, **kw):
+    """Flow past the Appendix A sphere (UV sphere of 1200 triangles), diameter 1 at the origin, M 0.3, Re 100
+    (steady axisymmetric wake), over [-3, 9] x [-3, 3] x [-3, 3]; forces normalised by the frontal area."""
+    verts, tris = uv_sphere(radius=0.5)
+    return case3d_spec(verts, tris, (nx, ny, nz), (-3.0, -3.0, -3.0), (9.0, 3.0, 3.0), 0.3, 100.0, FAR3D,
+                       ref_area=math.pi * 0.25, name="sphere_M0.3_Re100_%dx%dx%d" % (nx, ny, nz), **kw)
+
+
 def random_polygon(rng, n, center=(0.0, 0.0), rmin=0.3, rmax=1.0):
     """Star-shaped random polygon (CCW) for brute-force classification checks."""
     a = np.sort(rng.uniform(0.0, 2.0 * math.pi, n))
