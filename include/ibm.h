@@ -260,8 +260,8 @@ ibm_status ibm_surface(ibm_case *c, double *cp, double *cf, int nseg);
  *     (Eq. 3), all pointing out of the body.
  * The computation uses IEEE basic operations and sqrt only (face and vertex
  * normals, which need acos, are formed once on the host at creation), so its
- * results are reproducible bit for bit.  The 3-D flow solver is not built: a
- * body can be classified, not stepped. */
+ * results are reproducible bit for bit.  The 3-D flow solver (ibm_case3d_*
+ * below) runs on these results. */
 typedef struct ibm_body3d ibm_body3d;
 
 typedef struct {
@@ -311,6 +311,100 @@ ibm_status ibm_body3d_get(ibm_body3d *b, int what, void *dst, size_t bytes);
 
 /* Release the body's device memory (and its own stream).  NULL is a no-op. */
 ibm_status ibm_body3d_destroy(ibm_body3d *b);
+
+/* ---- 3-D flow (Sec. 2-6 on a 3-D block; Appendix A's sphere) ----
+ *
+ * One uniform block of nx * ny * nz cells (cell (i, j, k) centred at lo +
+ * (index + 1/2) (hi - lo) / n, index (k ny + j) nx + i) around a static closed
+ * triangulated body (as for ibm_body3d_create; none when ntris = 0), in FP64,
+ * advanced by explicit SSP-RK3 steps with the CFL rule (or dt_fixed).  At
+ * creation the body is classified, tagged and listed on the lattice of cell
+ * centres (ibm_body3d_classify) and every listed node gets its stencil:
+ *   - the boundary point P' is the foot of the node X on the plane through its
+ *     closest surface point C normal to the local normal n (the pseudo-normal
+ *     of the closest feature, out of the body): P' = X - xi_node n with
+ *     xi_node = (X - C).n -- the closest point itself on a face;
+ *   - an IB node's probe lies one cell diagonal sqrt(dx^2 + dy^2 + dz^2)
+ *     beyond the node along n; a ghost node's image point is its mirror image
+ *     through P' (at least min(dx, dy, dz) / 2 from P'); either is pushed out
+ *     by min(dx, dy, dz), up to three times, while its cube has no valid
+ *     corner (IBM_ESTENCIL when none is found);
+ *   - interpolation over the cube of the eight surrounding cell centres:
+ *     trilinear when all eight are valid (fluid; fluid or IB for image
+ *     points), else inverse-distance weights 1 / r^2 over the valid ones.
+ * Per RK stage: IB nodes from their probes (static wall: velocity zero at P'
+ * and linear along n, Eq. 4; pressure and temperature the probe's, Eq. 5-6
+ * and 8), then the three ghost layers from their image points (Sec. 5), the
+ * domain halos (free stream, zero-gradient outflow or periodic, as in 2-D),
+ * and the fused residual of Sec. 2 in three directions -- WENO5 on (rho, u, v,
+ * w, p), LDFSS(0), central viscous flux with the Stokes hypothesis -- with the
+ * stage update of the fluid cells.  Forces follow Eq. 9 with one midpoint per
+ * triangle, the probe one cell diagonal out along the face normal.  These
+ * tags, lists and stencils are bit-identical to an FP64 evaluation of the same
+ * formulas in IEEE basic operations; the state agrees with such an evaluation
+ * to FP64 rounding. */
+typedef struct ibm_case3d ibm_case3d;
+
+typedef struct {
+  int nx, ny, nz;   /* cells, each >= 4 */
+  double lo[3], hi[3];
+  int bc[6];        /* IBM_BC_* for x-low, x-high, y-low, y-high, z-low, z-high */
+  double mach, re, gamma, prandtl, cfl;  /* re <= 0: inviscid */
+  double uinf[3];   /* free-stream velocity in reference-speed units */
+  double dt_fixed;  /* > 0: fixed time step, else the CFL rule */
+  double ref_area;  /* force normalisation area (> 0) */
+} ibm_flow3d;
+
+/* one IB or ghost node of the 3-D case and its stencil */
+typedef struct {
+  int32_t node;      /* (k ny + j) nx + i */
+  int32_t kind;      /* 0 IB, 1..3 ghost layer */
+  int32_t region;    /* closest feature: IBM_FEATURE_* */
+  int32_t nstep;     /* probe push-outs (0..3) */
+  int32_t i0, j0, k0;/* lowest corner of the interpolation cube */
+  int32_t mask;      /* bit b set: corner (i0 + (b & 1), j0 + (b >> 1 & 1), k0 + (b >> 2)) valid */
+  double n[3];       /* local normal */
+  double b[3];       /* boundary point P' */
+  double xi_node, xi_probe;
+  double w[8];       /* interpolation weights, 0 on invalid corners */
+} ibm_stencil3d;
+
+/* what for ibm_case3d_get (IBM_3D_TAGS and IBM_3D_COUNTS as for ibm_body3d_get) */
+enum {
+  IBM_3D_STATE = 4,    /* double[5][nz][ny][nx]: rho, rho u, rho v, rho w, rho E */
+  IBM_3D_STENCILS = 5, /* ibm_stencil3d[#IB + #G1 + #G2 + #G3], IB first, each class in node-index order */
+  IBM_3D_TIME = 6      /* double[2]: t, last dt */
+};
+
+/* Create a case at the uniform free stream, t = 0, classify its body and build
+ * the stencils (synchronous).  verts: 3*nverts doubles, tris: 3*ntris indices
+ * (host, copied; ntris = 0: no body).  cuda_stream: a cudaStream_t or NULL
+ * (the case then creates its own).  IBM_EINVAL for bad arguments, IBM_ESTENCIL
+ * if a listed node finds no probe corner, IBM_ENOMEM / IBM_ECUDA on device
+ * errors (no case is returned then). */
+ibm_status ibm_case3d_create(const double *verts, int nverts, const int32_t *tris, int ntris,
+                             const ibm_flow3d *flow, void *cuda_stream, ibm_case3d **out);
+
+/* Advance nsteps SSP-RK3 steps.  Asynchronous. */
+ibm_status ibm_case3d_step(ibm_case3d *c, int nsteps);
+
+/* Copy a quantity to host (dst_on_device = 0) or device memory (1); bytes at
+ * least its size.  Synchronises the case stream. */
+ibm_status ibm_case3d_get(ibm_case3d *c, int what, void *dst, size_t bytes, int dst_on_device);
+
+/* Overwrite the conserved state (double[5][nz][ny][nx]) from host or device
+ * memory (a host source is copied before the call returns). */
+ibm_status ibm_case3d_set_state(ibm_case3d *c, const void *src, size_t bytes, int src_on_device);
+
+/* Force on the body at the current state (Eq. 9): out = {Cx, Cy, Cz, Fx, Fy,
+ * Fz}, C = F / (1/2 rho_inf U_ref^2 ref_area).  Synchronises. */
+ibm_status ibm_case3d_forces(ibm_case3d *c, double out[6]);
+
+/* Kernel launches enqueued by the case so far. */
+int64_t ibm_case3d_launch_count(const ibm_case3d *c);
+
+/* Release the case (synchronises first).  NULL is a no-op. */
+ibm_status ibm_case3d_destroy(ibm_case3d *c);
 
 /* Measured arithmetic ceiling (no counterpart in the paper; the rooflines of the ALU-bound kernels are
  * taken against it): one launch of iters fused multiply-adds per recurrence, 8 independent recurrences per

@@ -12,7 +12,7 @@ LIB = os.path.join(PKG, "libibm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # geometry: IEEE basic operations only, no contraction, so tags / lists / stencils are bit-reproducible
 # FP32-bulk kernels: approximate division / square root are within the FP32 path's error budget
-SOURCES = {"geometry.cu": ["-fmad=false"], "flow.cu": [], "flow32.cu": ["-use_fast_math"], "batch32.cu": ["-use_fast_math"], "dual32.cu": ["-use_fast_math"], "step32.cu": ["-use_fast_math"], "capi.cu": [], "serve.cu": [], "peaks.cu": [], "geometry3d.cu": ["-fmad=false"]}
+SOURCES = {"geometry.cu": ["-fmad=false"], "flow.cu": [], "flow32.cu": ["-use_fast_math"], "batch32.cu": ["-use_fast_math"], "dual32.cu": ["-use_fast_math"], "step32.cu": ["-use_fast_math"], "capi.cu": [], "serve.cu": [], "peaks.cu": [], "geometry3d.cu": ["-fmad=false"], "flow3d.cu": []}
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 

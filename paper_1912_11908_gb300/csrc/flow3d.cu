@@ -1,0 +1,722 @@
+// 3-D flow on the GPU in FP64 (Sec. 2-6 of arXiv 1912.11908 on one uniform 3-D block around a static closed
+// triangulated body): explicit SSP-RK3 steps, each stage
+//   IB nodes from their probes and the three ghost layers from their image points (Sec. 4.3-4.6, Sec. 5),
+//   domain halos, primitives, the face fluxes of the three directions (WENO5 on (rho, u, v, w, p), LDFSS(0),
+//   central viscous flux with the Stokes hypothesis; Sec. 2) and the stage update of the fluid cells,
+// and Eq. 9's force over the triangles.  Classification, tags, lists and the stencils of the listed nodes and
+// of the force probes come from the 3-D pre-processing (geometry3d.cu), once at creation (the body is static).
+//
+// Layout: structure of arrays over the cells with three halo layers, cell (i, j, k) of the (nx + 6) x (ny + 6)
+// x (nz + 6) array at ((k + 3) H + j + 3) W + i + 3; face i + 1/2 (j + 1/2, k + 1/2) of a direction is stored
+// at its lower cell.  One thread per cell, per face or per listed node.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "ibm.h"
+
+extern "C" ibm_status ibm__noalloc_fail(ibm_status s, const char *msg);
+ibm_status ibm__body3d_stencils(ibm_body3d *b, double h, double dmin, ibm_stencil3d *out, int *nerr,
+                                const uint8_t **tags, const int **counts, int *cap);
+ibm_status ibm__surface3d_stencils(ibm_body3d *b, const double *mn, int ntri, double h, double dmin,
+                                   ibm_stencil3d *out);
+int ibm__body3d_capacity(const ibm_body3d *b);
+
+namespace {
+
+constexpr int NG = 3;
+constexpr int TB = 256;
+constexpr uint8_t TAG_FLUID = IBM_TAG_FLUID;
+
+struct Grid3 {
+  int nx, ny, nz, W, H, D;
+  long long plane, ncell;
+  double dx, dy, dz, idx, idy, idz;
+  double lo[3];
+  int bc[6];
+};
+
+struct Phys3 {
+  double gamma, R, mu, kappa, prandtl, cfl, pinf, dt_fixed;
+  double Uinf[5];
+};
+
+struct F5 {
+  double *v[5];
+};
+struct F6 {
+  double *v[6];  // rho, u, v, w, p, T
+};
+
+__device__ __forceinline__ long long cid(const Grid3 &g, int i, int j, int k) {
+  return ((long long)(k + NG) * g.H + (j + NG)) * g.W + (i + NG);
+}
+
+// Sec. 2: WENO5 (Jiang-Shu indicators, linear weights 1/10, 6/10, 3/10, eps = 1e-6), left-biased value at the
+// face between f[2] and f[3] of f[0..4]
+__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4) {
+  const double eps = 1e-6;
+  double a = f0 - 2.0 * f1 + f2, b = f0 - 4.0 * f1 + 3.0 * f2;
+  const double b0 = (13.0 / 12.0) * a * a + 0.25 * b * b;
+  a = f1 - 2.0 * f2 + f3;
+  b = f1 - f3;
+  const double b1 = (13.0 / 12.0) * a * a + 0.25 * b * b;
+  a = f2 - 2.0 * f3 + f4;
+  b = 3.0 * f2 - 4.0 * f3 + f4;
+  const double b2 = (13.0 / 12.0) * a * a + 0.25 * b * b;
+  const double q0 = (2.0 * f0 - 7.0 * f1 + 11.0 * f2) * (1.0 / 6.0);
+  const double q1 = (-f1 + 5.0 * f2 + 2.0 * f3) * (1.0 / 6.0);
+  const double q2 = (2.0 * f2 + 5.0 * f3 - f4) * (1.0 / 6.0);
+  const double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+  // alpha_k = d_k / e_k^2 over a common denominator: one division
+  const double s0 = e1 * e1 * e2 * e2, s1 = e0 * e0 * e2 * e2, s2 = e0 * e0 * e1 * e1;
+  const double a0 = 0.1 * s0, a1 = 0.6 * s1, a2 = 0.3 * s2;
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// Sec. 2: LDFSS(0) across a face of unit normal along axis DIR (plain: Mr = 1, so c' = (c_L + c_R) / 2);
+// q = (rho, u, v, w, p)
+template <int DIR>
+__device__ __forceinline__ void ldfss(const double qL[5], const double qR[5], double gamma, double F[5]) {
+  const double rL = qL[0], pL = qL[4], rR = qR[0], pR = qR[4];
+  const double irL = 1.0 / rL, irR = 1.0 / rR;
+  const double cL = sqrt(gamma * pL * irL), cR = sqrt(gamma * pR * irR);
+  const double gg = gamma / (gamma - 1.0);
+  const double HL = gg * pL * irL + 0.5 * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]);
+  const double HR = gg * pR * irR + 0.5 * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]);
+  const double unL = qL[1 + DIR], unR = qR[1 + DIR];
+  const double cs = 0.5 * (cL + cR), ics = 1.0 / cs;
+  const double ML = unL * ics, MR = unR * ics;
+  const double aL = ML >= 0.0 ? 1.0 : 0.0, aR = MR >= 0.0 ? 0.0 : 1.0;
+  const double tL = 1.0 - floor(fabs(ML)), tR = 1.0 - floor(fabs(MR));
+  const double bL = -fmax(tL, 0.0), bR = -fmax(tR, 0.0);
+  const double MpL = 0.25 * (ML + 1.0) * (ML + 1.0);
+  const double MmR = -0.25 * (MR - 1.0) * (MR - 1.0);
+  const double CVL = aL * (1.0 + bL) * ML - bL * MpL;
+  const double CVR = aR * (1.0 + bR) * MR - bR * MmR;
+  const double sq = sqrt(0.5 * (ML * ML + MR * MR)) - 1.0;
+  const double Mh = 0.25 * bL * bR * sq * sq;
+  const double dp = pL - pR, adp = fabs(dp), ic2 = 0.5 * ics * ics;
+  const double MhP = Mh * (1.0 - (dp + adp) * ic2 * irL);
+  const double MhM = Mh * (1.0 - (-dp + adp) * ic2 * irR);
+  const double Cp = CVL - MhP, Cm = CVR + MhM;
+  const double PpL = 0.25 * (ML + 1.0) * (ML + 1.0) * (2.0 - ML);
+  const double PmR = 0.25 * (MR - 1.0) * (MR - 1.0) * (2.0 + MR);
+  const double DL = aL * (1.0 + bL) - bL * PpL;
+  const double DR = aR * (1.0 + bR) - bR * PmR;
+  const double mL = rL * cs * Cp, mR = rR * cs * Cm;
+  const double ph = DL * pL + DR * pR;
+  F[0] = mL + mR;
+  F[1] = mL * qL[1] + mR * qR[1];
+  F[2] = mL * qL[2] + mR * qR[2];
+  F[3] = mL * qL[3] + mR * qR[3];
+  F[1 + DIR] += ph;
+  F[4] = mL * HL + mR * HR;
+}
+
+// primitives (rho, u, v, w, p) and T of every cell, halos included
+__global__ void __launch_bounds__(TB) k3_prim(Grid3 g, Phys3 ph, F5 U, F6 Q) {
+  const long long m = (long long)blockIdx.x * TB + threadIdx.x;
+  if (m >= g.ncell) return;
+  const double r = U.v[0][m], ir = 1.0 / r;
+  const double u = U.v[1][m] * ir, v = U.v[2][m] * ir, w = U.v[3][m] * ir;
+  const double p = (ph.gamma - 1.0) * (U.v[4][m] - 0.5 * r * (u * u + v * v + w * w));
+  Q.v[0][m] = r;
+  Q.v[1][m] = u;
+  Q.v[2][m] = v;
+  Q.v[3][m] = w;
+  Q.v[4][m] = p;
+  Q.v[5][m] = p * ir / ph.R;
+}
+
+// face fluxes of direction DIR: inviscid (WENO5 states, first order where a density or pressure is not
+// positive; LDFSS) minus viscous (normal derivatives across the face, tangential ones from four-cell central
+// averages)
+template <int DIR>
+__global__ void __launch_bounds__(TB) k3_flux(Grid3 g, Phys3 ph, F6 Q, F5 Fo) {
+  const int ex = g.nx + (DIR == 0), ey = g.ny + (DIR == 1), ez = g.nz + (DIR == 2);
+  const long long t = (long long)blockIdx.x * TB + threadIdx.x;
+  if (t >= (long long)ex * ey * ez) return;
+  int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
+  if (DIR == 0) i -= 1;
+  if (DIR == 1) j -= 1;
+  if (DIR == 2) k -= 1;
+  const long long st = DIR == 0 ? 1 : DIR == 1 ? (long long)g.W : g.plane;
+  const long long a = cid(g, i, j, k), b = a + st;
+  double qL[5], qR[5];
+  for (int v = 0; v < 5; v++) {
+    const double *q = Q.v[v];
+    const double f0 = q[a - 2 * st], f1 = q[a - st], f2 = q[a], f3 = q[b], f4 = q[b + st], f5 = q[b + 2 * st];
+    qL[v] = weno5(f0, f1, f2, f3, f4);
+    qR[v] = weno5(f5, f4, f3, f2, f1);
+  }
+  if (!(qL[0] > 0.0) || !(qL[4] > 0.0) || !(qR[0] > 0.0) || !(qR[4] > 0.0)) {
+    for (int v = 0; v < 5; v++) {
+      qL[v] = Q.v[v][a];
+      qR[v] = Q.v[v][b];
+    }
+  }
+  double F[5];
+  ldfss<DIR>(qL, qR, ph.gamma, F);
+  if (ph.mu > 0.0) {
+    // the two tangential directions t1 < t2 and their strides and inverse spacings
+    const int t1 = DIR == 0 ? 1 : 0, t2 = DIR == 2 ? 1 : 2;
+    const long long s1 = t1 == 0 ? 1 : (long long)g.W, s2 = t2 == 1 ? (long long)g.W : g.plane;
+    const double ih[3] = {g.idx, g.idy, g.idz};
+    const double in = ih[DIR], i1 = 0.25 * ih[t1], i2 = 0.25 * ih[t2];
+    const double *T = Q.v[5];
+    double dn[3], d1[3], d2[3];  // d(u, v, w)/dn and the tangential derivatives
+    for (int c = 0; c < 3; c++) {
+      const double *q = Q.v[1 + c];
+      dn[c] = (q[b] - q[a]) * in;
+      d1[c] = (q[a + s1] - q[a - s1] + q[b + s1] - q[b - s1]) * i1;
+      d2[c] = (q[a + s2] - q[a - s2] + q[b + s2] - q[b - s2]) * i2;
+    }
+    // velocity gradient G[c][e] = d u_c / d x_e
+    double G[3][3];
+    for (int c = 0; c < 3; c++) {
+      G[c][DIR] = dn[c];
+      G[c][t1] = d1[c];
+      G[c][t2] = d2[c];
+    }
+    const double div = G[0][0] + G[1][1] + G[2][2];
+    double tau[3];  // row DIR of the viscous stress
+    for (int c = 0; c < 3; c++) tau[c] = ph.mu * (G[c][DIR] + G[DIR][c]);
+    tau[DIR] = ph.mu * (2.0 * G[DIR][DIR] - (2.0 / 3.0) * div);
+    const double qn = -ph.kappa * (T[b] - T[a]) * in;
+    double work = 0.0;
+    for (int c = 0; c < 3; c++) {
+      F[1 + c] -= tau[c];
+      work += 0.5 * (Q.v[1 + c][a] + Q.v[1 + c][b]) * tau[c];
+    }
+    F[4] -= work - qn;
+  }
+  for (int v = 0; v < 5; v++) Fo.v[v][a] = F[v];
+}
+
+// SSP-RK3 stage on the fluid cells: out = Un + dt L, 3/4 Un + 1/4 (in + dt L), 1/3 Un + 2/3 (in + dt L)
+__global__ void __launch_bounds__(TB) k3_update(Grid3 g, Phys3 ph, int stage, F5 Fx, F5 Fy, F5 Fz, F5 Un, F5 In,
+                                                F5 Out, const uint8_t *__restrict__ tags,
+                                                const unsigned long long *__restrict__ lmax) {
+  const long long n = (long long)blockIdx.x * TB + threadIdx.x;
+  if (n >= (long long)g.nx * g.ny * g.nz) return;
+  if (tags[n] != TAG_FLUID) return;
+  const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+  const long long m = cid(g, i, j, k);
+  const double dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl / __longlong_as_double((long long)*lmax);
+  for (int v = 0; v < 5; v++) {
+    const double L = -((Fx.v[v][m] - Fx.v[v][m - 1]) * g.idx + (Fy.v[v][m] - Fy.v[v][m - g.W]) * g.idy +
+                       (Fz.v[v][m] - Fz.v[v][m - g.plane]) * g.idz);
+    double o;
+    if (stage == 1) o = Un.v[v][m] + dt * L;
+    else if (stage == 2) o = 0.75 * Un.v[v][m] + 0.25 * (In.v[v][m] + dt * L);
+    else o = (1.0 / 3.0) * Un.v[v][m] + (2.0 / 3.0) * (In.v[v][m] + dt * L);
+    Out.v[v][m] = o;
+  }
+}
+
+// CFL rule: the largest (|u|+c)/dx + (|v|+c)/dy + (|w|+c)/dz + 2 gamma mu/(Pr rho)(1/dx^2 + 1/dy^2 + 1/dz^2)
+// over the fluid cells (max of positive doubles through their bit patterns: order independent)
+__global__ void __launch_bounds__(TB) k3_lambda(Grid3 g, Phys3 ph, F5 U, const uint8_t *__restrict__ tags,
+                                                unsigned long long *__restrict__ lmax) {
+  const long long n = (long long)blockIdx.x * TB + threadIdx.x;
+  double lam = 0.0;
+  if (n < (long long)g.nx * g.ny * g.nz && tags[n] == TAG_FLUID) {
+    const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+    const long long m = cid(g, i, j, k);
+    const double r = U.v[0][m], ir = 1.0 / r;
+    const double u = U.v[1][m] * ir, v = U.v[2][m] * ir, w = U.v[3][m] * ir;
+    const double p = (ph.gamma - 1.0) * (U.v[4][m] - 0.5 * r * (u * u + v * v + w * w));
+    const double c = sqrt(ph.gamma * ph.R * (p * ir / ph.R));
+    lam = (fabs(u) + c) * g.idx + (fabs(v) + c) * g.idy + (fabs(w) + c) * g.idz +
+          (2.0 * ph.gamma * ph.mu / (ph.prandtl * r)) * (g.idx * g.idx + g.idy * g.idy + g.idz * g.idz);
+  }
+  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  if ((threadIdx.x & 31) == 0 && lam > 0.0) atomicMax(lmax, (unsigned long long)__double_as_longlong(lam));
+}
+
+// domain halos in closed form: the free stream if the cell lies beyond a free-stream side along any axis,
+// else the interior cell reached by mapping each out-of-range index (periodic wrap or zero-gradient clamp)
+__global__ void __launch_bounds__(TB) k3_halo(Grid3 g, Phys3 ph, F5 U) {
+  const long long m = (long long)blockIdx.x * TB + threadIdx.x;
+  if (m >= g.ncell) return;
+  const int I[3] = {(int)(m % g.W) - NG, (int)((m / g.W) % g.H) - NG, (int)(m / g.plane) - NG};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  int S[3];
+  bool halo = false, fs = false;
+  for (int a = 0; a < 3; a++) {
+    S[a] = I[a];
+    if (I[a] >= 0 && I[a] < n[a]) continue;
+    halo = true;
+    const int bc = g.bc[2 * a + (I[a] < 0 ? 0 : 1)];
+    if (bc == IBM_BC_PERIODIC) S[a] = I[a] < 0 ? I[a] + n[a] : I[a] - n[a];
+    else if (bc == IBM_BC_OUTFLOW) S[a] = I[a] < 0 ? 0 : n[a] - 1;
+    else fs = true;
+  }
+  if (!halo) return;
+  if (fs) {
+    for (int v = 0; v < 5; v++) U.v[v][m] = ph.Uinf[v];
+  } else {
+    const long long s = cid(g, S[0], S[1], S[2]);
+    for (int v = 0; v < 5; v++) U.v[v][m] = U.v[v][s];
+  }
+}
+
+// Sec. 4.4-4.6 and Sec. 5 with a static wall: the node takes the probe's (image point's) pressure and
+// temperature and its velocity scaled by xi_node / xi_probe (zero at P')
+__global__ void __launch_bounds__(TB) k3_reconstruct(Grid3 g, Phys3 ph, F5 U, const ibm_stencil3d *__restrict__ st,
+                                                     int first, int count) {
+  const int e = blockIdx.x * TB + threadIdx.x;
+  if (e >= count) return;
+  const ibm_stencil3d &s = st[first + e];
+  const int mask = s.mask;
+  if (mask == 0) return;
+  double qp[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // p, u, v, w, T
+  for (int b = 0; b < 8; b++) {
+    if (!(mask >> b & 1)) continue;
+    const long long id = cid(g, s.i0 + (b & 1), s.j0 + (b >> 1 & 1), s.k0 + (b >> 2));
+    const double r = U.v[0][id], ir = 1.0 / r;
+    const double u = U.v[1][id] * ir, v = U.v[2][id] * ir, w = U.v[3][id] * ir;
+    const double p = (ph.gamma - 1.0) * (U.v[4][id] - 0.5 * r * (u * u + v * v + w * w));
+    const double wb = s.w[b];
+    qp[0] += wb * p;
+    qp[1] += wb * u;
+    qp[2] += wb * v;
+    qp[3] += wb * w;
+    qp[4] += wb * (p * ir / ph.R);
+  }
+  const double ratio = s.xi_node / s.xi_probe;
+  const double u = qp[1] * ratio, v = qp[2] * ratio, w = qp[3] * ratio;
+  const double r = qp[0] / (ph.R * qp[4]);
+  const int node = s.node;
+  const long long id = cid(g, node % g.nx, (node / g.nx) % g.ny, node / (g.nx * g.ny));
+  U.v[0][id] = r;
+  U.v[1][id] = r * u;
+  U.v[2][id] = r * v;
+  U.v[3][id] = r * w;
+  U.v[4][id] = qp[0] / (ph.gamma - 1.0) + 0.5 * r * (u * u + v * v + w * w);
+}
+
+// Eq. 9 per triangle (tri: area per triangle; st: its probe): (-(p_s - p_inf) n + mu (u - (u.n) n) / xi) A
+__global__ void __launch_bounds__(TB) k3_surface_force(Grid3 g, Phys3 ph, F5 U, const ibm_stencil3d *__restrict__ st,
+                                                       const double *__restrict__ area, int ntri,
+                                                       double *__restrict__ fout) {
+  const int f = blockIdx.x * TB + threadIdx.x;
+  if (f >= ntri) return;
+  const ibm_stencil3d &s = st[f];
+  double F[3] = {0.0, 0.0, 0.0};
+  if (s.mask) {
+    double qp[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < 8; b++) {
+      if (!(s.mask >> b & 1)) continue;
+      const long long id = cid(g, s.i0 + (b & 1), s.j0 + (b >> 1 & 1), s.k0 + (b >> 2));
+      const double r = U.v[0][id], ir = 1.0 / r;
+      const double u = U.v[1][id] * ir, v = U.v[2][id] * ir, w = U.v[3][id] * ir;
+      const double p = (ph.gamma - 1.0) * (U.v[4][id] - 0.5 * r * (u * u + v * v + w * w));
+      qp[0] += s.w[b] * p;
+      qp[1] += s.w[b] * u;
+      qp[2] += s.w[b] * v;
+      qp[3] += s.w[b] * w;
+    }
+    const double un = qp[1] * s.n[0] + qp[2] * s.n[1] + qp[3] * s.n[2];
+    for (int a = 0; a < 3; a++) {
+      const double tau = ph.mu * (qp[1 + a] - un * s.n[a]) / s.xi_probe;
+      F[a] = (-(qp[0] - ph.pinf) * s.n[a] + tau) * area[f];
+    }
+  }
+  for (int a = 0; a < 3; a++) fout[3 * f + a] = F[a];
+}
+
+// fixed-order sum of the per-triangle forces (one block: strided partial sums, then a tree)
+__global__ void __launch_bounds__(TB) k3_force_sum(const double *__restrict__ fin, int ntri, double *__restrict__ out) {
+  __shared__ double sh[3][TB];
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int f = threadIdx.x; f < ntri; f += TB)
+    for (int a = 0; a < 3; a++) s[a] += fin[3 * f + a];
+  for (int a = 0; a < 3; a++) sh[a][threadIdx.x] = s[a];
+  __syncthreads();
+  for (int w = TB / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int a = 0; a < 3; a++) sh[a][threadIdx.x] += sh[a][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// end of step on the device: t += dt, last dt
+__global__ void k3_step_end(Phys3 ph, const unsigned long long *__restrict__ lmax, double *__restrict__ time) {
+  const double dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl / __longlong_as_double((long long)*lmax);
+  time[0] = time[0] + dt;
+  time[1] = dt;
+}
+
+inline unsigned nblk(long long n) { return (unsigned)((n + TB - 1) / TB); }
+
+}  // namespace
+
+struct ibm_case3d {
+  Grid3 g{};
+  Phys3 ph{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  ibm_body3d *body = nullptr;
+  int ntri = 0;
+  char *mem = nullptr;  // one allocation for every array below
+  F5 A{}, B{}, C{}, Fx{}, Fy{}, Fz{};
+  F6 Q{};
+  uint8_t *tags = nullptr;        // the body's tags, or the case's own (all fluid) without a body
+  uint8_t *own_tags = nullptr;
+  ibm_stencil3d *st = nullptr;    // listed nodes
+  ibm_stencil3d *sst = nullptr;   // force probes, one per triangle
+  double *tri = nullptr;          // per triangle: centroid, normal (6 doubles), then the areas
+  double *fbuf = nullptr;         // per-triangle forces, then the summed force (3 doubles)
+  unsigned long long *lmax = nullptr;
+  double *time = nullptr;         // t, last dt
+  int *nerr = nullptr;
+  int counts[4] = {0, 0, 0, 0};
+  double ref_area = 1.0;
+  int64_t launches = 0;
+};
+
+static ibm_status cfail(cudaError_t e) { return ibm__noalloc_fail(IBM_ECUDA, cudaGetErrorString(e)); }
+
+extern "C" ibm_status ibm_case3d_destroy(ibm_case3d *c) {
+  if (!c) return IBM_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  ibm_body3d_destroy(c->body);
+  cudaFree(c->mem);
+  cudaFree(c->own_tags);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_case3d_create(const double *verts, int nverts, const int32_t *tris, int ntris,
+                                        const ibm_flow3d *fl, void *cuda_stream, ibm_case3d **out) {
+  if (!out || !fl) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: NULL argument");
+  *out = nullptr;
+  if (fl->nx < 4 || fl->ny < 4 || fl->nz < 4) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: fewer than 4 cells along an axis");
+  for (int a = 0; a < 3; a++)
+    if (!(fl->hi[a] > fl->lo[a])) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: empty domain");
+  for (int k = 0; k < 6; k++)
+    if (fl->bc[k] < IBM_BC_FREESTREAM || fl->bc[k] > IBM_BC_PERIODIC) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: bad boundary condition");
+  for (int a = 0; a < 3; a++)
+    if ((fl->bc[2 * a] == IBM_BC_PERIODIC) != (fl->bc[2 * a + 1] == IBM_BC_PERIODIC))
+      return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: periodic on one side of an axis only");
+  if (!(fl->mach > 0.0) || !(fl->gamma > 1.0) || !(fl->prandtl > 0.0) || !(fl->ref_area > 0.0) ||
+      !(fl->dt_fixed > 0.0 || fl->cfl > 0.0))
+    return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: bad flow parameters");
+  if (ntris < 0 || (ntris > 0 && (!verts || !tris))) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: bad mesh");
+  const long long nn = (long long)fl->nx * fl->ny * fl->nz;
+  if (nn > (1LL << 31) - 1) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: more than 2^31 - 1 cells");
+  ibm_case3d *c = new ibm_case3d();
+  c->ref_area = fl->ref_area;
+  Grid3 &g = c->g;
+  g.nx = fl->nx;
+  g.ny = fl->ny;
+  g.nz = fl->nz;
+  g.W = g.nx + 2 * NG;
+  g.H = g.ny + 2 * NG;
+  g.D = g.nz + 2 * NG;
+  g.plane = (long long)g.W * g.H;
+  g.ncell = g.plane * g.D;
+  g.dx = (fl->hi[0] - fl->lo[0]) / fl->nx;
+  g.dy = (fl->hi[1] - fl->lo[1]) / fl->ny;
+  g.dz = (fl->hi[2] - fl->lo[2]) / fl->nz;
+  g.idx = 1.0 / g.dx;
+  g.idy = 1.0 / g.dy;
+  g.idz = 1.0 / g.dz;
+  for (int a = 0; a < 3; a++) g.lo[a] = fl->lo[a];
+  for (int k = 0; k < 6; k++) g.bc[k] = fl->bc[k];
+  Phys3 &ph = c->ph;
+  ph.gamma = fl->gamma;
+  ph.pinf = 1.0 / (fl->gamma * fl->mach * fl->mach);
+  ph.R = ph.pinf;
+  ph.mu = fl->re > 0.0 ? 1.0 / fl->re : 0.0;
+  ph.kappa = ph.mu * (fl->gamma * ph.R / (fl->gamma - 1.0)) / fl->prandtl;
+  ph.prandtl = fl->prandtl;
+  ph.cfl = fl->cfl;
+  ph.dt_fixed = fl->dt_fixed;
+  const double u = fl->uinf[0], v = fl->uinf[1], w = fl->uinf[2];
+  ph.Uinf[0] = 1.0;
+  ph.Uinf[1] = u;
+  ph.Uinf[2] = v;
+  ph.Uinf[3] = w;
+  ph.Uinf[4] = ph.pinf / (fl->gamma - 1.0) + 0.5 * (u * u + v * v + w * w);
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    c->own_stream = e == cudaSuccess;
+    if (e != cudaSuccess) {
+      delete c;
+      return cfail(e);
+    }
+  }
+  // geometry: classification, tags, lists and stencils on the case stream
+  const double h = std::sqrt(g.dx * g.dx + g.dy * g.dy + g.dz * g.dz);
+  const double dmin = std::fmin(g.dx, std::fmin(g.dy, g.dz));
+  int cap = 0;
+  c->ntri = ntris;
+  if (ntris > 0) {
+    ibm_status s = ibm_body3d_create(verts, nverts, tris, ntris, c->stream, &c->body);
+    if (s == IBM_OK) {
+      ibm_grid3d lg;
+      lg.nx = g.nx;
+      lg.ny = g.ny;
+      lg.nz = g.nz;
+      for (int a = 0; a < 3; a++) {
+        lg.lo[a] = fl->lo[a];
+        lg.hi[a] = fl->hi[a];
+      }
+      s = ibm_body3d_classify(c->body, &lg);
+    }
+    if (s != IBM_OK) {
+      ibm_case3d_destroy(c);
+      return s;
+    }
+    cap = ibm__body3d_capacity(c->body);
+  }
+  // one allocation: 3 x 5 state arrays, 6 primitive arrays, 3 x 5 flux arrays, stencils, triangles, forces
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t arr = up((size_t)g.ncell * sizeof(double));
+  const size_t s_st = up((size_t)std::max(cap, 1) * sizeof(ibm_stencil3d));
+  const size_t s_sst = up((size_t)std::max(ntris, 1) * sizeof(ibm_stencil3d));
+  const size_t s_tri = up((size_t)std::max(ntris, 1) * 7 * sizeof(double));
+  const size_t s_f = up(((size_t)std::max(ntris, 1) * 3 + 3) * sizeof(double));
+  const size_t total = arr * 36 + s_st + s_sst + s_tri + s_f + 256 * 3;
+  e = cudaMalloc(&c->mem, total);
+  if (e != cudaSuccess) {
+    ibm_case3d_destroy(c);
+    return ibm__noalloc_fail(IBM_ENOMEM, "ibm_case3d_create: device allocation failed");
+  }
+  char *p = c->mem;
+  auto take = [&](size_t n) {
+    char *q = p;
+    p += n;
+    return q;
+  };
+  for (int v = 0; v < 5; v++) {
+    c->A.v[v] = (double *)take(arr);
+    c->B.v[v] = (double *)take(arr);
+    c->C.v[v] = (double *)take(arr);
+    c->Fx.v[v] = (double *)take(arr);
+    c->Fy.v[v] = (double *)take(arr);
+    c->Fz.v[v] = (double *)take(arr);
+  }
+  for (int v = 0; v < 6; v++) c->Q.v[v] = (double *)take(arr);
+  c->st = (ibm_stencil3d *)take(s_st);
+  c->sst = (ibm_stencil3d *)take(s_sst);
+  c->tri = (double *)take(s_tri);
+  c->fbuf = (double *)take(s_f);
+  c->lmax = (unsigned long long *)take(256);
+  c->time = (double *)take(256);
+  c->nerr = (int *)take(256);
+  // free stream everywhere (halos and solid cells included)
+  {
+    std::vector<double> fsv((size_t)g.ncell);
+    for (int v = 0; v < 5 && e == cudaSuccess; v++) {
+      std::fill(fsv.begin(), fsv.end(), ph.Uinf[v]);
+      e = cudaMemcpyAsync(c->A.v[v], fsv.data(), (size_t)g.ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c->B.v[v], c->A.v[v], (size_t)g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c->C.v[v], c->A.v[v], (size_t)g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // fsv is reused
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->time, 0, 256, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->nerr, 0, 256, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->lmax, 0, 256, c->stream);
+  if (e != cudaSuccess) {
+    ibm_case3d_destroy(c);
+    return cfail(e);
+  }
+  if (ntris > 0) {
+    // per triangle on the host: centroid, unit normal (the cross product of the edges from the first vertex),
+    // area
+    std::vector<double> td((size_t)ntris * 7);
+    for (int f = 0; f < ntris; f++) {
+      const double *Av = verts + 3 * tris[3 * f], *Bv = verts + 3 * tris[3 * f + 1], *Cv = verts + 3 * tris[3 * f + 2];
+      double e1[3], e2[3], cr[3];
+      for (int a = 0; a < 3; a++) {
+        e1[a] = Bv[a] - Av[a];
+        e2[a] = Cv[a] - Av[a];
+        td[(size_t)6 * f + a] = (Av[a] + Bv[a] + Cv[a]) / 3.0;
+      }
+      cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+      cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+      cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+      const double len = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+      for (int a = 0; a < 3; a++) td[(size_t)6 * f + 3 + a] = cr[a] / len;
+      td[(size_t)6 * ntris + f] = 0.5 * len;
+    }
+    e = cudaMemcpyAsync(c->tri, td.data(), td.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      ibm_case3d_destroy(c);
+      return cfail(e);
+    }
+    const int *dcounts = nullptr;
+    const uint8_t *dtags = nullptr;
+    ibm_status s = ibm__body3d_stencils(c->body, h, dmin, c->st, c->nerr, &dtags, &dcounts, &cap);
+    if (s == IBM_OK) s = ibm__surface3d_stencils(c->body, c->tri, ntris, h, dmin, c->sst);
+    if (s != IBM_OK) {
+      ibm_case3d_destroy(c);
+      return s;
+    }
+    c->tags = (uint8_t *)dtags;
+    int herr = 0;
+    e = cudaMemcpyAsync(c->counts, dcounts, sizeof(c->counts), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, c->nerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      ibm_case3d_destroy(c);
+      return cfail(e);
+    }
+    c->launches += 7;
+    if ((long long)c->counts[0] + c->counts[1] + c->counts[2] + c->counts[3] > cap) {
+      ibm_case3d_destroy(c);
+      return ibm__noalloc_fail(IBM_ECAPACITY, "ibm_case3d_create: more listed nodes than the capacity");
+    }
+    if (herr > 0) {
+      ibm_case3d_destroy(c);
+      return ibm__noalloc_fail(IBM_ESTENCIL, "ibm_case3d_create: a listed node found no valid probe corner");
+    }
+  } else {
+    e = cudaMalloc(&c->own_tags, (size_t)nn);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->own_tags, 0, (size_t)nn, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      ibm_case3d_destroy(c);
+      return cfail(e);
+    }
+    c->tags = c->own_tags;
+  }
+  *out = c;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_case3d_step(ibm_case3d *c, int nsteps) {
+  if (!c || nsteps < 0) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_step: bad argument");
+  const Grid3 &g = c->g;
+  const Phys3 &ph = c->ph;
+  const long long nint = (long long)g.nx * g.ny * g.nz;
+  const int nib = c->counts[0], ngh = c->counts[1] + c->counts[2] + c->counts[3];
+  cudaStream_t s = c->stream;
+  for (int it = 0; it < nsteps; it++) {
+    if (ph.dt_fixed <= 0.0) {
+      cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), s);
+      k3_lambda<<<nblk(nint), TB, 0, s>>>(g, ph, c->A, c->tags, c->lmax);
+      c->launches++;
+    }
+    F5 in[3] = {c->A, c->B, c->C}, out[3] = {c->B, c->C, c->A};
+    for (int k = 0; k < 3; k++) {
+      if (nib) k3_reconstruct<<<nblk(nib), TB, 0, s>>>(g, ph, in[k], c->st, 0, nib);
+      if (ngh) k3_reconstruct<<<nblk(ngh), TB, 0, s>>>(g, ph, in[k], c->st, nib, ngh);
+      k3_halo<<<nblk(g.ncell), TB, 0, s>>>(g, ph, in[k]);
+      k3_prim<<<nblk(g.ncell), TB, 0, s>>>(g, ph, in[k], c->Q);
+      k3_flux<0><<<nblk((long long)(g.nx + 1) * g.ny * g.nz), TB, 0, s>>>(g, ph, c->Q, c->Fx);
+      k3_flux<1><<<nblk((long long)g.nx * (g.ny + 1) * g.nz), TB, 0, s>>>(g, ph, c->Q, c->Fy);
+      k3_flux<2><<<nblk((long long)g.nx * g.ny * (g.nz + 1)), TB, 0, s>>>(g, ph, c->Q, c->Fz);
+      k3_update<<<nblk(nint), TB, 0, s>>>(g, ph, k + 1, c->Fx, c->Fy, c->Fz, c->A, in[k], out[k], c->tags, c->lmax);
+      c->launches += 6 + (nib ? 1 : 0) + (ngh ? 1 : 0);
+    }
+    k3_step_end<<<1, 1, 0, s>>>(ph, c->lmax, c->time);
+    c->launches++;
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? IBM_OK : cfail(e);
+}
+
+extern "C" ibm_status ibm_case3d_get(ibm_case3d *c, int what, void *dst, size_t bytes, int dst_on_device) {
+  if (!c || !dst) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_get: NULL argument");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cfail(e);
+  const Grid3 &g = c->g;
+  const long long nn = (long long)g.nx * g.ny * g.nz;
+  const int total = c->counts[0] + c->counts[1] + c->counts[2] + c->counts[3];
+  const cudaMemcpyKind kd = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  switch (what) {
+    case IBM_3D_TAGS:
+      if (bytes < (size_t)nn) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_get: dst too small");
+      e = cudaMemcpy(dst, c->tags, (size_t)nn, kd);
+      break;
+    case IBM_3D_COUNTS:
+      if (bytes < sizeof(c->counts)) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_get: dst too small");
+      e = cudaMemcpy(dst, c->counts, sizeof(c->counts), dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+      break;
+    case IBM_3D_STENCILS:
+      if (bytes < (size_t)total * sizeof(ibm_stencil3d)) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_get: dst too small");
+      if (total) e = cudaMemcpy(dst, c->st, (size_t)total * sizeof(ibm_stencil3d), kd);
+      break;
+    case IBM_3D_TIME:
+      if (bytes < 2 * sizeof(double)) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_get: dst too small");
+      e = cudaMemcpy(dst, c->time, 2 * sizeof(double), kd);
+      break;
+    case IBM_3D_STATE: {
+      if (bytes < (size_t)5 * nn * sizeof(double)) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_get: dst too small");
+      // interior rows of every variable: one strided 3-D copy per variable
+      for (int v = 0; v < 5 && e == cudaSuccess; v++) {
+        cudaMemcpy3DParms prm = {};
+        prm.srcPtr = make_cudaPitchedPtr(c->A.v[v], (size_t)g.W * sizeof(double), g.W, g.H);
+        prm.srcPos = make_cudaPos(NG * sizeof(double), NG, NG);
+        prm.dstPtr = make_cudaPitchedPtr((double *)dst + (size_t)v * nn, (size_t)g.nx * sizeof(double), g.nx, g.ny);
+        prm.dstPos = make_cudaPos(0, 0, 0);
+        prm.extent = make_cudaExtent((size_t)g.nx * sizeof(double), g.ny, g.nz);
+        prm.kind = kd;
+        e = cudaMemcpy3D(&prm);
+      }
+      break;
+    }
+    default:
+      return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_get: unknown quantity");
+  }
+  return e == cudaSuccess ? IBM_OK : cfail(e);
+}
+
+extern "C" ibm_status ibm_case3d_set_state(ibm_case3d *c, const void *src, size_t bytes, int src_on_device) {
+  if (!c || !src) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_set_state: NULL argument");
+  const Grid3 &g = c->g;
+  const long long nn = (long long)g.nx * g.ny * g.nz;
+  if (bytes < (size_t)5 * nn * sizeof(double)) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_set_state: src too small");
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < 5 && e == cudaSuccess; v++) {
+    cudaMemcpy3DParms prm = {};
+    prm.srcPtr = make_cudaPitchedPtr((void *)((const double *)src + (size_t)v * nn), (size_t)g.nx * sizeof(double), g.nx, g.ny);
+    prm.srcPos = make_cudaPos(0, 0, 0);
+    prm.dstPtr = make_cudaPitchedPtr(c->A.v[v], (size_t)g.W * sizeof(double), g.W, g.H);
+    prm.dstPos = make_cudaPos(NG * sizeof(double), NG, NG);
+    prm.extent = make_cudaExtent((size_t)g.nx * sizeof(double), g.ny, g.nz);
+    prm.kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    e = cudaMemcpy3DAsync(&prm, c->stream);
+  }
+  if (e == cudaSuccess && !src_on_device) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? IBM_OK : cfail(e);
+}
+
+extern "C" ibm_status ibm_case3d_forces(ibm_case3d *c, double out[6]) {
+  if (!c || !out) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_forces: NULL argument");
+  double F[3] = {0.0, 0.0, 0.0};
+  cudaError_t e = cudaSuccess;
+  if (c->ntri > 0) {
+    k3_surface_force<<<nblk(c->ntri), TB, 0, c->stream>>>(c->g, c->ph, c->A, c->sst, c->tri + (size_t)6 * c->ntri,
+                                                          c->ntri, c->fbuf);
+    k3_force_sum<<<1, TB, 0, c->stream>>>(c->fbuf, c->ntri, c->fbuf + (size_t)3 * c->ntri);
+    c->launches += 2;
+    e = cudaMemcpyAsync(F, c->fbuf + (size_t)3 * c->ntri, sizeof(F), cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cfail(e);
+  const double qref = 0.5 * c->ref_area;  // 1/2 rho_inf U_ref^2 A_ref with rho_inf = U_ref = 1
+  for (int a = 0; a < 3; a++) {
+    out[a] = F[a] / qref;
+    out[3 + a] = F[a];
+  }
+  return IBM_OK;
+}
+
+extern "C" int64_t ibm_case3d_launch_count(const ibm_case3d *c) { return c ? c->launches : 0; }

@@ -415,6 +415,155 @@ void host_normals(int nv, const double *v, int ntri, const int *tri, std::vector
   for (int k = 0; k < nv; k++) unit(&vn[(size_t)3 * k]);
 }
 
+// Sec. 4.3-4.6 and Sec. 5 in 3-D: the interpolation cube around X over the cell centres and its weights --
+// trilinear when all eight corners carry an allowed tag, otherwise 1 / r^2 over the allowed ones (a corner hit
+// exactly takes all the weight); returns the corner mask
+__device__ int cube_weights(const Lattice &L, const uint8_t *__restrict__ tags, const double X[3], unsigned allowed,
+                            int o[3], double w[8]) {
+  const int n[3] = {L.nx, L.ny, L.nz};
+  for (int a = 0; a < 3; a++) o[a] = (int)floor((X[a] - L.lo[a]) / L.d[a] - 0.5);
+  int mask = 0;
+  for (int b = 0; b < 8; b++) {
+    const int ci = o[0] + (b & 1), cj = o[1] + (b >> 1 & 1), ck = o[2] + (b >> 2);
+    w[b] = 0.0;
+    if (ci < 0 || ci >= n[0] || cj < 0 || cj >= n[1] || ck < 0 || ck >= n[2]) continue;
+    if (allowed & (1u << tags[((long long)ck * n[1] + cj) * n[0] + ci])) mask |= 1 << b;
+  }
+  if (mask == 255) {
+    double f[3];
+    for (int a = 0; a < 3; a++) {
+      const double c0 = L.lo[a] + ((double)o[a] + 0.5) * L.d[a];
+      f[a] = (X[a] - c0) / L.d[a];
+    }
+    for (int b = 0; b < 8; b++) {
+      const double wx = (b & 1) ? f[0] : 1.0 - f[0];
+      const double wy = (b >> 1 & 1) ? f[1] : 1.0 - f[1];
+      const double wz = (b >> 2) ? f[2] : 1.0 - f[2];
+      w[b] = wx * wy * wz;
+    }
+  } else if (mask != 0) {
+    double inv[8];
+    int hit = -1;
+    for (int b = 0; b < 8; b++) inv[b] = 0.0;
+    for (int b = 0; b < 8 && hit < 0; b++) {
+      if (!(mask >> b & 1)) continue;
+      const int idx[3] = {o[0] + (b & 1), o[1] + (b >> 1 & 1), o[2] + (b >> 2)};
+      double r2 = 0.0;
+      for (int a = 0; a < 3; a++) {
+        const double r = X[a] - (L.lo[a] + ((double)idx[a] + 0.5) * L.d[a]);
+        r2 = r2 + r * r;
+      }
+      if (r2 == 0.0) hit = b;
+      else inv[b] = 1.0 / r2;
+    }
+    if (hit >= 0) {
+      w[hit] = 1.0;
+    } else {
+      double sum = 0.0;
+      for (int b = 0; b < 8; b++)
+        if (mask >> b & 1) sum += inv[b];
+      for (int b = 0; b < 8; b++)
+        if (mask >> b & 1) w[b] = inv[b] / sum;
+    }
+  }
+  return mask;
+}
+
+// one stencil per listed node (IB first, then G1..G3, as listed): boundary point P' = X - xi_node n on the
+// tangent plane through the closest point, probe one cell diagonal h beyond an IB node, mirror image point of a
+// ghost node (at least dmin / 2 from P'), pushed out by dmin up to three times while the cube has no valid
+// corner; a node left without one counts in *nerr
+__global__ void __launch_bounds__(B3) k3_stencils(Lattice L, const uint8_t *__restrict__ tags,
+                                                  const int *__restrict__ nodes, const int *__restrict__ counts,
+                                                  int cap, const ibm_closest3d *__restrict__ rec, double h,
+                                                  double dmin, ibm_stencil3d *__restrict__ out,
+                                                  int *__restrict__ nerr) {
+  const int c0 = counts[0], c1 = counts[1], c2 = counts[2];
+  const int total = min(cap, c0 + c1 + c2 + counts[3]);
+  const int e = blockIdx.x * B3 + threadIdx.x;
+  if (e >= total) return;
+  const int kind = e < c0 ? 0 : e < c0 + c1 ? 1 : e < c0 + c1 + c2 ? 2 : 3;
+  const ibm_closest3d r = rec[e];
+  double X[3];
+  int ijk[3];
+  node_xyz(L, nodes[e], X, ijk);
+  const double xi_node = (X[0] - r.cp[0]) * r.n[0] + (X[1] - r.cp[1]) * r.n[1] + (X[2] - r.cp[2]) * r.n[2];
+  double b[3];
+  for (int a = 0; a < 3; a++) b[a] = X[a] - xi_node * r.n[a];
+  double xi_probe;
+  if (kind == 0) {
+    xi_probe = xi_node + h;
+  } else {
+    xi_probe = -xi_node;
+    if (xi_probe < 0.5 * dmin) xi_probe = 0.5 * dmin;
+  }
+  const unsigned allowed = kind == 0 ? (1u << T_FLUID) : ((1u << T_FLUID) | (1u << T_IB));
+  ibm_stencil3d s;
+  int o[3] = {0, 0, 0}, mask = 0, nstep = 0;
+  for (;;) {
+    double P[3];
+    for (int a = 0; a < 3; a++) P[a] = b[a] + xi_probe * r.n[a];
+    mask = cube_weights(L, tags, P, allowed, o, s.w);
+    if (mask != 0 || nstep == 3) break;
+    xi_probe = xi_probe + dmin;
+    nstep++;
+  }
+  if (mask == 0) atomicAdd(nerr, 1);
+  s.node = nodes[e];
+  s.kind = kind;
+  s.region = r.kind;
+  s.nstep = nstep;
+  s.i0 = o[0];
+  s.j0 = o[1];
+  s.k0 = o[2];
+  s.mask = mask;
+  for (int a = 0; a < 3; a++) {
+    s.n[a] = r.n[a];
+    s.b[a] = b[a];
+  }
+  s.xi_node = xi_node;
+  s.xi_probe = xi_probe;
+  out[e] = s;
+}
+
+// Sec. 6 (Eq. 9) in 3-D: the probe of each triangle one cell diagonal out along its normal from its centroid
+// (mn: per triangle the centroid and the unit normal, 6 doubles), pushed out by dmin up to three times while its
+// cube has no fluid corner; the record's b is the centroid, xi_probe the probe distance, node the triangle
+__global__ void __launch_bounds__(B3) k3_surface_stencils(Lattice L, const uint8_t *__restrict__ tags,
+                                                          const double *__restrict__ mn, int ntri, double h,
+                                                          double dmin, ibm_stencil3d *__restrict__ out) {
+  const int f = blockIdx.x * B3 + threadIdx.x;
+  if (f >= ntri) return;
+  const double m[3] = {mn[6 * f], mn[6 * f + 1], mn[6 * f + 2]}, n[3] = {mn[6 * f + 3], mn[6 * f + 4], mn[6 * f + 5]};
+  ibm_stencil3d s;
+  double xi = h;
+  int o[3] = {0, 0, 0}, mask = 0, nstep = 0;
+  for (int st = 0; st <= 3; st++) {
+    const double P[3] = {m[0] + xi * n[0], m[1] + xi * n[1], m[2] + xi * n[2]};
+    mask = cube_weights(L, tags, P, 1u << T_FLUID, o, s.w);
+    if (mask) break;
+    if (st < 3) {
+      xi = xi + dmin;
+      nstep++;
+    }
+  }
+  s.node = f;
+  s.kind = 0;
+  s.region = IBM_FEATURE_FACE;
+  s.nstep = nstep;
+  s.i0 = o[0];
+  s.j0 = o[1];
+  s.k0 = o[2];
+  s.mask = mask;
+  for (int a = 0; a < 3; a++) {
+    s.n[a] = n[a];
+    s.b[a] = m[a];
+  }
+  s.xi_node = 0.0;
+  s.xi_probe = xi;
+  out[f] = s;
+}
+
 }  // namespace
 
 struct ibm_body3d {
@@ -661,4 +810,33 @@ extern "C" ibm_status ibm_body3d_destroy(ibm_body3d *b) {
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
   return IBM_OK;
+}
+
+// The 3-D flow solver's view of a classification: enqueue the stencils of the listed nodes (k3_stencils) on the
+// body's stream, with h the probe distance and dmin the push-out step, into out (capacity b->cap entries);
+// *nerr (device) receives the number of nodes without a valid corner.  Returns the device tags and per-class
+// counts and the list capacity.
+ibm_status ibm__body3d_stencils(ibm_body3d *b, double h, double dmin, ibm_stencil3d *out, int *nerr,
+                                const uint8_t **tags, const int **counts, int *cap) {
+  if (!b || !b->classified) return ibm__noalloc_fail(IBM_ESTATE, "3-D stencils: body not classified");
+  k3_stencils<<<(b->cap + B3 - 1) / B3, B3, 0, b->stream>>>(b->L, b->tags, b->nodes, b->counts, b->cap, b->rec, h,
+                                                           dmin, out, nerr);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e);
+  *tags = b->tags;
+  *counts = b->counts;
+  *cap = b->cap;
+  return IBM_OK;
+}
+
+int ibm__body3d_capacity(const ibm_body3d *b) { return b ? b->cap : 0; }
+
+// The force probes of the 3-D flow solver (k3_surface_stencils) on the body's stream.
+ibm_status ibm__surface3d_stencils(ibm_body3d *b, const double *mn, int ntri, double h, double dmin,
+                                   ibm_stencil3d *out) {
+  if (!b || !b->classified) return ibm__noalloc_fail(IBM_ESTATE, "3-D surface probes: body not classified");
+  if (ntri > 0)
+    k3_surface_stencils<<<(ntri + B3 - 1) / B3, B3, 0, b->stream>>>(b->L, b->tags, mn, ntri, h, dmin, out);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? IBM_OK : cuda_fail(e);
 }

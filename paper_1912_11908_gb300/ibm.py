@@ -61,7 +61,22 @@ class ibm_grid3d(ctypes.Structure):
 
 CLOSEST3D_DTYPE = np.dtype([("node", "<i4"), ("tri", "<i4"), ("kind", "<i4"), ("reserved", "<i4"),
                             ("cp", "<f8", (3,)), ("n", "<f8", (3,))])
-IBM_3D_TAGS, IBM_3D_COUNTS, IBM_3D_NODES, IBM_3D_CLOSEST = range(4)
+IBM_3D_TAGS, IBM_3D_COUNTS, IBM_3D_NODES, IBM_3D_CLOSEST, IBM_3D_STATE, IBM_3D_STENCILS, IBM_3D_TIME = range(7)
+
+
+class ibm_flow3d(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("bc", ctypes.c_int * 6), ("mach", ctypes.c_double),
+                ("re", ctypes.c_double), ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("uinf", ctypes.c_double * 3), ("dt_fixed", ctypes.c_double),
+                ("ref_area", ctypes.c_double)]
+
+
+STENCIL3D_DTYPE = np.dtype([
+    ("node", "<i4"), ("kind", "<i4"), ("region", "<i4"), ("nstep", "<i4"),
+    ("i0", "<i4"), ("j0", "<i4"), ("k0", "<i4"), ("mask", "<i4"),
+    ("n", "<f8", (3,)), ("b", "<f8", (3,)), ("xi_node", "<f8"), ("xi_probe", "<f8"), ("w", "<f8", (8,)),
+])
 
 
 class ibm_result(ctypes.Structure):
@@ -78,7 +93,8 @@ EXPORTS = ["ibm_create_case", "ibm_classify", "ibm_step", "ibm_get_state", "ibm_
            "ibm_server_destroy", "ibm_server_set_mode", "ibm_server_stats", "ibm_autotune", "ibm_use_tma",
            "ibm_use_persistent", "ibm_persistent_grid", "ibm_stage_launches",
            "ibm_check_float_conversions", "ibm_fma_peak", "ibm_body3d_create", "ibm_body3d_classify",
-           "ibm_body3d_get", "ibm_body3d_destroy"]
+           "ibm_body3d_get", "ibm_body3d_destroy", "ibm_case3d_create", "ibm_case3d_step", "ibm_case3d_get",
+           "ibm_case3d_set_state", "ibm_case3d_forces", "ibm_case3d_launch_count", "ibm_case3d_destroy"]
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 SERVE_BATCHED, SERVE_AUTOTUNE = 1, 2
 SERVER_STATS = ["group_graphs", "group_steps", "group_kernels", "autotune_runs", "capture_us"]
@@ -115,6 +131,17 @@ def load():
     L.ibm_body3d_destroy.argtypes = [vp]
     for name in ("ibm_body3d_create", "ibm_body3d_classify", "ibm_body3d_get", "ibm_body3d_destroy"):
         getattr(L, name).restype = ip
+    L.ibm_case3d_create.argtypes = [vp, ip, vp, ip, ctypes.POINTER(ibm_flow3d), vp, ctypes.POINTER(vp)]
+    L.ibm_case3d_step.argtypes = [vp, ip]
+    L.ibm_case3d_get.argtypes = [vp, ip, vp, sz, ip]
+    L.ibm_case3d_set_state.argtypes = [vp, vp, sz, ip]
+    L.ibm_case3d_forces.argtypes = [vp, vp]
+    L.ibm_case3d_destroy.argtypes = [vp]
+    for name in ("ibm_case3d_create", "ibm_case3d_step", "ibm_case3d_get", "ibm_case3d_set_state",
+                 "ibm_case3d_forces", "ibm_case3d_destroy"):
+        getattr(L, name).restype = ip
+    L.ibm_case3d_launch_count.argtypes = [vp]
+    L.ibm_case3d_launch_count.restype = ctypes.c_int64
     L.ibm_sync.argtypes = [vp]
     L.ibm_destroy_case.argtypes = [vp]
     L.ibm_case_device_bytes.argtypes = [ctypes.POINTER(ibm_geometry), ctypes.POINTER(ibm_grid),
@@ -489,6 +516,76 @@ class Body3D:
     def close(self):
         if getattr(self, "h", None):
             lib().ibm_body3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Case3D:
+    """A 3-D case (ibm_case3d_*): a static closed triangulated body in a uniform block, FP64 SSP-RK3 steps.
+    ``spec`` is a dict from ``workloads.case3d_spec``."""
+
+    def __init__(self, spec, stream=None):
+        self.spec = spec
+        self.n = tuple(spec["n"])
+        self.verts = np.ascontiguousarray(spec["verts"], np.float64).reshape(-1, 3)
+        self.tris = np.ascontiguousarray(spec["tris"], np.int32).reshape(-1, 3)
+        f = ibm_flow3d()
+        f.nx, f.ny, f.nz = self.n
+        for a in range(3):
+            f.lo[a], f.hi[a], f.uinf[a] = spec["lo"][a], spec["hi"][a], spec["uinf"][a]
+        for k in range(6):
+            f.bc[k] = spec["bc"][k]
+        f.mach, f.re, f.gamma, f.prandtl, f.cfl = spec["mach"], spec["re"], spec["gamma"], spec["prandtl"], spec["cfl"]
+        f.dt_fixed, f.ref_area = spec["dt_fixed"], spec["ref_area"]
+        self._flow = f
+        h = ctypes.c_void_p()
+        _check(lib().ibm_case3d_create(self.verts.ctypes.data_as(ctypes.c_void_p), self.verts.shape[0],
+                                       self.tris.ctypes.data_as(ctypes.c_void_p), self.tris.shape[0],
+                                       ctypes.byref(f), ctypes.c_void_p(stream) if stream else None,
+                                       ctypes.byref(h)))
+        self.h = h
+        self.shape = (self.n[2], self.n[1], self.n[0])
+
+    def step(self, n=1):
+        _check(lib().ibm_case3d_step(self.h, int(n)))
+
+    def _get(self, what, arr):
+        _check(lib().ibm_case3d_get(self.h, what, arr.ctypes.data_as(ctypes.c_void_p), arr.nbytes, 0))
+        return arr
+
+    def state(self):
+        return self._get(IBM_3D_STATE, np.empty((5,) + self.shape, np.float64))
+
+    def set_state(self, a):
+        a = np.ascontiguousarray(a, np.float64)
+        assert a.shape == (5,) + self.shape
+        _check(lib().ibm_case3d_set_state(self.h, a.ctypes.data_as(ctypes.c_void_p), a.nbytes, 0))
+
+    def tags(self):
+        return self._get(IBM_3D_TAGS, np.empty(self.shape, np.uint8))
+
+    def counts(self):
+        return self._get(IBM_3D_COUNTS, np.zeros(4, np.int32))
+
+    def stencils(self):
+        return self._get(IBM_3D_STENCILS, np.zeros(int(self.counts().sum()), STENCIL3D_DTYPE))
+
+    def time(self):
+        return self._get(IBM_3D_TIME, np.zeros(2, np.float64))
+
+    def forces(self):
+        out = np.zeros(6, np.float64)
+        _check(lib().ibm_case3d_forces(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def launches(self):
+        return int(lib().ibm_case3d_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ibm_case3d_destroy(self.h)
             self.h = None
 
     def __del__(self):

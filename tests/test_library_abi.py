@@ -103,7 +103,8 @@ def test_header_constants_match_the_binding(ibm):
              "INTERP_LINEAR": "IBM_INTERP_LINEAR", "INTERP_QUADRATIC": "IBM_INTERP_QUADRATIC"}
     for py, c in pairs.items():
         assert getattr(W, py) == h[c], py
-    for name in ("IBM_3D_TAGS", "IBM_3D_COUNTS", "IBM_3D_NODES", "IBM_3D_CLOSEST"):
+    for name in ("IBM_3D_TAGS", "IBM_3D_COUNTS", "IBM_3D_NODES", "IBM_3D_CLOSEST", "IBM_3D_STATE",
+                 "IBM_3D_STENCILS", "IBM_3D_TIME"):
         assert getattr(ibm, name) == h[name], name
 
 
@@ -115,7 +116,8 @@ def test_struct_layouts_match_the_header(ibm, tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("no C compiler")
     structs = {"ibm_geometry": ibm.ibm_geometry, "ibm_grid": ibm.ibm_grid, "ibm_flow": ibm.ibm_flow,
-               "ibm_motion": ibm.ibm_motion, "ibm_result": ibm.ibm_result, "ibm_grid3d": ibm.ibm_grid3d}
+               "ibm_motion": ibm.ibm_motion, "ibm_result": ibm.ibm_result, "ibm_grid3d": ibm.ibm_grid3d,
+               "ibm_flow3d": ibm.ibm_flow3d}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ibm.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (name, name))
@@ -124,6 +126,9 @@ def test_struct_layouts_match_the_header(ibm, tmp_path):
     for f in ibm.STENCIL_DTYPE.names:  # the stencil record is read into a numpy structured array
         lines.append('  printf("ibm_stencil.%s %%zu\\n", offsetof(ibm_stencil, %s));' % (f, f))
     lines.append('  printf("ibm_stencil %zu\\n", sizeof(ibm_stencil));')
+    for f in ibm.STENCIL3D_DTYPE.names:
+        lines.append('  printf("ibm_stencil3d.%s %%zu\\n", offsetof(ibm_stencil3d, %s));' % (f, f))
+    lines.append('  printf("ibm_stencil3d %zu\\n", sizeof(ibm_stencil3d));')
     lines.append("  return 0;\n}")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -137,6 +142,9 @@ def test_struct_layouts_match_the_header(ibm, tmp_path):
     assert int(got["ibm_stencil"]) == ibm.STENCIL_DTYPE.itemsize
     for f in ibm.STENCIL_DTYPE.names:
         assert int(got["ibm_stencil.%s" % f]) == ibm.STENCIL_DTYPE.fields[f][1], f
+    assert int(got["ibm_stencil3d"]) == ibm.STENCIL3D_DTYPE.itemsize
+    for f in ibm.STENCIL3D_DTYPE.names:
+        assert int(got["ibm_stencil3d.%s" % f]) == ibm.STENCIL3D_DTYPE.fields[f][1], f
 
 
 def test_unknown_reconstruction_rejected(ibm):
