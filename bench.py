@@ -53,6 +53,10 @@ FLOPS_PER_CELL_STAGE = 91 * 8 + 110 * 2 + 40 * 2 + 25 + 20
 # BDF part 32 + FP64 output 32 + FP32 mirror 16) and FP64 flops per cell and pseudo stage of the point-implicit
 # update (counted from the formulas, FMA = 2, a division = 1: BDF2 term 13, conversion to primitives 32, enthalpy
 # 10, structured solve 26, stage combination 16, conversion back 28, misc 1)
+# 3-D FP64 flow (sphere): floating-point operations per cell and stage of the 3-D kernels, counted from their
+# formulas as above (FMA = 2, a division or square root = 1): per face WENO5 72 (x 5 variables x 2 sides), LDFSS
+# 119, viscous 62, three faces per cell; primitives 17 and the stage update 60 per cell
+FLOPS3D_PER_CELL_STAGE = 3 * (72 * 10 + 119 + 62) + 17 + 60
 DUAL_BYTES_PER_CELL_STAGE = 161.0
 DUAL_FP64_FLOPS_PER_CELL = 126
 L2_FLUSH_BYTES = 512 << 20
@@ -475,6 +479,11 @@ def run_ours(args, rank, world):
                  "paper_table_a1_context": "4.296e-2 s for 40^3 nodes on one Xeon E5-2670 core (the paper's "
                                            "pre-processing; other hardware, context only)"}
 
+    # 3-D flow past Appendix A's sphere (FP64 SSP-RK3 steps on the case's stream)
+    flow3d = None
+    if rank == 0 and not args.skip_flow3d:
+        flow3d = flow3d_block(ibm, stream, fma)
+
     accuracy = None
     if rank == 0 and not args.skip_accuracy:
         accuracy = accuracy_block(ibm, stream.cuda_stream)
@@ -511,6 +520,7 @@ def run_ours(args, rank, world):
         "kernel_ms_per_step": {g: ms / nprof for g, (ms, n) in prof.items()},
         "accuracy": accuracy,
         "geometry3d": geo3d,
+        "flow3d": flow3d,
         "fp64": fp64,
         "dual_time": dual,
         "moving_body": moving,
@@ -525,6 +535,40 @@ def run_ours(args, rank, world):
     case.close()
     if dist:
         dist.destroy_process_group()
+
+
+def flow3d_block(ibm, stream, fma, steps=10, warmup=3):
+    """FP64 3-D steps of the 192 x 96 x 96 sphere case, CUDA events on the case's stream (the ~600 MB working set
+    is larger than L2); achieved FP64 rate against the measured FP64 FMA rate."""
+    import torch
+    from paper_1912_11908_gb300 import workloads as W
+    spec = W.sphere_m03_re100()
+    c = ibm.Case3D(spec, stream=stream.cuda_stream)
+    cells = int((c.tags() != 1).sum())
+    c.step(warmup)
+    c.time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = c.launches()
+    e0.record(stream)
+    c.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = (c.launches() - n0) // steps
+    f = c.forces()
+    t_end = float(c.time()[0])
+    c.close()
+    nint = spec["n"][0] * spec["n"][1] * spec["n"][2]
+    tflops = FLOPS3D_PER_CELL_STAGE * nint * 3 / (ms * 1e-3) / 1e12
+    peak = fma["fp64"]["tflops"] if fma else None
+    return {"workload": spec["name"], "precision": "fp64", "time_scheme": "SSP-RK3", "grid": list(spec["n"]),
+            "active_cells": cells, "value": cells * 3 / (ms * 1e3), "unit": "Mcell-updates/s", "ms_per_step": ms,
+            "steps": steps, "kernels_per_step": int(launches),
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": tflops, "peak": peak,
+                         "frac": tflops / peak if peak else None,
+                         "peak_source": "measured: FP64 FMA rate (ibm_fma_peak)",
+                         "flops_per_cell_stage": FLOPS3D_PER_CELL_STAGE},
+            "cx_cy_cz": [float(v) for v in f[:3]], "t": t_end}
 
 
 def accuracy_block(ibm, stream):
@@ -688,7 +732,25 @@ def cpu_baseline(args, cells_gpu=None, sample_s=10.0, max_steps=400):
             "sample": "%d RK3 steps of %s after 1 warm-up step (%.1f s)" % (n, spec["name"], t),
             "cpu_model": _cpu_model(), "nproc": os.cpu_count(),
             "single_core": _oracle_single_core(args.workload),
-            "geometry3d_single_core": None if args.skip_geometry3d else _oracle_geometry3d_single_core()}
+            "geometry3d_single_core": None if args.skip_geometry3d else _oracle_geometry3d_single_core(),
+            "flow3d": None if args.skip_flow3d else _oracle_flow3d_step()}
+
+
+def _oracle_flow3d_step():
+    """One FP64 step of the oracle's 3-D sphere case (192 x 96 x 96) on this host's cores, after its
+    classification."""
+    import oracle
+    from paper_1912_11908_gb300 import workloads as W
+    spec = W.sphere_m03_re100()
+    c = oracle.Case3D(spec)
+    c.classify()
+    t0 = time.perf_counter()
+    c.step(1)
+    t = time.perf_counter() - t0
+    cells = int((c.tags() != 1).sum())
+    return {"value": cells * 3 / t / 1e6, "unit": "Mcell-updates/s", "seconds_per_step": t,
+            "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+            "sample": "1 SSP-RK3 step of %s" % spec["name"]}
 
 
 def _oracle_geometry3d_single_core(n=40):
@@ -809,6 +871,7 @@ def main():
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-peaks", action="store_true", help="do not measure the FMA peaks (profiling runs)")
     ap.add_argument("--skip-geometry3d", action="store_true")
+    ap.add_argument("--skip-flow3d", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=32)
     ap.add_argument("--serve-chunk", type=int, default=10)
