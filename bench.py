@@ -538,37 +538,49 @@ def run_ours(args, rank, world):
 
 
 def flow3d_block(ibm, stream, fma, steps=10, warmup=3):
-    """FP64 3-D steps of the 192 x 96 x 96 sphere case, CUDA events on the case's stream (the ~600 MB working set
-    is larger than L2); achieved FP64 rate against the measured FP64 FMA rate."""
+    """3-D steps of the 192 x 96 x 96 sphere case in FP32-bulk and in FP64, CUDA events on the case's stream (the
+    working set, ~600 MB, is larger than L2); the achieved rate of the step's algorithmic flops against the
+    measured FMA rate of the precision the fluxes run in."""
     import torch
     from paper_1912_11908_gb300 import workloads as W
-    spec = W.sphere_m03_re100()
-    c = ibm.Case3D(spec, stream=stream.cuda_stream)
-    cells = int((c.tags() != 1).sum())
-    c.step(warmup)
-    c.time()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n0 = c.launches()
-    e0.record(stream)
-    c.step(steps)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    launches = (c.launches() - n0) // steps
-    f = c.forces()
-    t_end = float(c.time()[0])
-    c.close()
-    nint = spec["n"][0] * spec["n"][1] * spec["n"][2]
-    tflops = FLOPS3D_PER_CELL_STAGE * nint * 3 / (ms * 1e-3) / 1e12
-    peak = fma["fp64"]["tflops"] if fma else None
-    return {"workload": spec["name"], "precision": "fp64", "time_scheme": "SSP-RK3", "grid": list(spec["n"]),
-            "active_cells": cells, "value": cells * 3 / (ms * 1e3), "unit": "Mcell-updates/s", "ms_per_step": ms,
-            "steps": steps, "kernels_per_step": int(launches),
-            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": tflops, "peak": peak,
-                         "frac": tflops / peak if peak else None,
-                         "peak_source": "measured: FP64 FMA rate (ibm_fma_peak)",
-                         "flops_per_cell_stage": FLOPS3D_PER_CELL_STAGE},
-            "cx_cy_cz": [float(v) for v in f[:3]], "t": t_end}
+
+    def run(precision, nsteps):
+        spec = dict(W.sphere_m03_re100(), precision=precision)
+        c = ibm.Case3D(spec, stream=stream.cuda_stream)
+        cells = int((c.tags() != 1).sum())
+        c.step(warmup)
+        c.time()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = c.launches()
+        e0.record(stream)
+        c.step(nsteps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / nsteps
+        launches = (c.launches() - n0) // nsteps
+        f = c.forces()
+        t_end = float(c.time()[0])
+        c.close()
+        nint = spec["n"][0] * spec["n"][1] * spec["n"][2]
+        tflops = FLOPS3D_PER_CELL_STAGE * nint * 3 / (ms * 1e-3) / 1e12
+        key = "fp32" if precision == W.PREC_FP32_BULK else "fp64"
+        peak = fma[key]["tflops"] if fma else None
+        return spec, {"value": cells * 3 / (ms * 1e3), "unit": "Mcell-updates/s", "ms_per_step": ms,
+                      "steps": nsteps, "kernels_per_step": int(launches), "active_cells": cells,
+                      "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": tflops, "peak": peak,
+                                   "frac": tflops / peak if peak else None,
+                                   "peak_source": "measured: %s FMA rate (ibm_fma_peak)" % key.upper(),
+                                   "flops_per_cell_stage": FLOPS3D_PER_CELL_STAGE,
+                                   "scope": "whole step (all kernels) over its device time"},
+                      "cx_cy_cz": [float(v) for v in f[:3]], "t": t_end}
+
+    spec, f32 = run(W.PREC_FP32_BULK, steps * 5)
+    _, f64 = run(W.PREC_FP64, steps)
+    out = {"workload": spec["name"], "time_scheme": "SSP-RK3", "grid": list(spec["n"]), "precision": "fp32_bulk"}
+    out.update(f32)
+    out["fp64"] = f64
+    out["fp32_bulk_speedup"] = f32["value"] / f64["value"]
+    return out
 
 
 def accuracy_block(ibm, stream):

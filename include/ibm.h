@@ -341,8 +341,8 @@ ibm_status ibm_body3d_destroy(ibm_body3d *b);
  * stage update of the fluid cells.  Forces follow Eq. 9 with one midpoint per
  * triangle, the probe one cell diagonal out along the face normal.  These
  * tags, lists and stencils are bit-identical to an FP64 evaluation of the same
- * formulas in IEEE basic operations; the state agrees with such an evaluation
- * to FP64 rounding. */
+ * formulas in IEEE basic operations; the FP64 state agrees with such an
+ * evaluation to FP64 rounding. */
 typedef struct ibm_case3d ibm_case3d;
 
 typedef struct {
@@ -353,6 +353,10 @@ typedef struct {
   double uinf[3];   /* free-stream velocity in reference-speed units */
   double dt_fixed;  /* > 0: fixed time step, else the CFL rule */
   double ref_area;  /* force normalisation area (> 0) */
+  int precision;    /* IBM_PREC_FP64, or IBM_PREC_FP32_BULK: the face fluxes in FP32 on perturbations from the
+                       free stream (rho - 1, u - U_inf, p - p_inf, T - 1; the pressure flux less p_inf and the
+                       energy equation in rho E - rho H_inf, so that no free-stream constant enters an FP32 sum),
+                       the stage combination, IB / ghost reconstruction, halos and dt in FP64 */
 } ibm_flow3d;
 
 /* one IB or ghost node of the 3-D case and its stencil */
@@ -379,7 +383,8 @@ enum {
 /* Create a case at the uniform free stream, t = 0, classify its body and build
  * the stencils (synchronous).  verts: 3*nverts doubles, tris: 3*ntris indices
  * (host, copied; ntris = 0: no body).  cuda_stream: a cudaStream_t or NULL
- * (the case then creates its own).  IBM_EINVAL for bad arguments, IBM_ESTENCIL
+ * (the case then creates its own, which synchronises with the legacy default
+ * stream).  IBM_EINVAL for bad arguments, IBM_ESTENCIL
  * if a listed node finds no probe corner, IBM_ENOMEM / IBM_ECUDA on device
  * errors (no case is returned then). */
 ibm_status ibm_case3d_create(const double *verts, int nverts, const int32_t *tris, int ntris,

@@ -354,6 +354,184 @@ __global__ void k3_step_end(Phys3 ph, const unsigned long long *__restrict__ lma
   time[1] = dt;
 }
 
+// ---- FP32-bulk stages: the face fluxes in FP32 on perturbations from the free stream --------------------------
+// The FP64 stage state is turned into FP32 perturbation primitives (rho', u', v', w', p', T') = (rho - 1,
+// u - U_inf, ..., p - p_inf, T - 1); the fluxes are assembled so that no free-stream constant enters an FP32
+// sum: the pressure term as (p_half - p_inf) = p_inf (D_L + D_R - 1) + D_L p'_L + D_R p'_R, and the energy
+// equation in the variable rho E - rho H_inf, whose flux is rho u H' (H' = H - H_inf); the update restores
+// L(rho E) = L' + H_inf L(rho) and combines the stages in FP64.
+
+struct P32 {
+  float pinf, gamma, gg, mu, kappa, u0[3];  // gg = gamma / (gamma - 1)
+};
+
+struct F5f {
+  float *v[5];
+};
+struct F6f {
+  float *v[6];  // rho', u', v', w', p', T'
+};
+
+__global__ void __launch_bounds__(TB) k3_prim32(Grid3 g, Phys3 ph, F5 U, F6f Q) {
+  const long long m = (long long)blockIdx.x * TB + threadIdx.x;
+  if (m >= g.ncell) return;
+  const double r = U.v[0][m], ir = 1.0 / r;
+  const double u = U.v[1][m] * ir, v = U.v[2][m] * ir, w = U.v[3][m] * ir;
+  const double p = (ph.gamma - 1.0) * (U.v[4][m] - 0.5 * r * (u * u + v * v + w * w));
+  Q.v[0][m] = (float)(r - 1.0);
+  Q.v[1][m] = (float)(u - ph.Uinf[1]);
+  Q.v[2][m] = (float)(v - ph.Uinf[2]);
+  Q.v[3][m] = (float)(w - ph.Uinf[3]);
+  Q.v[4][m] = (float)(p - ph.pinf);
+  Q.v[5][m] = (float)(p * ir / ph.R - 1.0);
+}
+
+__device__ __forceinline__ float weno5f(float f0, float f1, float f2, float f3, float f4) {
+  const float eps = 1e-6f;
+  float a = f0 - 2.0f * f1 + f2, b = f0 - 4.0f * f1 + 3.0f * f2;
+  const float b0 = (13.0f / 12.0f) * a * a + 0.25f * b * b;
+  a = f1 - 2.0f * f2 + f3;
+  b = f1 - f3;
+  const float b1 = (13.0f / 12.0f) * a * a + 0.25f * b * b;
+  a = f2 - 2.0f * f3 + f4;
+  b = 3.0f * f2 - 4.0f * f3 + f4;
+  const float b2 = (13.0f / 12.0f) * a * a + 0.25f * b * b;
+  const float q0 = (2.0f * f0 - 7.0f * f1 + 11.0f * f2) * (1.0f / 6.0f);
+  const float q1 = (-f1 + 5.0f * f2 + 2.0f * f3) * (1.0f / 6.0f);
+  const float q2 = (2.0f * f2 + 5.0f * f3 - f4) * (1.0f / 6.0f);
+  // alpha_k = d_k / (eps + beta_k)^2 through FP32 reciprocals (in range for beta_k up to ~1e19)
+  const float e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+  const float i0 = __frcp_rn(e0 * e0), i1 = __frcp_rn(e1 * e1), i2 = __frcp_rn(e2 * e2);
+  const float a0 = 0.1f * i0, a1 = 0.6f * i1, a2 = 0.3f * i2;
+  return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+}
+
+// LDFSS(0) (Mr = 1) on perturbation states q' = (rho', u', v', w', p'); F = mass, momentum less p_inf n,
+// rho u H'
+template <int DIR>
+__device__ __forceinline__ void ldfss32(const float qL[5], const float qR[5], const P32 &c, float F[5]) {
+  const float rL = 1.0f + qL[0], rR = 1.0f + qR[0];
+  const float irL = __frcp_rn(rL), irR = __frcp_rn(rR);
+  const float pL = c.pinf + qL[4], pR = c.pinf + qR[4];
+  const float cL = sqrtf(c.gamma * pL * irL), cR = sqrtf(c.gamma * pR * irR);
+  float uL[3], uR[3];
+  for (int a = 0; a < 3; a++) {
+    uL[a] = c.u0[a] + qL[1 + a];
+    uR[a] = c.u0[a] + qR[1 + a];
+  }
+  // H' = gamma/(gamma-1) (p / rho - p_inf) + (|u|^2 - |U_inf|^2) / 2
+  float kL = 0.0f, kR = 0.0f;
+  for (int a = 0; a < 3; a++) {
+    kL += qL[1 + a] * (2.0f * c.u0[a] + qL[1 + a]);
+    kR += qR[1 + a] * (2.0f * c.u0[a] + qR[1 + a]);
+  }
+  const float HL = c.gg * (qL[4] - c.pinf * qL[0]) * irL + 0.5f * kL;
+  const float HR = c.gg * (qR[4] - c.pinf * qR[0]) * irR + 0.5f * kR;
+  const float unL = uL[DIR], unR = uR[DIR];
+  const float cs = 0.5f * (cL + cR), ics = __frcp_rn(cs);
+  const float ML = unL * ics, MR = unR * ics;
+  const float aL = ML >= 0.0f ? 1.0f : 0.0f, aR = MR >= 0.0f ? 0.0f : 1.0f;
+  const float bL = -fmaxf(1.0f - floorf(fabsf(ML)), 0.0f), bR = -fmaxf(1.0f - floorf(fabsf(MR)), 0.0f);
+  const float MpL = 0.25f * (ML + 1.0f) * (ML + 1.0f);
+  const float MmR = -0.25f * (MR - 1.0f) * (MR - 1.0f);
+  const float CVL = aL * (1.0f + bL) * ML - bL * MpL;
+  const float CVR = aR * (1.0f + bR) * MR - bR * MmR;
+  const float sq = sqrtf(0.5f * (ML * ML + MR * MR)) - 1.0f;
+  const float Mh = 0.25f * bL * bR * sq * sq;
+  const float dp = qL[4] - qR[4], adp = fabsf(dp), ic2 = 0.5f * ics * ics;
+  const float MhP = Mh * (1.0f - (dp + adp) * ic2 * irL);
+  const float MhM = Mh * (1.0f - (-dp + adp) * ic2 * irR);
+  const float Cp = CVL - MhP, Cm = CVR + MhM;
+  const float PpL = 0.25f * (ML + 1.0f) * (ML + 1.0f) * (2.0f - ML);
+  const float PmR = 0.25f * (MR - 1.0f) * (MR - 1.0f) * (2.0f + MR);
+  const float DL = aL * (1.0f + bL) - bL * PpL;
+  const float DR = aR * (1.0f + bR) - bR * PmR;
+  const float mL = rL * cs * Cp, mR = rR * cs * Cm;
+  const float php = c.pinf * ((DL + DR) - 1.0f) + (DL * qL[4] + DR * qR[4]);
+  F[0] = mL + mR;
+  for (int a = 0; a < 3; a++) F[1 + a] = mL * uL[a] + mR * uR[a];
+  F[1 + DIR] += php;
+  F[4] = mL * HL + mR * HR;
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(TB) k3_flux32(Grid3 g, P32 c, F6f Q, F5f Fo) {
+  const int ex = g.nx + (DIR == 0), ey = g.ny + (DIR == 1), ez = g.nz + (DIR == 2);
+  const long long t = (long long)blockIdx.x * TB + threadIdx.x;
+  if (t >= (long long)ex * ey * ez) return;
+  int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
+  if (DIR == 0) i -= 1;
+  if (DIR == 1) j -= 1;
+  if (DIR == 2) k -= 1;
+  const long long st = DIR == 0 ? 1 : DIR == 1 ? (long long)g.W : g.plane;
+  const long long a = cid(g, i, j, k), b = a + st;
+  float qL[5], qR[5];
+  for (int v = 0; v < 5; v++) {
+    const float *q = Q.v[v];
+    const float f0 = q[a - 2 * st], f1 = q[a - st], f2 = q[a], f3 = q[b], f4 = q[b + st], f5 = q[b + 2 * st];
+    qL[v] = weno5f(f0, f1, f2, f3, f4);
+    qR[v] = weno5f(f5, f4, f3, f2, f1);
+  }
+  if (!(1.0f + qL[0] > 0.0f) || !(c.pinf + qL[4] > 0.0f) || !(1.0f + qR[0] > 0.0f) || !(c.pinf + qR[4] > 0.0f)) {
+    for (int v = 0; v < 5; v++) {
+      qL[v] = Q.v[v][a];
+      qR[v] = Q.v[v][b];
+    }
+  }
+  float F[5];
+  ldfss32<DIR>(qL, qR, c, F);
+  if (c.mu > 0.0f) {
+    const int t1 = DIR == 0 ? 1 : 0, t2 = DIR == 2 ? 1 : 2;
+    const long long s1 = t1 == 0 ? 1 : (long long)g.W, s2 = t2 == 1 ? (long long)g.W : g.plane;
+    const float ih[3] = {(float)g.idx, (float)g.idy, (float)g.idz};
+    const float in = ih[DIR], i1 = 0.25f * ih[t1], i2 = 0.25f * ih[t2];
+    float G[3][3];
+    for (int cc = 0; cc < 3; cc++) {
+      const float *q = Q.v[1 + cc];
+      G[cc][DIR] = (q[b] - q[a]) * in;
+      G[cc][t1] = (q[a + s1] - q[a - s1] + q[b + s1] - q[b - s1]) * i1;
+      G[cc][t2] = (q[a + s2] - q[a - s2] + q[b + s2] - q[b - s2]) * i2;
+    }
+    const float div = G[0][0] + G[1][1] + G[2][2];
+    float tau[3];
+    for (int cc = 0; cc < 3; cc++) tau[cc] = c.mu * (G[cc][DIR] + G[DIR][cc]);
+    tau[DIR] = c.mu * (2.0f * G[DIR][DIR] - (2.0f / 3.0f) * div);
+    const float qn = -c.kappa * (Q.v[5][b] - Q.v[5][a]) * in;
+    float work = 0.0f;
+    for (int cc = 0; cc < 3; cc++) {
+      F[1 + cc] -= tau[cc];
+      work += (c.u0[cc] + 0.5f * (Q.v[1 + cc][a] + Q.v[1 + cc][b])) * tau[cc];
+    }
+    F[4] -= work - qn;
+  }
+  for (int v = 0; v < 5; v++) Fo.v[v][a] = F[v];
+}
+
+// SSP-RK3 stage on the fluid cells in FP64 from the FP32 flux divergence (L(rho E) = L' + H_inf L(rho))
+__global__ void __launch_bounds__(TB) k3_update32(Grid3 g, Phys3 ph, double Hinf, int stage, F5f Fx, F5f Fy, F5f Fz,
+                                                  F5 Un, F5 In, F5 Out, const uint8_t *__restrict__ tags,
+                                                  const unsigned long long *__restrict__ lmax) {
+  const long long n = (long long)blockIdx.x * TB + threadIdx.x;
+  if (n >= (long long)g.nx * g.ny * g.nz) return;
+  if (tags[n] != TAG_FLUID) return;
+  const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+  const long long m = cid(g, i, j, k);
+  const double dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl / __longlong_as_double((long long)*lmax);
+  const float ix = (float)g.idx, iy = (float)g.idy, iz = (float)g.idz;
+  double L[5];
+  for (int v = 0; v < 5; v++)
+    L[v] = (double)(-((Fx.v[v][m] - Fx.v[v][m - 1]) * ix + (Fy.v[v][m] - Fy.v[v][m - g.W]) * iy +
+                      (Fz.v[v][m] - Fz.v[v][m - g.plane]) * iz));
+  L[4] += Hinf * L[0];
+  for (int v = 0; v < 5; v++) {
+    double o;
+    if (stage == 1) o = Un.v[v][m] + dt * L[v];
+    else if (stage == 2) o = 0.75 * Un.v[v][m] + 0.25 * (In.v[v][m] + dt * L[v]);
+    else o = (1.0 / 3.0) * Un.v[v][m] + (2.0 / 3.0) * (In.v[v][m] + dt * L[v]);
+    Out.v[v][m] = o;
+  }
+}
+
 inline unsigned nblk(long long n) { return (unsigned)((n + TB - 1) / TB); }
 
 }  // namespace
@@ -379,6 +557,9 @@ struct ibm_case3d {
   int *nerr = nullptr;
   int counts[4] = {0, 0, 0, 0};
   double ref_area = 1.0;
+  int precision = IBM_PREC_FP64;
+  P32 p32{};
+  double Hinf = 0.0;
   int64_t launches = 0;
 };
 
@@ -413,8 +594,11 @@ extern "C" ibm_status ibm_case3d_create(const double *verts, int nverts, const i
   if (ntris < 0 || (ntris > 0 && (!verts || !tris))) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: bad mesh");
   const long long nn = (long long)fl->nx * fl->ny * fl->nz;
   if (nn > (1LL << 31) - 1) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: more than 2^31 - 1 cells");
+  if (fl->precision != IBM_PREC_FP64 && fl->precision != IBM_PREC_FP32_BULK)
+    return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_create: unknown precision");
   ibm_case3d *c = new ibm_case3d();
   c->ref_area = fl->ref_area;
+  c->precision = fl->precision;
   Grid3 &g = c->g;
   g.nx = fl->nx;
   g.ny = fl->ny;
@@ -447,11 +631,18 @@ extern "C" ibm_status ibm_case3d_create(const double *verts, int nverts, const i
   ph.Uinf[2] = v;
   ph.Uinf[3] = w;
   ph.Uinf[4] = ph.pinf / (fl->gamma - 1.0) + 0.5 * (u * u + v * v + w * w);
+  c->Hinf = fl->gamma / (fl->gamma - 1.0) * ph.pinf + 0.5 * (u * u + v * v + w * w);
+  c->p32.pinf = (float)ph.pinf;
+  c->p32.gamma = (float)fl->gamma;
+  c->p32.gg = (float)(fl->gamma / (fl->gamma - 1.0));
+  c->p32.mu = (float)ph.mu;
+  c->p32.kappa = (float)ph.kappa;
+  for (int a = 0; a < 3; a++) c->p32.u0[a] = (float)fl->uinf[a];
   cudaError_t e = cudaSuccess;
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
   } else {
-    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    e = cudaStreamCreate(&c->stream);  // synchronises with the legacy default stream, as a 2-D case's own
     c->own_stream = e == cudaSuccess;
     if (e != cudaSuccess) {
       delete c;
@@ -618,11 +809,31 @@ extern "C" ibm_status ibm_case3d_step(ibm_case3d *c, int nsteps) {
       if (nib) k3_reconstruct<<<nblk(nib), TB, 0, s>>>(g, ph, in[k], c->st, 0, nib);
       if (ngh) k3_reconstruct<<<nblk(ngh), TB, 0, s>>>(g, ph, in[k], c->st, nib, ngh);
       k3_halo<<<nblk(g.ncell), TB, 0, s>>>(g, ph, in[k]);
-      k3_prim<<<nblk(g.ncell), TB, 0, s>>>(g, ph, in[k], c->Q);
-      k3_flux<0><<<nblk((long long)(g.nx + 1) * g.ny * g.nz), TB, 0, s>>>(g, ph, c->Q, c->Fx);
-      k3_flux<1><<<nblk((long long)g.nx * (g.ny + 1) * g.nz), TB, 0, s>>>(g, ph, c->Q, c->Fy);
-      k3_flux<2><<<nblk((long long)g.nx * g.ny * (g.nz + 1)), TB, 0, s>>>(g, ph, c->Q, c->Fz);
-      k3_update<<<nblk(nint), TB, 0, s>>>(g, ph, k + 1, c->Fx, c->Fy, c->Fz, c->A, in[k], out[k], c->tags, c->lmax);
+      const unsigned bx = nblk((long long)(g.nx + 1) * g.ny * g.nz), by = nblk((long long)g.nx * (g.ny + 1) * g.nz),
+                     bz = nblk((long long)g.nx * g.ny * (g.nz + 1));
+      if (c->precision == IBM_PREC_FP32_BULK) {
+        // the FP32 arrays live in the FP64 primitive and flux arrays' storage
+        F6f q;
+        F5f fx, fy, fz;
+        for (int v = 0; v < 6; v++) q.v[v] = (float *)c->Q.v[v];
+        for (int v = 0; v < 5; v++) {
+          fx.v[v] = (float *)c->Fx.v[v];
+          fy.v[v] = (float *)c->Fy.v[v];
+          fz.v[v] = (float *)c->Fz.v[v];
+        }
+        k3_prim32<<<nblk(g.ncell), TB, 0, s>>>(g, ph, in[k], q);
+        k3_flux32<0><<<bx, TB, 0, s>>>(g, c->p32, q, fx);
+        k3_flux32<1><<<by, TB, 0, s>>>(g, c->p32, q, fy);
+        k3_flux32<2><<<bz, TB, 0, s>>>(g, c->p32, q, fz);
+        k3_update32<<<nblk(nint), TB, 0, s>>>(g, ph, c->Hinf, k + 1, fx, fy, fz, c->A, in[k], out[k], c->tags,
+                                              c->lmax);
+      } else {
+        k3_prim<<<nblk(g.ncell), TB, 0, s>>>(g, ph, in[k], c->Q);
+        k3_flux<0><<<bx, TB, 0, s>>>(g, ph, c->Q, c->Fx);
+        k3_flux<1><<<by, TB, 0, s>>>(g, ph, c->Q, c->Fy);
+        k3_flux<2><<<bz, TB, 0, s>>>(g, ph, c->Q, c->Fz);
+        k3_update<<<nblk(nint), TB, 0, s>>>(g, ph, k + 1, c->Fx, c->Fy, c->Fz, c->A, in[k], out[k], c->tags, c->lmax);
+      }
       c->launches += 6 + (nib ? 1 : 0) + (ngh ? 1 : 0);
     }
     k3_step_end<<<1, 1, 0, s>>>(ph, c->lmax, c->time);

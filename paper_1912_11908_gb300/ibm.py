@@ -69,7 +69,7 @@ class ibm_flow3d(ctypes.Structure):
                 ("hi", ctypes.c_double * 3), ("bc", ctypes.c_int * 6), ("mach", ctypes.c_double),
                 ("re", ctypes.c_double), ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("uinf", ctypes.c_double * 3), ("dt_fixed", ctypes.c_double),
-                ("ref_area", ctypes.c_double)]
+                ("ref_area", ctypes.c_double), ("precision", ctypes.c_int)]
 
 
 STENCIL3D_DTYPE = np.dtype([
@@ -539,6 +539,7 @@ class Case3D:
             f.bc[k] = spec["bc"][k]
         f.mach, f.re, f.gamma, f.prandtl, f.cfl = spec["mach"], spec["re"], spec["gamma"], spec["prandtl"], spec["cfl"]
         f.dt_fixed, f.ref_area = spec["dt_fixed"], spec["ref_area"]
+        f.precision = spec.get("precision", W.PREC_FP64)
         self._flow = f
         h = ctypes.c_void_p()
         _check(lib().ibm_case3d_create(self.verts.ctypes.data_as(ctypes.c_void_p), self.verts.shape[0],

@@ -221,7 +221,7 @@ def box_mesh(lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
 
 
 def case3d_spec(verts, tris, n, lo, hi, mach, re, bc, *, cfl=0.5, uinf=(1.0, 0.0, 0.0), gamma=1.4, prandtl=0.72,
-                dt_fixed=0.0, ref_area=1.0, name=""):
+                dt_fixed=0.0, ref_area=1.0, precision=PREC_FP64, name=""):
     """A 3-D case: nx * ny * nz cells over [lo, hi], a static closed triangulated body (verts None: no body),
     domain sides in the order x-low, x-high, y-low, y-high, z-low, z-high."""
     if verts is None:
@@ -230,7 +230,8 @@ def case3d_spec(verts, tris, n, lo, hi, mach, re, bc, *, cfl=0.5, uinf=(1.0, 0.0
                 tris=np.ascontiguousarray(tris, np.int32).reshape(-1, 3), n=tuple(int(v) for v in n),
                 lo=tuple(float(v) for v in lo), hi=tuple(float(v) for v in hi), mach=float(mach), re=float(re),
                 bc=tuple(int(b) for b in bc), cfl=float(cfl), uinf=tuple(float(u) for u in uinf), gamma=float(gamma),
-                prandtl=float(prandtl), dt_fixed=float(dt_fixed), ref_area=float(ref_area))
+                prandtl=float(prandtl), dt_fixed=float(dt_fixed), ref_area=float(ref_area),
+                precision=int(precision))
 
 
 FAR3D = (BC_FREESTREAM, BC_OUTFLOW) + (BC_FREESTREAM,) * 4

@@ -154,6 +154,51 @@ def test_quiescent_sphere_stays_at_rest(ibm):
     assert np.abs(U[0][live] - 1.0).max() < 1e-13
 
 
+@pytest.mark.parametrize("body", ["sphere", "box"])
+def test_fp32_bulk_against_the_fp64_oracle(ibm, orc, body):
+    """FP32-bulk fluxes (perturbation form) with FP64 stage accumulation: forces within 1e-3 of the FP64
+    oracle's (the FP32-bulk bar of the 2-D solver), state within 1e-4 of each variable's range, geometry
+    unchanged."""
+    if body == "sphere":
+        spec, n = _sphere(), 12
+    else:
+        verts, tris = W.box_mesh((-0.3, -0.25, -0.35), (0.35, 0.3, 0.25))
+        spec = W.case3d_spec(verts, tris, (29, 23, 27), (-1.0, -0.9, -1.1), (1.9, 1.4, 1.6), 0.5, 200.0,
+                             (FS, OUT, FS, OUT, FS, OUT), uinf=(0.8, 0.3, -0.4), ref_area=0.5)
+        n = 8
+    g = ibm.Case3D(dict(spec, precision=W.PREC_FP32_BULK))
+    o = orc.Case3D(spec)
+    g.step(n)
+    o.step(n)
+    np.testing.assert_array_equal(g.tags(), o.tags())
+    e = _state_error(g.state(), o.state(), o.tags())
+    d = np.abs(g.forces()[:3] - o.forces()[:3])
+    print("3-D %s FP32-bulk, %d steps: state %.2e, |dC| %s (oracle %s)" % (body, n, e, d, o.forces()[:3]))
+    assert e <= 1e-4, e
+    assert d.max() <= 1e-3, d
+    np.testing.assert_allclose(g.time(), [o.time(), o.last_dt()], rtol=1e-6)
+
+
+def test_fp32_bulk_keeps_rest_and_free_stream(ibm):
+    """The perturbation form keeps p_inf and H_inf out of the FP32 sums: fluid at rest around the sphere stays
+    at rest, and a uniform stream in a box without a body stays uniform, to FP64 rounding."""
+    verts, tris = W.uv_sphere(radius=0.5)
+    spec = W.case3d_spec(verts, tris, (24, 24, 24), (-1, -1, -1), (1, 1, 1), 0.3, 100.0, (FS,) * 6,
+                         uinf=(0.0, 0.0, 0.0), dt_fixed=1e-3, precision=W.PREC_FP32_BULK)
+    g = ibm.Case3D(spec)
+    g.step(3)
+    U = g.state()
+    live = g.tags() != 1
+    assert np.abs(U[1:4][:, live]).max() < 1e-12
+    assert np.abs(U[0][live] - 1.0).max() < 1e-13
+    spec = W.case3d_spec(None, None, (20, 12, 9), (0, 0, 0), (1, 1, 1), 0.8, 100.0, W.FAR3D, uinf=(0.9, -0.2, 0.3),
+                         precision=W.PREC_FP32_BULK)
+    g = ibm.Case3D(spec)
+    U0 = g.state()
+    g.step(4)
+    np.testing.assert_allclose(g.state(), U0, rtol=1e-14, atol=1e-14)
+
+
 def test_bad_probe_is_reported(ibm):
     """A body whose IB probes leave the domain (a box touching a domain side) is refused with IBM_ESTENCIL,
     not stepped with an empty stencil."""
