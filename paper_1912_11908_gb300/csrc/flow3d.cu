@@ -29,7 +29,9 @@ int ibm__body3d_capacity(const ibm_body3d *b);
 namespace {
 
 constexpr int NG = 3;
-constexpr int TB = 256;
+constexpr int TB = 256;        // threads per block of the list kernels
+constexpr int BX = 32, BY = 4; // block of the per-cell and per-face kernels: 32 cells along x, 4 rows
+constexpr int TC = BX * BY;
 constexpr uint8_t TAG_FLUID = IBM_TAG_FLUID;
 
 struct Grid3 {
@@ -119,9 +121,10 @@ __device__ __forceinline__ void ldfss(const double qL[5], const double qR[5], do
 }
 
 // primitives (rho, u, v, w, p) and T of every cell, halos included
-__global__ void __launch_bounds__(TB) k3_prim(Grid3 g, Phys3 ph, F5 U, F6 Q) {
-  const long long m = (long long)blockIdx.x * TB + threadIdx.x;
-  if (m >= g.ncell) return;
+__global__ void __launch_bounds__(TC) k3_prim(Grid3 g, Phys3 ph, F5 U, F6 Q) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  if (x >= g.W || y >= g.H) return;
+  const long long m = ((long long)blockIdx.z * g.H + y) * g.W + x;
   const double r = U.v[0][m], ir = 1.0 / r;
   const double u = U.v[1][m] * ir, v = U.v[2][m] * ir, w = U.v[3][m] * ir;
   const double p = (ph.gamma - 1.0) * (U.v[4][m] - 0.5 * r * (u * u + v * v + w * w));
@@ -137,11 +140,10 @@ __global__ void __launch_bounds__(TB) k3_prim(Grid3 g, Phys3 ph, F5 U, F6 Q) {
 // positive; LDFSS) minus viscous (normal derivatives across the face, tangential ones from four-cell central
 // averages)
 template <int DIR>
-__global__ void __launch_bounds__(TB) k3_flux(Grid3 g, Phys3 ph, F6 Q, F5 Fo) {
-  const int ex = g.nx + (DIR == 0), ey = g.ny + (DIR == 1), ez = g.nz + (DIR == 2);
-  const long long t = (long long)blockIdx.x * TB + threadIdx.x;
-  if (t >= (long long)ex * ey * ez) return;
-  int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
+__global__ void __launch_bounds__(TC) k3_flux(Grid3 g, Phys3 ph, F6 Q, F5 Fo) {
+  // faces i + 1/2 (DIR 0) for i in [-1, nx - 1], likewise along y and z; one thread per face
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx + (DIR == 0) || j >= g.ny + (DIR == 1)) return;
   if (DIR == 0) i -= 1;
   if (DIR == 1) j -= 1;
   if (DIR == 2) k -= 1;
@@ -199,15 +201,13 @@ __global__ void __launch_bounds__(TB) k3_flux(Grid3 g, Phys3 ph, F6 Q, F5 Fo) {
 }
 
 // SSP-RK3 stage on the fluid cells: out = Un + dt L, 3/4 Un + 1/4 (in + dt L), 1/3 Un + 2/3 (in + dt L)
-__global__ void __launch_bounds__(TB) k3_update(Grid3 g, Phys3 ph, int stage, F5 Fx, F5 Fy, F5 Fz, F5 Un, F5 In,
-                                                F5 Out, const uint8_t *__restrict__ tags,
-                                                const unsigned long long *__restrict__ lmax) {
-  const long long n = (long long)blockIdx.x * TB + threadIdx.x;
-  if (n >= (long long)g.nx * g.ny * g.nz) return;
-  if (tags[n] != TAG_FLUID) return;
-  const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+__global__ void __launch_bounds__(TC) k3_update(Grid3 g, int stage, F5 Fx, F5 Fy, F5 Fz, F5 Un, F5 In, F5 Out,
+                                                const uint8_t *__restrict__ tags, const double *__restrict__ dtp) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  if (tags[((long long)k * g.ny + j) * g.nx + i] != TAG_FLUID) return;
   const long long m = cid(g, i, j, k);
-  const double dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl / __longlong_as_double((long long)*lmax);
+  const double dt = *dtp;
   for (int v = 0; v < 5; v++) {
     const double L = -((Fx.v[v][m] - Fx.v[v][m - 1]) * g.idx + (Fy.v[v][m] - Fy.v[v][m - g.W]) * g.idy +
                        (Fz.v[v][m] - Fz.v[v][m - g.plane]) * g.idz);
@@ -221,12 +221,11 @@ __global__ void __launch_bounds__(TB) k3_update(Grid3 g, Phys3 ph, int stage, F5
 
 // CFL rule: the largest (|u|+c)/dx + (|v|+c)/dy + (|w|+c)/dz + 2 gamma mu/(Pr rho)(1/dx^2 + 1/dy^2 + 1/dz^2)
 // over the fluid cells (max of positive doubles through their bit patterns: order independent)
-__global__ void __launch_bounds__(TB) k3_lambda(Grid3 g, Phys3 ph, F5 U, const uint8_t *__restrict__ tags,
+__global__ void __launch_bounds__(TC) k3_lambda(Grid3 g, Phys3 ph, F5 U, const uint8_t *__restrict__ tags,
                                                 unsigned long long *__restrict__ lmax) {
-  const long long n = (long long)blockIdx.x * TB + threadIdx.x;
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   double lam = 0.0;
-  if (n < (long long)g.nx * g.ny * g.nz && tags[n] == TAG_FLUID) {
-    const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+  if (i < g.nx && j < g.ny && tags[((long long)k * g.ny + j) * g.nx + i] == TAG_FLUID) {
     const long long m = cid(g, i, j, k);
     const double r = U.v[0][m], ir = 1.0 / r;
     const double u = U.v[1][m] * ir, v = U.v[2][m] * ir, w = U.v[3][m] * ir;
@@ -241,10 +240,11 @@ __global__ void __launch_bounds__(TB) k3_lambda(Grid3 g, Phys3 ph, F5 U, const u
 
 // domain halos in closed form: the free stream if the cell lies beyond a free-stream side along any axis,
 // else the interior cell reached by mapping each out-of-range index (periodic wrap or zero-gradient clamp)
-__global__ void __launch_bounds__(TB) k3_halo(Grid3 g, Phys3 ph, F5 U) {
-  const long long m = (long long)blockIdx.x * TB + threadIdx.x;
-  if (m >= g.ncell) return;
-  const int I[3] = {(int)(m % g.W) - NG, (int)((m / g.W) % g.H) - NG, (int)(m / g.plane) - NG};
+__global__ void __launch_bounds__(TC) k3_halo(Grid3 g, Phys3 ph, F5 U) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  if (x >= g.W || y >= g.H) return;
+  const long long m = ((long long)blockIdx.z * g.H + y) * g.W + x;
+  const int I[3] = {x - NG, y - NG, (int)blockIdx.z - NG};
   const int n[3] = {g.nx, g.ny, g.nz};
   int S[3];
   bool halo = false, fs = false;
@@ -268,9 +268,9 @@ __global__ void __launch_bounds__(TB) k3_halo(Grid3 g, Phys3 ph, F5 U) {
 
 // Sec. 4.4-4.6 and Sec. 5 with a static wall: the node takes the probe's (image point's) pressure and
 // temperature and its velocity scaled by xi_node / xi_probe (zero at P')
-__global__ void __launch_bounds__(TB) k3_reconstruct(Grid3 g, Phys3 ph, F5 U, const ibm_stencil3d *__restrict__ st,
+__global__ void __launch_bounds__(32) k3_reconstruct(Grid3 g, Phys3 ph, F5 U, const ibm_stencil3d *__restrict__ st,
                                                      int first, int count) {
-  const int e = blockIdx.x * TB + threadIdx.x;
+  const int e = blockIdx.x * 32 + threadIdx.x;
   if (e >= count) return;
   const ibm_stencil3d &s = st[first + e];
   const int mask = s.mask;
@@ -348,8 +348,8 @@ __global__ void __launch_bounds__(TB) k3_force_sum(const double *__restrict__ fi
 }
 
 // end of step on the device: t += dt, last dt
-__global__ void k3_step_end(Phys3 ph, const unsigned long long *__restrict__ lmax, double *__restrict__ time) {
-  const double dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl / __longlong_as_double((long long)*lmax);
+__global__ void k3_step_end(const double *__restrict__ dtp, double *__restrict__ time) {
+  const double dt = *dtp;
   time[0] = time[0] + dt;
   time[1] = dt;
 }
@@ -362,7 +362,7 @@ __global__ void k3_step_end(Phys3 ph, const unsigned long long *__restrict__ lma
 // L(rho E) = L' + H_inf L(rho) and combines the stages in FP64.
 
 struct P32 {
-  float pinf, gamma, gg, mu, kappa, u0[3];  // gg = gamma / (gamma - 1)
+  float pinf, ipinf, gamma, gg, mu, kappa, ipr, u0[3];  // gg = gamma / (gamma - 1), ipr = 1 / Pr
 };
 
 struct F5f {
@@ -372,18 +372,63 @@ struct F6f {
   float *v[6];  // rho', u', v', w', p', T'
 };
 
-__global__ void __launch_bounds__(TB) k3_prim32(Grid3 g, Phys3 ph, F5 U, F6f Q) {
-  const long long m = (long long)blockIdx.x * TB + threadIdx.x;
-  if (m >= g.ncell) return;
-  const double r = U.v[0][m], ir = 1.0 / r;
-  const double u = U.v[1][m] * ir, v = U.v[2][m] * ir, w = U.v[3][m] * ir;
-  const double p = (ph.gamma - 1.0) * (U.v[4][m] - 0.5 * r * (u * u + v * v + w * w));
-  Q.v[0][m] = (float)(r - 1.0);
-  Q.v[1][m] = (float)(u - ph.Uinf[1]);
-  Q.v[2][m] = (float)(v - ph.Uinf[2]);
-  Q.v[3][m] = (float)(w - ph.Uinf[3]);
-  Q.v[4][m] = (float)(p - ph.pinf);
-  Q.v[5][m] = (float)(p * ir / ph.R - 1.0);
+__global__ void __launch_bounds__(TC) k3_prim32(Grid3 g, Phys3 ph, P32 c, F5 U, F6f Q) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  if (x >= g.W || y >= g.H) return;
+  const long long m = ((long long)blockIdx.z * g.H + y) * g.W + x;
+  // conserved perturbations in FP64, then FP32 arithmetic on them only:
+  //   u' = (dm - U_inf drho) / rho,  p' = (gamma - 1) (dE - (rho u'.(2 U_inf + u') + drho |U_inf|^2) / 2),
+  //   T' = (p' / p_inf - drho) / rho  (R = p_inf)
+  const float dr = (float)(U.v[0][m] - ph.Uinf[0]);
+  const float dm[3] = {(float)(U.v[1][m] - ph.Uinf[1]), (float)(U.v[2][m] - ph.Uinf[2]),
+                       (float)(U.v[3][m] - ph.Uinf[3])};
+  const float dE = (float)(U.v[4][m] - ph.Uinf[4]);
+  const float r = 1.0f + dr, ir = __fdividef(1.0f, r);
+  float up[3], k = 0.0f, u2 = 0.0f;
+  for (int a = 0; a < 3; a++) {
+    up[a] = (dm[a] - c.u0[a] * dr) * ir;
+    k += up[a] * (2.0f * c.u0[a] + up[a]);
+    u2 += c.u0[a] * c.u0[a];
+  }
+  const float pp = (c.gamma - 1.0f) * (dE - 0.5f * (r * k + dr * u2));
+  Q.v[0][m] = dr;
+  Q.v[1][m] = up[0];
+  Q.v[2][m] = up[1];
+  Q.v[3][m] = up[2];
+  Q.v[4][m] = pp;
+  Q.v[5][m] = (pp * c.ipinf - dr) * ir;
+}
+
+// dt of the step from the CFL reduction (or the fixed step), once
+__global__ void k3_dt(Phys3 ph, const unsigned long long *__restrict__ lmax, double *__restrict__ dt) {
+  *dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl / __longlong_as_double((long long)*lmax);
+}
+
+// CFL reduction of the FP32-bulk mode: the same bound in FP32 from the conserved perturbations
+__global__ void __launch_bounds__(TC) k3_lambda32(Grid3 g, Phys3 ph, P32 c, F5 U, const uint8_t *__restrict__ tags,
+                                                  unsigned long long *__restrict__ lmax) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  float lam = 0.0f;
+  if (i < g.nx && j < g.ny && tags[((long long)k * g.ny + j) * g.nx + i] == TAG_FLUID) {
+    const long long m = cid(g, i, j, k);
+    const float dr = (float)(U.v[0][m] - ph.Uinf[0]);
+    const float dE = (float)(U.v[4][m] - ph.Uinf[4]);
+    const float r = 1.0f + dr, ir = __fdividef(1.0f, r);
+    float u[3], kk = 0.0f, u2 = 0.0f;
+    for (int a = 0; a < 3; a++) {
+      const float up = ((float)(U.v[1 + a][m] - ph.Uinf[1 + a]) - c.u0[a] * dr) * ir;
+      kk += up * (2.0f * c.u0[a] + up);
+      u2 += c.u0[a] * c.u0[a];
+      u[a] = c.u0[a] + up;
+    }
+    const float p = c.pinf + (c.gamma - 1.0f) * (dE - 0.5f * (r * kk + dr * u2));
+    const float c2 = c.gamma * p * ir, cs = c2 * rsqrtf(c2);
+    lam = (fabsf(u[0]) + cs) * (float)g.idx + (fabsf(u[1]) + cs) * (float)g.idy + (fabsf(u[2]) + cs) * (float)g.idz +
+          (2.0f * c.gamma * c.mu * c.ipr * ir) * (float)(g.idx * g.idx + g.idy * g.idy + g.idz * g.idz);
+  }
+  for (int o = 16; o > 0; o >>= 1) lam = fmaxf(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  if (((threadIdx.y * BX + threadIdx.x) & 31) == 0 && lam > 0.0f)
+    atomicMax(lmax, (unsigned long long)__double_as_longlong((double)lam));
 }
 
 __device__ __forceinline__ float weno5f(float f0, float f1, float f2, float f3, float f4) {
@@ -401,7 +446,7 @@ __device__ __forceinline__ float weno5f(float f0, float f1, float f2, float f3, 
   const float q2 = (2.0f * f2 + 5.0f * f3 - f4) * (1.0f / 6.0f);
   // alpha_k = d_k / (eps + beta_k)^2 through FP32 reciprocals (in range for beta_k up to ~1e19)
   const float e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
-  const float i0 = __frcp_rn(e0 * e0), i1 = __frcp_rn(e1 * e1), i2 = __frcp_rn(e2 * e2);
+  const float i0 = __fdividef(1.0f, e0 * e0), i1 = __fdividef(1.0f, e1 * e1), i2 = __fdividef(1.0f, e2 * e2);
   const float a0 = 0.1f * i0, a1 = 0.6f * i1, a2 = 0.3f * i2;
   return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
 }
@@ -411,9 +456,10 @@ __device__ __forceinline__ float weno5f(float f0, float f1, float f2, float f3, 
 template <int DIR>
 __device__ __forceinline__ void ldfss32(const float qL[5], const float qR[5], const P32 &c, float F[5]) {
   const float rL = 1.0f + qL[0], rR = 1.0f + qR[0];
-  const float irL = __frcp_rn(rL), irR = __frcp_rn(rR);
+  const float irL = __fdividef(1.0f, rL), irR = __fdividef(1.0f, rR);
   const float pL = c.pinf + qL[4], pR = c.pinf + qR[4];
-  const float cL = sqrtf(c.gamma * pL * irL), cR = sqrtf(c.gamma * pR * irR);
+  const float c2L = c.gamma * pL * irL, c2R = c.gamma * pR * irR;
+  const float cL = c2L * rsqrtf(c2L), cR = c2R * rsqrtf(c2R);  // sound speeds (approximate square roots)
   float uL[3], uR[3];
   for (int a = 0; a < 3; a++) {
     uL[a] = c.u0[a] + qL[1 + a];
@@ -428,7 +474,7 @@ __device__ __forceinline__ void ldfss32(const float qL[5], const float qR[5], co
   const float HL = c.gg * (qL[4] - c.pinf * qL[0]) * irL + 0.5f * kL;
   const float HR = c.gg * (qR[4] - c.pinf * qR[0]) * irR + 0.5f * kR;
   const float unL = uL[DIR], unR = uR[DIR];
-  const float cs = 0.5f * (cL + cR), ics = __frcp_rn(cs);
+  const float cs = 0.5f * (cL + cR), ics = __fdividef(1.0f, cs);
   const float ML = unL * ics, MR = unR * ics;
   const float aL = ML >= 0.0f ? 1.0f : 0.0f, aR = MR >= 0.0f ? 0.0f : 1.0f;
   const float bL = -fmaxf(1.0f - floorf(fabsf(ML)), 0.0f), bR = -fmaxf(1.0f - floorf(fabsf(MR)), 0.0f);
@@ -436,7 +482,8 @@ __device__ __forceinline__ void ldfss32(const float qL[5], const float qR[5], co
   const float MmR = -0.25f * (MR - 1.0f) * (MR - 1.0f);
   const float CVL = aL * (1.0f + bL) * ML - bL * MpL;
   const float CVR = aR * (1.0f + bR) * MR - bR * MmR;
-  const float sq = sqrtf(0.5f * (ML * ML + MR * MR)) - 1.0f;
+  const float m2 = 0.5f * (ML * ML + MR * MR);
+  const float sq = (m2 > 0.0f ? m2 * rsqrtf(m2) : 0.0f) - 1.0f;
   const float Mh = 0.25f * bL * bR * sq * sq;
   const float dp = qL[4] - qR[4], adp = fabsf(dp), ic2 = 0.5f * ics * ics;
   const float MhP = Mh * (1.0f - (dp + adp) * ic2 * irL);
@@ -455,11 +502,10 @@ __device__ __forceinline__ void ldfss32(const float qL[5], const float qR[5], co
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(TB) k3_flux32(Grid3 g, P32 c, F6f Q, F5f Fo) {
-  const int ex = g.nx + (DIR == 0), ey = g.ny + (DIR == 1), ez = g.nz + (DIR == 2);
-  const long long t = (long long)blockIdx.x * TB + threadIdx.x;
-  if (t >= (long long)ex * ey * ez) return;
-  int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
+__global__ void __launch_bounds__(TC) k3_flux32(Grid3 g, P32 c, F6f Q, F5f Fo) {
+  // faces i + 1/2 (DIR 0) for i in [-1, nx - 1], likewise along y and z; one thread per face
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx + (DIR == 0) || j >= g.ny + (DIR == 1)) return;
   if (DIR == 0) i -= 1;
   if (DIR == 1) j -= 1;
   if (DIR == 2) k -= 1;
@@ -507,32 +553,35 @@ __global__ void __launch_bounds__(TB) k3_flux32(Grid3 g, P32 c, F6f Q, F5f Fo) {
   for (int v = 0; v < 5; v++) Fo.v[v][a] = F[v];
 }
 
-// SSP-RK3 stage on the fluid cells in FP64 from the FP32 flux divergence (L(rho E) = L' + H_inf L(rho))
-__global__ void __launch_bounds__(TB) k3_update32(Grid3 g, Phys3 ph, double Hinf, int stage, F5f Fx, F5f Fy, F5f Fz,
-                                                  F5 Un, F5 In, F5 Out, const uint8_t *__restrict__ tags,
-                                                  const unsigned long long *__restrict__ lmax) {
-  const long long n = (long long)blockIdx.x * TB + threadIdx.x;
-  if (n >= (long long)g.nx * g.ny * g.nz) return;
-  if (tags[n] != TAG_FLUID) return;
-  const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+// SSP-RK3 stage on the fluid cells from the FP32 flux divergence (L(rho E) = L' + H_inf L(rho)): the stage
+// increment over Un in FP32 -- dt L, (In - Un + dt L) / 4, 2 (In - Un + dt L) / 3 -- accumulated onto the FP64 Un
+__global__ void __launch_bounds__(TC) k3_update32(Grid3 g, float Hinf, int stage, F5f Fx, F5f Fy, F5f Fz, F5 Un,
+                                                  F5 In, F5 Out, const uint8_t *__restrict__ tags,
+                                                  const double *__restrict__ dtp) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  if (tags[((long long)k * g.ny + j) * g.nx + i] != TAG_FLUID) return;
   const long long m = cid(g, i, j, k);
-  const double dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl / __longlong_as_double((long long)*lmax);
+  const float dt = (float)*dtp;
   const float ix = (float)g.idx, iy = (float)g.idy, iz = (float)g.idz;
-  double L[5];
+  float L[5];
   for (int v = 0; v < 5; v++)
-    L[v] = (double)(-((Fx.v[v][m] - Fx.v[v][m - 1]) * ix + (Fy.v[v][m] - Fy.v[v][m - g.W]) * iy +
-                      (Fz.v[v][m] - Fz.v[v][m - g.plane]) * iz));
+    L[v] = -((Fx.v[v][m] - Fx.v[v][m - 1]) * ix + (Fy.v[v][m] - Fy.v[v][m - g.W]) * iy +
+             (Fz.v[v][m] - Fz.v[v][m - g.plane]) * iz);
   L[4] += Hinf * L[0];
   for (int v = 0; v < 5; v++) {
-    double o;
-    if (stage == 1) o = Un.v[v][m] + dt * L[v];
-    else if (stage == 2) o = 0.75 * Un.v[v][m] + 0.25 * (In.v[v][m] + dt * L[v]);
-    else o = (1.0 / 3.0) * Un.v[v][m] + (2.0 / 3.0) * (In.v[v][m] + dt * L[v]);
-    Out.v[v][m] = o;
+    const double un = Un.v[v][m];
+    float d;
+    if (stage == 1) d = dt * L[v];
+    else if (stage == 2) d = 0.25f * ((float)(In.v[v][m] - un) + dt * L[v]);
+    else d = (2.0f / 3.0f) * ((float)(In.v[v][m] - un) + dt * L[v]);
+    Out.v[v][m] = un + (double)d;
   }
 }
 
 inline unsigned nblk(long long n) { return (unsigned)((n + TB - 1) / TB); }
+inline dim3 cells(int ex, int ey, int ez) { return dim3((ex + BX - 1) / BX, (ey + BY - 1) / BY, ez); }
+const dim3 CB(BX, BY, 1);
 
 }  // namespace
 
@@ -554,6 +603,7 @@ struct ibm_case3d {
   double *fbuf = nullptr;         // per-triangle forces, then the summed force (3 doubles)
   unsigned long long *lmax = nullptr;
   double *time = nullptr;         // t, last dt
+  double *dt = nullptr;           // dt of the current step
   int *nerr = nullptr;
   int counts[4] = {0, 0, 0, 0};
   double ref_area = 1.0;
@@ -633,6 +683,8 @@ extern "C" ibm_status ibm_case3d_create(const double *verts, int nverts, const i
   ph.Uinf[4] = ph.pinf / (fl->gamma - 1.0) + 0.5 * (u * u + v * v + w * w);
   c->Hinf = fl->gamma / (fl->gamma - 1.0) * ph.pinf + 0.5 * (u * u + v * v + w * w);
   c->p32.pinf = (float)ph.pinf;
+  c->p32.ipinf = (float)(1.0 / ph.pinf);
+  c->p32.ipr = (float)(1.0 / fl->prandtl);
   c->p32.gamma = (float)fl->gamma;
   c->p32.gg = (float)(fl->gamma / (fl->gamma - 1.0));
   c->p32.mu = (float)ph.mu;
@@ -680,7 +732,7 @@ extern "C" ibm_status ibm_case3d_create(const double *verts, int nverts, const i
   const size_t s_sst = up((size_t)std::max(ntris, 1) * sizeof(ibm_stencil3d));
   const size_t s_tri = up((size_t)std::max(ntris, 1) * 7 * sizeof(double));
   const size_t s_f = up(((size_t)std::max(ntris, 1) * 3 + 3) * sizeof(double));
-  const size_t total = arr * 36 + s_st + s_sst + s_tri + s_f + 256 * 3;
+  const size_t total = arr * 36 + s_st + s_sst + s_tri + s_f + 256 * 4;
   e = cudaMalloc(&c->mem, total);
   if (e != cudaSuccess) {
     ibm_case3d_destroy(c);
@@ -708,6 +760,7 @@ extern "C" ibm_status ibm_case3d_create(const double *verts, int nverts, const i
   c->lmax = (unsigned long long *)take(256);
   c->time = (double *)take(256);
   c->nerr = (int *)take(256);
+  c->dt = (double *)take(256);
   // free stream everywhere (halos and solid cells included)
   {
     std::vector<double> fsv((size_t)g.ncell);
@@ -795,23 +848,27 @@ extern "C" ibm_status ibm_case3d_step(ibm_case3d *c, int nsteps) {
   if (!c || nsteps < 0) return ibm__noalloc_fail(IBM_EINVAL, "ibm_case3d_step: bad argument");
   const Grid3 &g = c->g;
   const Phys3 &ph = c->ph;
-  const long long nint = (long long)g.nx * g.ny * g.nz;
   const int nib = c->counts[0], ngh = c->counts[1] + c->counts[2] + c->counts[3];
   cudaStream_t s = c->stream;
   for (int it = 0; it < nsteps; it++) {
+    const bool f32 = c->precision == IBM_PREC_FP32_BULK;
     if (ph.dt_fixed <= 0.0) {
       cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), s);
-      k3_lambda<<<nblk(nint), TB, 0, s>>>(g, ph, c->A, c->tags, c->lmax);
+      if (f32) k3_lambda32<<<cells(g.nx, g.ny, g.nz), CB, 0, s>>>(g, ph, c->p32, c->A, c->tags, c->lmax);
+      else k3_lambda<<<cells(g.nx, g.ny, g.nz), CB, 0, s>>>(g, ph, c->A, c->tags, c->lmax);
       c->launches++;
     }
+    k3_dt<<<1, 1, 0, s>>>(ph, c->lmax, c->dt);
+    c->launches++;
     F5 in[3] = {c->A, c->B, c->C}, out[3] = {c->B, c->C, c->A};
     for (int k = 0; k < 3; k++) {
-      if (nib) k3_reconstruct<<<nblk(nib), TB, 0, s>>>(g, ph, in[k], c->st, 0, nib);
-      if (ngh) k3_reconstruct<<<nblk(ngh), TB, 0, s>>>(g, ph, in[k], c->st, nib, ngh);
-      k3_halo<<<nblk(g.ncell), TB, 0, s>>>(g, ph, in[k]);
-      const unsigned bx = nblk((long long)(g.nx + 1) * g.ny * g.nz), by = nblk((long long)g.nx * (g.ny + 1) * g.nz),
-                     bz = nblk((long long)g.nx * g.ny * (g.nz + 1));
-      if (c->precision == IBM_PREC_FP32_BULK) {
+      // one warp per block: the listed nodes (a few thousand) spread over every SM
+      if (nib) k3_reconstruct<<<(nib + 31) / 32, 32, 0, s>>>(g, ph, in[k], c->st, 0, nib);
+      if (ngh) k3_reconstruct<<<(ngh + 31) / 32, 32, 0, s>>>(g, ph, in[k], c->st, nib, ngh);
+      k3_halo<<<cells(g.W, g.H, g.D), CB, 0, s>>>(g, ph, in[k]);
+      const dim3 bx = cells(g.nx + 1, g.ny, g.nz), by = cells(g.nx, g.ny + 1, g.nz), bz = cells(g.nx, g.ny, g.nz + 1);
+      const dim3 ball = cells(g.W, g.H, g.D), bint = cells(g.nx, g.ny, g.nz);
+      if (f32) {
         // the FP32 arrays live in the FP64 primitive and flux arrays' storage
         F6f q;
         F5f fx, fy, fz;
@@ -821,22 +878,21 @@ extern "C" ibm_status ibm_case3d_step(ibm_case3d *c, int nsteps) {
           fy.v[v] = (float *)c->Fy.v[v];
           fz.v[v] = (float *)c->Fz.v[v];
         }
-        k3_prim32<<<nblk(g.ncell), TB, 0, s>>>(g, ph, in[k], q);
-        k3_flux32<0><<<bx, TB, 0, s>>>(g, c->p32, q, fx);
-        k3_flux32<1><<<by, TB, 0, s>>>(g, c->p32, q, fy);
-        k3_flux32<2><<<bz, TB, 0, s>>>(g, c->p32, q, fz);
-        k3_update32<<<nblk(nint), TB, 0, s>>>(g, ph, c->Hinf, k + 1, fx, fy, fz, c->A, in[k], out[k], c->tags,
-                                              c->lmax);
+        k3_prim32<<<ball, CB, 0, s>>>(g, ph, c->p32, in[k], q);
+        k3_flux32<0><<<bx, CB, 0, s>>>(g, c->p32, q, fx);
+        k3_flux32<1><<<by, CB, 0, s>>>(g, c->p32, q, fy);
+        k3_flux32<2><<<bz, CB, 0, s>>>(g, c->p32, q, fz);
+        k3_update32<<<bint, CB, 0, s>>>(g, (float)c->Hinf, k + 1, fx, fy, fz, c->A, in[k], out[k], c->tags, c->dt);
       } else {
-        k3_prim<<<nblk(g.ncell), TB, 0, s>>>(g, ph, in[k], c->Q);
-        k3_flux<0><<<bx, TB, 0, s>>>(g, ph, c->Q, c->Fx);
-        k3_flux<1><<<by, TB, 0, s>>>(g, ph, c->Q, c->Fy);
-        k3_flux<2><<<bz, TB, 0, s>>>(g, ph, c->Q, c->Fz);
-        k3_update<<<nblk(nint), TB, 0, s>>>(g, ph, k + 1, c->Fx, c->Fy, c->Fz, c->A, in[k], out[k], c->tags, c->lmax);
+        k3_prim<<<ball, CB, 0, s>>>(g, ph, in[k], c->Q);
+        k3_flux<0><<<bx, CB, 0, s>>>(g, ph, c->Q, c->Fx);
+        k3_flux<1><<<by, CB, 0, s>>>(g, ph, c->Q, c->Fy);
+        k3_flux<2><<<bz, CB, 0, s>>>(g, ph, c->Q, c->Fz);
+        k3_update<<<bint, CB, 0, s>>>(g, k + 1, c->Fx, c->Fy, c->Fz, c->A, in[k], out[k], c->tags, c->dt);
       }
       c->launches += 6 + (nib ? 1 : 0) + (ngh ? 1 : 0);
     }
-    k3_step_end<<<1, 1, 0, s>>>(ph, c->lmax, c->time);
+    k3_step_end<<<1, 1, 0, s>>>(c->dt, c->time);
     c->launches++;
   }
   const cudaError_t e = cudaGetLastError();
