@@ -142,6 +142,45 @@ def test_full_size_sphere_one_step(ibm, orc):
     np.testing.assert_allclose(g.forces(), fo, rtol=0, atol=1e-9 * np.abs(fo).max())
 
 
+def test_full_size_sphere_fp32_bulk(ibm, orc):
+    """The benchmark's launch configuration (FP32-bulk, 192 x 96 x 96): two steps against the FP64 oracle."""
+    spec = W.sphere_m03_re100()
+    g, o = ibm.Case3D(dict(spec, precision=W.PREC_FP32_BULK)), orc.Case3D(spec)
+    g.step(2)
+    o.step(2)
+    e = _state_error(g.state(), o.state(), o.tags())
+    d = np.abs(g.forces()[:3] - o.forces()[:3])
+    assert e <= 1e-4, e
+    assert d.max() <= 1e-3, d
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32_BULK])
+def test_degenerate_sizes(ibm, orc, precision):
+    """A body smaller than the spacing that holds no node (empty lists; it is stepped as free flow, and its
+    force probes see the free stream), and the smallest grid (4 cells per axis, a ragged single block)."""
+    verts, tris = W.uv_sphere(radius=0.01, center=(0.013, 0.011, 0.012))
+    spec = W.case3d_spec(verts, tris, (20, 10, 10), (-1, -0.5, -0.5), (1, 0.5, 0.5), 0.3, 100.0, W.FAR3D,
+                         precision=precision)
+    g, o = ibm.Case3D(spec), orc.Case3D(spec)
+    assert o.classify() == 0 and (o.tags() == 0).all()
+    np.testing.assert_array_equal(g.counts(), [0, 0, 0, 0])
+    g.step(3)
+    o.step(3)
+    assert _state_error(g.state(), o.state(), o.tags()) <= (1e-10 if precision == W.PREC_FP64 else 1e-4)
+    spec = W.case3d_spec(None, None, (4, 4, 4), (0, 0, 0), (1, 1, 1), 0.5, 50.0, (PER,) * 6, uinf=(0.3, 0.2, 0.1),
+                         precision=precision)
+    rng = np.random.default_rng(5)
+    U = np.stack([np.ones((4, 4, 4)), 0.3 + 0.01 * rng.standard_normal((4, 4, 4)),
+                  0.2 * np.ones((4, 4, 4)), 0.1 * np.ones((4, 4, 4)), np.zeros((4, 4, 4))])
+    U[4] = (1.0 / (1.4 * 0.25)) / 0.4 + 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]
+    g, o = ibm.Case3D(spec), orc.Case3D(spec)
+    g.set_state(U)
+    o.set_state(U)
+    g.step(2)
+    o.step(2)
+    assert _state_error(g.state(), o.state(), o.tags()) <= (1e-10 if precision == W.PREC_FP64 else 1e-4)
+
+
 def test_quiescent_sphere_stays_at_rest(ibm):
     verts, tris = W.uv_sphere(radius=0.5)
     spec = W.case3d_spec(verts, tris, (24, 24, 24), (-1, -1, -1), (1, 1, 1), 0.3, 100.0, (FS,) * 6,
