@@ -239,66 +239,89 @@ __global__ void __launch_bounds__(TC) k3_lambda(Grid3 g, Phys3 ph, F5 U, const u
 }
 
 // domain halos in closed form: the free stream if the cell lies beyond a free-stream side along any axis,
-// else the interior cell reached by mapping each out-of-range index (periodic wrap or zero-gradient clamp)
-__global__ void __launch_bounds__(TC) k3_halo(Grid3 g, Phys3 ph, F5 U) {
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
-  if (x >= g.W || y >= g.H) return;
-  const long long m = ((long long)blockIdx.z * g.H + y) * g.W + x;
-  const int I[3] = {x - NG, y - NG, (int)blockIdx.z - NG};
+// else the interior cell reached by mapping each out-of-range index (periodic wrap or zero-gradient clamp).
+// One thread per halo cell: the two z slabs (every x, y), the two y slabs of the interior z range (every x),
+// the two x slabs of the interior y, z range
+__global__ void __launch_bounds__(TB) k3_halo(Grid3 g, Phys3 ph, F5 U) {
+  const int t = blockIdx.x * TB + threadIdx.x;
+  const int nzs = 2 * NG * g.W * g.H, nys = 2 * NG * g.nz * g.W, nxs = 2 * NG * g.nz * g.ny;
+  int x, y, z;
+  if (t < nzs) {
+    const int zz = t / (g.W * g.H), rem = t - zz * (g.W * g.H);
+    z = zz < NG ? zz : g.nz + zz;
+    y = rem / g.W;
+    x = rem - y * g.W;
+  } else if (t < nzs + nys) {
+    const int u = t - nzs, zz = u / (2 * NG * g.W), rem = u - zz * (2 * NG * g.W), yy = rem / g.W;
+    z = NG + zz;
+    y = yy < NG ? yy : g.ny + yy;
+    x = rem - yy * g.W;
+  } else if (t < nzs + nys + nxs) {
+    const int u = t - nzs - nys, zz = u / (2 * NG * g.ny), rem = u - zz * (2 * NG * g.ny), yy = rem / (2 * NG);
+    const int xx = rem - yy * (2 * NG);
+    z = NG + zz;
+    y = NG + yy;
+    x = xx < NG ? xx : g.nx + xx;
+  } else {
+    return;
+  }
+  const long long m = ((long long)z * g.H + y) * g.W + x;
+  const int I[3] = {x - NG, y - NG, z - NG};
   const int n[3] = {g.nx, g.ny, g.nz};
   int S[3];
-  bool halo = false, fs = false;
+  bool fs = false;
   for (int a = 0; a < 3; a++) {
     S[a] = I[a];
     if (I[a] >= 0 && I[a] < n[a]) continue;
-    halo = true;
     const int bc = g.bc[2 * a + (I[a] < 0 ? 0 : 1)];
     if (bc == IBM_BC_PERIODIC) S[a] = I[a] < 0 ? I[a] + n[a] : I[a] - n[a];
     else if (bc == IBM_BC_OUTFLOW) S[a] = I[a] < 0 ? 0 : n[a] - 1;
     else fs = true;
   }
-  if (!halo) return;
   if (fs) {
     for (int v = 0; v < 5; v++) U.v[v][m] = ph.Uinf[v];
   } else {
-    const long long s = cid(g, S[0], S[1], S[2]);
-    for (int v = 0; v < 5; v++) U.v[v][m] = U.v[v][s];
+    const long long src = cid(g, S[0], S[1], S[2]);
+    for (int v = 0; v < 5; v++) U.v[v][m] = U.v[v][src];
   }
 }
 
 // Sec. 4.4-4.6 and Sec. 5 with a static wall: the node takes the probe's (image point's) pressure and
-// temperature and its velocity scaled by xi_node / xi_probe (zero at P')
-__global__ void __launch_bounds__(32) k3_reconstruct(Grid3 g, Phys3 ph, F5 U, const ibm_stencil3d *__restrict__ st,
-                                                     int first, int count) {
-  const int e = blockIdx.x * 32 + threadIdx.x;
-  if (e >= count) return;
-  const ibm_stencil3d &s = st[first + e];
-  const int mask = s.mask;
-  if (mask == 0) return;
-  double qp[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // p, u, v, w, T
-  for (int b = 0; b < 8; b++) {
-    if (!(mask >> b & 1)) continue;
-    const long long id = cid(g, s.i0 + (b & 1), s.j0 + (b >> 1 & 1), s.k0 + (b >> 2));
+// temperature and its velocity scaled by xi_node / xi_probe (zero at P').  Eight lanes per node, one cube corner
+// each, the weighted sums formed by a fixed shuffle tree (a warp holds four nodes)
+__global__ void __launch_bounds__(128) k3_reconstruct(Grid3 g, Phys3 ph, F5 U, const ibm_stencil3d *__restrict__ st,
+                                                      int first, int count) {
+  const int t = blockIdx.x * 128 + threadIdx.x;
+  const int e = t >> 3, b = t & 7;
+  const bool live = e < count;
+  const ibm_stencil3d *sp = st + first + (live ? e : 0);
+  const int mask = live ? sp->mask : 0;
+  double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // this corner's weighted p, u, v, w, T
+  if (mask >> b & 1) {
+    const long long id = cid(g, sp->i0 + (b & 1), sp->j0 + (b >> 1 & 1), sp->k0 + (b >> 2));
     const double r = U.v[0][id], ir = 1.0 / r;
     const double u = U.v[1][id] * ir, v = U.v[2][id] * ir, w = U.v[3][id] * ir;
     const double p = (ph.gamma - 1.0) * (U.v[4][id] - 0.5 * r * (u * u + v * v + w * w));
-    const double wb = s.w[b];
-    qp[0] += wb * p;
-    qp[1] += wb * u;
-    qp[2] += wb * v;
-    qp[3] += wb * w;
-    qp[4] += wb * (p * ir / ph.R);
+    const double wb = sp->w[b];
+    q[0] = wb * p;
+    q[1] = wb * u;
+    q[2] = wb * v;
+    q[3] = wb * w;
+    q[4] = wb * (p * ir / ph.R);
   }
-  const double ratio = s.xi_node / s.xi_probe;
-  const double u = qp[1] * ratio, v = qp[2] * ratio, w = qp[3] * ratio;
-  const double r = qp[0] / (ph.R * qp[4]);
-  const int node = s.node;
+  for (int o = 4; o > 0; o >>= 1)
+    for (int v = 0; v < 5; v++) q[v] += __shfl_xor_sync(0xffffffffu, q[v], o);
+  if (!live || b != 0 || mask == 0) return;
+  const double ratio = sp->xi_node / sp->xi_probe;
+  const double u = q[1] * ratio, v = q[2] * ratio, w = q[3] * ratio;
+  const double r = q[0] / (ph.R * q[4]);
+  const int node = sp->node;
   const long long id = cid(g, node % g.nx, (node / g.nx) % g.ny, node / (g.nx * g.ny));
   U.v[0][id] = r;
   U.v[1][id] = r * u;
   U.v[2][id] = r * v;
   U.v[3][id] = r * w;
-  U.v[4][id] = qp[0] / (ph.gamma - 1.0) + 0.5 * r * (u * u + v * v + w * w);
+  U.v[4][id] = q[0] / (ph.gamma - 1.0) + 0.5 * r * (u * u + v * v + w * w);
 }
 
 // Eq. 9 per triangle (tri: area per triangle; st: its probe): (-(p_s - p_inf) n + mu (u - (u.n) n) / xi) A
@@ -862,10 +885,11 @@ extern "C" ibm_status ibm_case3d_step(ibm_case3d *c, int nsteps) {
     c->launches++;
     F5 in[3] = {c->A, c->B, c->C}, out[3] = {c->B, c->C, c->A};
     for (int k = 0; k < 3; k++) {
-      // one warp per block: the listed nodes (a few thousand) spread over every SM
-      if (nib) k3_reconstruct<<<(nib + 31) / 32, 32, 0, s>>>(g, ph, in[k], c->st, 0, nib);
-      if (ngh) k3_reconstruct<<<(ngh + 31) / 32, 32, 0, s>>>(g, ph, in[k], c->st, nib, ngh);
-      k3_halo<<<cells(g.W, g.H, g.D), CB, 0, s>>>(g, ph, in[k]);
+      // eight lanes per listed node (one cube corner each)
+      if (nib) k3_reconstruct<<<(nib + 15) / 16, 128, 0, s>>>(g, ph, in[k], c->st, 0, nib);
+      if (ngh) k3_reconstruct<<<(ngh + 15) / 16, 128, 0, s>>>(g, ph, in[k], c->st, nib, ngh);
+      k3_halo<<<nblk(2LL * NG * ((long long)g.W * g.H + (long long)g.nz * g.W + (long long)g.nz * g.ny)), TB, 0, s>>>(
+          g, ph, in[k]);
       const dim3 bx = cells(g.nx + 1, g.ny, g.nz), by = cells(g.nx, g.ny + 1, g.nz), bz = cells(g.nx, g.ny, g.nz + 1);
       const dim3 ball = cells(g.W, g.H, g.D), bint = cells(g.nx, g.ny, g.nz);
       if (f32) {
