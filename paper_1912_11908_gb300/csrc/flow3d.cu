@@ -385,7 +385,10 @@ __global__ void k3_step_end(const double *__restrict__ dtp, double *__restrict__
 // L(rho E) = L' + H_inf L(rho) and combines the stages in FP64.
 
 struct P32 {
-  float pinf, ipinf, gamma, gg, mu, kappa, ipr, u0[3];  // gg = gamma / (gamma - 1), ipr = 1 / Pr
+  float pinf, ipinf, gamma, gg, igm1, mu, kappa, ipr, u0[3], u2;  // gg = gamma / (gamma - 1), igm1 = 1 / (gamma - 1),
+                                                                   // ipr = 1 / Pr, u2 = |U_inf|^2
+  float ih[3], ih2;  // inverse spacings 1/dx, 1/dy, 1/dz and 1/dx^2 + 1/dy^2 + 1/dz^2
+  float Hinf;        // free-stream total enthalpy
 };
 
 struct F5f {
@@ -395,25 +398,36 @@ struct F6f {
   float *v[6];  // rho', u', v', w', p', T'
 };
 
-__global__ void __launch_bounds__(TC) k3_prim32(Grid3 g, Phys3 ph, P32 c, F5 U, F6f Q) {
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
-  if (x >= g.W || y >= g.H) return;
-  const long long m = ((long long)blockIdx.z * g.H + y) * g.W + x;
-  // conserved perturbations in FP64, then FP32 arithmetic on them only:
-  //   u' = (dm - U_inf drho) / rho,  p' = (gamma - 1) (dE - (rho u'.(2 U_inf + u') + drho |U_inf|^2) / 2),
-  //   T' = (p' / p_inf - drho) / rho  (R = p_inf)
-  const float dr = (float)(U.v[0][m] - ph.Uinf[0]);
-  const float dm[3] = {(float)(U.v[1][m] - ph.Uinf[1]), (float)(U.v[2][m] - ph.Uinf[2]),
-                       (float)(U.v[3][m] - ph.Uinf[3])};
-  const float dE = (float)(U.v[4][m] - ph.Uinf[4]);
-  const float r = 1.0f + dr, ir = __fdividef(1.0f, r);
-  float up[3], k = 0.0f, u2 = 0.0f;
+// primitive perturbations of a conserved perturbation (drho, dm, dE) in FP32, free of cancellation:
+//   u' = (dm - U_inf drho) / rho,  p' = (gamma - 1) (dE - (rho u'.(2 U_inf + u') + drho |U_inf|^2) / 2)
+__device__ __forceinline__ void pert_prim(const P32 &c, float dr, const float dm[3], float dE, float &ir, float up[3],
+                                          float &pp) {
+  const float r = 1.0f + dr;
+  ir = __fdividef(1.0f, r);
+  float k = 0.0f;
   for (int a = 0; a < 3; a++) {
     up[a] = (dm[a] - c.u0[a] * dr) * ir;
     k += up[a] * (2.0f * c.u0[a] + up[a]);
-    u2 += c.u0[a] * c.u0[a];
   }
-  const float pp = (c.gamma - 1.0f) * (dE - 0.5f * (r * k + dr * u2));
+  pp = (c.gamma - 1.0f) * (dE - 0.5f * (r * k + dr * c.u2));
+}
+
+// FP32 perturbation sets of the FP64 master: S = U - U_inf over every cell (creation, ibm_case3d_set_state)
+__global__ void __launch_bounds__(TC) k3_mirror32(Grid3 g, Phys3 ph, F5 U, F5f S) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  if (x >= g.W || y >= g.H) return;
+  const long long m = ((long long)blockIdx.z * g.H + y) * g.W + x;
+  for (int v = 0; v < 5; v++) S.v[v][m] = (float)(U.v[v][m] - ph.Uinf[v]);
+}
+
+// primitive perturbations (rho', u', v', w', p', T') of an FP32 stage set, every cell (T' = (p'/p_inf - rho')/rho)
+__global__ void __launch_bounds__(TC) k3_prim32(Grid3 g, P32 c, F5f S, F6f Q) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  if (x >= g.W || y >= g.H) return;
+  const long long m = ((long long)blockIdx.z * g.H + y) * g.W + x;
+  const float dr = S.v[0][m], dm[3] = {S.v[1][m], S.v[2][m], S.v[3][m]}, dE = S.v[4][m];
+  float ir, up[3], pp;
+  pert_prim(c, dr, dm, dE, ir, up, pp);
   Q.v[0][m] = dr;
   Q.v[1][m] = up[0];
   Q.v[2][m] = up[1];
@@ -427,31 +441,126 @@ __global__ void k3_dt(Phys3 ph, const unsigned long long *__restrict__ lmax, dou
   *dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl / __longlong_as_double((long long)*lmax);
 }
 
-// CFL reduction of the FP32-bulk mode: the same bound in FP32 from the conserved perturbations
-__global__ void __launch_bounds__(TC) k3_lambda32(Grid3 g, Phys3 ph, P32 c, F5 U, const uint8_t *__restrict__ tags,
+// CFL reduction of the FP32-bulk mode, in FP32 from the mirror of the master: each thread strides over z, the
+// block reduces in shared memory and one atomic per block takes the maximum
+__global__ void __launch_bounds__(TC) k3_lambda32(Grid3 g, P32 c, F5f M, const uint8_t *__restrict__ tags,
                                                   unsigned long long *__restrict__ lmax) {
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  __shared__ float wmax[TC / 32];
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   float lam = 0.0f;
-  if (i < g.nx && j < g.ny && tags[((long long)k * g.ny + j) * g.nx + i] == TAG_FLUID) {
-    const long long m = cid(g, i, j, k);
-    const float dr = (float)(U.v[0][m] - ph.Uinf[0]);
-    const float dE = (float)(U.v[4][m] - ph.Uinf[4]);
-    const float r = 1.0f + dr, ir = __fdividef(1.0f, r);
-    float u[3], kk = 0.0f, u2 = 0.0f;
-    for (int a = 0; a < 3; a++) {
-      const float up = ((float)(U.v[1 + a][m] - ph.Uinf[1 + a]) - c.u0[a] * dr) * ir;
-      kk += up * (2.0f * c.u0[a] + up);
-      u2 += c.u0[a] * c.u0[a];
-      u[a] = c.u0[a] + up;
+  if (i < g.nx && j < g.ny) {
+    for (int k = blockIdx.z; k < g.nz; k += gridDim.z) {
+      if (tags[((long long)k * g.ny + j) * g.nx + i] != TAG_FLUID) continue;
+      const long long m = cid(g, i, j, k);
+      const float dr = M.v[0][m], dm[3] = {M.v[1][m], M.v[2][m], M.v[3][m]};
+      float ir, up[3], pp;
+      pert_prim(c, dr, dm, M.v[4][m], ir, up, pp);
+      const float p = c.pinf + pp, c2 = c.gamma * p * ir, cs = c2 * rsqrtf(c2);
+      const float l = (fabsf(c.u0[0] + up[0]) + cs) * c.ih[0] + (fabsf(c.u0[1] + up[1]) + cs) * c.ih[1] +
+                      (fabsf(c.u0[2] + up[2]) + cs) * c.ih[2] + (2.0f * c.gamma * c.mu * c.ipr * ir) * c.ih2;
+      lam = fmaxf(lam, l);
     }
-    const float p = c.pinf + (c.gamma - 1.0f) * (dE - 0.5f * (r * kk + dr * u2));
-    const float c2 = c.gamma * p * ir, cs = c2 * rsqrtf(c2);
-    lam = (fabsf(u[0]) + cs) * (float)g.idx + (fabsf(u[1]) + cs) * (float)g.idy + (fabsf(u[2]) + cs) * (float)g.idz +
-          (2.0f * c.gamma * c.mu * c.ipr * ir) * (float)(g.idx * g.idx + g.idy * g.idy + g.idz * g.idz);
   }
   for (int o = 16; o > 0; o >>= 1) lam = fmaxf(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-  if (((threadIdx.y * BX + threadIdx.x) & 31) == 0 && lam > 0.0f)
-    atomicMax(lmax, (unsigned long long)__double_as_longlong((double)lam));
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  if ((tid & 31) == 0) wmax[tid >> 5] = lam;
+  __syncthreads();
+  if (tid == 0) {
+    float b = wmax[0];
+    for (int w = 1; w < TC / 32; w++) b = fmaxf(b, wmax[w]);
+    if (b > 0.0f) atomicMax(lmax, (unsigned long long)__double_as_longlong((double)b));
+  }
+}
+
+// Sec. 4.4-4.6 and Sec. 5 on an FP32 stage set (the FP64 kernel's rule in perturbation form): eight lanes per
+// node, one cube corner each, sums of (p', u', v', w', T') by a fixed shuffle tree; the node's conserved
+// perturbation follows from p = p_inf + p', u = (U_inf + u') xi_node / xi_probe, T = 1 + T'.  With master set,
+// the node's value is also written to the FP64 master (the first stage's reconstruction, from U^n).
+__global__ void __launch_bounds__(128) k3_reconstruct32(Grid3 g, Phys3 ph, P32 c, F5f S,
+                                                        const ibm_stencil3d *__restrict__ st, int first, int count,
+                                                        F5 A, int master) {
+  const int t = blockIdx.x * 128 + threadIdx.x;
+  const int e = t >> 3, b = t & 7;
+  const bool live = e < count;
+  const ibm_stencil3d *sp = st + first + (live ? e : 0);
+  const int mask = live ? sp->mask : 0;
+  float q[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if (mask >> b & 1) {
+    const long long id = cid(g, sp->i0 + (b & 1), sp->j0 + (b >> 1 & 1), sp->k0 + (b >> 2));
+    const float dr = S.v[0][id], dm[3] = {S.v[1][id], S.v[2][id], S.v[3][id]};
+    float ir, up[3], pp;
+    pert_prim(c, dr, dm, S.v[4][id], ir, up, pp);
+    const float wb = (float)sp->w[b];
+    q[0] = wb * pp;
+    q[1] = wb * up[0];
+    q[2] = wb * up[1];
+    q[3] = wb * up[2];
+    q[4] = wb * ((pp * c.ipinf - dr) * ir);
+  }
+  for (int o = 4; o > 0; o >>= 1)
+    for (int v = 0; v < 5; v++) q[v] += __shfl_xor_sync(0xffffffffu, q[v], o);
+  if (!live || b != 0 || mask == 0) return;
+  const float ratio = (float)(sp->xi_node / sp->xi_probe);
+  const float pp = q[0], Tp = q[4];
+  const float dr = (pp * c.ipinf - Tp) * __fdividef(1.0f, 1.0f + Tp);  // rho - 1 = (p / p_inf) / (1 + T') - 1
+  float out[5], k = 0.0f;
+  out[0] = dr;
+  for (int a = 0; a < 3; a++) {
+    const float up = ratio * (c.u0[a] + q[1 + a]) - c.u0[a];
+    out[1 + a] = up + dr * (c.u0[a] + up);  // rho u - U_inf
+    k += up * (2.0f * c.u0[a] + up);
+  }
+  out[4] = pp * c.igm1 + 0.5f * ((1.0f + dr) * k + dr * c.u2);
+  const int node = sp->node;
+  const long long id = cid(g, node % g.nx, (node / g.nx) % g.ny, node / (g.nx * g.ny));
+  for (int v = 0; v < 5; v++) S.v[v][id] = out[v];
+  if (master)
+    for (int v = 0; v < 5; v++) A.v[v][id] = ph.Uinf[v] + (double)out[v];
+}
+
+// domain halos of an FP32 stage set (perturbations: the free stream is 0), the FP64 kernel's closed form
+__global__ void __launch_bounds__(TB) k3_halo32(Grid3 g, F5f U) {
+  const int t = blockIdx.x * TB + threadIdx.x;
+  const int nzs = 2 * NG * g.W * g.H, nys = 2 * NG * g.nz * g.W, nxs = 2 * NG * g.nz * g.ny;
+  int x, y, z;
+  if (t < nzs) {
+    const int zz = t / (g.W * g.H), rem = t - zz * (g.W * g.H);
+    z = zz < NG ? zz : g.nz + zz;
+    y = rem / g.W;
+    x = rem - y * g.W;
+  } else if (t < nzs + nys) {
+    const int u = t - nzs, zz = u / (2 * NG * g.W), rem = u - zz * (2 * NG * g.W), yy = rem / g.W;
+    z = NG + zz;
+    y = yy < NG ? yy : g.ny + yy;
+    x = rem - yy * g.W;
+  } else if (t < nzs + nys + nxs) {
+    const int u = t - nzs - nys, zz = u / (2 * NG * g.ny), rem = u - zz * (2 * NG * g.ny), yy = rem / (2 * NG);
+    const int xx = rem - yy * (2 * NG);
+    z = NG + zz;
+    y = NG + yy;
+    x = xx < NG ? xx : g.nx + xx;
+  } else {
+    return;
+  }
+  const long long m = ((long long)z * g.H + y) * g.W + x;
+  const int I[3] = {x - NG, y - NG, z - NG};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  int S[3];
+  bool fs = false;
+  for (int a = 0; a < 3; a++) {
+    S[a] = I[a];
+    if (I[a] >= 0 && I[a] < n[a]) continue;
+    const int bc = g.bc[2 * a + (I[a] < 0 ? 0 : 1)];
+    if (bc == IBM_BC_PERIODIC) S[a] = I[a] < 0 ? I[a] + n[a] : I[a] - n[a];
+    else if (bc == IBM_BC_OUTFLOW) S[a] = I[a] < 0 ? 0 : n[a] - 1;
+    else fs = true;
+  }
+  if (fs) {
+    for (int v = 0; v < 5; v++) U.v[v][m] = 0.0f;
+  } else {
+    const long long src = cid(g, S[0], S[1], S[2]);
+    for (int v = 0; v < 5; v++) U.v[v][m] = U.v[v][src];
+  }
 }
 
 __device__ __forceinline__ float weno5f(float f0, float f1, float f2, float f3, float f4) {
@@ -552,8 +661,7 @@ __global__ void __launch_bounds__(TC) k3_flux32(Grid3 g, P32 c, F6f Q, F5f Fo) {
   if (c.mu > 0.0f) {
     const int t1 = DIR == 0 ? 1 : 0, t2 = DIR == 2 ? 1 : 2;
     const long long s1 = t1 == 0 ? 1 : (long long)g.W, s2 = t2 == 1 ? (long long)g.W : g.plane;
-    const float ih[3] = {(float)g.idx, (float)g.idy, (float)g.idz};
-    const float in = ih[DIR], i1 = 0.25f * ih[t1], i2 = 0.25f * ih[t2];
+    const float in = c.ih[DIR], i1 = 0.25f * c.ih[t1], i2 = 0.25f * c.ih[t2];
     float G[3][3];
     for (int cc = 0; cc < 3; cc++) {
       const float *q = Q.v[1 + cc];
@@ -576,29 +684,50 @@ __global__ void __launch_bounds__(TC) k3_flux32(Grid3 g, P32 c, F6f Q, F5f Fo) {
   for (int v = 0; v < 5; v++) Fo.v[v][a] = F[v];
 }
 
-// SSP-RK3 stage on the fluid cells from the FP32 flux divergence (L(rho E) = L' + H_inf L(rho)): the stage
-// increment over Un in FP32 -- dt L, (In - Un + dt L) / 4, 2 (In - Un + dt L) / 3 -- accumulated onto the FP64 Un
-__global__ void __launch_bounds__(TC) k3_update32(Grid3 g, float Hinf, int stage, F5f Fx, F5f Fy, F5f Fz, F5 Un,
-                                                  F5 In, F5 Out, const uint8_t *__restrict__ tags,
+// SSP-RK3 stages 1 and 2 on the fluid cells in FP32 from the flux divergence (L(rho E) = L' + H_inf L(rho)),
+// on perturbations: out = M + dt L, M + ((In - M) + dt L) / 4, with M the mirror of U^n
+__device__ __forceinline__ void flux_div32(const Grid3 &g, const P32 &c, const F5f &Fx, const F5f &Fy, const F5f &Fz,
+                                           long long m, float L[5]) {
+  const float ix = c.ih[0], iy = c.ih[1], iz = c.ih[2], Hinf = c.Hinf;
+  for (int v = 0; v < 5; v++)
+    L[v] = -((Fx.v[v][m] - Fx.v[v][m - 1]) * ix + (Fy.v[v][m] - Fy.v[v][m - g.W]) * iy +
+             (Fz.v[v][m] - Fz.v[v][m - g.plane]) * iz);
+  L[4] += Hinf * L[0];
+}
+
+__global__ void __launch_bounds__(TC) k3_update32(Grid3 g, P32 c, int stage, F5f Fx, F5f Fy, F5f Fz, F5f M,
+                                                  F5f In, F5f Out, const uint8_t *__restrict__ tags,
                                                   const double *__restrict__ dtp) {
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= g.nx || j >= g.ny) return;
   if (tags[((long long)k * g.ny + j) * g.nx + i] != TAG_FLUID) return;
   const long long m = cid(g, i, j, k);
   const float dt = (float)*dtp;
-  const float ix = (float)g.idx, iy = (float)g.idy, iz = (float)g.idz;
   float L[5];
-  for (int v = 0; v < 5; v++)
-    L[v] = -((Fx.v[v][m] - Fx.v[v][m - 1]) * ix + (Fy.v[v][m] - Fy.v[v][m - g.W]) * iy +
-             (Fz.v[v][m] - Fz.v[v][m - g.plane]) * iz);
-  L[4] += Hinf * L[0];
+  flux_div32(g, c, Fx, Fy, Fz, m, L);
   for (int v = 0; v < 5; v++) {
-    const double un = Un.v[v][m];
-    float d;
-    if (stage == 1) d = dt * L[v];
-    else if (stage == 2) d = 0.25f * ((float)(In.v[v][m] - un) + dt * L[v]);
-    else d = (2.0f / 3.0f) * ((float)(In.v[v][m] - un) + dt * L[v]);
-    Out.v[v][m] = un + (double)d;
+    const float mv = M.v[v][m];
+    Out.v[v][m] = stage == 1 ? mv + dt * L[v] : mv + 0.25f * ((In.v[v][m] - mv) + dt * L[v]);
+  }
+}
+
+// SSP-RK3 stage 3: the increment 2/3 ((In - M) + dt L) in FP32, accumulated onto the FP64 master, whose new
+// value refreshes the mirror
+__global__ void __launch_bounds__(TC) k3_update32_last(Grid3 g, Phys3 ph, P32 c, F5f Fx, F5f Fy, F5f Fz, F5 A,
+                                                       F5f M, F5f In, const uint8_t *__restrict__ tags,
+                                                       const double *__restrict__ dtp) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  if (tags[((long long)k * g.ny + j) * g.nx + i] != TAG_FLUID) return;
+  const long long m = cid(g, i, j, k);
+  const float dt = (float)*dtp;
+  float L[5];
+  flux_div32(g, c, Fx, Fy, Fz, m, L);
+  for (int v = 0; v < 5; v++) {
+    const float d = (2.0f / 3.0f) * ((In.v[v][m] - M.v[v][m]) + dt * L[v]);
+    const double a = A.v[v][m] + (double)d;
+    A.v[v][m] = a;
+    M.v[v][m] = (float)(a - ph.Uinf[v]);
   }
 }
 
@@ -633,6 +762,10 @@ struct ibm_case3d {
   int precision = IBM_PREC_FP64;
   P32 p32{};
   double Hinf = 0.0;
+  // FP32-bulk views into the storage of the FP64 stage, primitive and flux arrays: the mirror of the master
+  // and the two intermediate stage sets (perturbations), primitives, face fluxes
+  F5f mirror{}, s1{}, s2{}, fx32{}, fy32{}, fz32{};
+  F6f q32{};
   int64_t launches = 0;
 };
 
@@ -707,6 +840,13 @@ extern "C" ibm_status ibm_case3d_create(const double *verts, int nverts, const i
   c->Hinf = fl->gamma / (fl->gamma - 1.0) * ph.pinf + 0.5 * (u * u + v * v + w * w);
   c->p32.pinf = (float)ph.pinf;
   c->p32.ipinf = (float)(1.0 / ph.pinf);
+  c->p32.igm1 = (float)(1.0 / (fl->gamma - 1.0));
+  c->p32.u2 = (float)(u * u + v * v + w * w);
+  c->p32.Hinf = (float)c->Hinf;
+  c->p32.ih[0] = (float)g.idx;
+  c->p32.ih[1] = (float)g.idy;
+  c->p32.ih[2] = (float)g.idz;
+  c->p32.ih2 = (float)(g.idx * g.idx + g.idy * g.idy + g.idz * g.idz);
   c->p32.ipr = (float)(1.0 / fl->prandtl);
   c->p32.gamma = (float)fl->gamma;
   c->p32.gg = (float)(fl->gamma / (fl->gamma - 1.0));
@@ -795,6 +935,24 @@ extern "C" ibm_status ibm_case3d_create(const double *verts, int nverts, const i
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // fsv is reused
     }
   }
+  for (int v = 0; v < 5; v++) {
+    c->mirror.v[v] = (float *)c->B.v[v];
+    c->s2.v[v] = (float *)c->B.v[v] + g.ncell;
+    c->s1.v[v] = (float *)c->C.v[v];
+    c->fx32.v[v] = (float *)c->Fx.v[v];
+    c->fy32.v[v] = (float *)c->Fy.v[v];
+    c->fz32.v[v] = (float *)c->Fz.v[v];
+  }
+  for (int v = 0; v < 6; v++) c->q32.v[v] = (float *)c->Q.v[v];
+  if (e == cudaSuccess && c->precision == IBM_PREC_FP32_BULK) {
+    // all three FP32 sets start as the master's perturbation (solid cells away from the body keep it)
+    const dim3 ball = cells(g.W, g.H, g.D);
+    k3_mirror32<<<ball, CB, 0, c->stream>>>(g, ph, c->A, c->mirror);
+    k3_mirror32<<<ball, CB, 0, c->stream>>>(g, ph, c->A, c->s1);
+    k3_mirror32<<<ball, CB, 0, c->stream>>>(g, ph, c->A, c->s2);
+    c->launches += 3;
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->time, 0, 256, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->nerr, 0, 256, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->lmax, 0, 256, c->stream);
@@ -873,48 +1031,54 @@ extern "C" ibm_status ibm_case3d_step(ibm_case3d *c, int nsteps) {
   const Phys3 &ph = c->ph;
   const int nib = c->counts[0], ngh = c->counts[1] + c->counts[2] + c->counts[3];
   cudaStream_t s = c->stream;
+  const bool f32 = c->precision == IBM_PREC_FP32_BULK;
+  const dim3 bx = cells(g.nx + 1, g.ny, g.nz), by = cells(g.nx, g.ny + 1, g.nz), bz = cells(g.nx, g.ny, g.nz + 1);
+  const dim3 ball = cells(g.W, g.H, g.D), bint = cells(g.nx, g.ny, g.nz);
+  const unsigned bhalo = nblk(2LL * NG * ((long long)g.W * g.H + (long long)g.nz * g.W + (long long)g.nz * g.ny));
+  // eight lanes per listed node (one cube corner each), 16 nodes per block
+  const unsigned bib = (unsigned)((nib + 15) / 16), bgh = (unsigned)((ngh + 15) / 16);
   for (int it = 0; it < nsteps; it++) {
-    const bool f32 = c->precision == IBM_PREC_FP32_BULK;
     if (ph.dt_fixed <= 0.0) {
       cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), s);
-      if (f32) k3_lambda32<<<cells(g.nx, g.ny, g.nz), CB, 0, s>>>(g, ph, c->p32, c->A, c->tags, c->lmax);
-      else k3_lambda<<<cells(g.nx, g.ny, g.nz), CB, 0, s>>>(g, ph, c->A, c->tags, c->lmax);
+      if (f32) k3_lambda32<<<cells(g.nx, g.ny, std::min(g.nz, 8)), CB, 0, s>>>(g, c->p32, c->mirror, c->tags, c->lmax);
+      else k3_lambda<<<bint, CB, 0, s>>>(g, ph, c->A, c->tags, c->lmax);
       c->launches++;
     }
     k3_dt<<<1, 1, 0, s>>>(ph, c->lmax, c->dt);
     c->launches++;
-    F5 in[3] = {c->A, c->B, c->C}, out[3] = {c->B, c->C, c->A};
-    for (int k = 0; k < 3; k++) {
-      // eight lanes per listed node (one cube corner each)
-      if (nib) k3_reconstruct<<<(nib + 15) / 16, 128, 0, s>>>(g, ph, in[k], c->st, 0, nib);
-      if (ngh) k3_reconstruct<<<(ngh + 15) / 16, 128, 0, s>>>(g, ph, in[k], c->st, nib, ngh);
-      k3_halo<<<nblk(2LL * NG * ((long long)g.W * g.H + (long long)g.nz * g.W + (long long)g.nz * g.ny)), TB, 0, s>>>(
-          g, ph, in[k]);
-      const dim3 bx = cells(g.nx + 1, g.ny, g.nz), by = cells(g.nx, g.ny + 1, g.nz), bz = cells(g.nx, g.ny, g.nz + 1);
-      const dim3 ball = cells(g.W, g.H, g.D), bint = cells(g.nx, g.ny, g.nz);
-      if (f32) {
-        // the FP32 arrays live in the FP64 primitive and flux arrays' storage
-        F6f q;
-        F5f fx, fy, fz;
-        for (int v = 0; v < 6; v++) q.v[v] = (float *)c->Q.v[v];
-        for (int v = 0; v < 5; v++) {
-          fx.v[v] = (float *)c->Fx.v[v];
-          fy.v[v] = (float *)c->Fy.v[v];
-          fz.v[v] = (float *)c->Fz.v[v];
-        }
-        k3_prim32<<<ball, CB, 0, s>>>(g, ph, c->p32, in[k], q);
-        k3_flux32<0><<<bx, CB, 0, s>>>(g, c->p32, q, fx);
-        k3_flux32<1><<<by, CB, 0, s>>>(g, c->p32, q, fy);
-        k3_flux32<2><<<bz, CB, 0, s>>>(g, c->p32, q, fz);
-        k3_update32<<<bint, CB, 0, s>>>(g, (float)c->Hinf, k + 1, fx, fy, fz, c->A, in[k], out[k], c->tags, c->dt);
-      } else {
+    if (f32) {
+      // FP32 stage sets: the mirror M of U^n, U^1, U^2 (perturbations); FP64 only in the last stage's
+      // accumulation onto the master
+      const F5f in[3] = {c->mirror, c->s1, c->s2};
+      for (int k = 0; k < 3; k++) {
+        if (nib) k3_reconstruct32<<<bib, 128, 0, s>>>(g, ph, c->p32, in[k], c->st, 0, nib, c->A, k == 0);
+        if (ngh) k3_reconstruct32<<<bgh, 128, 0, s>>>(g, ph, c->p32, in[k], c->st, nib, ngh, c->A, k == 0);
+        k3_halo32<<<bhalo, TB, 0, s>>>(g, in[k]);
+        k3_prim32<<<ball, CB, 0, s>>>(g, c->p32, in[k], c->q32);
+        k3_flux32<0><<<bx, CB, 0, s>>>(g, c->p32, c->q32, c->fx32);
+        k3_flux32<1><<<by, CB, 0, s>>>(g, c->p32, c->q32, c->fy32);
+        k3_flux32<2><<<bz, CB, 0, s>>>(g, c->p32, c->q32, c->fz32);
+        if (k < 2)
+          k3_update32<<<bint, CB, 0, s>>>(g, c->p32, k + 1, c->fx32, c->fy32, c->fz32, c->mirror, in[k],
+                                          k == 0 ? c->s1 : c->s2, c->tags, c->dt);
+        else
+          k3_update32_last<<<bint, CB, 0, s>>>(g, ph, c->p32, c->fx32, c->fy32, c->fz32, c->A, c->mirror,
+                                               in[k], c->tags, c->dt);
+        c->launches += 6 + (nib ? 1 : 0) + (ngh ? 1 : 0);
+      }
+    } else {
+      F5 in[3] = {c->A, c->B, c->C}, out[3] = {c->B, c->C, c->A};
+      for (int k = 0; k < 3; k++) {
+        if (nib) k3_reconstruct<<<bib, 128, 0, s>>>(g, ph, in[k], c->st, 0, nib);
+        if (ngh) k3_reconstruct<<<bgh, 128, 0, s>>>(g, ph, in[k], c->st, nib, ngh);
+        k3_halo<<<bhalo, TB, 0, s>>>(g, ph, in[k]);
         k3_prim<<<ball, CB, 0, s>>>(g, ph, in[k], c->Q);
         k3_flux<0><<<bx, CB, 0, s>>>(g, ph, c->Q, c->Fx);
         k3_flux<1><<<by, CB, 0, s>>>(g, ph, c->Q, c->Fy);
         k3_flux<2><<<bz, CB, 0, s>>>(g, ph, c->Q, c->Fz);
         k3_update<<<bint, CB, 0, s>>>(g, k + 1, c->Fx, c->Fy, c->Fz, c->A, in[k], out[k], c->tags, c->dt);
+        c->launches += 6 + (nib ? 1 : 0) + (ngh ? 1 : 0);
       }
-      c->launches += 6 + (nib ? 1 : 0) + (ngh ? 1 : 0);
     }
     k3_step_end<<<1, 1, 0, s>>>(c->dt, c->time);
     c->launches++;
@@ -984,6 +1148,11 @@ extern "C" ibm_status ibm_case3d_set_state(ibm_case3d *c, const void *src, size_
     prm.extent = make_cudaExtent((size_t)g.nx * sizeof(double), g.ny, g.nz);
     prm.kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     e = cudaMemcpy3DAsync(&prm, c->stream);
+  }
+  if (e == cudaSuccess && c->precision == IBM_PREC_FP32_BULK) {
+    k3_mirror32<<<cells(g.W, g.H, g.D), CB, 0, c->stream>>>(g, c->ph, c->A, c->mirror);
+    c->launches++;
+    e = cudaGetLastError();
   }
   if (e == cudaSuccess && !src_on_device) e = cudaStreamSynchronize(c->stream);
   return e == cudaSuccess ? IBM_OK : cfail(e);
