@@ -353,10 +353,11 @@ typedef struct {
   double uinf[3];   /* free-stream velocity in reference-speed units */
   double dt_fixed;  /* > 0: fixed time step, else the CFL rule */
   double ref_area;  /* force normalisation area (> 0) */
-  int precision;    /* IBM_PREC_FP64, or IBM_PREC_FP32_BULK: the face fluxes in FP32 on perturbations from the
-                       free stream (rho - 1, u - U_inf, p - p_inf, T - 1; the pressure flux less p_inf and the
-                       energy equation in rho E - rho H_inf, so that no free-stream constant enters an FP32 sum),
-                       the stage combination, IB / ghost reconstruction, halos and dt in FP64 */
+  int precision;    /* IBM_PREC_FP64, or IBM_PREC_FP32_BULK: stage values, IB / ghost reconstruction, halos, CFL
+                       bound and fluxes in FP32 on perturbations from the free stream (rho - 1, u - U_inf,
+                       p - p_inf, T - 1; the pressure flux less p_inf and the energy equation in rho E - rho H_inf,
+                       so that no free-stream constant enters an FP32 sum), each step's increment accumulated onto
+                       an FP64 master (the state that ibm_case3d_get returns and the forces read) */
 } ibm_flow3d;
 
 /* one IB or ghost node of the 3-D case and its stencil */

@@ -377,12 +377,14 @@ __global__ void k3_step_end(const double *__restrict__ dtp, double *__restrict__
   time[1] = dt;
 }
 
-// ---- FP32-bulk stages: the face fluxes in FP32 on perturbations from the free stream --------------------------
-// The FP64 stage state is turned into FP32 perturbation primitives (rho', u', v', w', p', T') = (rho - 1,
-// u - U_inf, ..., p - p_inf, T - 1); the fluxes are assembled so that no free-stream constant enters an FP32
-// sum: the pressure term as (p_half - p_inf) = p_inf (D_L + D_R - 1) + D_L p'_L + D_R p'_R, and the energy
-// equation in the variable rho E - rho H_inf, whose flux is rho u H' (H' = H - H_inf); the update restores
-// L(rho E) = L' + H_inf L(rho) and combines the stages in FP64.
+// ---- FP32-bulk stages: values and fluxes in FP32 on perturbations from the free stream ------------------------
+// The stage values are FP32 conserved perturbations U - U_inf: a mirror of the FP64 master U^n and the two
+// intermediate stages.  Reconstruction, halos (the free stream is 0), primitives (rho', u', v', w', p', T') =
+// (rho - 1, u - U_inf, ..., p - p_inf, T - 1), the CFL bound and the first two updates run in FP32; the fluxes
+// are assembled so that no free-stream constant enters an FP32 sum: the pressure term as (p_half - p_inf) =
+// p_inf (D_L + D_R - 1) + D_L p'_L + D_R p'_R, and the energy equation in the variable rho E - rho H_inf, whose
+// flux is rho u H' (H' = H - H_inf); the updates restore L(rho E) = L' + H_inf L(rho).  FP64 appears only in the
+// last stage, which accumulates its FP32 increment onto the master and refreshes the mirror from it.
 
 struct P32 {
   float pinf, ipinf, gamma, gg, igm1, mu, kappa, ipr, u0[3], u2;  // gg = gamma / (gamma - 1), igm1 = 1 / (gamma - 1),
