@@ -34,7 +34,9 @@
  *   3-D residual + RK3   pinned: a field constant along one axis reproduces the 2-D oracle bit for bit in each
  *                        of the three coordinate planes (oracle3d.c)
  *   3-D IB / ghost       pinned: linear profiles at axis-aligned and oblique plane walls, quiescent sphere
- *   3-D forces           pinned: linear pressure field on a closed polyhedron (divergence theorem, Eq. 9)
+ *   3-D forces           pinned: linear pressure and velocity fields on a closed box (per-triangle closed form),
+ *                        uniform pressure on the sphere (closed surface, Eq. 9)
+ *   3-D CFL rule         pinned: closed form on a uniform state
  */
 #ifndef IBM_ORACLE_H
 #define IBM_ORACLE_H

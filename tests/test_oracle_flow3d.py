@@ -289,3 +289,19 @@ def test_forces_vanish_in_uniform_pressure(orc):
     c.set_state(np.stack([1.3 * one, 0 * one, 0 * one, 0 * one, 1.3 * pinf / (g - 1.0) * one]))
     F = c.forces()
     assert np.abs(F[3:]).max() < 1e-12 * pinf
+
+
+def test_cfl_rule_in_closed_form(orc):
+    """The CFL rule of the 3-D oracle on a uniform state (periodic box, so the state stays uniform):
+    dt = CFL / ((|u|+c)/dx + (|v|+c)/dy + (|w|+c)/dz + 2 gamma mu / (Pr rho) (1/dx^2 + 1/dy^2 + 1/dz^2)), the rule
+    written out here from the formula with c = sqrt(gamma p / rho) = 1 / M (free stream: rho = T = 1)."""
+    n, lo, hi, mach, re, cfl, uinf = (10, 7, 6), (0.0, -1.0, 0.5), (2.0, 0.4, 1.7), 0.4, 80.0, 0.45, (0.7, -0.5, 0.3)
+    spec = W.case3d_spec(None, None, n, lo, hi, mach, re, (PER,) * 6, uinf=uinf, cfl=cfl)
+    c = orc.Case3D(spec)
+    c.step(1)
+    d = [(hi[a] - lo[a]) / n[a] for a in range(3)]
+    cs = 1.0 / mach
+    lam = sum((abs(uinf[a]) + cs) / d[a] for a in range(3)) + \
+        (2.0 * 1.4 * (1.0 / re) / 0.72) * sum(1.0 / (d[a] * d[a]) for a in range(3))
+    assert abs(c.last_dt() - cfl / lam) <= 1e-14 * (cfl / lam)
+    assert abs(c.time() - cfl / lam) <= 1e-14 * (cfl / lam)
