@@ -97,37 +97,127 @@ __device__ __forceinline__ int crosses(const Mesh &m, int f, const double P[3], 
   return ((num > 0.0 && n[axis] > 0.0) || (num < 0.0 && n[axis] < 0.0)) ? 1 : 0;
 }
 
-// classification: one warp per node, lanes splitting the faces; three axis rays vote on the crossing parity
-__global__ void __launch_bounds__(B3) k3_classify(Lattice L, Mesh m, uint8_t *__restrict__ solid) {
-  const long long nn = (long long)L.nx * L.ny * L.nz;
-  const int lane = threadIdx.x & 31;
+// classification along lattice lines: one warp per line along `axis`.  Whether the ray from a node crosses a
+// face depends on the face's edge functions at the line's two transverse coordinates, the same for every node of
+// the line; only "ahead of the node", the sign of n.(a - P), depends on the node.  So the warp collects the faces
+// the line crosses once (lanes splitting the faces, the FP32 box cull of the per-node test), then every node of
+// the line evaluates its own n.(a - P) over those faces -- the operations of testing every face from every node,
+// hence the same parity.  Passes over the three axes accumulate the parities in solid[] (pass 0 writes, pass 1
+// adds, pass 2 adds and writes the vote, >= 2 of 3, for nodes inside the surface's bounding box and 0 outside).
+// A line crossing more than HCAP faces takes the per-node test over all faces instead.
+constexpr int HCAP = 48;
+
+__global__ void __launch_bounds__(B3) k3_classify_lines(Lattice L, Mesh m, int axis, uint8_t *__restrict__ solid) {
+  __shared__ double hn[B3 / 32][HCAP][3], ha[B3 / 32][HCAP][3];  // per warp: normal and first vertex of each hit
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int u = axis == 0 ? 1 : (axis == 1 ? 2 : 0), v = axis == 0 ? 2 : (axis == 1 ? 0 : 1);
+  const int n[3] = {L.nx, L.ny, L.nz};
+  const long long nlines = (long long)n[u] * n[v];
   const long long warps = (long long)gridDim.x * (B3 / 32);
-  for (long long n = (long long)blockIdx.x * (B3 / 32) + (threadIdx.x >> 5); n < nn; n += warps) {
-    double P[3];
+  for (long long li = (long long)blockIdx.x * (B3 / 32) + warp; li < nlines; li += warps) {
     int ijk[3];
-    node_xyz(L, n, P, ijk);
-    if (P[0] < m.bb[0] || P[0] > m.bb[3] || P[1] < m.bb[1] || P[1] > m.bb[4] || P[2] < m.bb[2] || P[2] > m.bb[5]) {
-      if (lane == 0) solid[n] = 0;
-      continue;
-    }
-    // a face whose box (widened by the cull margin, FP32) misses the node's line along the ray cannot be
-    // crossed; the margin is far above FP32 rounding, so no face the exact test would count is skipped
-    const float pf[3] = {(float)P[0], (float)P[1], (float)P[2]};
-    int votes = 0;
-    for (int axis = 0; axis < 3; axis++) {
-      const int u = axis == 0 ? 1 : (axis == 1 ? 2 : 0), v = axis == 0 ? 2 : (axis == 1 ? 0 : 1);
-      unsigned h = 0;
-      for (int f = lane; f < m.ntri; f += 32) {
-        const float4 lo = __ldg(m.fbox + 2 * f), hi = __ldg(m.fbox + 2 * f + 1);
-        const float lu = u == 0 ? lo.x : (u == 1 ? lo.y : lo.z), hu = u == 0 ? hi.x : (u == 1 ? hi.y : hi.z);
-        const float lv = v == 0 ? lo.x : (v == 1 ? lo.y : lo.z), hv = v == 0 ? hi.x : (v == 1 ? hi.y : hi.z);
-        const float ha = axis == 0 ? hi.x : (axis == 1 ? hi.y : hi.z);  // a face wholly behind the node is skipped
-        if (pf[u] < lu || pf[u] > hu || pf[v] < lv || pf[v] > hv || pf[axis] > ha) continue;
-        h += (unsigned)crosses(m, f, P, axis);
+    ijk[u] = (int)(li % n[u]);
+    ijk[v] = (int)(li / n[u]);
+    double P[3];
+    P[u] = L.lo[u] + ((double)ijk[u] + 0.5) * L.d[u];
+    P[v] = L.lo[v] + ((double)ijk[v] + 0.5) * L.d[v];
+    P[axis] = L.lo[axis];
+    const bool line_in = !(P[u] < m.bb[u] || P[u] > m.bb[3 + u] || P[v] < m.bb[v] || P[v] > m.bb[3 + v]);
+    int cnt = 0;
+    if (line_in) {
+      const float pu = (float)P[u], pv = (float)P[v];
+      for (int f0 = 0; f0 < m.ntri; f0 += 32) {
+        const int f = f0 + lane;
+        bool hit = false;
+        double nf[3] = {0.0, 0.0, 0.0}, af[3] = {0.0, 0.0, 0.0};
+        if (f < m.ntri) {
+          const float4 lo = __ldg(m.fbox + 2 * f), hi = __ldg(m.fbox + 2 * f + 1);
+          const float lu = u == 0 ? lo.x : (u == 1 ? lo.y : lo.z), hu = u == 0 ? hi.x : (u == 1 ? hi.y : hi.z);
+          const float lv = v == 0 ? lo.x : (v == 1 ? lo.y : lo.z), hv = v == 0 ? hi.x : (v == 1 ? hi.y : hi.z);
+          if (!(pu < lu || pu > hu || pv < lv || pv > hv)) {
+            const int i0 = __ldg(m.tri + 3 * f), i1 = __ldg(m.tri + 3 * f + 1), i2 = __ldg(m.tri + 3 * f + 2);
+            double A[3], B[3], C[3];
+            for (int q = 0; q < 3; q++) {
+              A[q] = __ldg(m.v + 3 * i0 + q);
+              B[q] = __ldg(m.v + 3 * i1 + q);
+              C[q] = __ldg(m.v + 3 * i2 + q);
+            }
+            const int s0 = edge_sign(A, i0, B, i1, P, u, v);
+            const int s1 = edge_sign(B, i1, C, i2, P, u, v);
+            const int s2 = edge_sign(C, i2, A, i0, P, u, v);
+            if (s0 != 0 && s0 == s1 && s1 == s2) {
+              const double e1[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+              const double e2[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+              nf[0] = e1[1] * e2[2] - e1[2] * e2[1];
+              nf[1] = e1[2] * e2[0] - e1[0] * e2[2];
+              nf[2] = e1[0] * e2[1] - e1[1] * e2[0];
+              hit = nf[axis] != 0.0;
+              for (int q = 0; q < 3; q++) af[q] = A[q];
+            }
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
+          if (slot < HCAP)
+            for (int q = 0; q < 3; q++) {
+              hn[warp][slot][q] = nf[q];
+              ha[warp][slot][q] = af[q];
+            }
+        }
+        cnt += __popc(bal);
       }
-      votes += (int)(__reduce_add_sync(0xffffffffu, h) & 1u);
     }
-    if (lane == 0) solid[n] = (uint8_t)(votes >= 2);
+    __syncwarp();
+    if (cnt <= HCAP) {
+      for (int t = lane; t < n[axis]; t += 32) {
+        ijk[axis] = t;
+        double Q[3] = {P[0], P[1], P[2]};
+        Q[axis] = L.lo[axis] + ((double)t + 0.5) * L.d[axis];
+        int par = 0;
+        for (int h = 0; h < cnt; h++) {
+          const double num = hn[warp][h][0] * (ha[warp][h][0] - Q[0]) + hn[warp][h][1] * (ha[warp][h][1] - Q[1]) +
+                             hn[warp][h][2] * (ha[warp][h][2] - Q[2]);
+          const double na = hn[warp][h][axis];
+          par += ((num > 0.0 && na > 0.0) || (num < 0.0 && na < 0.0)) ? 1 : 0;
+        }
+        const long long idx = ((long long)ijk[2] * L.ny + ijk[1]) * L.nx + ijk[0];
+        const bool inside = !(Q[0] < m.bb[0] || Q[0] > m.bb[3] || Q[1] < m.bb[1] || Q[1] > m.bb[4] ||
+                              Q[2] < m.bb[2] || Q[2] > m.bb[5]);
+        const uint8_t p1 = (uint8_t)(par & 1);
+        if (axis == 0) solid[idx] = p1;
+        else if (axis == 1) solid[idx] = (uint8_t)(solid[idx] + p1);
+        else solid[idx] = (uint8_t)(inside && solid[idx] + p1 >= 2);
+      }
+    } else {
+      // more crossings than the warp keeps: every node of the line tests every face (lanes splitting them)
+      const float pu = (float)P[u], pv = (float)P[v];
+      for (int t = 0; t < n[axis]; t++) {
+        ijk[axis] = t;
+        double Q[3] = {P[0], P[1], P[2]};
+        Q[axis] = L.lo[axis] + ((double)t + 0.5) * L.d[axis];
+        const float pa = (float)Q[axis];
+        unsigned h = 0;
+        for (int f = lane; f < m.ntri; f += 32) {
+          const float4 lo = __ldg(m.fbox + 2 * f), hi = __ldg(m.fbox + 2 * f + 1);
+          const float lu = u == 0 ? lo.x : (u == 1 ? lo.y : lo.z), hu = u == 0 ? hi.x : (u == 1 ? hi.y : hi.z);
+          const float lv = v == 0 ? lo.x : (v == 1 ? lo.y : lo.z), hv = v == 0 ? hi.x : (v == 1 ? hi.y : hi.z);
+          const float ha_ = axis == 0 ? hi.x : (axis == 1 ? hi.y : hi.z);
+          if (pu < lu || pu > hu || pv < lv || pv > hv || pa > ha_) continue;
+          h += (unsigned)crosses(m, f, Q, axis);
+        }
+        const int par = (int)(__reduce_add_sync(0xffffffffu, h) & 1u);
+        if (lane == 0) {
+          const long long idx = ((long long)ijk[2] * L.ny + ijk[1]) * L.nx + ijk[0];
+          const bool inside = !(Q[0] < m.bb[0] || Q[0] > m.bb[3] || Q[1] < m.bb[1] || Q[1] > m.bb[4] ||
+                                Q[2] < m.bb[2] || Q[2] > m.bb[5]);
+          if (axis == 0) solid[idx] = (uint8_t)par;
+          else if (axis == 1) solid[idx] = (uint8_t)(solid[idx] + par);
+          else solid[idx] = (uint8_t)(inside && solid[idx] + par >= 2);
+        }
+      }
+    }
+    __syncwarp();  // the hit list is rewritten by the warp's next line
   }
 }
 
@@ -755,8 +845,8 @@ extern "C" ibm_status ibm_body3d_classify(ibm_body3d *b, const ibm_grid3d *g) {
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int gw = nsm * 8;  // 8 blocks of 8 warps per SM, striding over the nodes
-  k3_classify<<<gw, B3, 0, b->stream>>>(L, b->m, b->solid);
+  const int gw = nsm * 8;  // 8 blocks of 8 warps per SM, striding over the lines (classification) or nodes
+  for (int axis = 0; axis < 3; axis++) k3_classify_lines<<<gw, B3, 0, b->stream>>>(L, b->m, axis, b->solid);
   k3_tags<<<b->nblk, CBLK, 0, b->stream>>>(L, b->solid, b->tags, b->blockcounts);
   k3_scan<<<1, 1024, 0, b->stream>>>(b->nblk, b->blockcounts, b->counts);
   k3_scatter<<<b->nblk, CBLK, 0, b->stream>>>(L, b->tags, b->blockcounts, b->counts, b->nodes, b->cap);
