@@ -475,7 +475,7 @@ def run_ours(args, rank, world):
             g3["%d^3" % n3] = {"ms": e0.elapsed_time(e1) / reps, "listed_nodes": int(b3.counts().sum())}
         b3.close()
         geo3d = {"workload": "Appendix A: UV sphere of 1200 triangles, radius 0.35, in n^3 lattice nodes over the unit "
-                             "cube", "kernels": "k3_classify, k3_tags, k3_scan, k3_scatter, k3_closest", "gpu": g3,
+                             "cube", "kernels": "k3_classify_lines (x3), k3_tags, k3_scan, k3_scatter, k3_closest", "gpu": g3,
                  "paper_table_a1_context": "4.296e-2 s for 40^3 nodes on one Xeon E5-2670 core (the paper's "
                                            "pre-processing; other hardware, context only)"}
 
