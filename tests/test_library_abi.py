@@ -157,3 +157,35 @@ def test_unknown_reconstruction_rejected(ibm):
         st = L.ibm_create_case(ctypes.byref(geo), ctypes.byref(gr), ctypes.byref(fl), ctypes.byref(mo), None,
                                ctypes.byref(h))
         assert st == ibm.IBM_EINVAL and not h.value, bad
+
+
+def test_case3d_arguments_rejected_before_device_work(ibm):
+    """ibm_case3d_create refuses malformed cases with IBM_EINVAL and returns no case, before any device call (so
+    this runs without a GPU): fewer than 4 cells along an axis, an unknown boundary condition, periodic on one
+    side of an axis only, an unknown precision, a non-positive Mach number or reference area, a mesh pointer
+    missing for a non-empty mesh."""
+    L = ibm.lib()
+    good = W.case3d_spec(None, None, (8, 8, 8), (0, 0, 0), (1, 1, 1), 0.3, 100.0, W.FAR3D)
+    bads = [dict(n=(3, 8, 8)), dict(bc=(0, 1, 0, 0, 0, 9)), dict(bc=(2, 1, 0, 0, 0, 0)), dict(precision=3),
+            dict(mach=0.0), dict(ref_area=0.0)]
+    for bad in bads:
+        s = dict(good, **bad)
+        f = ibm.ibm_flow3d()
+        f.nx, f.ny, f.nz = s["n"]
+        for a in range(3):
+            f.lo[a], f.hi[a], f.uinf[a] = s["lo"][a], s["hi"][a], s["uinf"][a]
+        for k in range(6):
+            f.bc[k] = s["bc"][k]
+        f.mach, f.re, f.gamma, f.prandtl, f.cfl = s["mach"], s["re"], s["gamma"], s["prandtl"], s["cfl"]
+        f.dt_fixed, f.ref_area, f.precision = s["dt_fixed"], s["ref_area"], s["precision"]
+        h = ctypes.c_void_p()
+        st = L.ibm_case3d_create(None, 0, None, 0, ctypes.byref(f), None, ctypes.byref(h))
+        assert st == ibm.IBM_EINVAL and not h.value, bad
+    f = ibm.ibm_flow3d()
+    f.nx = f.ny = f.nz = 8
+    for a in range(3):
+        f.lo[a], f.hi[a] = 0.0, 1.0
+    f.mach, f.gamma, f.prandtl, f.cfl, f.ref_area = 0.3, 1.4, 0.72, 0.5, 1.0
+    h = ctypes.c_void_p()
+    assert L.ibm_case3d_create(None, 8, None, 12, ctypes.byref(f), None, ctypes.byref(h)) == ibm.IBM_EINVAL
+    assert not h.value
